@@ -1,0 +1,94 @@
+"""Seeded synthetic supernodes.
+
+This module only draws random numbers and lays them out; it holds none of the
+method's arithmetic.  Both the CUDA path's tests and the oracle's tests take
+their inputs from here, so the two sides see identical matrices.
+
+A supernode is an n x p column-major float64 array (Section 1, eq. (1.1)):
+rows 0..p-1 hold A11 (symmetric; both triangles are filled here, only the lower
+one is read), rows p..n-1 hold A21.
+
+Workloads (shapes and value distributions of the paper's random experiments,
+Section 7.1, and of the build's configurations):
+  * ``single_small``: n=2000, p=64, N(0,1) entries, u = 0.01; eight A11
+    rows/columns scaled by 1e-8 (diagonal entry by 1e-16) to force delays.
+  * ``single_large``: n=200000, p=256, entries uniform in [-1, 1].
+  * ``batch``: 8192 supernodes, p log-uniform in [8, 256], n-p log-uniform in
+    [0, 16p] (drawn as floor(exp(U(0, ln(16p+1)))) - 1), N(0,1) entries with 2%
+    of the A11 diagonal set to zero.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def supernode(n, p, seed=0, dist="normal", scale_cols=0, scale=1e-8, zero_diag_frac=0.0,
+              diag_boost=0.0):
+    """One n x p supernode.  ``dist`` is ``normal`` (N(0,1)) or ``uniform`` (U[-1,1]).
+    ``scale_cols`` A11 rows/columns (chosen by the seeded generator) are scaled by
+    ``scale``; a fraction ``zero_diag_frac`` of the A11 diagonal is set to zero;
+    ``diag_boost`` adds boost*sign(a_jj) to each diagonal entry."""
+    rng = np.random.default_rng(seed)
+    if dist == "normal":
+        A = rng.standard_normal((n, p))
+    elif dist == "uniform":
+        A = rng.uniform(-1.0, 1.0, (n, p))
+    else:
+        raise ValueError(dist)
+    A = np.asfortranarray(A)
+    # symmetric A11 from the lower triangle that was drawn
+    A11 = np.tril(A[:p, :p])
+    A[:p, :p] = A11 + np.tril(A11, -1).T
+    if scale_cols:
+        idx = rng.choice(p, size=min(scale_cols, p), replace=False)
+        for j in idx:
+            A[:p, j] *= scale
+            A[j, :p] *= scale
+    if zero_diag_frac > 0.0:
+        nz = int(round(zero_diag_frac * p))
+        if nz > 0:
+            idx = rng.choice(p, size=nz, replace=False)
+            A[idx, idx] = 0.0
+    if diag_boost:
+        d = np.arange(p)
+        A[d, d] += diag_boost * np.where(A[d, d] >= 0, 1.0, -1.0)
+    return A
+
+
+def single_small(seed=0):
+    return supernode(2000, 64, seed=seed, dist="normal", scale_cols=8, scale=1e-8)
+
+
+def single_large(seed=0, n=200000, p=256):
+    return supernode(n, p, seed=seed, dist="uniform")
+
+
+def batch_shapes(count=8192, seed=0, pmin=8, pmax=256, ratio=16):
+    """(n, p) pairs of the uneven batch: p log-uniform in [pmin, pmax], n-p
+    log-uniform in [0, ratio*p]."""
+    rng = np.random.default_rng(seed)
+    p = np.floor(np.exp(rng.uniform(np.log(pmin), np.log(pmax + 1), count))).astype(np.int64)
+    p = np.clip(p, pmin, pmax)
+    m = np.floor(np.exp(rng.uniform(0.0, np.log(ratio * p + 1.0)))).astype(np.int64) - 1
+    m = np.clip(m, 0, ratio * p)
+    return np.stack([p + m, p], axis=1)
+
+
+def batch(count=8192, seed=0, pmin=8, pmax=256, ratio=16, zero_diag_frac=0.02):
+    """List of supernodes of the uneven batch (N(0,1), 2% zero diagonals)."""
+    shapes = batch_shapes(count, seed, pmin, pmax, ratio)
+    return [supernode(int(n), int(p), seed=seed * 1_000_003 + k + 1, dist="normal",
+                      zero_diag_frac=zero_diag_frac) for k, (n, p) in enumerate(shapes)]
+
+
+def symmetric(n, seed=0, dist="normal"):
+    """Dense symmetric n x n matrix (both triangles)."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, n)) if dist == "normal" else rng.uniform(-1, 1, (n, n))
+    L = np.tril(X)
+    return np.asfortranarray(L + np.tril(L, -1).T)
+
+
+def rhs(n, k=1, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.asfortranarray(rng.standard_normal((n, k)))
