@@ -1,0 +1,150 @@
+/*
+ * ctp.h -- C ABI of libctp: compressed threshold pivoting for supernodal LDL^T
+ * on NVIDIA GB300 (sm_103a).
+ *
+ * Method: J. D. Hogg and J. A. Scott, "Compressed threshold pivoting for sparse
+ * symmetric indefinite systems", arXiv 1305.2353.  Section numbers below refer
+ * to that paper.
+ *
+ * A supernode (Section 1, eq. (1.1)) is a dense n x p trapezoid A = [A11; A21]:
+ * A11 is p x p symmetric (only its lower triangle is read), A21 is (n-p) x p.
+ * All matrices are column-major double precision with leading dimension
+ * lda >= n.  m = n - p is the number of A21 rows, e = nelim the number of
+ * eliminated columns, d = p - e the number of delayed columns.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named d_* (and A, C, S, D, perm, piv, nelim, workspace) are
+ *    DEVICE pointers owned by the caller; pointers named *_host are host
+ *    pointers.  The library never frees caller memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every entry
+ *    point only enqueues work on it and returns without synchronising, except
+ *    where stated ("synchronises").
+ *  - Argument errors detected on the host return CTP_EINVAL (or
+ *    CTP_EUNSUPPORTED) before anything is launched.  Conditions found on the
+ *    device (non-finite input, a bounded wait that ran out) are recorded in the
+ *    info word at the start of the workspace and read back by ctp_read_info().
+ *    No kernel traps.
+ *  - The workspace is caller-allocated device memory of at least the size
+ *    returned by ctp_workspace_size(), 256-byte aligned.
+ */
+#ifndef CTP_H
+#define CTP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CTP_OK = 0,
+    CTP_EINVAL = 1,       /* bad argument (null pointer, n < p, lda < n, u not in (0, 0.5], ...) */
+    CTP_ENOMEM = 2,       /* workspace too small */
+    CTP_ECUDA = 3,        /* a CUDA runtime call failed */
+    CTP_ENONFINITE = 4,   /* device: an input entry was Inf or NaN */
+    CTP_ETIMEOUT = 5,     /* device: a bounded wait gave up */
+    CTP_ECAPACITY = 6,    /* device: a size limit was exceeded */
+    CTP_EUNSUPPORTED = 7  /* valid request this build does not handle (e.g. p above the limit) */
+} ctp_status;
+
+/* Pivoting strategy. */
+typedef enum {
+    CTP_PIV_STRICT = 0,     /* strict compressed pivoting, Section 4.1 (eq. (4.1), eq. (4.3)) */
+    CTP_PIV_RELAXED = 1,    /* relaxed compressed pivoting, Section 4.2 */
+    CTP_PIV_TPP = 2,        /* threshold partial pivoting on all n rows, Listing 1 (Section 2) */
+    CTP_PIV_RESTRICTED = 3  /* restricted pivoting: tests look at A11 only, Section 3.2 */
+} ctp_pivot;
+
+/* Arithmetic of the Solve and Form steps.  Pivot selection, the 2x2 pivot
+ * inversions and D11 are always FP64. */
+typedef enum {
+    CTP_FP64 = 0,  /* FP64 throughout */
+    CTP_BF16 = 1   /* Form on the tensor cores: BF16 operands, FP32 accumulation */
+} ctp_prec;
+
+/* Storage of the Schur complement S (lower triangle of an m x m column-major
+ * matrix, leading dimension lds >= m; the strict upper triangle is not written). */
+typedef enum { CTP_S_NONE = 0, CTP_S_FP64 = 1, CTP_S_FP32 = 2 } ctp_smode;
+
+/* Per-position pivot kinds written to piv[]. */
+#define CTP_PIVKIND_1X1 1
+#define CTP_PIVKIND_2X2_FIRST 2
+#define CTP_PIVKIND_2X2_SECOND 0
+#define CTP_PIVKIND_ZERO (-1)
+#define CTP_PIVKIND_DELAYED 3
+
+typedef struct {
+    double u;       /* threshold, 0 < u <= 0.5 (Section 2; default 0.01) */
+    double small;   /* entries below `small` count as zero (default 1e-20) */
+    int32_t pivot;  /* ctp_pivot */
+    int32_t prec;   /* ctp_prec */
+    int32_t smode;  /* ctp_smode */
+    int32_t reserved;
+} ctp_options;
+
+typedef struct ctp_ctx ctp_ctx;
+
+/* Largest p this build factors (the pivot search keeps [A11; C] on chip). */
+int32_t ctp_max_p(void);
+
+/* Create a context bound to CUDA device `device` (it queries the device and
+ * caches launch limits; it allocates no device memory).  Returns CTP_ECUDA if
+ * the device is unusable. */
+ctp_status ctp_create(ctp_ctx **ctx, int32_t device);
+ctp_status ctp_destroy(ctp_ctx *ctx);
+
+/* Bytes of device workspace needed by ctp_factor_supernode / ctp_compress_* for
+ * an n x p supernode with these options. */
+ctp_status ctp_workspace_size(const ctp_ctx *ctx, int64_t n, int32_t p, const ctp_options *opt,
+                              size_t *bytes);
+
+/* Strict compression of A21 (Section 4.1, eq. (4.1)): for every A21 row i,
+ * J(i) = argmax_k |a21(i,k)| with ties to the lowest k, and
+ * c(j,k) = max_{i : J(i) = j} |a21(i,k)|, or 0 when no row has J(i) = j.
+ * A21: m x p device matrix (lda >= m).  C: p x p device output, ROW-major
+ * (C[j*p + k] = c(j,k)); every entry is exactly |a21(i,k)| of some row or 0.
+ * J: device int32[m] output, or NULL.  Exact: no rounding takes place. */
+ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double *A21, int64_t lda,
+                               double *C, int32_t *J, void *workspace, size_t ws_bytes,
+                               void *stream);
+
+/* The whole per-supernode hot path (Section 1 task list; Figure 4.1):
+ * compression of A21 (strict or relaxed), pivot selection by Listing 1 on
+ * [A11; C] in FP64 (with the worst-case update eq. (4.3) of C for strict), the
+ * Solve L21 = A21 P^T (D11 L11^T)^{-1}, the update of the delayed columns and
+ * the Form S = L21 D11 L21^T.
+ *
+ * In:  A (n x p, lda) holds [A11 lower; A21].
+ * Out: A, in place and in pivot order:
+ *        rows 0..p-1, lower triangle: unit lower L11 (diagonal implied) in the
+ *          first e columns, D on the diagonal and in the (q+1, q) slot of each
+ *          2x2 block, L rows of the delayed columns, and the updated delayed
+ *          block (Schur complement of the eliminated pivots) in the last d
+ *          columns; the strict upper triangle is unspecified;
+ *        rows p..n-1: L21 in columns 0..e-1, updated delayed columns after.
+ *      perm[p] (int32): perm[k] = original column at position k (0-based);
+ *        positions e..p-1 are the delayed columns in their original order.
+ *      piv[p] (int32): CTP_PIVKIND_* per position.
+ *      D[2p] (double): D[2k] = D(k,k); D[2k+1] = D(k+1,k) for the first column
+ *        of a 2x2 block, else 0.  Zero pivots have D = 0 and an all-zero L column.
+ *      nelim[1] (int32): e.
+ *      S (m x m, lds), written iff opt->smode != CTP_S_NONE: lower triangle of
+ *        L21 D11 L21^T in FP64 or FP32.
+ * All of perm, piv, D, nelim, S are device pointers.  Nothing is synchronised:
+ * e is only known on the device, and the Solve and Form kernels read it there. */
+ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, int64_t lda,
+                                const ctp_options *opt, int32_t *perm, int32_t *piv, double *D,
+                                int32_t *nelim, void *S, int64_t lds, void *workspace,
+                                size_t ws_bytes, void *stream);
+
+/* Read the device info word of a workspace used by the calls above
+ * (synchronises `stream`).  *info_host receives CTP_OK or the first device-side
+ * condition (CTP_ENONFINITE, CTP_ETIMEOUT, CTP_ECAPACITY).  The word is cleared
+ * at the start of every factor or compress call. */
+ctp_status ctp_read_info(ctp_ctx *ctx, const void *workspace, int32_t *info_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTP_H */

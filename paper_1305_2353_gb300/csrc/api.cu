@@ -1,0 +1,168 @@
+// api.cu -- the C ABI of libctp (declared in include/ctp.h): argument checks,
+// workspace layout and the launch sequence of the per-supernode hot path.
+#include <stdlib.h>
+
+#include "ctp_internal.cuh"
+
+struct ctp_ctx {
+    int device;
+    int num_sms;
+};
+
+namespace ctp {
+
+WsLayout ws_layout(int64_t n, int p, const ctp_options *opt) {
+    WsLayout L;
+    const int64_t m = n - p;
+    size_t off = 0;
+    L.info = off;
+    off += 256;
+    L.C = off;
+    const bool compressed = opt->pivot == CTP_PIV_STRICT || opt->pivot == CTP_PIV_RELAXED;
+    off += align256(compressed ? sizeof(double) * (size_t)p * p : 0);
+    L.Dinv = off;
+    off += align256(sizeof(double) * (2 * (size_t)p + 2));
+    L.W21 = off;
+    off += align256(opt->smode != CTP_S_NONE ? sizeof(double) * (size_t)m * p : 0);
+    L.aux = off;
+    L.total = off;
+    return L;
+}
+
+}  // namespace ctp
+
+using namespace ctp;
+
+#define CTP_CUDA(x)                            \
+    do {                                       \
+        if ((x) != cudaSuccess) return CTP_ECUDA; \
+    } while (0)
+
+extern "C" {
+
+int32_t ctp_max_p(void) { return kMaxP; }
+
+ctp_status ctp_create(ctp_ctx **ctx, int32_t device) {
+    if (ctx == nullptr) return CTP_EINVAL;
+    *ctx = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CTP_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return CTP_ECUDA;
+    ctp_ctx *c = (ctp_ctx *)malloc(sizeof(ctp_ctx));
+    if (c == nullptr) return CTP_ENOMEM;
+    c->device = device;
+    c->num_sms = sms;
+    *ctx = c;
+    return CTP_OK;
+}
+
+ctp_status ctp_destroy(ctp_ctx *ctx) {
+    free(ctx);
+    return CTP_OK;
+}
+
+static ctp_status check_opts(const ctp_options *opt) {
+    if (opt == nullptr) return CTP_EINVAL;
+    if (!(opt->u > 0.0) || opt->u > 0.5) return CTP_EINVAL;
+    if (!(opt->small >= 0.0)) return CTP_EINVAL;
+    if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
+    if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16) return CTP_EINVAL;
+    if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP32) return CTP_EINVAL;
+    return CTP_OK;
+}
+
+ctp_status ctp_workspace_size(const ctp_ctx *ctx, int64_t n, int32_t p, const ctp_options *opt,
+                              size_t *bytes) {
+    if (ctx == nullptr || bytes == nullptr || p < 1 || n < p) return CTP_EINVAL;
+    ctp_status s = check_opts(opt);
+    if (s != CTP_OK) return s;
+    *bytes = ws_layout(n, p, opt).total;
+    return CTP_OK;
+}
+
+ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double *A21, int64_t lda,
+                               double *C, int32_t *J, void *workspace, size_t ws_bytes,
+                               void *stream) {
+    if (ctx == nullptr || A21 == nullptr || C == nullptr || workspace == nullptr) return CTP_EINVAL;
+    if (m < 0 || p < 1 || lda < (m > 0 ? m : 1)) return CTP_EINVAL;
+    ctp_options o = {0.01, 1e-20, CTP_PIV_STRICT, CTP_FP64, CTP_S_NONE, 0};
+    WsLayout L = ws_layout(m + p, p, &o);
+    if (ws_bytes < L.total) return CTP_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    int32_t *info = (int32_t *)(ws + L.info);
+    unsigned long long *keys = (unsigned long long *)(ws + L.C);
+    CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+    CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));
+    CTP_CUDA(launch_compress_strict(A21, m, p, lda, keys, J, info, ctx->num_sms, st));
+    CTP_CUDA(launch_keys_to_rowmajor(keys, C, p, st));
+    return CTP_OK;
+}
+
+ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, int64_t lda,
+                                const ctp_options *opt, int32_t *perm, int32_t *piv, double *D,
+                                int32_t *nelim, void *S, int64_t lds, void *workspace,
+                                size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || A == nullptr || perm == nullptr || piv == nullptr || D == nullptr ||
+        nelim == nullptr || workspace == nullptr)
+        return CTP_EINVAL;
+    if (p < 1 || n < p || lda < n) return CTP_EINVAL;
+    ctp_status s = check_opts(opt);
+    if (s != CTP_OK) return s;
+    const int64_t m = n - p;
+    if (opt->smode != CTP_S_NONE && (S == nullptr || lds < (m > 0 ? m : 1))) return CTP_EINVAL;
+    if (p > kMaxP) return CTP_EUNSUPPORTED;
+    if (opt->pivot == CTP_PIV_RELAXED || opt->pivot == CTP_PIV_TPP) return CTP_EUNSUPPORTED;
+    if (opt->prec != CTP_FP64) return CTP_EUNSUPPORTED;
+    WsLayout L = ws_layout(n, p, opt);
+    if (ws_bytes < L.total) return CTP_ENOMEM;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    int32_t *info = (int32_t *)(ws + L.info);
+    double *Dinv = (double *)(ws + L.Dinv);
+    double *W21 = opt->smode != CTP_S_NONE ? (double *)(ws + L.W21) : nullptr;
+    CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+
+    FactorArgs fa;
+    fa.A = A;
+    fa.lda = lda;
+    fa.p = p;
+    fa.u = opt->u;
+    fa.small = opt->small;
+    fa.perm = perm;
+    fa.piv = piv;
+    fa.nelim = nelim;
+    fa.D = D;
+    fa.Dinv = Dinv;
+    fa.info = info;
+    if (opt->pivot == CTP_PIV_STRICT) {
+        unsigned long long *keys = (unsigned long long *)(ws + L.C);
+        CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));
+        CTP_CUDA(launch_compress_strict(A + p, m, p, lda, keys, nullptr, info, ctx->num_sms, st));
+        fa.R = p;
+        fa.abs_update = 1;
+        fa.C = (const double *)keys;  // non-negative keys are the doubles themselves
+    } else {  // restricted: the tests look at A11 only
+        fa.R = 0;
+        fa.abs_update = 0;
+        fa.C = nullptr;
+    }
+    CTP_CUDA(launch_factor_cluster(fa, st));
+    CTP_CUDA(launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, st));
+    if (opt->smode != CTP_S_NONE)
+        CTP_CUDA(launch_form_fp64(A + p, lda, W21, m, m, nelim, S, lds, opt->smode, st));
+    return CTP_OK;
+}
+
+ctp_status ctp_read_info(ctp_ctx *ctx, const void *workspace, int32_t *info_host, void *stream) {
+    if (ctx == nullptr || workspace == nullptr || info_host == nullptr) return CTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    CTP_CUDA(cudaMemcpyAsync(info_host, workspace, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CTP_CUDA(cudaStreamSynchronize(st));
+    return CTP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,183 @@
+// compress.cu -- K1: strict compression of A21 (Section 4.1, eq. (4.1)).
+//
+// For every A21 row i: J(i) = argmax_k |a21(i,k)| (ties to the lowest k), then
+// c(J(i), k) = max(c(J(i), k), |a21(i,k)|).  Everything is a comparison of
+// magnitudes, so the kernel never touches the FP64 pipe (which is narrow on
+// GB300): |x| is the IEEE bit pattern with the sign cleared, and for
+// non-negative doubles the unsigned 64-bit integer order is the numeric order.
+// C is kept as such integer keys in the workspace and merged across CTAs with
+// a test-then-atomicMax, which is exact and order independent.
+//
+// Data movement: A21 is column-major, so a tile of TR consecutive rows is one
+// contiguous TR*8-byte segment per column.  Each warp-wide cp.async moves 32
+// consecutive doubles of one column (coalesced), straight into a padded shared
+// tile [p][TR+1] without passing through registers; STAGES tiles are in flight
+// per CTA.  The CTA grid is persistent (a multiple of the SM count).
+#include "ctp_internal.cuh"
+
+namespace ctp {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTR = 16;      // rows per tile
+constexpr int kStages = 3;   // tiles in flight per CTA
+constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long kInfKey = 0x7FF0000000000000ull;
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
+}
+
+// Issue the loads of tile `t` into stage buffer `buf`.
+__device__ __forceinline__ void load_tile(const double *__restrict__ A21, int64_t m, int p,
+                                          int64_t lda, int64_t t, double *buf) {
+    const int64_t row0 = t * kTR;
+    const int total = kTR * p;
+    for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+        int k = idx / kTR, r = idx - k * kTR;
+        int64_t row = row0 + r;
+        if (row < m) cp_async8(buf + k * (kTR + 1) + r, A21 + (int64_t)k * lda + row);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_compress_strict(const double *__restrict__ A21, int64_t m, int p, int64_t lda,
+                      unsigned long long *__restrict__ Ckeys, int32_t *__restrict__ J,
+                      int32_t *__restrict__ info) {
+    extern __shared__ __align__(16) double smem[];
+    const int tile_elems = p * (kTR + 1);
+    double *tiles = smem;                                               // [kStages][p][kTR+1]
+    unsigned long long *pkey =
+        reinterpret_cast<unsigned long long *>(smem + kStages * tile_elems);  // [NG][kTR]
+    constexpr int NG = kThreads / kTR;                                  // column groups
+    int *pidx = reinterpret_cast<int *>(pkey + NG * kTR);               // [NG][kTR]
+    int *rowJ = pidx + NG * kTR;                                        // [kTR]
+
+    const int64_t ntiles = (m + kTR - 1) / kTR;
+    const int r = threadIdx.x % kTR, g = threadIdx.x / kTR;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    bool nonfinite = false;
+
+    // prologue: fill the pipeline
+    int64_t t_load = blockIdx.x;
+    for (int s = 0; s < kStages - 1; s++) {
+        if (t_load < ntiles) load_tile(A21, m, p, lda, t_load, tiles + s * tile_elems);
+        cp_async_commit();
+        t_load += gridDim.x;
+    }
+    int stage = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        // keep kStages-1 tiles ahead
+        int ls = (stage + kStages - 1) % kStages;
+        if (t_load < ntiles) load_tile(A21, m, p, lda, t_load, tiles + ls * tile_elems);
+        cp_async_commit();
+        t_load += gridDim.x;
+        cp_async_wait<kStages - 1>();
+        __syncthreads();
+
+        const double *tile = tiles + stage * tile_elems;
+        const int64_t row0 = t * kTR;
+        const int nrows = (int)((m - row0) < kTR ? (m - row0) : kTR);
+
+        // (1) row argmax: thread (r, g) scans columns g, g+NG, ... ascending
+        unsigned long long best = 0;
+        int bidx = -1;
+        if (r < nrows) {
+            for (int k = g; k < p; k += NG) {
+                unsigned long long key = abs_key(tile[k * (kTR + 1) + r]);
+                nonfinite |= key >= kInfKey;
+                if (bidx < 0 || key > best) {
+                    best = key;
+                    bidx = k;
+                }
+            }
+        }
+        pkey[g * kTR + r] = best;
+        pidx[g * kTR + r] = bidx;
+        __syncthreads();
+        if (threadIdx.x < kTR) {
+            unsigned long long b = 0;
+            int bi = -1;
+            for (int gg = 0; gg < NG; gg++) {
+                int ii = pidx[gg * kTR + threadIdx.x];
+                unsigned long long kk = pkey[gg * kTR + threadIdx.x];
+                if (ii < 0) continue;
+                if (bi < 0 || kk > b || (kk == b && ii < bi)) {
+                    b = kk;
+                    bi = ii;
+                }
+            }
+            rowJ[threadIdx.x] = bi;
+            if (J != nullptr && threadIdx.x < nrows) J[row0 + threadIdx.x] = bi;
+        }
+        __syncthreads();
+
+        // (2) merge the tile's rows into C: warp w takes rows w, w+8, ...; lanes walk k
+        for (int rr = warp; rr < nrows; rr += kThreads / 32) {
+            const int j = rowJ[rr];
+            unsigned long long *crow = Ckeys + (int64_t)j * p;
+            for (int k = lane; k < p; k += 32) {
+                unsigned long long key = abs_key(tile[k * (kTR + 1) + rr]);
+                unsigned long long cur = __ldcg(crow + k);
+                if (key > cur) atomicMax(crow + k, key);
+            }
+        }
+        __syncthreads();  // the buffer is refilled next round
+        stage = (stage + 1) % kStages;
+    }
+    cp_async_wait<0>();
+    if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
+}
+
+__global__ void k_keys_to_rowmajor(const unsigned long long *__restrict__ Ckeys,
+                                   double *__restrict__ C, int pp) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < pp) C[i] = __longlong_as_double((long long)Ckeys[i]);
+}
+
+}  // namespace
+
+static size_t strict_smem(int p) {
+    constexpr int NG = kThreads / kTR;
+    return sizeof(double) * (size_t)kStages * p * (kTR + 1) + NG * kTR * (sizeof(unsigned long long) + sizeof(int)) +
+           kTR * sizeof(int);
+}
+
+cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
+                                   unsigned long long *Ckeys, int32_t *J, int32_t *info,
+                                   int num_sms, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    size_t smem = strict_smem(p);
+    cudaError_t err = cudaFuncSetAttribute(k_compress_strict, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress_strict, kThreads, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    int64_t ntiles = (m + kTR - 1) / kTR;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    k_compress_strict<<<(unsigned)grid, kThreads, smem, st>>>(A21, m, p, lda, Ckeys, J, info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_to_rowmajor(const unsigned long long *Ckeys, double *C, int p,
+                                    cudaStream_t st) {
+    int pp = p * p;
+    k_keys_to_rowmajor<<<(pp + 255) / 256, 256, 0, st>>>(Ckeys, C, pp);
+    return cudaGetLastError();
+}
+
+}  // namespace ctp

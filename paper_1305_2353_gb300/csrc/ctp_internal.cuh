@@ -1,0 +1,62 @@
+// ctp_internal.cuh -- internal declarations shared by the libctp translation units.
+// Product code only: nothing here is used by, or uses, the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ctp.h"
+
+namespace ctp {
+
+// Largest supernode width handled on chip by the pivot search (kernel K3).
+constexpr int kMaxP = 256;
+
+// Device info word codes (first int32 of the workspace).
+constexpr int kInfoOk = 0;
+
+// Workspace layout (all offsets 256-byte aligned):
+//   [0, 256)            info word + scratch counters
+//   C                   p*p doubles, row-major compressed matrix (strict: as uint64 keys)
+//   Dinv                2p doubles: inverse pivot blocks, same slots as D
+//   W21                 m*p doubles (FP64 Y = L21 D11) when the Form step runs
+//   aux                 method-specific scratch (relaxed candidate lists)
+struct WsLayout {
+    size_t info, C, Dinv, W21, aux, total;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+WsLayout ws_layout(int64_t n, int p, const ctp_options *opt);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns cudaError_t of the launch)
+cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
+                                   unsigned long long *Ckeys, int32_t *J, int32_t *info,
+                                   int num_sms, cudaStream_t st);
+cudaError_t launch_keys_to_rowmajor(const unsigned long long *Ckeys, double *C, int p,
+                                    cudaStream_t st);
+
+struct FactorArgs {
+    double *A;          // n x p supernode (in/out)
+    int64_t lda;
+    int p;
+    int R;              // outer rows held on chip: p (compressed) or 0 (restricted)
+    int abs_update;     // 1: strict worst-case update of the outer rows
+    const double *C;    // R x p row-major outer rows (doubles), or nullptr
+    double u, small;
+    int32_t *perm, *piv, *nelim;
+    double *D, *Dinv;
+    int32_t *info;
+};
+cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st);
+
+cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
+                              const int32_t *piv, const double *Dinv, const int32_t *nelim,
+                              double *W21, int64_t ldw, cudaStream_t st);
+
+cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
+                             int64_t m, const int32_t *nelim, void *S, int64_t lds, int smode,
+                             cudaStream_t st);
+
+}  // namespace ctp

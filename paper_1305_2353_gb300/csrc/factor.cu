@@ -1,0 +1,482 @@
+// factor.cu -- K3: pivot selection on [A11; C] by Listing 1 (Section 2) in FP64,
+// with the worst-case update of the strict compressed matrix (eq. (4.3); the
+// 2x2 form follows the proof of Theorem 5.2).
+//
+// GB300 design.  The working matrix [A11; C] (A11 held in full symmetric form so
+// that every column carries all of its entries, C the R = p outer rows) is
+// 2p x p doubles -- 1 MB at p = 256, far beyond one SM -- and GB300's FP64 pipe
+// is narrow, so the right-looking updates must be spread over many SMs.  One
+// thread-block cluster of G CTAs owns the matrix: column c lives in the shared
+// memory of CTA (c mod G).  The pivot loop is sequential by definition; each
+// candidate costs one cluster barrier (two when it is accepted):
+//   phase A  the owner of candidate m runs the tests of Listing 1 on its own
+//            column and reads the partner column t through distributed shared
+//            memory (DSMEM); it publishes a small decision record;
+//   phase B  every CTA reads the decision, copies the pivot column(s) from
+//            their owners over DSMEM and updates its own live columns.
+// Columns are never moved: accepted pivots leave the live set, and because the
+// paper's stable shift never reorders the remaining columns, the candidate
+// order is simply the original column order of the live columns.  The final
+// pivot order (accepted pivots in acceptance order, then the delayed columns in
+// original order) is applied only when the factor is written back.
+//
+// Determinism: every CTA holds the same replicated control state (live flags,
+// nelim, m) and executes the same sequence of barriers; all decisions are taken
+// by one CTA and broadcast, so there is no divergence between CTAs.  The test
+// arithmetic uses explicitly rounded operations (no FMA contraction) so that
+// it matches the plain-CPU formulas up to the rounding of the inputs.
+#include <cooperative_groups.h>
+
+#include "ctp_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ctp {
+
+namespace {
+
+constexpr int kT = 256;  // threads per CTA
+constexpr int kNW = kT / 32;
+
+enum { DEC_REJECT = 0, DEC_1X1 = 1, DEC_2X2 = 2, DEC_ZERO = -1 };
+
+struct Decision {
+    int kind, t, m, pad;
+    double d0, d1, d2;  // 1x1: d0 = d; 2x2: a_tt, a_tm, a_mm
+    double i0, i1, i2;  // 1x1: i0 = 1/d; 2x2: D^-1 entries (t,t), (m,t), (m,m)
+};
+
+struct Shared {
+    Decision dec[2];
+    Decision cur;
+    double red[kNW];
+    int redi[kNW];
+    unsigned char live[kMaxP];
+    int order[kMaxP];
+    int kind[kMaxP];
+    int pos_of[kMaxP];
+    double sD[2 * kMaxP + 2];
+    double sInv[2 * kMaxP + 2];
+};
+
+__device__ __forceinline__ double block_max(double v, Shared &sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sh.red[w] = v;
+    __syncthreads();
+    double r = sh.red[0];
+#pragma unroll
+    for (int i = 1; i < kNW; i++) r = fmax(r, sh.red[i]);
+    __syncthreads();
+    return r;
+}
+
+// argmax of v over threads, ties to the lowest index; idx < 0 means "none".
+__device__ __forceinline__ int block_argmax(double v, int idx, Shared &sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (oi >= 0 && (idx < 0 || ov > v || (ov == v && oi < idx))) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    if (lane == 0) {
+        sh.red[w] = v;
+        sh.redi[w] = idx;
+    }
+    __syncthreads();
+    double bv = sh.red[0];
+    int bi = sh.redi[0];
+    for (int i = 1; i < kNW; i++) {
+        double ov = sh.red[i];
+        int oi = sh.redi[i];
+        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    __syncthreads();
+    return bi;
+}
+
+// Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
+// test of eq. (2.2), |D^-1| (maxt, maxm)^T <= 1/u.  Fills d on acceptance.
+__device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, double maxt,
+                                         double maxm, double u, double small, Decision &d) {
+    double amax = fmax(fabs(a_tt), fmax(fabs(a_tm), fabs(a_mm)));
+    if (amax < small) return false;
+    double detscale = __ddiv_rn(1.0, amax);
+    double detpiv1 = __dmul_rn(__dmul_rn(a_tm, detscale), a_tm);
+    double detpiv0 = __dmul_rn(__dmul_rn(a_mm, detscale), a_tt);
+    double detpiv = __dsub_rn(detpiv0, detpiv1);
+    double guard = fmax(small, fmax(0.5 * fabs(detpiv0), 0.5 * fabs(detpiv1)));
+    if (fabs(detpiv) <= guard) return false;
+    bool ok;
+    if (fmax(maxm, maxt) < small) {
+        ok = true;
+    } else {
+        double ad = fabs(detpiv);
+        double gt = __ddiv_rn(__dmul_rn(__dadd_rn(__dmul_rn(fabs(a_mm), maxt), __dmul_rn(fabs(a_tm), maxm)), detscale), ad);
+        double gm = __ddiv_rn(__dmul_rn(__dadd_rn(__dmul_rn(fabs(a_tm), maxt), __dmul_rn(fabs(a_tt), maxm)), detscale), ad);
+        double iu = __ddiv_rn(1.0, u);
+        ok = (gt <= iu) && (gm <= iu);
+    }
+    if (ok) {
+        d.d0 = a_tt;
+        d.d1 = a_tm;
+        d.d2 = a_mm;
+        d.i0 = __ddiv_rn(__dmul_rn(a_mm, detscale), detpiv);
+        d.i1 = __ddiv_rn(__dmul_rn(-a_tm, detscale), detpiv);
+        d.i2 = __ddiv_rn(__dmul_rn(a_tt, detscale), detpiv);
+    }
+    return ok;
+}
+
+__global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ Shared sh;
+
+    const int p = a.p, R = a.R, LD = p + R;
+    const int rank = (int)cluster.block_rank();
+    const int ncl = (p + G - 1) / G;
+    double *cols = dsm;                 // [ncl][LD]
+    double *pc0 = dsm + (size_t)ncl * LD;  // pivot column copies
+    double *pc1 = pc0 + LD;
+    const int tid = threadIdx.x;
+
+    // ---- load: own columns of A11 (full symmetric) and of the outer rows
+    bool nonfinite = false;
+    for (int lc = 0; lc < ncl; lc++) {
+        const int c = lc * G + rank;
+        if (c >= p) break;
+        double *col = cols + (size_t)lc * LD;
+        for (int i = tid; i < LD; i += kT) {
+            double v;
+            if (i < p)
+                v = (i >= c) ? a.A[(int64_t)c * a.lda + i] : a.A[(int64_t)i * a.lda + c];
+            else
+                v = a.C[(int64_t)(i - p) * p + c];
+            nonfinite |= !isfinite(v);
+            col[i] = v;
+        }
+    }
+    for (int i = tid; i < p; i += kT) sh.live[i] = 1;
+    if (nonfinite) atomicCAS(a.info, kInfoOk, (int32_t)CTP_ENONFINITE);
+    cluster.sync();
+
+    const double u = a.u, small = a.small;
+    int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, step = 0;
+    for (;;) {
+        if (nelim >= p) break;
+        while (m < p && !sh.live[m]) m++;
+        if (m >= p) {
+            if (!accepted) break;
+            accepted = 0;
+            m = 0;
+            continue;
+        }
+        const int owner = m % G, slot = step & 1;
+        // ---------------- phase A: tests of Listing 1 for candidate m
+        if (rank == owner) {
+            Decision d;
+            d.kind = DEC_REJECT;
+            d.t = -1;
+            d.m = m;
+            d.pad = 0;
+            d.d0 = d.d1 = d.d2 = d.i0 = d.i1 = d.i2 = 0.0;
+            const double *cm = cols + (size_t)(m / G) * LD;
+            double v = 0.0;
+            for (int i = tid; i < LD; i += kT)
+                if (i >= p || sh.live[i]) v = fmax(v, fabs(cm[i]));
+            const double cmax = block_max(v, sh);
+            if (cmax < small) {
+                d.kind = DEC_ZERO;
+            } else {
+                // partner t: largest |a(m, j)| over live j < m, lowest j on ties
+                double bv = -1.0;
+                int bi = -1;
+                for (int j = tid; j < m; j += kT)
+                    if (sh.live[j]) {
+                        double av = fabs(cm[j]);
+                        if (bi < 0 || av > bv) {
+                            bv = av;
+                            bi = j;
+                        }
+                    }
+                const int t = block_argmax(bv, bi, sh);
+                double maxm2 = 0.0;
+                if (t >= 0) {
+                    const double *ct = cluster.map_shared_rank(cols, t % G) + (size_t)(t / G) * LD;
+                    double vm = 0.0, vt = 0.0;
+                    for (int i = tid; i < LD; i += kT)
+                        if (i >= p || (sh.live[i] && i != t && i != m)) {
+                            vm = fmax(vm, fabs(cm[i]));
+                            vt = fmax(vt, fabs(ct[i]));
+                        }
+                    maxm2 = block_max(vm, sh);
+                    const double maxt = block_max(vt, sh);
+                    if (test_2x2(ct[t], cm[t], cm[m], maxt, maxm2, u, small, d)) {
+                        d.kind = DEC_2X2;
+                        d.t = t;
+                    }
+                }
+                if (d.kind != DEC_2X2) {
+                    double maxm1;
+                    if (t >= 0) {
+                        maxm1 = fmax(maxm2, fabs(cm[t]));
+                    } else {
+                        double w = 0.0;
+                        for (int i = tid; i < LD; i += kT)
+                            if (i >= p || (sh.live[i] && i != m)) w = fmax(w, fabs(cm[i]));
+                        maxm1 = block_max(w, sh);
+                    }
+                    const double amm = cm[m];
+                    if (fabs(amm) >= __dmul_rn(u, maxm1)) {
+                        d.kind = DEC_1X1;
+                        d.d0 = amm;
+                        d.i0 = __ddiv_rn(1.0, amm);
+                    }
+                }
+            }
+            if (tid == 0) sh.dec[slot] = d;
+        }
+        cluster.sync();
+        if (tid == 0) sh.cur = *cluster.map_shared_rank(&sh.dec[slot], owner);
+        __syncthreads();
+        const Decision dv = sh.cur;
+        step++;
+        if (dv.kind == DEC_REJECT) {
+            m++;
+            continue;
+        }
+        if (dv.kind == DEC_ZERO) {
+            __syncthreads();
+            if (tid == 0) {
+                sh.live[m] = 0;
+                sh.order[nelim] = m;
+                sh.kind[nelim] = CTP_PIVKIND_ZERO;
+                sh.sD[2 * nelim] = sh.sD[2 * nelim + 1] = 0.0;
+                sh.sInv[2 * nelim] = sh.sInv[2 * nelim + 1] = 0.0;
+            }
+            __syncthreads();
+            nelim++;
+            accepted = 1;
+            m++;
+            continue;
+        }
+        // ---------------- phase B: apply the pivot to the own live columns
+        const int q0 = (dv.kind == DEC_2X2) ? dv.t : dv.m;
+        const int q1 = (dv.kind == DEC_2X2) ? dv.m : -1;
+        {
+            const double *s0 = cluster.map_shared_rank(cols, q0 % G) + (size_t)(q0 / G) * LD;
+            for (int i = tid; i < LD; i += kT) pc0[i] = s0[i];
+            if (q1 >= 0) {
+                const double *s1 = cluster.map_shared_rank(cols, q1 % G) + (size_t)(q1 / G) * LD;
+                for (int i = tid; i < LD; i += kT) pc1[i] = s1[i];
+            }
+        }
+        __syncthreads();
+        const bool abs_rows = a.abs_update != 0;
+        for (int lc = 0; lc < ncl; lc++) {
+            const int c = lc * G + rank;
+            if (c >= p) break;
+            if (!sh.live[c] || c == q0 || c == q1) continue;
+            double *col = cols + (size_t)lc * LD;
+            if (q1 < 0) {
+                // 1x1: a(i,c) -= a(i,q) a(c,q) / d  (symmetric in i and c)
+                const double inv = dv.i0, ainv = fabs(dv.i0);
+                const double akq = pc0[c], aakq = fabs(akq);
+                for (int i = tid; i < LD; i += kT) {
+                    if (i < p) {
+                        if (!sh.live[i] || i == q0) continue;
+                        col[i] -= (pc0[i] * akq) * inv;
+                    } else if (abs_rows) {
+                        col[i] += (pc0[i] * aakq) * ainv;  // eq. (4.3)
+                    } else {
+                        col[i] -= (pc0[i] * akq) * inv;
+                    }
+                }
+            } else {
+                // 2x2: a(i,c) -= [a(i,t) a(i,m)] D^-1 [a(c,t) a(c,m)]^T
+                const double i11 = dv.i0, i21 = dv.i1, i22 = dv.i2;
+                const double b0 = pc0[c], b1 = pc1[c];
+                const double ab0 = fabs(b0), ab1 = fabs(b1);
+                const double j11 = fabs(i11), j21 = fabs(i21), j22 = fabs(i22);
+                for (int i = tid; i < LD; i += kT) {
+                    const double x0 = pc0[i], x1 = pc1[i];
+                    if (i < p) {
+                        if (!sh.live[i] || i == q0 || i == q1) continue;
+                        col[i] -= i11 * (x0 * b0) + i21 * (x0 * b1 + x1 * b0) + i22 * (x1 * b1);
+                    } else if (abs_rows) {
+                        col[i] += j11 * (x0 * ab0) + j21 * (x0 * ab1 + x1 * ab0) + j22 * (x1 * ab1);
+                    } else {
+                        col[i] -= i11 * (x0 * b0) + i21 * (x0 * b1 + x1 * b0) + i22 * (x1 * b1);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (q1 < 0) {
+                sh.live[q0] = 0;
+                sh.order[nelim] = q0;
+                sh.kind[nelim] = CTP_PIVKIND_1X1;
+                sh.sD[2 * nelim] = dv.d0;
+                sh.sD[2 * nelim + 1] = 0.0;
+                sh.sInv[2 * nelim] = dv.i0;
+                sh.sInv[2 * nelim + 1] = 0.0;
+            } else {
+                sh.live[q0] = 0;
+                sh.live[q1] = 0;
+                sh.order[nelim] = q0;
+                sh.order[nelim + 1] = q1;
+                sh.kind[nelim] = CTP_PIVKIND_2X2_FIRST;
+                sh.kind[nelim + 1] = CTP_PIVKIND_2X2_SECOND;
+                sh.sD[2 * nelim] = dv.d0;
+                sh.sD[2 * nelim + 1] = dv.d1;
+                sh.sD[2 * nelim + 2] = dv.d2;
+                sh.sD[2 * nelim + 3] = 0.0;
+                sh.sInv[2 * nelim] = dv.i0;
+                sh.sInv[2 * nelim + 1] = dv.i1;
+                sh.sInv[2 * nelim + 2] = dv.i2;
+                sh.sInv[2 * nelim + 3] = 0.0;
+            }
+        }
+        __syncthreads();
+        nelim += (q1 < 0) ? 1 : 2;
+        accepted = 1;
+        m++;
+        cluster.sync();  // every update done before the next tests read columns
+    }
+
+    // ---- final order: accepted pivots, then the delayed columns in original order
+    const int e = nelim;
+    if (tid == 0) {
+        int k = e;
+        for (int c = 0; c < p; c++)
+            if (sh.live[c]) {
+                sh.order[k] = c;
+                sh.kind[k] = CTP_PIVKIND_DELAYED;
+                sh.sD[2 * k] = sh.sD[2 * k + 1] = 0.0;
+                sh.sInv[2 * k] = sh.sInv[2 * k + 1] = 0.0;
+                k++;
+            }
+    }
+    __syncthreads();
+    for (int k = tid; k < p; k += kT) sh.pos_of[sh.order[k]] = k;
+    __syncthreads();
+
+    // ---- write back the A11 block in pivot order (lower triangle)
+    for (int lc = 0; lc < ncl; lc++) {
+        const int c = lc * G + rank;
+        if (c >= p) break;
+        const double *col = cols + (size_t)lc * LD;
+        const int pos = sh.pos_of[c];
+        const int kd = sh.kind[pos];
+        double *out = a.A + (int64_t)pos * a.lda;
+        if (kd == CTP_PIVKIND_DELAYED) {
+            for (int i = tid; i < p; i += kT) {
+                const int pi = sh.pos_of[i];
+                if (pi >= pos) out[pi] = col[i];
+            }
+        } else if (kd == CTP_PIVKIND_ZERO) {
+            for (int i = tid; i < p; i += kT) {
+                const int pi = sh.pos_of[i];
+                if (pi >= pos) out[pi] = 0.0;
+            }
+        } else if (kd == CTP_PIVKIND_1X1) {
+            const double inv = sh.sInv[2 * pos];
+            for (int i = tid; i < p; i += kT) {
+                const int pi = sh.pos_of[i];
+                if (pi > pos) out[pi] = col[i] * inv;
+            }
+            if (tid == 0) out[pos] = sh.sD[2 * pos];
+        } else if (kd == CTP_PIVKIND_2X2_FIRST) {
+            const int mo = sh.order[pos + 1];
+            const double *cmo = cluster.map_shared_rank(cols, mo % G) + (size_t)(mo / G) * LD;
+            const double i11 = sh.sInv[2 * pos], i21 = sh.sInv[2 * pos + 1];
+            for (int i = tid; i < p; i += kT) {
+                const int pi = sh.pos_of[i];
+                if (pi > pos + 1) out[pi] = col[i] * i11 + cmo[i] * i21;
+            }
+            if (tid == 0) {
+                out[pos] = sh.sD[2 * pos];
+                out[pos + 1] = sh.sD[2 * pos + 1];
+            }
+        } else {  // second column of a 2x2
+            const int to = sh.order[pos - 1];
+            const double *cto = cluster.map_shared_rank(cols, to % G) + (size_t)(to / G) * LD;
+            const double i21 = sh.sInv[2 * (pos - 1) + 1], i22 = sh.sInv[2 * (pos - 1) + 2];
+            for (int i = tid; i < p; i += kT) {
+                const int pi = sh.pos_of[i];
+                if (pi > pos) out[pi] = cto[i] * i21 + col[i] * i22;
+            }
+            if (tid == 0) out[pos] = sh.sD[2 * pos];
+        }
+    }
+    if (rank == 0) {
+        for (int k = tid; k < p; k += kT) {
+            a.perm[k] = sh.order[k];
+            a.piv[k] = sh.kind[k];
+            a.D[2 * k] = sh.sD[2 * k];
+            a.D[2 * k + 1] = sh.sD[2 * k + 1];
+            a.Dinv[2 * k] = sh.sInv[2 * k];
+            a.Dinv[2 * k + 1] = sh.sInv[2 * k + 1];
+        }
+        if (tid == 0) *a.nelim = e;
+    }
+    cluster.sync();  // no CTA leaves while its shared memory may still be read
+}
+
+}  // namespace
+
+static size_t factor_smem(int p, int R, int G) {
+    int ncl = (p + G - 1) / G;
+    return sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R));
+}
+
+cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st) {
+    // preferred cluster width by p: more CTAs give more FP64 lanes to the
+    // right-looking update; widen further if the columns do not fit on chip
+    int G = a.p > 128 ? 16 : (a.p > 64 ? 8 : (a.p > 16 ? 4 : 1));
+    while (factor_smem(a.p, a.R, G) > 200 * 1024 && G < 16) G <<= 1;
+    size_t smem = factor_smem(a.p, a.R, G);
+    cudaError_t err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    if (G > 8) {
+        err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (err != cudaSuccess) return err;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kT, 1, 1);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // fall back to narrower clusters if this one cannot be scheduled
+    for (;;) {
+        smem = factor_smem(a.p, a.R, G);
+        cfg.gridDim = dim3(G, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        attr[0].val.clusterDim.x = G;
+        int nclusters = 0;
+        err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) err = cudaOccupancyMaxActiveClusters(&nclusters, k_factor_cluster, &cfg);
+        if (err == cudaSuccess && nclusters > 0) break;
+        (void)cudaGetLastError();
+        if (G <= 1 || factor_smem(a.p, a.R, G >> 1) > 200 * 1024) return err != cudaSuccess ? err : cudaErrorLaunchOutOfResources;
+        G >>= 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k_factor_cluster, a, G);
+}
+
+}  // namespace ctp

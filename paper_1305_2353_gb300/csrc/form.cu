@@ -1,0 +1,86 @@
+// form.cu -- K6 (FP64): the Form task S = L21 D11 L21^T = W21 L21^T (Section 1
+// task list), lower triangle only.
+//
+// W21 = L21 D11 is the Y produced by the Solve kernel.  The kernel walks only the
+// tiles on or below the diagonal (a triangular tile index), stages 64 x 16
+// slabs of W21 and L21 in shared memory, and gives each of 256 threads a 4 x 4
+// block of S.  The inner dimension e is read from device memory (it is only
+// known after pivoting).  S is written as FP64 or FP32; strictly upper entries
+// of diagonal tiles are not written.
+#include "ctp_internal.cuh"
+
+namespace ctp {
+
+namespace {
+
+constexpr int kTile = 64, kK = 16, kTh = 256;
+
+template <typename OutT>
+__global__ void __launch_bounds__(kTh)
+    k_form_fp64(const double *__restrict__ L21, int64_t ldl, const double *__restrict__ W21,
+                int64_t ldw, int64_t m, const int32_t *__restrict__ nelim_p, OutT *__restrict__ S,
+                int64_t lds) {
+    __shared__ double sw[kK][kTile + 1];
+    __shared__ double sl[kK][kTile + 1];
+    // triangular tile index -> (ti, tj), ti >= tj
+    const int64_t b = blockIdx.x;
+    int64_t ti = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= b) ti++;
+    while (ti * (ti + 1) / 2 > b) ti--;
+    const int64_t tj = b - ti * (ti + 1) / 2;
+    const int64_t i0 = ti * kTile, j0 = tj * kTile;
+    const int e = *nelim_p;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < e; k0 += kK) {
+        for (int idx = threadIdx.x; idx < kK * kTile; idx += kTh) {
+            const int kk = idx / kTile, rr = idx % kTile;
+            const int k = k0 + kk;
+            const int64_t gi = i0 + rr, gj = j0 + rr;
+            sw[kk][rr] = (k < e && gi < m) ? W21[(int64_t)k * ldw + gi] : 0.0;
+            sl[kk][rr] = (k < e && gj < m) ? L21[(int64_t)k * ldl + gj] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kK; kk++) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                a[q] = sw[kk][ty + 16 * q];
+                bb[q] = sl[kk][tx + 16 * q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+#pragma unroll
+                for (int s = 0; s < 4; s++) acc[q][s] += a[q] * bb[s];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            const int64_t gi = i0 + ty + 16 * q, gj = j0 + tx + 16 * s;
+            if (gi < m && gj < m && gi >= gj) S[gj * lds + gi] = (OutT)acc[q][s];
+        }
+}
+
+}  // namespace
+
+cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
+                             int64_t m, const int32_t *nelim, void *S, int64_t lds, int smode,
+                             cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    const int64_t nt = (m + kTile - 1) / kTile;
+    const int64_t ntiles = nt * (nt + 1) / 2;
+    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (smode == CTP_S_FP64)
+        k_form_fp64<double><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
+                                                              (double *)S, lds);
+    else
+        k_form_fp64<float><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
+                                                             (float *)S, lds);
+    return cudaGetLastError();
+}
+
+}  // namespace ctp

@@ -1,0 +1,198 @@
+"""Thin Python binding of libctp (the C ABI declared in include/ctp.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of libctp.so.  PyTorch provides device memory and streams.  There is
+no fallback: if the library is missing, ``load()`` raises.
+
+Matrices cross the boundary column-major.  A column-major n x p device matrix
+with leading dimension lda is held here as a torch tensor of shape (p, lda)
+(row j of the tensor is column j of the matrix); ``colmajor()`` and
+``to_numpy()`` convert.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libctp.so")
+
+CTP_OK, CTP_EINVAL, CTP_ENOMEM, CTP_ECUDA, CTP_ENONFINITE, CTP_ETIMEOUT, CTP_ECAPACITY, \
+    CTP_EUNSUPPORTED = range(8)
+STATUS = {0: "CTP_OK", 1: "CTP_EINVAL", 2: "CTP_ENOMEM", 3: "CTP_ECUDA", 4: "CTP_ENONFINITE",
+          5: "CTP_ETIMEOUT", 6: "CTP_ECAPACITY", 7: "CTP_EUNSUPPORTED"}
+PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3}
+PREC = {"fp64": 0, "bf16": 1}
+SMODE = {"none": 0, "fp64": 1, "fp32": 2}
+PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
+
+EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_compress_strict",
+           "ctp_factor_supernode", "ctp_read_info"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_double), ("small", ctypes.c_double), ("pivot", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("smode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def options(u=0.01, small=1e-20, pivot="strict", prec="fp64", smode="none"):
+    return Options(u, small, PIVOT[pivot], PREC[prec], SMODE[smode], 0)
+
+
+class CtpError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} returned {STATUS.get(code, code)}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libctp.so (built by ``paper_1305_2353_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libctp.so not found at {path}: run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    i32, i64, sz, P = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+    L.ctp_max_p.restype = i32
+    L.ctp_max_p.argtypes = []
+    L.ctp_create.argtypes = [ctypes.POINTER(P), i32]
+    L.ctp_destroy.argtypes = [P]
+    L.ctp_workspace_size.argtypes = [P, i64, i32, ctypes.POINTER(Options), ctypes.POINTER(sz)]
+    L.ctp_compress_strict.argtypes = [P, i64, i32, P, i64, P, P, P, sz, P]
+    L.ctp_factor_supernode.argtypes = [P, i64, i32, P, i64, ctypes.POINTER(Options), P, P, P, P, P,
+                                       i64, P, sz, P]
+    L.ctp_read_info.argtypes = [P, P, ctypes.POINTER(i32), P]
+    for f in EXPORTS[1:]:
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(fn, code):
+    if code != CTP_OK:
+        raise CtpError(fn, code)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A libctp context bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check("ctp_create", self.lib.ctp_create(ctypes.byref(h), device))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self.lib.ctp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_size(self, n, p, opt):
+        b = ctypes.c_size_t()
+        _check("ctp_workspace_size",
+               self.lib.ctp_workspace_size(self.handle, n, p, ctypes.byref(opt), ctypes.byref(b)))
+        return int(b.value)
+
+    def workspace(self, n, p, opt):
+        import torch
+        nbytes = self.workspace_size(n, p, opt)
+        return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def compress_strict(self, A21, m, p, lda, C, J=None, ws=None, stream=None):
+        """A21: device tensor holding the m x p column-major A21 (leading dim lda);
+        C: device float64 tensor of p*p (row-major output); J: int32[m] or None."""
+        if ws is None:
+            ws = self.workspace(m + p, p, options())
+        _check("ctp_compress_strict",
+               self.lib.ctp_compress_strict(self.handle, m, p, _ptr(A21), lda, _ptr(C), _ptr(J),
+                                            _ptr(ws), ws.numel(), _stream(stream)))
+        return ws
+
+    def factor_supernode(self, A, n, p, lda, opt, perm, piv, D, nelim, S=None, lds=0, ws=None,
+                         stream=None):
+        if ws is None:
+            ws = self.workspace(n, p, opt)
+        _check("ctp_factor_supernode",
+               self.lib.ctp_factor_supernode(self.handle, n, p, _ptr(A), lda, ctypes.byref(opt),
+                                             _ptr(perm), _ptr(piv), _ptr(D), _ptr(nelim), _ptr(S),
+                                             lds, _ptr(ws), ws.numel(), _stream(stream)))
+        return ws
+
+    def read_info(self, ws, stream=None):
+        v = ctypes.c_int32()
+        _check("ctp_read_info", self.lib.ctp_read_info(self.handle, _ptr(ws), ctypes.byref(v),
+                                                        _stream(stream)))
+        return int(v.value)
+
+
+# ---------------------------------------------------------------------------
+# layout helpers (no arithmetic)
+
+def colmajor(a: np.ndarray, device="cuda"):
+    """numpy (rows x cols) -> device tensor (cols, rows) holding it column-major."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a).T)).to(device)
+
+
+def to_numpy(t) -> np.ndarray:
+    """Inverse of ``colmajor``."""
+    return t.detach().cpu().numpy().T.copy()
+
+
+class Supernode:
+    """Device buffers for one factorization of an n x p supernode."""
+
+    def __init__(self, ctx: Context, A_host: np.ndarray, p: int, opt, s_dtype=None):
+        import torch
+        self.ctx = ctx
+        self.n, self.p = A_host.shape[0], p
+        dev = f"cuda:{ctx.device}"
+        self.A = colmajor(A_host, dev)
+        self.perm = torch.empty(p, dtype=torch.int32, device=dev)
+        self.piv = torch.empty(p, dtype=torch.int32, device=dev)
+        self.D = torch.empty(2 * p, dtype=torch.float64, device=dev)
+        self.nelim = torch.empty(1, dtype=torch.int32, device=dev)
+        m = self.n - p
+        self.S = None
+        if opt.smode != 0:
+            dt = torch.float64 if opt.smode == 1 else torch.float32
+            self.S = torch.zeros((m, m), dtype=dt, device=dev)  # column-major m x m
+        self.opt = opt
+        self.ws = ctx.workspace(self.n, p, opt)
+
+    def run(self, stream=None):
+        self.ctx.factor_supernode(self.A, self.n, self.p, self.n, self.opt, self.perm, self.piv,
+                                  self.D, self.nelim, self.S, max(self.n - self.p, 1), self.ws,
+                                  stream)
+
+    def result(self):
+        out = dict(A=to_numpy(self.A), perm=self.perm.cpu().numpy(), piv=self.piv.cpu().numpy(),
+                   D=self.D.cpu().numpy(), nelim=int(self.nelim.cpu()[0]))
+        if self.S is not None:
+            out["S"] = to_numpy(self.S)
+        out["info"] = self.ctx.read_info(self.ws)
+        return out

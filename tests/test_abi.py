@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/ctp.h declares; host-side argument checks reject bad calls before any
+device work (these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1305_2353_gb300 import build as B
+from paper_1305_2353_gb300 import ctp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ctp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ctp_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return ctp.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert "ctp_factor_supernode" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(ctp.EXPORTS)
+
+
+def test_max_p(lib):
+    assert lib.ctp_max_p() == 256
+
+
+def test_host_argument_checks(lib):
+    opt = ctp.options()
+    sz = ctypes.c_size_t()
+    # null context
+    assert lib.ctp_workspace_size(None, 100, 10, ctypes.byref(opt), ctypes.byref(sz)) == ctp.CTP_EINVAL
+    assert lib.ctp_factor_supernode(None, 100, 10, None, 100, ctypes.byref(opt), None, None, None,
+                                    None, None, 0, None, 0, None) == ctp.CTP_EINVAL
+    assert lib.ctp_compress_strict(None, 10, 4, None, 10, None, None, None, 0, None) == ctp.CTP_EINVAL
+    assert lib.ctp_read_info(None, None, None, None) == ctp.CTP_EINVAL
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.ctp_create(ctypes.byref(h), 0) == ctp.CTP_ECUDA
+    assert not h.value

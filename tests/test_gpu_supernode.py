@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: the strict compressed matrix and the row sets J are bit-exact; pivot
+sequences, pivot kinds and nelim are identical whenever no threshold test of
+the oracle lies within 1e-10 (relative) of its bound; L, D, the delayed block
+and S agree within FP64 rounding (1e-10 relative to the largest entry); the
+GPU factor satisfies ||PAP^T - LDL^T|| / ||A|| <= 1e-13 (max-abs norm over
+the stored trapezoid, delayed block counted as residual).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1305_2353_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1305_2353_gb300 import build, ctp
+    build.build()
+    return ctp.Context(0)
+
+
+def min_margin(log):
+    if len(log) == 0:
+        return np.inf
+    lhs, rhs = np.abs(log["lhs"]), np.abs(log["rhs"])
+    den = np.maximum(np.maximum(lhs, rhs), 1e-300)
+    return float(np.min(np.abs(lhs - rhs) / den))
+
+
+def run_gpu(ctx, A, p, pivot="strict", smode="none", u=0.01):
+    from paper_1305_2353_gb300 import ctp
+    opt = ctp.options(u=u, pivot=pivot, smode=smode)
+    sn = ctp.Supernode(ctx, A, p, opt)
+    sn.run()
+    torch.cuda.synchronize()
+    return sn.result()
+
+
+def recon_error(A, p, res):
+    n = A.shape[0]
+    e = res["nelim"]
+    L, Dm, R = O.unpack(res, p)
+    Ap = O.permuted_supernode(A, p, res["perm"])
+    rec = L @ Dm @ L[:p, :].T
+    rec[:, e:] += R
+    mask = np.ones((n, p), bool)
+    mask[:p, :] = np.tril(np.ones((p, p), bool))
+    return np.abs(Ap - rec)[mask].max() / np.abs(A).max()
+
+
+def compare(ref, got, p, A, check_recon=True):
+    assert got["info"] == 0
+    margin = min_margin(ref["log"])
+    if margin > 1e-10:
+        assert got["nelim"] == ref["nelim"]
+        assert np.array_equal(got["perm"], ref["perm"])
+        assert np.array_equal(got["piv"], ref["piv"])
+        Ag, Ar = got["A"].copy(), ref["A"].copy()
+        # the strict upper triangle of the A11 block is unspecified
+        iu = np.triu_indices(p, 1)
+        Ag[:p][iu] = 0.0
+        Ar[:p][iu] = 0.0
+        scale = max(np.abs(Ar).max(), 1.0)
+        assert np.allclose(Ag, Ar, rtol=1e-10, atol=1e-10 * scale)
+        assert np.allclose(got["D"], ref["D"], rtol=1e-10, atol=1e-10 * np.abs(ref["D"]).max())
+    if check_recon:
+        assert recon_error(A, p, got) <= 1e-13
+
+
+# --------------------------------------------------------------------------- K1
+
+@pytest.mark.parametrize("m,p", [(5, 3), (1, 1), (17, 1), (100, 7), (1000, 64), (4099, 128),
+                                 (20011, 256), (33, 200)])
+def test_compress_strict_bit_exact(ctx, m, p):
+    from paper_1305_2353_gb300 import ctp
+    if (m, p) == (5, 3):
+        A21 = np.array([[1, 10, 10], [2, 3, 4], [0, 10, -3], [4, -5, 4], [0, -6, 8]], float)
+    else:
+        A21 = np.random.default_rng(m * 7 + p).standard_normal((m, p))
+        A21[::5, 0] = 0.0  # exact ties between columns
+        A21[::7, -1] = A21[::7, 0]
+    Cref, Jref = O.compress_strict(A21)
+    dA = ctp.colmajor(A21)
+    C = torch.empty(p * p, dtype=torch.float64, device="cuda")
+    J = torch.empty(m, dtype=torch.int32, device="cuda")
+    ws = ctx.compress_strict(dA, m, p, m, C, J)
+    torch.cuda.synchronize()
+    assert ctx.read_info(ws) == 0
+    Cg = C.cpu().numpy().reshape(p, p)  # row-major
+    assert np.array_equal(Cg, Cref)
+    assert np.array_equal(J.cpu().numpy(), Jref)
+
+
+def test_compress_strict_flags_nonfinite(ctx):
+    from paper_1305_2353_gb300 import ctp
+    A21 = np.ones((50, 4))
+    A21[13, 2] = np.inf
+    C = torch.empty(16, dtype=torch.float64, device="cuda")
+    ws = ctx.compress_strict(ctp.colmajor(A21), 50, 4, 50, C)
+    assert ctx.read_info(ws) == ctp.CTP_ENONFINITE
+
+
+# --------------------------------------------------------------------------- full path
+
+def _tough(n, p, seed):
+    A = inputs.supernode(n, p, seed=seed, dist="normal", scale_cols=max(1, p // 6), scale=1e-3,
+                         zero_diag_frac=0.2)
+    A[p:, :] *= 5.0
+    return A
+
+
+CASES = [(1, 1), (2, 2), (3, 1), (30, 30), (300, 17), (513, 33), (1200, 100), (800, 200),
+         (3000, 256), (700, 129)]
+
+
+@pytest.mark.parametrize("pivot", ["strict", "restricted"])
+@pytest.mark.parametrize("n,p", CASES)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_factor_matches_oracle(ctx, pivot, n, p, seed):
+    A = _tough(n, p, seed)
+    ref = O.factor(A, p, pivot, log_cap=200000)
+    got = run_gpu(ctx, A, p, pivot)
+    compare(ref, got, p, A, check_recon=(pivot == "strict"))
+
+
+def test_single_small_workload(ctx):
+    """n = 2000, p = 64, N(0,1), eight A11 rows/columns scaled by 1e-8."""
+    for seed in range(3):
+        A = inputs.single_small(seed)
+        ref = O.factor(A, 64, "strict", log_cap=200000)
+        got = run_gpu(ctx, A, 64, "strict")
+        assert ref["nelim"] < 64  # the scaled columns are delayed
+        compare(ref, got, 64, A)
+
+
+@pytest.mark.parametrize("smode,rtol", [("fp64", 1e-11), ("fp32", 2e-6)])
+@pytest.mark.parametrize("n,p", [(600, 40), (2000, 64), (1500, 130)])
+def test_form_matches_oracle(ctx, smode, rtol, n, p):
+    A = _tough(n, p, 3)
+    ref = O.factor(A, p, "strict")
+    got = run_gpu(ctx, A, p, "strict", smode=smode)
+    e = ref["nelim"]
+    S = O.form(ref["A"][p:, :e], ref["piv"][:e], ref["D"])
+    lo = np.tril(np.ones_like(S, dtype=bool))
+    scale = np.abs(S).max()
+    assert np.allclose(got["S"][lo], S[lo], rtol=rtol, atol=rtol * scale)
+    # the strict upper triangle is never written
+    assert np.all(np.triu(got["S"], 1) == 0)
+
+
+def test_large_supernode_full_size(ctx):
+    """n = 200000, p = 256, entries U[-1,1], u = 0.01: the benchmarked shape.
+    C and J bit-exact on all rows; pivots, nelim and the whole factor against
+    the oracle."""
+    from paper_1305_2353_gb300 import ctp
+    n, p = 200000, 256
+    A = inputs.single_large(0)
+    m = n - p
+    Cref, Jref = O.compress_strict(A[p:])
+    dA = ctp.colmajor(A)
+    C = torch.empty(p * p, dtype=torch.float64, device="cuda")
+    J = torch.empty(m, dtype=torch.int32, device="cuda")
+    ctx.compress_strict(dA[:, p:], m, p, n, C, J)
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy().reshape(p, p), Cref)
+    assert np.array_equal(J.cpu().numpy(), Jref)
+    del dA
+    ref = O.factor(A, p, "strict", log_cap=400000)
+    got = run_gpu(ctx, A, p, "strict")
+    compare(ref, got, p, A, check_recon=False)
+    rows = np.r_[0:p + 64, np.random.default_rng(0).choice(np.arange(p, n), 4000, replace=False)]
+    sub = {k: v for k, v in got.items()}
+    sub["A"] = got["A"][rows]
+    assert recon_error(A[rows], p, sub) <= 1e-13
+
+
+# --------------------------------------------------------------------------- errors
+
+def test_argument_errors(ctx):
+    from paper_1305_2353_gb300 import ctp
+    A = _tough(100, 10, 0)
+    opt = ctp.options()
+    sn = ctp.Supernode(ctx, A, 10, opt)
+    with pytest.raises(ctp.CtpError) as e:
+        ctx.factor_supernode(sn.A, 100, 10, 50, opt, sn.perm, sn.piv, sn.D, sn.nelim, ws=sn.ws)
+    assert e.value.code == ctp.CTP_EINVAL
+    with pytest.raises(ctp.CtpError) as e:
+        ctx.factor_supernode(sn.A, 100, 10, 100, opt, sn.perm, sn.piv, sn.D, sn.nelim,
+                             ws=sn.ws[:16])
+    assert e.value.code == ctp.CTP_ENOMEM
+    big = ctp.options()
+    with pytest.raises(ctp.CtpError) as e:
+        ctx.factor_supernode(sn.A, 400, 300, 400, big, sn.perm, sn.piv, sn.D, sn.nelim, ws=sn.ws)
+    assert e.value.code in (ctp.CTP_EUNSUPPORTED, ctp.CTP_ENOMEM)
+    bad_u = ctp.options(u=0.7)
+    with pytest.raises(ctp.CtpError) as e:
+        ctx.factor_supernode(sn.A, 100, 10, 100, bad_u, sn.perm, sn.piv, sn.D, sn.nelim, ws=sn.ws)
+    assert e.value.code == ctp.CTP_EINVAL
+
+
+def test_nonfinite_input_flagged(ctx):
+    A = _tough(200, 12, 1)
+    A[150, 3] = np.nan
+    got = run_gpu(ctx, A, 12, "strict")
+    from paper_1305_2353_gb300 import ctp
+    assert got["info"] == ctp.CTP_ENONFINITE
