@@ -1,0 +1,384 @@
+"""Benchmark: per-supernode LDL^T with compressed threshold pivoting on GB300.
+
+One step = one pass of the whole per-supernode hot path over one synthetic
+supernode: compression of A21, pivot search on [A11; C], Solve with the
+delayed-column update, and Form of the Schur complement S.
+
+Default workload: a single supernode shaped like the paper's large random
+examples (Section 7.1): n = 200000, p = 256, A11 symmetric and A21 with entries
+uniform in [-1, 1], u = 0.01, strict compressed pivoting, FP64 arithmetic, S
+stored as FP32 (lower triangle).  Every timed step factors its own fresh copy
+of the input (409 MB each, larger than L2), so no L2 flush is needed.
+
+Metric: GFLOP/s of the supernode factorization under the flop model
+  factor+solve = sum_{k=1..e} [(n-k) + 2((n-p)(p-k) + (p-k)(p-k+1)/2)]
+  form         = (n-p)(n-p+1) e
+with e = nelim (the pivots actually eliminated).  Compression and pivot search
+are counted as overhead, not as flops.
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same
+workload (the paper's method has no other reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM traffic per launch from ncu captures (profiles/), valid only for the
+# kernel source they were taken on (sha1 of the .cu file).
+NCU_TRAFFIC = {}
+
+
+def flops_model(n, p, e):
+    m = n - p
+    fs = 0
+    for k in range(1, e + 1):
+        fs += (n - k) + 2 * (m * (p - k) + (p - k) * (p - k + 1) // 2)
+    form = m * (m + 1) * e
+    return fs, form
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=200000)
+    ap.add_argument("--p", type=int, default=256)
+    ap.add_argument("--pivot", default="strict", choices=["strict", "relaxed", "restricted"])
+    ap.add_argument("--smode", default="fp32", choices=["none", "fp32", "fp64"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    kind = {"strict": "strict compressed", "relaxed": "relaxed compressed",
+            "restricted": "restricted"}[a.pivot]
+    return f"single supernode n={a.n} p={a.p}, A11/A21 U[-1,1], u=0.01, {kind} pivoting"
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(a, target_s=12.0):
+    """Time the CPU oracle (single thread) on a bounded sample of the workload:
+    the first m_s rows of A21 for the factor+solve and the first m_f rows for
+    the Form.  Returns (flops, seconds, description)."""
+    from oracle import oracle
+    from paper_1305_2353_gb300 import inputs
+    A = inputs.single_large(a.seed, n=a.n, p=a.p)
+    p = a.p
+    ms = min(a.n - p, 20000)
+    As = np.asfortranarray(A[:p + ms])
+    t0 = time.perf_counter()
+    r = oracle.factor(As, p, a.pivot)
+    t_fs = time.perf_counter() - t0
+    e = r["nelim"]
+    fs, _ = flops_model(p + ms, p, e)
+    mf = ms
+    if a.smode != "none" and e > 0:
+        # Form on the first m_f rows, sized to fit the time budget (~1 GFLOP/s)
+        budget = max(target_s - t_fs, 2.0)
+        mf = int(min(ms, max(200, np.sqrt(budget * 1.0e9 / max(e, 1)))))
+        t1 = time.perf_counter()
+        oracle.form(r["A"][p:p + mf, :e], r["piv"][:e], r["D"])
+        t_form = time.perf_counter() - t1
+        form = mf * (mf + 1) * e
+    else:
+        t_form, form = 0.0, 0
+    desc = (f"oracle factor+solve on the first {ms} A21 rows (n={p + ms}, p={p}, nelim={e}) and "
+            f"Form on the first {mf} rows; single-threaded C, -O2")
+    return fs + form, t_fs + t_form, desc
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for i in range(a.warmup + a.steps):
+        fl, t, desc = oracle_sample(a, target_s=6.0)
+        if i >= a.warmup:
+            vals.append((fl, t))
+    fl = sum(v[0] for v in vals)
+    t = sum(v[1] for v in vals)
+    value = fl / t / 1e9
+    line = {
+        "impl": "reference", "metric": "Supernode LDL^T GFLOP/s", "value": value,
+        "unit": "GFLOP/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * t / len(vals), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "pivot": a.pivot,
+                   "smode": a.smode},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fp64_peak_tflops(torch, dev):
+    """cuBLAS DGEMM throughput on this GPU, measured now (best of 5, 4096^3)."""
+    N = 4096
+    x = torch.randn(N, N, dtype=torch.float64, device=dev)
+    y = torch.randn(N, N, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        x @ y
+    best = 1e9
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        s.record()
+        x @ y
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e) / 1e3)
+    del x, y
+    return 2 * N ** 3 / best / 1e12
+
+
+def kernel_roofline(name, launches, ms, a, e, peaks):
+    """Algorithmic work of one launch of `name` and its roofline."""
+    n, p = a.n, a.p
+    m = n - p
+    t = ms / launches / 1e3
+    if name in ("compress_strict", "compress_relaxed"):
+        work = 8.0 * m * p
+        bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
+        achieved = work / t / 1e9
+    elif name in ("form_fp64", "solve_fp64"):
+        fs, form = flops_model(n, p, e)
+        work = form if name == "form_fp64" else fs
+        bound, unit, peak = "alu", "TFLOP/s", peaks["fp64_tflops"]
+        src = "cuBLAS DGEMM measured in this run (no FP64 entry in MEASURED_PEAKS.json)"
+        achieved = work / t / 1e12
+    else:
+        return None
+    traffic = None
+    rec = NCU_TRAFFIC.get(name)
+    if rec is not None:
+        src_file = os.path.join(ROOT, "paper_1305_2353_gb300", "csrc", rec["file"])
+        h = hashlib.sha1(open(src_file, "rb").read()).hexdigest()
+        if h == rec["sha1"]:
+            traffic = rec["bytes_per_unit"] * (m if rec["unit"] == "row" else 1)
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+            "work_per_launch": work, "launch_ms": ms / launches}
+
+
+def run_native(a):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    from paper_1305_2353_gb300 import ctp, inputs
+
+    peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {"hbm_gbs": 6800.0}
+    peaks = dict(peaks)
+    peaks["fp64_tflops"] = fp64_peak_tflops(torch, dev)
+
+    ctx = ctp.Context(local)
+    n, p = a.n, a.p
+    m = n - p
+    A_host = inputs.single_large(a.seed, n=n, p=p)
+    opt = ctp.options(pivot=a.pivot, smode=a.smode)
+    nbuf = a.warmup + a.steps
+    A0 = ctp.colmajor(A_host, dev)
+    bufs = [A0.clone() for _ in range(nbuf)]
+    perm = torch.empty(p, dtype=torch.int32, device=dev)
+    piv = torch.empty(p, dtype=torch.int32, device=dev)
+    D = torch.empty(2 * p, dtype=torch.float64, device=dev)
+    nelim = torch.empty(1, dtype=torch.int32, device=dev)
+    S = None
+    if a.smode != "none":
+        S = torch.empty((m, m), dtype=torch.float32 if a.smode == "fp32" else torch.float64,
+                        device=dev)
+    ws = ctx.workspace(n, p, opt)
+    stream = torch.cuda.current_stream()
+
+    def step(buf):
+        ctx.factor_supernode(buf, n, p, n, opt, perm, piv, D, nelim, S, max(m, 1), ws, stream)
+
+    for i in range(a.warmup):
+        step(bufs[i])
+    torch.cuda.synchronize()
+    if ctx.read_info(ws) != 0:
+        raise RuntimeError(f"device info {ctx.read_info(ws)}")
+    e = int(nelim.cpu()[0])
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ctx.profile_begin()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(a.steps):
+        step(bufs[a.warmup + i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    kern = ctx.profile_end()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt[0])
+    fs, form = flops_model(n, p, e)
+    flops_step = fs + (form if a.smode != "none" else 0)
+    value = world * flops_step * a.steps / (ms / 1e3) / 1e9
+    del bufs
+
+    # e2e through the public API with host buffers: H2D of the supernode from
+    # pinned memory, the factorization, D2H of the factor and the pivots
+    e2e = None
+    if not a.no_e2e:
+        hA = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()
+        hOut = torch.empty_like(hA).pin_memory()
+        hp = torch.empty(p, dtype=torch.int32).pin_memory()
+        hv = torch.empty(p, dtype=torch.int32).pin_memory()
+        hD = torch.empty(2 * p, dtype=torch.float64).pin_memory()
+        hn = torch.empty(1, dtype=torch.int32).pin_memory()
+        dA = torch.empty_like(A0)
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            step(dA)
+            hOut.copy_(dA, non_blocking=True)
+            hp.copy_(perm, non_blocking=True)
+            hv.copy_(piv, non_blocking=True)
+            hD.copy_(D, non_blocking=True)
+            hn.copy_(nelim, non_blocking=True)
+
+        for _ in range(max(1, a.warmup - 1)):
+            e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        s0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - s0
+        if dist:
+            tt = torch.tensor([te], dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt[0])
+        e2e = {"value": world * flops_step * a.steps / te / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": hA.numel() * 8,
+               "d2h_bytes_per_step": hOut.numel() * 8 + hp.numel() * 4 + hv.numel() * 4 +
+               hD.numel() * 8 + 4}
+
+    # dominant kernel
+    top = max(kern.items(), key=lambda kv: kv[1][1])
+    roof = kernel_roofline(top[0], top[1][0], top[1][1], a, e, peaks)
+    launches = sum(v[0] for v in kern.values())
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        fl, t, desc = oracle_sample(a)
+        cpu = {"value": fl / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": desc}
+    if rank == 0:
+        line = {
+            "metric": "Supernode LDL^T GFLOP/s", "value": value, "unit": "GFLOP/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": n, "p": p, "u": 0.01,
+                       "pivot": a.pivot, "prec": "fp64", "S": a.smode, "nelim": e,
+                       "flops_per_step": flops_step, "factor_solve_flops": fs,
+                       "form_flops": form if a.smode != "none" else 0,
+                       "l2": "inputs larger than L2: a distinct 409 MB input copy per step",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()},
+            "clocks": clk,
+            "fp64_dgemm_tflops": peaks["fp64_tflops"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_native(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,6 +109,16 @@ ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double 
                                double *C, int32_t *J, void *workspace, size_t ws_bytes,
                                void *stream);
 
+/* Relaxed compression of A21 (Section 4.2): for j = 1..p in turn, the A21 row
+ * holding the largest |a21(i,j)| among rows not chosen yet (lowest row on ties)
+ * becomes row j of C, with its signs.  A21: m x p device matrix (lda >= m).
+ * C: p x p device output, ROW-major.  rows: device int32[p] output (the chosen
+ * A21 row per C row, -1 when every row was already taken and C's row is zero),
+ * or NULL.  Exact: entries of C are copies of entries of A21. */
+ctp_status ctp_compress_relaxed(ctp_ctx *ctx, int64_t m, int32_t p, const double *A21,
+                                int64_t lda, double *C, int32_t *rows, void *workspace,
+                                size_t ws_bytes, void *stream);
+
 /* The whole per-supernode hot path (Section 1 task list; Figure 4.1):
  * compression of A21 (strict or relaxed), pivot selection by Listing 1 on
  * [A11; C] in FP64 (with the worst-case update eq. (4.3) of C for strict), the
@@ -143,6 +153,18 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
  * condition (CTP_ENONFINITE, CTP_ETIMEOUT, CTP_ECAPACITY).  The word is cleared
  * at the start of every factor or compress call. */
 ctp_status ctp_read_info(ctp_ctx *ctx, const void *workspace, int32_t *info_host, void *stream);
+
+
+/* Optional per-kernel timing.  Between ctp_profile_begin() and ctp_profile_end()
+ * every kernel this library launches is bracketed by two CUDA events recorded
+ * on its launch stream (at most 4096 launches are recorded).  ctp_profile_end()
+ * synchronises those events and reports, per kernel name, the number of
+ * launches and their summed device time in milliseconds.  names receives up to
+ * max_kernels NUL-terminated names of at most 47 characters, 48 bytes apart;
+ * *nkernels receives the number of distinct kernels. */
+ctp_status ctp_profile_begin(ctp_ctx *ctx);
+ctp_status ctp_profile_end(ctp_ctx *ctx, int32_t max_kernels, char *names, double *total_ms,
+                           int32_t *launches, int32_t *nkernels);
 
 #ifdef __cplusplus
 }

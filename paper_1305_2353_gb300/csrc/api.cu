@@ -1,17 +1,43 @@
 // api.cu -- the C ABI of libctp (declared in include/ctp.h): argument checks,
 // workspace layout and the launch sequence of the per-supernode hot path.
 #include <stdlib.h>
+#include <string.h>
 
 #include "ctp_internal.cuh"
+
+namespace {
+constexpr int kMaxRec = 4096;
+enum KernelId { K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_NUM_IDS };
+const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
+                                       "factor_cluster", "solve_fp64", "form_fp64"};
+}  // namespace
 
 struct ctp_ctx {
     int device;
     int num_sms;
+    bool profiling;
+    int nrec;
+    int rec_id[kMaxRec];
+    cudaEvent_t ev[2 * kMaxRec];
+    bool events_made;
 };
+
+// Launch `expr` (a cudaError_t expression enqueueing one kernel on `st`),
+// bracketed by profiling events when enabled.
+template <typename F>
+static cudaError_t timed(ctp_ctx *ctx, int id, cudaStream_t st, F &&launch) {
+    if (!ctx->profiling || ctx->nrec >= kMaxRec) return launch();
+    const int r = ctx->nrec++;
+    ctx->rec_id[r] = id;
+    cudaEventRecord(ctx->ev[2 * r], st);
+    cudaError_t e = launch();
+    cudaEventRecord(ctx->ev[2 * r + 1], st);
+    return e;
+}
 
 namespace ctp {
 
-WsLayout ws_layout(int64_t n, int p, const ctp_options *opt) {
+WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     WsLayout L;
     const int64_t m = n - p;
     size_t off = 0;
@@ -25,6 +51,7 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt) {
     L.W21 = off;
     off += align256(opt->smode != CTP_S_NONE ? sizeof(double) * (size_t)m * p : 0);
     L.aux = off;
+    off += align256(opt->pivot == CTP_PIV_RELAXED ? relaxed_aux_bytes(m, p, num_sms) : 0);
     L.total = off;
     return L;
 }
@@ -54,11 +81,16 @@ ctp_status ctp_create(ctp_ctx **ctx, int32_t device) {
     if (c == nullptr) return CTP_ENOMEM;
     c->device = device;
     c->num_sms = sms;
+    c->profiling = false;
+    c->nrec = 0;
+    c->events_made = false;
     *ctx = c;
     return CTP_OK;
 }
 
 ctp_status ctp_destroy(ctp_ctx *ctx) {
+    if (ctx != nullptr && ctx->events_made)
+        for (int i = 0; i < 2 * kMaxRec; i++) cudaEventDestroy(ctx->ev[i]);
     free(ctx);
     return CTP_OK;
 }
@@ -78,7 +110,7 @@ ctp_status ctp_workspace_size(const ctp_ctx *ctx, int64_t n, int32_t p, const ct
     if (ctx == nullptr || bytes == nullptr || p < 1 || n < p) return CTP_EINVAL;
     ctp_status s = check_opts(opt);
     if (s != CTP_OK) return s;
-    *bytes = ws_layout(n, p, opt).total;
+    *bytes = ws_layout(n, p, opt, ctx->num_sms).total;
     return CTP_OK;
 }
 
@@ -87,8 +119,9 @@ ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double 
                                void *stream) {
     if (ctx == nullptr || A21 == nullptr || C == nullptr || workspace == nullptr) return CTP_EINVAL;
     if (m < 0 || p < 1 || lda < (m > 0 ? m : 1)) return CTP_EINVAL;
+    if (p > kMaxP) return CTP_EUNSUPPORTED;
     ctp_options o = {0.01, 1e-20, CTP_PIV_STRICT, CTP_FP64, CTP_S_NONE, 0};
-    WsLayout L = ws_layout(m + p, p, &o);
+    WsLayout L = ws_layout(m + p, p, &o, ctx->num_sms);
     if (ws_bytes < L.total) return CTP_ENOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)workspace;
@@ -96,8 +129,29 @@ ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double 
     unsigned long long *keys = (unsigned long long *)(ws + L.C);
     CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
     CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));
-    CTP_CUDA(launch_compress_strict(A21, m, p, lda, keys, J, info, ctx->num_sms, st));
-    CTP_CUDA(launch_keys_to_rowmajor(keys, C, p, st));
+    CTP_CUDA(timed(ctx, K_COMPRESS_STRICT, st, [&] {
+        return launch_compress_strict(A21, m, p, lda, keys, J, info, ctx->num_sms, st);
+    }));
+    CTP_CUDA(timed(ctx, K_KEYS, st, [&] { return launch_keys_to_rowmajor(keys, C, p, st); }));
+    return CTP_OK;
+}
+
+ctp_status ctp_compress_relaxed(ctp_ctx *ctx, int64_t m, int32_t p, const double *A21,
+                                int64_t lda, double *C, int32_t *rows, void *workspace,
+                                size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || A21 == nullptr || C == nullptr || workspace == nullptr) return CTP_EINVAL;
+    if (m < 0 || p < 1 || lda < (m > 0 ? m : 1)) return CTP_EINVAL;
+    if (p > kMaxP) return CTP_EUNSUPPORTED;
+    ctp_options o = {0.01, 1e-20, CTP_PIV_RELAXED, CTP_FP64, CTP_S_NONE, 0};
+    WsLayout L = ws_layout(m + p, p, &o, ctx->num_sms);
+    if (ws_bytes < L.total) return CTP_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    int32_t *info = (int32_t *)(ws + L.info);
+    CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+    CTP_CUDA(timed(ctx, K_RELAXED, st, [&] {
+        return launch_compress_relaxed(A21, m, p, lda, C, rows, ws + L.aux, info, ctx->num_sms, st);
+    }));
     return CTP_OK;
 }
 
@@ -114,9 +168,9 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     const int64_t m = n - p;
     if (opt->smode != CTP_S_NONE && (S == nullptr || lds < (m > 0 ? m : 1))) return CTP_EINVAL;
     if (p > kMaxP) return CTP_EUNSUPPORTED;
-    if (opt->pivot == CTP_PIV_RELAXED || opt->pivot == CTP_PIV_TPP) return CTP_EUNSUPPORTED;
+    if (opt->pivot == CTP_PIV_TPP) return CTP_EUNSUPPORTED;
     if (opt->prec != CTP_FP64) return CTP_EUNSUPPORTED;
-    WsLayout L = ws_layout(n, p, opt);
+    WsLayout L = ws_layout(n, p, opt, ctx->num_sms);
     if (ws_bytes < L.total) return CTP_ENOMEM;
 
     cudaStream_t st = (cudaStream_t)stream;
@@ -141,19 +195,35 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     if (opt->pivot == CTP_PIV_STRICT) {
         unsigned long long *keys = (unsigned long long *)(ws + L.C);
         CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));
-        CTP_CUDA(launch_compress_strict(A + p, m, p, lda, keys, nullptr, info, ctx->num_sms, st));
+        CTP_CUDA(timed(ctx, K_COMPRESS_STRICT, st, [&] {
+            return launch_compress_strict(A + p, m, p, lda, keys, nullptr, info, ctx->num_sms, st);
+        }));
         fa.R = p;
         fa.abs_update = 1;
         fa.C = (const double *)keys;  // non-negative keys are the doubles themselves
+    } else if (opt->pivot == CTP_PIV_RELAXED) {
+        double *C = (double *)(ws + L.C);
+        CTP_CUDA(timed(ctx, K_RELAXED, st, [&] {
+            return launch_compress_relaxed(A + p, m, p, lda, C, nullptr, ws + L.aux, info,
+                                           ctx->num_sms, st);
+        }));
+        fa.R = p;
+        fa.abs_update = 0;
+        fa.C = C;
     } else {  // restricted: the tests look at A11 only
         fa.R = 0;
         fa.abs_update = 0;
         fa.C = nullptr;
     }
-    CTP_CUDA(launch_factor_cluster(fa, st));
-    CTP_CUDA(launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, st));
-    if (opt->smode != CTP_S_NONE)
-        CTP_CUDA(launch_form_fp64(A + p, lda, W21, m, m, nelim, S, lds, opt->smode, st));
+    CTP_CUDA(timed(ctx, K_FACTOR, st, [&] { return launch_factor_cluster(fa, st); }));
+    if (m > 0)
+        CTP_CUDA(timed(ctx, K_SOLVE, st, [&] {
+            return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, st);
+        }));
+    if (opt->smode != CTP_S_NONE && m > 0)
+        CTP_CUDA(timed(ctx, K_FORM, st, [&] {
+            return launch_form_fp64(A + p, lda, W21, m, m, nelim, S, lds, opt->smode, st);
+        }));
     return CTP_OK;
 }
 
@@ -162,6 +232,50 @@ ctp_status ctp_read_info(ctp_ctx *ctx, const void *workspace, int32_t *info_host
     cudaStream_t st = (cudaStream_t)stream;
     CTP_CUDA(cudaMemcpyAsync(info_host, workspace, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CTP_CUDA(cudaStreamSynchronize(st));
+    return CTP_OK;
+}
+
+ctp_status ctp_profile_begin(ctp_ctx *ctx) {
+    if (ctx == nullptr) return CTP_EINVAL;
+    if (!ctx->events_made) {
+        for (int i = 0; i < 2 * kMaxRec; i++)
+            if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) return CTP_ECUDA;
+        ctx->events_made = true;
+    }
+    ctx->nrec = 0;
+    ctx->profiling = true;
+    return CTP_OK;
+}
+
+ctp_status ctp_profile_end(ctp_ctx *ctx, int32_t max_kernels, char *names, double *total_ms,
+                           int32_t *launches, int32_t *nkernels) {
+    if (ctx == nullptr || nkernels == nullptr || max_kernels < 0) return CTP_EINVAL;
+    ctx->profiling = false;
+    double tot[K_NUM_IDS] = {};
+    int cnt[K_NUM_IDS] = {};
+    for (int r = 0; r < ctx->nrec; r++) {
+        if (cudaEventSynchronize(ctx->ev[2 * r + 1]) != cudaSuccess) return CTP_ECUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2 * r], ctx->ev[2 * r + 1]) != cudaSuccess)
+            return CTP_ECUDA;
+        tot[ctx->rec_id[r]] += ms;
+        cnt[ctx->rec_id[r]]++;
+    }
+    int k = 0;
+    for (int id = 0; id < K_NUM_IDS; id++) {
+        if (cnt[id] == 0) continue;
+        if (k < max_kernels) {
+            if (names) {
+                strncpy(names + 48 * k, kKernelNames[id], 47);
+                names[48 * k + 47] = 0;
+            }
+            if (total_ms) total_ms[k] = tot[id];
+            if (launches) launches[k] = cnt[id];
+        }
+        k++;
+    }
+    *nkernels = k;
+    ctx->nrec = 0;
     return CTP_OK;
 }
 

@@ -20,7 +20,7 @@ namespace ctp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTR = 16;      // rows per tile
+constexpr int kTR = 32;      // rows per tile (one 256-byte segment per column)
 constexpr int kStages = 3;   // tiles in flight per CTA
 constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long kInfKey = 0x7FF0000000000000ull;
@@ -123,15 +123,23 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
 
-        // (2) merge the tile's rows into C: warp w takes rows w, w+8, ...; lanes walk k
+        // (2) merge the tile's rows into C: warp w takes rows w, w+8, ...; lanes
+        // walk k.  All C keys of a row are loaded before any compare so that the
+        // L2 round trips overlap; the atomic fires only on a new maximum.
+        constexpr int KPL = kMaxP / 32;  // keys per lane
         for (int rr = warp; rr < nrows; rr += kThreads / 32) {
             const int j = rowJ[rr];
             unsigned long long *crow = Ckeys + (int64_t)j * p;
-            for (int k = lane; k < p; k += 32) {
-                unsigned long long key = abs_key(tile[k * (kTR + 1) + rr]);
-                unsigned long long cur = __ldcg(crow + k);
-                if (key > cur) atomicMax(crow + k, key);
+            unsigned long long cur[KPL], key[KPL];
+#pragma unroll
+            for (int q = 0; q < KPL; q++) {
+                const int k = lane + 32 * q;
+                cur[q] = (k < p) ? __ldcg(crow + k) : ~0ull;
+                key[q] = (k < p) ? abs_key(tile[k * (kTR + 1) + rr]) : 0ull;
             }
+#pragma unroll
+            for (int q = 0; q < KPL; q++)
+                if (key[q] > cur[q]) atomicMax(crow + lane + 32 * q, key[q]);
         }
         __syncthreads();  // the buffer is refilled next round
         stage = (stage + 1) % kStages;

@@ -27,13 +27,18 @@ struct WsLayout {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-WsLayout ws_layout(int64_t n, int p, const ctp_options *opt);
+WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms);
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns cudaError_t of the launch)
 cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
                                    unsigned long long *Ckeys, int32_t *J, int32_t *info,
                                    int num_sms, cudaStream_t st);
+int relaxed_segments(int64_t m, int p, int num_sms);
+size_t relaxed_aux_bytes(int64_t m, int p, int num_sms);
+cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t lda, double *C,
+                                    int32_t *rows, void *aux, int32_t *info, int num_sms,
+                                    cudaStream_t st);
 cudaError_t launch_keys_to_rowmajor(const unsigned long long *Ckeys, double *C, int p,
                                     cudaStream_t st);
 

@@ -7,13 +7,21 @@
 // 2p x p doubles -- 1 MB at p = 256, far beyond one SM -- and GB300's FP64 pipe
 // is narrow, so the right-looking updates must be spread over many SMs.  One
 // thread-block cluster of G CTAs owns the matrix: column c lives in the shared
-// memory of CTA (c mod G).  The pivot loop is sequential by definition; each
-// candidate costs one cluster barrier (two when it is accepted):
-//   phase A  the owner of candidate m runs the tests of Listing 1 on its own
-//            column and reads the partner column t through distributed shared
-//            memory (DSMEM); it publishes a small decision record;
-//   phase B  every CTA reads the decision, copies the pivot column(s) from
-//            their owners over DSMEM and updates its own live columns.
+// memory of CTA (c mod G); partner columns are read through distributed shared
+// memory (DSMEM).
+//
+// Listing 1 is sequential, but a rejected candidate leaves the matrix unchanged,
+// so every candidate tested between two acceptances sees the same matrix.  The
+// kernel therefore tests a window of candidates at once (one warp per candidate,
+// every CTA its own columns) and accepts the lowest-index candidate that passes;
+// all candidates before it in the window were rejected by Listing 1 as well.
+// A round costs one cluster barrier, plus one for the update when a pivot is
+// accepted, instead of one barrier per test:
+//   test round   each warp runs the zero test, the 2x2 test with its partner t
+//                (largest |a(m, j)| over live j < m) and the 1x1 test for one
+//                candidate; results are published as a bit mask per CTA;
+//   update       every CTA copies the pivot column(s) over DSMEM and applies the
+//                1x1 or 2x2 update to its own live columns.
 // Columns are never moved: accepted pivots leave the live set, and because the
 // paper's stable shift never reorders the remaining columns, the candidate
 // order is simply the original column order of the live columns.  The final
@@ -21,10 +29,9 @@
 // original order) is applied only when the factor is written back.
 //
 // Determinism: every CTA holds the same replicated control state (live flags,
-// nelim, m) and executes the same sequence of barriers; all decisions are taken
-// by one CTA and broadcast, so there is no divergence between CTAs.  The test
-// arithmetic uses explicitly rounded operations (no FMA contraction) so that
-// it matches the plain-CPU formulas up to the rounding of the inputs.
+// nelim, m) and executes the same sequence of barriers.  The test arithmetic
+// uses explicitly rounded operations (no FMA contraction) so that it matches
+// the plain-CPU formulas up to the rounding of the inputs.
 #include <cooperative_groups.h>
 
 #include "ctp_internal.cuh"
@@ -47,34 +54,28 @@ struct Decision {
 };
 
 struct Shared {
-    Decision dec[2];
+    Decision res[2][kMaxP];  // per own column slot (ncl <= kMaxP), double-buffered
     Decision cur;
-    double red[kNW];
-    int redi[kNW];
+    unsigned int mask[2][kMaxP / 32];  // passing candidates, by global column index
+    int hi[2];                         // first own candidate not tested this round
     unsigned char live[kMaxP];
     int order[kMaxP];
     int kind[kMaxP];
     int pos_of[kMaxP];
     double sD[2 * kMaxP + 2];
     double sInv[2 * kMaxP + 2];
+    int cand[kNW];
+    int cstar, hiall;
 };
 
-__device__ __forceinline__ double block_max(double v, Shared &sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sh.red[w] = v;
-    __syncthreads();
-    double r = sh.red[0];
-#pragma unroll
-    for (int i = 1; i < kNW; i++) r = fmax(r, sh.red[i]);
-    __syncthreads();
-    return r;
+    return v;
 }
 
-// argmax of v over threads, ties to the lowest index; idx < 0 means "none".
-__device__ __forceinline__ int block_argmax(double v, int idx, Shared &sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// argmax over the warp, ties to the lowest index; idx < 0 means "none".
+__device__ __forceinline__ int warp_argmax(double v, int idx) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         double ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -84,23 +85,7 @@ __device__ __forceinline__ int block_argmax(double v, int idx, Shared &sh) {
             idx = oi;
         }
     }
-    if (lane == 0) {
-        sh.red[w] = v;
-        sh.redi[w] = idx;
-    }
-    __syncthreads();
-    double bv = sh.red[0];
-    int bi = sh.redi[0];
-    for (int i = 1; i < kNW; i++) {
-        double ov = sh.red[i];
-        int oi = sh.redi[i];
-        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
-            bv = ov;
-            bi = oi;
-        }
-    }
-    __syncthreads();
-    return bi;
+    return idx;
 }
 
 // Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
@@ -136,6 +121,73 @@ __device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, 
     return ok;
 }
 
+// The tests of Listing 1 for candidate c (one warp): zero test, 2x2 with the
+// partner t, 1x1.  cm is the candidate's column (rows 0..p-1 A11, then outer).
+template <typename ColPtr>
+__device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColPtr colptr,
+                                                   const unsigned char *live, int p, int LD,
+                                                   double u, double small) {
+    const int lane = threadIdx.x & 31;
+    Decision d;
+    d.kind = DEC_REJECT;
+    d.t = -1;
+    d.m = c;
+    d.pad = 0;
+    d.d0 = d.d1 = d.d2 = d.i0 = d.i1 = d.i2 = 0.0;
+    double v = 0.0;
+    for (int i = lane; i < LD; i += 32)
+        if (i >= p || live[i]) v = fmax(v, fabs(cm[i]));
+    if (warp_max(v) < small) {
+        d.kind = DEC_ZERO;
+        return d;
+    }
+    // partner t: largest |a(c, j)| over live j < c, lowest j on ties
+    double bv = -1.0;
+    int bi = -1;
+    for (int j = lane; j < c; j += 32)
+        if (live[j]) {
+            double av = fabs(cm[j]);
+            if (bi < 0 || av > bv) {
+                bv = av;
+                bi = j;
+            }
+        }
+    const int t = warp_argmax(bv, bi);
+    double maxm2 = 0.0;
+    if (t >= 0) {
+        const double *ct = colptr(t);
+        double vm = 0.0, vt = 0.0;
+        for (int i = lane; i < LD; i += 32)
+            if (i >= p || (live[i] && i != t && i != c)) {
+                vm = fmax(vm, fabs(cm[i]));
+                vt = fmax(vt, fabs(ct[i]));
+            }
+        maxm2 = warp_max(vm);
+        const double maxt = warp_max(vt);
+        if (test_2x2(ct[t], cm[t], cm[c], maxt, maxm2, u, small, d)) {
+            d.kind = DEC_2X2;
+            d.t = t;
+            return d;
+        }
+    }
+    double maxm1;
+    if (t >= 0) {
+        maxm1 = fmax(maxm2, fabs(cm[t]));
+    } else {
+        double w = 0.0;
+        for (int i = lane; i < LD; i += 32)
+            if (i >= p || (live[i] && i != c)) w = fmax(w, fabs(cm[i]));
+        maxm1 = warp_max(w);
+    }
+    const double amm = cm[c];
+    if (fabs(amm) >= __dmul_rn(u, maxm1)) {
+        d.kind = DEC_1X1;
+        d.d0 = amm;
+        d.i0 = __ddiv_rn(1.0, amm);
+    }
+    return d;
+}
+
 __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) double dsm[];
@@ -144,10 +196,14 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
     const int p = a.p, R = a.R, LD = p + R;
     const int rank = (int)cluster.block_rank();
     const int ncl = (p + G - 1) / G;
-    double *cols = dsm;                 // [ncl][LD]
+    double *cols = dsm;                    // [ncl][LD]
     double *pc0 = dsm + (size_t)ncl * LD;  // pivot column copies
     double *pc1 = pc0 + LD;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nmask = (p + 31) / 32;
+    auto colptr = [&](int c) -> const double * {
+        return cluster.map_shared_rank(cols, c % G) + (size_t)(c / G) * LD;
+    };
 
     // ---- load: own columns of A11 (full symmetric) and of the outer rows
     bool nonfinite = false;
@@ -170,95 +226,81 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
     cluster.sync();
 
     const double u = a.u, small = a.small;
-    int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, step = 0;
+    int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, round = 0;
     for (;;) {
         if (nelim >= p) break;
         while (m < p && !sh.live[m]) m++;
         if (m >= p) {
-            if (!accepted) break;
+            if (!accepted) break;  // a whole sweep without a pivot: stop
             accepted = 0;
-            m = 0;
+            m = 0;  // new sweep from the first live column
             continue;
         }
-        const int owner = m % G, slot = step & 1;
-        // ---------------- phase A: tests of Listing 1 for candidate m
-        if (rank == owner) {
-            Decision d;
-            d.kind = DEC_REJECT;
-            d.t = -1;
-            d.m = m;
-            d.pad = 0;
-            d.d0 = d.d1 = d.d2 = d.i0 = d.i1 = d.i2 = 0.0;
-            const double *cm = cols + (size_t)(m / G) * LD;
-            double v = 0.0;
-            for (int i = tid; i < LD; i += kT)
-                if (i >= p || sh.live[i]) v = fmax(v, fabs(cm[i]));
-            const double cmax = block_max(v, sh);
-            if (cmax < small) {
-                d.kind = DEC_ZERO;
-            } else {
-                // partner t: largest |a(m, j)| over live j < m, lowest j on ties
-                double bv = -1.0;
-                int bi = -1;
-                for (int j = tid; j < m; j += kT)
-                    if (sh.live[j]) {
-                        double av = fabs(cm[j]);
-                        if (bi < 0 || av > bv) {
-                            bv = av;
-                            bi = j;
-                        }
-                    }
-                const int t = block_argmax(bv, bi, sh);
-                double maxm2 = 0.0;
-                if (t >= 0) {
-                    const double *ct = cluster.map_shared_rank(cols, t % G) + (size_t)(t / G) * LD;
-                    double vm = 0.0, vt = 0.0;
-                    for (int i = tid; i < LD; i += kT)
-                        if (i >= p || (sh.live[i] && i != t && i != m)) {
-                            vm = fmax(vm, fabs(cm[i]));
-                            vt = fmax(vt, fabs(ct[i]));
-                        }
-                    maxm2 = block_max(vm, sh);
-                    const double maxt = block_max(vt, sh);
-                    if (test_2x2(ct[t], cm[t], cm[m], maxt, maxm2, u, small, d)) {
-                        d.kind = DEC_2X2;
-                        d.t = t;
-                    }
+        const int buf = round & 1;
+        round++;
+        // ---------------- test round: one warp per own live candidate c >= m
+        if (tid < nmask) sh.mask[buf][tid] = 0u;
+        if (tid == 0) {
+            // the window: the first kNW own live columns >= m
+            int k = 0, hi = p;
+            for (int lc = 0; lc < ncl; lc++) {
+                const int c = lc * G + rank;
+                if (c >= p) break;
+                if (c < m || !sh.live[c]) continue;
+                if (k < kNW) {
+                    sh.cand[k++] = c;
+                } else {
+                    hi = c;
+                    break;
                 }
-                if (d.kind != DEC_2X2) {
-                    double maxm1;
-                    if (t >= 0) {
-                        maxm1 = fmax(maxm2, fabs(cm[t]));
-                    } else {
-                        double w = 0.0;
-                        for (int i = tid; i < LD; i += kT)
-                            if (i >= p || (sh.live[i] && i != m)) w = fmax(w, fabs(cm[i]));
-                        maxm1 = block_max(w, sh);
-                    }
-                    const double amm = cm[m];
-                    if (fabs(amm) >= __dmul_rn(u, maxm1)) {
-                        d.kind = DEC_1X1;
-                        d.d0 = amm;
-                        d.i0 = __ddiv_rn(1.0, amm);
+            }
+            for (int w = k; w < kNW; w++) sh.cand[w] = -1;
+            sh.hi[buf] = hi;
+        }
+        __syncthreads();
+        {
+            const int c = sh.cand[warp];
+            if (c >= 0) {
+                Decision d = test_candidate(c, cols + (size_t)(c / G) * LD, colptr, sh.live, p, LD,
+                                            u, small);
+                if (lane == 0) {
+                    sh.res[buf][c / G] = d;
+                    if (d.kind != DEC_REJECT) atomicOr(&sh.mask[buf][c >> 5], 1u << (c & 31));
+                }
+            }
+        }
+        cluster.sync();
+        // lowest passing candidate over the cluster, and the end of the tested window
+        if (tid == 0) {
+            int cstar = p, hi = p;
+            for (int r = 0; r < G; r++) {
+                const unsigned int *mk = cluster.map_shared_rank(&sh.mask[buf][0], r);
+                hi = min(hi, *cluster.map_shared_rank(&sh.hi[buf], r));
+                for (int w = 0; w < nmask; w++) {
+                    const unsigned int bits = mk[w];
+                    if (bits) {
+                        cstar = min(cstar, w * 32 + __ffs(bits) - 1);
+                        break;
                     }
                 }
             }
-            if (tid == 0) sh.dec[slot] = d;
+            sh.cstar = cstar;
+            sh.hiall = hi;
+            if (cstar < hi) sh.cur = *cluster.map_shared_rank(&sh.res[buf][cstar / G], cstar % G);
         }
-        cluster.sync();
-        if (tid == 0) sh.cur = *cluster.map_shared_rank(&sh.dec[slot], owner);
         __syncthreads();
-        const Decision dv = sh.cur;
-        step++;
-        if (dv.kind == DEC_REJECT) {
-            m++;
+        const int cstar = sh.cstar;
+        if (cstar >= sh.hiall) {
+            // every tested candidate before the window's end failed: the sweep
+            // continues there
+            m = sh.hiall;
             continue;
         }
+        const Decision dv = sh.cur;
         if (dv.kind == DEC_ZERO) {
-            __syncthreads();
             if (tid == 0) {
-                sh.live[m] = 0;
-                sh.order[nelim] = m;
+                sh.live[cstar] = 0;
+                sh.order[nelim] = cstar;
                 sh.kind[nelim] = CTP_PIVKIND_ZERO;
                 sh.sD[2 * nelim] = sh.sD[2 * nelim + 1] = 0.0;
                 sh.sInv[2 * nelim] = sh.sInv[2 * nelim + 1] = 0.0;
@@ -266,17 +308,19 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
             __syncthreads();
             nelim++;
             accepted = 1;
-            m++;
+            m = cstar + 1;
+            // no update; the next round writes the other buffers, and the round
+            // after that comes behind the next cluster barrier
             continue;
         }
-        // ---------------- phase B: apply the pivot to the own live columns
+        // ---------------- update: apply the pivot to the own live columns
         const int q0 = (dv.kind == DEC_2X2) ? dv.t : dv.m;
         const int q1 = (dv.kind == DEC_2X2) ? dv.m : -1;
         {
-            const double *s0 = cluster.map_shared_rank(cols, q0 % G) + (size_t)(q0 / G) * LD;
+            const double *s0 = colptr(q0);
             for (int i = tid; i < LD; i += kT) pc0[i] = s0[i];
             if (q1 >= 0) {
-                const double *s1 = cluster.map_shared_rank(cols, q1 % G) + (size_t)(q1 / G) * LD;
+                const double *s1 = colptr(q1);
                 for (int i = tid; i < LD; i += kT) pc1[i] = s1[i];
             }
         }
@@ -350,7 +394,7 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
         __syncthreads();
         nelim += (q1 < 0) ? 1 : 2;
         accepted = 1;
-        m++;
+        m = cstar + 1;
         cluster.sync();  // every update done before the next tests read columns
     }
 
@@ -444,7 +488,7 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st) {
     // preferred cluster width by p: more CTAs give more FP64 lanes to the
     // right-looking update; widen further if the columns do not fit on chip
     int G = a.p > 128 ? 16 : (a.p > 64 ? 8 : (a.p > 16 ? 4 : 1));
-    while (factor_smem(a.p, a.R, G) > 200 * 1024 && G < 16) G <<= 1;
+    while (factor_smem(a.p, a.R, G) > 160 * 1024 && G < 16) G <<= 1;
     size_t smem = factor_smem(a.p, a.R, G);
     cudaError_t err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
@@ -473,7 +517,7 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st) {
         if (err == cudaSuccess) err = cudaOccupancyMaxActiveClusters(&nclusters, k_factor_cluster, &cfg);
         if (err == cudaSuccess && nclusters > 0) break;
         (void)cudaGetLastError();
-        if (G <= 1 || factor_smem(a.p, a.R, G >> 1) > 200 * 1024) return err != cudaSuccess ? err : cudaErrorLaunchOutOfResources;
+        if (G <= 1 || factor_smem(a.p, a.R, G >> 1) > 160 * 1024) return err != cudaSuccess ? err : cudaErrorLaunchOutOfResources;
         G >>= 1;
     }
     return cudaLaunchKernelEx(&cfg, k_factor_cluster, a, G);

@@ -1,0 +1,248 @@
+// relaxed.cu -- K2: relaxed compression of A21 (Section 4.2).
+//
+// The paper's construction is sequential: for j = 1..p, the unflagged row with
+// the largest |a21(i,j)| (lowest row on ties) is flagged and copied into row j
+// of C.  Before column j at most j-1 rows are flagged, so its choice is always
+// among the j largest entries of column j in the order (|a| desc, row asc).  The
+// GPU form is therefore exact and one-pass:
+//   phase 1  (HBM-bound) each CTA streams one contiguous segment of one column
+//            and keeps the top K_j = j+1 entries of that segment: values that
+//            beat the current K-th best are appended to a shared buffer, which
+//            is compacted by a bitonic sort whenever it fills (rarely: for
+//            random data a handful of times per segment);
+//   phase 2  one CTA runs the paper's greedy: for each column it merges the
+//            sorted segment lists and takes the first unflagged row;
+//   phase 3  the chosen rows are gathered, with their signs, into C.
+// Magnitudes are compared as integer keys (sign bit cleared), so no FP64
+// arithmetic is involved and the result is bit-exact.
+#include "ctp_internal.cuh"
+
+namespace ctp {
+
+namespace {
+
+constexpr int kT1 = 512;      // threads per CTA in phase 1
+constexpr int kCap = 4096;    // candidate buffer (power of two)
+constexpr int kChunk = 2048;  // rows read per iteration (4 per thread)
+constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long kInfKey = 0x7FF0000000000000ull;
+
+struct Cand {
+    unsigned long long key;  // |a| as an integer key
+    int row;                 // A21 row
+    int pad;
+};
+
+// a precedes b in the paper's order: larger magnitude first, lower row on ties
+__device__ __forceinline__ bool before(const Cand &a, const Cand &b) {
+    return a.key > b.key || (a.key == b.key && a.row < b.row);
+}
+
+// Sort buf[0..N) (N a power of two) into descending order.
+__device__ void bitonic_desc(Cand *buf, int N) {
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    Cand a = buf[i], b = buf[ixj];
+                    const bool first_block = (i & k) == 0;  // this block descends
+                    const bool swap = first_block ? before(b, a) : before(a, b);
+                    if (swap) {
+                        buf[i] = b;
+                        buf[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+    int n = 1;
+    while (n < x) n <<= 1;
+    return n;
+}
+
+// Phase 1: CTA (seg, j) keeps the top K_j entries of rows [seg*L, (seg+1)*L) of column j.
+__global__ void __launch_bounds__(kT1)
+    k_relaxed_topk(const double *__restrict__ A21, int64_t m, int p, int64_t lda, int64_t L,
+                   int nseg, Cand *__restrict__ lists, int *__restrict__ lens,
+                   int32_t *__restrict__ info) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Cand *buf = reinterpret_cast<Cand *>(smraw);
+    __shared__ int cnt;
+    __shared__ Cand thr;  // current K-th best (valid when have_thr)
+    __shared__ int have_thr;
+    const int j = blockIdx.y, seg = blockIdx.x;
+    const int K = (int)((int64_t)j + 1 < m ? (int64_t)j + 1 : m);
+    const int64_t r0 = (int64_t)seg * L, r1 = (r0 + L < m) ? r0 + L : m;
+    const double *col = A21 + (int64_t)j * lda;
+    if (threadIdx.x == 0) {
+        cnt = 0;
+        have_thr = 0;
+        thr.key = 0;
+        thr.row = 0x7fffffff;
+    }
+    __syncthreads();
+    bool nonfinite = false;
+    for (int64_t base = r0; base < r1; base += kChunk) {
+        const int ht = have_thr;
+        const Cand th = thr;
+        double v[kChunk / kT1];
+#pragma unroll
+        for (int q = 0; q < kChunk / kT1; q++) {
+            const int64_t r = base + q * kT1 + threadIdx.x;
+            v[q] = (r < r1) ? __ldcs(col + r) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk / kT1; q++) {
+            const int64_t r = base + q * kT1 + threadIdx.x;
+            if (r >= r1) continue;
+            Cand c;
+            c.key = (unsigned long long)__double_as_longlong(v[q]) & kAbsMask;
+            c.row = (int)r;
+            c.pad = 0;
+            nonfinite |= c.key >= kInfKey;
+            if (!ht || before(c, th)) {
+                const int at = atomicAdd(&cnt, 1);
+                buf[at] = c;  // at < kCap: compaction keeps at least kChunk slots free
+            }
+        }
+        __syncthreads();
+        if (cnt > kCap - kChunk) {
+            const int n = cnt, N = next_pow2(n);
+            for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
+                buf[i].key = 0;
+                buf[i].row = 0x7fffffff;
+                buf[i].pad = 1;  // padding sorts last
+            }
+            __syncthreads();
+            bitonic_desc(buf, N);
+            if (threadIdx.x == 0) {
+                cnt = min(n, K);
+                if (n >= K) {
+                    have_thr = 1;
+                    thr = buf[K - 1];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // final compaction and output of the sorted top-K
+    {
+        const int n = cnt, N = next_pow2(max(n, 1));
+        for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
+            buf[i].key = 0;
+            buf[i].row = 0x7fffffff;
+            buf[i].pad = 1;
+        }
+        __syncthreads();
+        bitonic_desc(buf, N);
+        const int k = min(n, K);
+        Cand *out = lists + ((int64_t)j * nseg + seg) * (int64_t)p;
+        for (int i = threadIdx.x; i < k; i += blockDim.x) out[i] = buf[i];
+        if (threadIdx.x == 0) lens[j * nseg + seg] = k;
+    }
+    if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
+}
+
+// Phases 2 and 3: the greedy of Section 4.2 over the merged candidate lists,
+// then the gather of the chosen rows into C (row-major, signed).
+__global__ void __launch_bounds__(256)
+    k_relaxed_greedy(const double *__restrict__ A21, int64_t lda, int p, int nseg,
+                     const Cand *__restrict__ lists, const int *__restrict__ lens,
+                     double *__restrict__ C, int32_t *__restrict__ rows_out) {
+    __shared__ int chosen[kMaxP];
+    __shared__ int head[64];  // nseg <= 64
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        for (int j = 0; j < p; j++) {
+            for (int s = lane; s < nseg; s += 32) head[s] = 0;
+            __syncwarp();
+            int r = -1;
+            for (;;) {
+                // the best head over the segment lists of column j
+                Cand best;
+                best.key = 0;
+                best.row = 0x7fffffff;
+                int bs = -1;
+                for (int s = 0; s < nseg; s++) {
+                    const int h = head[s];
+                    if (h < lens[j * nseg + s]) {
+                        const Cand c = lists[((int64_t)j * nseg + s) * p + h];
+                        if (bs < 0 || before(c, best)) {
+                            best = c;
+                            bs = s;
+                        }
+                    }
+                }
+                if (bs < 0) break;  // every A21 row is already flagged
+                // flagged already?
+                bool hit = false;
+                for (int q = lane; q < j; q += 32) hit |= (chosen[q] == best.row);
+                hit = __any_sync(0xffffffffu, hit);
+                if (!hit) {
+                    r = best.row;
+                    break;
+                }
+                if (lane == 0) head[bs]++;
+                __syncwarp();
+            }
+            if (lane == 0) chosen[j] = r;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < p * p; idx += blockDim.x) {
+        const int j = idx / p, k = idx % p;
+        const int r = chosen[j];
+        C[idx] = (r >= 0) ? A21[(int64_t)k * lda + r] : 0.0;
+    }
+    if (rows_out != nullptr)
+        for (int j = threadIdx.x; j < p; j += blockDim.x) rows_out[j] = chosen[j];
+}
+
+}  // namespace
+
+size_t relaxed_aux_bytes(int64_t m, int p, int num_sms) {
+    const int nseg = relaxed_segments(m, p, num_sms);
+    return sizeof(Cand) * (size_t)p * nseg * p + sizeof(int) * (size_t)p * nseg;
+}
+
+int relaxed_segments(int64_t m, int p, int num_sms) {
+    // enough CTAs to cover the SMs several times, segments of at least 8 chunks
+    int64_t want = (8LL * num_sms + p - 1) / p;
+    int64_t maxseg = (m + 8 * kChunk - 1) / (8 * kChunk);
+    int64_t s = want < maxseg ? want : maxseg;
+    if (s < 1) s = 1;
+    if (s > 64) s = 64;
+    return (int)s;
+}
+
+cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t lda, double *C,
+                                    int32_t *rows, void *aux, int32_t *info, int num_sms,
+                                    cudaStream_t st) {
+    const int nseg = relaxed_segments(m, p, num_sms);
+    Cand *lists = reinterpret_cast<Cand *>(aux);
+    int *lens = reinterpret_cast<int *>(lists + (size_t)p * nseg * p);
+    if (m > 0) {
+        const int64_t L = (m + nseg - 1) / nseg;
+        const size_t smem = sizeof(Cand) * kCap;
+        cudaError_t err =
+            cudaFuncSetAttribute(k_relaxed_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        dim3 grid(nseg, p);
+        k_relaxed_topk<<<grid, kT1, smem, st>>>(A21, m, p, lda, L, nseg, lists, lens, info);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    } else {
+        cudaError_t err = cudaMemsetAsync(lens, 0, sizeof(int) * (size_t)p * nseg, st);
+        if (err != cudaSuccess) return err;
+    }
+    k_relaxed_greedy<<<1, 256, 0, st>>>(A21, lda, p, nseg, lists, lens, C, rows);
+    return cudaGetLastError();
+}
+
+}  // namespace ctp

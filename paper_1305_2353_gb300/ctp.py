@@ -29,7 +29,7 @@ SMODE = {"none": 0, "fp64": 1, "fp32": 2}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
 
 EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_compress_strict",
-           "ctp_factor_supernode", "ctp_read_info"]
+           "ctp_compress_relaxed", "ctp_factor_supernode", "ctp_read_info", "ctp_profile_begin", "ctp_profile_end"]
 
 
 class Options(ctypes.Structure):
@@ -65,9 +65,12 @@ def load(path: str = LIB_PATH):
     L.ctp_destroy.argtypes = [P]
     L.ctp_workspace_size.argtypes = [P, i64, i32, ctypes.POINTER(Options), ctypes.POINTER(sz)]
     L.ctp_compress_strict.argtypes = [P, i64, i32, P, i64, P, P, P, sz, P]
+    L.ctp_compress_relaxed.argtypes = [P, i64, i32, P, i64, P, P, P, sz, P]
     L.ctp_factor_supernode.argtypes = [P, i64, i32, P, i64, ctypes.POINTER(Options), P, P, P, P, P,
                                        i64, P, sz, P]
     L.ctp_read_info.argtypes = [P, P, ctypes.POINTER(i32), P]
+    L.ctp_profile_begin.argtypes = [P]
+    L.ctp_profile_end.argtypes = [P, i32, P, P, P, ctypes.POINTER(i32)]
     for f in EXPORTS[1:]:
         getattr(L, f).restype = ctypes.c_int
     _lib = L
@@ -132,6 +135,16 @@ class Context:
                                             _ptr(ws), ws.numel(), _stream(stream)))
         return ws
 
+    def compress_relaxed(self, A21, m, p, lda, C, rows=None, ws=None, stream=None):
+        """A21: m x p column-major device matrix; C: float64[p*p] (row-major
+        output); rows: int32[p] or None."""
+        if ws is None:
+            ws = self.workspace(m + p, p, options(pivot="relaxed"))
+        _check("ctp_compress_relaxed",
+               self.lib.ctp_compress_relaxed(self.handle, m, p, _ptr(A21), lda, _ptr(C), _ptr(rows),
+                                             _ptr(ws), ws.numel(), _stream(stream)))
+        return ws
+
     def factor_supernode(self, A, n, p, lda, opt, perm, piv, D, nelim, S=None, lds=0, ws=None,
                          stream=None):
         if ws is None:
@@ -141,6 +154,24 @@ class Context:
                                              _ptr(perm), _ptr(piv), _ptr(D), _ptr(nelim), _ptr(S),
                                              lds, _ptr(ws), ws.numel(), _stream(stream)))
         return ws
+
+    def profile_begin(self):
+        _check("ctp_profile_begin", self.lib.ctp_profile_begin(self.handle))
+
+    def profile_end(self):
+        """{kernel name: (launches, total device ms)} since profile_begin()."""
+        k = 32
+        names = ctypes.create_string_buffer(48 * k)
+        tot = (ctypes.c_double * k)()
+        cnt = (ctypes.c_int32 * k)()
+        nk = ctypes.c_int32()
+        _check("ctp_profile_end", self.lib.ctp_profile_end(self.handle, k, names, tot, cnt,
+                                                            ctypes.byref(nk)))
+        out = {}
+        for i in range(min(nk.value, k)):
+            nm = names.raw[48 * i:48 * i + 48].split(b"\0", 1)[0].decode()
+            out[nm] = (int(cnt[i]), float(tot[i]))
+        return out
 
     def read_info(self, ws, stream=None):
         v = ctypes.c_int32()
