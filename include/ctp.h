@@ -56,11 +56,12 @@ typedef enum {
     CTP_PIV_RESTRICTED = 3  /* restricted pivoting: tests look at A11 only, Section 3.2 */
 } ctp_pivot;
 
-/* Arithmetic of the Solve and Form steps.  Pivot selection, the 2x2 pivot
- * inversions and D11 are always FP64. */
+/* Arithmetic of the Form step.  Compression, pivot selection, the 2x2 pivot
+ * inversions, D11 and the Solve are always FP64. */
 typedef enum {
     CTP_FP64 = 0,  /* FP64 throughout */
-    CTP_BF16 = 1   /* Form on the tensor cores: BF16 operands, FP32 accumulation */
+    CTP_BF16 = 1   /* Form on the tensor cores: BF16 operands, FP32 accumulation and
+                      FP32 S (requires smode = CTP_S_FP32) */
 } ctp_prec;
 
 /* Storage of the Schur complement S (lower triangle of an m x m column-major

@@ -7,9 +7,9 @@
 
 namespace {
 constexpr int kMaxRec = 4096;
-enum KernelId { K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_NUM_IDS };
+enum KernelId { K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_NUM_IDS };
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
-                                       "factor_cluster", "solve_fp64", "form_fp64"};
+                                       "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16"};
 }  // namespace
 
 struct ctp_ctx {
@@ -48,8 +48,14 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     off += align256(compressed ? sizeof(double) * (size_t)p * p : 0);
     L.Dinv = off;
     off += align256(sizeof(double) * (2 * (size_t)p + 2));
+    const bool tc = opt->prec == CTP_BF16 && opt->smode != CTP_S_NONE;
     L.W21 = off;
-    off += align256(opt->smode != CTP_S_NONE ? sizeof(double) * (size_t)m * p : 0);
+    off += align256(opt->smode != CTP_S_NONE && !tc ? sizeof(double) * (size_t)m * p : 0);
+    const size_t nb = tc ? 2 * (size_t)m * form_tc_kpad(p) : 0;
+    L.Wb = off;
+    off += align256(nb);
+    L.Lb = off;
+    off += align256(nb);
     L.aux = off;
     off += align256(opt->pivot == CTP_PIV_RELAXED ? relaxed_aux_bytes(m, p, num_sms) : 0);
     L.total = off;
@@ -169,7 +175,8 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     if (opt->smode != CTP_S_NONE && (S == nullptr || lds < (m > 0 ? m : 1))) return CTP_EINVAL;
     if (p > kMaxP) return CTP_EUNSUPPORTED;
     if (opt->pivot == CTP_PIV_TPP) return CTP_EUNSUPPORTED;
-    if (opt->prec != CTP_FP64) return CTP_EUNSUPPORTED;
+    const bool tc = opt->prec == CTP_BF16 && opt->smode != CTP_S_NONE;
+    if (tc && opt->smode != CTP_S_FP32) return CTP_EUNSUPPORTED;  // the tensor-core Form writes FP32
     WsLayout L = ws_layout(n, p, opt, ctx->num_sms);
     if (ws_bytes < L.total) return CTP_ENOMEM;
 
@@ -177,7 +184,10 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     char *ws = (char *)workspace;
     int32_t *info = (int32_t *)(ws + L.info);
     double *Dinv = (double *)(ws + L.Dinv);
-    double *W21 = opt->smode != CTP_S_NONE ? (double *)(ws + L.W21) : nullptr;
+    double *W21 = (opt->smode != CTP_S_NONE && !tc) ? (double *)(ws + L.W21) : nullptr;
+    void *Wb = tc ? (void *)(ws + L.Wb) : nullptr;
+    void *Lbf = tc ? (void *)(ws + L.Lb) : nullptr;
+    const int Kp = form_tc_kpad(p);
     CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
 
     FactorArgs fa;
@@ -218,12 +228,18 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     CTP_CUDA(timed(ctx, K_FACTOR, st, [&] { return launch_factor_cluster(fa, st); }));
     if (m > 0)
         CTP_CUDA(timed(ctx, K_SOLVE, st, [&] {
-            return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, st);
+            return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, Wb, Lbf, Kp, st);
         }));
-    if (opt->smode != CTP_S_NONE && m > 0)
-        CTP_CUDA(timed(ctx, K_FORM, st, [&] {
-            return launch_form_fp64(A + p, lda, W21, m, m, nelim, S, lds, opt->smode, st);
-        }));
+    if (opt->smode != CTP_S_NONE && m > 0) {
+        if (tc)
+            CTP_CUDA(timed(ctx, K_FORM_TC, st, [&] {
+                return launch_form_tc(Wb, Lbf, m, Kp, nelim, (float *)S, lds, info, ctx->num_sms, st);
+            }));
+        else
+            CTP_CUDA(timed(ctx, K_FORM, st, [&] {
+                return launch_form_fp64(A + p, lda, W21, m, m, nelim, S, lds, opt->smode, st);
+            }));
+    }
     return CTP_OK;
 }
 

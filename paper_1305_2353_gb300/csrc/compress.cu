@@ -123,23 +123,38 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
 
-        // (2) merge the tile's rows into C: warp w takes rows w, w+8, ...; lanes
-        // walk k.  All C keys of a row are loaded before any compare so that the
-        // L2 round trips overlap; the atomic fires only on a new maximum.
-        constexpr int KPL = kMaxP / 32;  // keys per lane
-        for (int rr = warp; rr < nrows; rr += kThreads / 32) {
-            const int j = rowJ[rr];
-            unsigned long long *crow = Ckeys + (int64_t)j * p;
-            unsigned long long cur[KPL], key[KPL];
+        // (2) merge the tile's rows into C: warp w takes rows w, w+8, w+16, w+24;
+        // lanes walk k.  All C keys of the warp's rows are loaded before any
+        // compare so that the L2 round trips overlap; the atomic fires only on
+        // a new maximum.
+        constexpr int KPL = kMaxP / 32;          // keys per lane and row
+        constexpr int RPW = kTR / (kThreads / 32);  // rows per warp
+        {
+            unsigned long long cur[RPW][KPL];
 #pragma unroll
-            for (int q = 0; q < KPL; q++) {
-                const int k = lane + 32 * q;
-                cur[q] = (k < p) ? __ldcg(crow + k) : ~0ull;
-                key[q] = (k < p) ? abs_key(tile[k * (kTR + 1) + rr]) : 0ull;
+            for (int q = 0; q < RPW; q++) {
+                const int rr = warp + q * (kThreads / 32);
+                const unsigned long long *crow = Ckeys + (int64_t)(rr < nrows ? rowJ[rr] : 0) * p;
+#pragma unroll
+                for (int t = 0; t < KPL; t++) {
+                    const int k = lane + 32 * t;
+                    cur[q][t] = (rr < nrows && k < p) ? __ldcg(crow + k) : ~0ull;
+                }
             }
 #pragma unroll
-            for (int q = 0; q < KPL; q++)
-                if (key[q] > cur[q]) atomicMax(crow + lane + 32 * q, key[q]);
+            for (int q = 0; q < RPW; q++) {
+                const int rr = warp + q * (kThreads / 32);
+                if (rr >= nrows) continue;
+                unsigned long long *crow = Ckeys + (int64_t)rowJ[rr] * p;
+#pragma unroll
+                for (int t = 0; t < KPL; t++) {
+                    const int k = lane + 32 * t;
+                    if (k < p) {
+                        const unsigned long long key = abs_key(tile[k * (kTR + 1) + rr]);
+                        if (key > cur[q][t]) atomicMax(crow + k, key);
+                    }
+                }
+            }
         }
         __syncthreads();  // the buffer is refilled next round
         stage = (stage + 1) % kStages;

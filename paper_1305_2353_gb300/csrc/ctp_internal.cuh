@@ -19,10 +19,11 @@ constexpr int kInfoOk = 0;
 //   [0, 256)            info word + scratch counters
 //   C                   p*p doubles, row-major compressed matrix (strict: as uint64 keys)
 //   Dinv                2p doubles: inverse pivot blocks, same slots as D
-//   W21                 m*p doubles (FP64 Y = L21 D11) when the Form step runs
+//   W21                 m*p doubles (FP64 Y = L21 D11) when the FP64 Form step runs
+//   Wb, Lb              m*Kp BF16 copies of Y and L21 for the tensor-core Form
 //   aux                 method-specific scratch (relaxed candidate lists)
 struct WsLayout {
-    size_t info, C, Dinv, W21, aux, total;
+    size_t info, C, Dinv, W21, Wb, Lb, aux, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -58,7 +59,13 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st);
 
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,
-                              double *W21, int64_t ldw, cudaStream_t st);
+                              double *W21, int64_t ldw, void *Wb, void *Lb, int Kp,
+                              cudaStream_t st);
+
+// K-padding of the BF16 operand copies used by the tensor-core Form.
+int form_tc_kpad(int p);
+cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
+                           float *S, int64_t lds, int32_t *info, int num_sms, cudaStream_t st);
 
 cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
                              int64_t m, const int32_t *nelim, void *S, int64_t lds, int smode,

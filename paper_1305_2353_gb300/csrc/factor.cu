@@ -68,26 +68,6 @@ struct Shared {
     int cstar, hiall;
 };
 
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// argmax over the warp, ties to the lowest index; idx < 0 means "none".
-__device__ __forceinline__ int warp_argmax(double v, int idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (oi >= 0 && (idx < 0 || ov > v || (ov == v && oi < idx))) {
-            v = ov;
-            idx = oi;
-        }
-    }
-    return idx;
-}
-
 // Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
 // test of eq. (2.2), |D^-1| (maxt, maxm)^T <= 1/u.  Fills d on acceptance.
 __device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, double maxt,
@@ -121,8 +101,25 @@ __device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, 
     return ok;
 }
 
+__device__ __forceinline__ unsigned long long akey(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ double key_val(unsigned long long k) {
+    return __longlong_as_double((long long)k);
+}
+
 // The tests of Listing 1 for candidate c (one warp): zero test, 2x2 with the
 // partner t, 1x1.  cm is the candidate's column (rows 0..p-1 A11, then outer).
+// Column maxima of |a| are taken on the IEEE bit patterns with the sign cleared
+// (integer order = magnitude order), which keeps the scans off the FP64 pipe.
 template <typename ColPtr>
 __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColPtr colptr,
                                                    const unsigned char *live, int p, int LD,
@@ -134,36 +131,49 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     d.m = c;
     d.pad = 0;
     d.d0 = d.d1 = d.d2 = d.i0 = d.i1 = d.i2 = 0.0;
-    double v = 0.0;
+    unsigned long long v = 0;
     for (int i = lane; i < LD; i += 32)
-        if (i >= p || live[i]) v = fmax(v, fabs(cm[i]));
-    if (warp_max(v) < small) {
+        if (i >= p || live[i]) {
+            const unsigned long long k = akey(cm[i]);
+            v = k > v ? k : v;
+        }
+    if (key_val(warp_max_key(v)) < small) {
         d.kind = DEC_ZERO;
         return d;
     }
     // partner t: largest |a(c, j)| over live j < c, lowest j on ties
-    double bv = -1.0;
+    unsigned long long bv = 0;
     int bi = -1;
     for (int j = lane; j < c; j += 32)
         if (live[j]) {
-            double av = fabs(cm[j]);
-            if (bi < 0 || av > bv) {
-                bv = av;
+            const unsigned long long k = akey(cm[j]);
+            if (bi < 0 || k > bv) {
+                bv = k;
                 bi = j;
             }
         }
-    const int t = warp_argmax(bv, bi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    const int t = bi;
     double maxm2 = 0.0;
     if (t >= 0) {
         const double *ct = colptr(t);
-        double vm = 0.0, vt = 0.0;
+        unsigned long long vm = 0, vt = 0;
         for (int i = lane; i < LD; i += 32)
             if (i >= p || (live[i] && i != t && i != c)) {
-                vm = fmax(vm, fabs(cm[i]));
-                vt = fmax(vt, fabs(ct[i]));
+                const unsigned long long km = akey(cm[i]), kt = akey(ct[i]);
+                vm = km > vm ? km : vm;
+                vt = kt > vt ? kt : vt;
             }
-        maxm2 = warp_max(vm);
-        const double maxt = warp_max(vt);
+        maxm2 = key_val(warp_max_key(vm));
+        const double maxt = key_val(warp_max_key(vt));
         if (test_2x2(ct[t], cm[t], cm[c], maxt, maxm2, u, small, d)) {
             d.kind = DEC_2X2;
             d.t = t;
@@ -174,10 +184,13 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     if (t >= 0) {
         maxm1 = fmax(maxm2, fabs(cm[t]));
     } else {
-        double w = 0.0;
+        unsigned long long w = 0;
         for (int i = lane; i < LD; i += 32)
-            if (i >= p || (live[i] && i != c)) w = fmax(w, fabs(cm[i]));
-        maxm1 = warp_max(w);
+            if (i >= p || (live[i] && i != c)) {
+                const unsigned long long k = akey(cm[i]);
+                w = k > w ? k : w;
+            }
+        maxm1 = key_val(warp_max_key(w));
     }
     const double amm = cm[c];
     if (fabs(amm) >= __dmul_rn(u, maxm1)) {
@@ -270,23 +283,31 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
             }
         }
         cluster.sync();
-        // lowest passing candidate over the cluster, and the end of the tested window
-        if (tid == 0) {
-            int cstar = p, hi = p;
-            for (int r = 0; r < G; r++) {
-                const unsigned int *mk = cluster.map_shared_rank(&sh.mask[buf][0], r);
-                hi = min(hi, *cluster.map_shared_rank(&sh.hi[buf], r));
+        // lowest passing candidate over the cluster, and the end of the tested
+        // window: lane r of warp 0 reads CTA r's mask and window end over DSMEM
+        if (warp == 0) {
+            int cs = p, h = p;
+            if (lane < G) {
+                h = *cluster.map_shared_rank(&sh.hi[buf], lane);
+                const unsigned int *mk = cluster.map_shared_rank(&sh.mask[buf][0], lane);
                 for (int w = 0; w < nmask; w++) {
                     const unsigned int bits = mk[w];
                     if (bits) {
-                        cstar = min(cstar, w * 32 + __ffs(bits) - 1);
+                        cs = w * 32 + __ffs(bits) - 1;
                         break;
                     }
                 }
             }
-            sh.cstar = cstar;
-            sh.hiall = hi;
-            if (cstar < hi) sh.cur = *cluster.map_shared_rank(&sh.res[buf][cstar / G], cstar % G);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                cs = min(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+                h = min(h, __shfl_xor_sync(0xffffffffu, h, o));
+            }
+            if (lane == 0) {
+                sh.cstar = cs;
+                sh.hiall = h;
+                if (cs < h) sh.cur = *cluster.map_shared_rank(&sh.res[buf][cs / G], cs % G);
+            }
         }
         __syncthreads();
         const int cstar = sh.cstar;
@@ -332,34 +353,36 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
             if (!sh.live[c] || c == q0 || c == q1) continue;
             double *col = cols + (size_t)lc * LD;
             if (q1 < 0) {
-                // 1x1: a(i,c) -= a(i,q) a(c,q) / d  (symmetric in i and c)
-                const double inv = dv.i0, ainv = fabs(dv.i0);
-                const double akq = pc0[c], aakq = fabs(akq);
+                // 1x1: a(i,c) -= a(i,q) (a(c,q) / d); C rows (strict): c += chat |a(c,q)|
+                const double s0 = pc0[c] * dv.i0;
+                const double as0 = fabs(pc0[c]) * fabs(dv.i0);
                 for (int i = tid; i < LD; i += kT) {
                     if (i < p) {
                         if (!sh.live[i] || i == q0) continue;
-                        col[i] -= (pc0[i] * akq) * inv;
+                        col[i] -= pc0[i] * s0;
                     } else if (abs_rows) {
-                        col[i] += (pc0[i] * aakq) * ainv;  // eq. (4.3)
+                        col[i] += pc0[i] * as0;  // eq. (4.3)
                     } else {
-                        col[i] -= (pc0[i] * akq) * inv;
+                        col[i] -= pc0[i] * s0;
                     }
                 }
             } else {
-                // 2x2: a(i,c) -= [a(i,t) a(i,m)] D^-1 [a(c,t) a(c,m)]^T
+                // 2x2: a(i,c) -= [a(i,t) a(i,m)] (D^-1 [a(c,t) a(c,m)]^T)
                 const double i11 = dv.i0, i21 = dv.i1, i22 = dv.i2;
                 const double b0 = pc0[c], b1 = pc1[c];
+                const double s0 = i11 * b0 + i21 * b1, s1 = i21 * b0 + i22 * b1;
                 const double ab0 = fabs(b0), ab1 = fabs(b1);
-                const double j11 = fabs(i11), j21 = fabs(i21), j22 = fabs(i22);
+                const double as0 = fabs(i11) * ab0 + fabs(i21) * ab1;
+                const double as1 = fabs(i21) * ab0 + fabs(i22) * ab1;
                 for (int i = tid; i < LD; i += kT) {
                     const double x0 = pc0[i], x1 = pc1[i];
                     if (i < p) {
                         if (!sh.live[i] || i == q0 || i == q1) continue;
-                        col[i] -= i11 * (x0 * b0) + i21 * (x0 * b1 + x1 * b0) + i22 * (x1 * b1);
+                        col[i] -= x0 * s0 + x1 * s1;
                     } else if (abs_rows) {
-                        col[i] += j11 * (x0 * ab0) + j21 * (x0 * ab1 + x1 * ab0) + j22 * (x1 * ab1);
+                        col[i] += x0 * as0 + x1 * as1;
                     } else {
-                        col[i] -= i11 * (x0 * b0) + i21 * (x0 * b1 + x1 * b0) + i22 * (x1 * b1);
+                        col[i] -= x0 * s0 + x1 * s1;
                     }
                 }
             }

@@ -1,0 +1,367 @@
+// form_tc.cu -- K6 (tensor cores): the Form task S = L21 D11 L21^T = W21 L21^T
+// (Section 1 task list), lower triangle, with BF16 operands and FP32
+// accumulation on the 5th-generation tensor cores (tcgen05), S stored as FP32.
+//
+// Layout: W21 and L21 are BF16 copies written by the Solve kernel, row-major
+// m x Kp (K = pivot position contiguous, Kp = p rounded up to 64, zero beyond
+// e).  Both GEMM operands are therefore K-major, which is what the tensor core
+// reads directly: S(i,j) = sum_k W21(i,k) L21(j,k).
+//
+// Kernel: persistent, one CTA per SM, walking the tiles of the lower triangle
+// (128 rows of S by 256 columns).  Warp roles:
+//   warp 0     TMA producer: 128B-swizzled K-blocks (64 BF16 = 128 bytes per
+//              row) of W21 (128 rows) and L21 (256 rows) into a 4-stage ring;
+//              also allocates and frees the tensor memory.
+//   warp 1     MMA issuer: one thread issues tcgen05.mma (M=128, N=256, K=16)
+//              into one of two FP32 accumulators of 256 TMEM columns each and
+//              commits stage releases and accumulator completion to mbarriers.
+//   warps 2-9  epilogue: tcgen05.ld of a 32-lane x 32-column slice, coalesced
+//              stores of column-major S (lanes are consecutive rows), masking
+//              the strict upper triangle; the accumulator is handed back as
+//              soon as it has been read, so MMA of the next tile overlaps the
+//              stores of this one.
+// Every mbarrier wait is bounded; on timeout the kernel records CTP_ETIMEOUT in
+// the info word, stops issuing work, waits for nothing further, frees its
+// tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "ctp_internal.cuh"
+
+namespace ctp {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4;
+constexpr int kUmmaK = 16;
+constexpr int kEpiWarps = 8;
+constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
+constexpr uint32_t kStageA = kBM * kBK * 2;  // 16 KB
+constexpr uint32_t kStageB = kBN * kBK * 2;  // 32 KB
+constexpr uint32_t kTmemCols = 512;          // two 256-column FP32 accumulators
+constexpr long kSpinLimit = 1L << 22;
+
+struct Bars {
+    unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of `bar` with the given parity; false on timeout
+// or when another role has already aborted.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, Bars *b) {
+    for (long it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && *(volatile int *)&b->abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand in the canonical
+// 128-byte-swizzle layout written by TMA: rows of 128 bytes, groups of 8 rows
+// 1024 bytes apart (stride byte offset), version bits 46-47 = 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Tiles of the lower triangle: row block a (128 rows) meets column blocks
+// 0..floor(a/2) (256 columns), so T(a) = a + floor(a/2) floor((a-1)/2) tiles
+// precede row block a.
+__host__ __device__ inline int64_t tiles_before(int64_t a) {
+    return a + (a / 2) * ((a - 1) / 2);
+}
+__device__ __forceinline__ void decode_tile(int64_t t, int nM, int &ti, int &tj) {
+    int lo = 0, hi = nM;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tiles_before(mid) <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    ti = lo;
+    tj = (int)(t - tiles_before(lo));
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_form_tc(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapL,
+              int64_t m, const int32_t *__restrict__ nelim_p, float *__restrict__ S, int64_t lds,
+              int32_t *__restrict__ info) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ Bars bars;
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;                               // [kStages][kStageA]
+    uint8_t *sB = smem + (size_t)kStages * kStageA;   // [kStages][kStageB]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = *nelim_p;
+    const int KB = (e + kBK - 1) / kBK;
+    const int nM = (int)((m + kBM - 1) / kBM);
+    const int64_t ntiles = tiles_before(nM);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&bars.full[s], 1);
+            mbar_init(&bars.empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bars.acc_full[b], 1);
+            mbar_init(&bars.acc_empty[b], kEpiWarps);
+        }
+        bars.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&bars.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_base;
+    const uint32_t idesc = idesc_bf16(kBM, kBN);
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0 && KB > 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int ti, tj;
+                decode_tile(t, nM, ti, tj);
+                bool ok = true;
+                for (int kb = 0; kb < KB; kb++) {
+                    if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&bars.full[stage], kStageA + kStageB);
+                    tma_load_2d(sA + (size_t)stage * kStageA, &mapW, kb * kBK, ti * kBM, &bars.full[stage]);
+                    tma_load_2d(sB + (size_t)stage * kStageB, &mapL, kb * kBK, tj * kBN, &bars.full[stage]);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) {
+                    atomicExch(&bars.abort, 1);
+                    break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, accphase = 0;
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars)) {
+                    atomicExch(&bars.abort, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(acc * kBN);
+                bool ok = true;
+                for (int kb = 0; kb < KB; kb++) {
+                    if (!mbar_wait(&bars.full[stage], phase, &bars)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + (size_t)stage * kStageA);
+                    const uint32_t b0 = smem_u32(sB + (size_t)stage * kStageB);
+#pragma unroll
+                    for (int k = 0; k < kBK / kUmmaK; k++) {
+                        // advance 16 BF16 = 32 bytes along K inside the swizzled rows
+                        umma_bf16(dt, sdesc(a0 + k * 32), sdesc(b0 + k * 32), idesc,
+                                  (kb > 0 || k > 0) ? 1u : 0u);
+                    }
+                    umma_commit(&bars.empty[stage]);  // stage free once these MMAs finish
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) {
+                    atomicExch(&bars.abort, 1);
+                    break;
+                }
+                umma_commit(&bars.acc_full[acc]);  // accumulator ready
+                if (++acc == 2) {
+                    acc = 0;
+                    accphase ^= 1u;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9
+        const int q = warp & 3;             // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;   // 128-column half of the 256-column tile
+        int acc = 0;
+        uint32_t accphase = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int ti, tj;
+            decode_tile(t, nM, ti, tj);
+            if (!mbar_wait(&bars.acc_full[acc], accphase, &bars)) {
+                if (lane == 0) atomicExch(&bars.abort, 1);
+                break;
+            }
+            tc_fence_after();
+            const int64_t i = (int64_t)ti * kBM + q * 32 + lane;
+            const int64_t jbase = (int64_t)tj * kBN + half * 128;
+#pragma unroll 1
+            for (int c = 0; c < 4; c++) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + half * 128 + c * 32);
+                tmem_ld32(taddr, r);
+                const int64_t j0 = jbase + c * 32;
+                if (i < m) {
+#pragma unroll
+                    for (int x = 0; x < 32; x++) {
+                        const int64_t j = j0 + x;
+                        if (j <= i && j < m) S[j * lds + i] = (KB > 0) ? __uint_as_float(r[x]) : 0.0f;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.acc_empty[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                accphase ^= 1u;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && bars.abort) atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn == nullptr) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (enc == nullptr) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int form_tc_kpad(int p) { return (p + kBK - 1) / kBK * kBK; }
+
+cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
+                           float *S, int64_t lds, int32_t *info, int num_sms, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    if ((((uintptr_t)Wb) | ((uintptr_t)Lb)) & 15) return cudaErrorMisalignedAddress;
+    CUtensorMap mW, mL;
+    if (!make_map(&mW, Wb, m, Kp, kBM) || !make_map(&mL, Lb, m, Kp, kBN)) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kStages * (kStageA + kStageB) + 1024;
+    cudaError_t err = cudaFuncSetAttribute(k_form_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int nM = (int)((m + kBM - 1) / kBM);
+    const int64_t ntiles = tiles_before(nM);
+    const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+    k_form_tc<<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, info);
+    return cudaGetLastError();
+}
+
+}  // namespace ctp

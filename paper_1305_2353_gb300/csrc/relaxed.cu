@@ -38,20 +38,25 @@ __device__ __forceinline__ bool before(const Cand &a, const Cand &b) {
     return a.key > b.key || (a.key == b.key && a.row < b.row);
 }
 
-// Sort buf[0..N) (N a power of two) into descending order.
-__device__ void bitonic_desc(Cand *buf, int N) {
+// Sort (key, row)[0..N) (N a power of two) into the paper's order (larger
+// magnitude first, lower row on ties).  Keys and rows live in separate arrays
+// so that each thread's accesses are 8- and 4-byte words (few bank conflicts).
+__device__ void bitonic_desc(unsigned long long *key, int *row, int N) {
     for (int k = 2; k <= N; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < N; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    Cand a = buf[i], b = buf[ixj];
-                    const bool first_block = (i & k) == 0;  // this block descends
-                    const bool swap = first_block ? before(b, a) : before(a, b);
-                    if (swap) {
-                        buf[i] = b;
-                        buf[ixj] = a;
-                    }
+            for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+                // t-th pair of this phase: i has bit j clear
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                const int ixj = i | j;
+                const unsigned long long ka = key[i], kb = key[ixj];
+                const int ra = row[i], rb = row[ixj];
+                const bool a_first = ka > kb || (ka == kb && ra < rb);
+                const bool first_block = (i & k) == 0;  // this block descends
+                if (first_block != a_first) {
+                    key[i] = kb;
+                    key[ixj] = ka;
+                    row[i] = rb;
+                    row[ixj] = ra;
                 }
             }
             __syncthreads();
@@ -71,10 +76,11 @@ __global__ void __launch_bounds__(kT1)
                    int nseg, Cand *__restrict__ lists, int *__restrict__ lens,
                    int32_t *__restrict__ info) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    Cand *buf = reinterpret_cast<Cand *>(smraw);
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(smraw);  // [kCap]
+    int *row = reinterpret_cast<int *>(key + kCap);                           // [kCap]
     __shared__ int cnt;
-    __shared__ Cand thr;  // current K-th best (valid when have_thr)
-    __shared__ int have_thr;
+    __shared__ unsigned long long thr_key;  // current K-th best (valid when have_thr)
+    __shared__ int thr_row, have_thr;
     const int j = blockIdx.y, seg = blockIdx.x;
     const int K = (int)((int64_t)j + 1 < m ? (int64_t)j + 1 : m);
     const int64_t r0 = (int64_t)seg * L, r1 = (r0 + L < m) ? r0 + L : m;
@@ -82,14 +88,33 @@ __global__ void __launch_bounds__(kT1)
     if (threadIdx.x == 0) {
         cnt = 0;
         have_thr = 0;
-        thr.key = 0;
-        thr.row = 0x7fffffff;
+        thr_key = 0;
+        thr_row = 0x7fffffff;
     }
     __syncthreads();
     bool nonfinite = false;
+    auto compact = [&](bool final) {
+        const int n = cnt, N = next_pow2(n > 1 ? n : 1);
+        for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
+            key[i] = 0;
+            row[i] = 0x7fffffff;  // padding sorts last
+        }
+        __syncthreads();
+        bitonic_desc(key, row, N);
+        if (!final && threadIdx.x == 0) {
+            cnt = n < K ? n : K;
+            if (n >= K) {
+                have_thr = 1;
+                thr_key = key[K - 1];
+                thr_row = row[K - 1];
+            }
+        }
+        __syncthreads();
+    };
     for (int64_t base = r0; base < r1; base += kChunk) {
         const int ht = have_thr;
-        const Cand th = thr;
+        const unsigned long long tk = thr_key;
+        const int tr = thr_row;
         double v[kChunk / kT1];
 #pragma unroll
         for (int q = 0; q < kChunk / kT1; q++) {
@@ -100,51 +125,29 @@ __global__ void __launch_bounds__(kT1)
         for (int q = 0; q < kChunk / kT1; q++) {
             const int64_t r = base + q * kT1 + threadIdx.x;
             if (r >= r1) continue;
-            Cand c;
-            c.key = (unsigned long long)__double_as_longlong(v[q]) & kAbsMask;
-            c.row = (int)r;
-            c.pad = 0;
-            nonfinite |= c.key >= kInfKey;
-            if (!ht || before(c, th)) {
+            const unsigned long long k = (unsigned long long)__double_as_longlong(v[q]) & kAbsMask;
+            nonfinite |= k >= kInfKey;
+            if (!ht || k > tk || (k == tk && (int)r < tr)) {
                 const int at = atomicAdd(&cnt, 1);
-                buf[at] = c;  // at < kCap: compaction keeps at least kChunk slots free
+                key[at] = k;  // at < kCap: a compaction keeps at least kChunk slots free
+                row[at] = (int)r;
             }
         }
         __syncthreads();
-        if (cnt > kCap - kChunk) {
-            const int n = cnt, N = next_pow2(n);
-            for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
-                buf[i].key = 0;
-                buf[i].row = 0x7fffffff;
-                buf[i].pad = 1;  // padding sorts last
-            }
-            __syncthreads();
-            bitonic_desc(buf, N);
-            if (threadIdx.x == 0) {
-                cnt = min(n, K);
-                if (n >= K) {
-                    have_thr = 1;
-                    thr = buf[K - 1];
-                }
-            }
-            __syncthreads();
-        }
+        // set the threshold as soon as K candidates exist, and compact when full
+        if ((!have_thr && cnt >= K) || cnt > kCap - kChunk) compact(false);
     }
-    // final compaction and output of the sorted top-K
-    {
-        const int n = cnt, N = next_pow2(max(n, 1));
-        for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
-            buf[i].key = 0;
-            buf[i].row = 0x7fffffff;
-            buf[i].pad = 1;
-        }
-        __syncthreads();
-        bitonic_desc(buf, N);
-        const int k = min(n, K);
-        Cand *out = lists + ((int64_t)j * nseg + seg) * (int64_t)p;
-        for (int i = threadIdx.x; i < k; i += blockDim.x) out[i] = buf[i];
-        if (threadIdx.x == 0) lens[j * nseg + seg] = k;
+    compact(true);
+    const int k = cnt < K ? cnt : K;
+    Cand *out = lists + ((int64_t)j * nseg + seg) * (int64_t)p;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        Cand c;
+        c.key = key[i];
+        c.row = row[i];
+        c.pad = 0;
+        out[i] = c;
     }
+    if (threadIdx.x == 0) lens[j * nseg + seg] = k;
     if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
 }
 
@@ -229,7 +232,7 @@ cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t
     int *lens = reinterpret_cast<int *>(lists + (size_t)p * nseg * p);
     if (m > 0) {
         const int64_t L = (m + nseg - 1) / nseg;
-        const size_t smem = sizeof(Cand) * kCap;
+        const size_t smem = (sizeof(unsigned long long) + sizeof(int)) * kCap;
         cudaError_t err =
             cudaFuncSetAttribute(k_relaxed_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;

@@ -10,79 +10,134 @@
 // eliminated in place, and written back in place (L21 in the first e columns,
 // the updated delayed columns after them).  Y = L21 D11 is also written to the
 // workspace when the Form step needs it.  Arithmetic is O(p^2) FP64 FMAs per row
-// and the GB300 FP64 pipe is the bound; L columns are broadcast from L1.
+// and the GB300 FP64 pipe is the bound: eight warps share each row tile (each
+// updates every eighth column) so that every FP64 pipe of the SM has work.
+#include <cuda_bf16.h>
+
 #include "ctp_internal.cuh"
 
 namespace ctp {
 
 namespace {
 
-constexpr int kRows = 32;     // rows per tile = threads per CTA (one row per thread)
-constexpr int kThreadsS = 32;
+constexpr int kRows = 32;   // rows per tile (one per lane)
+constexpr int kWarps = 8;   // warps per CTA: warp w updates the columns k = w (mod 8)
 
-__global__ void __launch_bounds__(kThreadsS)
+// Right-looking substitution over a tile of 32 rows: for each eliminated
+// position j, every warp reads y_j of its lane's row and updates its share of
+// the later columns; a CTA barrier separates consecutive pivots.  Eight warps
+// per CTA (and three CTAs per SM) keep all four FP64 pipes of an SM busy.
+__global__ void __launch_bounds__(kRows * kWarps)
     k_solve_fp64(double *__restrict__ A, int64_t n, int p, int64_t lda,
                  const int32_t *__restrict__ perm, const int32_t *__restrict__ piv,
                  const double *__restrict__ Dinv, const int32_t *__restrict__ nelim_p,
-                 double *__restrict__ W21, int64_t ldw) {
+                 double *__restrict__ W21, int64_t ldw, __nv_bfloat16 *__restrict__ Wb,
+                 __nv_bfloat16 *__restrict__ Lb, int Kp) {
     extern __shared__ __align__(16) double xs[];  // [p][kRows+1]
+    constexpr int LDX = kRows + 1;
     const int64_t m = n - p;
     const int64_t row0 = (int64_t)blockIdx.x * kRows;
-    if (row0 >= m) return;
-    const int r = threadIdx.x;
-    const int64_t row = row0 + r;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = row0 + lane;
     const bool valid = row < m;
     const int e = *nelim_p;
     double *A21 = A + p;
-    constexpr int LDX = kRows + 1;
 
-    // gather x = A21(rows, perm) (coalesced: consecutive threads, consecutive rows)
-    for (int k = 0; k < p; k++) {
+    // gather x = A21(rows, perm): each warp reads 32 consecutive rows of a column
+    for (int k = w; k < p; k += kWarps) {
         const int c = perm[k];
-        xs[k * LDX + r] = valid ? A21[(int64_t)c * lda + row] : 0.0;
+        xs[k * LDX + lane] = valid ? A21[(int64_t)c * lda + row] : 0.0;
     }
-    __syncwarp();
+    __syncthreads();
 
-    // forward substitution, right-looking over the eliminated positions
     for (int j = 0; j < e;) {
         const int kd = piv[j];
         if (kd == CTP_PIVKIND_2X2_FIRST) {
-            const double y0 = xs[j * LDX + r], y1 = xs[(j + 1) * LDX + r];
+            const double y0 = xs[j * LDX + lane], y1 = xs[(j + 1) * LDX + lane];
             const double *l0 = A + (int64_t)j * lda, *l1 = A + (int64_t)(j + 1) * lda;
-            for (int k = j + 2; k < p; k++) {
-                xs[k * LDX + r] -= y0 * __ldg(l0 + k) + y1 * __ldg(l1 + k);
-            }
+            for (int k = j + 2 + w; k < p; k += kWarps)
+                xs[k * LDX + lane] -= y0 * __ldg(l0 + k) + y1 * __ldg(l1 + k);
             j += 2;
         } else {
             if (kd == CTP_PIVKIND_1X1) {
-                const double y0 = xs[j * LDX + r];
+                const double y0 = xs[j * LDX + lane];
                 const double *l0 = A + (int64_t)j * lda;
-                for (int k = j + 1; k < p; k++) xs[k * LDX + r] -= y0 * __ldg(l0 + k);
+                for (int k = j + 1 + w; k < p; k += kWarps) xs[k * LDX + lane] -= y0 * __ldg(l0 + k);
             }
             j += 1;  // zero pivots have an all-zero L column
         }
+        __syncthreads();
     }
 
-    if (valid) {
-        // W21 = Y (= L21 D11) for the Form step
-        if (W21 != nullptr)
-            for (int j = 0; j < e; j++) W21[(int64_t)j * ldw + row] = xs[j * LDX + r];
-        // L21 = Y D11^{-1}
-        for (int j = 0; j < e;) {
-            const int kd = piv[j];
-            if (kd == CTP_PIVKIND_2X2_FIRST) {
-                const double y0 = xs[j * LDX + r], y1 = xs[(j + 1) * LDX + r];
-                const double i11 = Dinv[2 * j], i21 = Dinv[2 * j + 1], i22 = Dinv[2 * j + 2];
-                A21[(int64_t)j * lda + row] = y0 * i11 + y1 * i21;
-                A21[(int64_t)(j + 1) * lda + row] = y0 * i21 + y1 * i22;
-                j += 2;
-            } else {
-                A21[(int64_t)j * lda + row] =
-                    (kd == CTP_PIVKIND_1X1) ? xs[j * LDX + r] * Dinv[2 * j] : 0.0;
-                j += 1;
+    // BF16 copy of Y = W21 for the tensor-core Form: row-major, K contiguous,
+    // zero beyond e (a warp writes one row at a time: coalesced)
+    if (Wb != nullptr) {
+        for (int rr = w; rr < kRows; rr += kWarps) {
+            const int64_t rw = row0 + rr;
+            if (rw >= m) break;
+            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Wb + rw * Kp);
+            for (int k2 = lane; k2 < Kp / 2; k2 += 32) {
+                const int k = 2 * k2;
+                const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
+                const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
+                __nv_bfloat162 b;
+                b.x = __double2bfloat16(v0);
+                b.y = __double2bfloat16(v1);
+                dst[k2] = b;
             }
         }
-        for (int k = e; k < p; k++) A21[(int64_t)k * lda + row] = xs[k * LDX + r];
+    }
+    // W21 = Y (= L21 D11) for the FP64 Form step, L21 = Y D11^{-1}, delayed columns
+    constexpr int kPer = kMaxP / kWarps;
+    double lv[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        const int k = w + q * kWarps;
+        lv[q] = 0.0;
+        if (k >= p) continue;
+        const double y = xs[k * LDX + lane];
+        double out;
+        if (k >= e) {
+            out = y;
+        } else {
+            if (W21 != nullptr && valid) W21[(int64_t)k * ldw + row] = y;
+            const int kd = piv[k];
+            if (kd == CTP_PIVKIND_1X1) {
+                out = y * Dinv[2 * k];
+            } else if (kd == CTP_PIVKIND_2X2_FIRST) {
+                out = y * Dinv[2 * k] + xs[(k + 1) * LDX + lane] * Dinv[2 * k + 1];
+            } else if (kd == CTP_PIVKIND_2X2_SECOND) {
+                out = xs[(k - 1) * LDX + lane] * Dinv[2 * (k - 1) + 1] + y * Dinv[2 * k];
+            } else {
+                out = 0.0;
+            }
+        }
+        lv[q] = out;
+        if (valid) A21[(int64_t)k * lda + row] = out;
+    }
+    // BF16 copy of L21 for the tensor-core Form
+    if (Lb != nullptr) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const int k = w + q * kWarps;
+            if (k < e) xs[k * LDX + lane] = lv[q];
+        }
+        __syncthreads();
+        for (int rr = w; rr < kRows; rr += kWarps) {
+            const int64_t rw = row0 + rr;
+            if (rw >= m) break;
+            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Lb + rw * Kp);
+            for (int k2 = lane; k2 < Kp / 2; k2 += 32) {
+                const int k = 2 * k2;
+                const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
+                const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
+                __nv_bfloat162 b;
+                b.x = __double2bfloat16(v0);
+                b.y = __double2bfloat16(v1);
+                dst[k2] = b;
+            }
+        }
     }
 }
 
@@ -90,7 +145,8 @@ __global__ void __launch_bounds__(kThreadsS)
 
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,
-                              double *W21, int64_t ldw, cudaStream_t st) {
+                              double *W21, int64_t ldw, void *Wb, void *Lb, int Kp,
+                              cudaStream_t st) {
     const int64_t m = n - p;
     if (m <= 0) return cudaSuccess;
     size_t smem = sizeof(double) * (size_t)p * (kRows + 1);
@@ -98,8 +154,8 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
         cudaFuncSetAttribute(k_solve_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int64_t grid = (m + kRows - 1) / kRows;
-    k_solve_fp64<<<(unsigned)grid, kThreadsS, smem, st>>>(A, n, p, lda, perm, piv, Dinv, nelim,
-                                                          W21, ldw);
+    k_solve_fp64<<<(unsigned)grid, kRows * kWarps, smem, st>>>(
+        A, n, p, lda, perm, piv, Dinv, nelim, W21, ldw, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb, Kp);
     return cudaGetLastError();
 }
 

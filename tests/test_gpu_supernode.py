@@ -269,3 +269,67 @@ def test_nonfinite_input_flagged(ctx):
     got = run_gpu(ctx, A, 12, "strict")
     from paper_1305_2353_gb300 import ctp
     assert got["info"] == ctp.CTP_ENONFINITE
+
+
+# --------------------------------------------------------------------------- tensor-core Form
+
+def _bf16_bound(Wd, L21):
+    """|W||L|^T: the scale of the rounding error of a BF16-operand, FP32-accumulate
+    product (each operand is rounded once, relative error 2^-9 each)."""
+    return np.abs(Wd) @ np.abs(L21).T
+
+
+@pytest.mark.parametrize("pivot", ["strict", "relaxed"])
+@pytest.mark.parametrize("n,p", [(600, 40), (2000, 64), (1500, 130), (3000, 256), (700, 200)])
+def test_form_tensor_cores_bf16(ctx, pivot, n, p):
+    """S from the tcgen05 kernel (BF16 operands, FP32 accumulation) against the
+    oracle's FP64 S: |dS| <= 2^-7 |W21||L21|^T elementwise (lower triangle)."""
+    from paper_1305_2353_gb300 import ctp
+    A = _tough(n, p, 5)
+    ref = O.factor(A, p, pivot)
+    opt = ctp.options(pivot=pivot, prec="bf16", smode="fp32")
+    sn = ctp.Supernode(ctx, A, p, opt)
+    sn.run()
+    torch.cuda.synchronize()
+    got = sn.result()
+    assert got["info"] == 0
+    e = ref["nelim"]
+    assert got["nelim"] == e
+    L21 = ref["A"][p:, :e]
+    _, Dm, _ = O.unpack(ref, p)
+    Wd = L21 @ Dm
+    S = O.form(L21, ref["piv"][:e], ref["D"])
+    lo = np.tril(np.ones_like(S, dtype=bool))
+    bound = _bf16_bound(Wd, L21)
+    err = np.abs(got["S"] - S)
+    assert np.all(err[lo] <= 2.0 ** -7 * bound[lo] + 1e-30)
+    assert np.all(np.triu(got["S"], 1) == 0)
+
+
+def test_form_tensor_cores_large(ctx):
+    """n = 20000, p = 256, relaxed (e = 256): 610 tiles per row band region, sampled
+    entries of S against the oracle, including the diagonal and the last rows."""
+    from paper_1305_2353_gb300 import ctp
+    n, p = 20000, 256
+    A = inputs.single_large(2, n=n, p=p)
+    ref = O.factor(A, p, "relaxed")
+    opt = ctp.options(pivot="relaxed", prec="bf16", smode="fp32")
+    sn = ctp.Supernode(ctx, A, p, opt)
+    sn.run()
+    torch.cuda.synchronize()
+    assert ctx.read_info(sn.ws) == 0
+    m, e = n - p, ref["nelim"]
+    rng = np.random.default_rng(0)
+    ii = rng.integers(0, m, 6000)
+    jj = rng.integers(0, m, 6000)
+    ii, jj = np.maximum(ii, jj), np.minimum(ii, jj)
+    ii = np.r_[ii, np.arange(m - 300, m), np.arange(0, m, 997)]
+    jj = np.r_[jj, np.arange(m - 300, m), np.arange(0, m, 997)]
+    L21 = ref["A"][p:, :e]
+    want = O.form_entries(L21, ref["piv"][:e], ref["D"], ii, jj)
+    Sg = sn.S  # (m, m) tensor holding S column-major: element (i, j) at [j, i]
+    got = Sg[torch.as_tensor(jj, device="cuda"), torch.as_tensor(ii, device="cuda")].cpu().numpy()
+    _, Dm, _ = O.unpack(ref, p)
+    Wd = L21 @ Dm
+    bound = np.einsum("tk,tk->t", np.abs(Wd[ii]), np.abs(L21[jj]))
+    assert np.all(np.abs(got - want) <= 2.0 ** -7 * bound)
