@@ -6,9 +6,13 @@ delayed-column update, and Form of the Schur complement S.
 
 Default workload: a single supernode shaped like the paper's large random
 examples (Section 7.1): n = 200000, p = 256, A11 symmetric and A21 with entries
-uniform in [-1, 1], u = 0.01, strict compressed pivoting, FP64 arithmetic, S
-stored as FP32 (lower triangle).  Every timed step factors its own fresh copy
-of the input (409 MB each, larger than L2), so no L2 flush is needed.
+uniform in [-1, 1], u = 0.01, relaxed compressed pivoting (on this input every
+pivot is accepted, as with threshold partial pivoting; strict compressed
+pivoting accepts 12 of 256), FP64 arithmetic throughout, S stored in FP64
+(lower-packed, 160 GB).  Every timed step factors its own fresh copy of the
+input (409 MB each, larger than L2), so no L2 flush is needed.  The line also
+carries a "mixed" measurement of the same workload with the Form on the
+tensor cores (BF16 operands, FP32 accumulation, S in FP32).
 
 Metric: GFLOP/s of the supernode factorization under the flop model
   factor+solve = sum_{k=1..e} [(n-k) + 2((n-p)(p-k) + (p-k)(p-k+1)/2)]
@@ -58,11 +62,16 @@ def parse_args():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=200000)
     ap.add_argument("--p", type=int, default=256)
-    ap.add_argument("--pivot", default="strict", choices=["strict", "relaxed", "restricted"])
-    ap.add_argument("--smode", default="fp32", choices=["none", "fp32", "fp64"])
+    ap.add_argument("--pivot", default="relaxed", choices=["strict", "relaxed", "restricted"])
+    ap.add_argument("--smode", default="fp64_packed",
+                    choices=["none", "fp32", "fp64", "fp32_packed", "fp64_packed"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16"],
+                    help="Form arithmetic: FP64, or BF16 tensor cores with FP32 accumulation")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the extra measurement with the Form on the tensor cores")
     return ap.parse_args()
 
 
@@ -204,11 +213,26 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
         work = 8.0 * m * p
         bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
         achieved = work / t / 1e9
+    elif name == "form_tc_bf16":
+        # S written as FP32 (lower triangle) dominates the bytes: 128 flop/byte at
+        # e = 256, below the BF16 ridge, so the HBM roofline bounds this kernel
+        _, form = flops_model(n, p, e)
+        work = 4.0 * m * (m + 1) / 2 + 2 * 2.0 * m * ((p + 63) // 64 * 64)
+        bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
+        achieved = work / t / 1e9
+        tensor = form / t / 1e12
+        out = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+               "frac": achieved / peak, "traffic": None, "peak_source": src,
+               "work_per_launch": work, "launch_ms": ms / launches,
+               "tensor_tflops": tensor,
+               "tensor_frac_of_bf16_sustained": tensor / peaks.get("bf16_tflops_sustained", 1715.6)}
+        return out
     elif name in ("form_fp64", "solve_fp64"):
         fs, form = flops_model(n, p, e)
         work = form if name == "form_fp64" else fs
-        bound, unit, peak = "alu", "TFLOP/s", peaks["fp64_tflops"]
-        src = "cuBLAS DGEMM measured in this run (no FP64 entry in MEASURED_PEAKS.json)"
+        bound, unit, peak = "alu", "TFLOP/s", 1.25
+        src = ("nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table; no FP64 entry in "
+               "MEASURED_PEAKS.json); cuBLAS DGEMM 4096^3 in this run: %.3f" % peaks["fp64_tflops"])
         achieved = work / t / 1e12
     else:
         return None
@@ -222,6 +246,110 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic, "peak_source": src,
             "work_per_launch": work, "launch_ms": ms / launches}
+
+
+def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, world, dist):
+    """Time `steps` factorizations (after `warmup`), each on a fresh input copy.
+    Returns a dict of the measured quantities."""
+    import torch
+    from paper_1305_2353_gb300 import ctp
+    n, p = a.n, a.p
+    m = n - p
+    opt = ctp.options(pivot=a.pivot, smode=smode, prec=prec)
+    A0 = ctp.colmajor(A_host, dev)
+    bufs = [A0.clone() for _ in range(warmup + steps)]
+    perm = torch.empty(p, dtype=torch.int32, device=dev)
+    piv = torch.empty(p, dtype=torch.int32, device=dev)
+    D = torch.empty(2 * p, dtype=torch.float64, device=dev)
+    nelim = torch.empty(1, dtype=torch.int32, device=dev)
+    S = None
+    if smode != "none":
+        dt = torch.float64 if smode.startswith("fp64") else torch.float32
+        S = (torch.empty(m * (m + 1) // 2, dtype=dt, device=dev) if smode.endswith("packed")
+             else torch.empty((m, m), dtype=dt, device=dev))
+    ws = ctx.workspace(n, p, opt)
+    stream = torch.cuda.current_stream()
+
+    def step(buf):
+        ctx.factor_supernode(buf, n, p, n, opt, perm, piv, D, nelim, S, max(m, 1), ws, stream)
+
+    for i in range(warmup):
+        step(bufs[i])
+    torch.cuda.synchronize()
+    info = ctx.read_info(ws)
+    if info != 0:
+        raise RuntimeError(f"device info {info}")
+    e = int(nelim.cpu()[0])
+
+    clocks = ClockSampler(int(dev.split(":")[1]))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ctx.profile_begin()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        step(bufs[warmup + i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    kern = ctx.profile_end()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt[0])
+    fs, form = flops_model(n, p, e)
+    flops_step = fs + (form if smode != "none" else 0)
+    value = world * flops_step * steps / (ms / 1e3) / 1e9
+    del bufs
+
+    # e2e through the public API with host buffers: H2D of the supernode from
+    # pinned memory, the factorization, D2H of the factor and the pivots
+    e2e = None
+    if e2e_steps > 0:
+        hA = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()
+        hOut = torch.empty_like(hA).pin_memory()
+        hp = torch.empty(p, dtype=torch.int32).pin_memory()
+        hv = torch.empty(p, dtype=torch.int32).pin_memory()
+        hD = torch.empty(2 * p, dtype=torch.float64).pin_memory()
+        hn = torch.empty(1, dtype=torch.int32).pin_memory()
+        dA = torch.empty_like(A0)
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            step(dA)
+            hOut.copy_(dA, non_blocking=True)
+            hp.copy_(perm, non_blocking=True)
+            hv.copy_(piv, non_blocking=True)
+            hD.copy_(D, non_blocking=True)
+            hn.copy_(nelim, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        s0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - s0
+        if dist:
+            tt = torch.tensor([te], dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt[0])
+        e2e = {"value": world * flops_step * e2e_steps / te / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": hA.numel() * 8,
+               "d2h_bytes_per_step": hOut.numel() * 8 + hp.numel() * 4 + hv.numel() * 4 +
+               hD.numel() * 8 + 4}
+    del S, A0, ws
+    torch.cuda.empty_cache()
+    top = max(kern.items(), key=lambda kv: kv[1][1])
+    roof = kernel_roofline(top[0], top[1][0], top[1][1], a, e, peaks)
+    return dict(value=value, ms=ms, e=e, fs=fs, form=form, flops_step=flops_step, kern=kern,
+                clocks=clk, e2e=e2e, roofline=roof, launches=sum(v[0] for v in kern.values()))
 
 
 def run_native(a):
@@ -240,107 +368,20 @@ def run_native(a):
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {"hbm_gbs": 6800.0}
     peaks = dict(peaks)
     peaks["fp64_tflops"] = fp64_peak_tflops(torch, dev)
-
     ctx = ctp.Context(local)
-    n, p = a.n, a.p
-    m = n - p
-    A_host = inputs.single_large(a.seed, n=n, p=p)
-    opt = ctp.options(pivot=a.pivot, smode=a.smode)
-    nbuf = a.warmup + a.steps
-    A0 = ctp.colmajor(A_host, dev)
-    bufs = [A0.clone() for _ in range(nbuf)]
-    perm = torch.empty(p, dtype=torch.int32, device=dev)
-    piv = torch.empty(p, dtype=torch.int32, device=dev)
-    D = torch.empty(2 * p, dtype=torch.float64, device=dev)
-    nelim = torch.empty(1, dtype=torch.int32, device=dev)
-    S = None
-    if a.smode != "none":
-        S = torch.empty((m, m), dtype=torch.float32 if a.smode == "fp32" else torch.float64,
-                        device=dev)
-    ws = ctx.workspace(n, p, opt)
-    stream = torch.cuda.current_stream()
+    A_host = inputs.single_large(a.seed, n=a.n, p=a.p)
 
-    def step(buf):
-        ctx.factor_supernode(buf, n, p, n, opt, perm, piv, D, nelim, S, max(m, 1), ws, stream)
-
-    for i in range(a.warmup):
-        step(bufs[i])
-    torch.cuda.synchronize()
-    if ctx.read_info(ws) != 0:
-        raise RuntimeError(f"device info {ctx.read_info(ws)}")
-    e = int(nelim.cpu()[0])
-
-    clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    ctx.profile_begin()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for i in range(a.steps):
-        step(bufs[a.warmup + i])
-    t1.record(stream)
-    torch.cuda.synchronize()
-    kern = ctx.profile_end()
-    clk = clocks.stop()
-    if dist:
-        dist.barrier()
-    ms = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt[0])
-    fs, form = flops_model(n, p, e)
-    flops_step = fs + (form if a.smode != "none" else 0)
-    value = world * flops_step * a.steps / (ms / 1e3) / 1e9
-    del bufs
-
-    # e2e through the public API with host buffers: H2D of the supernode from
-    # pinned memory, the factorization, D2H of the factor and the pivots
-    e2e = None
-    if not a.no_e2e:
-        hA = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()
-        hOut = torch.empty_like(hA).pin_memory()
-        hp = torch.empty(p, dtype=torch.int32).pin_memory()
-        hv = torch.empty(p, dtype=torch.int32).pin_memory()
-        hD = torch.empty(2 * p, dtype=torch.float64).pin_memory()
-        hn = torch.empty(1, dtype=torch.int32).pin_memory()
-        dA = torch.empty_like(A0)
-
-        def e2e_step():
-            dA.copy_(hA, non_blocking=True)
-            step(dA)
-            hOut.copy_(dA, non_blocking=True)
-            hp.copy_(perm, non_blocking=True)
-            hv.copy_(piv, non_blocking=True)
-            hD.copy_(D, non_blocking=True)
-            hn.copy_(nelim, non_blocking=True)
-
-        for _ in range(max(1, a.warmup - 1)):
-            e2e_step()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        s0 = time.perf_counter()
-        for _ in range(a.steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        te = time.perf_counter() - s0
-        if dist:
-            tt = torch.tensor([te], dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt[0])
-        e2e = {"value": world * flops_step * a.steps / te / 1e9, "unit": "GFLOP/s",
-               "h2d_bytes_per_step": hA.numel() * 8,
-               "d2h_bytes_per_step": hOut.numel() * 8 + hp.numel() * 4 + hv.numel() * 4 +
-               hD.numel() * 8 + 4}
-
-    # dominant kernel
-    top = max(kern.items(), key=lambda kv: kv[1][1])
-    roof = kernel_roofline(top[0], top[1][0], top[1][1], a, e, peaks)
-    launches = sum(v[0] for v in kern.values())
+    main = measure(a, ctx, dev, A_host, a.prec, a.smode, a.steps, a.warmup,
+                   0 if a.no_e2e else a.steps, peaks, world, dist)
+    mixed = None
+    if not a.no_mixed and a.prec == "fp64":
+        mx = measure(a, ctx, dev, A_host, "bf16", "fp32_packed", max(a.steps, 5), max(a.warmup, 3),
+                     0 if a.no_e2e else max(a.steps, 5), peaks, world, dist)
+        mixed = {"value": mx["value"], "unit": "GFLOP/s", "ms_per_step": mx["ms"] / max(a.steps, 5),
+                 "prec": "Form on tensor cores: bf16 x bf16 -> f32, S fp32 packed; the rest f64",
+                 "roofline": mx["roofline"], "e2e": mx["e2e"], "gpu_launches": mx["launches"],
+                 "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in mx["kern"].items()},
+                 "clocks": mx["clocks"]}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -348,24 +389,28 @@ def run_native(a):
         cpu = {"value": fl / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": desc}
     if rank == 0:
+        e = main["e"]
         line = {
-            "metric": "Supernode LDL^T GFLOP/s", "value": value, "unit": "GFLOP/s",
-            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "metric": "Supernode LDL^T GFLOP/s", "value": main["value"], "unit": "GFLOP/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": main["ms"] / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if a.prec == "fp64" else "f64 (Form: bf16 x bf16 -> f32)",
             "data": "synthetic",
-            "config": {"workload": workload_name(a), "n": n, "p": p, "u": 0.01,
-                       "pivot": a.pivot, "prec": "fp64", "S": a.smode, "nelim": e,
-                       "flops_per_step": flops_step, "factor_solve_flops": fs,
-                       "form_flops": form if a.smode != "none" else 0,
+            "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "u": 0.01,
+                       "pivot": a.pivot, "prec": a.prec, "S": a.smode, "nelim": e,
+                       "flops_per_step": main["flops_step"], "factor_solve_flops": main["fs"],
+                       "form_flops": main["form"] if a.smode != "none" else 0,
                        "l2": "inputs larger than L2: a distinct 409 MB input copy per step",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof,
+            "roofline": main["roofline"],
             "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()},
-            "clocks": clk,
+            "e2e": main["e2e"],
+            "gpu_launches": main["launches"],
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in main["kern"].items()},
+            "clocks": main["clocks"],
             "fp64_dgemm_tflops": peaks["fp64_tflops"],
+            "mixed": mixed,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -61,14 +61,24 @@ typedef enum {
 typedef enum {
     CTP_FP64 = 0,  /* FP64 throughout */
     CTP_BF16 = 1   /* Form on the tensor cores: BF16 operands, FP32 accumulation and
-                      FP32 S (requires smode = CTP_S_FP32) */
+                      FP32 S (requires smode CTP_S_FP32 or CTP_S_FP32_PACKED) */
 } ctp_prec;
 
-/* Storage of the Schur complement S (lower triangle of an m x m column-major
- * matrix, leading dimension lds >= m; the strict upper triangle is not written). */
-typedef enum { CTP_S_NONE = 0, CTP_S_FP64 = 1, CTP_S_FP32 = 2 } ctp_smode;
+/* Storage of the Schur complement S (its lower triangle only):
+ *  CTP_S_FP64 / CTP_S_FP32: m x m column-major, leading dimension lds >= m; the
+ *    strict upper triangle is not written;
+ *  CTP_S_FP64_PACKED / CTP_S_FP32_PACKED: lower-packed by columns (LAPACK 'L'
+ *    packed): S(i,j), i >= j, at index j*m - j*(j-1)/2 + (i-j); m*(m+1)/2
+ *    entries; lds is ignored. */
+typedef enum {
+    CTP_S_NONE = 0,
+    CTP_S_FP64 = 1,
+    CTP_S_FP32 = 2,
+    CTP_S_FP64_PACKED = 3,
+    CTP_S_FP32_PACKED = 4
+} ctp_smode;
 
-/* Per-position pivot kinds written to piv[]. */
+/* Per-position pivot kinds written to piv[] (CTP_S_* above). */
 #define CTP_PIVKIND_1X1 1
 #define CTP_PIVKIND_2X2_FIRST 2
 #define CTP_PIVKIND_2X2_SECOND 0
@@ -140,8 +150,8 @@ ctp_status ctp_compress_relaxed(ctp_ctx *ctx, int64_t m, int32_t p, const double
  *      D[2p] (double): D[2k] = D(k,k); D[2k+1] = D(k+1,k) for the first column
  *        of a 2x2 block, else 0.  Zero pivots have D = 0 and an all-zero L column.
  *      nelim[1] (int32): e.
- *      S (m x m, lds), written iff opt->smode != CTP_S_NONE: lower triangle of
- *        L21 D11 L21^T in FP64 or FP32.
+ *      S, written iff opt->smode != CTP_S_NONE: lower triangle of L21 D11 L21^T
+ *        in FP64 or FP32, full (lds) or packed storage (see ctp_smode).
  * All of perm, piv, D, nelim, S are device pointers.  Nothing is synchronised:
  * e is only known on the device, and the Solve and Form kernels read it there. */
 ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, int64_t lda,

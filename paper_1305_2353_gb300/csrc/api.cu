@@ -107,7 +107,7 @@ static ctp_status check_opts(const ctp_options *opt) {
     if (!(opt->small >= 0.0)) return CTP_EINVAL;
     if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
     if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16) return CTP_EINVAL;
-    if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP32) return CTP_EINVAL;
+    if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP32_PACKED) return CTP_EINVAL;
     return CTP_OK;
 }
 
@@ -172,11 +172,14 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     ctp_status s = check_opts(opt);
     if (s != CTP_OK) return s;
     const int64_t m = n - p;
-    if (opt->smode != CTP_S_NONE && (S == nullptr || lds < (m > 0 ? m : 1))) return CTP_EINVAL;
+    const bool packed = opt->smode == CTP_S_FP64_PACKED || opt->smode == CTP_S_FP32_PACKED;
+    if (opt->smode != CTP_S_NONE && (S == nullptr || (!packed && lds < (m > 0 ? m : 1))))
+        return CTP_EINVAL;
     if (p > kMaxP) return CTP_EUNSUPPORTED;
     if (opt->pivot == CTP_PIV_TPP) return CTP_EUNSUPPORTED;
     const bool tc = opt->prec == CTP_BF16 && opt->smode != CTP_S_NONE;
-    if (tc && opt->smode != CTP_S_FP32) return CTP_EUNSUPPORTED;  // the tensor-core Form writes FP32
+    if (tc && opt->smode != CTP_S_FP32 && opt->smode != CTP_S_FP32_PACKED)
+        return CTP_EUNSUPPORTED;  // the tensor-core Form writes FP32
     WsLayout L = ws_layout(n, p, opt, ctx->num_sms);
     if (ws_bytes < L.total) return CTP_ENOMEM;
 
@@ -233,7 +236,8 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     if (opt->smode != CTP_S_NONE && m > 0) {
         if (tc)
             CTP_CUDA(timed(ctx, K_FORM_TC, st, [&] {
-                return launch_form_tc(Wb, Lbf, m, Kp, nelim, (float *)S, lds, info, ctx->num_sms, st);
+                return launch_form_tc(Wb, Lbf, m, Kp, nelim, (float *)S, lds, packed ? 1 : 0, info,
+                                      ctx->num_sms, st);
             }));
         else
             CTP_CUDA(timed(ctx, K_FORM, st, [&] {

@@ -65,7 +65,8 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
 // K-padding of the BF16 operand copies used by the tensor-core Form.
 int form_tc_kpad(int p);
 cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
-                           float *S, int64_t lds, int32_t *info, int num_sms, cudaStream_t st);
+                           float *S, int64_t lds, int packed, int32_t *info, int num_sms,
+                           cudaStream_t st);
 
 cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
                              int64_t m, const int32_t *nelim, void *S, int64_t lds, int smode,

@@ -5,8 +5,8 @@
 // tiles on or below the diagonal (a triangular tile index), stages 64 x 16
 // slabs of W21 and L21 in shared memory, and gives each of 256 threads a 4 x 4
 // block of S.  The inner dimension e is read from device memory (it is only
-// known after pivoting).  S is written as FP64 or FP32; strictly upper entries
-// of diagonal tiles are not written.
+// known after pivoting).  S is written as FP64 or FP32, full column-major or
+// lower-packed by columns; strictly upper entries are never written.
 #include "ctp_internal.cuh"
 
 namespace ctp {
@@ -15,7 +15,7 @@ namespace {
 
 constexpr int kTile = 64, kK = 16, kTh = 256;
 
-template <typename OutT>
+template <typename OutT, bool kPacked>
 __global__ void __launch_bounds__(kTh)
     k_form_fp64(const double *__restrict__ L21, int64_t ldl, const double *__restrict__ W21,
                 int64_t ldw, int64_t m, const int32_t *__restrict__ nelim_p, OutT *__restrict__ S,
@@ -61,7 +61,10 @@ __global__ void __launch_bounds__(kTh)
 #pragma unroll
         for (int s = 0; s < 4; s++) {
             const int64_t gi = i0 + ty + 16 * q, gj = j0 + tx + 16 * s;
-            if (gi < m && gj < m && gi >= gj) S[gj * lds + gi] = (OutT)acc[q][s];
+            if (gi < m && gj < m && gi >= gj) {
+                const int64_t idx = kPacked ? gj * m - gj * (gj - 1) / 2 + (gi - gj) : gj * lds + gi;
+                S[idx] = (OutT)acc[q][s];
+            }
         }
 }
 
@@ -75,11 +78,17 @@ cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, 
     const int64_t ntiles = nt * (nt + 1) / 2;
     if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (smode == CTP_S_FP64)
-        k_form_fp64<double><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
-                                                              (double *)S, lds);
+        k_form_fp64<double, false><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
+                                                                     (double *)S, lds);
+    else if (smode == CTP_S_FP32)
+        k_form_fp64<float, false><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
+                                                                    (float *)S, lds);
+    else if (smode == CTP_S_FP64_PACKED)
+        k_form_fp64<double, true><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
+                                                                    (double *)S, lds);
     else
-        k_form_fp64<float><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
-                                                             (float *)S, lds);
+        k_form_fp64<float, true><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
+                                                                   (float *)S, lds);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // form_tc.cu -- K6 (tensor cores): the Form task S = L21 D11 L21^T = W21 L21^T
 // (Section 1 task list), lower triangle, with BF16 operands and FP32
-// accumulation on the 5th-generation tensor cores (tcgen05), S stored as FP32.
+// accumulation on the 5th-generation tensor cores (tcgen05), S stored as FP32
+// (full column-major or lower-packed by columns).
 //
 // Layout: W21 and L21 are BF16 copies written by the Solve kernel, row-major
 // m x Kp (K = pivot position contiguous, Kp = p rounded up to 64, zero beyond
@@ -161,7 +162,7 @@ __device__ __forceinline__ void decode_tile(int64_t t, int nM, int &ti, int &tj)
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_form_tc(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapL,
               int64_t m, const int32_t *__restrict__ nelim_p, float *__restrict__ S, int64_t lds,
-              int32_t *__restrict__ info) {
+              int packed, int32_t *__restrict__ info) {
     extern __shared__ unsigned char smraw[];
     __shared__ Bars bars;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -296,7 +297,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
                     for (int x = 0; x < 32; x++) {
                         const int64_t j = j0 + x;
-                        if (j <= i && j < m) S[j * lds + i] = (KB > 0) ? __uint_as_float(r[x]) : 0.0f;
+                        if (j <= i && j < m) {
+                            const int64_t idx = packed ? j * m - j * (j - 1) / 2 + (i - j) : j * lds + i;
+                            S[idx] = (KB > 0) ? __uint_as_float(r[x]) : 0.0f;
+                        }
                     }
                 }
             }
@@ -349,7 +353,8 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_
 int form_tc_kpad(int p) { return (p + kBK - 1) / kBK * kBK; }
 
 cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
-                           float *S, int64_t lds, int32_t *info, int num_sms, cudaStream_t st) {
+                           float *S, int64_t lds, int packed, int32_t *info, int num_sms,
+                           cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     if ((((uintptr_t)Wb) | ((uintptr_t)Lb)) & 15) return cudaErrorMisalignedAddress;
     CUtensorMap mW, mL;
@@ -360,7 +365,7 @@ cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, co
     const int nM = (int)((m + kBM - 1) / kBM);
     const int64_t ntiles = tiles_before(nM);
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-    k_form_tc<<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, info);
+    k_form_tc<<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, packed, info);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ STATUS = {0: "CTP_OK", 1: "CTP_EINVAL", 2: "CTP_ENOMEM", 3: "CTP_ECUDA", 4: "CTP
           5: "CTP_ETIMEOUT", 6: "CTP_ECAPACITY", 7: "CTP_EUNSUPPORTED"}
 PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3}
 PREC = {"fp64": 0, "bf16": 1}
-SMODE = {"none": 0, "fp64": 1, "fp32": 2}
+SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
 
 EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_compress_strict",
@@ -194,6 +194,16 @@ def to_numpy(t) -> np.ndarray:
     return t.detach().cpu().numpy().T.copy()
 
 
+def unpack_lower(packed: np.ndarray, m: int) -> np.ndarray:
+    """Lower-packed-by-columns vector -> m x m matrix (upper triangle zero)."""
+    S = np.zeros((m, m), dtype=packed.dtype)
+    off = 0
+    for j in range(m):
+        S[j:, j] = packed[off:off + m - j]
+        off += m - j
+    return S
+
+
 class Supernode:
     """Device buffers for one factorization of an n x p supernode."""
 
@@ -210,8 +220,11 @@ class Supernode:
         m = self.n - p
         self.S = None
         if opt.smode != 0:
-            dt = torch.float64 if opt.smode == 1 else torch.float32
-            self.S = torch.zeros((m, m), dtype=dt, device=dev)  # column-major m x m
+            dt = torch.float64 if opt.smode in (1, 3) else torch.float32
+            if opt.smode in (3, 4):
+                self.S = torch.zeros(max(m * (m + 1) // 2, 1), dtype=dt, device=dev)  # packed
+            else:
+                self.S = torch.zeros((m, m), dtype=dt, device=dev)  # column-major m x m
         self.opt = opt
         self.ws = ctx.workspace(self.n, p, opt)
 
@@ -224,6 +237,9 @@ class Supernode:
         out = dict(A=to_numpy(self.A), perm=self.perm.cpu().numpy(), piv=self.piv.cpu().numpy(),
                    D=self.D.cpu().numpy(), nelim=int(self.nelim.cpu()[0]))
         if self.S is not None:
-            out["S"] = to_numpy(self.S)
+            if self.opt.smode in (3, 4):
+                out["S"] = unpack_lower(self.S.cpu().numpy(), self.n - self.p)
+            else:
+                out["S"] = to_numpy(self.S)
         out["info"] = self.ctx.read_info(self.ws)
         return out

@@ -172,7 +172,8 @@ def test_single_small_workload(ctx):
         compare(ref, got, 64, A)
 
 
-@pytest.mark.parametrize("smode,rtol", [("fp64", 1e-11), ("fp32", 2e-6)])
+@pytest.mark.parametrize("smode,rtol", [("fp64", 1e-11), ("fp32", 2e-6), ("fp64_packed", 1e-11),
+                                        ("fp32_packed", 2e-6)])
 @pytest.mark.parametrize("n,p", [(600, 40), (2000, 64), (1500, 130)])
 def test_form_matches_oracle(ctx, smode, rtol, n, p):
     A = _tough(n, p, 3)
@@ -279,15 +280,16 @@ def _bf16_bound(Wd, L21):
     return np.abs(Wd) @ np.abs(L21).T
 
 
-@pytest.mark.parametrize("pivot", ["strict", "relaxed"])
+@pytest.mark.parametrize("pivot,smode", [("strict", "fp32"), ("relaxed", "fp32"),
+                                         ("relaxed", "fp32_packed")])
 @pytest.mark.parametrize("n,p", [(600, 40), (2000, 64), (1500, 130), (3000, 256), (700, 200)])
-def test_form_tensor_cores_bf16(ctx, pivot, n, p):
+def test_form_tensor_cores_bf16(ctx, pivot, smode, n, p):
     """S from the tcgen05 kernel (BF16 operands, FP32 accumulation) against the
     oracle's FP64 S: |dS| <= 2^-7 |W21||L21|^T elementwise (lower triangle)."""
     from paper_1305_2353_gb300 import ctp
     A = _tough(n, p, 5)
     ref = O.factor(A, p, pivot)
-    opt = ctp.options(pivot=pivot, prec="bf16", smode="fp32")
+    opt = ctp.options(pivot=pivot, prec="bf16", smode=smode)
     sn = ctp.Supernode(ctx, A, p, opt)
     sn.run()
     torch.cuda.synchronize()
