@@ -120,6 +120,25 @@ ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double 
                                double *C, int32_t *J, void *workspace, size_t ws_bytes,
                                void *stream);
 
+/* Strict compression that allocates nothing (the paper has no counterpart:
+ * this is a service of the library, not a step of the method).  For callers
+ * that cannot allocate device memory at the call site -- e.g. a plugin inside
+ * an application that owns every device allocation through its own pool, or a
+ * latency-critical path that must not pay for cudaMalloc -- the kernel's
+ * scratch (an info word and the p x p keys of C, 512 KiB at the largest p) is a
+ * fixed array inside this library that every GPU holds from the moment the
+ * library is loaded on it until the process exits.  Same inputs and outputs as
+ * ctp_compress_strict, on the CURRENT device, with no context and no
+ * workspace.  p above ctp_max_p() returns CTP_ECAPACITY.  The first call on a
+ * device looks up the array's device address (a one-time set-up; make that
+ * first call before any stream capture).  All calls share the one array and
+ * every call clears it first: calls that overlap on the GPU (two streams, or
+ * two threads) race and must be serialised by the caller.  If info_host is not
+ * NULL the call synchronises `stream` and stores the device info word there
+ * (CTP_OK or CTP_ENONFINITE). */
+ctp_status ctp_compress_strict_noalloc(int64_t m, int32_t p, const double *A21, int64_t lda,
+                                       double *C, int32_t *J, int32_t *info_host, void *stream);
+
 /* Relaxed compression of A21 (Section 4.2): for j = 1..p in turn, the A21 row
  * holding the largest |a21(i,j)| among rows not chosen yet (lowest row on ties)
  * becomes row j of C, with its signs.  A21: m x p device matrix (lda >= m).

@@ -204,3 +204,77 @@ cudaError_t launch_keys_to_rowmajor(const unsigned long long *Ckeys, double *C, 
 }
 
 }  // namespace ctp
+
+// ---------------------------------------------------------------------------
+// Strict compression without any device allocation.
+//
+// Some host programs cannot allocate device memory at the point where they
+// need the compression: a plugin inside an application that owns every device
+// allocation through its own pool, or a caller on a latency-critical path that
+// must not pay for cudaMalloc and its implicit synchronisation.  For them the
+// scratch of the kernel (the info word and the p x p integer keys of C) lives
+// in one file-scope device array, sized for the largest supported p, that every
+// GPU holds from the moment this library is loaded on it until the process
+// exits.  Host code must not use the array's name as a device address (it is a
+// host-side stand-in); the device address is looked up once per device.
+
+#include <mutex>
+
+namespace {
+
+constexpr int kNoAllocMaxP = ctp::kMaxP;
+constexpr size_t kNoAllocBytes = 256 + sizeof(unsigned long long) * (size_t)kNoAllocMaxP * kNoAllocMaxP;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on the
+// first call for that device).  Returns nullptr if the lookup fails.
+void *noalloc_scratch_current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        g_noalloc_addr[dev] = ptr;
+    }
+    return g_noalloc_addr[dev];
+}
+
+}  // namespace
+
+extern "C" ctp_status ctp_compress_strict_noalloc(int64_t m, int32_t p, const double *A21, int64_t lda,
+                                                  double *C, int32_t *J, int32_t *info_host,
+                                                  void *stream) {
+    if (A21 == nullptr || C == nullptr) return CTP_EINVAL;
+    if (m < 0 || p < 1 || lda < (m > 0 ? m : 1)) return CTP_EINVAL;
+    if (p > kNoAllocMaxP) return CTP_ECAPACITY;
+    unsigned char *scratch = static_cast<unsigned char *>(noalloc_scratch_current_device());
+    if (scratch == nullptr) return CTP_ECUDA;
+    int num_sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CTP_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *info = reinterpret_cast<int32_t *>(scratch);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch + 256);
+    // the array keeps the previous call's contents: clear the info word and the keys
+    if (cudaMemsetAsync(info, 0, sizeof(int32_t), st) != cudaSuccess) return CTP_ECUDA;
+    if (cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)p * p, st) != cudaSuccess)
+        return CTP_ECUDA;
+    if (ctp::launch_compress_strict(A21, m, p, lda, keys, J, info, num_sms, st) != cudaSuccess)
+        return CTP_ECUDA;
+    if (ctp::launch_keys_to_rowmajor(keys, C, p, st) != cudaSuccess) return CTP_ECUDA;
+    if (info_host != nullptr) {
+        if (cudaMemcpyAsync(info_host, info, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CTP_ECUDA;
+    }
+    return CTP_OK;
+}

@@ -29,7 +29,7 @@ SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
 
 EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_compress_strict",
-           "ctp_compress_relaxed", "ctp_factor_supernode", "ctp_read_info", "ctp_profile_begin", "ctp_profile_end"]
+           "ctp_compress_strict_noalloc", "ctp_compress_relaxed", "ctp_factor_supernode", "ctp_read_info", "ctp_profile_begin", "ctp_profile_end"]
 
 
 class Options(ctypes.Structure):
@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
     L.ctp_workspace_size.argtypes = [P, i64, i32, ctypes.POINTER(Options), ctypes.POINTER(sz)]
     L.ctp_compress_strict.argtypes = [P, i64, i32, P, i64, P, P, P, sz, P]
     L.ctp_compress_relaxed.argtypes = [P, i64, i32, P, i64, P, P, P, sz, P]
+    L.ctp_compress_strict_noalloc.argtypes = [i64, i32, P, i64, P, P, ctypes.POINTER(i32), P]
     L.ctp_factor_supernode.argtypes = [P, i64, i32, P, i64, ctypes.POINTER(Options), P, P, P, P, P,
                                        i64, P, sz, P]
     L.ctp_read_info.argtypes = [P, P, ctypes.POINTER(i32), P]
@@ -178,6 +179,19 @@ class Context:
         _check("ctp_read_info", self.lib.ctp_read_info(self.handle, _ptr(ws), ctypes.byref(v),
                                                         _stream(stream)))
         return int(v.value)
+
+
+def compress_strict_noalloc(A21, m, p, lda, C, J=None, stream=None):
+    """Strict compression with the library's own fixed scratch (no workspace, no
+    device allocation) on the current device; returns the device info word.
+    For callers that cannot allocate device memory at the call site; calls that
+    overlap on the GPU race on the shared scratch."""
+    L = load()
+    info = ctypes.c_int32(-1)
+    _check("ctp_compress_strict_noalloc",
+           L.ctp_compress_strict_noalloc(m, p, _ptr(A21), lda, _ptr(C), _ptr(J), ctypes.byref(info),
+                                         _stream(stream)))
+    return int(info.value)
 
 
 # ---------------------------------------------------------------------------
