@@ -64,12 +64,14 @@ def parse_args():
     ap.add_argument("--p", type=int, default=256)
     ap.add_argument("--pivot", default="relaxed", choices=["strict", "relaxed", "restricted"])
     ap.add_argument("--smode", default="fp64_packed",
-                    choices=["none", "fp32", "fp64", "fp32_packed", "fp64_packed"])
+                    choices=["none", "fp32", "fp64", "fp32_packed", "fp64_packed", "fp32_tiled"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16"],
                     help="Form arithmetic: FP64, or BF16 tensor cores with FP32 accumulation")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tpp", action="store_true",
+                    help="skip the comparator: threshold partial pivoting on all rows (GPU)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the extra measurement with the Form on the tensor cores")
     return ap.parse_args()
@@ -265,8 +267,13 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
     S = None
     if smode != "none":
         dt = torch.float64 if smode.startswith("fp64") else torch.float32
-        S = (torch.empty(m * (m + 1) // 2, dtype=dt, device=dev) if smode.endswith("packed")
-             else torch.empty((m, m), dtype=dt, device=dev))
+        if smode.endswith("packed"):
+            S = torch.empty(m * (m + 1) // 2, dtype=dt, device=dev)
+        elif smode.endswith("tiled"):
+            nb = (m + 127) // 128
+            S = torch.empty(nb * (nb + 1) // 2 * 16384, dtype=dt, device=dev)
+        else:
+            S = torch.empty((m, m), dtype=dt, device=dev)
     ws = ctx.workspace(n, p, opt)
     stream = torch.cuda.current_stream()
 
@@ -375,13 +382,28 @@ def run_native(a):
                    0 if a.no_e2e else a.steps, peaks, world, dist)
     mixed = None
     if not a.no_mixed and a.prec == "fp64":
-        mx = measure(a, ctx, dev, A_host, "bf16", "fp32_packed", max(a.steps, 5), max(a.warmup, 3),
+        mx = measure(a, ctx, dev, A_host, "bf16", "fp32_tiled", max(a.steps, 5), max(a.warmup, 3),
                      0 if a.no_e2e else max(a.steps, 5), peaks, world, dist)
         mixed = {"value": mx["value"], "unit": "GFLOP/s", "ms_per_step": mx["ms"] / max(a.steps, 5),
-                 "prec": "Form on tensor cores: bf16 x bf16 -> f32, S fp32 packed; the rest f64",
+                 "prec": "Form on tensor cores: bf16 x bf16 -> f32, S fp32 in 128x128 blocks; "
+                         "the rest f64",
                  "roofline": mx["roofline"], "e2e": mx["e2e"], "gpu_launches": mx["launches"],
                  "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in mx["kern"].items()},
                  "clocks": mx["clocks"]}
+
+    tpp = None
+    if not a.no_tpp and a.pivot != "restricted":
+        import argparse as _ap
+        at = _ap.Namespace(**vars(a))
+        at.pivot = "tpp"
+        tp = measure(at, ctx, dev, A_host, "fp64", "none", 3, 1, 0, peaks, world, dist)
+        comp_ms = sum(v[1] for k, v in main["kern"].items() if not k.startswith("form")) / a.steps
+        tpp = {"pivot": "tpp (Listing 1 on all n rows, GPU)", "nelim": tp["e"],
+               "factor_solve_ms": tp["ms"] / 3,
+               "factor_solve_gflops": tp["fs"] * 3 / (tp["ms"] / 1e3) / 1e9,
+               "compressed_factor_solve_ms": comp_ms,
+               "compressed_factor_solve_gflops": main["fs"] / (comp_ms / 1e3) / 1e9,
+               "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in tp["kern"].items()}}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -411,6 +433,7 @@ def run_native(a):
             "clocks": main["clocks"],
             "fp64_dgemm_tflops": peaks["fp64_tflops"],
             "mixed": mixed,
+            "tpp_comparator": tpp,
         }
         print(json.dumps(line), flush=True)
     if dist:

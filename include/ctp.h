@@ -52,7 +52,9 @@ typedef enum {
 typedef enum {
     CTP_PIV_STRICT = 0,     /* strict compressed pivoting, Section 4.1 (eq. (4.1), eq. (4.3)) */
     CTP_PIV_RELAXED = 1,    /* relaxed compressed pivoting, Section 4.2 */
-    CTP_PIV_TPP = 2,        /* threshold partial pivoting on all n rows, Listing 1 (Section 2) */
+    CTP_PIV_TPP = 2,        /* threshold partial pivoting on all n rows, Listing 1 (Section 2);
+                               the comparator of the compressed strategies (smode must be
+                               CTP_S_NONE) */
     CTP_PIV_RESTRICTED = 3  /* restricted pivoting: tests look at A11 only, Section 3.2 */
 } ctp_pivot;
 
@@ -61,7 +63,8 @@ typedef enum {
 typedef enum {
     CTP_FP64 = 0,  /* FP64 throughout */
     CTP_BF16 = 1   /* Form on the tensor cores: BF16 operands, FP32 accumulation and
-                      FP32 S (requires smode CTP_S_FP32 or CTP_S_FP32_PACKED) */
+                      FP32 S (requires smode CTP_S_FP32, CTP_S_FP32_PACKED or
+                      CTP_S_FP32_TILED) */
 } ctp_prec;
 
 /* Storage of the Schur complement S (its lower triangle only):
@@ -69,13 +72,23 @@ typedef enum {
  *    strict upper triangle is not written;
  *  CTP_S_FP64_PACKED / CTP_S_FP32_PACKED: lower-packed by columns (LAPACK 'L'
  *    packed): S(i,j), i >= j, at index j*m - j*(j-1)/2 + (i-j); m*(m+1)/2
- *    entries; lds is ignored. */
+ *    entries; lds is ignored.
+ *  CTP_S_FP32_TILED: the lower block triangle in 128 x 128 blocks, each block
+ *    stored contiguously and column-major inside: with nb = ceil(m/128),
+ *    block (bi, bj), bi >= bj, starts at element
+ *    16384 * (bj*nb - bj*(bj-1)/2 + (bi - bj)), and S(i,j) sits at
+ *    (j mod 128)*128 + (i mod 128) inside it; nb*(nb+1)/2 blocks in all.
+ *    Diagonal blocks hold both triangles (S is symmetric); rows past m in the
+ *    last block row are zero.  Only with CTP_BF16 (the tensor-core Form writes
+ *    whole blocks front to back, which HBM absorbs at full speed, unlike the
+ *    column pieces of the full or packed layouts).  lds is ignored. */
 typedef enum {
     CTP_S_NONE = 0,
     CTP_S_FP64 = 1,
     CTP_S_FP32 = 2,
     CTP_S_FP64_PACKED = 3,
-    CTP_S_FP32_PACKED = 4
+    CTP_S_FP32_PACKED = 4,
+    CTP_S_FP32_TILED = 5
 } ctp_smode;
 
 /* Per-position pivot kinds written to piv[] (CTP_S_* above). */

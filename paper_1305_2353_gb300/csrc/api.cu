@@ -7,9 +7,12 @@
 
 namespace {
 constexpr int kMaxRec = 4096;
-enum KernelId { K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_NUM_IDS };
+enum KernelId {
+    K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP, K_NUM_IDS
+};
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
-                                       "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16"};
+                                       "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16",
+                                       "tpp_full_column"};
 }  // namespace
 
 struct ctp_ctx {
@@ -57,7 +60,8 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     L.Lb = off;
     off += align256(nb);
     L.aux = off;
-    off += align256(opt->pivot == CTP_PIV_RELAXED ? relaxed_aux_bytes(m, p, num_sms) : 0);
+    off += align256(opt->pivot == CTP_PIV_RELAXED ? relaxed_aux_bytes(m, p, num_sms)
+                                                  : (opt->pivot == CTP_PIV_TPP ? tpp_ws_bytes(p) : 0));
     L.total = off;
     return L;
 }
@@ -107,7 +111,7 @@ static ctp_status check_opts(const ctp_options *opt) {
     if (!(opt->small >= 0.0)) return CTP_EINVAL;
     if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
     if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16) return CTP_EINVAL;
-    if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP32_PACKED) return CTP_EINVAL;
+    if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP32_TILED) return CTP_EINVAL;
     return CTP_OK;
 }
 
@@ -172,14 +176,17 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     ctp_status s = check_opts(opt);
     if (s != CTP_OK) return s;
     const int64_t m = n - p;
-    const bool packed = opt->smode == CTP_S_FP64_PACKED || opt->smode == CTP_S_FP32_PACKED;
+    const bool packed = opt->smode == CTP_S_FP64_PACKED || opt->smode == CTP_S_FP32_PACKED ||
+                        opt->smode == CTP_S_FP32_TILED;
     if (opt->smode != CTP_S_NONE && (S == nullptr || (!packed && lds < (m > 0 ? m : 1))))
         return CTP_EINVAL;
     if (p > kMaxP) return CTP_EUNSUPPORTED;
-    if (opt->pivot == CTP_PIV_TPP) return CTP_EUNSUPPORTED;
+    if (opt->pivot == CTP_PIV_TPP && opt->smode != CTP_S_NONE) return CTP_EUNSUPPORTED;
     const bool tc = opt->prec == CTP_BF16 && opt->smode != CTP_S_NONE;
-    if (tc && opt->smode != CTP_S_FP32 && opt->smode != CTP_S_FP32_PACKED)
+    if (tc && opt->smode != CTP_S_FP32 && opt->smode != CTP_S_FP32_PACKED &&
+        opt->smode != CTP_S_FP32_TILED)
         return CTP_EUNSUPPORTED;  // the tensor-core Form writes FP32
+    if (!tc && opt->smode == CTP_S_FP32_TILED) return CTP_EUNSUPPORTED;
     WsLayout L = ws_layout(n, p, opt, ctx->num_sms);
     if (ws_bytes < L.total) return CTP_ENOMEM;
 
@@ -193,6 +200,14 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     const int Kp = form_tc_kpad(p);
     CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
 
+    if (opt->pivot == CTP_PIV_TPP) {
+        // Listing 1 on all n rows: factor and solve in one cooperative kernel
+        CTP_CUDA(timed(ctx, K_TPP, st, [&] {
+            return launch_tpp(A, n, p, lda, opt->u, opt->small, ws + L.aux, perm, piv, D, Dinv, nelim,
+                              info, ctx->num_sms, st);
+        }));
+        return CTP_OK;
+    }
     FactorArgs fa;
     fa.A = A;
     fa.lda = lda;
@@ -236,7 +251,8 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     if (opt->smode != CTP_S_NONE && m > 0) {
         if (tc)
             CTP_CUDA(timed(ctx, K_FORM_TC, st, [&] {
-                return launch_form_tc(Wb, Lbf, m, Kp, nelim, (float *)S, lds, packed ? 1 : 0, info,
+                return launch_form_tc(Wb, Lbf, m, Kp, nelim, (float *)S, lds,
+                                      opt->smode == CTP_S_FP32_TILED ? 2 : (packed ? 1 : 0), info,
                                       ctx->num_sms, st);
             }));
         else

@@ -62,11 +62,17 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
                               double *W21, int64_t ldw, void *Wb, void *Lb, int Kp,
                               cudaStream_t st);
 
+// Threshold partial pivoting on all n rows (the comparator of the compressed path).
+size_t tpp_ws_bytes(int p);
+cudaError_t launch_tpp(double *A, int64_t n, int p, int64_t lda, double u, double small, void *ws,
+                       int32_t *perm, int32_t *piv, double *D, double *Dinv, int32_t *nelim,
+                       int32_t *info, int num_sms, cudaStream_t st);
+
 // K-padding of the BF16 operand copies used by the tensor-core Form.
 int form_tc_kpad(int p);
 cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
-                           float *S, int64_t lds, int packed, int32_t *info, int num_sms,
-                           cudaStream_t st);
+                           float *S, int64_t lds, int layout /* 0 full, 1 packed, 2 tiled */,
+                           int32_t *info, int num_sms, cudaStream_t st);
 
 cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
                              int64_t m, const int32_t *nelim, void *S, int64_t lds, int smode,

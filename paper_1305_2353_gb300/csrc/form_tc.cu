@@ -1,7 +1,9 @@
 // form_tc.cu -- K6 (tensor cores): the Form task S = L21 D11 L21^T = W21 L21^T
 // (Section 1 task list), lower triangle, with BF16 operands and FP32
-// accumulation on the 5th-generation tensor cores (tcgen05), S stored as FP32
-// (full column-major or lower-packed by columns).
+// accumulation on the 5th-generation tensor cores (tcgen05), S stored as FP32:
+// full column-major, lower-packed by columns, or in contiguous 128 x 128 blocks
+// (the layout HBM absorbs at full write speed: each block is written front to
+// back, where the column layouts scatter 512-byte pieces over 256 columns).
 //
 // Layout: W21 and L21 are BF16 copies written by the Solve kernel, row-major
 // m x Kp (K = pivot position contiguous, Kp = p rounded up to 64, zero beyond
@@ -11,8 +13,10 @@
 // Kernel: persistent, one CTA per SM, walking the tiles of the lower triangle
 // (128 rows of S by 256 columns).  Warp roles:
 //   warp 0     TMA producer: 128B-swizzled K-blocks (64 BF16 = 128 bytes per
-//              row) of W21 (128 rows) and L21 (256 rows) into a 4-stage ring;
-//              also allocates and frees the tensor memory.
+//              row).  The L21 block of a column block of S (256 rows, all of K)
+//              stays resident in shared memory while consecutive tiles of this
+//              CTA share it; W21 blocks (128 rows) stream through a 6-stage
+//              ring.  Warp 0 also allocates and frees the tensor memory.
 //   warp 1     MMA issuer: one thread issues tcgen05.mma (M=128, N=256, K=16)
 //              into one of two FP32 accumulators of 256 TMEM columns each and
 //              commits stage releases and accumulator completion to mbarriers.
@@ -33,7 +37,8 @@ namespace ctp {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 6;
+constexpr int kMaxKB = 4;  // K blocks of 64 (p <= 256)
 constexpr int kUmmaK = 16;
 constexpr int kEpiWarps = 8;
 constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
@@ -43,7 +48,7 @@ constexpr uint32_t kTmemCols = 512;          // two 256-column FP32 accumulators
 constexpr long kSpinLimit = 1L << 22;
 
 struct Bars {
-    unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2];
+    unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2], bfull, bempty;
     uint32_t tmem_base;
     int abort;
 };
@@ -126,7 +131,7 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -137,42 +142,46 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
           "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Tiles of the lower triangle: row block a (128 rows) meets column blocks
-// 0..floor(a/2) (256 columns), so T(a) = a + floor(a/2) floor((a-1)/2) tiles
-// precede row block a.
-__host__ __device__ inline int64_t tiles_before(int64_t a) {
-    return a + (a / 2) * ((a - 1) / 2);
+// Tiles of the lower triangle, walked column block by column block: column
+// block b (256 columns) meets row blocks 2b..nM-1 (128 rows), so
+// T(b) = b*nM - b(b-1) tiles precede column block b.  Consecutive tiles --
+// which run at the same time on neighbouring SMs -- are vertically adjacent,
+// so their stores into a column of S land next to each other in HBM.
+__host__ __device__ inline int64_t tiles_before_col(int64_t b, int64_t nM) { return b * nM - b * (b - 1); }
+__host__ __device__ inline int64_t tile_count(int64_t nM) {
+    const int64_t nN = (nM + 1) / 2;  // column blocks that meet the triangle
+    return tiles_before_col(nN, nM);
 }
 __device__ __forceinline__ void decode_tile(int64_t t, int nM, int &ti, int &tj) {
-    int lo = 0, hi = nM;
+    int lo = 0, hi = (nM + 1) / 2;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (tiles_before(mid) <= t)
+        if (tiles_before_col(mid, nM) <= t)
             lo = mid;
         else
             hi = mid;
     }
-    ti = lo;
-    tj = (int)(t - tiles_before(lo));
+    tj = lo;
+    ti = 2 * lo + (int)(t - tiles_before_col(lo, nM));
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_form_tc(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapL,
               int64_t m, const int32_t *__restrict__ nelim_p, float *__restrict__ S, int64_t lds,
-              int packed, int32_t *__restrict__ info) {
+              int layout, int32_t *__restrict__ info) {
     extern __shared__ unsigned char smraw[];
     __shared__ Bars bars;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sA = smem;                               // [kStages][kStageA]
-    uint8_t *sB = smem + (size_t)kStages * kStageA;   // [kStages][kStageB]
+    uint8_t *sB = smem;                                 // [kMaxKB][kStageB]: resident L21 block
+    uint8_t *sA = smem + (size_t)kMaxKB * kStageB;     // [kStages][kStageA]: W21 ring
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e = *nelim_p;
     const int KB = (e + kBK - 1) / kBK;
     const int nM = (int)((m + kBM - 1) / kBM);
-    const int64_t ntiles = tiles_before(nM);
+    const int64_t ntiles = tile_count(nM);
+    const int64_t nb = nM;  // 128 x 128 blocks per block column in the tiled layout
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
@@ -183,6 +192,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mbar_init(&bars.acc_full[b], 1);
             mbar_init(&bars.acc_empty[b], kEpiWarps);
         }
+        mbar_init(&bars.bfull, 1);
+        mbar_init(&bars.bempty, 1);
         bars.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -200,22 +211,33 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const uint32_t idesc = idesc_bf16(kBM, kBN);
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: the L21 block of the current column block
+        // stays resident while consecutive tiles share it; W21 blocks stream
         if (lane == 0 && KB > 0) {
-            int stage = 0;
-            uint32_t phase = 0;
+            int stage = 0, cur_tj = -1;
+            uint32_t phase = 0, bphase = 0;
             for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 int ti, tj;
                 decode_tile(t, nM, ti, tj);
                 bool ok = true;
+                if (tj != cur_tj) {
+                    if (!mbar_wait(&bars.bempty, bphase ^ 1u, &bars)) {
+                        atomicExch(&bars.abort, 1);
+                        break;
+                    }
+                    mbar_expect_tx(&bars.bfull, (uint32_t)KB * kStageB);
+                    for (int kb = 0; kb < KB; kb++)
+                        tma_load_2d(sB + (size_t)kb * kStageB, &mapL, kb * kBK, tj * kBN, &bars.bfull);
+                    bphase ^= 1u;
+                    cur_tj = tj;
+                }
                 for (int kb = 0; kb < KB; kb++) {
                     if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&bars.full[stage], kStageA + kStageB);
+                    mbar_expect_tx(&bars.full[stage], kStageA);
                     tma_load_2d(sA + (size_t)stage * kStageA, &mapW, kb * kBK, ti * kBM, &bars.full[stage]);
-                    tma_load_2d(sB + (size_t)stage * kStageB, &mapL, kb * kBK, tj * kBN, &bars.full[stage]);
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1u;
@@ -230,16 +252,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int stage = 0, acc = 0;
-            uint32_t phase = 0, accphase = 0;
+            int stage = 0, acc = 0, cur_tj = -1;
+            uint32_t phase = 0, accphase = 0, bphase = 0;
             for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int ti, tj;
+                decode_tile(t, nM, ti, tj);
                 if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars)) {
                     atomicExch(&bars.abort, 1);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(acc * kBN);
                 bool ok = true;
+                if (KB > 0 && tj != cur_tj) {
+                    if (!mbar_wait(&bars.bfull, bphase, &bars)) {
+                        atomicExch(&bars.abort, 1);
+                        break;
+                    }
+                    tc_fence_after();
+                    bphase ^= 1u;
+                    cur_tj = tj;
+                }
+                const uint32_t dt = tmem + (uint32_t)(acc * kBN);
                 for (int kb = 0; kb < KB; kb++) {
                     if (!mbar_wait(&bars.full[stage], phase, &bars)) {
                         ok = false;
@@ -247,14 +280,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + (size_t)stage * kStageA);
-                    const uint32_t b0 = smem_u32(sB + (size_t)stage * kStageB);
+                    const uint32_t b0 = smem_u32(sB + (size_t)kb * kStageB);
 #pragma unroll
                     for (int k = 0; k < kBK / kUmmaK; k++) {
                         // advance 16 BF16 = 32 bytes along K inside the swizzled rows
                         umma_bf16(dt, sdesc(a0 + k * 32), sdesc(b0 + k * 32), idesc,
                                   (kb > 0 || k > 0) ? 1u : 0u);
                     }
-                    umma_commit(&bars.empty[stage]);  // stage free once these MMAs finish
+                    umma_commit(&bars.empty[stage]);  // W21 stage free once these MMAs finish
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1u;
@@ -265,6 +298,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     break;
                 }
                 umma_commit(&bars.acc_full[acc]);  // accumulator ready
+                // release the resident L21 block when the next tile needs another
+                if (KB > 0) {
+                    const int64_t tn = t + gridDim.x;
+                    int tin = 0, tjn = -1;
+                    if (tn < ntiles) decode_tile(tn, nM, tin, tjn);
+                    if (tjn != tj) umma_commit(&bars.bempty);
+                }
                 if (++acc == 2) {
                     acc = 0;
                     accphase ^= 1u;
@@ -287,23 +327,66 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             tc_fence_after();
             const int64_t i = (int64_t)ti * kBM + q * 32 + lane;
             const int64_t jbase = (int64_t)tj * kBN + half * 128;
+            // tiles strictly below the diagonal and inside S need no masking
+            const bool interior = (jbase + 127 < (int64_t)ti * kBM) && ((int64_t)ti * kBM + kBM <= m);
+            // block layout: this half of the tile is block (ti, 2 tj + half) of S;
+            // blocks above the block diagonal are not part of S
+            const int64_t bj = 2 * (int64_t)tj + half;
+            const bool tiled = layout == 2;
+            if (tiled && bj > ti) goto next_tile_half;
 #pragma unroll 1
-            for (int c = 0; c < 4; c++) {
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + half * 128 + c * 32);
-                tmem_ld32(taddr, r);
-                const int64_t j0 = jbase + c * 32;
-                if (i < m) {
+            for (int c = 0; c < 4; c += 2) {
+                uint32_t r[64];
+                const uint32_t taddr =
+                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + half * 128 + c * 32);
+                tmem_ld32_nowait(taddr, *reinterpret_cast<uint32_t(*)[32]>(&r[0]));
+                tmem_ld32_nowait(taddr + 32, *reinterpret_cast<uint32_t(*)[32]>(&r[32]));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (KB == 0) {
 #pragma unroll
-                    for (int x = 0; x < 32; x++) {
-                        const int64_t j = j0 + x;
-                        if (j <= i && j < m) {
-                            const int64_t idx = packed ? j * m - j * (j - 1) / 2 + (i - j) : j * lds + i;
-                            S[idx] = (KB > 0) ? __uint_as_float(r[x]) : 0.0f;
+                    for (int x = 0; x < 64; x++) r[x] = 0u;
+                }
+                const int64_t j0 = jbase + c * 32;
+                if (tiled) {
+                    // whole blocks, front to back: column c of the block is the
+                    // 512 bytes written by the four lane quarters
+                    float *blk = S + (int64_t)16384 * (bj * nb - bj * (bj - 1) / 2 + (ti - bj));
+                    float *ptr = blk + (int64_t)(c * 32) * 128 + q * 32 + lane;
+#pragma unroll
+                    for (int x = 0; x < 64; x++) ptr[x * 128] = __uint_as_float(r[x]);
+                    continue;
+                }
+                // S(i, j) lives at S + col(j) + i, with col(j) = j*lds (full) or
+                // j*m - j(j+1)/2 (packed; consecutive columns are m-1-j apart)
+                const bool packed = layout == 1;
+                float *ptr = S + (packed ? j0 * m - j0 * (j0 + 1) / 2 : j0 * lds) + i;
+                if (interior) {
+                    if (packed) {
+                        int d = (int)(m - 1 - j0);
+#pragma unroll
+                        for (int x = 0; x < 64; x++) {
+                            *ptr = __uint_as_float(r[x]);
+                            ptr += d;
+                            --d;
                         }
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < 64; x++) {
+                            *ptr = __uint_as_float(r[x]);
+                            ptr += lds;
+                        }
+                    }
+                } else {
+                    int64_t j = j0;
+#pragma unroll
+                    for (int x = 0; x < 64; x++) {
+                        if (i < m && j <= i) *ptr = __uint_as_float(r[x]);
+                        ptr += packed ? (m - 1 - j) : lds;
+                        ++j;
                     }
                 }
             }
+        next_tile_half:
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.acc_empty[acc]);
@@ -353,19 +436,19 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_
 int form_tc_kpad(int p) { return (p + kBK - 1) / kBK * kBK; }
 
 cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
-                           float *S, int64_t lds, int packed, int32_t *info, int num_sms,
+                           float *S, int64_t lds, int layout, int32_t *info, int num_sms,
                            cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     if ((((uintptr_t)Wb) | ((uintptr_t)Lb)) & 15) return cudaErrorMisalignedAddress;
     CUtensorMap mW, mL;
     if (!make_map(&mW, Wb, m, Kp, kBM) || !make_map(&mL, Lb, m, Kp, kBN)) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kStages * (kStageA + kStageB) + 1024;
+    const size_t smem = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA + 1024;
     cudaError_t err = cudaFuncSetAttribute(k_form_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const int nM = (int)((m + kBM - 1) / kBM);
-    const int64_t ntiles = tiles_before(nM);
+    const int64_t ntiles = tile_count(nM);
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-    k_form_tc<<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, packed, info);
+    k_form_tc<<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, layout, info);
     return cudaGetLastError();
 }
 

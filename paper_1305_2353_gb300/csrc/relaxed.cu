@@ -153,48 +153,120 @@ __global__ void __launch_bounds__(kT1)
 
 // Phases 2 and 3: the greedy of Section 4.2 over the merged candidate lists,
 // then the gather of the chosen rows into C (row-major, signed).
+//   (a) every thread merges, for one column, the first kHead entries of each
+//       segment list into one sorted prefix; the prefix is exact up to the
+//       smallest staged entry of any segment that holds more than kHead;
+//   (b) one thread runs the sequential greedy over those prefixes, with the
+//       chosen rows in a small open-addressing hash set; a column that
+//       exhausts its exact prefix (many collisions) falls back to walking the
+//       full segment lists in global memory.
+constexpr int kHead = 4;
+constexpr int kHash = 1024;  // > 2 * kMaxP slots
+
+__device__ __forceinline__ unsigned hslot(int row) { return ((unsigned)row * 2654435761u) >> 22; }
+__device__ __forceinline__ bool hash_has(const int *set, int row) {
+    for (unsigned h = hslot(row) & (kHash - 1);; h = (h + 1) & (kHash - 1)) {
+        if (set[h] == row) return true;
+        if (set[h] < 0) return false;
+    }
+}
+__device__ __forceinline__ void hash_put(int *set, int row) {
+    unsigned h = hslot(row) & (kHash - 1);
+    while (set[h] >= 0) h = (h + 1) & (kHash - 1);
+    set[h] = row;
+}
+
 __global__ void __launch_bounds__(256)
     k_relaxed_greedy(const double *__restrict__ A21, int64_t lda, int p, int nseg,
                      const Cand *__restrict__ lists, const int *__restrict__ lens,
                      double *__restrict__ C, int32_t *__restrict__ rows_out) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    const int W = nseg * kHead;                                      // merged prefix width
+    Cand *mrg = reinterpret_cast<Cand *>(gsm);                       // [p][W]
+    int *mlen = reinterpret_cast<int *>(mrg + (size_t)p * W);        // [p] exact prefix length
     __shared__ int chosen[kMaxP];
-    __shared__ int head[64];  // nseg <= 64
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        for (int j = 0; j < p; j++) {
-            for (int s = lane; s < nseg; s += 32) head[s] = 0;
-            __syncwarp();
-            int r = -1;
-            for (;;) {
-                // the best head over the segment lists of column j
-                Cand best;
-                best.key = 0;
-                best.row = 0x7fffffff;
-                int bs = -1;
-                for (int s = 0; s < nseg; s++) {
-                    const int h = head[s];
-                    if (h < lens[j * nseg + s]) {
-                        const Cand c = lists[((int64_t)j * nseg + s) * p + h];
-                        if (bs < 0 || before(c, best)) {
-                            best = c;
-                            bs = s;
-                        }
-                    }
+    __shared__ int hset[kHash];
+    for (int i = threadIdx.x; i < kHash; i += blockDim.x) hset[i] = -1;
+    // (a) per-column merge of the staged heads
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        Cand *out = mrg + (size_t)j * W;
+        int cnt = 0;
+        bool have_lim = false;
+        Cand lim;
+        lim.key = 0;
+        lim.row = 0x7fffffff;
+        for (int s = 0; s < nseg; s++) {
+            const int li = j * nseg + s;
+            const int len = lens[li];
+            const int h = len < kHead ? len : kHead;
+            for (int q = 0; q < h; q++) {
+                const Cand c = lists[(int64_t)li * p + q];
+                int at = cnt++;
+                while (at > 0 && before(c, out[at - 1])) {  // insertion into the sorted prefix
+                    out[at] = out[at - 1];
+                    --at;
                 }
-                if (bs < 0) break;  // every A21 row is already flagged
-                // flagged already?
-                bool hit = false;
-                for (int q = lane; q < j; q += 32) hit |= (chosen[q] == best.row);
-                hit = __any_sync(0xffffffffu, hit);
-                if (!hit) {
-                    r = best.row;
+                out[at] = c;
+            }
+            if (len > kHead) {
+                // entries beyond this segment's staged ones may come after its last staged entry
+                const Cand last = lists[(int64_t)li * p + kHead - 1];
+                if (!have_lim || before(last, lim)) {
+                    lim = last;
+                    have_lim = true;
+                }
+            }
+        }
+        int exact = cnt;
+        if (have_lim) {
+            exact = 0;
+            while (exact < cnt && !before(lim, out[exact])) ++exact;  // out[exact] <= lim in order
+        }
+        mlen[j] = exact;
+    }
+    __syncthreads();
+    // (b) the sequential greedy
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < p; j++) {
+            const Cand *pre = mrg + (size_t)j * W;
+            const int ex = mlen[j];
+            int r = -1;
+            bool done = false;
+            for (int q = 0; q < ex; q++)
+                if (!hash_has(hset, pre[q].row)) {
+                    r = pre[q].row;
+                    done = true;
                     break;
                 }
-                if (lane == 0) head[bs]++;
-                __syncwarp();
+            if (!done) {
+                // slow path: walk the full segment lists of column j in order
+                int head[64];
+                for (int s = 0; s < nseg; s++) head[s] = 0;
+                for (;;) {
+                    int bs = -1;
+                    Cand best;
+                    best.key = 0;
+                    best.row = 0x7fffffff;
+                    for (int s = 0; s < nseg; s++) {
+                        const int li = j * nseg + s;
+                        if (head[s] < lens[li]) {
+                            const Cand c = lists[(int64_t)li * p + head[s]];
+                            if (bs < 0 || before(c, best)) {
+                                best = c;
+                                bs = s;
+                            }
+                        }
+                    }
+                    if (bs < 0) break;  // every A21 row is already flagged
+                    if (!hash_has(hset, best.row)) {
+                        r = best.row;
+                        break;
+                    }
+                    head[bs]++;
+                }
             }
-            if (lane == 0) chosen[j] = r;
-            __syncwarp();
+            chosen[j] = r;
+            if (r >= 0) hash_put(hset, r);
         }
     }
     __syncthreads();
@@ -220,7 +292,7 @@ int relaxed_segments(int64_t m, int p, int num_sms) {
     int64_t maxseg = (m + 8 * kChunk - 1) / (8 * kChunk);
     int64_t s = want < maxseg ? want : maxseg;
     if (s < 1) s = 1;
-    if (s > 64) s = 64;
+    if (s > 8) s = 8;  // the greedy stages 4 heads of every list in shared memory
     return (int)s;
 }
 
@@ -244,7 +316,11 @@ cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t
         cudaError_t err = cudaMemsetAsync(lens, 0, sizeof(int) * (size_t)p * nseg, st);
         if (err != cudaSuccess) return err;
     }
-    k_relaxed_greedy<<<1, 256, 0, st>>>(A21, lda, p, nseg, lists, lens, C, rows);
+    const size_t gsmem = sizeof(Cand) * (size_t)p * nseg * kHead + sizeof(int) * (size_t)p;
+    cudaError_t err2 =
+        cudaFuncSetAttribute(k_relaxed_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+    if (err2 != cudaSuccess) return err2;
+    k_relaxed_greedy<<<1, 256, gsmem, st>>>(A21, lda, p, nseg, lists, lens, C, rows);
     return cudaGetLastError();
 }
 

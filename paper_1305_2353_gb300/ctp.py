@@ -25,7 +25,7 @@ STATUS = {0: "CTP_OK", 1: "CTP_EINVAL", 2: "CTP_ENOMEM", 3: "CTP_ECUDA", 4: "CTP
           5: "CTP_ETIMEOUT", 6: "CTP_ECAPACITY", 7: "CTP_EUNSUPPORTED"}
 PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3}
 PREC = {"fp64": 0, "bf16": 1}
-SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4}
+SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4, "fp32_tiled": 5}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
 
 EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_compress_strict",
@@ -218,6 +218,20 @@ def unpack_lower(packed: np.ndarray, m: int) -> np.ndarray:
     return S
 
 
+def unpack_tiled(blocks: np.ndarray, m: int) -> np.ndarray:
+    """128 x 128 block layout (lower block triangle, blocks column-major inside)
+    -> m x m matrix holding the lower triangle (strict upper part zeroed)."""
+    nb = (m + 127) // 128
+    S = np.zeros((nb * 128, nb * 128), dtype=blocks.dtype)
+    k = 0
+    for bj in range(nb):
+        for bi in range(bj, nb):
+            S[bi * 128:(bi + 1) * 128, bj * 128:(bj + 1) * 128] = \
+                blocks[k * 16384:(k + 1) * 16384].reshape(128, 128).T
+            k += 1
+    return np.tril(S[:m, :m])
+
+
 class Supernode:
     """Device buffers for one factorization of an n x p supernode."""
 
@@ -237,6 +251,9 @@ class Supernode:
             dt = torch.float64 if opt.smode in (1, 3) else torch.float32
             if opt.smode in (3, 4):
                 self.S = torch.zeros(max(m * (m + 1) // 2, 1), dtype=dt, device=dev)  # packed
+            elif opt.smode == 5:
+                nb = (m + 127) // 128
+                self.S = torch.zeros(max(nb * (nb + 1) // 2 * 16384, 1), dtype=dt, device=dev)
             else:
                 self.S = torch.zeros((m, m), dtype=dt, device=dev)  # column-major m x m
         self.opt = opt
@@ -253,6 +270,8 @@ class Supernode:
         if self.S is not None:
             if self.opt.smode in (3, 4):
                 out["S"] = unpack_lower(self.S.cpu().numpy(), self.n - self.p)
+            elif self.opt.smode == 5:
+                out["S"] = unpack_tiled(self.S.cpu().numpy(), self.n - self.p)
             else:
                 out["S"] = to_numpy(self.S)
         out["info"] = self.ctx.read_info(self.ws)

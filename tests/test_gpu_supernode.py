@@ -152,7 +152,7 @@ CASES = [(1, 1), (2, 2), (3, 1), (30, 30), (300, 17), (513, 33), (1200, 100), (8
          (3000, 256), (700, 129)]
 
 
-@pytest.mark.parametrize("pivot", ["strict", "relaxed", "restricted"])
+@pytest.mark.parametrize("pivot", ["strict", "relaxed", "restricted", "tpp"])
 @pytest.mark.parametrize("n,p", CASES)
 @pytest.mark.parametrize("seed", [0, 1])
 def test_factor_matches_oracle(ctx, pivot, n, p, seed):
@@ -209,6 +209,21 @@ def test_large_supernode_relaxed_full_size(ctx):
     assert ref["nelim"] == p
     compare(ref, got, p, A, check_recon=False)
     rows_s = np.r_[0:p + 64, np.random.default_rng(1).choice(np.arange(p, n), 4000, replace=False)]
+    sub = dict(got)
+    sub["A"] = got["A"][rows_s]
+    assert recon_error(A[rows_s], p, sub) <= 1e-14
+
+
+def test_large_supernode_tpp_full_size(ctx):
+    """Full-column threshold partial pivoting (the comparator) at n = 200000,
+    p = 256 against the oracle's Listing 1 on all rows."""
+    n, p = 200000, 256
+    A = inputs.single_large(0)
+    ref = O.factor(A, p, "tpp", log_cap=400000)
+    got = run_gpu(ctx, A, p, "tpp")
+    assert ref["nelim"] == p
+    compare(ref, got, p, A, check_recon=False)
+    rows_s = np.r_[0:p + 64, np.random.default_rng(2).choice(np.arange(p, n), 4000, replace=False)]
     sub = dict(got)
     sub["A"] = got["A"][rows_s]
     assert recon_error(A[rows_s], p, sub) <= 1e-14
@@ -281,7 +296,8 @@ def _bf16_bound(Wd, L21):
 
 
 @pytest.mark.parametrize("pivot,smode", [("strict", "fp32"), ("relaxed", "fp32"),
-                                         ("relaxed", "fp32_packed")])
+                                         ("relaxed", "fp32_packed"), ("relaxed", "fp32_tiled"),
+                                         ("strict", "fp32_tiled")])
 @pytest.mark.parametrize("n,p", [(600, 40), (2000, 64), (1500, 130), (3000, 256), (700, 200)])
 def test_form_tensor_cores_bf16(ctx, pivot, smode, n, p):
     """S from the tcgen05 kernel (BF16 operands, FP32 accumulation) against the
