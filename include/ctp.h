@@ -198,6 +198,57 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
 ctp_status ctp_read_info(ctp_ctx *ctx, const void *workspace, int32_t *info_host, void *stream);
 
 
+/* ------------------------------------------------------------------------ */
+/* Batched factorization of many independent supernodes (the fronts of an
+ * assembly tree), each exactly as ctp_factor_supernode would factor it.
+ *
+ * Device-visible descriptor of one front (an array of them lives in device
+ * memory); all pointers are device pointers with the meaning they have in
+ * ctp_factor_supernode.  S is written in the layout given by opt->smode. */
+typedef struct {
+    int64_t n;
+    int32_t p;
+    int32_t reserved;
+    double *A;
+    int64_t lda;
+    int32_t *perm;
+    int32_t *piv;
+    double *D;
+    int32_t *nelim;
+    void *S;
+    int64_t lds;
+} ctp_front;
+
+typedef struct ctp_plan ctp_plan;
+
+/* Plan a batch from the fronts' shapes (host arrays n_host[nb], p_host[nb];
+ * 1 <= p <= ctp_max_p(), n >= p).  The plan holds the launch geometry and the
+ * tables the kernels need; *ws_bytes receives the device workspace the batch
+ * needs.  Pivoting: CTP_PIV_STRICT or CTP_PIV_RESTRICTED; prec/smode: FP64
+ * with CTP_S_NONE / CTP_S_FP64_PACKED / CTP_S_FP32_PACKED, or CTP_BF16 with
+ * CTP_S_FP32_TILED (Form on the tensor cores). */
+ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host,
+                                 const int32_t *p_host, const ctp_options *opt, ctp_plan **plan,
+                                 size_t *ws_bytes);
+ctp_status ctp_batch_plan_destroy(ctp_plan *plan);
+
+/* Copy the plan's tables into the workspace (one host-to-device copy on
+ * `stream`); required once per workspace before ctp_factor_batch. */
+ctp_status ctp_batch_upload(ctp_ctx *ctx, const ctp_plan *plan, void *workspace, size_t ws_bytes,
+                            void *stream);
+
+/* Factor every front of the batch: only kernel launches on `stream` (no host
+ * synchronisation, no copy, no allocation), so the call can be captured into
+ * a CUDA graph and replayed.  fronts: device array of nb descriptors. */
+ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front *fronts,
+                            void *workspace, size_t ws_bytes, void *stream);
+
+/* Per-front device info words of the last ctp_factor_batch on this workspace
+ * (synchronises `stream`): flags_host[nb] receives CTP_OK or a device-side
+ * condition per front. */
+ctp_status ctp_batch_read_info(ctp_ctx *ctx, const ctp_plan *plan, const void *workspace,
+                               int32_t *flags_host, void *stream);
+
 /* Optional per-kernel timing.  Between ctp_profile_begin() and ctp_profile_end()
  * every kernel this library launches is bracketed by two CUDA events recorded
  * on its launch stream (at most 4096 launches are recorded).  ctp_profile_end()

@@ -8,11 +8,16 @@
 namespace {
 constexpr int kMaxRec = 4096;
 enum KernelId {
-    K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP, K_NUM_IDS
+    K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP,
+    K_B_PREPARE, K_B_COMPRESS, K_B_FACTOR_G1, K_B_FACTOR_G2, K_B_FACTOR_G4, K_B_FACTOR_G8,
+    K_B_FACTOR_G16, K_B_SOLVE, K_B_FORM, K_NUM_IDS
 };
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
                                        "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16",
-                                       "tpp_full_column"};
+                                       "tpp_full_column", "batch_prepare", "batch_compress_strict",
+                                       "batch_factor_g1", "batch_factor_g2", "batch_factor_g4",
+                                       "batch_factor_g8", "batch_factor_g16", "batch_solve_fp64",
+                                       "batch_form"};
 }  // namespace
 
 struct ctp_ctx {
@@ -312,6 +317,24 @@ ctp_status ctp_profile_end(ctp_ctx *ctx, int32_t max_kernels, char *names, doubl
     }
     *nkernels = k;
     ctx->nrec = 0;
+    return CTP_OK;
+}
+
+ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front *fronts,
+                            void *workspace, size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || plan == nullptr || fronts == nullptr || workspace == nullptr) return CTP_EINVAL;
+    if (ws_bytes < batch_total(plan)) return CTP_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)workspace;
+    CTP_CUDA(timed(ctx, K_B_PREPARE, st, [&] { return batch_prepare(plan, w, st); }));
+    CTP_CUDA(timed(ctx, K_B_COMPRESS, st, [&] { return batch_compress(plan, fronts, w, ctx->num_sms, st); }));
+    for (int c = 0; c < batch_num_classes(plan); c++) {
+        const int G = batch_class_G(plan, c);
+        const int id = K_B_FACTOR_G1 + (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4);
+        CTP_CUDA(timed(ctx, id, st, [&] { return batch_factor_class(plan, c, fronts, w, st); }));
+    }
+    CTP_CUDA(timed(ctx, K_B_SOLVE, st, [&] { return batch_solve(plan, fronts, w, st); }));
+    CTP_CUDA(timed(ctx, K_B_FORM, st, [&] { return batch_form(plan, fronts, w, ctx->num_sms, st); }));
     return CTP_OK;
 }
 

@@ -1,0 +1,403 @@
+// batch.cu -- factorization of many independent supernodes (fronts) in a few
+// launches: the batched path of the per-supernode hot path.
+//
+// The host builds a plan once from the fronts' shapes: a workspace section per
+// front, the work-item tables of every batched kernel (item -> front maps and
+// per-front first items), the fronts grouped by the cluster width of the pivot
+// search, and the rows of each front in the stacked BF16 operand buffers of the
+// tensor-core Form (each front padded to 256 rows, K stride 256).  The tables
+// are copied into the workspace once (ctp_batch_upload); ctp_factor_batch then
+// only launches kernels -- prepare, compress, one pivot-search launch per
+// cluster width, Solve, Form -- so it can be captured into a CUDA graph.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ctp_internal.cuh"
+
+namespace ctp {
+
+int64_t form_fp64_tiles(int64_t m);
+int64_t form_tc_tiles(int64_t m);
+
+namespace {
+
+constexpr int kTR = 32;     // rows per compression item
+constexpr int kThreads = 256;
+constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long kInfKey = 0x7FF0000000000000ull;
+
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
+}
+
+// clear every front's info word and (strict) compressed-matrix keys, and the
+// batch-wide info word
+__global__ void k_batch_prepare(const BFront *__restrict__ tab, char *ws, BatchOpts o, int32_t *ginfo) {
+    const int f = blockIdx.x;
+    if (f == 0 && threadIdx.x == 0) *ginfo = 0;
+    const BFront bt = tab[f];
+    ctp_options oo;
+    oo.pivot = o.pivot;
+    oo.smode = o.smode;
+    oo.prec = o.prec;
+    const BSection sec = bsection(bt.n, bt.p, &oo);
+    char *base = ws + bt.ws;
+    if (threadIdx.x == 0) *reinterpret_cast<int32_t *>(base + sec.info) = 0;
+    if (o.pivot == CTP_PIV_STRICT) {
+        unsigned long long *keys = reinterpret_cast<unsigned long long *>(base + sec.C);
+        for (int i = threadIdx.x; i < bt.p * bt.p; i += blockDim.x) keys[i] = 0;
+    }
+}
+
+// Strict compression (Section 4.1, eq. (4.1)), one 32-row tile of one front per
+// CTA: integer argmax per row, then test-then-atomicMax into the front's C.
+__global__ void __launch_bounds__(kThreads)
+    k_compress_strict_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
+                            char *ws, const int *__restrict__ item_front, BatchOpts o) {
+    extern __shared__ __align__(16) double tile[];  // [p][kTR+1]
+    __shared__ unsigned long long pkey[kThreads];
+    __shared__ int pidx[kThreads];
+    __shared__ int rowJ[kTR];
+    const int f = item_front[blockIdx.x];
+    const BFront bt = tab[f];
+    const ctp_front fr = fronts[f];
+    ctp_options oo;
+    oo.pivot = o.pivot;
+    oo.smode = o.smode;
+    oo.prec = o.prec;
+    const BSection sec = bsection(bt.n, bt.p, &oo);
+    char *base = ws + bt.ws;
+    unsigned long long *Ckeys = reinterpret_cast<unsigned long long *>(base + sec.C);
+    const int p = bt.p;
+    const int64_t m = bt.m;
+    const int64_t row0 = (blockIdx.x - bt.c0) * (int64_t)kTR;
+    const double *A21 = fr.A + p;
+    const int nrows = (int)((m - row0) < kTR ? (m - row0) : kTR);
+    for (int idx = threadIdx.x; idx < kTR * p; idx += kThreads) {
+        const int k = idx / kTR, r = idx % kTR;
+        tile[k * (kTR + 1) + r] = r < nrows ? A21[(int64_t)k * fr.lda + row0 + r] : 0.0;
+    }
+    __syncthreads();
+    constexpr int NG = kThreads / kTR;
+    const int r = threadIdx.x % kTR, g = threadIdx.x / kTR;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    bool nonfinite = false;
+    unsigned long long best = 0;
+    int bidx = -1;
+    if (r < nrows)
+        for (int k = g; k < p; k += NG) {
+            const unsigned long long key = abs_key(tile[k * (kTR + 1) + r]);
+            nonfinite |= key >= kInfKey;
+            if (bidx < 0 || key > best) {
+                best = key;
+                bidx = k;
+            }
+        }
+    pkey[g * kTR + r] = best;
+    pidx[g * kTR + r] = bidx;
+    __syncthreads();
+    if (threadIdx.x < kTR) {
+        unsigned long long b = 0;
+        int bi = -1;
+        for (int gg = 0; gg < NG; gg++) {
+            const int ii = pidx[gg * kTR + threadIdx.x];
+            const unsigned long long kk = pkey[gg * kTR + threadIdx.x];
+            if (ii < 0) continue;
+            if (bi < 0 || kk > b || (kk == b && ii < bi)) {
+                b = kk;
+                bi = ii;
+            }
+        }
+        rowJ[threadIdx.x] = bi;
+    }
+    __syncthreads();
+    for (int rr = warp; rr < nrows; rr += kThreads / 32) {
+        unsigned long long *crow = Ckeys + (int64_t)rowJ[rr] * p;
+        for (int k = lane; k < p; k += 32) {
+            const unsigned long long key = abs_key(tile[k * (kTR + 1) + rr]);
+            if (key > __ldcg(crow + k)) atomicMax(crow + k, key);
+        }
+    }
+    if (nonfinite) atomicCAS(reinterpret_cast<int32_t *>(base + sec.info), kInfoOk, (int32_t)CTP_ENONFINITE);
+}
+
+// gather the per-front info words into one array (a batch-wide condition, such
+// as a timeout in the batched Form, is reported for every front still OK)
+__global__ void k_batch_flags(const BFront *__restrict__ tab, const char *ws, BatchOpts o, int nb,
+                              const int32_t *ginfo, int32_t *flags) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nb) return;
+    const BFront bt = tab[f];
+    ctp_options oo;
+    oo.pivot = o.pivot;
+    oo.smode = o.smode;
+    oo.prec = o.prec;
+    const BSection sec = bsection(bt.n, bt.p, &oo);
+    const int32_t v = *reinterpret_cast<const int32_t *>(ws + bt.ws + sec.info);
+    flags[f] = v != kInfoOk ? v : *ginfo;
+}
+
+}  // namespace
+
+cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                                         const int *item_front, int64_t items, BatchOpts o,
+                                         int num_sms, cudaStream_t st) {
+    (void)num_sms;
+    if (items == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * (size_t)kMaxP * (kTR + 1);
+    cudaError_t err = cudaFuncSetAttribute(k_compress_strict_batch,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_compress_strict_batch<<<(unsigned)items, kThreads, smem, st>>>(fronts, tab, ws, item_front, o);
+    return cudaGetLastError();
+}
+
+}  // namespace ctp
+
+// ---------------------------------------------------------------------------
+// plan
+
+using namespace ctp;
+
+struct ctp_plan {
+    int nb;
+    ctp_options opt;
+    BatchOpts bo;
+    int pmax;
+    bool tc;
+    // workspace layout
+    size_t off_ginfo, off_tab, off_citem, off_sitem, off_fitem, off_lists, off_flags, off_sections, off_wb,
+        off_lb;
+    size_t total;
+    int64_t c_items, s_items, f_items, total_rows;
+    struct Class {
+        int G, pmax, count;
+        size_t list_off;  // element offset in the class-list array
+    };
+    std::vector<Class> classes;
+    std::vector<unsigned char> blob;  // tables, in workspace order (up to off_sections)
+};
+
+static int batch_cluster_width(int p, int R) {
+    // narrowest cluster whose shared memory (columns of [A11; C] plus two pivot
+    // columns) stays under ~100 KB, so that two clusters' CTAs share an SM
+    for (int G = 1; G <= 16; G <<= 1) {
+        const int ncl = (p + G - 1) / G;
+        const size_t smem = sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R));
+        if (smem <= 100 * 1024) return G;
+    }
+    return 16;
+}
+
+extern "C" {
+
+ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host,
+                                 const int32_t *p_host, const ctp_options *opt, ctp_plan **plan,
+                                 size_t *ws_bytes) {
+    if (ctx == nullptr || plan == nullptr || opt == nullptr || nb < 1 || n_host == nullptr ||
+        p_host == nullptr)
+        return CTP_EINVAL;
+    *plan = nullptr;
+    if (!(opt->u > 0.0) || opt->u > 0.5 || !(opt->small >= 0.0)) return CTP_EINVAL;
+    if (opt->pivot != CTP_PIV_STRICT && opt->pivot != CTP_PIV_RESTRICTED) return CTP_EUNSUPPORTED;
+    const bool tc = opt->prec == CTP_BF16 && opt->smode != CTP_S_NONE;
+    if (tc && opt->smode != CTP_S_FP32_TILED) return CTP_EUNSUPPORTED;
+    if (!tc && opt->smode != CTP_S_NONE && opt->smode != CTP_S_FP64_PACKED &&
+        opt->smode != CTP_S_FP32_PACKED)
+        return CTP_EUNSUPPORTED;
+    for (int f = 0; f < nb; f++) {
+        if (p_host[f] < 1 || n_host[f] < p_host[f]) return CTP_EINVAL;
+        if (p_host[f] > kMaxP) return CTP_EUNSUPPORTED;
+        if (n_host[f] - p_host[f] > 0x7fffffffLL) return CTP_EUNSUPPORTED;
+    }
+    ctp_plan *P = new ctp_plan();
+    P->nb = nb;
+    P->opt = *opt;
+    P->bo.u = opt->u;
+    P->bo.small = opt->small;
+    P->bo.pivot = opt->pivot;
+    P->bo.smode = opt->smode;
+    P->bo.prec = opt->prec;
+    P->tc = tc;
+    P->pmax = 1;
+    std::vector<BFront> tab(nb);
+    std::vector<int> citem, sitem, fitem;
+    size_t sec_off = 0;
+    int64_t row0 = 0;
+    for (int f = 0; f < nb; f++) {
+        BFront &b = tab[f];
+        b.n = n_host[f];
+        b.p = p_host[f];
+        b.m = b.n - b.p;
+        b.nM = (int)((b.m + 127) / 128);
+        b.ws = (int64_t)sec_off;
+        sec_off += bsection(b.n, b.p, opt).total;
+        b.row0 = row0;
+        if (tc) row0 += (b.m + 255) / 256 * 256;
+        b.c0 = (int64_t)citem.size();
+        const int64_t nt = (b.m + kTR - 1) / kTR;
+        if (opt->pivot == CTP_PIV_STRICT)
+            for (int64_t t = 0; t < nt; t++) citem.push_back(f);
+        b.s0 = (int64_t)sitem.size();
+        for (int64_t t = 0; t < nt; t++) sitem.push_back(f);
+        b.f0 = (int64_t)fitem.size();
+        if (opt->smode != CTP_S_NONE) {
+            const int64_t ft = tc ? form_tc_tiles(b.m) : form_fp64_tiles(b.m);
+            for (int64_t t = 0; t < ft; t++) fitem.push_back(f);
+        }
+        P->pmax = std::max(P->pmax, b.p);
+    }
+    // fronts by cluster width of the pivot search
+    std::vector<std::vector<int>> byG(5);
+    std::vector<int> pmaxG(5, 1);
+    for (int f = 0; f < nb; f++) {
+        const int R = opt->pivot == CTP_PIV_STRICT ? tab[f].p : 0;
+        const int G = batch_cluster_width(tab[f].p, R);
+        const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4;
+        byG[gi].push_back(f);
+        pmaxG[gi] = std::max(pmaxG[gi], tab[f].p);
+    }
+    std::vector<int> lists;
+    for (int gi = 0; gi < 5; gi++) {
+        if (byG[gi].empty()) continue;
+        ctp_plan::Class c;
+        c.G = 1 << gi;
+        c.pmax = pmaxG[gi];
+        c.count = (int)byG[gi].size();
+        c.list_off = lists.size();
+        lists.insert(lists.end(), byG[gi].begin(), byG[gi].end());
+        P->classes.push_back(c);
+    }
+    P->c_items = (int64_t)citem.size();
+    P->s_items = (int64_t)sitem.size();
+    P->f_items = (int64_t)fitem.size();
+    P->total_rows = row0;
+    // workspace layout
+    size_t off = 0;
+    P->off_ginfo = off;  // batch-wide info word (tensor-core Form timeouts)
+    off += 256;
+    P->off_tab = off;
+    off += align256(sizeof(BFront) * (size_t)nb);
+    P->off_citem = off;
+    off += align256(sizeof(int) * citem.size());
+    P->off_sitem = off;
+    off += align256(sizeof(int) * sitem.size());
+    P->off_fitem = off;
+    off += align256(sizeof(int) * fitem.size());
+    P->off_lists = off;
+    off += align256(sizeof(int) * lists.size());
+    P->off_flags = off;
+    off += align256(sizeof(int32_t) * (size_t)nb);
+    const size_t tables_end = off;
+    P->off_sections = off;
+    off += align256(sec_off);
+    P->off_wb = off;
+    off += align256(tc ? 2 * (size_t)row0 * kBatchKp : 0);
+    P->off_lb = off;
+    off += align256(tc ? 2 * (size_t)row0 * kBatchKp : 0);
+    P->total = off;
+    // section offsets are relative to the sections base: shift them to the workspace base
+    for (int f = 0; f < nb; f++) tab[f].ws += (int64_t)P->off_sections;
+    P->blob.assign(tables_end, 0);
+    memcpy(P->blob.data() + P->off_tab, tab.data(), sizeof(BFront) * (size_t)nb);
+    if (!citem.empty()) memcpy(P->blob.data() + P->off_citem, citem.data(), sizeof(int) * citem.size());
+    if (!sitem.empty()) memcpy(P->blob.data() + P->off_sitem, sitem.data(), sizeof(int) * sitem.size());
+    if (!fitem.empty()) memcpy(P->blob.data() + P->off_fitem, fitem.data(), sizeof(int) * fitem.size());
+    if (!lists.empty()) memcpy(P->blob.data() + P->off_lists, lists.data(), sizeof(int) * lists.size());
+    *plan = P;
+    if (ws_bytes) *ws_bytes = P->total;
+    return CTP_OK;
+}
+
+ctp_status ctp_batch_plan_destroy(ctp_plan *plan) {
+    delete plan;
+    return CTP_OK;
+}
+
+ctp_status ctp_batch_upload(ctp_ctx *ctx, const ctp_plan *plan, void *workspace, size_t ws_bytes,
+                            void *stream) {
+    if (ctx == nullptr || plan == nullptr || workspace == nullptr) return CTP_EINVAL;
+    if (ws_bytes < plan->total) return CTP_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)workspace;
+    if (cudaMemcpyAsync(w, plan->blob.data(), plan->blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return CTP_ECUDA;
+    if (plan->tc) {
+        // padding rows of the stacked operands must read as zero
+        if (cudaMemsetAsync(w + plan->off_wb, 0, plan->off_lb - plan->off_wb, st) != cudaSuccess ||
+            cudaMemsetAsync(w + plan->off_lb, 0, plan->total - plan->off_lb, st) != cudaSuccess)
+            return CTP_ECUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CTP_ECUDA;  // the blob is pageable
+    return CTP_OK;
+}
+
+ctp_status ctp_batch_read_info(ctp_ctx *ctx, const ctp_plan *plan, const void *workspace,
+                               int32_t *flags_host, void *stream) {
+    if (ctx == nullptr || plan == nullptr || workspace == nullptr || flags_host == nullptr)
+        return CTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)const_cast<void *>(workspace);
+    k_batch_flags<<<(plan->nb + 255) / 256, 256, 0, st>>>(
+        reinterpret_cast<const BFront *>(w + plan->off_tab), w, plan->bo, plan->nb,
+        reinterpret_cast<const int32_t *>(w + plan->off_ginfo), reinterpret_cast<int32_t *>(w + plan->off_flags));
+    if (cudaGetLastError() != cudaSuccess) return CTP_ECUDA;
+    if (cudaMemcpyAsync(flags_host, w + plan->off_flags, sizeof(int32_t) * (size_t)plan->nb,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return CTP_ECUDA;
+    return CTP_OK;
+}
+
+}  // extern "C"
+
+// The launch sequence (called from api.cu, which owns the profiling hooks).
+namespace ctp {
+
+struct BatchLaunch {
+    const ctp_plan *P;
+    const ctp_front *fronts;
+    char *w;
+};
+
+int batch_num_classes(const ctp_plan *P) { return (int)P->classes.size(); }
+int batch_class_G(const ctp_plan *P, int c) { return P->classes[c].G; }
+size_t batch_total(const ctp_plan *P) { return P->total; }
+
+cudaError_t batch_prepare(const ctp_plan *P, char *w, cudaStream_t st) {
+    k_batch_prepare<<<P->nb, 256, 0, st>>>(reinterpret_cast<const BFront *>(w + P->off_tab), w, P->bo,
+                                            reinterpret_cast<int32_t *>(w + P->off_ginfo));
+    return cudaGetLastError();
+}
+cudaError_t batch_compress(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st) {
+    if (P->opt.pivot != CTP_PIV_STRICT) return cudaSuccess;
+    return launch_compress_strict_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
+                                        reinterpret_cast<const int *>(w + P->off_citem), P->c_items, P->bo,
+                                        num_sms, st);
+}
+cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st) {
+    const ctp_plan::Class &c = P->classes[ci];
+    return launch_factor_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
+                               reinterpret_cast<const int *>(w + P->off_lists) + c.list_off, c.count, c.G,
+                               c.pmax, P->bo, st);
+}
+cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, cudaStream_t st) {
+    return launch_solve_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
+                              reinterpret_cast<const int *>(w + P->off_sitem), P->s_items, P->bo,
+                              P->tc ? w + P->off_wb : nullptr, P->tc ? w + P->off_lb : nullptr, P->pmax,
+                              st);
+}
+cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st) {
+    if (P->opt.smode == CTP_S_NONE) return cudaSuccess;
+    const BFront *tab = reinterpret_cast<const BFront *>(w + P->off_tab);
+    const int *fitem = reinterpret_cast<const int *>(w + P->off_fitem);
+    if (P->tc)
+        return launch_form_tc_batch(fr, tab, fitem, P->f_items, P->total_rows, w + P->off_wb, w + P->off_lb,
+                                    reinterpret_cast<int32_t *>(w + P->off_ginfo), num_sms, st);
+    return launch_form_fp64_batch(fr, tab, w, fitem, P->f_items, P->bo, st);
+}
+
+}  // namespace ctp

@@ -57,6 +57,69 @@ struct FactorArgs {
 };
 cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// batched path: per-front table (built on the host by the plan, uploaded into
+// the workspace) and the per-front workspace sections
+struct BFront {
+    int64_t n, m;
+    int32_t p, nM;       // nM: 128-row blocks of S (tensor-core Form)
+    int64_t ws;          // byte offset of this front's workspace section
+    int64_t row0;        // first row of this front in the stacked BF16 operand buffers
+    int64_t c0, s0, f0;  // first compression / solve / form work item of this front
+};
+// offsets inside a front's section: info word, compressed matrix (strict),
+// Dinv, and W21 = L21 D11 when an FP64 Form follows
+struct BSection {
+    size_t info, C, Dinv, W21, total;
+};
+__host__ __device__ inline size_t align256hd(size_t x) { return (x + 255) & ~size_t(255); }
+__host__ __device__ inline BSection bsection(int64_t n, int p, const ctp_options *opt) {
+    BSection s;
+    size_t off = 0;
+    s.info = off;
+    off += 256;
+    s.C = off;
+    off += align256hd(opt->pivot == CTP_PIV_STRICT ? sizeof(double) * (size_t)p * p : 0);
+    s.Dinv = off;
+    off += align256hd(sizeof(double) * (2 * (size_t)p + 2));
+    s.W21 = off;
+    off += align256hd((opt->smode != CTP_S_NONE && opt->prec == CTP_FP64) ? sizeof(double) * (size_t)(n - p) * p : 0);
+    s.total = off;
+    return s;
+}
+
+struct BatchOpts {
+    double u, small;
+    int pivot;  // ctp_pivot
+    int smode, prec;
+};
+cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                                const int *list, int count, int G, int pmax, BatchOpts o,
+                                cudaStream_t st);
+cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                                         const int *item_front, int64_t items, BatchOpts o,
+                                         int num_sms, cudaStream_t st);
+cudaError_t launch_solve_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                               const int *item_front, int64_t items, BatchOpts o, void *Wb, void *Lb,
+                               int pmax, cudaStream_t st);
+cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                                   const int *item_front, int64_t items, BatchOpts o,
+                                   cudaStream_t st);
+cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
+                                 int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
+                                 int32_t *info, int num_sms, cudaStream_t st);
+constexpr int kBatchKp = 256;  // K stride of the stacked BF16 operand buffers
+
+// the batched launch sequence (batch.cu); the plan type is declared in ctp.h
+int batch_num_classes(const ctp_plan *P);
+int batch_class_G(const ctp_plan *P, int c);
+size_t batch_total(const ctp_plan *P);
+cudaError_t batch_prepare(const ctp_plan *P, char *w, cudaStream_t st);
+cudaError_t batch_compress(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
+cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st);
+cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, cudaStream_t st);
+cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
+
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,
                               double *W21, int64_t ldw, void *Wb, void *Lb, int Kp,

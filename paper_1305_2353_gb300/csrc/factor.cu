@@ -66,6 +66,8 @@ struct Shared {
     double sInv[2 * kMaxP + 2];
     int cand[kNW];
     int cstar, hiall;
+    int rowmap[kMaxP];  // nonzero outer rows
+    int nz_count;
 };
 
 // Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
@@ -84,19 +86,21 @@ __device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, 
     if (fmax(maxm, maxt) < small) {
         ok = true;
     } else {
-        double ad = fabs(detpiv);
-        double gt = __ddiv_rn(__dmul_rn(__dadd_rn(__dmul_rn(fabs(a_mm), maxt), __dmul_rn(fabs(a_tm), maxm)), detscale), ad);
-        double gm = __ddiv_rn(__dmul_rn(__dadd_rn(__dmul_rn(fabs(a_tm), maxt), __dmul_rn(fabs(a_tt), maxm)), detscale), ad);
-        double iu = __ddiv_rn(1.0, u);
-        ok = (gt <= iu) && (gm <= iu);
+        // |D^-1| (maxt, maxm)^T <= 1/u, each row compared as num*detscale <= |detpiv|/u
+        // (the quotient form of the test, without FP64 divisions)
+        const double lim = __dmul_rn(fabs(detpiv), __drcp_rn(u));
+        const double gt = __dmul_rn(__dadd_rn(__dmul_rn(fabs(a_mm), maxt), __dmul_rn(fabs(a_tm), maxm)), detscale);
+        const double gm = __dmul_rn(__dadd_rn(__dmul_rn(fabs(a_tm), maxt), __dmul_rn(fabs(a_tt), maxm)), detscale);
+        ok = (gt <= lim) && (gm <= lim);
     }
     if (ok) {
+        const double rdet = __ddiv_rn(detscale, detpiv);
         d.d0 = a_tt;
         d.d1 = a_tm;
         d.d2 = a_mm;
-        d.i0 = __ddiv_rn(__dmul_rn(a_mm, detscale), detpiv);
-        d.i1 = __ddiv_rn(__dmul_rn(-a_tm, detscale), detpiv);
-        d.i2 = __ddiv_rn(__dmul_rn(a_tt, detscale), detpiv);
+        d.i0 = __dmul_rn(a_mm, rdet);
+        d.i1 = __dmul_rn(-a_tm, rdet);
+        d.i2 = __dmul_rn(a_tt, rdet);
     }
     return ok;
 }
@@ -201,24 +205,44 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     return d;
 }
 
-__global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
+__device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) double dsm[];
     __shared__ Shared sh;
 
-    const int p = a.p, R = a.R, LD = p + R;
+    const int p = a.p;
     const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // Outer rows: rows of C that are identically zero (a strict C row whose set
+    // J_j is empty, or a relaxed row past the last A21 row) stay zero under the
+    // updates and never change a column maximum, so only the nonzero rows are
+    // kept: R <= min(p, m).  Every CTA builds the same list.
+    if (tid == 0) sh.nz_count = 0;
+    __syncthreads();
+    for (int j = tid; j < a.R; j += kT) {
+        bool nz = false;
+        for (int k = 0; k < p && !nz; k++) nz = a.C[(int64_t)j * p + k] != 0.0;
+        sh.rowmap[j] = nz ? 1 : 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int r = 0;
+        for (int j = 0; j < a.R; j++)
+            if (sh.rowmap[j]) sh.rowmap[r++] = j;
+        sh.nz_count = r;
+    }
+    __syncthreads();
+    const int R = sh.nz_count, LD = p + R;
     const int ncl = (p + G - 1) / G;
     double *cols = dsm;                    // [ncl][LD]
     double *pc0 = dsm + (size_t)ncl * LD;  // pivot column copies
     double *pc1 = pc0 + LD;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nmask = (p + 31) / 32;
     auto colptr = [&](int c) -> const double * {
         return cluster.map_shared_rank(cols, c % G) + (size_t)(c / G) * LD;
     };
 
-    // ---- load: own columns of A11 (full symmetric) and of the outer rows
+    // ---- load: own columns of A11 (full symmetric) and of the nonzero outer rows
     bool nonfinite = false;
     for (int lc = 0; lc < ncl; lc++) {
         const int c = lc * G + rank;
@@ -229,7 +253,7 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
             if (i < p)
                 v = (i >= c) ? a.A[(int64_t)c * a.lda + i] : a.A[(int64_t)i * a.lda + c];
             else
-                v = a.C[(int64_t)(i - p) * p + c];
+                v = a.C[(int64_t)sh.rowmap[i - p] * p + c];
             nonfinite |= !isfinite(v);
             col[i] = v;
         }
@@ -240,6 +264,8 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
 
     const double u = a.u, small = a.small;
     int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, round = 0;
+    int win = 1;                  // candidates tested in the next round
+    const int win_max = kNW * G;  // no CTA owns more than kNW of them
     for (;;) {
         if (nelim >= p) break;
         while (m < p && !sh.live[m]) m++;
@@ -251,21 +277,28 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
         }
         const int buf = round & 1;
         round++;
-        // ---------------- test round: one warp per own live candidate c >= m
+        // ---------------- test round: the first `win` live candidates >= m
+        // (cluster-wide order); each CTA tests the ones it owns, one per warp.
+        // The window is 1 after an acceptance and doubles after a round with no
+        // pass, so accepted-first candidates cost a single test and runs of
+        // rejections are tested in parallel.
         if (tid < nmask) sh.mask[buf][tid] = 0u;
         if (tid == 0) {
-            // the window: the first kNW own live columns >= m
-            int k = 0, hi = p;
-            for (int lc = 0; lc < ncl; lc++) {
-                const int c = lc * G + rank;
-                if (c >= p) break;
-                if (c < m || !sh.live[c]) continue;
-                if (k < kNW) {
-                    sh.cand[k++] = c;
-                } else {
+            // the window ends at the first live column that would exceed `win`
+            // candidates or a CTA's kNW warps; every CTA computes the same end
+            int owned[16];
+            for (int r = 0; r < G; r++) owned[r] = 0;
+            int k = 0, seen = 0, hi = p;
+            for (int c = m; c < p; c++) {
+                if (!sh.live[c]) continue;
+                const int o = c % G;
+                if (seen == win || owned[o] == kNW) {
                     hi = c;
                     break;
                 }
+                seen++;
+                owned[o]++;
+                if (o == rank) sh.cand[k++] = c;
             }
             for (int w = k; w < kNW; w++) sh.cand[w] = -1;
             sh.hi[buf] = hi;
@@ -313,10 +346,12 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
         const int cstar = sh.cstar;
         if (cstar >= sh.hiall) {
             // every tested candidate before the window's end failed: the sweep
-            // continues there
+            // continues there, with a wider window
             m = sh.hiall;
+            win = win * 2 < win_max ? win * 2 : win_max;
             continue;
         }
+        win = 1;
         const Decision dv = sh.cur;
         if (dv.kind == DEC_ZERO) {
             if (tid == 0) {
@@ -500,6 +535,40 @@ __global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) {
     cluster.sync();  // no CTA leaves while its shared memory may still be read
 }
 
+__global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) { factor_cluster_body(a, G); }
+
+// Batched: cluster c factors front list[c]; its arguments come from the
+// front's descriptor and its workspace section.
+__global__ void __launch_bounds__(kT)
+    k_factor_cluster_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
+                           char *ws, const int *__restrict__ list, BatchOpts o, int G) {
+    const int f = list[blockIdx.x / G];
+    const ctp_front fr = fronts[f];
+    const BFront bt = tab[f];
+    ctp_options oo;
+    oo.pivot = o.pivot;
+    oo.smode = o.smode;
+    oo.prec = o.prec;
+    const BSection sec = bsection(bt.n, bt.p, &oo);
+    char *base = ws + bt.ws;
+    FactorArgs a;
+    a.A = fr.A;
+    a.lda = fr.lda;
+    a.p = bt.p;
+    a.R = o.pivot == CTP_PIV_STRICT ? bt.p : 0;
+    a.abs_update = o.pivot == CTP_PIV_STRICT ? 1 : 0;
+    a.C = reinterpret_cast<const double *>(base + sec.C);
+    a.u = o.u;
+    a.small = o.small;
+    a.perm = fr.perm;
+    a.piv = fr.piv;
+    a.nelim = fr.nelim;
+    a.D = fr.D;
+    a.Dinv = reinterpret_cast<double *>(base + sec.Dinv);
+    a.info = reinterpret_cast<int32_t *>(base + sec.info);
+    factor_cluster_body(a, G);
+}
+
 }  // namespace
 
 static size_t factor_smem(int p, int R, int G) {
@@ -544,6 +613,34 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st) {
         G >>= 1;
     }
     return cudaLaunchKernelEx(&cfg, k_factor_cluster, a, G);
+}
+
+cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                                const int *list, int count, int G, int pmax, BatchOpts o,
+                                cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const int R = o.pivot == CTP_PIV_STRICT ? pmax : 0;
+    const size_t smem = factor_smem(pmax, R, G);
+    cudaError_t err = cudaFuncSetAttribute(k_factor_cluster_batch,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    if (G > 8) {
+        err = cudaFuncSetAttribute(k_factor_cluster_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (err != cudaSuccess) return err;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(count * G), 1, 1);
+    cfg.blockDim = dim3(kT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_factor_cluster_batch, fronts, tab, ws, list, o, G);
 }
 
 }  // namespace ctp

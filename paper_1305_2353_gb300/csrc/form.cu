@@ -16,20 +16,17 @@ namespace {
 constexpr int kTile = 64, kK = 16, kTh = 256;
 
 template <typename OutT, bool kPacked>
-__global__ void __launch_bounds__(kTh)
-    k_form_fp64(const double *__restrict__ L21, int64_t ldl, const double *__restrict__ W21,
-                int64_t ldw, int64_t m, const int32_t *__restrict__ nelim_p, OutT *__restrict__ S,
-                int64_t lds) {
+__device__ __forceinline__ void form_tile(const double *__restrict__ L21, int64_t ldl,
+                                          const double *__restrict__ W21, int64_t ldw, int64_t m,
+                                          int e, OutT *__restrict__ S, int64_t lds, int64_t b) {
     __shared__ double sw[kK][kTile + 1];
     __shared__ double sl[kK][kTile + 1];
     // triangular tile index -> (ti, tj), ti >= tj
-    const int64_t b = blockIdx.x;
     int64_t ti = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
     while ((ti + 1) * (ti + 2) / 2 <= b) ti++;
     while (ti * (ti + 1) / 2 > b) ti--;
     const int64_t tj = b - ti * (ti + 1) / 2;
     const int64_t i0 = ti * kTile, j0 = tj * kTile;
-    const int e = *nelim_p;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < e; k0 += kK) {
@@ -68,6 +65,33 @@ __global__ void __launch_bounds__(kTh)
         }
 }
 
+template <typename OutT, bool kPacked>
+__global__ void __launch_bounds__(kTh)
+    k_form_fp64(const double *__restrict__ L21, int64_t ldl, const double *__restrict__ W21,
+                int64_t ldw, int64_t m, const int32_t *__restrict__ nelim_p, OutT *__restrict__ S,
+                int64_t lds) {
+    form_tile<OutT, kPacked>(L21, ldl, W21, ldw, m, *nelim_p, S, lds, blockIdx.x);
+}
+
+// Batched: CTA b takes work item b = (front, triangular 64 x 64 tile of its S).
+template <typename OutT>
+__global__ void __launch_bounds__(kTh)
+    k_form_fp64_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
+                      const int *__restrict__ item_front, BatchOpts o) {
+    const int f = item_front[blockIdx.x];
+    const ctp_front fr = fronts[f];
+    const BFront bt = tab[f];
+    ctp_options oo;
+    oo.pivot = o.pivot;
+    oo.smode = o.smode;
+    oo.prec = o.prec;
+    const BSection sec = bsection(bt.n, bt.p, &oo);
+    const double *W21 = reinterpret_cast<const double *>(ws + bt.ws + sec.W21);
+    form_tile<OutT, true>(fr.A + bt.p, fr.lda, W21, bt.m, bt.m, *fr.nelim, (OutT *)fr.S, fr.lds,
+                          (int64_t)blockIdx.x - bt.f0);
+}
+
+
 }  // namespace
 
 cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
@@ -90,6 +114,22 @@ cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, 
         k_form_fp64<float, true><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
                                                                    (float *)S, lds);
     return cudaGetLastError();
+}
+
+cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                                   const int *item_front, int64_t items, BatchOpts o,
+                                   cudaStream_t st) {
+    if (items == 0) return cudaSuccess;
+    if (o.smode == CTP_S_FP64_PACKED)
+        k_form_fp64_batch<double><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);
+    else
+        k_form_fp64_batch<float><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);
+    return cudaGetLastError();
+}
+
+int64_t form_fp64_tiles(int64_t m) {
+    const int64_t nt = (m + kTile - 1) / kTile;
+    return nt * (nt + 1) / 2;
 }
 
 }  // namespace ctp

@@ -167,21 +167,70 @@ __device__ __forceinline__ void decode_tile(int64_t t, int nM, int &ti, int &tj)
     ti = 2 * lo + (int)(t - tiles_before_col(lo, nM));
 }
 
+// Everything the roles need to know about one tile of work.
+struct TileInfo {
+    int ti, tj, KB, key;  // key: identifies the resident L21 block (front and column block)
+    int64_t arow, brow;   // first rows of the W21 / L21 boxes in the operand buffers
+    int64_t m, nb, lds;
+    float *S;
+    int layout;
+};
+
+struct BatchTab {
+    const ctp_front *fronts;
+    const BFront *tab;
+    const int *item_front;
+};
+
+template <bool kBatch>
+__device__ __forceinline__ TileInfo tile_info(int64_t t, int nM, int KB, int64_t m, float *S,
+                                              int64_t lds, int layout, const BatchTab &bt) {
+    TileInfo x;
+    if (!kBatch) {
+        decode_tile(t, nM, x.ti, x.tj);
+        x.KB = KB;
+        x.key = x.tj;
+        x.arow = (int64_t)x.ti * kBM;
+        x.brow = (int64_t)x.tj * kBN;
+        x.m = m;
+        x.nb = nM;
+        x.S = S;
+        x.lds = lds;
+        x.layout = layout;
+    } else {
+        const int f = bt.item_front[t];
+        const BFront b = bt.tab[f];
+        decode_tile(t - b.f0, b.nM, x.ti, x.tj);
+        const int e = *bt.fronts[f].nelim;
+        x.KB = (e + kBK - 1) / kBK;
+        x.key = f * 65536 + x.tj;
+        x.arow = b.row0 + (int64_t)x.ti * kBM;
+        x.brow = b.row0 + (int64_t)x.tj * kBN;
+        x.m = b.m;
+        x.nb = b.nM;
+        x.S = reinterpret_cast<float *>(bt.fronts[f].S);
+        x.lds = 0;
+        x.layout = 2;
+    }
+    return x;
+}
+
+template <bool kBatch>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_form_tc(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapL,
-              int64_t m, const int32_t *__restrict__ nelim_p, float *__restrict__ S, int64_t lds,
-              int layout, int32_t *__restrict__ info) {
+              int64_t m_single, const int32_t *__restrict__ nelim_p, float *__restrict__ S_single,
+              int64_t lds_single, int layout_single, int32_t *__restrict__ info, int64_t ntiles_batch,
+              BatchTab btab) {
     extern __shared__ unsigned char smraw[];
     __shared__ Bars bars;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     uint8_t *sB = smem;                                 // [kMaxKB][kStageB]: resident L21 block
     uint8_t *sA = smem + (size_t)kMaxKB * kStageB;     // [kStages][kStageA]: W21 ring
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int e = *nelim_p;
-    const int KB = (e + kBK - 1) / kBK;
-    const int nM = (int)((m + kBM - 1) / kBM);
-    const int64_t ntiles = tile_count(nM);
-    const int64_t nb = nM;  // 128 x 128 blocks per block column in the tiled layout
+    const int KB1 = kBatch ? 0 : (*nelim_p + kBK - 1) / kBK;
+    const int nM1 = kBatch ? 0 : (int)((m_single + kBM - 1) / kBM);
+    const int64_t ntiles = kBatch ? ntiles_batch : tile_count(nM1);
+#define TILE(t) tile_info<kBatch>((t), nM1, KB1, m_single, S_single, lds_single, layout_single, btab)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
@@ -213,31 +262,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (warp == 0) {
         // ---------------- TMA producer: the L21 block of the current column block
         // stays resident while consecutive tiles share it; W21 blocks stream
-        if (lane == 0 && KB > 0) {
-            int stage = 0, cur_tj = -1;
+        if (lane == 0) {
+            int stage = 0, cur_key = -1;
             uint32_t phase = 0, bphase = 0;
             for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                int ti, tj;
-                decode_tile(t, nM, ti, tj);
+                const TileInfo x = TILE(t);
+                if (x.KB == 0) continue;
                 bool ok = true;
-                if (tj != cur_tj) {
+                if (x.key != cur_key) {
                     if (!mbar_wait(&bars.bempty, bphase ^ 1u, &bars)) {
                         atomicExch(&bars.abort, 1);
                         break;
                     }
-                    mbar_expect_tx(&bars.bfull, (uint32_t)KB * kStageB);
-                    for (int kb = 0; kb < KB; kb++)
-                        tma_load_2d(sB + (size_t)kb * kStageB, &mapL, kb * kBK, tj * kBN, &bars.bfull);
+                    mbar_expect_tx(&bars.bfull, (uint32_t)x.KB * kStageB);
+                    for (int kb = 0; kb < x.KB; kb++)
+                        tma_load_2d(sB + (size_t)kb * kStageB, &mapL, kb * kBK, (int)x.brow, &bars.bfull);
                     bphase ^= 1u;
-                    cur_tj = tj;
+                    cur_key = x.key;
                 }
-                for (int kb = 0; kb < KB; kb++) {
+                for (int kb = 0; kb < x.KB; kb++) {
                     if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars)) {
                         ok = false;
                         break;
                     }
                     mbar_expect_tx(&bars.full[stage], kStageA);
-                    tma_load_2d(sA + (size_t)stage * kStageA, &mapW, kb * kBK, ti * kBM, &bars.full[stage]);
+                    tma_load_2d(sA + (size_t)stage * kStageA, &mapW, kb * kBK, (int)x.arow, &bars.full[stage]);
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1u;
@@ -252,28 +301,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int stage = 0, acc = 0, cur_tj = -1;
+            int stage = 0, acc = 0, cur_key = -1;
             uint32_t phase = 0, accphase = 0, bphase = 0;
             for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                int ti, tj;
-                decode_tile(t, nM, ti, tj);
+                const TileInfo x = TILE(t);
                 if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars)) {
                     atomicExch(&bars.abort, 1);
                     break;
                 }
                 tc_fence_after();
                 bool ok = true;
-                if (KB > 0 && tj != cur_tj) {
+                if (x.KB > 0 && x.key != cur_key) {
                     if (!mbar_wait(&bars.bfull, bphase, &bars)) {
                         atomicExch(&bars.abort, 1);
                         break;
                     }
                     tc_fence_after();
                     bphase ^= 1u;
-                    cur_tj = tj;
+                    cur_key = x.key;
                 }
                 const uint32_t dt = tmem + (uint32_t)(acc * kBN);
-                for (int kb = 0; kb < KB; kb++) {
+                for (int kb = 0; kb < x.KB; kb++) {
                     if (!mbar_wait(&bars.full[stage], phase, &bars)) {
                         ok = false;
                         break;
@@ -298,12 +346,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     break;
                 }
                 umma_commit(&bars.acc_full[acc]);  // accumulator ready
-                // release the resident L21 block when the next tile needs another
-                if (KB > 0) {
-                    const int64_t tn = t + gridDim.x;
-                    int tin = 0, tjn = -1;
-                    if (tn < ntiles) decode_tile(tn, nM, tin, tjn);
-                    if (tjn != tj) umma_commit(&bars.bempty);
+                // release the resident L21 block when the next tile with work needs another
+                if (x.KB > 0) {
+                    int next_key = -2;
+                    for (int64_t tn = t + gridDim.x; tn < ntiles; tn += gridDim.x) {
+                        const TileInfo y = TILE(tn);
+                        if (y.KB > 0) {
+                            next_key = y.key;
+                            break;
+                        }
+                    }
+                    if (next_key != x.key) umma_commit(&bars.bempty);
                 }
                 if (++acc == 2) {
                     acc = 0;
@@ -318,8 +371,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         int acc = 0;
         uint32_t accphase = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            int ti, tj;
-            decode_tile(t, nM, ti, tj);
+            const TileInfo x = TILE(t);
+            const int ti = x.ti, tj = x.tj, KB = x.KB, layout = x.layout;
+            const int64_t m = x.m, nb = x.nb, lds = x.lds;
+            float *S = x.S;
             if (!mbar_wait(&bars.acc_full[acc], accphase, &bars)) {
                 if (lane == 0) atomicExch(&bars.abort, 1);
                 break;
@@ -396,6 +451,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
         }
     }
+#undef TILE
     __syncthreads();
     if (threadIdx.x == 0 && bars.abort) atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
     if (warp == 0) {
@@ -443,12 +499,34 @@ cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, co
     CUtensorMap mW, mL;
     if (!make_map(&mW, Wb, m, Kp, kBM) || !make_map(&mL, Lb, m, Kp, kBN)) return cudaErrorInvalidValue;
     const size_t smem = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA + 1024;
-    cudaError_t err = cudaFuncSetAttribute(k_form_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_form_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const int nM = (int)((m + kBM - 1) / kBM);
     const int64_t ntiles = tile_count(nM);
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-    k_form_tc<<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, layout, info);
+    BatchTab none = {nullptr, nullptr, nullptr};
+    k_form_tc<false><<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, layout, info, 0, none);
+    return cudaGetLastError();
+}
+
+int64_t form_tc_tiles(int64_t m) { return m > 0 ? tile_count((m + kBM - 1) / kBM) : 0; }
+
+cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
+                                 int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
+                                 int32_t *info, int num_sms, cudaStream_t st) {
+    if (items == 0) return cudaSuccess;
+    if ((((uintptr_t)Wb) | ((uintptr_t)Lb)) & 15) return cudaErrorMisalignedAddress;
+    CUtensorMap mW, mL;
+    if (!make_map(&mW, Wb, total_rows, kBatchKp, kBM) || !make_map(&mL, Lb, total_rows, kBatchKp, kBN))
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA + 1024;
+    cudaError_t err =
+        cudaFuncSetAttribute(k_form_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int grid = (int)(items < num_sms ? items : num_sms);
+    BatchTab bt = {fronts, tab, item_front};
+    k_form_tc<true><<<grid, kThreadsTC, smem, st>>>(mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt);
     return cudaGetLastError();
 }
 

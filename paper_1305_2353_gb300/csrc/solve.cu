@@ -27,20 +27,22 @@ constexpr int kWarps = 8;   // warps per CTA: warp w updates the columns k = w (
 // position j, every warp reads y_j of its lane's row and updates its share of
 // the later columns; a CTA barrier separates consecutive pivots.  Eight warps
 // per CTA (and three CTAs per SM) keep all four FP64 pipes of an SM busy.
-__global__ void __launch_bounds__(kRows * kWarps)
-    k_solve_fp64(double *__restrict__ A, int64_t n, int p, int64_t lda,
-                 const int32_t *__restrict__ perm, const int32_t *__restrict__ piv,
-                 const double *__restrict__ Dinv, const int32_t *__restrict__ nelim_p,
-                 double *__restrict__ W21, int64_t ldw, __nv_bfloat16 *__restrict__ Wb,
-                 __nv_bfloat16 *__restrict__ Lb, int Kp) {
-    extern __shared__ __align__(16) double xs[];  // [p][kRows+1]
+// One 32-row tile.  brow0: row of this front's first A21 row in the BF16
+// operand copies (0 for a single supernode; the stacked offset in a batch).
+__device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, int p, int64_t lda,
+                                           const int32_t *__restrict__ perm,
+                                           const int32_t *__restrict__ piv,
+                                           const double *__restrict__ Dinv, int e,
+                                           double *__restrict__ W21, int64_t ldw,
+                                           __nv_bfloat16 *__restrict__ Wb,
+                                           __nv_bfloat16 *__restrict__ Lb, int Kp, int64_t brow0,
+                                           int64_t tile, double *xs) {
     constexpr int LDX = kRows + 1;
     const int64_t m = n - p;
-    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int64_t row0 = tile * kRows;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t row = row0 + lane;
     const bool valid = row < m;
-    const int e = *nelim_p;
     double *A21 = A + p;
 
     // gather x = A21(rows, perm): each warp reads 32 consecutive rows of a column
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(kRows * kWarps)
         for (int rr = w; rr < kRows; rr += kWarps) {
             const int64_t rw = row0 + rr;
             if (rw >= m) break;
-            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Wb + rw * Kp);
+            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Wb + (brow0 + rw) * Kp);
             for (int k2 = lane; k2 < Kp / 2; k2 += 32) {
                 const int k = 2 * k2;
                 const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kRows * kWarps)
         for (int rr = w; rr < kRows; rr += kWarps) {
             const int64_t rw = row0 + rr;
             if (rw >= m) break;
-            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Lb + rw * Kp);
+            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Lb + (brow0 + rw) * Kp);
             for (int k2 = lane; k2 < Kp / 2; k2 += 32) {
                 const int k = 2 * k2;
                 const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
@@ -140,6 +142,38 @@ __global__ void __launch_bounds__(kRows * kWarps)
         }
     }
 }
+
+__global__ void __launch_bounds__(kRows * kWarps)
+    k_solve_fp64(double *__restrict__ A, int64_t n, int p, int64_t lda,
+                 const int32_t *__restrict__ perm, const int32_t *__restrict__ piv,
+                 const double *__restrict__ Dinv, const int32_t *__restrict__ nelim_p,
+                 double *__restrict__ W21, int64_t ldw, __nv_bfloat16 *__restrict__ Wb,
+                 __nv_bfloat16 *__restrict__ Lb, int Kp) {
+    extern __shared__ __align__(16) double xs[];  // [p][kRows+1]
+    solve_tile(A, n, p, lda, perm, piv, Dinv, *nelim_p, W21, ldw, Wb, Lb, Kp, 0, blockIdx.x, xs);
+}
+
+// Batched: CTA b takes work item b = (front, 32-row tile of its A21).
+__global__ void __launch_bounds__(kRows * kWarps)
+    k_solve_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
+                  const int *__restrict__ item_front, BatchOpts o, __nv_bfloat16 *__restrict__ Wb,
+                  __nv_bfloat16 *__restrict__ Lb) {
+    extern __shared__ __align__(16) double xs[];
+    const int f = item_front[blockIdx.x];
+    const ctp_front fr = fronts[f];
+    const BFront bt = tab[f];
+    ctp_options oo;
+    oo.pivot = o.pivot;
+    oo.smode = o.smode;
+    oo.prec = o.prec;
+    const BSection sec = bsection(bt.n, bt.p, &oo);
+    char *base = ws + bt.ws;
+    const bool w64 = o.smode != CTP_S_NONE && o.prec == CTP_FP64;
+    solve_tile(fr.A, bt.n, bt.p, fr.lda, fr.perm, fr.piv, reinterpret_cast<const double *>(base + sec.Dinv),
+               *fr.nelim, w64 ? reinterpret_cast<double *>(base + sec.W21) : nullptr, bt.m, Wb, Lb,
+               kBatchKp, bt.row0, (int64_t)blockIdx.x - bt.s0, xs);
+}
+
 
 }  // namespace
 
@@ -158,5 +192,20 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
         A, n, p, lda, perm, piv, Dinv, nelim, W21, ldw, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb, Kp);
     return cudaGetLastError();
 }
+
+cudaError_t launch_solve_batch(const ctp_front *fronts, const BFront *tab, char *ws,
+                               const int *item_front, int64_t items, BatchOpts o, void *Wb, void *Lb,
+                               int pmax, cudaStream_t st) {
+    if (items == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * (size_t)pmax * (kRows + 1);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_solve_batch<<<(unsigned)items, kRows * kWarps, smem, st>>>(
+        fronts, tab, ws, item_front, o, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb);
+    return cudaGetLastError();
+}
+
+int solve_rows_per_tile() { return kRows; }
 
 }  // namespace ctp

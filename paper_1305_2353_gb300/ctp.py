@@ -29,7 +29,9 @@ SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4, "f
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
 
 EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_compress_strict",
-           "ctp_compress_strict_noalloc", "ctp_compress_relaxed", "ctp_factor_supernode", "ctp_read_info", "ctp_profile_begin", "ctp_profile_end"]
+           "ctp_compress_strict_noalloc", "ctp_compress_relaxed", "ctp_factor_supernode",
+           "ctp_read_info", "ctp_profile_begin", "ctp_profile_end", "ctp_batch_plan_create",
+           "ctp_batch_plan_destroy", "ctp_batch_upload", "ctp_factor_batch", "ctp_batch_read_info"]
 
 
 class Options(ctypes.Structure):
@@ -39,6 +41,14 @@ class Options(ctypes.Structure):
 
 def options(u=0.01, small=1e-20, pivot="strict", prec="fp64", smode="none"):
     return Options(u, small, PIVOT[pivot], PREC[prec], SMODE[smode], 0)
+
+
+class Front(ctypes.Structure):
+    """Mirror of ctp_front (device-visible descriptor of one front)."""
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("perm", ctypes.c_void_p),
+                ("piv", ctypes.c_void_p), ("D", ctypes.c_void_p), ("nelim", ctypes.c_void_p),
+                ("S", ctypes.c_void_p), ("lds", ctypes.c_int64)]
 
 
 class CtpError(RuntimeError):
@@ -70,6 +80,12 @@ def load(path: str = LIB_PATH):
     L.ctp_factor_supernode.argtypes = [P, i64, i32, P, i64, ctypes.POINTER(Options), P, P, P, P, P,
                                        i64, P, sz, P]
     L.ctp_read_info.argtypes = [P, P, ctypes.POINTER(i32), P]
+    L.ctp_batch_plan_create.argtypes = [P, i32, P, P, ctypes.POINTER(Options), ctypes.POINTER(P),
+                                        ctypes.POINTER(sz)]
+    L.ctp_batch_plan_destroy.argtypes = [P]
+    L.ctp_batch_upload.argtypes = [P, P, P, sz, P]
+    L.ctp_factor_batch.argtypes = [P, P, P, P, sz, P]
+    L.ctp_batch_read_info.argtypes = [P, P, P, P, P]
     L.ctp_profile_begin.argtypes = [P]
     L.ctp_profile_end.argtypes = [P, i32, P, P, P, ctypes.POINTER(i32)]
     for f in EXPORTS[1:]:
@@ -276,3 +292,101 @@ class Supernode:
                 out["S"] = to_numpy(self.S)
         out["info"] = self.ctx.read_info(self.ws)
         return out
+
+
+class Batch:
+    """Device buffers and plan for the batched factorization of many fronts.
+    All fronts live in a few pooled tensors; the descriptor array is built on
+    the host and copied to the device once."""
+
+    def __init__(self, ctx: Context, A_list, p_list, opt):
+        import torch
+        self.ctx, self.opt = ctx, opt
+        dev = f"cuda:{ctx.device}"
+        self.nb = len(A_list)
+        self.n = np.array([a.shape[0] for a in A_list], np.int64)
+        self.p = np.array(p_list, np.int32)
+        m = self.n - self.p
+        a_off = np.concatenate([[0], np.cumsum(self.n * self.p)])
+        p_off = np.concatenate([[0], np.cumsum(self.p)])
+        if opt.smode in (3, 4):
+            s_len = m * (m + 1) // 2
+        elif opt.smode == 5:
+            nbk = (m + 127) // 128
+            s_len = nbk * (nbk + 1) // 2 * 16384
+        else:
+            s_len = np.zeros(self.nb, np.int64)
+        s_off = np.concatenate([[0], np.cumsum(s_len)])
+        host = np.empty(int(a_off[-1]), np.float64)
+        for k, a in enumerate(A_list):
+            host[a_off[k]:a_off[k + 1]] = np.asarray(a, np.float64).ravel(order="F")
+        self.A = torch.from_numpy(host).to(dev)
+        self.perm = torch.empty(int(p_off[-1]), dtype=torch.int32, device=dev)
+        self.piv = torch.empty(int(p_off[-1]), dtype=torch.int32, device=dev)
+        self.D = torch.empty(2 * int(p_off[-1]), dtype=torch.float64, device=dev)
+        self.nelim = torch.empty(self.nb, dtype=torch.int32, device=dev)
+        sdt = torch.float64 if opt.smode == 3 else torch.float32
+        self.S = torch.zeros(max(int(s_off[-1]), 1), dtype=sdt, device=dev) if opt.smode else None
+        self.a_off, self.p_off, self.s_off = a_off, p_off, s_off
+        fr = (Front * self.nb)()
+        base = self.A.data_ptr()
+        for k in range(self.nb):
+            fr[k].n, fr[k].p = int(self.n[k]), int(self.p[k])
+            fr[k].A = base + 8 * int(a_off[k])
+            fr[k].lda = int(self.n[k])
+            fr[k].perm = self.perm.data_ptr() + 4 * int(p_off[k])
+            fr[k].piv = self.piv.data_ptr() + 4 * int(p_off[k])
+            fr[k].D = self.D.data_ptr() + 8 * 2 * int(p_off[k])
+            fr[k].nelim = self.nelim.data_ptr() + 4 * k
+            fr[k].S = (self.S.data_ptr() + self.S.element_size() * int(s_off[k])) if self.S is not None else None
+            fr[k].lds = max(int(m[k]), 1)
+        raw = np.frombuffer(bytes(fr), dtype=np.uint8)
+        self.fronts = torch.from_numpy(raw.copy()).to(dev)
+        plan = ctypes.c_void_p()
+        wsb = ctypes.c_size_t()
+        _check("ctp_batch_plan_create",
+               ctx.lib.ctp_batch_plan_create(ctx.handle, self.nb, self.n.ctypes.data_as(ctypes.c_void_p),
+                                             self.p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt),
+                                             ctypes.byref(plan), ctypes.byref(wsb)))
+        self.plan = plan
+        self.ws = torch.empty(max(int(wsb.value), 256), dtype=torch.uint8, device=dev)
+        _check("ctp_batch_upload", ctx.lib.ctp_batch_upload(ctx.handle, self.plan, _ptr(self.ws),
+                                                             self.ws.numel(), _stream(None)))
+        self.A0 = self.A.clone()
+
+    def reset(self):
+        self.A.copy_(self.A0)
+
+    def run(self, stream=None):
+        _check("ctp_factor_batch", self.ctx.lib.ctp_factor_batch(
+            self.ctx.handle, self.plan, _ptr(self.fronts), _ptr(self.ws), self.ws.numel(),
+            _stream(stream)))
+
+    def flags(self, stream=None):
+        out = np.zeros(self.nb, np.int32)
+        _check("ctp_batch_read_info", self.ctx.lib.ctp_batch_read_info(
+            self.ctx.handle, self.plan, _ptr(self.ws), out.ctypes.data_as(ctypes.c_void_p),
+            _stream(stream)))
+        return out
+
+    def result(self, k):
+        n, p = int(self.n[k]), int(self.p[k])
+        A = self.A[int(self.a_off[k]):int(self.a_off[k + 1])].cpu().numpy().reshape(p, n).T.copy()
+        pv = slice(int(self.p_off[k]), int(self.p_off[k + 1]))
+        out = dict(A=A, perm=self.perm[pv].cpu().numpy(), piv=self.piv[pv].cpu().numpy(),
+                   D=self.D[2 * pv.start:2 * pv.stop].cpu().numpy(),
+                   nelim=int(self.nelim[k].cpu()), info=0)
+        if self.S is not None:
+            seg = self.S[int(self.s_off[k]):int(self.s_off[k + 1])].cpu().numpy()
+            m = n - p
+            out["S"] = unpack_tiled(seg, m) if self.opt.smode == 5 else unpack_lower(seg, m)
+        return out
+
+    def __del__(self):
+        try:
+            if self.plan:
+                self.ctx.lib.ctp_batch_plan_destroy(self.plan)
+                self.plan = None
+        except Exception:
+            pass
+

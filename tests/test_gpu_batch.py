@@ -1,0 +1,95 @@
+"""The batched path (many fronts in a few launches) against the oracle, front
+by front, with the same bars as the single-supernode parity tests."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1305_2353_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from test_gpu_supernode import compare, min_margin, _bf16_bound  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1305_2353_gb300 import build, ctp
+    build.build()
+    return ctp.Context(0)
+
+
+def _fronts(count, seed, pmax=256):
+    shapes = inputs.batch_shapes(count, seed=seed, pmax=pmax)
+    fr = [inputs.supernode(int(n), int(p), seed=seed * 7919 + k, zero_diag_frac=0.02)
+          for k, (n, p) in enumerate(shapes)]
+    # edge cases: a 1x1 front, a front without A21 rows, the widest front
+    fr += [inputs.supernode(1, 1, seed=5), inputs.supernode(40, 40, seed=6),
+           inputs.supernode(700, 256, seed=7, zero_diag_frac=0.02)]
+    return fr
+
+
+@pytest.mark.parametrize("pivot", ["strict", "restricted"])
+def test_batch_factor_matches_oracle(ctx, pivot):
+    from paper_1305_2353_gb300 import ctp
+    fr = _fronts(60, seed=3)
+    b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr], ctp.options(pivot=pivot))
+    b.run()
+    torch.cuda.synchronize()
+    assert np.all(b.flags() == 0)
+    for k, A in enumerate(fr):
+        p = A.shape[1]
+        ref = O.factor(A, p, pivot, log_cap=200000)
+        compare(ref, b.result(k), p, A)
+
+
+def test_batch_graph_replay(ctx):
+    """The batch call only launches kernels: capture it once, replay it."""
+    from paper_1305_2353_gb300 import ctp
+    fr = _fronts(30, seed=4)
+    b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr], ctp.options(pivot="strict", smode="fp64_packed"))
+    s = torch.cuda.Stream()
+    b.run()  # warm-up outside the capture (kernel attributes are set once)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(stream=s)
+    for _ in range(2):
+        b.reset()
+        g.replay()
+    torch.cuda.synchronize()
+    for k, A in enumerate(fr):
+        p = A.shape[1]
+        ref = O.factor(A, p, "strict")
+        got = b.result(k)
+        compare(ref, got, p, A)
+        e = ref["nelim"]
+        S = O.form(ref["A"][p:, :e], ref["piv"][:e], ref["D"])
+        if S.size:
+            assert np.allclose(got["S"], np.tril(S), rtol=1e-11, atol=1e-11 * max(np.abs(S).max(), 1))
+
+
+def test_batch_tensor_core_form(ctx):
+    from paper_1305_2353_gb300 import ctp
+    fr = _fronts(40, seed=5)
+    b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr],
+                  ctp.options(pivot="strict", prec="bf16", smode="fp32_tiled"))
+    b.run()
+    torch.cuda.synchronize()
+    assert np.all(b.flags() == 0)
+    for k, A in enumerate(fr):
+        p = A.shape[1]
+        ref = O.factor(A, p, "strict")
+        got = b.result(k)
+        compare(ref, got, p, A)
+        e = ref["nelim"]
+        L21 = ref["A"][p:, :e]
+        _, Dm, _ = O.unpack(ref, p)
+        S = O.form(L21, ref["piv"][:e], ref["D"])
+        if S.size == 0:
+            continue
+        bound = _bf16_bound(L21 @ Dm, L21)
+        lo = np.tril(np.ones_like(S, dtype=bool))
+        assert np.all(np.abs(got["S"] - S)[lo] <= 2.0 ** -7 * bound[lo] + 1e-30)
