@@ -92,3 +92,28 @@ def symmetric(n, seed=0, dist="normal"):
 def rhs(n, k=1, seed=0):
     rng = np.random.default_rng(seed)
     return np.asfortranarray(rng.standard_normal((n, k)))
+
+
+def two_node(A, seed=0):
+    """The symmetric matrix M = [[A11, A21^T], [A21, A22]] of order n in which an
+    n x p supernode A is the first block column; A22 is symmetric with N(0,1)
+    entries drawn from ``seed``.  Full storage, column-major."""
+    A = np.asarray(A, dtype=np.float64)
+    n, p = A.shape
+    rng = np.random.default_rng(seed + 7_919)
+    A22 = rng.standard_normal((n - p, n - p))
+    A22 = np.tril(A22) + np.tril(A22, -1).T
+    M = np.zeros((n, n), order="F")
+    A11 = np.tril(A[:p, :p]) + np.tril(A[:p, :p], -1).T
+    M[:p, :p] = A11
+    M[p:, :p] = A[p:, :]
+    M[:p, p:] = A[p:, :].T
+    M[p:, p:] = A22
+    return M
+
+
+def dense_symmetric(N, seed=0, dist="normal"):
+    """A dense symmetric N x N matrix with N(0,1) (or U[-1,1]) entries."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, N)) if dist == "normal" else rng.uniform(-1.0, 1.0, (N, N))
+    return np.asfortranarray(np.tril(X) + np.tril(X, -1).T)
