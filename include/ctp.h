@@ -53,8 +53,8 @@ typedef enum {
     CTP_PIV_STRICT = 0,     /* strict compressed pivoting, Section 4.1 (eq. (4.1), eq. (4.3)) */
     CTP_PIV_RELAXED = 1,    /* relaxed compressed pivoting, Section 4.2 */
     CTP_PIV_TPP = 2,        /* threshold partial pivoting on all n rows, Listing 1 (Section 2);
-                               the comparator of the compressed strategies (smode must be
-                               CTP_S_NONE) */
+                               the comparator of the compressed strategies (FP64 only;
+                               any smode but CTP_S_FP32_TILED) */
     CTP_PIV_RESTRICTED = 3  /* restricted pivoting: tests look at A11 only, Section 3.2 */
 } ctp_pivot;
 
@@ -62,9 +62,15 @@ typedef enum {
  * inversions, D11 and the Solve are always FP64. */
 typedef enum {
     CTP_FP64 = 0,  /* FP64 throughout */
-    CTP_BF16 = 1   /* Form on the tensor cores: BF16 operands, FP32 accumulation and
-                      FP32 S (requires smode CTP_S_FP32, CTP_S_FP32_PACKED or
-                      CTP_S_FP32_TILED) */
+    CTP_BF16 = 1,  /* Form on the tensor cores: BF16 operands, FP32 accumulation and
+                      FP32 S (requires smode CTP_S_FP32, CTP_S_FP32_PACKED,
+                      CTP_S_FP32_TILED or CTP_S_FP64_SUB); products carry the
+                      BF16 rounding of L21 and W21 (relative 2^-8) */
+    CTP_BF16X3 = 2 /* as CTP_BF16, with each operand split into hi = bf16(x) and
+                      lo = bf16(x - hi) and the three products hi*hi + hi*lo + lo*hi
+                      accumulated in FP32 (Henry, Tang & Heinecke, 2019): products
+                      close to FP32 accuracy at the same bytes of S; the accuracy
+                      FP64 iterative refinement needs to converge */
 } ctp_prec;
 
 /* Storage of the Schur complement S (its lower triangle only):
@@ -88,7 +94,8 @@ typedef enum {
     CTP_S_FP32 = 2,
     CTP_S_FP64_PACKED = 3,
     CTP_S_FP32_PACKED = 4,
-    CTP_S_FP32_TILED = 5
+    CTP_S_FP32_TILED = 5,
+    CTP_S_FP64_SUB = 6
 } ctp_smode;
 
 /* Per-position pivot kinds written to piv[] (CTP_S_* above). */
@@ -248,6 +255,95 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
  * condition per front. */
 ctp_status ctp_batch_read_info(ctp_ctx *ctx, const ctp_plan *plan, const void *workspace,
                                int32_t *flags_host, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Complete systems: solve, backward error and iterative refinement (Section 7).
+ *
+ * A factored system is a list of fronts in elimination order (children before
+ * parents).  Front f covers n rows of the system, named by the variable indices
+ * rows[0..n): rows[0..p) are its p fully-summed variables in the order they had
+ * when the front was factored, rows[p..n) the variables of the rows below.
+ * L (leading dimension ldl), perm, piv, D and nelim are ctp_factor_supernode's
+ * in-place outputs for that front.  All pointers are device pointers.  The
+ * fronts together give P M P^T = L D L^T for the system matrix M of order N
+ * (eq. (1.2) applied front by front; a front's delayed variables are
+ * eliminated by a later front). */
+typedef struct {
+    int64_t n;
+    int32_t p;
+    int32_t reserved;
+    const double *L;
+    int64_t ldl;
+    const int32_t *perm;
+    const int32_t *piv;
+    const double *D;
+    const int32_t *nelim;
+    const int32_t *rows;
+} ctp_sfront;
+
+/* Workspace of ctp_solve for fronts of at most nmax rows and nrhs right-hand sides. */
+ctp_status ctp_solve_workspace_size(int64_t nmax, int32_t nrhs, size_t *bytes);
+
+/* X <- M^{-1} X in place (N x nrhs, column-major, ldx >= N) with the factors in
+ * fronts[0..nf) (a HOST array of descriptors): forward substitution with the
+ * unit lower factors, the block-diagonal solve with D (1x1 and 2x2 blocks; a
+ * zero pivot gives a zero component) and back substitution, front by front.
+ * Kernel launches only; nothing is synchronised. */
+ctp_status ctp_solve(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N, int32_t nrhs,
+                     double *X, int64_t ldx, void *workspace, size_t ws_bytes, void *stream);
+
+/* Workspace of ctp_backward_error and ctp_refine (systems of order N, fronts
+ * of at most nmax rows, nrhs right-hand sides). */
+ctp_status ctp_refine_workspace_size(int64_t N, int64_t nmax, int32_t nrhs, size_t *bytes);
+
+/* Scaled backward error of Section 7 per right-hand side, in FP64 on the device:
+ *   berr[r] = ||M x_r - b_r||_inf / (||M||_inf ||x_r||_inf + ||b_r||_inf).
+ * M: symmetric, lower triangle stored column-major (ldm >= N; the strict upper
+ * triangle is not read).  berr: device array of nrhs doubles. */
+ctp_status ctp_backward_error(ctp_ctx *ctx, int64_t N, const double *M, int64_t ldm, int32_t nrhs,
+                              const double *B, int64_t ldb, const double *X, int64_t ldx,
+                              double *berr, void *workspace, size_t ws_bytes, void *stream);
+
+/* Solve M X = B by the factors in fronts[0..nf) with iterative refinement
+ * (Section 7: FP64 residuals, at most max_steps corrections, max_steps <= 100):
+ *   X = solve(B);  while max_r berr_r > tol and fewer than max_steps
+ *   corrections were made:  X += solve(B - M X).
+ * M (lower triangle, as in ctp_backward_error) is the matrix before
+ * factorization; the factors may be those of a perturbed M (a low-precision
+ * Form), refinement then converges to the solution of M.  berr_host (host,
+ * capacity (max_steps+1)*nrhs) receives the backward error of every iterate,
+ * *steps_host the corrections made.  Synchronises `stream` once per iterate. */
+ctp_status ctp_refine(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
+                      const double *M, int64_t ldm, int32_t nrhs, const double *B, int64_t ldb,
+                      double *X, int64_t ldx, int32_t max_steps, double tol, double *berr_host,
+                      int32_t *steps_host, void *workspace, size_t ws_bytes, void *stream);
+
+typedef struct ctp_chain ctp_chain;
+
+/* Factor a dense symmetric matrix M (order N, lower triangle, column-major,
+ * ldm >= N) in place as a chain of fronts.  The first front takes the leading
+ * p_first columns and all N rows -- the supernode [A11; A21] of Section 1 --
+ * with opt_first; every later one takes the leading min(w_rest, rows left)
+ * columns of the current Schur complement, which begin with the columns the
+ * previous front delayed, with opt_rest.  Each front is factored by
+ * ctp_factor_supernode; its Form subtracts L21 D11 L21^T from the trailing
+ * lower triangle in place (CTP_S_FP64_SUB; opt->prec picks the FP64 or the
+ * tensor-core Form; opt->smode is ignored).  A compressed or restricted front
+ * that eliminates nothing is factored again with CTP_PIV_TPP (FP64).
+ * Returns CTP_ECAPACITY if a front with rows below still eliminates nothing or
+ * columns stay delayed with no rows below, or the first device-side condition
+ * (CTP_ENONFINITE, CTP_ETIMEOUT).  Synchronises `stream` once per front (its
+ * nelim and perm shape the next front).  *chain receives the factors (device
+ * memory owned by the chain; M holds L and D); release with ctp_chain_destroy. */
+ctp_status ctp_factor_dense(ctp_ctx *ctx, int64_t N, double *M, int64_t ldm, int32_t p_first,
+                            const ctp_options *opt_first, int32_t w_rest,
+                            const ctp_options *opt_rest, ctp_chain **chain, void *stream);
+/* The chain's fronts (a host array valid until ctp_chain_destroy). */
+ctp_status ctp_chain_fronts(const ctp_chain *chain, int32_t *nf, const ctp_sfront **fronts);
+/* Per front (up to cap): nelim, columns taken and the pivoting actually used. */
+ctp_status ctp_chain_info(const ctp_chain *chain, int32_t cap, int32_t *nelim, int32_t *p,
+                          int32_t *pivot);
+ctp_status ctp_chain_destroy(ctp_chain *chain);
 
 /* Optional per-kernel timing.  Between ctp_profile_begin() and ctp_profile_end()
  * every kernel this library launches is bracketed by two CUDA events recorded

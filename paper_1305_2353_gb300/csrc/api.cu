@@ -3,6 +3,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "ctp_internal.cuh"
 
 namespace {
@@ -10,14 +12,16 @@ constexpr int kMaxRec = 4096;
 enum KernelId {
     K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP,
     K_B_PREPARE, K_B_COMPRESS, K_B_FACTOR_G1, K_B_FACTOR_G2, K_B_FACTOR_G4, K_B_FACTOR_G8,
-    K_B_FACTOR_G16, K_B_SOLVE, K_B_FORM, K_NUM_IDS
+    K_B_FACTOR_G16, K_B_SOLVE, K_B_FORM, K_W21, K_SYS_FWD, K_SYS_BWD, K_SYMV, K_BERR, K_AXPY,
+    K_NUM_IDS
 };
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
                                        "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16",
                                        "tpp_full_column", "batch_prepare", "batch_compress_strict",
                                        "batch_factor_g1", "batch_factor_g2", "batch_factor_g4",
                                        "batch_factor_g8", "batch_factor_g16", "batch_solve_fp64",
-                                       "batch_form"};
+                                       "batch_form", "w21_from_l", "sys_forward", "sys_backward",
+                                       "symv_residual", "backward_error", "axpy"};
 }  // namespace
 
 struct ctp_ctx {
@@ -56,10 +60,11 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     off += align256(compressed ? sizeof(double) * (size_t)p * p : 0);
     L.Dinv = off;
     off += align256(sizeof(double) * (2 * (size_t)p + 2));
-    const bool tc = opt->prec == CTP_BF16 && opt->smode != CTP_S_NONE;
+    const bool tc = opt->prec != CTP_FP64 && opt->smode != CTP_S_NONE;
     L.W21 = off;
     off += align256(opt->smode != CTP_S_NONE && !tc ? sizeof(double) * (size_t)m * p : 0);
-    const size_t nb = tc ? 2 * (size_t)m * form_tc_kpad(p) : 0;
+    // BF16 operand copies (hi, and for the split form the lo parts after them)
+    const size_t nb = tc ? 2 * (size_t)m * form_tc_kpad(p) * (opt->prec == CTP_BF16X3 ? 2 : 1) : 0;
     L.Wb = off;
     off += align256(nb);
     L.Lb = off;
@@ -115,8 +120,8 @@ static ctp_status check_opts(const ctp_options *opt) {
     if (!(opt->u > 0.0) || opt->u > 0.5) return CTP_EINVAL;
     if (!(opt->small >= 0.0)) return CTP_EINVAL;
     if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
-    if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16) return CTP_EINVAL;
-    if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP32_TILED) return CTP_EINVAL;
+    if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16 && opt->prec != CTP_BF16X3) return CTP_EINVAL;
+    if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP64_SUB) return CTP_EINVAL;
     return CTP_OK;
 }
 
@@ -186,11 +191,11 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     if (opt->smode != CTP_S_NONE && (S == nullptr || (!packed && lds < (m > 0 ? m : 1))))
         return CTP_EINVAL;
     if (p > kMaxP) return CTP_EUNSUPPORTED;
-    if (opt->pivot == CTP_PIV_TPP && opt->smode != CTP_S_NONE) return CTP_EUNSUPPORTED;
-    const bool tc = opt->prec == CTP_BF16 && opt->smode != CTP_S_NONE;
+    const bool tc = opt->prec != CTP_FP64 && opt->smode != CTP_S_NONE;
+    if (opt->pivot == CTP_PIV_TPP && tc) return CTP_EUNSUPPORTED;
     if (tc && opt->smode != CTP_S_FP32 && opt->smode != CTP_S_FP32_PACKED &&
-        opt->smode != CTP_S_FP32_TILED)
-        return CTP_EUNSUPPORTED;  // the tensor-core Form writes FP32
+        opt->smode != CTP_S_FP32_TILED && opt->smode != CTP_S_FP64_SUB)
+        return CTP_EUNSUPPORTED;  // the tensor-core Form writes FP32 (or subtracts into FP64)
     if (!tc && opt->smode == CTP_S_FP32_TILED) return CTP_EUNSUPPORTED;
     WsLayout L = ws_layout(n, p, opt, ctx->num_sms);
     if (ws_bytes < L.total) return CTP_ENOMEM;
@@ -203,6 +208,7 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     void *Wb = tc ? (void *)(ws + L.Wb) : nullptr;
     void *Lbf = tc ? (void *)(ws + L.Lb) : nullptr;
     const int Kp = form_tc_kpad(p);
+    const int64_t lo_off = (tc && opt->prec == CTP_BF16X3) ? m * Kp : 0;
     CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
 
     if (opt->pivot == CTP_PIV_TPP) {
@@ -211,6 +217,14 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
             return launch_tpp(A, n, p, lda, opt->u, opt->small, ws + L.aux, perm, piv, D, Dinv, nelim,
                               info, ctx->num_sms, st);
         }));
+        if (opt->smode != CTP_S_NONE && m > 0) {
+            CTP_CUDA(timed(ctx, K_W21, st, [&] {
+                return launch_w21_from_l(A, lda, p, m, piv, D, nelim, W21, m, st);
+            }));
+            CTP_CUDA(timed(ctx, K_FORM, st, [&] {
+                return launch_form_fp64(A + p, lda, W21, m, m, nelim, S, lds, opt->smode, st);
+            }));
+        }
         return CTP_OK;
     }
     FactorArgs fa;
@@ -251,13 +265,14 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     CTP_CUDA(timed(ctx, K_FACTOR, st, [&] { return launch_factor_cluster(fa, st); }));
     if (m > 0)
         CTP_CUDA(timed(ctx, K_SOLVE, st, [&] {
-            return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, Wb, Lbf, Kp, st);
+            return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, Wb, Lbf, Kp, lo_off, st);
         }));
     if (opt->smode != CTP_S_NONE && m > 0) {
         if (tc)
             CTP_CUDA(timed(ctx, K_FORM_TC, st, [&] {
-                return launch_form_tc(Wb, Lbf, m, Kp, nelim, (float *)S, lds,
-                                      opt->smode == CTP_S_FP32_TILED ? 2 : (packed ? 1 : 0), info,
+                return launch_form_tc(Wb, Lbf, lo_off, m, Kp, nelim, (float *)S, lds,
+                                      opt->smode == CTP_S_FP64_SUB ? 3
+                                      : opt->smode == CTP_S_FP32_TILED ? 2 : (packed ? 1 : 0), info,
                                       ctx->num_sms, st);
             }));
         else
@@ -335,6 +350,329 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
     }
     CTP_CUDA(timed(ctx, K_B_SOLVE, st, [&] { return batch_solve(plan, fronts, w, st); }));
     CTP_CUDA(timed(ctx, K_B_FORM, st, [&] { return batch_form(plan, fronts, w, ctx->num_sms, st); }));
+    return CTP_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Complete systems                                                         */
+
+ctp_status ctp_solve_workspace_size(int64_t nmax, int32_t nrhs, size_t *bytes) {
+    if (bytes == nullptr || nmax < 0 || nrhs < 1) return CTP_EINVAL;
+    *bytes = sys_solve_ws_bytes(nmax, nrhs);
+    return CTP_OK;
+}
+
+static ctp_status check_fronts(int32_t nf, const ctp_sfront *fronts, int64_t N, int64_t ws_nmax_cap) {
+    if (nf < 0 || (nf > 0 && fronts == nullptr)) return CTP_EINVAL;
+    for (int32_t k = 0; k < nf; k++) {
+        const ctp_sfront &f = fronts[k];
+        if (f.p < 1 || f.p > kMaxP || f.n < f.p || f.n > N || f.n > ws_nmax_cap || f.ldl < f.n ||
+            f.L == nullptr || f.perm == nullptr || f.piv == nullptr || f.D == nullptr ||
+            f.nelim == nullptr || f.rows == nullptr)
+            return CTP_EINVAL;
+    }
+    return CTP_OK;
+}
+
+static cudaError_t solve_fronts(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int32_t nrhs,
+                                double *X, int64_t ldx, void *ws, cudaStream_t st) {
+    for (int32_t k = 0; k < nf; k++) {
+        cudaError_t e = timed(ctx, K_SYS_FWD, st, [&] {
+            return launch_sys_forward(fronts[k], X, ldx, nrhs, ws, st);
+        });
+        if (e != cudaSuccess) return e;
+    }
+    for (int32_t k = nf - 1; k >= 0; k--) {
+        cudaError_t e = timed(ctx, K_SYS_BWD, st, [&] {
+            return launch_sys_backward(fronts[k], X, ldx, nrhs, ws, st);
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+ctp_status ctp_solve(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N, int32_t nrhs,
+                     double *X, int64_t ldx, void *workspace, size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || X == nullptr || workspace == nullptr || N < 1 || nrhs < 1 || ldx < N)
+        return CTP_EINVAL;
+    int64_t nmax = 0;
+    for (int32_t k = 0; k < nf && fronts != nullptr; k++) nmax = fronts[k].n > nmax ? fronts[k].n : nmax;
+    ctp_status s = check_fronts(nf, fronts, N, nmax);
+    if (s != CTP_OK) return s;
+    if (ws_bytes < sys_solve_ws_bytes(nmax, nrhs)) return CTP_ENOMEM;
+    CTP_CUDA(solve_fronts(ctx, nf, fronts, nrhs, X, ldx, workspace, (cudaStream_t)stream));
+    return CTP_OK;
+}
+
+namespace {
+struct RefineLayout {
+    size_t solve, R, rowsum, mx, berr, total;
+};
+RefineLayout refine_layout(int64_t N, int64_t nmax, int nrhs) {
+    RefineLayout L;
+    size_t off = 0;
+    L.solve = off;
+    off += align256(sys_solve_ws_bytes(nmax, nrhs));
+    L.R = off;
+    off += align256(sizeof(double) * (size_t)N * nrhs);
+    L.rowsum = off;
+    off += align256(sizeof(double) * (size_t)N);
+    L.mx = off;
+    off += align256(sizeof(double) * (3 * (size_t)nrhs + 1));
+    L.berr = off;
+    off += align256(sizeof(double) * (size_t)nrhs);
+    L.total = off;
+    return L;
+}
+}  // namespace
+
+ctp_status ctp_refine_workspace_size(int64_t N, int64_t nmax, int32_t nrhs, size_t *bytes) {
+    if (bytes == nullptr || N < 1 || nmax < 0 || nrhs < 1) return CTP_EINVAL;
+    *bytes = refine_layout(N, nmax, nrhs).total;
+    return CTP_OK;
+}
+
+// R = B - M X, then the backward errors into berr (device)
+static cudaError_t residual_berr(ctp_ctx *ctx, int64_t N, const double *M, int64_t ldm, int nrhs,
+                                 const double *B, int64_t ldb, const double *X, int64_t ldx,
+                                 double *R, const double *rowsum, double *mx, double *berr,
+                                 cudaStream_t st) {
+    cudaError_t e = cudaMemcpy2DAsync(R, sizeof(double) * N, B, sizeof(double) * ldb,
+                                      sizeof(double) * N, nrhs, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = timed(ctx, K_SYMV, st, [&] { return launch_symv_residual(N, M, ldm, nrhs, X, ldx, R, N, st); });
+    if (e != cudaSuccess) return e;
+    return timed(ctx, K_BERR, st, [&] {
+        return launch_backward_error(N, nrhs, R, N, X, ldx, B, ldb, rowsum, mx, berr, st);
+    });
+}
+
+ctp_status ctp_backward_error(ctp_ctx *ctx, int64_t N, const double *M, int64_t ldm, int32_t nrhs,
+                              const double *B, int64_t ldb, const double *X, int64_t ldx,
+                              double *berr, void *workspace, size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || M == nullptr || B == nullptr || X == nullptr || berr == nullptr ||
+        workspace == nullptr || N < 1 || nrhs < 1 || ldm < N || ldb < N || ldx < N)
+        return CTP_EINVAL;
+    RefineLayout L = refine_layout(N, 0, nrhs);
+    if (ws_bytes < L.total) return CTP_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)workspace;
+    double *rowsum = (double *)(w + L.rowsum);
+    CTP_CUDA(cudaMemsetAsync(rowsum, 0, sizeof(double) * N, st));
+    CTP_CUDA(timed(ctx, K_SYMV, st, [&] { return launch_abs_rowsum(N, M, ldm, rowsum, st); }));
+    CTP_CUDA(residual_berr(ctx, N, M, ldm, nrhs, B, ldb, X, ldx, (double *)(w + L.R), rowsum,
+                           (double *)(w + L.mx), berr, st));
+    return CTP_OK;
+}
+
+ctp_status ctp_refine(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
+                      const double *M, int64_t ldm, int32_t nrhs, const double *B, int64_t ldb,
+                      double *X, int64_t ldx, int32_t max_steps, double tol, double *berr_host,
+                      int32_t *steps_host, void *workspace, size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || M == nullptr || B == nullptr || X == nullptr || berr_host == nullptr ||
+        steps_host == nullptr || workspace == nullptr || N < 1 || nrhs < 1 || ldm < N ||
+        ldb < N || ldx < N || max_steps < 0 || max_steps > 100 || !(tol >= 0.0))
+        return CTP_EINVAL;
+    int64_t nmax = 0;
+    for (int32_t k = 0; k < nf && fronts != nullptr; k++) nmax = fronts[k].n > nmax ? fronts[k].n : nmax;
+    ctp_status s = check_fronts(nf, fronts, N, nmax);
+    if (s != CTP_OK) return s;
+    RefineLayout L = refine_layout(N, nmax, nrhs);
+    if (ws_bytes < L.total) return CTP_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)workspace;
+    void *sws = w + L.solve;
+    double *R = (double *)(w + L.R), *rowsum = (double *)(w + L.rowsum);
+    double *mx = (double *)(w + L.mx), *berr = (double *)(w + L.berr);
+    *steps_host = 0;
+    CTP_CUDA(cudaMemsetAsync(rowsum, 0, sizeof(double) * N, st));
+    CTP_CUDA(timed(ctx, K_SYMV, st, [&] { return launch_abs_rowsum(N, M, ldm, rowsum, st); }));
+    CTP_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * ldx, B, sizeof(double) * ldb, sizeof(double) * N,
+                               nrhs, cudaMemcpyDeviceToDevice, st));
+    CTP_CUDA(solve_fronts(ctx, nf, fronts, nrhs, X, ldx, sws, st));
+    for (int32_t k = 0;; k++) {
+        CTP_CUDA(residual_berr(ctx, N, M, ldm, nrhs, B, ldb, X, ldx, R, rowsum, mx, berr, st));
+        double *bh = berr_host + (size_t)k * nrhs;
+        CTP_CUDA(cudaMemcpyAsync(bh, berr, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+        CTP_CUDA(cudaStreamSynchronize(st));
+        double worst = 0.0;
+        for (int r = 0; r < nrhs; r++) worst = bh[r] > worst || bh[r] != bh[r] ? bh[r] : worst;
+        if (!(worst > tol) || k == max_steps) break;
+        CTP_CUDA(solve_fronts(ctx, nf, fronts, nrhs, R, N, sws, st));
+        CTP_CUDA(timed(ctx, K_AXPY, st, [&] { return launch_axpy(N, nrhs, X, ldx, R, N, st); }));
+        *steps_host = k + 1;
+    }
+    return CTP_OK;
+}
+
+}  // extern "C"
+
+struct ctp_chain {
+    std::vector<ctp_sfront> fronts;
+    std::vector<void *> blocks;
+    std::vector<int32_t> nelim, p, pivot;
+};
+
+namespace {
+void chain_free(ctp_chain *c) {
+    if (c == nullptr) return;
+    for (void *b : c->blocks) cudaFree(b);
+    delete c;
+}
+}  // namespace
+
+extern "C" {
+
+ctp_status ctp_factor_dense(ctp_ctx *ctx, int64_t N, double *M, int64_t ldm, int32_t p_first,
+                            const ctp_options *opt_first, int32_t w_rest,
+                            const ctp_options *opt_rest, ctp_chain **chain, void *stream) {
+    if (ctx == nullptr || M == nullptr || chain == nullptr || N < 1 || ldm < N) return CTP_EINVAL;
+    *chain = nullptr;
+    if (p_first < 1 || p_first > kMaxP || w_rest < 1 || w_rest > kMaxP) return CTP_EINVAL;
+    ctp_status s = check_opts(opt_first);
+    if (s == CTP_OK) s = check_opts(opt_rest);
+    if (s != CTP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctp_options o[2] = {*opt_first, *opt_rest};
+    for (ctp_options &x : o) {
+        x.smode = CTP_S_FP64_SUB;
+        if (x.pivot == CTP_PIV_TPP) x.prec = CTP_FP64;
+    }
+    ctp_options otpp = o[1];
+    otpp.pivot = CTP_PIV_TPP;
+    otpp.prec = CTP_FP64;
+    const int wmax = p_first > w_rest ? p_first : w_rest;
+    size_t wsb = 0;
+    // workspace sizes grow with n for a fixed width: size for N rows at both widths
+    const ctp_options *cand[3] = {&o[0], &o[1], &otpp};
+    const int widths[2] = {(int)(p_first < N ? p_first : N), (int)(w_rest < N ? w_rest : N)};
+    for (const ctp_options *x : cand)
+        for (int wd : widths) {
+            const size_t b = ws_layout(N, wd, x, ctx->num_sms).total;
+            wsb = b > wsb ? b : wsb;
+        }
+    ctp_chain *c = new ctp_chain();
+    void *ws = nullptr, *snap = nullptr;
+    int32_t *hbuf = nullptr;
+    std::vector<int32_t> ord(N), tmp(kMaxP);
+    for (int64_t i = 0; i < N; i++) ord[i] = (int32_t)i;
+    ctp_status rc = CTP_OK;
+#define CHAIN_CUDA(x)             \
+    do {                          \
+        if ((x) != cudaSuccess) { \
+            rc = CTP_ECUDA;       \
+            goto done;            \
+        }                         \
+    } while (0)
+    CHAIN_CUDA(cudaMalloc(&ws, wsb));
+    CHAIN_CUDA(cudaMalloc(&snap, sizeof(double) * (size_t)N * wmax));
+    CHAIN_CUDA(cudaMallocHost((void **)&hbuf, sizeof(int32_t) * (kMaxP + 2)));
+    {
+        int64_t col = 0;
+        bool first = true;
+        while (col < N) {
+            const int64_t nk = N - col;
+            const ctp_options &opt = first ? o[0] : o[1];
+            const int w = (int)((first ? p_first : w_rest) < nk ? (first ? p_first : w_rest) : nk);
+            first = false;
+            // one device block per front: rows | perm | piv | nelim | D
+            const size_t ints = (size_t)nk + 2 * (size_t)w + 2;
+            const size_t bytes = align256(sizeof(int32_t) * ints) + sizeof(double) * 2 * (size_t)w;
+            void *blk = nullptr;
+            CHAIN_CUDA(cudaMalloc(&blk, bytes));
+            c->blocks.push_back(blk);
+            int32_t *rows = (int32_t *)blk, *perm = rows + nk, *piv = perm + w, *nel = piv + w;
+            double *D = (double *)((char *)blk + align256(sizeof(int32_t) * ints));
+            CHAIN_CUDA(cudaMemcpyAsync(rows, ord.data() + col, sizeof(int32_t) * nk,
+                                       cudaMemcpyHostToDevice, st));
+            double *A = M + col * ldm + col;
+            double *S = nk > w ? A + (int64_t)w * ldm + w : nullptr;
+            ctp_options ok = opt;
+            if (nk == w) ok.smode = CTP_S_NONE;
+            if (ok.pivot != CTP_PIV_TPP)
+                CHAIN_CUDA(cudaMemcpy2DAsync(snap, sizeof(double) * nk, A, sizeof(double) * ldm,
+                                             sizeof(double) * nk, w, cudaMemcpyDeviceToDevice, st));
+            int32_t info = CTP_OK, e = 0;
+            for (int attempt = 0; attempt < 2; attempt++) {
+                rc = ctp_factor_supernode(ctx, nk, w, A, ldm, &ok, perm, piv, D, nel, S, ldm, ws, wsb,
+                                          stream);
+                if (rc != CTP_OK) goto done;
+                CHAIN_CUDA(cudaMemcpyAsync(hbuf, nel, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CHAIN_CUDA(cudaMemcpyAsync(hbuf + 1, perm, sizeof(int32_t) * w, cudaMemcpyDeviceToHost, st));
+                CHAIN_CUDA(cudaMemcpyAsync(&info, ws, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CHAIN_CUDA(cudaStreamSynchronize(st));
+                if (info != CTP_OK) {
+                    rc = (ctp_status)info;
+                    goto done;
+                }
+                e = hbuf[0];
+                if (e > 0 || ok.pivot == CTP_PIV_TPP) break;
+                // nothing eliminated: put the front back and use full-column pivoting
+                CHAIN_CUDA(cudaMemcpy2DAsync(A, sizeof(double) * ldm, snap, sizeof(double) * nk,
+                                             sizeof(double) * nk, w, cudaMemcpyDeviceToDevice, st));
+                const int sm = ok.smode;
+                ok = otpp;
+                ok.smode = sm;
+            }
+            if (e < 1 || (nk == w && e < w)) {
+                rc = CTP_ECAPACITY;
+                goto done;
+            }
+            for (int q = 0; q < w; q++) tmp[q] = ord[col + hbuf[1 + q]];
+            for (int q = 0; q < w; q++) ord[col + q] = tmp[q];
+            ctp_sfront f;
+            f.n = nk;
+            f.p = w;
+            f.reserved = 0;
+            f.L = A;
+            f.ldl = ldm;
+            f.perm = perm;
+            f.piv = piv;
+            f.D = D;
+            f.nelim = nel;
+            f.rows = rows;
+            c->fronts.push_back(f);
+            c->nelim.push_back(e);
+            c->p.push_back(w);
+            c->pivot.push_back(ok.pivot);
+            col += e;
+        }
+    }
+done:
+#undef CHAIN_CUDA
+    cudaStreamSynchronize(st);
+    if (hbuf) cudaFreeHost(hbuf);
+    if (snap) cudaFree(snap);
+    if (ws) cudaFree(ws);
+    if (rc != CTP_OK) {
+        chain_free(c);
+        return rc;
+    }
+    *chain = c;
+    return CTP_OK;
+}
+
+ctp_status ctp_chain_fronts(const ctp_chain *chain, int32_t *nf, const ctp_sfront **fronts) {
+    if (chain == nullptr || nf == nullptr || fronts == nullptr) return CTP_EINVAL;
+    *nf = (int32_t)chain->fronts.size();
+    *fronts = chain->fronts.data();
+    return CTP_OK;
+}
+
+ctp_status ctp_chain_info(const ctp_chain *chain, int32_t cap, int32_t *nelim, int32_t *p,
+                          int32_t *pivot) {
+    if (chain == nullptr || cap < 0) return CTP_EINVAL;
+    const int32_t n = (int32_t)chain->fronts.size();
+    for (int32_t k = 0; k < n && k < cap; k++) {
+        if (nelim) nelim[k] = chain->nelim[k];
+        if (p) p[k] = chain->p[k];
+        if (pivot) pivot[k] = chain->pivot[k];
+    }
+    return CTP_OK;
+}
+
+ctp_status ctp_chain_destroy(ctp_chain *chain) {
+    chain_free(chain);
     return CTP_OK;
 }
 

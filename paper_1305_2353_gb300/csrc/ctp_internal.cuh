@@ -92,6 +92,7 @@ struct BatchOpts {
     double u, small;
     int pivot;  // ctp_pivot
     int smode, prec;
+    int64_t lo_off;  // elements from the hi to the lo BF16 operand copies (0: none)
 };
 cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                 const int *list, int count, int G, int pmax, BatchOpts o,
@@ -107,7 +108,7 @@ cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, c
                                    cudaStream_t st);
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
-                                 int32_t *info, int num_sms, cudaStream_t st);
+                                 bool split, int32_t *info, int num_sms, cudaStream_t st);
 constexpr int kBatchKp = 256;  // K stride of the stacked BF16 operand buffers
 
 // the batched launch sequence (batch.cu); the plan type is declared in ctp.h
@@ -122,7 +123,7 @@ cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_
 
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,
-                              double *W21, int64_t ldw, void *Wb, void *Lb, int Kp,
+                              double *W21, int64_t ldw, void *Wb, void *Lb, int Kp, int64_t lo_off,
                               cudaStream_t st);
 
 // Threshold partial pivoting on all n rows (the comparator of the compressed path).
@@ -133,12 +134,33 @@ cudaError_t launch_tpp(double *A, int64_t n, int p, int64_t lda, double u, doubl
 
 // K-padding of the BF16 operand copies used by the tensor-core Form.
 int form_tc_kpad(int p);
-cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
-                           float *S, int64_t lds, int layout /* 0 full, 1 packed, 2 tiled */,
+// lo_off: elements from the hi BF16 copies to the lo copies (0: plain BF16).
+cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64_t m, int Kp,
+                           const int32_t *nelim, float *S, int64_t lds,
+                           int layout /* 0 full, 1 packed, 2 tiled, 3 subtract from FP64 */,
                            int32_t *info, int num_sms, cudaStream_t st);
 
 cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
                              int64_t m, const int32_t *nelim, void *S, int64_t lds, int smode,
                              cudaStream_t st);
+
+// Complete systems: front-list solve, residual, backward error (system.cu).
+size_t sys_solve_ws_bytes(int64_t nmax, int nrhs);
+cudaError_t launch_sys_forward(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, void *ws,
+                               cudaStream_t st);
+cudaError_t launch_sys_backward(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, void *ws,
+                                cudaStream_t st);
+cudaError_t launch_symv_residual(int64_t N, const double *M, int64_t ldm, int nrhs, const double *X,
+                                 int64_t ldx, double *R, int64_t ldr, cudaStream_t st);
+cudaError_t launch_abs_rowsum(int64_t N, const double *M, int64_t ldm, double *rowsum,
+                              cudaStream_t st);
+cudaError_t launch_backward_error(int64_t N, int nrhs, const double *R, int64_t ldr, const double *X,
+                                  int64_t ldx, const double *B, int64_t ldb, const double *rowsum,
+                                  double *mx, double *berr, cudaStream_t st);
+cudaError_t launch_axpy(int64_t N, int nrhs, double *X, int64_t ldx, const double *Dx, int64_t ldd,
+                        cudaStream_t st);
+cudaError_t launch_w21_from_l(const double *A, int64_t lda, int p, int64_t m, const int32_t *piv,
+                              const double *D, const int32_t *nelim, double *W21, int64_t ldw,
+                              cudaStream_t st);
 
 }  // namespace ctp

@@ -15,7 +15,7 @@ namespace {
 
 constexpr int kTile = 64, kK = 16, kTh = 256;
 
-template <typename OutT, bool kPacked>
+template <typename OutT, bool kPacked, bool kSub = false>
 __device__ __forceinline__ void form_tile(const double *__restrict__ L21, int64_t ldl,
                                           const double *__restrict__ W21, int64_t ldw, int64_t m,
                                           int e, OutT *__restrict__ S, int64_t lds, int64_t b) {
@@ -60,17 +60,20 @@ __device__ __forceinline__ void form_tile(const double *__restrict__ L21, int64_
             const int64_t gi = i0 + ty + 16 * q, gj = j0 + tx + 16 * s;
             if (gi < m && gj < m && gi >= gj) {
                 const int64_t idx = kPacked ? gj * m - gj * (gj - 1) / 2 + (gi - gj) : gj * lds + gi;
-                S[idx] = (OutT)acc[q][s];
+                if (kSub)
+                    S[idx] -= (OutT)acc[q][s];
+                else
+                    S[idx] = (OutT)acc[q][s];
             }
         }
 }
 
-template <typename OutT, bool kPacked>
+template <typename OutT, bool kPacked, bool kSub = false>
 __global__ void __launch_bounds__(kTh)
     k_form_fp64(const double *__restrict__ L21, int64_t ldl, const double *__restrict__ W21,
                 int64_t ldw, int64_t m, const int32_t *__restrict__ nelim_p, OutT *__restrict__ S,
                 int64_t lds) {
-    form_tile<OutT, kPacked>(L21, ldl, W21, ldw, m, *nelim_p, S, lds, blockIdx.x);
+    form_tile<OutT, kPacked, kSub>(L21, ldl, W21, ldw, m, *nelim_p, S, lds, blockIdx.x);
 }
 
 // Batched: CTA b takes work item b = (front, triangular 64 x 64 tile of its S).
@@ -107,6 +110,9 @@ cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, 
     else if (smode == CTP_S_FP32)
         k_form_fp64<float, false><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
                                                                     (float *)S, lds);
+    else if (smode == CTP_S_FP64_SUB)
+        k_form_fp64<double, false, true><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
+                                                                           (double *)S, lds);
     else if (smode == CTP_S_FP64_PACKED)
         k_form_fp64<double, true><<<(unsigned)ntiles, kTh, 0, st>>>(L21, ldl, W21, ldw, m, nelim,
                                                                     (double *)S, lds);

@@ -144,27 +144,49 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[3
         : "r"(taddr));
 }
 
+// Tile shapes.  Plain BF16: tiles of 128 rows x 256 columns.  Split BF16
+// (kSplit): 128 x 128 tiles, and every operand is the pair hi = bf16(x),
+// lo = bf16(x - hi); the accumulator receives hi*hi + hi*lo + lo*hi, the
+// three-product scheme of Henry, Tang and Heinecke ("Leveraging the bfloat16
+// artificial intelligence datatype for higher-precision computations", 2019),
+// close to FP32 products.  Shared memory is the same in both modes: the
+// resident L21 block (KB blocks of 32 KB) and a 96 KB ring of W21 blocks.
+template <bool kSplit>
+struct Cfg {
+    static constexpr int BN = kSplit ? 128 : 256;
+    static constexpr int R = BN / kBM;                        // column blocks are R row blocks wide
+    static constexpr int Stages = kSplit ? 3 : 6;
+    static constexpr uint32_t PieceA = kBM * kBK * 2;        // one 128 x 64 BF16 block
+    static constexpr uint32_t PieceB = BN * kBK * 2;
+    static constexpr uint32_t StageA = PieceA * (kSplit ? 2 : 1);
+    static constexpr uint32_t StageB = PieceB * (kSplit ? 2 : 1);
+    static constexpr uint32_t TmemCols = 2 * BN;             // two FP32 accumulators
+};
+static_assert(Cfg<true>::StageB == kStageB && Cfg<false>::StageB == kStageB, "resident block size");
+static_assert(Cfg<true>::StageA * Cfg<true>::Stages == kStageA * kStages, "ring size");
+
 // Tiles of the lower triangle, walked column block by column block: column
-// block b (256 columns) meets row blocks 2b..nM-1 (128 rows), so
-// T(b) = b*nM - b(b-1) tiles precede column block b.  Consecutive tiles --
-// which run at the same time on neighbouring SMs -- are vertically adjacent,
-// so their stores into a column of S land next to each other in HBM.
-__host__ __device__ inline int64_t tiles_before_col(int64_t b, int64_t nM) { return b * nM - b * (b - 1); }
-__host__ __device__ inline int64_t tile_count(int64_t nM) {
-    const int64_t nN = (nM + 1) / 2;  // column blocks that meet the triangle
-    return tiles_before_col(nN, nM);
+// block b meets row blocks R*b..nM-1, so T(b) = b*nM - R*b(b-1)/2 tiles
+// precede it.  Consecutive tiles -- which run at the same time on
+// neighbouring SMs in the round-robin walk -- are vertically adjacent.
+__host__ __device__ inline int64_t tiles_before_col(int64_t b, int64_t nM, int R) {
+    return b * nM - R * (b * (b - 1) / 2);
 }
-__device__ __forceinline__ void decode_tile(int64_t t, int nM, int &ti, int &tj) {
-    int lo = 0, hi = (nM + 1) / 2;
+__host__ __device__ inline int64_t col_blocks(int64_t nM, int R) { return (nM + R - 1) / R; }
+__host__ __device__ inline int64_t tile_count(int64_t nM, int R) {
+    return tiles_before_col(col_blocks(nM, R), nM, R);
+}
+__device__ __forceinline__ void decode_tile(int64_t t, int nM, int R, int &ti, int &tj) {
+    int lo = 0, hi = (int)col_blocks(nM, R);
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (tiles_before_col(mid, nM) <= t)
+        if (tiles_before_col(mid, nM, R) <= t)
             lo = mid;
         else
             hi = mid;
     }
     tj = lo;
-    ti = 2 * lo + (int)(t - tiles_before_col(lo, nM));
+    ti = R * lo + (int)(t - tiles_before_col(lo, nM, R));
 }
 
 // Everything the roles need to know about one tile of work.
@@ -182,58 +204,106 @@ struct BatchTab {
     const int *item_front;
 };
 
-template <bool kBatch>
-__device__ __forceinline__ TileInfo tile_info(int64_t t, int nM, int KB, int64_t m, float *S,
-                                              int64_t lds, int layout, const BatchTab &bt) {
-    TileInfo x;
-    if (!kBatch) {
-        decode_tile(t, nM, x.ti, x.tj);
-        x.KB = KB;
-        x.key = x.tj;
-        x.arow = (int64_t)x.ti * kBM;
-        x.brow = (int64_t)x.tj * kBN;
-        x.m = m;
-        x.nb = nM;
-        x.S = S;
-        x.lds = lds;
-        x.layout = layout;
-    } else {
+// Which tiles a CTA takes.  mode 0: round robin over the column-block-major
+// tile list (all CTAs work down the same column block).  mode 1 (panels):
+// the column blocks are taken G at a time; CTA c owns one column block of
+// each panel (c, or G-1-c in odd panels, which evens out the work) and walks
+// it from the diagonal down, keeping its L21 block resident.  All CTAs then
+// move down the rows together, so each W21 block is fetched from HBM about
+// once per panel and served to the other CTAs from L2 -- what keeps the
+// operand traffic small when the operands do not fit in L2.
+struct Sched {
+    int mode, nM, G, c;
+    int64_t ntiles, nN;
+};
+
+template <bool kBatch, int R>
+__device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64_t m1, float *S1,
+                                       int64_t lds1, int layout1, const BatchTab &bt, TileInfo &x) {
+    int ti, tj;
+    if (kBatch) {
+        const int64_t t = s.c + k * s.G;
+        if (t >= s.ntiles) return false;
         const int f = bt.item_front[t];
         const BFront b = bt.tab[f];
-        decode_tile(t - b.f0, b.nM, x.ti, x.tj);
+        decode_tile(t - b.f0, b.nM, R, ti, tj);
         const int e = *bt.fronts[f].nelim;
+        x.ti = ti;
+        x.tj = tj;
         x.KB = (e + kBK - 1) / kBK;
-        x.key = f * 65536 + x.tj;
-        x.arow = b.row0 + (int64_t)x.ti * kBM;
-        x.brow = b.row0 + (int64_t)x.tj * kBN;
+        x.key = f * 65536 + tj;
+        x.arow = b.row0 + (int64_t)ti * kBM;
+        x.brow = b.row0 + (int64_t)tj * R * kBM;
         x.m = b.m;
         x.nb = b.nM;
         x.S = reinterpret_cast<float *>(bt.fronts[f].S);
         x.lds = 0;
         x.layout = 2;
+        return true;
     }
-    return x;
+    if (s.mode == 0) {
+        const int64_t t = s.c + k * s.G;
+        if (t >= s.ntiles) return false;
+        decode_tile(t, s.nM, R, ti, tj);
+    } else {
+        int64_t rem = k;
+        bool found = false;
+        for (int64_t P = 0; P * s.G < s.nN; P++) {
+            const int64_t j = P * s.G + ((P & 1) ? (s.G - 1 - s.c) : s.c);
+            if (j >= s.nN) continue;
+            const int64_t cnt = s.nM - R * j;
+            if (rem < cnt) {
+                tj = (int)j;
+                ti = (int)(R * j + rem);
+                found = true;
+                break;
+            }
+            rem -= cnt;
+        }
+        if (!found) return false;
+    }
+    x.ti = ti;
+    x.tj = tj;
+    x.KB = KB1;
+    x.key = tj;
+    x.arow = (int64_t)ti * kBM;
+    x.brow = (int64_t)tj * R * kBM;
+    x.m = m1;
+    x.nb = s.nM;
+    x.S = S1;
+    x.lds = lds1;
+    x.layout = layout1;
+    return true;
 }
 
-template <bool kBatch>
+// Maps: hi copies of W21 and L21 (mW, mL) and, for kSplit, the lo copies.
+template <bool kBatch, bool kSplit>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_form_tc(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapL,
+    k_form_tc(const __grid_constant__ CUtensorMap mW, const __grid_constant__ CUtensorMap mL,
+              const __grid_constant__ CUtensorMap mWl, const __grid_constant__ CUtensorMap mLl,
               int64_t m_single, const int32_t *__restrict__ nelim_p, float *__restrict__ S_single,
               int64_t lds_single, int layout_single, int32_t *__restrict__ info, int64_t ntiles_batch,
-              BatchTab btab) {
+              BatchTab btab, int sched_mode) {
+    using C = Cfg<kSplit>;
+    constexpr int BN = C::BN, R = C::R, NS = C::Stages;
     extern __shared__ unsigned char smraw[];
     __shared__ Bars bars;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sB = smem;                                 // [kMaxKB][kStageB]: resident L21 block
-    uint8_t *sA = smem + (size_t)kMaxKB * kStageB;     // [kStages][kStageA]: W21 ring
+    uint8_t *sB = smem;                                 // [kMaxKB][StageB]: resident L21 block
+    uint8_t *sA = smem + (size_t)kMaxKB * C::StageB;   // [NS][StageA]: W21 ring
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KB1 = kBatch ? 0 : (*nelim_p + kBK - 1) / kBK;
-    const int nM1 = kBatch ? 0 : (int)((m_single + kBM - 1) / kBM);
-    const int64_t ntiles = kBatch ? ntiles_batch : tile_count(nM1);
-#define TILE(t) tile_info<kBatch>((t), nM1, KB1, m_single, S_single, lds_single, layout_single, btab)
+    Sched sc;
+    sc.mode = kBatch ? 0 : sched_mode;
+    sc.nM = kBatch ? 0 : (int)((m_single + kBM - 1) / kBM);
+    sc.nN = kBatch ? 0 : col_blocks(sc.nM, R);
+    sc.ntiles = kBatch ? ntiles_batch : tile_count(sc.nM, R);
+    sc.G = gridDim.x;
+    sc.c = blockIdx.x;
+#define TILE_K(k, x) tile_k<kBatch, R>((k), sc, KB1, m_single, S_single, lds_single, layout_single, btab, (x))
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; s++) {
+        for (int s = 0; s < NS; s++) {
             mbar_init(&bars.full[s], 1);
             mbar_init(&bars.empty[s], 1);
         }
@@ -249,7 +319,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&bars.tmem_base)),
-                     "r"(kTmemCols)
+                     "r"(C::TmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -257,7 +327,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = bars.tmem_base;
-    const uint32_t idesc = idesc_bf16(kBM, kBN);
+    const uint32_t idesc = idesc_bf16(kBM, BN);
 
     if (warp == 0) {
         // ---------------- TMA producer: the L21 block of the current column block
@@ -265,8 +335,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if (lane == 0) {
             int stage = 0, cur_key = -1;
             uint32_t phase = 0, bphase = 0;
-            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                const TileInfo x = TILE(t);
+            TileInfo x;
+            for (int64_t k = 0; TILE_K(k, x); k++) {
                 if (x.KB == 0) continue;
                 bool ok = true;
                 if (x.key != cur_key) {
@@ -274,9 +344,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         atomicExch(&bars.abort, 1);
                         break;
                     }
-                    mbar_expect_tx(&bars.bfull, (uint32_t)x.KB * kStageB);
-                    for (int kb = 0; kb < x.KB; kb++)
-                        tma_load_2d(sB + (size_t)kb * kStageB, &mapL, kb * kBK, (int)x.brow, &bars.bfull);
+                    mbar_expect_tx(&bars.bfull, (uint32_t)x.KB * C::StageB);
+                    for (int kb = 0; kb < x.KB; kb++) {
+                        uint8_t *dst = sB + (size_t)kb * C::StageB;
+                        tma_load_2d(dst, &mL, kb * kBK, (int)x.brow, &bars.bfull);
+                        if (kSplit) tma_load_2d(dst + C::PieceB, &mLl, kb * kBK, (int)x.brow, &bars.bfull);
+                    }
                     bphase ^= 1u;
                     cur_key = x.key;
                 }
@@ -285,9 +358,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&bars.full[stage], kStageA);
-                    tma_load_2d(sA + (size_t)stage * kStageA, &mapW, kb * kBK, (int)x.arow, &bars.full[stage]);
-                    if (++stage == kStages) {
+                    mbar_expect_tx(&bars.full[stage], C::StageA);
+                    uint8_t *dst = sA + (size_t)stage * C::StageA;
+                    tma_load_2d(dst, &mW, kb * kBK, (int)x.arow, &bars.full[stage]);
+                    if (kSplit) tma_load_2d(dst + C::PieceA, &mWl, kb * kBK, (int)x.arow, &bars.full[stage]);
+                    if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -303,8 +378,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if (lane == 0) {
             int stage = 0, acc = 0, cur_key = -1;
             uint32_t phase = 0, accphase = 0, bphase = 0;
-            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                const TileInfo x = TILE(t);
+            TileInfo x;
+            for (int64_t k = 0; TILE_K(k, x); k++) {
                 if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars)) {
                     atomicExch(&bars.abort, 1);
                     break;
@@ -320,23 +395,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     bphase ^= 1u;
                     cur_key = x.key;
                 }
-                const uint32_t dt = tmem + (uint32_t)(acc * kBN);
+                const uint32_t dt = tmem + (uint32_t)(acc * BN);
                 for (int kb = 0; kb < x.KB; kb++) {
                     if (!mbar_wait(&bars.full[stage], phase, &bars)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + (size_t)stage * kStageA);
-                    const uint32_t b0 = smem_u32(sB + (size_t)kb * kStageB);
+                    const uint32_t a0 = smem_u32(sA + (size_t)stage * C::StageA);
+                    const uint32_t b0 = smem_u32(sB + (size_t)kb * C::StageB);
 #pragma unroll
-                    for (int k = 0; k < kBK / kUmmaK; k++) {
+                    for (int kk = 0; kk < kBK / kUmmaK; kk++) {
                         // advance 16 BF16 = 32 bytes along K inside the swizzled rows
-                        umma_bf16(dt, sdesc(a0 + k * 32), sdesc(b0 + k * 32), idesc,
-                                  (kb > 0 || k > 0) ? 1u : 0u);
+                        const uint64_t ah = sdesc(a0 + kk * 32), bh = sdesc(b0 + kk * 32);
+                        umma_bf16(dt, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        if (kSplit) {
+                            umma_bf16(dt, ah, sdesc(b0 + C::PieceB + kk * 32), idesc, 1u);
+                            umma_bf16(dt, sdesc(a0 + C::PieceA + kk * 32), bh, idesc, 1u);
+                        }
                     }
                     umma_commit(&bars.empty[stage]);  // W21 stage free once these MMAs finish
-                    if (++stage == kStages) {
+                    if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -349,8 +428,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 // release the resident L21 block when the next tile with work needs another
                 if (x.KB > 0) {
                     int next_key = -2;
-                    for (int64_t tn = t + gridDim.x; tn < ntiles; tn += gridDim.x) {
-                        const TileInfo y = TILE(tn);
+                    TileInfo y;
+                    for (int64_t kn = k + 1; TILE_K(kn, y); kn++) {
                         if (y.KB > 0) {
                             next_key = y.key;
                             break;
@@ -367,11 +446,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else {
         // ---------------- epilogue: warps 2..9
         const int q = warp & 3;             // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;   // 128-column half of the 256-column tile
+        const int half = (warp - 2) >> 2;   // which half of the tile's columns
         int acc = 0;
         uint32_t accphase = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const TileInfo x = TILE(t);
+        TileInfo x;
+        for (int64_t k = 0; TILE_K(k, x); k++) {
             const int ti = x.ti, tj = x.tj, KB = x.KB, layout = x.layout;
             const int64_t m = x.m, nb = x.nb, lds = x.lds;
             float *S = x.S;
@@ -381,34 +460,45 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
             tc_fence_after();
             const int64_t i = (int64_t)ti * kBM + q * 32 + lane;
-            const int64_t jbase = (int64_t)tj * kBN + half * 128;
+            const int64_t jbase = (int64_t)tj * BN + half * (BN / 2);
             // tiles strictly below the diagonal and inside S need no masking
-            const bool interior = (jbase + 127 < (int64_t)ti * kBM) && ((int64_t)ti * kBM + kBM <= m);
-            // block layout: this half of the tile is block (ti, 2 tj + half) of S;
-            // blocks above the block diagonal are not part of S
-            const int64_t bj = 2 * (int64_t)tj + half;
+            const bool interior = (jbase + BN / 2 - 1 < (int64_t)ti * kBM) && ((int64_t)ti * kBM + kBM <= m);
+            // block layout: these columns belong to block (ti, bj) of S, from
+            // column boff of the block on; blocks above the diagonal are not part of S
+            const int64_t bj = jbase / 128;
+            const int boff = (int)(jbase % 128);
             const bool tiled = layout == 2;
             if (tiled && bj > ti) goto next_tile_half;
 #pragma unroll 1
-            for (int c = 0; c < 4; c += 2) {
+            for (int c = 0; c < BN / 64; c += 2) {
                 uint32_t r[64];
                 const uint32_t taddr =
-                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + half * 128 + c * 32);
+                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + half * (BN / 2) + c * 32);
                 tmem_ld32_nowait(taddr, *reinterpret_cast<uint32_t(*)[32]>(&r[0]));
                 tmem_ld32_nowait(taddr + 32, *reinterpret_cast<uint32_t(*)[32]>(&r[32]));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (KB == 0) {
 #pragma unroll
-                    for (int x = 0; x < 64; x++) r[x] = 0u;
+                    for (int xx = 0; xx < 64; xx++) r[xx] = 0u;
                 }
                 const int64_t j0 = jbase + c * 32;
+                if (layout == 3) {
+                    // subtract into a full column-major FP64 matrix (lower triangle)
+                    double *dp = reinterpret_cast<double *>(S) + j0 * lds + i;
+#pragma unroll
+                    for (int xx = 0; xx < 64; xx++) {
+                        if (interior || (i < m && j0 + xx <= i)) *dp -= (double)__uint_as_float(r[xx]);
+                        dp += lds;
+                    }
+                    continue;
+                }
                 if (tiled) {
                     // whole blocks, front to back: column c of the block is the
                     // 512 bytes written by the four lane quarters
                     float *blk = S + (int64_t)16384 * (bj * nb - bj * (bj - 1) / 2 + (ti - bj));
-                    float *ptr = blk + (int64_t)(c * 32) * 128 + q * 32 + lane;
+                    float *ptr = blk + (int64_t)(boff + c * 32) * 128 + q * 32 + lane;
 #pragma unroll
-                    for (int x = 0; x < 64; x++) ptr[x * 128] = __uint_as_float(r[x]);
+                    for (int xx = 0; xx < 64; xx++) ptr[xx * 128] = __uint_as_float(r[xx]);
                     continue;
                 }
                 // S(i, j) lives at S + col(j) + i, with col(j) = j*lds (full) or
@@ -419,23 +509,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     if (packed) {
                         int d = (int)(m - 1 - j0);
 #pragma unroll
-                        for (int x = 0; x < 64; x++) {
-                            *ptr = __uint_as_float(r[x]);
+                        for (int xx = 0; xx < 64; xx++) {
+                            *ptr = __uint_as_float(r[xx]);
                             ptr += d;
                             --d;
                         }
                     } else {
 #pragma unroll
-                        for (int x = 0; x < 64; x++) {
-                            *ptr = __uint_as_float(r[x]);
+                        for (int xx = 0; xx < 64; xx++) {
+                            *ptr = __uint_as_float(r[xx]);
                             ptr += lds;
                         }
                     }
                 } else {
                     int64_t j = j0;
 #pragma unroll
-                    for (int x = 0; x < 64; x++) {
-                        if (i < m && j <= i) *ptr = __uint_as_float(r[x]);
+                    for (int xx = 0; xx < 64; xx++) {
+                        if (i < m && j <= i) *ptr = __uint_as_float(r[xx]);
                         ptr += packed ? (m - 1 - j) : lds;
                         ++j;
                     }
@@ -451,12 +541,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
         }
     }
-#undef TILE
+#undef TILE_K
     __syncthreads();
     if (threadIdx.x == 0 && bars.abort) atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TmemCols)
                      : "memory");
     }
 }
@@ -491,42 +581,74 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_
 
 int form_tc_kpad(int p) { return (p + kBK - 1) / kBK * kBK; }
 
-cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t m, int Kp, const int32_t *nelim,
-                           float *S, int64_t lds, int layout, int32_t *info, int num_sms,
-                           cudaStream_t st) {
+namespace {
+template <bool kBatch, bool kSplit>
+cudaError_t set_smem(size_t smem) {
+    return cudaFuncSetAttribute(k_form_tc<kBatch, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+constexpr size_t kSmemTC = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA + 1024;
+}  // namespace
+
+cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64_t m, int Kp,
+                           const int32_t *nelim, float *S, int64_t lds, int layout, int32_t *info,
+                           int num_sms, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    if ((((uintptr_t)Wb) | ((uintptr_t)Lb)) & 15) return cudaErrorMisalignedAddress;
-    CUtensorMap mW, mL;
-    if (!make_map(&mW, Wb, m, Kp, kBM) || !make_map(&mL, Lb, m, Kp, kBN)) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA + 1024;
-    cudaError_t err =
-        cudaFuncSetAttribute(k_form_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool split = lo_off != 0;
+    const void *Wl = split ? (const void *)((const char *)Wb + 2 * lo_off) : Wb;
+    const void *Ll = split ? (const void *)((const char *)Lb + 2 * lo_off) : Lb;
+    if ((((uintptr_t)Wb) | ((uintptr_t)Lb) | ((uintptr_t)Wl) | ((uintptr_t)Ll)) & 15)
+        return cudaErrorMisalignedAddress;
+    const int BN = split ? Cfg<true>::BN : Cfg<false>::BN, R = BN / kBM;
+    CUtensorMap mW, mL, mWl, mLl;
+    if (!make_map(&mW, Wb, m, Kp, kBM) || !make_map(&mL, Lb, m, Kp, BN) ||
+        !make_map(&mWl, Wl, m, Kp, kBM) || !make_map(&mLl, Ll, m, Kp, BN))
+        return cudaErrorInvalidValue;
+    cudaError_t err = split ? set_smem<false, true>(kSmemTC) : set_smem<false, false>(kSmemTC);
     if (err != cudaSuccess) return err;
     const int nM = (int)((m + kBM - 1) / kBM);
-    const int64_t ntiles = tile_count(nM);
+    const int64_t ntiles = tile_count(nM, R), nN = col_blocks(nM, R);
+    // panels when the split operands (twice the bytes) need the L2-friendly walk
+    const int mode = (split && nN >= 2 * (int64_t)num_sms) ? 1 : 0;
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
     BatchTab none = {nullptr, nullptr, nullptr};
-    k_form_tc<false><<<grid, kThreadsTC, smem, st>>>(mW, mL, m, nelim, S, lds, layout, info, 0, none);
+    if (split)
+        k_form_tc<false, true><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, m, nelim, S, lds, layout,
+                                                                   info, 0, none, mode);
+    else
+        k_form_tc<false, false><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, m, nelim, S, lds,
+                                                                    layout, info, 0, none, mode);
     return cudaGetLastError();
 }
 
-int64_t form_tc_tiles(int64_t m) { return m > 0 ? tile_count((m + kBM - 1) / kBM) : 0; }
+int64_t form_tc_tiles(int64_t m, bool split) {
+    const int R = (split ? Cfg<true>::BN : Cfg<false>::BN) / kBM;
+    return m > 0 ? tile_count((m + kBM - 1) / kBM, R) : 0;
+}
 
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
-                                 int32_t *info, int num_sms, cudaStream_t st) {
+                                 bool split, int32_t *info, int num_sms, cudaStream_t st) {
     if (items == 0) return cudaSuccess;
-    if ((((uintptr_t)Wb) | ((uintptr_t)Lb)) & 15) return cudaErrorMisalignedAddress;
-    CUtensorMap mW, mL;
-    if (!make_map(&mW, Wb, total_rows, kBatchKp, kBM) || !make_map(&mL, Lb, total_rows, kBatchKp, kBN))
+    const int64_t lo = split ? total_rows * kBatchKp : 0;
+    const void *Wl = (const char *)Wb + 2 * lo, *Ll = (const char *)Lb + 2 * lo;
+    if ((((uintptr_t)Wb) | ((uintptr_t)Lb) | ((uintptr_t)Wl) | ((uintptr_t)Ll)) & 15)
+        return cudaErrorMisalignedAddress;
+    const int BN = split ? Cfg<true>::BN : Cfg<false>::BN;
+    CUtensorMap mW, mL, mWl, mLl;
+    if (!make_map(&mW, Wb, total_rows, kBatchKp, kBM) || !make_map(&mL, Lb, total_rows, kBatchKp, BN) ||
+        !make_map(&mWl, Wl, total_rows, kBatchKp, kBM) || !make_map(&mLl, Ll, total_rows, kBatchKp, BN))
         return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA + 1024;
-    cudaError_t err =
-        cudaFuncSetAttribute(k_form_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = split ? set_smem<true, true>(kSmemTC) : set_smem<true, false>(kSmemTC);
     if (err != cudaSuccess) return err;
     const int grid = (int)(items < num_sms ? items : num_sms);
     BatchTab bt = {fronts, tab, item_front};
-    k_form_tc<true><<<grid, kThreadsTC, smem, st>>>(mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt);
+    if (split)
+        k_form_tc<true, true><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, 0, nullptr, nullptr, 0, 2,
+                                                                  info, items, bt, 0);
+    else
+        k_form_tc<true, false><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, 0, nullptr, nullptr, 0,
+                                                                   2, info, items, bt, 0);
     return cudaGetLastError();
 }
 

@@ -24,14 +24,18 @@ CTP_OK, CTP_EINVAL, CTP_ENOMEM, CTP_ECUDA, CTP_ENONFINITE, CTP_ETIMEOUT, CTP_ECA
 STATUS = {0: "CTP_OK", 1: "CTP_EINVAL", 2: "CTP_ENOMEM", 3: "CTP_ECUDA", 4: "CTP_ENONFINITE",
           5: "CTP_ETIMEOUT", 6: "CTP_ECAPACITY", 7: "CTP_EUNSUPPORTED"}
 PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3}
-PREC = {"fp64": 0, "bf16": 1}
-SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4, "fp32_tiled": 5}
+PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2}
+SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4, "fp32_tiled": 5,
+         "fp64_sub": 6}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
 
 EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_compress_strict",
            "ctp_compress_strict_noalloc", "ctp_compress_relaxed", "ctp_factor_supernode",
            "ctp_read_info", "ctp_profile_begin", "ctp_profile_end", "ctp_batch_plan_create",
-           "ctp_batch_plan_destroy", "ctp_batch_upload", "ctp_factor_batch", "ctp_batch_read_info"]
+           "ctp_batch_plan_destroy", "ctp_batch_upload", "ctp_factor_batch", "ctp_batch_read_info",
+           "ctp_solve_workspace_size", "ctp_solve", "ctp_refine_workspace_size",
+           "ctp_backward_error", "ctp_refine", "ctp_factor_dense", "ctp_chain_fronts",
+           "ctp_chain_info", "ctp_chain_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -49,6 +53,14 @@ class Front(ctypes.Structure):
                 ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("perm", ctypes.c_void_p),
                 ("piv", ctypes.c_void_p), ("D", ctypes.c_void_p), ("nelim", ctypes.c_void_p),
                 ("S", ctypes.c_void_p), ("lds", ctypes.c_int64)]
+
+
+class SFront(ctypes.Structure):
+    """Mirror of ctp_sfront (one front of a factored system)."""
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("L", ctypes.c_void_p), ("ldl", ctypes.c_int64), ("perm", ctypes.c_void_p),
+                ("piv", ctypes.c_void_p), ("D", ctypes.c_void_p), ("nelim", ctypes.c_void_p),
+                ("rows", ctypes.c_void_p)]
 
 
 class CtpError(RuntimeError):
@@ -86,6 +98,17 @@ def load(path: str = LIB_PATH):
     L.ctp_batch_upload.argtypes = [P, P, P, sz, P]
     L.ctp_factor_batch.argtypes = [P, P, P, P, sz, P]
     L.ctp_batch_read_info.argtypes = [P, P, P, P, P]
+    L.ctp_solve_workspace_size.argtypes = [i64, i32, ctypes.POINTER(sz)]
+    L.ctp_solve.argtypes = [P, i32, P, i64, i32, P, i64, P, sz, P]
+    L.ctp_refine_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(sz)]
+    L.ctp_backward_error.argtypes = [P, i64, P, i64, i32, P, i64, P, i64, P, P, sz, P]
+    L.ctp_refine.argtypes = [P, i32, P, i64, P, i64, i32, P, i64, P, i64, i32, ctypes.c_double,
+                             P, ctypes.POINTER(i32), P, sz, P]
+    L.ctp_factor_dense.argtypes = [P, i64, P, i64, i32, ctypes.POINTER(Options), i32,
+                                   ctypes.POINTER(Options), ctypes.POINTER(P), P]
+    L.ctp_chain_fronts.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(P)]
+    L.ctp_chain_info.argtypes = [P, i32, P, P, P]
+    L.ctp_chain_destroy.argtypes = [P]
     L.ctp_profile_begin.argtypes = [P]
     L.ctp_profile_end.argtypes = [P, i32, P, P, P, ctypes.POINTER(i32)]
     for f in EXPORTS[1:]:
@@ -213,6 +236,19 @@ def compress_strict_noalloc(A21, m, p, lda, C, J=None, stream=None):
 # ---------------------------------------------------------------------------
 # layout helpers (no arithmetic)
 
+class _CudaArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2}
+
+
+def device_view(ptr, n, dtype="int32"):
+    """A torch tensor viewing n elements of library-owned device memory (no copy)."""
+    import torch
+    ts = {"int32": "<i4", "float64": "<f8"}[dtype]
+    return torch.as_tensor(_CudaArray(ptr, n, ts), device="cuda")
+
+
 def colmajor(a: np.ndarray, device="cuda"):
     """numpy (rows x cols) -> device tensor (cols, rows) holding it column-major."""
     import torch
@@ -264,7 +300,7 @@ class Supernode:
         m = self.n - p
         self.S = None
         if opt.smode != 0:
-            dt = torch.float64 if opt.smode in (1, 3) else torch.float32
+            dt = torch.float64 if opt.smode in (1, 3, 6) else torch.float32
             if opt.smode in (3, 4):
                 self.S = torch.zeros(max(m * (m + 1) // 2, 1), dtype=dt, device=dev)  # packed
             elif opt.smode == 5:
@@ -292,6 +328,90 @@ class Supernode:
                 out["S"] = to_numpy(self.S)
         out["info"] = self.ctx.read_info(self.ws)
         return out
+
+
+class Chain:
+    """Factors of a dense symmetric system (``ctp_factor_dense``): a chain of
+    fronts, the first being the supernode [A11; A21]."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self.handle = ctx, handle
+        L = ctx.lib
+        nf = ctypes.c_int32()
+        arr = ctypes.c_void_p()
+        _check("ctp_chain_fronts", L.ctp_chain_fronts(handle, ctypes.byref(nf), ctypes.byref(arr)))
+        self.nf = int(nf.value)
+        self.fronts = ctypes.cast(arr, ctypes.POINTER(SFront))
+        e = np.zeros(self.nf, np.int32)
+        p = np.zeros(self.nf, np.int32)
+        piv = np.zeros(self.nf, np.int32)
+        _check("ctp_chain_info", L.ctp_chain_info(handle, self.nf, e.ctypes.data, p.ctypes.data,
+                                                  piv.ctypes.data))
+        self.nelim, self.p, self.pivot = e, p, piv
+
+    def destroy(self):
+        if self.handle:
+            self.ctx.lib.ctp_chain_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def factor_dense(ctx: Context, M, N, ldm, p_first, opt_first, w_rest, opt_rest, stream=None):
+    """Factor the dense symmetric matrix M (device tensor holding it column-major,
+    lower triangle read) in place as a chain of fronts; returns a ``Chain``."""
+    h = ctypes.c_void_p()
+    _check("ctp_factor_dense",
+           ctx.lib.ctp_factor_dense(ctx.handle, N, _ptr(M), ldm, p_first, ctypes.byref(opt_first),
+                                    w_rest, ctypes.byref(opt_rest), ctypes.byref(h),
+                                    _stream(stream)))
+    return Chain(ctx, h)
+
+
+def solve_workspace(ctx: Context, nmax, nrhs):
+    import torch
+    b = ctypes.c_size_t()
+    _check("ctp_solve_workspace_size", ctx.lib.ctp_solve_workspace_size(nmax, nrhs, ctypes.byref(b)))
+    return torch.empty(max(b.value, 1), dtype=torch.uint8, device=f"cuda:{ctx.device}")
+
+
+def refine_workspace(ctx: Context, N, nmax, nrhs):
+    import torch
+    b = ctypes.c_size_t()
+    _check("ctp_refine_workspace_size",
+           ctx.lib.ctp_refine_workspace_size(N, nmax, nrhs, ctypes.byref(b)))
+    return torch.empty(max(b.value, 1), dtype=torch.uint8, device=f"cuda:{ctx.device}")
+
+
+def solve(ctx: Context, fronts, nf, N, nrhs, X, ldx, ws, stream=None):
+    """X <- M^{-1} X (device tensor, column-major N x nrhs) with the fronts' factors."""
+    _check("ctp_solve", ctx.lib.ctp_solve(ctx.handle, nf, ctypes.cast(fronts, ctypes.c_void_p), N,
+                                          nrhs, _ptr(X), ldx, _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def backward_error(ctx: Context, N, M, ldm, nrhs, B, ldb, X, ldx, berr, ws, stream=None):
+    """Section 7 backward error per right-hand side into the device tensor berr."""
+    _check("ctp_backward_error",
+           ctx.lib.ctp_backward_error(ctx.handle, N, _ptr(M), ldm, nrhs, _ptr(B), ldb, _ptr(X), ldx,
+                                      _ptr(berr), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def refine(ctx: Context, fronts, nf, N, M, ldm, nrhs, B, ldb, X, ldx, ws, max_steps=10, tol=1e-14,
+           stream=None):
+    """Solve with iterative refinement; returns (history of backward errors as
+    a (steps+1) x nrhs array, corrections made)."""
+    hist = np.zeros((max_steps + 1) * nrhs)
+    steps = ctypes.c_int32()
+    _check("ctp_refine",
+           ctx.lib.ctp_refine(ctx.handle, nf, ctypes.cast(fronts, ctypes.c_void_p), N, _ptr(M), ldm,
+                              nrhs, _ptr(B), ldb, _ptr(X), ldx, max_steps, tol, hist.ctypes.data,
+                              ctypes.byref(steps), _ptr(ws), ws.numel(), _stream(stream)))
+    k = int(steps.value)
+    return hist[:(k + 1) * nrhs].reshape(k + 1, nrhs), k
 
 
 class Batch:

@@ -55,3 +55,32 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.ctp_create(ctypes.byref(h), 0) == ctp.CTP_ECUDA
     assert not h.value
+
+
+def test_system_entry_points_check_arguments(lib):
+    sz = ctypes.c_size_t()
+    assert lib.ctp_solve_workspace_size(-1, 1, ctypes.byref(sz)) == ctp.CTP_EINVAL
+    assert lib.ctp_solve_workspace_size(100, 0, ctypes.byref(sz)) == ctp.CTP_EINVAL
+    assert lib.ctp_solve_workspace_size(100, 2, ctypes.byref(sz)) == ctp.CTP_OK and sz.value > 0
+    assert lib.ctp_refine_workspace_size(0, 10, 1, ctypes.byref(sz)) == ctp.CTP_EINVAL
+    assert lib.ctp_solve(None, 0, None, 10, 1, None, 10, None, 0, None) == ctp.CTP_EINVAL
+    assert lib.ctp_backward_error(None, 10, None, 10, 1, None, 10, None, 10, None, None, 0,
+                                  None) == ctp.CTP_EINVAL
+    steps = ctypes.c_int32()
+    assert lib.ctp_refine(None, 0, None, 10, None, 10, 1, None, 10, None, 10, 10, 1e-14, None,
+                          ctypes.byref(steps), None, 0, None) == ctp.CTP_EINVAL
+    opt = ctp.options()
+    h = ctypes.c_void_p()
+    assert lib.ctp_factor_dense(None, 10, None, 10, 4, ctypes.byref(opt), 4, ctypes.byref(opt),
+                                ctypes.byref(h), None) == ctp.CTP_EINVAL
+    nf = ctypes.c_int32()
+    arr = ctypes.c_void_p()
+    assert lib.ctp_chain_fronts(None, ctypes.byref(nf), ctypes.byref(arr)) == ctp.CTP_EINVAL
+    assert lib.ctp_chain_destroy(None) == ctp.CTP_OK
+
+
+def test_sfront_mirror_matches_header():
+    """The Python mirror of ctp_sfront has the header's field order and size."""
+    assert ctypes.sizeof(ctp.SFront) == 8 + 4 + 4 + 8 + 8 + 5 * 8
+    assert [f for f, _ in ctp.SFront._fields_] == ["n", "p", "reserved", "L", "ldl", "perm", "piv",
+                                                  "D", "nelim", "rows"]

@@ -324,6 +324,64 @@ def test_form_tensor_cores_bf16(ctx, pivot, smode, n, p):
     assert np.all(np.triu(got["S"], 1) == 0)
 
 
+@pytest.mark.parametrize("smode", ["fp32", "fp32_packed", "fp32_tiled"])
+@pytest.mark.parametrize("n,p", [(600, 40), (2000, 64), (3000, 256), (700, 200)])
+def test_form_tensor_cores_bf16x3(ctx, smode, n, p):
+    """Split-operand form (hi*hi + hi*lo + lo*hi): |dS| <= 2^-13 |W21||L21|^T
+    elementwise, and at least 64 times below the plain BF16 form's largest
+    error on the same supernode (a dropped correction product fails this)."""
+    from paper_1305_2353_gb300 import ctp
+    A = _tough(n, p, 5)
+    ref = O.factor(A, p, "relaxed")
+    e = ref["nelim"]
+    L21 = ref["A"][p:, :e]
+    _, Dm, _ = O.unpack(ref, p)
+    S = O.form(L21, ref["piv"][:e], ref["D"])
+    lo = np.tril(np.ones_like(S, dtype=bool))
+    errs = {}
+    for prec in ("bf16", "bf16x3"):
+        sn = ctp.Supernode(ctx, A, p, ctp.options(pivot="relaxed", prec=prec, smode=smode))
+        sn.run()
+        torch.cuda.synchronize()
+        got = sn.result()
+        assert got["info"] == 0 and got["nelim"] == e
+        errs[prec] = np.abs(got["S"] - S)[lo]
+        assert np.all(np.triu(got["S"], 1) == 0)
+    bound = _bf16_bound(L21 @ Dm, L21)[lo]
+    assert np.all(errs["bf16x3"] <= 2.0 ** -13 * bound + 1e-30)
+    assert errs["bf16x3"].max() * 64 <= errs["bf16"].max()
+
+
+def test_form_tensor_cores_bf16x3_large(ctx):
+    """n = 40000, p = 256: the column-panel walk of the split form (more column
+    blocks than twice the SMs), sampled entries against the oracle."""
+    from paper_1305_2353_gb300 import ctp
+    n, p = 40000, 256
+    A = inputs.single_large(3, n=n, p=p)
+    ref = O.factor(A, p, "relaxed")
+    sn = ctp.Supernode(ctx, A, p, ctp.options(pivot="relaxed", prec="bf16x3", smode="fp32_tiled"))
+    sn.run()
+    torch.cuda.synchronize()
+    assert ctx.read_info(sn.ws) == 0
+    m, e = n - p, ref["nelim"]
+    rng = np.random.default_rng(1)
+    ii = rng.integers(0, m, 6000)
+    jj = rng.integers(0, m, 6000)
+    ii, jj = np.maximum(ii, jj), np.minimum(ii, jj)
+    ii = np.r_[ii, np.arange(m - 300, m), np.arange(0, m, 997)]
+    jj = np.r_[jj, np.arange(m - 300, m), np.arange(0, m, 997)]
+    L21 = ref["A"][p:, :e]
+    want = O.form_entries(L21, ref["piv"][:e], ref["D"], ii, jj)
+    nb = (m + 127) // 128
+    bi, bj = ii // 128, jj // 128
+    blk = bj * nb - bj * (bj - 1) // 2 + (bi - bj)
+    idx = blk * 16384 + (jj % 128) * 128 + (ii % 128)
+    got = sn.S[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    _, Dm, _ = O.unpack(ref, p)
+    bound = np.einsum("tk,tk->t", np.abs((L21 @ Dm)[ii]), np.abs(L21[jj]))
+    assert np.all(np.abs(got - want) <= 2.0 ** -13 * bound)
+
+
 def test_form_tensor_cores_large(ctx):
     """n = 20000, p = 256, relaxed (e = 256): 610 tiles per row band region, sampled
     entries of S against the oracle, including the diagonal and the last rows."""
