@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--pivot", default="relaxed", choices=["strict", "relaxed", "restricted"])
     ap.add_argument("--smode", default="fp64_packed",
                     choices=["none", "fp32", "fp64", "fp32_packed", "fp64_packed", "fp32_tiled"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16"],
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16", "bf16x3"],
                     help="Form arithmetic: FP64, or BF16 tensor cores with FP32 accumulation")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -75,6 +75,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched workload (8192 uneven supernodes, graph replay)")
     ap.add_argument("--batch-count", type=int, default=8192)
+    ap.add_argument("--no-system", action="store_true",
+                    help="skip the complete-system leg (2-node embedding, refinement)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the extra measurement with the Form on the tensor cores")
     return ap.parse_args()
@@ -218,11 +220,15 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
         work = 8.0 * m * p
         bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
         achieved = work / t / 1e9
-    elif name == "form_tc_bf16":
+    elif name in ("form_tc_bf16", "form_tc_bf16x3"):
         # S written as FP32 (lower triangle) dominates the bytes: 128 flop/byte at
-        # e = 256, below the BF16 ridge, so the HBM roofline bounds this kernel
+        # e = 256 (three products per flop of S for the split form: 384), below
+        # the BF16 ridge, so the HBM roofline bounds this kernel
         _, form = flops_model(n, p, e)
-        work = 4.0 * m * (m + 1) / 2 + 2 * 2.0 * m * ((p + 63) // 64 * 64)
+        split = name.endswith("x3")
+        work = 4.0 * m * (m + 1) / 2 + (2 if split else 1) * 2 * 2.0 * m * ((p + 63) // 64 * 64)
+        if split:
+            form *= 3  # tensor-core products actually executed
         bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
         achieved = work / t / 1e9
         tensor = form / t / 1e12
@@ -413,6 +419,78 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()}}
 
 
+def refine_embedded(ctx, dev, A, prec, b, mr="tpp", w_rest=256, seed=0):
+    """Embed supernode A in its complete system M (inputs.two_node), factor M on
+    the GPU as a chain of fronts (the first the supernode, its Form in `prec`),
+    refine with FP64 residuals.  Returns timings, steps and backward errors."""
+    import torch
+    from paper_1305_2353_gb300 import ctp, inputs
+    M = inputs.two_node(A, seed)
+    N, p = M.shape[0], A.shape[1]
+    Mlow = ctp.colmajor(np.tril(M), dev)
+    Md = ctp.colmajor(M, dev)
+    B = ctp.colmajor(b, dev)
+    X = torch.zeros_like(B)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ch = ctp.factor_dense(ctx, Md, N, N, p, ctp.options(pivot="strict", prec=prec), w_rest,
+                          ctp.options(pivot=mr))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ws = ctp.refine_workspace(ctx, N, N, b.shape[1])
+    ctx.profile_begin()
+    t2 = time.perf_counter()
+    hist, k = ctp.refine(ctx, ch.fronts, ch.nf, N, Mlow, N, b.shape[1], B, N, X, N, ws)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    kern = ctx.profile_end()
+    out = {"prec_first_front": prec, "fronts": ch.nf, "nelim_first": int(ch.nelim[0]),
+           "factor_ms": (t1 - t0) * 1e3, "refine_ms": (t3 - t2) * 1e3, "corrections": k,
+           "bwd_err_history": [float(v) for v in hist.max(axis=1)],
+           "kernels": {kk: {"launches": v[0], "ms": v[1]} for kk, v in kern.items()}}
+    ch.destroy()
+    del Md, Mlow, B, X, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_system(ctx, dev, inputs):
+    """The complete-system leg: the n = 2000, p = 64 supernode with eight tiny
+    columns embedded in its 2000 x 2000 system (A22 symmetric N(0,1)), strict
+    compressed pivoting on the supernode, threshold partial pivoting on the
+    rest, Section 7 backward error after FP64 refinement (at most ten
+    corrections, stop at 1e-14), for each precision of the supernode's Form."""
+    A = inputs.single_small(0)
+    b = np.random.default_rng(1).standard_normal((A.shape[0], 1))
+    out = {"workload": "n=2000 p=64 supernode (8 columns scaled 1e-8) in its 2-node system, "
+                       "1 RHS N(0,1), tol 1e-14, <= 10 corrections"}
+    for prec in ("fp64", "bf16x3", "bf16"):
+        out[prec] = refine_embedded(ctx, dev, A, prec, b)
+    return out
+
+
+def batch_accuracy(ctx, fronts, count=12, seed=0):
+    """Equal-accuracy check of the batch's precisions: a seeded sample of the
+    batch's fronts (spread over sizes), each embedded in its complete system and
+    refined; the worst final backward error and the most corrections per precision."""
+    rng = np.random.default_rng(seed)
+    order = np.argsort([f.shape[0] * f.shape[1] for f in fronts])
+    pick = order[np.linspace(0, len(order) - 1, count).astype(int)]
+    res = {"sample": f"{count} fronts spread over n*p (n from {fronts[pick[0]].shape[0]} to "
+                     f"{fronts[pick[-1]].shape[0]}), 2-node systems, 1 RHS, tol 1e-14"}
+    import torch
+    for prec in ("fp64", "bf16x3", "bf16"):
+        worst, steps = 0.0, 0
+        for k in pick:
+            A = fronts[k]
+            b = rng.standard_normal((A.shape[0], 1))
+            r = refine_embedded(ctx, "cuda", A, prec, b, seed=int(k))
+            worst = max(worst, r["bwd_err_history"][-1])
+            steps = max(steps, r["corrections"])
+        res[prec] = {"max_bwd_err": worst, "max_corrections": steps}
+    return res
+
+
 def run_native(a):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -434,16 +512,28 @@ def run_native(a):
 
     main = measure(a, ctx, dev, A_host, a.prec, a.smode, a.steps, a.warmup,
                    0 if a.no_e2e else a.steps, peaks, world, dist)
-    mixed = None
+    mixed = mixed_bf16 = None
     if not a.no_mixed and a.prec == "fp64":
-        mx = measure(a, ctx, dev, A_host, "bf16", "fp32_tiled", max(a.steps, 5), max(a.warmup, 3),
-                     0 if a.no_e2e else max(a.steps, 5), peaks, world, dist)
-        mixed = {"value": mx["value"], "unit": "GFLOP/s", "ms_per_step": mx["ms"] / max(a.steps, 5),
-                 "prec": "Form on tensor cores: bf16 x bf16 -> f32, S fp32 in 128x128 blocks; "
-                         "the rest f64",
-                 "roofline": mx["roofline"], "e2e": mx["e2e"], "gpu_launches": mx["launches"],
-                 "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in mx["kern"].items()},
-                 "clocks": mx["clocks"]}
+        def mixed_leg(prec, desc):
+            k = max(a.steps, 5)
+            mx = measure(a, ctx, dev, A_host, prec, "fp32_tiled", k, max(a.warmup, 3),
+                         0 if a.no_e2e else k, peaks, world, dist)
+            return {"value": mx["value"], "unit": "GFLOP/s", "ms_per_step": mx["ms"] / k,
+                    "prec": desc, "roofline": mx["roofline"], "e2e": mx["e2e"],
+                    "gpu_launches": mx["launches"],
+                    "kernels": {kk: {"launches": v[0], "ms": v[1]} for kk, v in mx["kern"].items()},
+                    "clocks": mx["clocks"]}
+        mixed = mixed_leg("bf16x3", "Form on tensor cores with split operands: hi*hi + hi*lo + "
+                                    "lo*hi (bf16 x bf16 -> f32), S fp32 in 128x128 blocks; the "
+                                    "rest f64 (refines to the FP64 backward error, see "
+                                    "complete_system)")
+        mixed_bf16 = mixed_leg("bf16", "Form on tensor cores: bf16 x bf16 -> f32 (single "
+                                       "product), S fp32 in 128x128 blocks; the rest f64 "
+                                       "(refinement does not reach 1e-12, see complete_system)")
+
+    system = None
+    if not a.no_system and rank == 0:
+        system = measure_system(ctx, dev, inputs)
 
     batch = None
     if not a.no_batch:
@@ -456,7 +546,9 @@ def run_native(a):
                  "timing": "CUDA graph of the batch call, replayed; inputs restored outside the "
                            "timed events"}
         batch["fp64"] = measure_batch(a, ctx, dev, fronts, "fp64", "fp64_packed", 3, 2)
-        batch["mixed"] = measure_batch(a, ctx, dev, fronts, "bf16", "fp32_tiled", 3, 2)
+        batch["mixed"] = measure_batch(a, ctx, dev, fronts, "bf16x3", "fp32_tiled", 3, 2)
+        batch["mixed_bf16"] = measure_batch(a, ctx, dev, fronts, "bf16", "fp32_tiled", 3, 2)
+        batch["accuracy"] = batch_accuracy(ctx, fronts)
         del fronts
 
     tpp = None
@@ -501,6 +593,8 @@ def run_native(a):
             "clocks": main["clocks"],
             "fp64_dgemm_tflops": peaks["fp64_tflops"],
             "mixed": mixed,
+            "mixed_bf16": mixed_bf16,
+            "complete_system": system,
             "tpp_comparator": tpp,
             "batch": batch,
         }

@@ -13,7 +13,7 @@ enum KernelId {
     K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP,
     K_B_PREPARE, K_B_COMPRESS, K_B_FACTOR_G1, K_B_FACTOR_G2, K_B_FACTOR_G4, K_B_FACTOR_G8,
     K_B_FACTOR_G16, K_B_SOLVE, K_B_FORM, K_W21, K_SYS_FWD, K_SYS_BWD, K_SYMV, K_BERR, K_AXPY,
-    K_NUM_IDS
+    K_FORM_TC3, K_NUM_IDS
 };
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
                                        "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16",
@@ -21,7 +21,7 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
                                        "batch_factor_g1", "batch_factor_g2", "batch_factor_g4",
                                        "batch_factor_g8", "batch_factor_g16", "batch_solve_fp64",
                                        "batch_form", "w21_from_l", "sys_forward", "sys_backward",
-                                       "symv_residual", "backward_error", "axpy"};
+                                       "symv_residual", "backward_error", "axpy", "form_tc_bf16x3"};
 }  // namespace
 
 struct ctp_ctx {
@@ -269,7 +269,7 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
         }));
     if (opt->smode != CTP_S_NONE && m > 0) {
         if (tc)
-            CTP_CUDA(timed(ctx, K_FORM_TC, st, [&] {
+            CTP_CUDA(timed(ctx, lo_off ? K_FORM_TC3 : K_FORM_TC, st, [&] {
                 return launch_form_tc(Wb, Lbf, lo_off, m, Kp, nelim, (float *)S, lds,
                                       opt->smode == CTP_S_FP64_SUB ? 3
                                       : opt->smode == CTP_S_FP32_TILED ? 2 : (packed ? 1 : 0), info,
