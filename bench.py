@@ -75,6 +75,9 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched workload (8192 uneven supernodes, graph replay)")
     ap.add_argument("--batch-count", type=int, default=8192)
+    ap.add_argument("--batch-eager", action="store_true",
+                    help="time the batch by direct calls instead of CUDA-graph replay "
+                         "(for profilers that cannot follow graph replays)")
     ap.add_argument("--no-system", action="store_true",
                     help="skip the complete-system leg (2-node embedding, refinement)")
     ap.add_argument("--no-mixed", action="store_true",
@@ -245,6 +248,13 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
         src = ("nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table; no FP64 entry in "
                "MEASURED_PEAKS.json); cuBLAS DGEMM 4096^3 in this run: %.3f" % peaks["fp64_tflops"])
         achieved = work / t / 1e12
+    elif name == "factor_cluster":
+        # right-looking FP64 update of [A11; C] per accepted pivot: ~2p(2p - k)
+        # FLOP for pivot k (latency-bound: one cluster barrier per round)
+        work = sum(2.0 * p * (2 * p - k) for k in range(e))
+        bound, unit, peak = "alu", "TFLOP/s", 1.25
+        src = "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table)"
+        achieved = work / t / 1e12
     else:
         return None
     traffic = None
@@ -288,6 +298,19 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
 
     def step(buf):
         ctx.factor_supernode(buf, n, p, n, opt, perm, piv, D, nelim, S, max(m, 1), ws, stream)
+
+    tuned = None
+    if prec != "fp64" and smode != "none":
+        # the library's autotuner picks the tensor-core Form's tile walk and the
+        # pivot search's cluster width for this workload (untimed)
+        names = {1: "round_robin", 2: "chunks", 3: "panels"}
+        cand = [(w, g) for w in (1, 2, 3) for g in (0, 8)]
+        tms, best = ctp.autotune_supernode(ctx, bufs[0], n, p, n, opt, perm, piv, D, nelim, S,
+                                           max(m, 1), ws, [ctp.TUNE_FORM_WALK, ctp.TUNE_FACTOR_G],
+                                           cand, stream)
+        tuned = {"form_walk": names[cand[best][0]], "factor_G": cand[best][1] or "auto",
+                 "candidates_ms": {f"{names[w]}/G{g or 'auto'}": float(t)
+                                   for (w, g), t in zip(cand, tms)}}
 
     for i in range(warmup):
         step(bufs[i])
@@ -364,8 +387,11 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
     torch.cuda.empty_cache()
     top = max(kern.items(), key=lambda kv: kv[1][1])
     roof = kernel_roofline(top[0], top[1][0], top[1][1], a, e, peaks)
+    ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
+    ctx.tune_set(ctp.TUNE_FACTOR_G, 0)
     return dict(value=value, ms=ms, e=e, fs=fs, form=form, flops_step=flops_step, kern=kern,
-                clocks=clk, e2e=e2e, roofline=roof, launches=sum(v[0] for v in kern.values()))
+                clocks=clk, e2e=e2e, roofline=roof, launches=sum(v[0] for v in kern.values()),
+                autotune=tuned)
 
 
 def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
@@ -378,6 +404,15 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
     b = ctp.Batch(ctx, fronts, [f.shape[1] for f in fronts], opt)
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
+    # the library's autotuner: cluster budget of the pivot search and the
+    # tensor-core Form's tile walk, timed on this batch (untimed here)
+    names = {0: "auto", 1: "round_robin", 2: "chunks"}
+    kbs = [64, 100, 160, 220]
+    walks = [2, 1] if prec != "fp64" else [0]
+    cand = [(k, w) for k in kbs for w in walks]
+    tms, best = b.autotune([ctp.TUNE_BATCH_SMEM_KB, ctp.TUNE_FORM_WALK], cand)
+    tuned = {"smem_kb": cand[best][0], "form_walk": names[cand[best][1]],
+             "candidates_ms": {f"{k}KB/{names[w]}": float(t) for (k, w), t in zip(cand, tms)}}
     b.run()
     torch.cuda.synchronize()
     # kernel split from one profiled run outside the graph
@@ -387,19 +422,24 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
     torch.cuda.synchronize()
     kern = ctx.profile_end()
     flags = b.flags()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        b.run(stream=stream)
+    if a.batch_eager:
+        g = None
+        launch = b.run
+    else:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            b.run(stream=stream)
+        launch = g.replay
     for _ in range(warmup):
         b.reset()
-        g.replay()
+        launch()
     torch.cuda.synchronize()
     total = 0.0
     for _ in range(steps):
         b.reset()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        g.replay()
+        launch()
         e1.record()
         torch.cuda.synchronize()
         total += e0.elapsed_time(e1)
@@ -411,11 +451,13 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
         form += f2 if smode != "none" else 0
     ms = total / steps
     del g, b
+    ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 200)
+    ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
     torch.cuda.empty_cache()
     return {"value": (fs + form) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_batch": ms,
             "prec": prec, "S": smode, "factor_solve_flops": fs, "form_flops": form,
             "nelim_total": int(ne.sum()), "p_total": int(sum(f.shape[1] for f in fronts)),
-            "device_flags_nonzero": int((flags != 0).sum()),
+            "device_flags_nonzero": int((flags != 0).sum()), "autotune": tuned,
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()}}
 
 
@@ -522,7 +564,7 @@ def run_native(a):
                     "prec": desc, "roofline": mx["roofline"], "e2e": mx["e2e"],
                     "gpu_launches": mx["launches"],
                     "kernels": {kk: {"launches": v[0], "ms": v[1]} for kk, v in mx["kern"].items()},
-                    "clocks": mx["clocks"]}
+                    "clocks": mx["clocks"], "autotune": mx["autotune"]}
         mixed = mixed_leg("bf16x3", "Form on tensor cores with split operands: hi*hi + hi*lo + "
                                     "lo*hi (bf16 x bf16 -> f32), S fp32 in 128x128 blocks; the "
                                     "rest f64 (refines to the FP64 backward error, see "
@@ -544,7 +586,7 @@ def run_native(a):
                  "sum_np": int((sh[:, 0] * sh[:, 1]).sum()), "max_n": int(sh[:, 0].max()),
                  "median_p": int(np.median(sh[:, 1])), "median_m": int(np.median(sh[:, 0] - sh[:, 1])),
                  "timing": "CUDA graph of the batch call, replayed; inputs restored outside the "
-                           "timed events"}
+                           "timed events; launch settings chosen by the library's autotuner first"}
         batch["fp64"] = measure_batch(a, ctx, dev, fronts, "fp64", "fp64_packed", 3, 2)
         batch["mixed"] = measure_batch(a, ctx, dev, fronts, "bf16x3", "fp32_tiled", 3, 2)
         batch["mixed_bf16"] = measure_batch(a, ctx, dev, fronts, "bf16", "fp32_tiled", 3, 2)

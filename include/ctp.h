@@ -345,6 +345,69 @@ ctp_status ctp_chain_info(const ctp_chain *chain, int32_t cap, int32_t *nelim, i
                           int32_t *pivot);
 ctp_status ctp_chain_destroy(ctp_chain *chain);
 
+/* ------------------------------------------------------------------------ */
+/* Tuning knobs of a context (no counterpart in the paper: launch choices of
+ * the GB300 kernels).  They change how work is scheduled, never the result.
+ *
+ * CTP_TUNE_FORM_WALK: the order in which the persistent tensor-core Form
+ *   kernel's CTAs take the tiles of S (a ctp_walk value):
+ *   CTP_WALK_AUTO (default): panels for the split form when S has at least
+ *     two column blocks per SM, contiguous runs otherwise;
+ *   CTP_WALK_ROUND_ROBIN: tile t to CTA t mod G down the column-block-major
+ *     list (all CTAs in one column block at a time);
+ *   CTP_WALK_CHUNKS: CTA c takes the c-th of G equal contiguous runs of that
+ *     list (consecutive tiles share the resident L21 block);
+ *   CTP_WALK_PANELS: column blocks G at a time, one per CTA, walked down in
+ *     step (the W21 blocks are shared through L2).
+ * CTP_TUNE_BATCH_SMEM_KB: shared memory (KB, 48..220; default 200) a CTA of
+ *   the batched pivot search may hold (capped at what the kernel can take
+ *   beside its static shared memory, about 190 KB); each front gets the
+ *   narrowest cluster (1..16 CTAs) whose CTAs fit it.  A larger budget means fewer CTAs per
+ *   front (cheaper cluster barriers, fewer parallel tests, fewer co-resident
+ *   clusters).  Read when a batch plan is created.
+ * CTP_TUNE_FACTOR_G: cluster width of the single-supernode pivot search
+ *   (0 = by p, the default; else 1, 2, 4, 8 or 16, widened when the columns do
+ *   not fit on chip). */
+typedef enum {
+    CTP_TUNE_FORM_WALK = 0,
+    CTP_TUNE_BATCH_SMEM_KB = 1,
+    CTP_TUNE_FACTOR_G = 2
+} ctp_tune_key;
+typedef enum {
+    CTP_WALK_AUTO = 0,
+    CTP_WALK_ROUND_ROBIN = 1,
+    CTP_WALK_CHUNKS = 2,
+    CTP_WALK_PANELS = 3
+} ctp_walk;
+ctp_status ctp_tune_set(ctp_ctx *ctx, int32_t key, int32_t value);
+ctp_status ctp_tune_get(const ctp_ctx *ctx, int32_t key, int32_t *value);
+
+/* The autotuner: time the real calls on the caller's own inputs for each
+ * candidate setting of the tuning knobs and keep the fastest in the context.
+ * A candidate sets the nk knobs keys[0..nk) to values[c*nk .. c*nk+nk).
+ * The inputs are backed up once (a device copy the tuner allocates and frees)
+ * and restored before every trial and at the end, so on return they hold
+ * their original values; the outputs hold the last trial's results.  Each
+ * trial is one warm-up call and one timed call (CUDA events on `stream`).
+ *
+ * ctp_autotune_batch: trials of ctp_factor_batch, each with a plan created
+ *   under the candidate's knobs.  fronts_host / fronts_dev: the same
+ *   descriptors in host and device memory.
+ * ctp_autotune_supernode: trials of one ctp_factor_supernode call (arguments
+ *   as there).
+ * ms_out[c] (host, optional) receives each candidate's time, *best (optional)
+ * the index chosen.  On failure the knobs keep their previous values. */
+ctp_status ctp_autotune_batch(ctp_ctx *ctx, int32_t nb, const int64_t *n_host, const int32_t *p_host,
+                              const ctp_options *opt, const ctp_front *fronts_host,
+                              const ctp_front *fronts_dev, int32_t nk, const int32_t *keys,
+                              int32_t ncand, const int32_t *values, double *ms_out, int32_t *best,
+                              void *stream);
+ctp_status ctp_autotune_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, int64_t lda,
+                                  const ctp_options *opt, int32_t *perm, int32_t *piv, double *D,
+                                  int32_t *nelim, void *S, int64_t lds, void *workspace,
+                                  size_t ws_bytes, int32_t nk, const int32_t *keys, int32_t ncand,
+                                  const int32_t *values, double *ms_out, int32_t *best, void *stream);
+
 /* Optional per-kernel timing.  Between ctp_profile_begin() and ctp_profile_end()
  * every kernel this library launches is bracketed by two CUDA events recorded
  * on its launch stream (at most 4096 launches are recorded).  ctp_profile_end()

@@ -27,6 +27,9 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
 struct ctp_ctx {
     int device;
     int num_sms;
+    int form_walk;   // CTP_TUNE_FORM_WALK
+    int batch_smem_kb; // CTP_TUNE_BATCH_SMEM_KB
+    int factor_g;      // CTP_TUNE_FACTOR_G
     bool profiling;
     int nrec;
     int rec_id[kMaxRec];
@@ -48,6 +51,8 @@ static cudaError_t timed(ctp_ctx *ctx, int id, cudaStream_t st, F &&launch) {
 }
 
 namespace ctp {
+
+int ctx_batch_smem_kb(const ctp_ctx *ctx) { return ctx->batch_smem_kb; }
 
 WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     WsLayout L;
@@ -101,6 +106,9 @@ ctp_status ctp_create(ctp_ctx **ctx, int32_t device) {
     if (c == nullptr) return CTP_ENOMEM;
     c->device = device;
     c->num_sms = sms;
+    c->form_walk = CTP_WALK_AUTO;
+    c->batch_smem_kb = 200;
+    c->factor_g = 0;
     c->profiling = false;
     c->nrec = 0;
     c->events_made = false;
@@ -122,6 +130,40 @@ static ctp_status check_opts(const ctp_options *opt) {
     if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
     if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16 && opt->prec != CTP_BF16X3) return CTP_EINVAL;
     if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP64_SUB) return CTP_EINVAL;
+    return CTP_OK;
+}
+
+ctp_status ctp_tune_set(ctp_ctx *ctx, int32_t key, int32_t value) {
+    if (ctx == nullptr) return CTP_EINVAL;
+    if (key == CTP_TUNE_FORM_WALK) {
+        if (value < CTP_WALK_AUTO || value > CTP_WALK_PANELS) return CTP_EINVAL;
+        ctx->form_walk = value;
+        return CTP_OK;
+    }
+    if (key == CTP_TUNE_BATCH_SMEM_KB) {
+        if (value < 48 || value > 220) return CTP_EINVAL;
+        ctx->batch_smem_kb = value;
+        return CTP_OK;
+    }
+    if (key == CTP_TUNE_FACTOR_G) {
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return CTP_EINVAL;
+        ctx->factor_g = value;
+        return CTP_OK;
+    }
+    return CTP_EINVAL;
+}
+
+ctp_status ctp_tune_get(const ctp_ctx *ctx, int32_t key, int32_t *value) {
+    if (ctx == nullptr || value == nullptr) return CTP_EINVAL;
+    if (key == CTP_TUNE_FORM_WALK)
+        *value = ctx->form_walk;
+    else if (key == CTP_TUNE_BATCH_SMEM_KB)
+        *value = ctx->batch_smem_kb;
+    else if (key == CTP_TUNE_FACTOR_G)
+        *value = ctx->factor_g;
+    else
+        return CTP_EINVAL;
     return CTP_OK;
 }
 
@@ -262,7 +304,7 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
         fa.abs_update = 0;
         fa.C = nullptr;
     }
-    CTP_CUDA(timed(ctx, K_FACTOR, st, [&] { return launch_factor_cluster(fa, st); }));
+    CTP_CUDA(timed(ctx, K_FACTOR, st, [&] { return launch_factor_cluster(fa, ctx->factor_g, st); }));
     if (m > 0)
         CTP_CUDA(timed(ctx, K_SOLVE, st, [&] {
             return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, Wb, Lbf, Kp, lo_off, st);
@@ -273,7 +315,7 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
                 return launch_form_tc(Wb, Lbf, lo_off, m, Kp, nelim, (float *)S, lds,
                                       opt->smode == CTP_S_FP64_SUB ? 3
                                       : opt->smode == CTP_S_FP32_TILED ? 2 : (packed ? 1 : 0), info,
-                                      ctx->num_sms, st);
+                                      ctx->num_sms, ctx->form_walk, st);
             }));
         else
             CTP_CUDA(timed(ctx, K_FORM, st, [&] {

@@ -181,13 +181,17 @@ struct ctp_plan {
     std::vector<unsigned char> blob;  // tables, in workspace order (up to off_sections)
 };
 
-static int batch_cluster_width(int p, int R) {
-    // narrowest cluster whose shared memory (columns of [A11; C] plus two pivot
-    // columns) stays under ~100 KB, so that two clusters' CTAs share an SM
+static int batch_cluster_width(int p, int R, int budget_kb) {
+    // narrowest cluster whose shared memory per CTA (its columns of [A11; C]
+    // plus two pivot columns) fits the budget (100 KB by default, so that two
+    // clusters' CTAs share an SM), and never more than the kernel can take
+    size_t budget = (size_t)budget_kb * 1024;
+    const size_t cap = factor_batch_max_dynamic_smem();
+    if (budget > cap) budget = cap;
     for (int G = 1; G <= 16; G <<= 1) {
         const int ncl = (p + G - 1) / G;
         const size_t smem = sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R));
-        if (smem <= 100 * 1024) return G;
+        if (smem <= budget) return G;
     }
     return 16;
 }
@@ -257,7 +261,7 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     std::vector<int> pmaxG(5, 1);
     for (int f = 0; f < nb; f++) {
         const int R = opt->pivot == CTP_PIV_STRICT ? tab[f].p : 0;
-        const int G = batch_cluster_width(tab[f].p, R);
+        const int G = batch_cluster_width(tab[f].p, R, ctx_batch_smem_kb(ctx));
         const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4;
         byG[gi].push_back(f);
         pmaxG[gi] = std::max(pmaxG[gi], tab[f].p);

@@ -29,6 +29,8 @@ struct WsLayout {
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms);
+int ctx_batch_smem_kb(const ctp_ctx *ctx);  // CTP_TUNE_BATCH_SMEM_KB of a context
+size_t factor_batch_max_dynamic_smem();     // dynamic shared memory the batched pivot search can take
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns cudaError_t of the launch)
@@ -55,7 +57,7 @@ struct FactorArgs {
     double *D, *Dinv;
     int32_t *info;
 };
-cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st);
+cudaError_t launch_factor_cluster(const FactorArgs &a, int G /* 0: by p */, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // batched path: per-front table (built on the host by the plan, uploaded into
@@ -138,7 +140,7 @@ int form_tc_kpad(int p);
 cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64_t m, int Kp,
                            const int32_t *nelim, float *S, int64_t lds,
                            int layout /* 0 full, 1 packed, 2 tiled, 3 subtract from FP64 */,
-                           int32_t *info, int num_sms, cudaStream_t st);
+                           int32_t *info, int num_sms, int walk /* ctp_walk */, cudaStream_t st);
 
 cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, int64_t ldw,
                              int64_t m, const int32_t *nelim, void *S, int64_t lds, int smode,

@@ -576,10 +576,11 @@ static size_t factor_smem(int p, int R, int G) {
     return sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R));
 }
 
-cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st) {
-    // preferred cluster width by p: more CTAs give more FP64 lanes to the
-    // right-looking update; widen further if the columns do not fit on chip
-    int G = a.p > 128 ? 16 : (a.p > 64 ? 8 : (a.p > 16 ? 4 : 1));
+cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t st) {
+    // preferred cluster width by p (unless the caller asks for one): more CTAs
+    // give more FP64 lanes to the right-looking update, fewer make the cluster
+    // barriers cheaper; widen further if the columns do not fit on chip
+    int G = G_req > 0 ? G_req : (a.p > 128 ? 16 : (a.p > 64 ? 8 : (a.p > 16 ? 4 : 1)));
     while (factor_smem(a.p, a.R, G) > 160 * 1024 && G < 16) G <<= 1;
     size_t smem = factor_smem(a.p, a.R, G);
     cudaError_t err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -613,6 +614,23 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, cudaStream_t st) {
         G >>= 1;
     }
     return cudaLaunchKernelEx(&cfg, k_factor_cluster, a, G);
+}
+
+size_t factor_batch_max_dynamic_smem() {
+    // per-CTA opt-in limit minus what the kernel holds statically
+    static size_t cached = 0;
+    if (cached == 0) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, k_factor_cluster_batch) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 100 * 1024;
+        }
+        cached = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    }
+    return cached;
 }
 
 cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,

@@ -205,7 +205,10 @@ struct BatchTab {
 };
 
 // Which tiles a CTA takes.  mode 0: round robin over the column-block-major
-// tile list (all CTAs work down the same column block).  mode 1 (panels):
+// tile list (all CTAs work down the same column block).  mode 2 (chunks): CTA
+// c takes the c-th of G equal contiguous runs of that list, so consecutive
+// tiles of a CTA share their column block and its resident L21 block (the walk
+// for operands that fit in L2).  mode 1 (panels):
 // the column blocks are taken G at a time; CTA c owns one column block of
 // each panel (c, or G-1-c in odd panels, which evens out the work) and walks
 // it from the diagonal down, keeping its L21 block resident.  All CTAs then
@@ -215,6 +218,7 @@ struct BatchTab {
 struct Sched {
     int mode, nM, G, c;
     int64_t ntiles, nN;
+    int64_t t0, t1;  // mode 2: this CTA's run [t0, t1)
 };
 
 template <bool kBatch, int R>
@@ -222,8 +226,8 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
                                        int64_t lds1, int layout1, const BatchTab &bt, TileInfo &x) {
     int ti, tj;
     if (kBatch) {
-        const int64_t t = s.c + k * s.G;
-        if (t >= s.ntiles) return false;
+        const int64_t t = s.mode == 2 ? s.t0 + k : s.c + k * s.G;
+        if (t >= (s.mode == 2 ? s.t1 : s.ntiles)) return false;
         const int f = bt.item_front[t];
         const BFront b = bt.tab[f];
         decode_tile(t - b.f0, b.nM, R, ti, tj);
@@ -241,9 +245,9 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
         x.layout = 2;
         return true;
     }
-    if (s.mode == 0) {
-        const int64_t t = s.c + k * s.G;
-        if (t >= s.ntiles) return false;
+    if (s.mode != 1) {
+        const int64_t t = s.mode == 2 ? s.t0 + k : s.c + k * s.G;
+        if (t >= (s.mode == 2 ? s.t1 : s.ntiles)) return false;
         decode_tile(t, s.nM, R, ti, tj);
     } else {
         int64_t rem = k;
@@ -294,12 +298,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KB1 = kBatch ? 0 : (*nelim_p + kBK - 1) / kBK;
     Sched sc;
-    sc.mode = kBatch ? 0 : sched_mode;
+    sc.mode = sched_mode;
     sc.nM = kBatch ? 0 : (int)((m_single + kBM - 1) / kBM);
     sc.nN = kBatch ? 0 : col_blocks(sc.nM, R);
     sc.ntiles = kBatch ? ntiles_batch : tile_count(sc.nM, R);
     sc.G = gridDim.x;
     sc.c = blockIdx.x;
+    sc.t0 = sc.ntiles * sc.c / sc.G;
+    sc.t1 = sc.ntiles * (sc.c + 1) / sc.G;
 #define TILE_K(k, x) tile_k<kBatch, R>((k), sc, KB1, m_single, S_single, lds_single, layout_single, btab, (x))
 
     if (threadIdx.x == 0) {
@@ -592,7 +598,7 @@ constexpr size_t kSmemTC = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA 
 
 cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64_t m, int Kp,
                            const int32_t *nelim, float *S, int64_t lds, int layout, int32_t *info,
-                           int num_sms, cudaStream_t st) {
+                           int num_sms, int walk, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     const bool split = lo_off != 0;
     const void *Wl = split ? (const void *)((const char *)Wb + 2 * lo_off) : Wb;
@@ -608,8 +614,17 @@ cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64
     if (err != cudaSuccess) return err;
     const int nM = (int)((m + kBM - 1) / kBM);
     const int64_t ntiles = tile_count(nM, R), nN = col_blocks(nM, R);
-    // panels when the split operands (twice the bytes) need the L2-friendly walk
-    const int mode = (split && nN >= 2 * (int64_t)num_sms) ? 1 : 0;
+    // walk: CTP_WALK_AUTO picks panels when the split operands (twice the
+    // bytes) need the L2-friendly walk, contiguous runs otherwise
+    int mode;
+    if (walk == CTP_WALK_ROUND_ROBIN)
+        mode = 0;
+    else if (walk == CTP_WALK_CHUNKS)
+        mode = 2;
+    else if (walk == CTP_WALK_PANELS)
+        mode = nN >= (int64_t)num_sms ? 1 : 2;
+    else
+        mode = (split && nN >= 2 * (int64_t)num_sms) ? 1 : 2;
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
     BatchTab none = {nullptr, nullptr, nullptr};
     if (split)
@@ -645,10 +660,10 @@ cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, con
     BatchTab bt = {fronts, tab, item_front};
     if (split)
         k_form_tc<true, true><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, 0, nullptr, nullptr, 0, 2,
-                                                                  info, items, bt, 0);
+                                                                  info, items, bt, 2);
     else
         k_form_tc<true, false><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, 0, nullptr, nullptr, 0,
-                                                                   2, info, items, bt, 0);
+                                                                   2, info, items, bt, 2);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,10 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_batch_plan_destroy", "ctp_batch_upload", "ctp_factor_batch", "ctp_batch_read_info",
            "ctp_solve_workspace_size", "ctp_solve", "ctp_refine_workspace_size",
            "ctp_backward_error", "ctp_refine", "ctp_factor_dense", "ctp_chain_fronts",
-           "ctp_chain_info", "ctp_chain_destroy"]
+           "ctp_chain_info", "ctp_chain_destroy", "ctp_tune_set", "ctp_tune_get",
+           "ctp_autotune_batch", "ctp_autotune_supernode"]
+TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G = 0, 1, 2
+WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
 
 class Options(ctypes.Structure):
@@ -109,6 +112,12 @@ def load(path: str = LIB_PATH):
     L.ctp_chain_fronts.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(P)]
     L.ctp_chain_info.argtypes = [P, i32, P, P, P]
     L.ctp_chain_destroy.argtypes = [P]
+    L.ctp_tune_set.argtypes = [P, i32, i32]
+    L.ctp_tune_get.argtypes = [P, i32, ctypes.POINTER(i32)]
+    L.ctp_autotune_batch.argtypes = [P, i32, P, P, ctypes.POINTER(Options), P, P, i32, P, i32, P, P,
+                                     ctypes.POINTER(i32), P]
+    L.ctp_autotune_supernode.argtypes = [P, i64, i32, P, i64, ctypes.POINTER(Options), P, P, P, P,
+                                         P, i64, P, sz, i32, P, i32, P, P, ctypes.POINTER(i32), P]
     L.ctp_profile_begin.argtypes = [P]
     L.ctp_profile_end.argtypes = [P, i32, P, P, P, ctypes.POINTER(i32)]
     for f in EXPORTS[1:]:
@@ -194,6 +203,14 @@ class Context:
                                              _ptr(perm), _ptr(piv), _ptr(D), _ptr(nelim), _ptr(S),
                                              lds, _ptr(ws), ws.numel(), _stream(stream)))
         return ws
+
+    def tune_set(self, key, value):
+        _check("ctp_tune_set", self.lib.ctp_tune_set(self.handle, key, value))
+
+    def tune_get(self, key):
+        v = ctypes.c_int32()
+        _check("ctp_tune_get", self.lib.ctp_tune_get(self.handle, key, ctypes.byref(v)))
+        return int(v.value)
 
     def profile_begin(self):
         _check("ctp_profile_begin", self.lib.ctp_profile_begin(self.handle))
@@ -372,6 +389,23 @@ def factor_dense(ctx: Context, M, N, ldm, p_first, opt_first, w_rest, opt_rest, 
     return Chain(ctx, h)
 
 
+def autotune_supernode(ctx: Context, A, n, p, lda, opt, perm, piv, D, nelim, S, lds, ws, keys,
+                       candidates, stream=None):
+    """The library's autotuner over candidate settings of the knobs `keys` for
+    one supernode factorization (inputs restored afterwards).  Returns
+    (per-candidate ms, chosen index)."""
+    k = np.array(keys, np.int32)
+    v = np.array(candidates, np.int32).reshape(len(candidates), len(keys))
+    ms = np.zeros(len(v))
+    best = ctypes.c_int32(-1)
+    _check("ctp_autotune_supernode", ctx.lib.ctp_autotune_supernode(
+        ctx.handle, n, p, _ptr(A), lda, ctypes.byref(opt), _ptr(perm), _ptr(piv), _ptr(D),
+        _ptr(nelim), _ptr(S), lds, _ptr(ws), ws.numel(), len(k), k.ctypes.data_as(ctypes.c_void_p),
+        len(v), v.ctypes.data_as(ctypes.c_void_p), ms.ctypes.data_as(ctypes.c_void_p),
+        ctypes.byref(best), _stream(stream)))
+    return ms, int(best.value)
+
+
 def solve_workspace(ctx: Context, nmax, nrhs):
     import torch
     b = ctypes.c_size_t()
@@ -461,18 +495,47 @@ class Batch:
             fr[k].S = (self.S.data_ptr() + self.S.element_size() * int(s_off[k])) if self.S is not None else None
             fr[k].lds = max(int(m[k]), 1)
         raw = np.frombuffer(bytes(fr), dtype=np.uint8)
+        self.fronts_host = fr
         self.fronts = torch.from_numpy(raw.copy()).to(dev)
+        self.plan = None
+        self.replan()
+        self.A0 = self.A.clone()
+
+    def replan(self):
+        """(Re)create the plan with the context's current tuning knobs."""
+        import torch
+        if self.plan:
+            self.ctx.lib.ctp_batch_plan_destroy(self.plan)
         plan = ctypes.c_void_p()
         wsb = ctypes.c_size_t()
         _check("ctp_batch_plan_create",
-               ctx.lib.ctp_batch_plan_create(ctx.handle, self.nb, self.n.ctypes.data_as(ctypes.c_void_p),
-                                             self.p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt),
-                                             ctypes.byref(plan), ctypes.byref(wsb)))
+               self.ctx.lib.ctp_batch_plan_create(
+                   self.ctx.handle, self.nb, self.n.ctypes.data_as(ctypes.c_void_p),
+                   self.p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.opt),
+                   ctypes.byref(plan), ctypes.byref(wsb)))
         self.plan = plan
-        self.ws = torch.empty(max(int(wsb.value), 256), dtype=torch.uint8, device=dev)
-        _check("ctp_batch_upload", ctx.lib.ctp_batch_upload(ctx.handle, self.plan, _ptr(self.ws),
-                                                             self.ws.numel(), _stream(None)))
-        self.A0 = self.A.clone()
+        self.ws = torch.empty(max(int(wsb.value), 256), dtype=torch.uint8,
+                              device=f"cuda:{self.ctx.device}")
+        _check("ctp_batch_upload", self.ctx.lib.ctp_batch_upload(
+            self.ctx.handle, self.plan, _ptr(self.ws), self.ws.numel(), _stream(None)))
+
+    def autotune(self, keys, candidates, stream=None):
+        """Run the library's autotuner over candidate settings of the knobs
+        `keys` (candidates: one tuple of values per candidate) on this batch's
+        own inputs, keep the fastest in the context and re-plan.  Returns
+        (per-candidate ms, chosen index)."""
+        k = np.array(keys, np.int32)
+        v = np.array(candidates, np.int32).reshape(len(candidates), len(keys))
+        ms = np.zeros(len(v))
+        best = ctypes.c_int32(-1)
+        _check("ctp_autotune_batch", self.ctx.lib.ctp_autotune_batch(
+            self.ctx.handle, self.nb, self.n.ctypes.data_as(ctypes.c_void_p),
+            self.p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.opt),
+            ctypes.cast(self.fronts_host, ctypes.c_void_p), _ptr(self.fronts), len(k),
+            k.ctypes.data_as(ctypes.c_void_p), len(v), v.ctypes.data_as(ctypes.c_void_p),
+            ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(best), _stream(stream)))
+        self.replan()
+        return ms, int(best.value)
 
     def reset(self):
         self.A.copy_(self.A0)

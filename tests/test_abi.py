@@ -84,3 +84,13 @@ def test_sfront_mirror_matches_header():
     assert ctypes.sizeof(ctp.SFront) == 8 + 4 + 4 + 8 + 8 + 5 * 8
     assert [f for f, _ in ctp.SFront._fields_] == ["n", "p", "reserved", "L", "ldl", "perm", "piv",
                                                   "D", "nelim", "rows"]
+
+
+def test_tuning_knobs_check_arguments(lib):
+    v = ctypes.c_int32()
+    assert lib.ctp_tune_set(None, 0, 0) == ctp.CTP_EINVAL
+    assert lib.ctp_tune_get(None, 0, ctypes.byref(v)) == ctp.CTP_EINVAL
+    assert lib.ctp_autotune_batch(None, 1, None, None, None, None, None, 1, None, 1, None, None,
+                                  None, None) == ctp.CTP_EINVAL
+    assert lib.ctp_autotune_supernode(None, 10, 2, None, 10, None, None, None, None, None, None, 0,
+                                      None, 0, 1, None, 1, None, None, None, None) == ctp.CTP_EINVAL

@@ -94,3 +94,48 @@ def test_batch_tensor_core_form(ctx, prec, tol):
         bound = _bf16_bound(L21 @ Dm, L21)
         lo = np.tril(np.ones_like(S, dtype=bool))
         assert np.all(np.abs(got["S"] - S)[lo] <= tol * bound[lo] + 1e-30)
+
+
+def test_batch_autotune_keeps_inputs_and_results(ctx):
+    """The autotuner times candidate launch settings on the batch's own inputs,
+    restores them, keeps the fastest setting; the re-planned batch gives the
+    oracle's results."""
+    from paper_1305_2353_gb300 import ctp
+    fr = _fronts(30, seed=9)
+    b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr],
+                  ctp.options(pivot="strict", prec="bf16x3", smode="fp32_tiled"))
+    before = b.A.clone()
+    cands = [(64, 2), (100, 1), (220, 2)]
+    ms, best = b.autotune([ctp.TUNE_BATCH_SMEM_KB, ctp.TUNE_FORM_WALK], cands)
+    torch.cuda.synchronize()
+    assert torch.equal(b.A, before)
+    assert 0 <= best < 3 and np.all(ms > 0)
+    assert ctx.tune_get(ctp.TUNE_BATCH_SMEM_KB) == cands[best][0]
+    assert ctx.tune_get(ctp.TUNE_FORM_WALK) == cands[best][1]
+    b.run()
+    torch.cuda.synchronize()
+    assert np.all(b.flags() == 0)
+    for k, A in enumerate(fr):
+        p = A.shape[1]
+        compare(O.factor(A, p, "strict"), b.result(k), p, A)
+    ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 200)
+    ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
+
+
+@pytest.mark.parametrize("kb", [64, 220])
+def test_batch_cluster_budget_same_results(ctx, kb):
+    """Another shared-memory budget changes the cluster widths of the pivot
+    search, never the pivots."""
+    from paper_1305_2353_gb300 import ctp
+    fr = _fronts(30, seed=11)
+    ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, kb)
+    try:
+        b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr], ctp.options(pivot="strict", smode="none"))
+    finally:
+        ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 200)
+    b.run()
+    torch.cuda.synchronize()
+    assert np.all(b.flags() == 0)
+    for k, A in enumerate(fr):
+        p = A.shape[1]
+        compare(O.factor(A, p, "strict"), b.result(k), p, A)

@@ -382,6 +382,72 @@ def test_form_tensor_cores_bf16x3_large(ctx):
     assert np.all(np.abs(got - want) <= 2.0 ** -13 * bound)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_form_walks_are_bit_identical(ctx, prec):
+    """The tile walks of the tensor-core Form change which CTA computes a tile,
+    not how: S is bit-identical under every walk (n = 40000 so that the panel
+    walk is taken)."""
+    from paper_1305_2353_gb300 import ctp
+    n, p = 40000, 192
+    A = inputs.single_large(4, n=n, p=p)
+    out = {}
+    for w in ("round_robin", "chunks", "panels"):
+        ctx.tune_set(ctp.TUNE_FORM_WALK, ctp.WALK[w])
+        try:
+            sn = ctp.Supernode(ctx, A, p, ctp.options(pivot="relaxed", prec=prec, smode="fp32_tiled"))
+            sn.run()
+            torch.cuda.synchronize()
+            assert ctx.read_info(sn.ws) == 0
+            out[w] = sn.S.clone()
+            del sn
+        finally:
+            ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
+    assert torch.equal(out["round_robin"], out["chunks"])
+    assert torch.equal(out["round_robin"], out["panels"])
+
+
+def test_supernode_autotune(ctx):
+    """The autotuner over Form walks and pivot-search cluster widths restores the
+    input and leaves the factorization unchanged."""
+    from paper_1305_2353_gb300 import ctp
+    n, p = 20000, 128
+    A = inputs.single_large(5, n=n, p=p)
+    opt = ctp.options(pivot="relaxed", prec="bf16x3", smode="fp32_tiled")
+    sn = ctp.Supernode(ctx, A, p, opt)
+    before = sn.A.clone()
+    cands = [(1, 0), (2, 4), (3, 8), (2, 16)]
+    ms, best = ctp.autotune_supernode(ctx, sn.A, n, p, n, opt, sn.perm, sn.piv, sn.D, sn.nelim,
+                                      sn.S, n - p, sn.ws, [ctp.TUNE_FORM_WALK, ctp.TUNE_FACTOR_G],
+                                      cands)
+    torch.cuda.synchronize()
+    assert 0 <= best < len(cands) and np.all(ms > 0)
+    assert torch.equal(sn.A, before)
+    assert ctx.tune_get(ctp.TUNE_FORM_WALK) == cands[best][0]
+    assert ctx.tune_get(ctp.TUNE_FACTOR_G) == cands[best][1]
+    sn.run()
+    torch.cuda.synchronize()
+    got = sn.result()
+    ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
+    ctx.tune_set(ctp.TUNE_FACTOR_G, 0)
+    ref = O.factor(A, p, "relaxed")
+    assert got["nelim"] == ref["nelim"]
+    assert np.array_equal(got["perm"], ref["perm"])
+
+
+@pytest.mark.parametrize("G", [1, 4, 8])
+def test_factor_cluster_width_same_pivots(ctx, G):
+    """Any cluster width of the pivot search gives the oracle's pivots."""
+    from paper_1305_2353_gb300 import ctp
+    A = _tough(3000, 200, 8)
+    ctx.tune_set(ctp.TUNE_FACTOR_G, G)
+    try:
+        got = run_gpu(ctx, A, 200, "strict")
+    finally:
+        ctx.tune_set(ctp.TUNE_FACTOR_G, 0)
+    ref = O.factor(A, 200, "strict", log_cap=100000)
+    compare(ref, got, 200, A)
+
+
 def test_form_tensor_cores_large(ctx):
     """n = 20000, p = 256, relaxed (e = 256): 610 tiles per row band region, sampled
     entries of S against the oracle, including the diagonal and the last rows."""
