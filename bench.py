@@ -42,7 +42,19 @@ sys.path.insert(0, ROOT)
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic per launch from ncu captures (profiles/), valid only for the
 # kernel source they were taken on (sha1 of the .cu file).
-NCU_TRAFFIC = {}
+# Measured at a smaller size than the bench's and scaled by the units one launch
+# processes (the traffic of these kernels is the S they write, proportional to
+# the number of S entries): see profiles/ for the captures.
+NCU_TRAFFIC = {
+    # ncu --set full, n=20000 p=256 relaxed, S FP64 lower-packed: 146.48 MB read +
+    # 1516.63 MB written for m(m+1)/2 = 194,921,640 entries
+    "form_fp64": {"file": "form.cu", "sha1": "7f2c353064294c79b58273da8095be00973639ff",
+                  "unit": "packed_entry", "bytes_per_unit": (146.477568e6 + 1516.633e6) / 194921640},
+    # ncu --set full, n=40000 p=256 relaxed, split BF16, S FP32 in 128x128 blocks:
+    # 228.97 MB read + 3118.61 MB written for 48,516 blocks of 16,384 entries
+    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "52739ecaf566efb8e08328d94973028f56c7f359",
+                       "unit": "tiled_entry", "bytes_per_unit": (228.966912e6 + 3118.611e6) / (48516 * 16384)},
+}
 
 
 def flops_model(n, p, e):
@@ -214,6 +226,21 @@ def fp64_peak_tflops(torch, dev):
     return 2 * N ** 3 / best / 1e12
 
 
+def ncu_traffic(name, m):
+    """DRAM bytes of one launch of `name` on m rows, from the ncu record, or None
+    when there is none or the kernel's source changed since it was taken."""
+    rec = NCU_TRAFFIC.get(name)
+    if rec is None:
+        return None
+    src_file = os.path.join(ROOT, "paper_1305_2353_gb300", "csrc", rec["file"])
+    if hashlib.sha1(open(src_file, "rb").read()).hexdigest() != rec["sha1"]:
+        return None
+    nbk = (m + 127) // 128
+    units = {"row": m, "packed_entry": m * (m + 1) // 2,
+             "tiled_entry": nbk * (nbk + 1) // 2 * 16384}[rec["unit"]]
+    return rec["bytes_per_unit"] * units
+
+
 def kernel_roofline(name, launches, ms, a, e, peaks):
     """Algorithmic work of one launch of `name` and its roofline."""
     n, p = a.n, a.p
@@ -236,7 +263,7 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
         achieved = work / t / 1e9
         tensor = form / t / 1e12
         out = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-               "frac": achieved / peak, "traffic": None, "peak_source": src,
+               "frac": achieved / peak, "traffic": ncu_traffic(name, m), "peak_source": src,
                "work_per_launch": work, "launch_ms": ms / launches,
                "tensor_tflops": tensor,
                "tensor_frac_of_bf16_sustained": tensor / peaks.get("bf16_tflops_sustained", 1715.6)}
@@ -257,13 +284,7 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
         achieved = work / t / 1e12
     else:
         return None
-    traffic = None
-    rec = NCU_TRAFFIC.get(name)
-    if rec is not None:
-        src_file = os.path.join(ROOT, "paper_1305_2353_gb300", "csrc", rec["file"])
-        h = hashlib.sha1(open(src_file, "rb").read()).hexdigest()
-        if h == rec["sha1"]:
-            traffic = rec["bytes_per_unit"] * (m if rec["unit"] == "row" else 1)
+    traffic = ncu_traffic(name, m)
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic, "peak_source": src,
             "work_per_launch": work, "launch_ms": ms / launches}
