@@ -159,3 +159,20 @@ def refine(M, fronts, b, steps=10, tol=1e-14):
         hist.append(backward_error(M, x, b))
         k += 1
     return x, hist, k
+
+
+def solve_gradient(fronts, x, gx):
+    """Gradient of a loss through x = M^{-1} b (Section 1's factors reused),
+    given gx = dloss/dx: returns (gb, gM) with gb = M^{-T} gx (M symmetric, so
+    the same solve) and gM the gradient with respect to the stored lower
+    triangle of M -- an off-diagonal stored entry m_ij stands for both m_ij and
+    m_ji, so it gets -(gb_i x_j + gb_j x_i); a diagonal entry gets -gb_i x_i
+    (from d(M^{-1} b) = -M^{-1} dM M^{-1} b).  The strict upper triangle of gM
+    is zero."""
+    gb = solve(fronts, gx)
+    G = np.atleast_2d(gb.T).T
+    X = np.atleast_2d(np.asarray(x).T).T
+    full = -(G @ X.T)
+    gM = np.tril(full + full.T)
+    np.fill_diagonal(gM, np.diag(full))
+    return gb, gM

@@ -132,3 +132,33 @@ def test_restricted_fails_where_strict_succeeds():
         fr = S.factor_chain(M, 64, mf, "tpp")
         _, hist, _ = S.refine(M, fr, b)
         assert (hist[-1] <= 1e-14) == ok, (mf, hist)
+
+
+def test_gradient_matches_finite_differences():
+    """The oracle's gradient of w^T M^{-1} b with respect to b and to the stored
+    lower triangle of M (an off-diagonal entry moves m_ij and m_ji together)
+    against central differences of a dense library solve, every entry."""
+    A = inputs.supernode(40, 8, seed=21, zero_diag_frac=0.25)
+    M = inputs.two_node(A, 21)
+    N = M.shape[0]
+    rng = np.random.default_rng(22)
+    b = rng.standard_normal(N)
+    w = rng.standard_normal(N)
+    fr = S.factor_chain(M, 8, "strict", "tpp", w_rest=16)
+    x = S.solve(fr, b)
+    gb, gM = S.solve_gradient(fr, x, w)
+
+    def loss(Mm, bb):
+        return w @ np.linalg.solve(Mm, bb)
+
+    h = 1e-6
+    fd_b = np.array([(loss(M, b + h * e) - loss(M, b - h * e)) / (2 * h) for e in np.eye(N)])
+    np.testing.assert_allclose(gb, fd_b, rtol=1e-6, atol=1e-7 * np.abs(fd_b).max())
+    fd_M = np.zeros_like(M)
+    for i in range(N):
+        for j in range(i + 1):
+            E = np.zeros_like(M)
+            E[i, j] = E[j, i] = h
+            fd_M[i, j] = (loss(M + E, b) - loss(M - E, b)) / (2 * h)
+    np.testing.assert_allclose(gM, fd_M, rtol=1e-5, atol=1e-7 * np.abs(fd_M).max())
+    assert np.all(np.triu(gM, 1) == 0)
