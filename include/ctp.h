@@ -318,6 +318,32 @@ ctp_status ctp_refine(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_
                       double *X, int64_t ldx, int32_t max_steps, double tol, double *berr_host,
                       int32_t *steps_host, void *workspace, size_t ws_bytes, void *stream);
 
+/* Adjoint solve: G <- M^{-T} G with the same factors and pivot sequence.  For
+ * the symmetric M of these factorizations (P M P^T = L D L^T with D symmetric:
+ * its 2x2 blocks are symmetric) M^{-T} = M^{-1}, so this is the solve of
+ * ctp_solve applied to G (N x nrhs, column-major, ldg >= N); it is the call the
+ * backward pass of a differentiated solve makes.  Arguments as ctp_solve. */
+ctp_status ctp_adjoint_solve(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
+                             int32_t nrhs, double *G, int64_t ldg, void *workspace, size_t ws_bytes,
+                             void *stream);
+
+/* Gradient of a loss through X = M^{-1} B with respect to the stored entries of
+ * the symmetric M, given Gb = M^{-T} dloss/dX (from ctp_adjoint_solve) and X:
+ * a stored off-diagonal entry m_ij (it stands for both m_ij and m_ji) gets
+ *   -sum_r (Gb(i,r) X(j,r) + Gb(j,r) X(i,r)),
+ * a diagonal entry -sum_r Gb(i,r) X(i,r)  (d(M^{-1}B) = -M^{-1} dM M^{-1}B).
+ * ctp_sym_grad_dense: out is N x N column-major (ldo >= N); its lower triangle
+ *   receives the gradient of the stored lower triangle, its strict upper
+ *   triangle zeros (those entries are never read by the factorization).
+ * ctp_sym_grad_pattern: out[k] for the stored entries (row[k], col[k]), k < nnz
+ *   (int32 device arrays; row == col marks a diagonal entry).
+ * All arrays are device memory; launches only. */
+ctp_status ctp_sym_grad_dense(ctp_ctx *ctx, int64_t N, int32_t nrhs, const double *Gb, int64_t ldg,
+                              const double *X, int64_t ldx, double *out, int64_t ldo, void *stream);
+ctp_status ctp_sym_grad_pattern(ctp_ctx *ctx, int64_t nnz, const int32_t *row, const int32_t *col,
+                                int64_t N, int32_t nrhs, const double *Gb, int64_t ldg,
+                                const double *X, int64_t ldx, double *out, void *stream);
+
 typedef struct ctp_chain ctp_chain;
 
 /* Factor a dense symmetric matrix M (order N, lower triangle, column-major,

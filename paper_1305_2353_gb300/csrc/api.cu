@@ -13,7 +13,7 @@ enum KernelId {
     K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP,
     K_B_PREPARE, K_B_COMPRESS, K_B_FACTOR_G1, K_B_FACTOR_G2, K_B_FACTOR_G4, K_B_FACTOR_G8,
     K_B_FACTOR_G16, K_B_SOLVE, K_B_FORM, K_W21, K_SYS_FWD, K_SYS_BWD, K_SYMV, K_BERR, K_AXPY,
-    K_FORM_TC3, K_NUM_IDS
+    K_FORM_TC3, K_GRAD, K_NUM_IDS
 };
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
                                        "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16",
@@ -21,7 +21,8 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
                                        "batch_factor_g1", "batch_factor_g2", "batch_factor_g4",
                                        "batch_factor_g8", "batch_factor_g16", "batch_solve_fp64",
                                        "batch_form", "w21_from_l", "sys_forward", "sys_backward",
-                                       "symv_residual", "backward_error", "axpy", "form_tc_bf16x3"};
+                                       "symv_residual", "backward_error", "axpy", "form_tc_bf16x3",
+                                       "sym_grad"};
 }  // namespace
 
 struct ctp_ctx {
@@ -443,6 +444,38 @@ ctp_status ctp_solve(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t
     if (s != CTP_OK) return s;
     if (ws_bytes < sys_solve_ws_bytes(nmax, nrhs)) return CTP_ENOMEM;
     CTP_CUDA(solve_fronts(ctx, nf, fronts, nrhs, X, ldx, workspace, (cudaStream_t)stream));
+    return CTP_OK;
+}
+
+ctp_status ctp_adjoint_solve(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
+                             int32_t nrhs, double *G, int64_t ldg, void *workspace, size_t ws_bytes,
+                             void *stream) {
+    // M is symmetric and so is its factored form: the adjoint is the same solve
+    return ctp_solve(ctx, nf, fronts, N, nrhs, G, ldg, workspace, ws_bytes, stream);
+}
+
+ctp_status ctp_sym_grad_dense(ctp_ctx *ctx, int64_t N, int32_t nrhs, const double *Gb, int64_t ldg,
+                              const double *X, int64_t ldx, double *out, int64_t ldo, void *stream) {
+    if (ctx == nullptr || Gb == nullptr || X == nullptr || out == nullptr || N < 1 || nrhs < 1 ||
+        ldg < N || ldx < N || ldo < N)
+        return CTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    CTP_CUDA(timed(ctx, K_GRAD, st, [&] {
+        return launch_sym_grad_dense(N, nrhs, Gb, ldg, X, ldx, out, ldo, st);
+    }));
+    return CTP_OK;
+}
+
+ctp_status ctp_sym_grad_pattern(ctp_ctx *ctx, int64_t nnz, const int32_t *row, const int32_t *col,
+                                int64_t N, int32_t nrhs, const double *Gb, int64_t ldg,
+                                const double *X, int64_t ldx, double *out, void *stream) {
+    if (ctx == nullptr || nnz < 0 || (nnz > 0 && (row == nullptr || col == nullptr || out == nullptr)) ||
+        Gb == nullptr || X == nullptr || N < 1 || nrhs < 1 || ldg < N || ldx < N)
+        return CTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    CTP_CUDA(timed(ctx, K_GRAD, st, [&] {
+        return launch_sym_grad_pattern(nnz, row, col, nrhs, Gb, ldg, X, ldx, out, st);
+    }));
     return CTP_OK;
 }
 

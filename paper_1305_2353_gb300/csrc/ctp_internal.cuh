@@ -161,6 +161,11 @@ cudaError_t launch_backward_error(int64_t N, int nrhs, const double *R, int64_t 
                                   double *mx, double *berr, cudaStream_t st);
 cudaError_t launch_axpy(int64_t N, int nrhs, double *X, int64_t ldx, const double *Dx, int64_t ldd,
                         cudaStream_t st);
+cudaError_t launch_sym_grad_dense(int64_t N, int nrhs, const double *G, int64_t ldg, const double *X,
+                                  int64_t ldx, double *out, int64_t ldo, cudaStream_t st);
+cudaError_t launch_sym_grad_pattern(int64_t nnz, const int32_t *row, const int32_t *col, int nrhs,
+                                    const double *G, int64_t ldg, const double *X, int64_t ldx,
+                                    double *out, cudaStream_t st);
 cudaError_t launch_w21_from_l(const double *A, int64_t lda, int p, int64_t m, const int32_t *piv,
                               const double *D, const int32_t *nelim, double *W21, int64_t ldw,
                               cudaStream_t st);

@@ -337,6 +337,52 @@ __global__ void __launch_bounds__(kTh) k_w21_from_l(const double *A, int64_t lda
     }
 }
 
+// Gradient of a loss through x = M^{-1} b with respect to the stored lower
+// triangle of the symmetric M (each stored off-diagonal entry stands for both
+// m_ij and m_ji): dL/dm_ij = -sum_r (g_ir x_jr + g_jr x_ir) for i > j and
+// -sum_r g_ir x_ir on the diagonal, with g = M^{-T} dL/dx.  Dense form: the lower
+// triangle of an N x N column-major output (strict upper triangle zeroed).
+__global__ void __launch_bounds__(kTh) k_sym_grad_dense(int64_t N, int nrhs, const double *__restrict__ G,
+                                                        int64_t ldg, const double *__restrict__ X,
+                                                        int64_t ldx, double *__restrict__ out,
+                                                        int64_t ldo) {
+    for (int64_t j = blockIdx.y; j < N; j += gridDim.y)
+    for (int64_t i = (int64_t)blockIdx.x * kTh + threadIdx.x; i < N; i += (int64_t)gridDim.x * kTh) {
+        double s = 0.0;
+        if (i > j) {
+            for (int r = 0; r < nrhs; r++)
+                s += G[(int64_t)r * ldg + i] * X[(int64_t)r * ldx + j] +
+                     G[(int64_t)r * ldg + j] * X[(int64_t)r * ldx + i];
+        } else if (i == j) {
+            for (int r = 0; r < nrhs; r++) s += G[(int64_t)r * ldg + i] * X[(int64_t)r * ldx + i];
+        }
+        out[j * ldo + i] = -s;
+    }
+}
+
+// The same restricted to a pattern of stored entries (row[k], col[k]), any order;
+// an entry with row == col is a diagonal entry, otherwise it stands for both
+// (row, col) and (col, row).
+__global__ void __launch_bounds__(kTh) k_sym_grad_pattern(int64_t nnz, const int32_t *__restrict__ row,
+                                                          const int32_t *__restrict__ col, int nrhs,
+                                                          const double *__restrict__ G, int64_t ldg,
+                                                          const double *__restrict__ X, int64_t ldx,
+                                                          double *__restrict__ out) {
+    for (int64_t k = (int64_t)blockIdx.x * kTh + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * kTh) {
+        const int64_t i = row[k], j = col[k];
+        double s = 0.0;
+        // the same expressions as the dense kernel, so both round alike
+        if (i != j) {
+            for (int r = 0; r < nrhs; r++)
+                s += G[(int64_t)r * ldg + i] * X[(int64_t)r * ldx + j] +
+                     G[(int64_t)r * ldg + j] * X[(int64_t)r * ldx + i];
+        } else {
+            for (int r = 0; r < nrhs; r++) s += G[(int64_t)r * ldg + i] * X[(int64_t)r * ldx + i];
+        }
+        out[k] = -s;
+    }
+}
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kTh - 1) / kTh); }
 
 constexpr size_t kTriSmem = sizeof(double) * (size_t)(kJB + kRB) * kMaxP;
@@ -408,6 +454,24 @@ cudaError_t launch_axpy(int64_t N, int nrhs, double *X, int64_t ldx, const doubl
     if (N == 0 || nrhs == 0) return cudaSuccess;
     const unsigned gx = (unsigned)((N + kTh - 1) / kTh < 1216 ? (N + kTh - 1) / kTh : 1216);
     k_axpy<<<dim3(gx, nrhs), kTh, 0, st>>>(N, nrhs, X, ldx, Dx, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_grad_dense(int64_t N, int nrhs, const double *G, int64_t ldg, const double *X,
+                                  int64_t ldx, double *out, int64_t ldo, cudaStream_t st) {
+    if (N == 0) return cudaSuccess;
+    const unsigned gx = blocks_for(N) < 64 ? blocks_for(N) : 64;
+    const unsigned gy = N < 65535 ? (unsigned)N : 65535u;
+    k_sym_grad_dense<<<dim3(gx, gy), kTh, 0, st>>>(N, nrhs, G, ldg, X, ldx, out, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_grad_pattern(int64_t nnz, const int32_t *row, const int32_t *col, int nrhs,
+                                    const double *G, int64_t ldg, const double *X, int64_t ldx,
+                                    double *out, cudaStream_t st) {
+    if (nnz == 0) return cudaSuccess;
+    const unsigned g = blocks_for(nnz) < 4096 ? blocks_for(nnz) : 4096;
+    k_sym_grad_pattern<<<g, kTh, 0, st>>>(nnz, row, col, nrhs, G, ldg, X, ldx, out);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,8 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_solve_workspace_size", "ctp_solve", "ctp_refine_workspace_size",
            "ctp_backward_error", "ctp_refine", "ctp_factor_dense", "ctp_chain_fronts",
            "ctp_chain_info", "ctp_chain_destroy", "ctp_tune_set", "ctp_tune_get",
-           "ctp_autotune_batch", "ctp_autotune_supernode"]
+           "ctp_autotune_batch", "ctp_autotune_supernode", "ctp_adjoint_solve",
+           "ctp_sym_grad_dense", "ctp_sym_grad_pattern"]
 TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G = 0, 1, 2
 WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
@@ -112,6 +113,9 @@ def load(path: str = LIB_PATH):
     L.ctp_chain_fronts.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(P)]
     L.ctp_chain_info.argtypes = [P, i32, P, P, P]
     L.ctp_chain_destroy.argtypes = [P]
+    L.ctp_adjoint_solve.argtypes = [P, i32, P, i64, i32, P, i64, P, sz, P]
+    L.ctp_sym_grad_dense.argtypes = [P, i64, i32, P, i64, P, i64, P, i64, P]
+    L.ctp_sym_grad_pattern.argtypes = [P, i64, P, P, i64, i32, P, i64, P, i64, P, P]
     L.ctp_tune_set.argtypes = [P, i32, i32]
     L.ctp_tune_get.argtypes = [P, i32, ctypes.POINTER(i32)]
     L.ctp_autotune_batch.argtypes = [P, i32, P, P, ctypes.POINTER(Options), P, P, i32, P, i32, P, P,
@@ -425,6 +429,102 @@ def solve(ctx: Context, fronts, nf, N, nrhs, X, ldx, ws, stream=None):
     """X <- M^{-1} X (device tensor, column-major N x nrhs) with the fronts' factors."""
     _check("ctp_solve", ctx.lib.ctp_solve(ctx.handle, nf, ctypes.cast(fronts, ctypes.c_void_p), N,
                                           nrhs, _ptr(X), ldx, _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def adjoint_solve(ctx: Context, fronts, nf, N, nrhs, G, ldg, ws, stream=None):
+    """G <- M^{-T} G with the same factors (M symmetric: the same solve)."""
+    _check("ctp_adjoint_solve", ctx.lib.ctp_adjoint_solve(
+        ctx.handle, nf, ctypes.cast(fronts, ctypes.c_void_p), N, nrhs, _ptr(G), ldg, _ptr(ws),
+        ws.numel(), _stream(stream)))
+
+
+def sym_grad_dense(ctx: Context, N, nrhs, Gb, ldg, X, ldx, out, ldo, stream=None):
+    """Lower triangle of out (column-major) <- gradient with respect to the
+    stored lower triangle of M, from Gb = M^{-T} dloss/dX and X."""
+    _check("ctp_sym_grad_dense", ctx.lib.ctp_sym_grad_dense(
+        ctx.handle, N, nrhs, _ptr(Gb), ldg, _ptr(X), ldx, _ptr(out), ldo, _stream(stream)))
+
+
+def sym_grad_pattern(ctx: Context, row, col, N, nrhs, Gb, ldg, X, ldx, out, stream=None):
+    """out[k] <- gradient with respect to the stored entry (row[k], col[k])."""
+    _check("ctp_sym_grad_pattern", ctx.lib.ctp_sym_grad_pattern(
+        ctx.handle, row.numel(), _ptr(row), _ptr(col), N, nrhs, _ptr(Gb), ldg, _ptr(X), ldx,
+        _ptr(out), _stream(stream)))
+
+
+_default_ctx = None
+
+
+def default_context():
+    global _default_ctx
+    if _default_ctx is None:
+        import torch
+        _default_ctx = Context(torch.cuda.current_device())
+    return _default_ctx
+
+
+_SymSolve = None
+
+
+def _sym_solve_fn():
+    """torch.autograd.Function: X = M^{-1} B through the chain factorization
+    (forward: factor + FP64 refinement; backward: the adjoint solve with the same
+    factors, refined, and the gradient of the stored lower triangle of M)."""
+    global _SymSolve
+    if _SymSolve is not None:
+        return _SymSolve
+    import torch
+
+    class SymSolve(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, A, B, ctx, p_first, opt_first, w_rest, opt_rest, steps, tol):
+            N = A.shape[0]
+            Mlow = A.detach().t().contiguous()   # column-major storage of the lower triangle
+            Md = Mlow.clone()                    # factored in place
+            ch = factor_dense(ctx, Md, N, N, min(p_first, N), opt_first, w_rest, opt_rest)
+            Bt = B.detach().reshape(N, -1).t().contiguous()
+            nrhs = Bt.shape[0]
+            X = torch.zeros_like(Bt)
+            ws = refine_workspace(ctx, N, N, nrhs)
+            hist, k = refine(ctx, ch.fronts, ch.nf, N, Mlow, N, nrhs, Bt, N, X, N, ws, steps, tol)
+            fctx.chain, fctx.Md, fctx.Mlow, fctx.ws = ch, Md, Mlow, ws
+            fctx.steps, fctx.tol, fctx.ctx, fctx.bshape = steps, tol, ctx, B.shape
+            fctx.history = hist
+            fctx.save_for_backward(X)
+            out = X.t().contiguous()
+            return out.reshape(B.shape)
+
+        @staticmethod
+        def backward(fctx, gX):
+            (X,) = fctx.saved_tensors
+            ctx, ch, N = fctx.ctx, fctx.chain, X.shape[1]
+            nrhs = X.shape[0]
+            G = gX.reshape(N, -1).t().contiguous()
+            Gb = torch.zeros_like(G)
+            refine(ctx, ch.fronts, ch.nf, N, fctx.Mlow, N, nrhs, G, N, Gb, N, fctx.ws, fctx.steps,
+                   fctx.tol)
+            gA = None
+            if fctx.needs_input_grad[0]:
+                out = torch.empty((N, N), dtype=torch.float64, device=X.device)
+                sym_grad_dense(ctx, N, nrhs, Gb, N, X, N, out, N)
+                gA = out.t()
+            gB = Gb.t().reshape(fctx.bshape) if fctx.needs_input_grad[1] else None
+            return gA, gB, None, None, None, None, None, None, None
+
+    _SymSolve = SymSolve
+    return SymSolve
+
+
+def sym_solve(A, B, ctx=None, pivot="strict", prec="fp64", p_first=256, w_rest=256,
+              pivot_rest="tpp", steps=10, tol=1e-14):
+    """Differentiable X = M^{-1} B for a symmetric indefinite M given by the lower
+    triangle of the (N, N) float64 CUDA tensor A (the strict upper triangle is
+    not read, and its gradient is zero); B is (N,) or (N, nrhs).  The first
+    front (p_first columns) uses `pivot`/`prec`, the rest `pivot_rest` in FP64."""
+    ctx = ctx or default_context()
+    o1 = options(pivot=pivot, prec=prec)
+    o2 = options(pivot=pivot_rest)
+    return _sym_solve_fn().apply(A, B, ctx, p_first, o1, w_rest, o2, steps, tol)
 
 
 def backward_error(ctx: Context, N, M, ldm, nrhs, B, ldb, X, ldx, berr, ws, stream=None):
