@@ -117,3 +117,80 @@ def dense_symmetric(N, seed=0, dist="normal"):
     rng = np.random.default_rng(seed)
     X = rng.standard_normal((N, N)) if dist == "normal" else rng.uniform(-1.0, 1.0, (N, N))
     return np.asfortranarray(np.tril(X) + np.tril(X, -1).T)
+
+
+def laplacian_3d(k, sigma=3.0):
+    """The 7-point Laplacian on a k x k x k grid (Dirichlet boundary) shifted by
+    -sigma I: diagonal 6 - sigma, -1 for each grid neighbour.  sigma = 3 is half
+    the mean eigenvalue (trace/N = 6), which makes the matrix indefinite.
+    Variable of grid point (x, y, z) is x + k (y + k z).  Returns the lower
+    triangle in compressed-column form: (colptr int64[N+1], rowind int32[nnz],
+    val float64[nnz]), rows ascending within a column, the diagonal first."""
+    N = k ** 3
+    idx = np.arange(N).reshape(k, k, k)  # [z, y, x]
+    cols = [[] for _ in range(N)]
+    rows, cidx, vals = [], [], []
+    for (dz, dy, dx) in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+        a = idx[: k - dz, : k - dy, : k - dx].ravel()
+        b = idx[dz:, dy:, dx:].ravel()
+        rows.append(b)
+        cidx.append(a)
+    r = np.concatenate([np.arange(N)] + rows)
+    c = np.concatenate([np.arange(N)] + cidx)
+    v = np.concatenate([np.full(N, 6.0 - sigma), -np.ones(sum(len(x) for x in rows))])
+    order = np.lexsort((r, c))
+    r, c, v = r[order], c[order], v[order]
+    colptr = np.zeros(N + 1, np.int64)
+    np.add.at(colptr, c + 1, 1)
+    colptr = np.cumsum(colptr)
+    return colptr, r.astype(np.int32), v
+
+
+def nested_dissection_3d(k, leaf=64):
+    """Geometric nested dissection of the k x k x k grid: a box is cut by the
+    middle plane across its longest side; the two halves are ordered first (each
+    recursively), the plane last.  Boxes of at most `leaf` points are not cut.
+    Returns (perm, blocks): perm[q] = variable eliminated q-th; blocks = start
+    positions of the blocks in that order (each leaf box and each plane is one
+    block, children before parents), with blocks[-1] = N."""
+    perm, blocks = [], []
+
+    def rec(x0, x1, y0, y1, z0, z1):
+        sx, sy, sz = x1 - x0, y1 - y0, z1 - z0
+        if sx <= 0 or sy <= 0 or sz <= 0:
+            return
+        if sx * sy * sz <= leaf or max(sx, sy, sz) < 3:
+            blocks.append(len(perm))
+            for z in range(z0, z1):
+                for y in range(y0, y1):
+                    for x in range(x0, x1):
+                        perm.append(x + k * (y + k * z))
+            return
+        if sx >= sy and sx >= sz:
+            m = x0 + sx // 2
+            rec(x0, m, y0, y1, z0, z1)
+            rec(m + 1, x1, y0, y1, z0, z1)
+            blocks.append(len(perm))
+            for z in range(z0, z1):
+                for y in range(y0, y1):
+                    perm.append(m + k * (y + k * z))
+        elif sy >= sz:
+            m = y0 + sy // 2
+            rec(x0, x1, y0, m, z0, z1)
+            rec(x0, x1, m + 1, y1, z0, z1)
+            blocks.append(len(perm))
+            for z in range(z0, z1):
+                for x in range(x0, x1):
+                    perm.append(x + k * (m + k * z))
+        else:
+            m = z0 + sz // 2
+            rec(x0, x1, y0, y1, z0, m)
+            rec(x0, x1, y0, y1, m + 1, z1)
+            blocks.append(len(perm))
+            for y in range(y0, y1):
+                for x in range(x0, x1):
+                    perm.append(x + k * (y + k * m))
+
+    rec(0, k, 0, k, 0, k)
+    blocks.append(len(perm))
+    return np.asarray(perm, np.int32), np.asarray(blocks, np.int64)
