@@ -344,6 +344,59 @@ ctp_status ctp_sym_grad_pattern(ctp_ctx *ctx, int64_t nnz, const int32_t *row, c
                                 int64_t N, int32_t nrhs, const double *Gb, int64_t ldg,
                                 const double *X, int64_t ldx, double *out, void *stream);
 
+/* The same for a sparse M given by its lower triangle in compressed columns
+ * (device arrays: colptr int64[N+1], rowind int32[nnz] with rows >= the column,
+ * val float64[nnz]); the residual applies both triangles. */
+ctp_status ctp_backward_error_csc(ctp_ctx *ctx, int64_t N, const int64_t *colptr, const int32_t *rowind,
+                                  const double *val, int32_t nrhs, const double *B, int64_t ldb,
+                                  const double *X, int64_t ldx, double *berr, void *workspace,
+                                  size_t ws_bytes, void *stream);
+ctp_status ctp_refine_csc(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
+                          const int64_t *colptr, const int32_t *rowind, const double *val, int32_t nrhs,
+                          const double *B, int64_t ldb, double *X, int64_t ldx, int32_t max_steps,
+                          double tol, double *berr_host, int32_t *steps_host, void *workspace,
+                          size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Multifrontal factorization of a sparse symmetric indefinite matrix (Section
+ * 1: Factor, Solve, Form and Scatter tasks over an assembly tree; delayed
+ * columns passed to the parent front).
+ *
+ * ctp_mf_analyse (host only): the lower triangle's pattern in compressed
+ *   columns (HOST arrays colptr int64[N+1], rowind int32[nnz], rows >= column),
+ *   an elimination order perm[q] = variable eliminated q-th, and its supernodes
+ *   as nblocks consecutive blocks of that order (blocks[0] = 0 < ... <
+ *   blocks[nblocks] = N; e.g. the separators and leaf boxes of nested
+ *   dissection).  Front s holds block s and struct(s), the later variables
+ *   joined to the block in the filled graph; its parent is the block of
+ *   struct(s)'s first variable.  *mf receives the analysis (owns host tables
+ *   and small device tables).
+ * ctp_mf_factor: the numeric factorization with values val (DEVICE float64[nnz],
+ *   in the pattern's order).  Fronts are processed children first: assembly of
+ *   original entries, extend-add of the children's contribution blocks, then
+ *   the fully-summed columns (the block's, then the children's delayed ones)
+ *   eliminated in panels of at most ctp_max_p() columns by ctp_factor_supernode
+ *   with opt (its smode is ignored: each panel's Form subtracts into the front,
+ *   whose trailing block becomes the contribution block).  A panel that
+ *   eliminates nothing ends its front; the columns left are delayed to the
+ *   parent.  A root front must eliminate all its columns (a panel there that
+ *   eliminates nothing is retried with CTP_PIV_TPP); otherwise CTP_ECAPACITY.
+ *   Device memory for the fronts is allocated by the call and held by *mf.
+ *   Synchronises `stream` once per panel.
+ * ctp_mf_fronts: the factored panels, in elimination order, as fronts for
+ *   ctp_solve / ctp_refine_csc (host array valid until the next factor or
+ *   destroy; rows name the ORIGINAL variables).
+ * ctp_mf_info: per block (up to cap): parent, front rows n, fully-summed
+ *   columns p (including delayed ones received), eliminated, delayed to parent. */
+typedef struct ctp_mf ctp_mf;
+ctp_status ctp_mf_analyse(ctp_ctx *ctx, int64_t N, const int64_t *colptr, const int32_t *rowind,
+                          const int32_t *perm, int32_t nblocks, const int64_t *blocks, ctp_mf **mf);
+ctp_status ctp_mf_factor(ctp_ctx *ctx, ctp_mf *mf, const double *val, const ctp_options *opt, void *stream);
+ctp_status ctp_mf_fronts(const ctp_mf *mf, int32_t *nf, const ctp_sfront **fronts);
+ctp_status ctp_mf_info(const ctp_mf *mf, int32_t cap, int32_t *nblocks, int32_t *parent, int64_t *n,
+                       int64_t *p, int64_t *nelim, int64_t *ndelayed);
+ctp_status ctp_mf_destroy(ctp_mf *mf);
+
 typedef struct ctp_chain ctp_chain;
 
 /* Factor a dense symmetric matrix M (order N, lower triangle, column-major,

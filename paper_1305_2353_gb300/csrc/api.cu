@@ -5,16 +5,10 @@
 
 #include <vector>
 
-#include "ctp_internal.cuh"
+#include "chain.cuh"
+#include "ctx.cuh"
 
-namespace {
-constexpr int kMaxRec = 4096;
-enum KernelId {
-    K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP,
-    K_B_PREPARE, K_B_COMPRESS, K_B_FACTOR_G1, K_B_FACTOR_G2, K_B_FACTOR_G4, K_B_FACTOR_G8,
-    K_B_FACTOR_G16, K_B_SOLVE, K_B_FORM, K_W21, K_SYS_FWD, K_SYS_BWD, K_SYMV, K_BERR, K_AXPY,
-    K_FORM_TC3, K_GRAD, K_NUM_IDS
-};
+namespace ctp {
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
                                        "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16",
                                        "tpp_full_column", "batch_prepare", "batch_compress_strict",
@@ -22,34 +16,8 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
                                        "batch_factor_g8", "batch_factor_g16", "batch_solve_fp64",
                                        "batch_form", "w21_from_l", "sys_forward", "sys_backward",
                                        "symv_residual", "backward_error", "axpy", "form_tc_bf16x3",
-                                       "sym_grad"};
-}  // namespace
-
-struct ctp_ctx {
-    int device;
-    int num_sms;
-    int form_walk;   // CTP_TUNE_FORM_WALK
-    int batch_smem_kb; // CTP_TUNE_BATCH_SMEM_KB
-    int factor_g;      // CTP_TUNE_FACTOR_G
-    bool profiling;
-    int nrec;
-    int rec_id[kMaxRec];
-    cudaEvent_t ev[2 * kMaxRec];
-    bool events_made;
-};
-
-// Launch `expr` (a cudaError_t expression enqueueing one kernel on `st`),
-// bracketed by profiling events when enabled.
-template <typename F>
-static cudaError_t timed(ctp_ctx *ctx, int id, cudaStream_t st, F &&launch) {
-    if (!ctx->profiling || ctx->nrec >= kMaxRec) return launch();
-    const int r = ctx->nrec++;
-    ctx->rec_id[r] = id;
-    cudaEventRecord(ctx->ev[2 * r], st);
-    cudaError_t e = launch();
-    cudaEventRecord(ctx->ev[2 * r + 1], st);
-    return e;
-}
+                                       "sym_grad", "mf_assemble", "mf_extend_add", "spmv_residual"};
+}  // namespace ctp
 
 namespace ctp {
 
@@ -86,10 +54,6 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
 
 using namespace ctp;
 
-#define CTP_CUDA(x)                            \
-    do {                                       \
-        if ((x) != cudaSuccess) return CTP_ECUDA; \
-    } while (0)
 
 extern "C" {
 
@@ -507,47 +471,68 @@ ctp_status ctp_refine_workspace_size(int64_t N, int64_t nmax, int32_t nrhs, size
     return CTP_OK;
 }
 
-// R = B - M X, then the backward errors into berr (device)
-static cudaError_t residual_berr(ctp_ctx *ctx, int64_t N, const double *M, int64_t ldm, int nrhs,
-                                 const double *B, int64_t ldb, const double *X, int64_t ldx,
-                                 double *R, const double *rowsum, double *mx, double *berr,
-                                 cudaStream_t st) {
+// The system matrix of a residual: dense (lower triangle, column-major) or
+// sparse (lower triangle in compressed columns), symmetric either way.
+struct MatOp {
+    const double *M = nullptr;
+    int64_t ldm = 0;
+    const int64_t *colptr = nullptr;
+    const int32_t *rowind = nullptr;
+    const double *val = nullptr;
+    bool sparse() const { return colptr != nullptr; }
+};
+
+static cudaError_t mat_residual(ctp_ctx *ctx, const MatOp &A, int64_t N, int nrhs, const double *X,
+                                int64_t ldx, double *R, cudaStream_t st) {
+    if (A.sparse())
+        return timed(ctx, K_SPMV, st, [&] {
+            return launch_spmv_csc_residual(N, A.colptr, A.rowind, A.val, nrhs, X, ldx, R, N, st);
+        });
+    return timed(ctx, K_SYMV, st, [&] { return launch_symv_residual(N, A.M, A.ldm, nrhs, X, ldx, R, N, st); });
+}
+
+static cudaError_t mat_abs_rowsum(ctp_ctx *ctx, const MatOp &A, int64_t N, double *rowsum, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(rowsum, 0, sizeof(double) * N, st);
+    if (e != cudaSuccess) return e;
+    if (A.sparse())
+        return timed(ctx, K_SPMV, st, [&] {
+            return launch_spmv_csc_abs_rowsum(N, A.colptr, A.rowind, A.val, rowsum, st);
+        });
+    return timed(ctx, K_SYMV, st, [&] { return launch_abs_rowsum(N, A.M, A.ldm, rowsum, st); });
+}
+
+// R = B - A X, then the backward errors into berr (device)
+static cudaError_t residual_berr(ctp_ctx *ctx, const MatOp &A, int64_t N, int nrhs, const double *B,
+                                 int64_t ldb, const double *X, int64_t ldx, double *R, const double *rowsum,
+                                 double *mx, double *berr, cudaStream_t st) {
     cudaError_t e = cudaMemcpy2DAsync(R, sizeof(double) * N, B, sizeof(double) * ldb,
                                       sizeof(double) * N, nrhs, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    e = timed(ctx, K_SYMV, st, [&] { return launch_symv_residual(N, M, ldm, nrhs, X, ldx, R, N, st); });
+    e = mat_residual(ctx, A, N, nrhs, X, ldx, R, st);
     if (e != cudaSuccess) return e;
     return timed(ctx, K_BERR, st, [&] {
         return launch_backward_error(N, nrhs, R, N, X, ldx, B, ldb, rowsum, mx, berr, st);
     });
 }
 
-ctp_status ctp_backward_error(ctp_ctx *ctx, int64_t N, const double *M, int64_t ldm, int32_t nrhs,
-                              const double *B, int64_t ldb, const double *X, int64_t ldx,
-                              double *berr, void *workspace, size_t ws_bytes, void *stream) {
-    if (ctx == nullptr || M == nullptr || B == nullptr || X == nullptr || berr == nullptr ||
-        workspace == nullptr || N < 1 || nrhs < 1 || ldm < N || ldb < N || ldx < N)
-        return CTP_EINVAL;
+static ctp_status backward_error_impl(ctp_ctx *ctx, const MatOp &A, int64_t N, int32_t nrhs,
+                                      const double *B, int64_t ldb, const double *X, int64_t ldx,
+                                      double *berr, void *workspace, size_t ws_bytes, void *stream) {
     RefineLayout L = refine_layout(N, 0, nrhs);
     if (ws_bytes < L.total) return CTP_ENOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)workspace;
     double *rowsum = (double *)(w + L.rowsum);
-    CTP_CUDA(cudaMemsetAsync(rowsum, 0, sizeof(double) * N, st));
-    CTP_CUDA(timed(ctx, K_SYMV, st, [&] { return launch_abs_rowsum(N, M, ldm, rowsum, st); }));
-    CTP_CUDA(residual_berr(ctx, N, M, ldm, nrhs, B, ldb, X, ldx, (double *)(w + L.R), rowsum,
+    CTP_CUDA(mat_abs_rowsum(ctx, A, N, rowsum, st));
+    CTP_CUDA(residual_berr(ctx, A, N, nrhs, B, ldb, X, ldx, (double *)(w + L.R), rowsum,
                            (double *)(w + L.mx), berr, st));
     return CTP_OK;
 }
 
-ctp_status ctp_refine(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
-                      const double *M, int64_t ldm, int32_t nrhs, const double *B, int64_t ldb,
-                      double *X, int64_t ldx, int32_t max_steps, double tol, double *berr_host,
-                      int32_t *steps_host, void *workspace, size_t ws_bytes, void *stream) {
-    if (ctx == nullptr || M == nullptr || B == nullptr || X == nullptr || berr_host == nullptr ||
-        steps_host == nullptr || workspace == nullptr || N < 1 || nrhs < 1 || ldm < N ||
-        ldb < N || ldx < N || max_steps < 0 || max_steps > 100 || !(tol >= 0.0))
-        return CTP_EINVAL;
+static ctp_status refine_impl(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N, const MatOp &A,
+                              int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                              int32_t max_steps, double tol, double *berr_host, int32_t *steps_host,
+                              void *workspace, size_t ws_bytes, void *stream) {
     int64_t nmax = 0;
     for (int32_t k = 0; k < nf && fronts != nullptr; k++) nmax = fronts[k].n > nmax ? fronts[k].n : nmax;
     ctp_status s = check_fronts(nf, fronts, N, nmax);
@@ -560,13 +545,12 @@ ctp_status ctp_refine(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_
     double *R = (double *)(w + L.R), *rowsum = (double *)(w + L.rowsum);
     double *mx = (double *)(w + L.mx), *berr = (double *)(w + L.berr);
     *steps_host = 0;
-    CTP_CUDA(cudaMemsetAsync(rowsum, 0, sizeof(double) * N, st));
-    CTP_CUDA(timed(ctx, K_SYMV, st, [&] { return launch_abs_rowsum(N, M, ldm, rowsum, st); }));
+    CTP_CUDA(mat_abs_rowsum(ctx, A, N, rowsum, st));
     CTP_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * ldx, B, sizeof(double) * ldb, sizeof(double) * N,
                                nrhs, cudaMemcpyDeviceToDevice, st));
     CTP_CUDA(solve_fronts(ctx, nf, fronts, nrhs, X, ldx, sws, st));
     for (int32_t k = 0;; k++) {
-        CTP_CUDA(residual_berr(ctx, N, M, ldm, nrhs, B, ldb, X, ldx, R, rowsum, mx, berr, st));
+        CTP_CUDA(residual_berr(ctx, A, N, nrhs, B, ldb, X, ldx, R, rowsum, mx, berr, st));
         double *bh = berr_host + (size_t)k * nrhs;
         CTP_CUDA(cudaMemcpyAsync(bh, berr, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
         CTP_CUDA(cudaStreamSynchronize(st));
@@ -580,21 +564,83 @@ ctp_status ctp_refine(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_
     return CTP_OK;
 }
 
+ctp_status ctp_backward_error(ctp_ctx *ctx, int64_t N, const double *M, int64_t ldm, int32_t nrhs,
+                              const double *B, int64_t ldb, const double *X, int64_t ldx,
+                              double *berr, void *workspace, size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || M == nullptr || B == nullptr || X == nullptr || berr == nullptr ||
+        workspace == nullptr || N < 1 || nrhs < 1 || ldm < N || ldb < N || ldx < N)
+        return CTP_EINVAL;
+    MatOp A;
+    A.M = M;
+    A.ldm = ldm;
+    return backward_error_impl(ctx, A, N, nrhs, B, ldb, X, ldx, berr, workspace, ws_bytes, stream);
+}
+
+ctp_status ctp_backward_error_csc(ctp_ctx *ctx, int64_t N, const int64_t *colptr, const int32_t *rowind,
+                                  const double *val, int32_t nrhs, const double *B, int64_t ldb,
+                                  const double *X, int64_t ldx, double *berr, void *workspace,
+                                  size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || colptr == nullptr || rowind == nullptr || val == nullptr || B == nullptr ||
+        X == nullptr || berr == nullptr || workspace == nullptr || N < 1 || nrhs < 1 || ldb < N || ldx < N)
+        return CTP_EINVAL;
+    MatOp A;
+    A.colptr = colptr;
+    A.rowind = rowind;
+    A.val = val;
+    return backward_error_impl(ctx, A, N, nrhs, B, ldb, X, ldx, berr, workspace, ws_bytes, stream);
+}
+
+ctp_status ctp_refine(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
+                      const double *M, int64_t ldm, int32_t nrhs, const double *B, int64_t ldb,
+                      double *X, int64_t ldx, int32_t max_steps, double tol, double *berr_host,
+                      int32_t *steps_host, void *workspace, size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || M == nullptr || B == nullptr || X == nullptr || berr_host == nullptr ||
+        steps_host == nullptr || workspace == nullptr || N < 1 || nrhs < 1 || ldm < N ||
+        ldb < N || ldx < N || max_steps < 0 || max_steps > 100 || !(tol >= 0.0))
+        return CTP_EINVAL;
+    MatOp A;
+    A.M = M;
+    A.ldm = ldm;
+    return refine_impl(ctx, nf, fronts, N, A, nrhs, B, ldb, X, ldx, max_steps, tol, berr_host, steps_host,
+                       workspace, ws_bytes, stream);
+}
+
+ctp_status ctp_refine_csc(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, int64_t N,
+                          const int64_t *colptr, const int32_t *rowind, const double *val, int32_t nrhs,
+                          const double *B, int64_t ldb, double *X, int64_t ldx, int32_t max_steps,
+                          double tol, double *berr_host, int32_t *steps_host, void *workspace,
+                          size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || colptr == nullptr || rowind == nullptr || val == nullptr || B == nullptr ||
+        X == nullptr || berr_host == nullptr || steps_host == nullptr || workspace == nullptr || N < 1 ||
+        nrhs < 1 || ldb < N || ldx < N || max_steps < 0 || max_steps > 100 || !(tol >= 0.0))
+        return CTP_EINVAL;
+    MatOp A;
+    A.colptr = colptr;
+    A.rowind = rowind;
+    A.val = val;
+    return refine_impl(ctx, nf, fronts, N, A, nrhs, B, ldb, X, ldx, max_steps, tol, berr_host, steps_host,
+                       workspace, ws_bytes, stream);
+}
+
 }  // extern "C"
 
 struct ctp_chain {
     std::vector<ctp_sfront> fronts;
-    std::vector<void *> blocks;
     std::vector<int32_t> nelim, p, pivot;
+    Arena arena;
 };
 
 namespace {
 void chain_free(ctp_chain *c) {
     if (c == nullptr) return;
-    for (void *b : c->blocks) cudaFree(b);
+    c->arena.release();
     delete c;
 }
 }  // namespace
+
+namespace ctp {
+int ctx_num_sms(const ctp_ctx *ctx) { return ctx->num_sms; }
+}  // namespace ctp
 
 extern "C" {
 
@@ -608,120 +654,31 @@ ctp_status ctp_factor_dense(ctp_ctx *ctx, int64_t N, double *M, int64_t ldm, int
     if (s == CTP_OK) s = check_opts(opt_rest);
     if (s != CTP_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    ctp_options o[2] = {*opt_first, *opt_rest};
-    for (ctp_options &x : o) {
-        x.smode = CTP_S_FP64_SUB;
-        if (x.pivot == CTP_PIV_TPP) x.prec = CTP_FP64;
-    }
-    ctp_options otpp = o[1];
-    otpp.pivot = CTP_PIV_TPP;
-    otpp.prec = CTP_FP64;
-    const int wmax = p_first > w_rest ? p_first : w_rest;
-    size_t wsb = 0;
-    // workspace sizes grow with n for a fixed width: size for N rows at both widths
-    const ctp_options *cand[3] = {&o[0], &o[1], &otpp};
-    const int widths[2] = {(int)(p_first < N ? p_first : N), (int)(w_rest < N ? w_rest : N)};
-    for (const ctp_options *x : cand)
-        for (int wd : widths) {
-            const size_t b = ws_layout(N, wd, x, ctx->num_sms).total;
-            wsb = b > wsb ? b : wsb;
-        }
+    ChainCfg cfg;
+    cfg.w_first = p_first;
+    cfg.w_rest = w_rest;
+    cfg.o_first = *opt_first;
+    cfg.o_rest = *opt_rest;
+    cfg.retry_tpp = true;
+    cfg.must_finish = true;
     ctp_chain *c = new ctp_chain();
-    void *ws = nullptr, *snap = nullptr;
-    int32_t *hbuf = nullptr;
-    std::vector<int32_t> ord(N), tmp(kMaxP);
+    c->arena.chunk_bytes = (size_t)64 << 20;
+    std::vector<int32_t> ord(N);
     for (int64_t i = 0; i < N; i++) ord[i] = (int32_t)i;
-    ctp_status rc = CTP_OK;
-#define CHAIN_CUDA(x)             \
-    do {                          \
-        if ((x) != cudaSuccess) { \
-            rc = CTP_ECUDA;       \
-            goto done;            \
-        }                         \
-    } while (0)
-    CHAIN_CUDA(cudaMalloc(&ws, wsb));
-    CHAIN_CUDA(cudaMalloc(&snap, sizeof(double) * (size_t)N * wmax));
-    CHAIN_CUDA(cudaMallocHost((void **)&hbuf, sizeof(int32_t) * (kMaxP + 2)));
-    {
-        int64_t col = 0;
-        bool first = true;
-        while (col < N) {
-            const int64_t nk = N - col;
-            const ctp_options &opt = first ? o[0] : o[1];
-            const int w = (int)((first ? p_first : w_rest) < nk ? (first ? p_first : w_rest) : nk);
-            first = false;
-            // one device block per front: rows | perm | piv | nelim | D
-            const size_t ints = (size_t)nk + 2 * (size_t)w + 2;
-            const size_t bytes = align256(sizeof(int32_t) * ints) + sizeof(double) * 2 * (size_t)w;
-            void *blk = nullptr;
-            CHAIN_CUDA(cudaMalloc(&blk, bytes));
-            c->blocks.push_back(blk);
-            int32_t *rows = (int32_t *)blk, *perm = rows + nk, *piv = perm + w, *nel = piv + w;
-            double *D = (double *)((char *)blk + align256(sizeof(int32_t) * ints));
-            CHAIN_CUDA(cudaMemcpyAsync(rows, ord.data() + col, sizeof(int32_t) * nk,
-                                       cudaMemcpyHostToDevice, st));
-            double *A = M + col * ldm + col;
-            double *S = nk > w ? A + (int64_t)w * ldm + w : nullptr;
-            ctp_options ok = opt;
-            if (nk == w) ok.smode = CTP_S_NONE;
-            if (ok.pivot != CTP_PIV_TPP)
-                CHAIN_CUDA(cudaMemcpy2DAsync(snap, sizeof(double) * nk, A, sizeof(double) * ldm,
-                                             sizeof(double) * nk, w, cudaMemcpyDeviceToDevice, st));
-            int32_t info = CTP_OK, e = 0;
-            for (int attempt = 0; attempt < 2; attempt++) {
-                rc = ctp_factor_supernode(ctx, nk, w, A, ldm, &ok, perm, piv, D, nel, S, ldm, ws, wsb,
-                                          stream);
-                if (rc != CTP_OK) goto done;
-                CHAIN_CUDA(cudaMemcpyAsync(hbuf, nel, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-                CHAIN_CUDA(cudaMemcpyAsync(hbuf + 1, perm, sizeof(int32_t) * w, cudaMemcpyDeviceToHost, st));
-                CHAIN_CUDA(cudaMemcpyAsync(&info, ws, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-                CHAIN_CUDA(cudaStreamSynchronize(st));
-                if (info != CTP_OK) {
-                    rc = (ctp_status)info;
-                    goto done;
-                }
-                e = hbuf[0];
-                if (e > 0 || ok.pivot == CTP_PIV_TPP) break;
-                // nothing eliminated: put the front back and use full-column pivoting
-                CHAIN_CUDA(cudaMemcpy2DAsync(A, sizeof(double) * ldm, snap, sizeof(double) * nk,
-                                             sizeof(double) * nk, w, cudaMemcpyDeviceToDevice, st));
-                const int sm = ok.smode;
-                ok = otpp;
-                ok.smode = sm;
-            }
-            if (e < 1 || (nk == w && e < w)) {
-                rc = CTP_ECAPACITY;
-                goto done;
-            }
-            for (int q = 0; q < w; q++) tmp[q] = ord[col + hbuf[1 + q]];
-            for (int q = 0; q < w; q++) ord[col + q] = tmp[q];
-            ctp_sfront f;
-            f.n = nk;
-            f.p = w;
-            f.reserved = 0;
-            f.L = A;
-            f.ldl = ldm;
-            f.perm = perm;
-            f.piv = piv;
-            f.D = D;
-            f.nelim = nel;
-            f.rows = rows;
-            c->fronts.push_back(f);
-            c->nelim.push_back(e);
-            c->p.push_back(w);
-            c->pivot.push_back(ok.pivot);
-            col += e;
-        }
-    }
-done:
-#undef CHAIN_CUDA
+    std::vector<PanelRec> panels;
+    int64_t elim = 0;
+    ChainWork wk;
+    s = chain_factor(ctx, M, N, ldm, N, cfg, ord.data(), c->arena, wk, panels, &elim, st);
     cudaStreamSynchronize(st);
-    if (hbuf) cudaFreeHost(hbuf);
-    if (snap) cudaFree(snap);
-    if (ws) cudaFree(ws);
-    if (rc != CTP_OK) {
+    if (s != CTP_OK) {
         chain_free(c);
-        return rc;
+        return s;
+    }
+    for (const PanelRec &r : panels) {
+        c->fronts.push_back(r.f);
+        c->nelim.push_back(r.e);
+        c->p.push_back(r.w);
+        c->pivot.push_back(r.pivot);
     }
     *chain = c;
     return CTP_OK;

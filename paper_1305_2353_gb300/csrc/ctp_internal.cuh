@@ -166,6 +166,11 @@ cudaError_t launch_sym_grad_dense(int64_t N, int nrhs, const double *G, int64_t 
 cudaError_t launch_sym_grad_pattern(int64_t nnz, const int32_t *row, const int32_t *col, int nrhs,
                                     const double *G, int64_t ldg, const double *X, int64_t ldx,
                                     double *out, cudaStream_t st);
+cudaError_t launch_spmv_csc_residual(int64_t N, const int64_t *colptr, const int32_t *rowind,
+                                     const double *val, int nrhs, const double *X, int64_t ldx, double *R,
+                                     int64_t ldr, cudaStream_t st);
+cudaError_t launch_spmv_csc_abs_rowsum(int64_t N, const int64_t *colptr, const int32_t *rowind,
+                                       const double *val, double *rowsum, cudaStream_t st);
 cudaError_t launch_w21_from_l(const double *A, int64_t lda, int p, int64_t m, const int32_t *piv,
                               const double *D, const int32_t *nelim, double *W21, int64_t ldw,
                               cudaStream_t st);

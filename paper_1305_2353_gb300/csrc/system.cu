@@ -383,6 +383,40 @@ __global__ void __launch_bounds__(kTh) k_sym_grad_pattern(int64_t nnz, const int
     }
 }
 
+// R -= A X for a symmetric A given by its lower triangle in compressed columns
+// (kAbs: R += |A| 1, the row sums of |A|).  One warp per column j: the
+// column's entries update R(i) (atomics) and their transposes accumulate into
+// R(j).
+template <bool kAbs>
+__global__ void __launch_bounds__(kTh) k_spmv_csc(int64_t N, const int64_t *__restrict__ colptr,
+                                                  const int32_t *__restrict__ rowind,
+                                                  const double *__restrict__ val, int nrhs,
+                                                  const double *__restrict__ X, int64_t ldx, double *R,
+                                                  int64_t ldr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kTh / 32);
+    const int nr = kAbs ? 1 : nrhs;
+    for (int64_t j = (int64_t)blockIdx.x * (kTh / 32) + (threadIdx.x >> 5); j < N; j += warps) {
+        const int64_t q0 = colptr[j], q1 = colptr[j + 1];
+        for (int r = 0; r < nr; r++) {
+            const double xj = kAbs ? 1.0 : X[(int64_t)r * ldx + j];
+            double t = 0.0;
+            for (int64_t q = q0 + lane; q < q1; q += 32) {
+                const int64_t i = rowind[q];
+                const double a = kAbs ? fabs(val[q]) : val[q];
+                if (i == j) {
+                    t += a * xj;
+                } else {
+                    atomicAdd(R + (int64_t)r * ldr + i, kAbs ? a : -a * xj);
+                    t += a * (kAbs ? 1.0 : X[(int64_t)r * ldx + i]);
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) atomicAdd(R + (int64_t)r * ldr + j, kAbs ? t : -t);
+        }
+    }
+}
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kTh - 1) / kTh); }
 
 constexpr size_t kTriSmem = sizeof(double) * (size_t)(kJB + kRB) * kMaxP;
@@ -472,6 +506,21 @@ cudaError_t launch_sym_grad_pattern(int64_t nnz, const int32_t *row, const int32
     if (nnz == 0) return cudaSuccess;
     const unsigned g = blocks_for(nnz) < 4096 ? blocks_for(nnz) : 4096;
     k_sym_grad_pattern<<<g, kTh, 0, st>>>(nnz, row, col, nrhs, G, ldg, X, ldx, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_csc_residual(int64_t N, const int64_t *colptr, const int32_t *rowind,
+                                     const double *val, int nrhs, const double *X, int64_t ldx, double *R,
+                                     int64_t ldr, cudaStream_t st) {
+    const int64_t g = (N + 7) / 8 < 4096 ? (N + 7) / 8 : 4096;
+    k_spmv_csc<false><<<(unsigned)g, kTh, 0, st>>>(N, colptr, rowind, val, nrhs, X, ldx, R, ldr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_csc_abs_rowsum(int64_t N, const int64_t *colptr, const int32_t *rowind,
+                                       const double *val, double *rowsum, cudaStream_t st) {
+    const int64_t g = (N + 7) / 8 < 4096 ? (N + 7) / 8 : 4096;
+    k_spmv_csc<true><<<(unsigned)g, kTh, 0, st>>>(N, colptr, rowind, val, 1, nullptr, 0, rowsum, N);
     return cudaGetLastError();
 }
 

@@ -37,7 +37,8 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_backward_error", "ctp_refine", "ctp_factor_dense", "ctp_chain_fronts",
            "ctp_chain_info", "ctp_chain_destroy", "ctp_tune_set", "ctp_tune_get",
            "ctp_autotune_batch", "ctp_autotune_supernode", "ctp_adjoint_solve",
-           "ctp_sym_grad_dense", "ctp_sym_grad_pattern"]
+           "ctp_sym_grad_dense", "ctp_sym_grad_pattern", "ctp_backward_error_csc", "ctp_refine_csc",
+           "ctp_mf_analyse", "ctp_mf_factor", "ctp_mf_fronts", "ctp_mf_info", "ctp_mf_destroy"]
 TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G = 0, 1, 2
 WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
@@ -116,6 +117,14 @@ def load(path: str = LIB_PATH):
     L.ctp_adjoint_solve.argtypes = [P, i32, P, i64, i32, P, i64, P, sz, P]
     L.ctp_sym_grad_dense.argtypes = [P, i64, i32, P, i64, P, i64, P, i64, P]
     L.ctp_sym_grad_pattern.argtypes = [P, i64, P, P, i64, i32, P, i64, P, i64, P, P]
+    L.ctp_backward_error_csc.argtypes = [P, i64, P, P, P, i32, P, i64, P, i64, P, P, sz, P]
+    L.ctp_refine_csc.argtypes = [P, i32, P, i64, P, P, P, i32, P, i64, P, i64, i32, ctypes.c_double,
+                                 P, ctypes.POINTER(i32), P, sz, P]
+    L.ctp_mf_analyse.argtypes = [P, i64, P, P, P, i32, P, ctypes.POINTER(P)]
+    L.ctp_mf_factor.argtypes = [P, P, P, ctypes.POINTER(Options), P]
+    L.ctp_mf_fronts.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(P)]
+    L.ctp_mf_info.argtypes = [P, i32, ctypes.POINTER(i32), P, P, P, P, P]
+    L.ctp_mf_destroy.argtypes = [P]
     L.ctp_tune_set.argtypes = [P, i32, i32]
     L.ctp_tune_get.argtypes = [P, i32, ctypes.POINTER(i32)]
     L.ctp_autotune_batch.argtypes = [P, i32, P, P, ctypes.POINTER(Options), P, P, i32, P, i32, P, P,
@@ -546,6 +555,83 @@ def refine(ctx: Context, fronts, nf, N, M, ldm, nrhs, B, ldb, X, ldx, ws, max_st
                               ctypes.byref(steps), _ptr(ws), ws.numel(), _stream(stream)))
     k = int(steps.value)
     return hist[:(k + 1) * nrhs].reshape(k + 1, nrhs), k
+
+
+class Multifrontal:
+    """A sparse symmetric matrix (lower triangle in compressed columns, host
+    numpy arrays), analysed for an elimination order and its supernode blocks,
+    factored multifrontally on the device (``ctp_mf_*``)."""
+
+    def __init__(self, ctx: Context, colptr, rowind, val, perm, blocks):
+        import torch
+        self.ctx = ctx
+        dev = f"cuda:{ctx.device}"
+        self.N = len(colptr) - 1
+        self.colptr = np.ascontiguousarray(colptr, np.int64)
+        self.rowind = np.ascontiguousarray(rowind, np.int32)
+        self.perm = np.ascontiguousarray(perm, np.int32)
+        self.blocks = np.ascontiguousarray(blocks, np.int64)
+        self.d_colptr = torch.from_numpy(self.colptr).to(dev)
+        self.d_rowind = torch.from_numpy(self.rowind).to(dev)
+        self.d_val = torch.from_numpy(np.ascontiguousarray(val, np.float64)).to(dev)
+        h = ctypes.c_void_p()
+        _check("ctp_mf_analyse", ctx.lib.ctp_mf_analyse(
+            ctx.handle, self.N, self.colptr.ctypes.data_as(ctypes.c_void_p),
+            self.rowind.ctypes.data_as(ctypes.c_void_p), self.perm.ctypes.data_as(ctypes.c_void_p),
+            len(self.blocks) - 1, self.blocks.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self.handle = h
+        self.nf = 0
+        self.fronts = None
+
+    def factor(self, opt, stream=None):
+        _check("ctp_mf_factor", self.ctx.lib.ctp_mf_factor(
+            self.ctx.handle, self.handle, _ptr(self.d_val), ctypes.byref(opt), _stream(stream)))
+        nf = ctypes.c_int32()
+        arr = ctypes.c_void_p()
+        _check("ctp_mf_fronts", self.ctx.lib.ctp_mf_fronts(self.handle, ctypes.byref(nf),
+                                                           ctypes.byref(arr)))
+        self.nf = int(nf.value)
+        self.fronts = ctypes.cast(arr, ctypes.POINTER(SFront))
+
+    def info(self):
+        nb = len(self.blocks) - 1
+        par = np.zeros(nb, np.int32)
+        n, p, e, d = (np.zeros(nb, np.int64) for _ in range(4))
+        k = ctypes.c_int32()
+        _check("ctp_mf_info", self.ctx.lib.ctp_mf_info(
+            self.handle, nb, ctypes.byref(k), par.ctypes.data_as(ctypes.c_void_p),
+            n.ctypes.data_as(ctypes.c_void_p), p.ctypes.data_as(ctypes.c_void_p),
+            e.ctypes.data_as(ctypes.c_void_p), d.ctypes.data_as(ctypes.c_void_p)))
+        return dict(parent=par, n=n, p=p, nelim=e, delayed=d)
+
+    def panel_perms(self):
+        return [device_view(self.fronts[k].perm, int(self.fronts[k].p), "int32").cpu().numpy()
+                for k in range(self.nf)]
+
+    def refine(self, B, X, ws, max_steps=10, tol=1e-14, stream=None):
+        """Solve with FP64 refinement against the sparse matrix (device B, X
+        column-major N x nrhs tensors).  Returns (history, corrections)."""
+        nrhs = B.shape[0]
+        hist = np.zeros((max_steps + 1) * nrhs)
+        steps = ctypes.c_int32()
+        _check("ctp_refine_csc", self.ctx.lib.ctp_refine_csc(
+            self.ctx.handle, self.nf, ctypes.cast(self.fronts, ctypes.c_void_p), self.N,
+            _ptr(self.d_colptr), _ptr(self.d_rowind), _ptr(self.d_val), nrhs, _ptr(B), self.N,
+            _ptr(X), self.N, max_steps, tol, hist.ctypes.data, ctypes.byref(steps), _ptr(ws),
+            ws.numel(), _stream(stream)))
+        k = int(steps.value)
+        return hist[:(k + 1) * nrhs].reshape(k + 1, nrhs), k
+
+    def destroy(self):
+        if self.handle:
+            self.ctx.lib.ctp_mf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 class Batch:
