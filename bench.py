@@ -77,7 +77,7 @@ def parse_args():
     ap.add_argument("--pivot", default="relaxed", choices=["strict", "relaxed", "restricted"])
     ap.add_argument("--smode", default="fp64_packed",
                     choices=["none", "fp32", "fp64", "fp32_packed", "fp64_packed", "fp32_tiled"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16", "bf16x3"],
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16", "bf16x3", "bf16x6"],
                     help="Form arithmetic: FP64, or BF16 tensor cores with FP32 accumulation")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -92,6 +92,8 @@ def parse_args():
                          "(for profilers that cannot follow graph replays)")
     ap.add_argument("--no-system", action="store_true",
                     help="skip the complete-system leg (2-node embedding, refinement)")
+    ap.add_argument("--no-multifrontal", action="store_true",
+                    help="skip the multifrontal leg (64^3 Laplacian)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the extra measurement with the Form on the tensor cores")
     return ap.parse_args()
@@ -250,15 +252,15 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
         work = 8.0 * m * p
         bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
         achieved = work / t / 1e9
-    elif name in ("form_tc_bf16", "form_tc_bf16x3"):
+    elif name in ("form_tc_bf16", "form_tc_bf16x3", "form_tc_bf16x6"):
         # S written as FP32 (lower triangle) dominates the bytes: 128 flop/byte at
-        # e = 256 (three products per flop of S for the split form: 384), below
-        # the BF16 ridge, so the HBM roofline bounds this kernel
+        # e = 256 (x3 / x6 products per flop of S for the split forms), so the
+        # HBM roofline bounds the plain form; the split forms approach the tensor one
         _, form = flops_model(n, p, e)
-        split = name.endswith("x3")
-        work = 4.0 * m * (m + 1) / 2 + (2 if split else 1) * 2 * 2.0 * m * ((p + 63) // 64 * 64)
-        if split:
-            form *= 3  # tensor-core products actually executed
+        pieces = {"form_tc_bf16": 1, "form_tc_bf16x3": 2, "form_tc_bf16x6": 3}[name]
+        products = {1: 1, 2: 3, 3: 6}[pieces]
+        work = 4.0 * m * (m + 1) / 2 + pieces * 2 * 2.0 * m * ((p + 63) // 64 * 64)
+        form *= products  # tensor-core products actually executed
         bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
         achieved = work / t / 1e9
         tensor = form / t / 1e12
@@ -532,6 +534,61 @@ def measure_system(ctx, dev, inputs):
     return out
 
 
+def measure_multifrontal(ctx, dev, inputs, k=64, nrhs=16):
+    """Config 4: the 7-point Laplacian on a k^3 grid shifted by -3 I (indefinite),
+    geometric nested dissection, multifrontal factorization with strict
+    compressed pivoting (FP64, and with split-BF16 Forms), then nrhs N(0,1)
+    right-hand sides solved with FP64 refinement against the sparse matrix."""
+    import torch
+    from paper_1305_2353_gb300 import ctp
+    cp, ri, v = inputs.laplacian_3d(k, 3.0)
+    perm, blocks = inputs.nested_dissection_3d(k, 64)
+    N = k ** 3
+    t0 = time.perf_counter()
+    mf = ctp.Multifrontal(ctx, cp, ri, v, perm, blocks)
+    t_an = time.perf_counter() - t0
+    B = np.random.default_rng(0).standard_normal((N, nrhs))
+    out = {"workload": f"7-point Laplacian {k}^3 shifted by -3I (N={N}, nnz(lower)={len(v)}), geometric "
+                       f"nested dissection ({len(blocks) - 1} blocks, leaves <= 64 points), strict "
+                       f"compressed pivoting, {nrhs} RHS N(0,1), refinement to 1e-14 (<= 10 steps)",
+           "analyse_s": t_an}
+    for prec in ("fp64", "bf16x6", "bf16x3"):
+        opt = ctp.options(pivot="strict", prec=prec)
+        mf.factor(opt)   # warm-up (allocations, module loads)
+        torch.cuda.synchronize()
+        ctx.profile_begin()
+        t0 = time.perf_counter()
+        mf.factor(opt)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        kern = ctx.profile_end()
+        n, p, e = mf.panel_info()
+        fs = form = 0
+        for a, b, c in zip(n, p, e):
+            f1, f2 = flops_model(int(a), int(b), int(c))
+            fs += f1
+            form += f2
+        info = mf.info()
+        Bd = ctp.colmajor(B, dev)
+        X = torch.zeros_like(Bd)
+        ws = ctp.refine_workspace(ctx, N, int(info["n"].max()), nrhs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist, steps = mf.refine(Bd, X, ws)
+        torch.cuda.synchronize()
+        tr = time.perf_counter() - t0
+        out[prec] = {"factor_s": tf, "factor_gflops": (fs + form) / tf / 1e9,
+                     "flops": fs + form, "panels": int(mf.nf),
+                     "max_front_n": int(info["n"].max()), "delayed_total": int(info["delayed"].sum()),
+                     "refine_s": tr, "corrections": steps,
+                     "bwd_err_history": [float(x) for x in hist.max(axis=1)],
+                     "kernels": {kk: {"launches": vv[0], "ms": vv[1]} for kk, vv in kern.items()}}
+        del Bd, X, ws
+    mf.destroy()
+    torch.cuda.empty_cache()
+    return out
+
+
 def batch_accuracy(ctx, fronts, count=12, seed=0):
     """Equal-accuracy check of the batch's precisions: a seeded sample of the
     batch's fronts (spread over sizes), each embedded in its complete system and
@@ -597,6 +654,9 @@ def run_native(a):
     system = None
     if not a.no_system and rank == 0:
         system = measure_system(ctx, dev, inputs)
+    multifrontal = None
+    if not a.no_multifrontal and rank == 0:
+        multifrontal = measure_multifrontal(ctx, dev, inputs)
 
     batch = None
     if not a.no_batch:
@@ -658,6 +718,7 @@ def run_native(a):
             "mixed": mixed,
             "mixed_bf16": mixed_bf16,
             "complete_system": system,
+            "multifrontal": multifrontal,
             "tpp_comparator": tpp,
             "batch": batch,
         }

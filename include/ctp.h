@@ -66,11 +66,15 @@ typedef enum {
                       FP32 S (requires smode CTP_S_FP32, CTP_S_FP32_PACKED,
                       CTP_S_FP32_TILED or CTP_S_FP64_SUB); products carry the
                       BF16 rounding of L21 and W21 (relative 2^-8) */
-    CTP_BF16X3 = 2 /* as CTP_BF16, with each operand split into hi = bf16(x) and
-                      lo = bf16(x - hi) and the three products hi*hi + hi*lo + lo*hi
-                      accumulated in FP32 (Henry, Tang & Heinecke, 2019): products
-                      close to FP32 accuracy at the same bytes of S; the accuracy
-                      FP64 iterative refinement needs to converge */
+    CTP_BF16X3 = 2, /* as CTP_BF16, with each operand split into hi = bf16(x) and
+                       lo = bf16(x - hi) and the three products hi*hi + hi*lo + lo*hi
+                       accumulated in FP32 (Henry, Tang & Heinecke, 2019): products
+                       to about 2^-17 relative at the same bytes of S */
+    CTP_BF16X6 = 3  /* three pieces hi, mid = bf16(x - hi), lo = bf16(x - hi - mid)
+                       and the six products of total order <= 2 (hi*hi, hi*mid,
+                       mid*hi, hi*lo, lo*hi, mid*mid): products close to FP32
+                       accuracy, what FP64 refinement needs on worse-conditioned
+                       systems (e.g. the shifted 3D Laplacian) */
 } ctp_prec;
 
 /* Storage of the Schur complement S (its lower triangle only):
@@ -395,6 +399,8 @@ ctp_status ctp_mf_factor(ctp_ctx *ctx, ctp_mf *mf, const double *val, const ctp_
 ctp_status ctp_mf_fronts(const ctp_mf *mf, int32_t *nf, const ctp_sfront **fronts);
 ctp_status ctp_mf_info(const ctp_mf *mf, int32_t cap, int32_t *nblocks, int32_t *parent, int64_t *n,
                        int64_t *p, int64_t *nelim, int64_t *ndelayed);
+/* Per factored panel (up to cap, elimination order): rows n, columns p, eliminated. */
+ctp_status ctp_mf_panel_info(const ctp_mf *mf, int32_t cap, int64_t *n, int32_t *p, int32_t *nelim);
 ctp_status ctp_mf_destroy(ctp_mf *mf);
 
 typedef struct ctp_chain ctp_chain;
@@ -489,7 +495,7 @@ ctp_status ctp_autotune_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A,
 
 /* Optional per-kernel timing.  Between ctp_profile_begin() and ctp_profile_end()
  * every kernel this library launches is bracketed by two CUDA events recorded
- * on its launch stream (at most 4096 launches are recorded).  ctp_profile_end()
+ * on its launch stream (at most 32768 launches are recorded).  ctp_profile_end()
  * synchronises those events and reports, per kernel name, the number of
  * launches and their summed device time in milliseconds.  names receives up to
  * max_kernels NUL-terminated names of at most 47 characters, 48 bytes apart;

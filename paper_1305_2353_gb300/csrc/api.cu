@@ -16,7 +16,8 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
                                        "batch_factor_g8", "batch_factor_g16", "batch_solve_fp64",
                                        "batch_form", "w21_from_l", "sys_forward", "sys_backward",
                                        "symv_residual", "backward_error", "axpy", "form_tc_bf16x3",
-                                       "sym_grad", "mf_assemble", "mf_extend_add", "spmv_residual"};
+                                       "sym_grad", "mf_assemble", "mf_extend_add", "spmv_residual",
+                                       "form_tc_bf16x6"};
 }  // namespace ctp
 
 namespace ctp {
@@ -38,7 +39,7 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     L.W21 = off;
     off += align256(opt->smode != CTP_S_NONE && !tc ? sizeof(double) * (size_t)m * p : 0);
     // BF16 operand copies (hi, and for the split form the lo parts after them)
-    const size_t nb = tc ? 2 * (size_t)m * form_tc_kpad(p) * (opt->prec == CTP_BF16X3 ? 2 : 1) : 0;
+    const size_t nb = tc ? 2 * (size_t)m * form_tc_kpad(p) * prec_pieces(opt->prec) : 0;
     L.Wb = off;
     off += align256(nb);
     L.Lb = off;
@@ -93,7 +94,7 @@ static ctp_status check_opts(const ctp_options *opt) {
     if (!(opt->u > 0.0) || opt->u > 0.5) return CTP_EINVAL;
     if (!(opt->small >= 0.0)) return CTP_EINVAL;
     if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
-    if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16 && opt->prec != CTP_BF16X3) return CTP_EINVAL;
+    if (opt->prec < CTP_FP64 || opt->prec > CTP_BF16X6) return CTP_EINVAL;
     if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP64_SUB) return CTP_EINVAL;
     return CTP_OK;
 }
@@ -215,7 +216,8 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     void *Wb = tc ? (void *)(ws + L.Wb) : nullptr;
     void *Lbf = tc ? (void *)(ws + L.Lb) : nullptr;
     const int Kp = form_tc_kpad(p);
-    const int64_t lo_off = (tc && opt->prec == CTP_BF16X3) ? m * Kp : 0;
+    const int pieces = tc ? prec_pieces(opt->prec) : 0;
+    const int64_t lo_off = pieces > 1 ? m * Kp : 0;
     CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
 
     if (opt->pivot == CTP_PIV_TPP) {
@@ -272,12 +274,13 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     CTP_CUDA(timed(ctx, K_FACTOR, st, [&] { return launch_factor_cluster(fa, ctx->factor_g, st); }));
     if (m > 0)
         CTP_CUDA(timed(ctx, K_SOLVE, st, [&] {
-            return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, Wb, Lbf, Kp, lo_off, st);
+            return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, Wb, Lbf, Kp, lo_off, pieces,
+                                     st);
         }));
     if (opt->smode != CTP_S_NONE && m > 0) {
         if (tc)
-            CTP_CUDA(timed(ctx, lo_off ? K_FORM_TC3 : K_FORM_TC, st, [&] {
-                return launch_form_tc(Wb, Lbf, lo_off, m, Kp, nelim, (float *)S, lds,
+            CTP_CUDA(timed(ctx, pieces == 3 ? K_FORM_TC6 : (pieces == 2 ? K_FORM_TC3 : K_FORM_TC), st, [&] {
+                return launch_form_tc(Wb, Lbf, lo_off, pieces, m, Kp, nelim, (float *)S, lds,
                                       opt->smode == CTP_S_FP64_SUB ? 3
                                       : opt->smode == CTP_S_FP32_TILED ? 2 : (packed ? 1 : 0), info,
                                       ctx->num_sms, ctx->form_walk, st);

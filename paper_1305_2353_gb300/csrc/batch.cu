@@ -20,7 +20,7 @@
 namespace ctp {
 
 int64_t form_fp64_tiles(int64_t m);
-int64_t form_tc_tiles(int64_t m, bool split);
+int64_t form_tc_tiles(int64_t m, int pieces);
 
 namespace {
 
@@ -207,9 +207,9 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     *plan = nullptr;
     if (!(opt->u > 0.0) || opt->u > 0.5 || !(opt->small >= 0.0)) return CTP_EINVAL;
     if (opt->pivot != CTP_PIV_STRICT && opt->pivot != CTP_PIV_RESTRICTED) return CTP_EUNSUPPORTED;
-    if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16 && opt->prec != CTP_BF16X3) return CTP_EINVAL;
+    if (opt->prec < CTP_FP64 || opt->prec > CTP_BF16X6) return CTP_EINVAL;
     const bool tc = opt->prec != CTP_FP64 && opt->smode != CTP_S_NONE;
-    const bool split = tc && opt->prec == CTP_BF16X3;
+    const int pieces = tc ? prec_pieces(opt->prec) : 0;
     if (tc && opt->smode != CTP_S_FP32_TILED) return CTP_EUNSUPPORTED;
     if (!tc && opt->smode != CTP_S_NONE && opt->smode != CTP_S_FP64_PACKED &&
         opt->smode != CTP_S_FP32_PACKED)
@@ -251,7 +251,7 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         for (int64_t t = 0; t < nt; t++) sitem.push_back(f);
         b.f0 = (int64_t)fitem.size();
         if (opt->smode != CTP_S_NONE) {
-            const int64_t ft = tc ? form_tc_tiles(b.m, split) : form_fp64_tiles(b.m);
+            const int64_t ft = tc ? form_tc_tiles(b.m, pieces) : form_fp64_tiles(b.m);
             for (int64_t t = 0; t < ft; t++) fitem.push_back(f);
         }
         P->pmax = std::max(P->pmax, b.p);
@@ -301,12 +301,13 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     P->off_sections = off;
     off += align256(sec_off);
     // BF16 operand copies: hi rows, then (split) the lo rows
-    const size_t copies = split ? 2 : 1;
+    const size_t copies = pieces > 0 ? pieces : 1;
     P->off_wb = off;
     off += align256(tc ? 2 * copies * (size_t)row0 * kBatchKp : 0);
     P->off_lb = off;
     off += align256(tc ? 2 * copies * (size_t)row0 * kBatchKp : 0);
-    P->bo.lo_off = split ? row0 * kBatchKp : 0;
+    P->bo.lo_off = pieces > 1 ? row0 * kBatchKp : 0;
+    P->bo.pieces = pieces;
     P->total = off;
     // section offsets are relative to the sections base: shift them to the workspace base
     for (int f = 0; f < nb; f++) tab[f].ws += (int64_t)P->off_sections;
@@ -405,7 +406,7 @@ cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_
     const int *fitem = reinterpret_cast<const int *>(w + P->off_fitem);
     if (P->tc)
         return launch_form_tc_batch(fr, tab, fitem, P->f_items, P->total_rows, w + P->off_wb, w + P->off_lb,
-                                    P->bo.lo_off != 0, reinterpret_cast<int32_t *>(w + P->off_ginfo),
+                                    P->bo.pieces, reinterpret_cast<int32_t *>(w + P->off_ginfo),
                                     num_sms, st);
     return launch_form_fp64_batch(fr, tab, w, fitem, P->f_items, P->bo, st);
 }

@@ -30,6 +30,10 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms);
 int ctx_batch_smem_kb(const ctp_ctx *ctx);  // CTP_TUNE_BATCH_SMEM_KB of a context
+// BF16 pieces per operand of the tensor-core Form for a precision (0: FP64 Form)
+inline int prec_pieces(int prec) {
+    return prec == CTP_BF16 ? 1 : (prec == CTP_BF16X3 ? 2 : (prec == CTP_BF16X6 ? 3 : 0));
+}
 size_t factor_batch_max_dynamic_smem();     // dynamic shared memory the batched pivot search can take
 
 // ---------------------------------------------------------------------------
@@ -94,7 +98,8 @@ struct BatchOpts {
     double u, small;
     int pivot;  // ctp_pivot
     int smode, prec;
-    int64_t lo_off;  // elements from the hi to the lo BF16 operand copies (0: none)
+    int64_t lo_off;  // elements between the BF16 pieces of the operand copies
+    int pieces;      // BF16 pieces per operand (1: plain; 2, 3: split)
 };
 cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                 const int *list, int count, int G, int pmax, BatchOpts o,
@@ -110,7 +115,7 @@ cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, c
                                    cudaStream_t st);
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
-                                 bool split, int32_t *info, int num_sms, cudaStream_t st);
+                                 int pieces, int32_t *info, int num_sms, cudaStream_t st);
 constexpr int kBatchKp = 256;  // K stride of the stacked BF16 operand buffers
 
 // the batched launch sequence (batch.cu); the plan type is declared in ctp.h
@@ -126,7 +131,7 @@ cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,
                               double *W21, int64_t ldw, void *Wb, void *Lb, int Kp, int64_t lo_off,
-                              cudaStream_t st);
+                              int pieces, cudaStream_t st);
 
 // Threshold partial pivoting on all n rows (the comparator of the compressed path).
 size_t tpp_ws_bytes(int p);
@@ -136,8 +141,8 @@ cudaError_t launch_tpp(double *A, int64_t n, int p, int64_t lda, double u, doubl
 
 // K-padding of the BF16 operand copies used by the tensor-core Form.
 int form_tc_kpad(int p);
-// lo_off: elements from the hi BF16 copies to the lo copies (0: plain BF16).
-cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64_t m, int Kp,
+// pieces: BF16 pieces per operand (1 plain, 2 or 3 split), piece_off elements apart.
+cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t piece_off, int pieces, int64_t m, int Kp,
                            const int32_t *nelim, float *S, int64_t lds,
                            int layout /* 0 full, 1 packed, 2 tiled, 3 subtract from FP64 */,
                            int32_t *info, int num_sms, int walk /* ctp_walk */, cudaStream_t st);

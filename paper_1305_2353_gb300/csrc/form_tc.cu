@@ -144,26 +144,35 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[3
         : "r"(taddr));
 }
 
-// Tile shapes.  Plain BF16: tiles of 128 rows x 256 columns.  Split BF16
-// (kSplit): 128 x 128 tiles, and every operand is the pair hi = bf16(x),
-// lo = bf16(x - hi); the accumulator receives hi*hi + hi*lo + lo*hi, the
-// three-product scheme of Henry, Tang and Heinecke ("Leveraging the bfloat16
-// artificial intelligence datatype for higher-precision computations", 2019),
-// close to FP32 products.  Shared memory is the same in both modes: the
-// resident L21 block (KB blocks of 32 KB) and a 96 KB ring of W21 blocks.
-template <bool kSplit>
+// Tile shapes and operand pieces.  Plain BF16 (P = 1): tiles of 128 rows x
+// 256 columns.  Split BF16: every operand x is held as P BF16 pieces -- P = 2:
+// hi = bf16(x), lo = bf16(x - hi); P = 3: hi, mid = bf16(x - hi), lo =
+// bf16(x - hi - mid) -- and the accumulator receives the products of pieces
+// whose orders sum to at most P - 1 (P = 2: hi*hi + hi*lo + lo*hi; P = 3: the
+// six products hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid), the splitting
+// scheme of Henry, Tang and Heinecke ("Leveraging the bfloat16 artificial
+// intelligence datatype for higher-precision computations", 2019): P = 2
+// gives products close to 2^-17 relative accuracy, P = 3 close to FP32's.  Split
+// tiles are 128 x 128.  For P <= 2 the L21 block of a column block stays
+// resident in shared memory (K blocks of 32 KB) beside a 96 KB ring of W21
+// blocks; for P = 3 both operands stream through a 2-stage ring of 96 KB.
+template <int P>
 struct Cfg {
-    static constexpr int BN = kSplit ? 128 : 256;
+    static constexpr int BN = P == 1 ? 256 : 128;
     static constexpr int R = BN / kBM;                        // column blocks are R row blocks wide
-    static constexpr int Stages = kSplit ? 3 : 6;
+    static constexpr bool kResident = P < 3;
+    static constexpr int Stages = P == 1 ? 6 : (P == 2 ? 3 : 2);
     static constexpr uint32_t PieceA = kBM * kBK * 2;        // one 128 x 64 BF16 block
     static constexpr uint32_t PieceB = BN * kBK * 2;
-    static constexpr uint32_t StageA = PieceA * (kSplit ? 2 : 1);
-    static constexpr uint32_t StageB = PieceB * (kSplit ? 2 : 1);
+    static constexpr uint32_t StageA = PieceA * P + (kResident ? 0 : PieceB * P);
+    static constexpr uint32_t StageB = PieceB * P;           // resident block, per K block
+    static constexpr size_t ResidentBytes = kResident ? (size_t)kMaxKB * StageB : 0;
     static constexpr uint32_t TmemCols = 2 * BN;             // two FP32 accumulators
 };
-static_assert(Cfg<true>::StageB == kStageB && Cfg<false>::StageB == kStageB, "resident block size");
-static_assert(Cfg<true>::StageA * Cfg<true>::Stages == kStageA * kStages, "ring size");
+constexpr size_t kSmemBody = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA;
+static_assert(Cfg<1>::ResidentBytes + Cfg<1>::Stages * Cfg<1>::StageA <= kSmemBody, "smem P=1");
+static_assert(Cfg<2>::ResidentBytes + Cfg<2>::Stages * Cfg<2>::StageA <= kSmemBody, "smem P=2");
+static_assert(Cfg<3>::ResidentBytes + Cfg<3>::Stages * Cfg<3>::StageA <= kSmemBody, "smem P=3");
 
 // Tiles of the lower triangle, walked column block by column block: column
 // block b meets row blocks R*b..nM-1, so T(b) = b*nM - R*b(b-1)/2 tiles
@@ -280,21 +289,24 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
     return true;
 }
 
-// Maps: hi copies of W21 and L21 (mW, mL) and, for kSplit, the lo copies.
-template <bool kBatch, bool kSplit>
+// Maps: pieces 1..3 of W21 (mW1..3) and of L21 (mL1..3); pieces beyond P unused.
+template <bool kBatch, int P>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_form_tc(const __grid_constant__ CUtensorMap mW, const __grid_constant__ CUtensorMap mL,
-              const __grid_constant__ CUtensorMap mWl, const __grid_constant__ CUtensorMap mLl,
+    k_form_tc(const __grid_constant__ CUtensorMap mW1, const __grid_constant__ CUtensorMap mL1,
+              const __grid_constant__ CUtensorMap mW2, const __grid_constant__ CUtensorMap mL2,
+              const __grid_constant__ CUtensorMap mW3, const __grid_constant__ CUtensorMap mL3,
               int64_t m_single, const int32_t *__restrict__ nelim_p, float *__restrict__ S_single,
               int64_t lds_single, int layout_single, int32_t *__restrict__ info, int64_t ntiles_batch,
               BatchTab btab, int sched_mode) {
-    using C = Cfg<kSplit>;
+    using C = Cfg<P>;
     constexpr int BN = C::BN, R = C::R, NS = C::Stages;
+    const CUtensorMap *mapW[3] = {&mW1, &mW2, &mW3};
+    const CUtensorMap *mapL[3] = {&mL1, &mL2, &mL3};
     extern __shared__ unsigned char smraw[];
     __shared__ Bars bars;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sB = smem;                                 // [kMaxKB][StageB]: resident L21 block
-    uint8_t *sA = smem + (size_t)kMaxKB * C::StageB;   // [NS][StageA]: W21 ring
+    uint8_t *sB = smem;                       // [kMaxKB][StageB]: resident L21 block (P <= 2)
+    uint8_t *sA = smem + C::ResidentBytes;    // [NS][StageA]: W21 ring (and L21 for P = 3)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KB1 = kBatch ? 0 : (*nelim_p + kBK - 1) / kBK;
     Sched sc;
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (int64_t k = 0; TILE_K(k, x); k++) {
                 if (x.KB == 0) continue;
                 bool ok = true;
-                if (x.key != cur_key) {
+                if (C::kResident && x.key != cur_key) {
                     if (!mbar_wait(&bars.bempty, bphase ^ 1u, &bars)) {
                         atomicExch(&bars.abort, 1);
                         break;
@@ -353,8 +365,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     mbar_expect_tx(&bars.bfull, (uint32_t)x.KB * C::StageB);
                     for (int kb = 0; kb < x.KB; kb++) {
                         uint8_t *dst = sB + (size_t)kb * C::StageB;
-                        tma_load_2d(dst, &mL, kb * kBK, (int)x.brow, &bars.bfull);
-                        if (kSplit) tma_load_2d(dst + C::PieceB, &mLl, kb * kBK, (int)x.brow, &bars.bfull);
+#pragma unroll
+                        for (int pc = 0; pc < P; pc++)
+                            tma_load_2d(dst + pc * C::PieceB, mapL[pc], kb * kBK, (int)x.brow, &bars.bfull);
                     }
                     bphase ^= 1u;
                     cur_key = x.key;
@@ -366,8 +379,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     }
                     mbar_expect_tx(&bars.full[stage], C::StageA);
                     uint8_t *dst = sA + (size_t)stage * C::StageA;
-                    tma_load_2d(dst, &mW, kb * kBK, (int)x.arow, &bars.full[stage]);
-                    if (kSplit) tma_load_2d(dst + C::PieceA, &mWl, kb * kBK, (int)x.arow, &bars.full[stage]);
+#pragma unroll
+                    for (int pc = 0; pc < P; pc++)
+                        tma_load_2d(dst + pc * C::PieceA, mapW[pc], kb * kBK, (int)x.arow, &bars.full[stage]);
+                    if (!C::kResident) {
+#pragma unroll
+                        for (int pc = 0; pc < P; pc++)
+                            tma_load_2d(dst + P * C::PieceA + pc * C::PieceB, mapL[pc], kb * kBK, (int)x.brow,
+                                        &bars.full[stage]);
+                    }
                     if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
@@ -392,7 +412,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 tc_fence_after();
                 bool ok = true;
-                if (x.KB > 0 && x.key != cur_key) {
+                if (C::kResident && x.KB > 0 && x.key != cur_key) {
                     if (!mbar_wait(&bars.bfull, bphase, &bars)) {
                         atomicExch(&bars.abort, 1);
                         break;
@@ -409,15 +429,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + (size_t)stage * C::StageA);
-                    const uint32_t b0 = smem_u32(sB + (size_t)kb * C::StageB);
+                    const uint32_t b0 = C::kResident ? smem_u32(sB + (size_t)kb * C::StageB)
+                                                     : a0 + P * C::PieceA;
 #pragma unroll
                     for (int kk = 0; kk < kBK / kUmmaK; kk++) {
-                        // advance 16 BF16 = 32 bytes along K inside the swizzled rows
-                        const uint64_t ah = sdesc(a0 + kk * 32), bh = sdesc(b0 + kk * 32);
-                        umma_bf16(dt, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                        if (kSplit) {
-                            umma_bf16(dt, ah, sdesc(b0 + C::PieceB + kk * 32), idesc, 1u);
-                            umma_bf16(dt, sdesc(a0 + C::PieceA + kk * 32), bh, idesc, 1u);
+                        // advance 16 BF16 = 32 bytes along K inside the swizzled rows;
+                        // products of pieces i, j with i + j <= P - 1
+                        const uint64_t a1 = sdesc(a0 + kk * 32), b1 = sdesc(b0 + kk * 32);
+                        umma_bf16(dt, a1, b1, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        if (P >= 2) {
+                            const uint64_t a2 = sdesc(a0 + C::PieceA + kk * 32);
+                            const uint64_t b2 = sdesc(b0 + C::PieceB + kk * 32);
+                            umma_bf16(dt, a1, b2, idesc, 1u);
+                            umma_bf16(dt, a2, b1, idesc, 1u);
+                            if (P >= 3) {
+                                umma_bf16(dt, a1, sdesc(b0 + 2 * C::PieceB + kk * 32), idesc, 1u);
+                                umma_bf16(dt, sdesc(a0 + 2 * C::PieceA + kk * 32), b1, idesc, 1u);
+                                umma_bf16(dt, a2, b2, idesc, 1u);
+                            }
                         }
                     }
                     umma_commit(&bars.empty[stage]);  // W21 stage free once these MMAs finish
@@ -432,7 +461,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 umma_commit(&bars.acc_full[acc]);  // accumulator ready
                 // release the resident L21 block when the next tile with work needs another
-                if (x.KB > 0) {
+                if (C::kResident && x.KB > 0) {
                     int next_key = -2;
                     TileInfo y;
                     for (int64_t kn = k + 1; TILE_K(kn, y); kn++) {
@@ -588,34 +617,50 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_
 int form_tc_kpad(int p) { return (p + kBK - 1) / kBK * kBK; }
 
 namespace {
-template <bool kBatch, bool kSplit>
+template <bool kBatch, int P>
 cudaError_t set_smem(size_t smem) {
-    return cudaFuncSetAttribute(k_form_tc<kBatch, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return cudaFuncSetAttribute(k_form_tc<kBatch, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
-constexpr size_t kSmemTC = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA + 1024;
+constexpr size_t kSmemTC = kSmemBody + 1024;
+
+int bn_of(int P) { return P == 1 ? Cfg<1>::BN : (P == 2 ? Cfg<2>::BN : Cfg<3>::BN); }
+
+// Tensor maps of the P pieces of both operands (pieces `off` elements apart).
+bool make_maps(CUtensorMap (&mW)[3], CUtensorMap (&mL)[3], const void *Wb, const void *Lb, int64_t off, int P,
+               int64_t rows, int Kp) {
+    for (int pc = 0; pc < 3; pc++) {
+        const int q = pc < P ? pc : 0;  // unused pieces: valid copies of the first
+        const char *w = (const char *)Wb + 2 * off * q, *l = (const char *)Lb + 2 * off * q;
+        if ((((uintptr_t)w) | ((uintptr_t)l)) & 15) return false;
+        if (!make_map(&mW[pc], w, rows, Kp, kBM) || !make_map(&mL[pc], l, rows, Kp, bn_of(P))) return false;
+    }
+    return true;
+}
+
+template <bool kBatch, int P>
+cudaError_t launch_p(int grid, const CUtensorMap (&mW)[3], const CUtensorMap (&mL)[3], int64_t m,
+                     const int32_t *nelim, float *S, int64_t lds, int layout, int32_t *info, int64_t items,
+                     const BatchTab &bt, int mode, cudaStream_t st) {
+    cudaError_t err = set_smem<kBatch, P>(kSmemTC);
+    if (err != cudaSuccess) return err;
+    k_form_tc<kBatch, P><<<grid, kThreadsTC, kSmemTC, st>>>(mW[0], mL[0], mW[1], mL[1], mW[2], mL[2], m, nelim, S,
+                                                             lds, layout, info, items, bt, mode);
+    return cudaGetLastError();
+}
 }  // namespace
 
-cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64_t m, int Kp,
+cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t piece_off, int pieces, int64_t m, int Kp,
                            const int32_t *nelim, float *S, int64_t lds, int layout, int32_t *info,
                            int num_sms, int walk, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    const bool split = lo_off != 0;
-    const void *Wl = split ? (const void *)((const char *)Wb + 2 * lo_off) : Wb;
-    const void *Ll = split ? (const void *)((const char *)Lb + 2 * lo_off) : Lb;
-    if ((((uintptr_t)Wb) | ((uintptr_t)Lb) | ((uintptr_t)Wl) | ((uintptr_t)Ll)) & 15)
-        return cudaErrorMisalignedAddress;
-    const int BN = split ? Cfg<true>::BN : Cfg<false>::BN, R = BN / kBM;
-    CUtensorMap mW, mL, mWl, mLl;
-    if (!make_map(&mW, Wb, m, Kp, kBM) || !make_map(&mL, Lb, m, Kp, BN) ||
-        !make_map(&mWl, Wl, m, Kp, kBM) || !make_map(&mLl, Ll, m, Kp, BN))
-        return cudaErrorInvalidValue;
-    cudaError_t err = split ? set_smem<false, true>(kSmemTC) : set_smem<false, false>(kSmemTC);
-    if (err != cudaSuccess) return err;
+    if (pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
+    CUtensorMap mW[3], mL[3];
+    if (!make_maps(mW, mL, Wb, Lb, piece_off, pieces, m, Kp)) return cudaErrorInvalidValue;
+    const int R = bn_of(pieces) / kBM;
     const int nM = (int)((m + kBM - 1) / kBM);
     const int64_t ntiles = tile_count(nM, R), nN = col_blocks(nM, R);
-    // walk: CTP_WALK_AUTO picks panels when the split operands (twice the
-    // bytes) need the L2-friendly walk, contiguous runs otherwise
+    // walk: CTP_WALK_AUTO picks panels when the split operands (two or three
+    // times the bytes) need the L2-friendly walk, contiguous runs otherwise
     int mode;
     if (walk == CTP_WALK_ROUND_ROBIN)
         mode = 0;
@@ -624,47 +669,32 @@ cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t lo_off, int64
     else if (walk == CTP_WALK_PANELS)
         mode = nN >= (int64_t)num_sms ? 1 : 2;
     else
-        mode = (split && nN >= 2 * (int64_t)num_sms) ? 1 : 2;
+        mode = (pieces > 1 && nN >= 2 * (int64_t)num_sms) ? 1 : 2;
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
     BatchTab none = {nullptr, nullptr, nullptr};
-    if (split)
-        k_form_tc<false, true><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, m, nelim, S, lds, layout,
-                                                                   info, 0, none, mode);
-    else
-        k_form_tc<false, false><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, m, nelim, S, lds,
-                                                                    layout, info, 0, none, mode);
-    return cudaGetLastError();
+    if (pieces == 1) return launch_p<false, 1>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
+    if (pieces == 2) return launch_p<false, 2>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
+    return launch_p<false, 3>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
 }
 
-int64_t form_tc_tiles(int64_t m, bool split) {
-    const int R = (split ? Cfg<true>::BN : Cfg<false>::BN) / kBM;
+int64_t form_tc_tiles(int64_t m, int pieces) {
+    const int R = bn_of(pieces) / kBM;
     return m > 0 ? tile_count((m + kBM - 1) / kBM, R) : 0;
 }
 
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
-                                 bool split, int32_t *info, int num_sms, cudaStream_t st) {
+                                 int pieces, int32_t *info, int num_sms, cudaStream_t st) {
     if (items == 0) return cudaSuccess;
-    const int64_t lo = split ? total_rows * kBatchKp : 0;
-    const void *Wl = (const char *)Wb + 2 * lo, *Ll = (const char *)Lb + 2 * lo;
-    if ((((uintptr_t)Wb) | ((uintptr_t)Lb) | ((uintptr_t)Wl) | ((uintptr_t)Ll)) & 15)
-        return cudaErrorMisalignedAddress;
-    const int BN = split ? Cfg<true>::BN : Cfg<false>::BN;
-    CUtensorMap mW, mL, mWl, mLl;
-    if (!make_map(&mW, Wb, total_rows, kBatchKp, kBM) || !make_map(&mL, Lb, total_rows, kBatchKp, BN) ||
-        !make_map(&mWl, Wl, total_rows, kBatchKp, kBM) || !make_map(&mLl, Ll, total_rows, kBatchKp, BN))
+    if (pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
+    CUtensorMap mW[3], mL[3];
+    if (!make_maps(mW, mL, Wb, Lb, total_rows * kBatchKp, pieces, total_rows, kBatchKp))
         return cudaErrorInvalidValue;
-    cudaError_t err = split ? set_smem<true, true>(kSmemTC) : set_smem<true, false>(kSmemTC);
-    if (err != cudaSuccess) return err;
     const int grid = (int)(items < num_sms ? items : num_sms);
     BatchTab bt = {fronts, tab, item_front};
-    if (split)
-        k_form_tc<true, true><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, 0, nullptr, nullptr, 0, 2,
-                                                                  info, items, bt, 2);
-    else
-        k_form_tc<true, false><<<grid, kThreadsTC, kSmemTC, st>>>(mW, mL, mWl, mLl, 0, nullptr, nullptr, 0,
-                                                                   2, info, items, bt, 2);
-    return cudaGetLastError();
+    if (pieces == 1) return launch_p<true, 1>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
+    if (pieces == 2) return launch_p<true, 2>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
+    return launch_p<true, 3>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
 }
 
 }  // namespace ctp

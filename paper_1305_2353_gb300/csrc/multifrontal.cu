@@ -260,7 +260,7 @@ ctp_status ctp_mf_factor(ctp_ctx *ctx, ctp_mf *mf, const double *val, const ctp_
     if (ctx == nullptr || mf == nullptr || val == nullptr || opt == nullptr) return CTP_EINVAL;
     if (!(opt->u > 0.0) || opt->u > 0.5 || !(opt->small >= 0.0)) return CTP_EINVAL;
     if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
-    if (opt->prec != CTP_FP64 && opt->prec != CTP_BF16 && opt->prec != CTP_BF16X3) return CTP_EINVAL;
+    if (opt->prec < CTP_FP64 || opt->prec > CTP_BF16X6) return CTP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     // a fresh factorization: drop the previous one's memory
     mf->arena.release();
@@ -361,6 +361,16 @@ ctp_status ctp_mf_info(const ctp_mf *mf, int32_t cap, int32_t *nblocks, int32_t 
         if (p) p[s] = mf->factored ? b.p : b.hi - b.lo;
         if (nelim) nelim[s] = b.elim;
         if (ndelayed) ndelayed[s] = b.ndel;
+    }
+    return CTP_OK;
+}
+
+ctp_status ctp_mf_panel_info(const ctp_mf *mf, int32_t cap, int64_t *n, int32_t *p, int32_t *nelim) {
+    if (mf == nullptr || cap < 0 || !mf->factored) return CTP_EINVAL;
+    for (int32_t k = 0; k < (int32_t)mf->panels.size() && k < cap; k++) {
+        if (n) n[k] = mf->panels[k].f.n;
+        if (p) p[k] = mf->panels[k].w;
+        if (nelim) nelim[k] = mf->panels[k].e;
     }
     return CTP_OK;
 }

@@ -29,8 +29,8 @@ constexpr int kWarps = 8;   // warps per CTA: warp w updates the columns k = w (
 // per CTA (and three CTAs per SM) keep all four FP64 pipes of an SM busy.
 // One 32-row tile.  brow0: row of this front's first A21 row in the BF16
 // operand copies (0 for a single supernode; the stacked offset in a batch).
-// lo_off != 0: also write the lo parts bf16(x - bf16(x)) of the split
-// operands, lo_off elements after the hi copies.
+// pieces > 1: also write the further BF16 pieces of the split operands (piece
+// k rounds what pieces 0..k-1 left), lo_off elements apart.
 __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, int p, int64_t lda,
                                            const int32_t *__restrict__ perm,
                                            const int32_t *__restrict__ piv,
@@ -38,7 +38,7 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
                                            double *__restrict__ W21, int64_t ldw,
                                            __nv_bfloat16 *__restrict__ Wb,
                                            __nv_bfloat16 *__restrict__ Lb, int Kp, int64_t brow0,
-                                           int64_t lo_off, int64_t tile, double *xs) {
+                                           int64_t lo_off, int pieces, int64_t tile, double *xs) {
     constexpr int LDX = kRows + 1;
     const int64_t m = n - p;
     const int64_t row0 = tile * kRows;
@@ -88,11 +88,17 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
                 b.x = __double2bfloat16(v0);
                 b.y = __double2bfloat16(v1);
                 dst[k2] = b;
-                if (lo_off != 0) {  // split operands: lo = bf16(v - hi)
-                    __nv_bfloat162 l;
-                    l.x = __double2bfloat16(v0 - (double)__bfloat162float(b.x));
-                    l.y = __double2bfloat16(v1 - (double)__bfloat162float(b.y));
-                    dst[k2 + lo_off / 2] = l;
+                if (pieces > 1) {  // split operands: each piece rounds what the previous left
+                    double r0 = v0 - (double)__bfloat162float(b.x);
+                    double r1 = v1 - (double)__bfloat162float(b.y);
+                    for (int pc = 1; pc < pieces; pc++) {
+                        __nv_bfloat162 l;
+                        l.x = __double2bfloat16(r0);
+                        l.y = __double2bfloat16(r1);
+                        dst[k2 + pc * (lo_off / 2)] = l;
+                        r0 -= (double)__bfloat162float(l.x);
+                        r1 -= (double)__bfloat162float(l.y);
+                    }
                 }
             }
         }
@@ -146,11 +152,17 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
                 b.x = __double2bfloat16(v0);
                 b.y = __double2bfloat16(v1);
                 dst[k2] = b;
-                if (lo_off != 0) {  // split operands: lo = bf16(v - hi)
-                    __nv_bfloat162 l;
-                    l.x = __double2bfloat16(v0 - (double)__bfloat162float(b.x));
-                    l.y = __double2bfloat16(v1 - (double)__bfloat162float(b.y));
-                    dst[k2 + lo_off / 2] = l;
+                if (pieces > 1) {  // split operands: each piece rounds what the previous left
+                    double r0 = v0 - (double)__bfloat162float(b.x);
+                    double r1 = v1 - (double)__bfloat162float(b.y);
+                    for (int pc = 1; pc < pieces; pc++) {
+                        __nv_bfloat162 l;
+                        l.x = __double2bfloat16(r0);
+                        l.y = __double2bfloat16(r1);
+                        dst[k2 + pc * (lo_off / 2)] = l;
+                        r0 -= (double)__bfloat162float(l.x);
+                        r1 -= (double)__bfloat162float(l.y);
+                    }
                 }
             }
         }
@@ -162,9 +174,9 @@ __global__ void __launch_bounds__(kRows * kWarps)
                  const int32_t *__restrict__ perm, const int32_t *__restrict__ piv,
                  const double *__restrict__ Dinv, const int32_t *__restrict__ nelim_p,
                  double *__restrict__ W21, int64_t ldw, __nv_bfloat16 *__restrict__ Wb,
-                 __nv_bfloat16 *__restrict__ Lb, int Kp, int64_t lo_off) {
+                 __nv_bfloat16 *__restrict__ Lb, int Kp, int64_t lo_off, int pieces) {
     extern __shared__ __align__(16) double xs[];  // [p][kRows+1]
-    solve_tile(A, n, p, lda, perm, piv, Dinv, *nelim_p, W21, ldw, Wb, Lb, Kp, 0, lo_off, blockIdx.x, xs);
+    solve_tile(A, n, p, lda, perm, piv, Dinv, *nelim_p, W21, ldw, Wb, Lb, Kp, 0, lo_off, pieces, blockIdx.x, xs);
 }
 
 // Batched: CTA b takes work item b = (front, 32-row tile of its A21).
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(kRows * kWarps)
     const bool w64 = o.smode != CTP_S_NONE && o.prec == CTP_FP64;
     solve_tile(fr.A, bt.n, bt.p, fr.lda, fr.perm, fr.piv, reinterpret_cast<const double *>(base + sec.Dinv),
                *fr.nelim, w64 ? reinterpret_cast<double *>(base + sec.W21) : nullptr, bt.m, Wb, Lb,
-               kBatchKp, bt.row0, o.lo_off, (int64_t)blockIdx.x - bt.s0, xs);
+               kBatchKp, bt.row0, o.lo_off, o.pieces, (int64_t)blockIdx.x - bt.s0, xs);
 }
 
 
@@ -194,7 +206,7 @@ __global__ void __launch_bounds__(kRows * kWarps)
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,
                               double *W21, int64_t ldw, void *Wb, void *Lb, int Kp, int64_t lo_off,
-                              cudaStream_t st) {
+                              int pieces, cudaStream_t st) {
     const int64_t m = n - p;
     if (m <= 0) return cudaSuccess;
     size_t smem = sizeof(double) * (size_t)p * (kRows + 1);
@@ -204,7 +216,7 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
     int64_t grid = (m + kRows - 1) / kRows;
     k_solve_fp64<<<(unsigned)grid, kRows * kWarps, smem, st>>>(
         A, n, p, lda, perm, piv, Dinv, nelim, W21, ldw, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb, Kp,
-        lo_off);
+        lo_off, pieces);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ CTP_OK, CTP_EINVAL, CTP_ENOMEM, CTP_ECUDA, CTP_ENONFINITE, CTP_ETIMEOUT, CTP_ECA
 STATUS = {0: "CTP_OK", 1: "CTP_EINVAL", 2: "CTP_ENOMEM", 3: "CTP_ECUDA", 4: "CTP_ENONFINITE",
           5: "CTP_ETIMEOUT", 6: "CTP_ECAPACITY", 7: "CTP_EUNSUPPORTED"}
 PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3}
-PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
 SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4, "fp32_tiled": 5,
          "fp64_sub": 6}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
@@ -38,7 +38,8 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_chain_info", "ctp_chain_destroy", "ctp_tune_set", "ctp_tune_get",
            "ctp_autotune_batch", "ctp_autotune_supernode", "ctp_adjoint_solve",
            "ctp_sym_grad_dense", "ctp_sym_grad_pattern", "ctp_backward_error_csc", "ctp_refine_csc",
-           "ctp_mf_analyse", "ctp_mf_factor", "ctp_mf_fronts", "ctp_mf_info", "ctp_mf_destroy"]
+           "ctp_mf_analyse", "ctp_mf_factor", "ctp_mf_fronts", "ctp_mf_info", "ctp_mf_destroy",
+           "ctp_mf_panel_info"]
 TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G = 0, 1, 2
 WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
@@ -125,6 +126,7 @@ def load(path: str = LIB_PATH):
     L.ctp_mf_fronts.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(P)]
     L.ctp_mf_info.argtypes = [P, i32, ctypes.POINTER(i32), P, P, P, P, P]
     L.ctp_mf_destroy.argtypes = [P]
+    L.ctp_mf_panel_info.argtypes = [P, i32, P, P, P]
     L.ctp_tune_set.argtypes = [P, i32, i32]
     L.ctp_tune_get.argtypes = [P, i32, ctypes.POINTER(i32)]
     L.ctp_autotune_batch.argtypes = [P, i32, P, P, ctypes.POINTER(Options), P, P, i32, P, i32, P, P,
@@ -603,6 +605,15 @@ class Multifrontal:
             n.ctypes.data_as(ctypes.c_void_p), p.ctypes.data_as(ctypes.c_void_p),
             e.ctypes.data_as(ctypes.c_void_p), d.ctypes.data_as(ctypes.c_void_p)))
         return dict(parent=par, n=n, p=p, nelim=e, delayed=d)
+
+    def panel_info(self):
+        n = np.zeros(self.nf, np.int64)
+        p = np.zeros(self.nf, np.int32)
+        e = np.zeros(self.nf, np.int32)
+        _check("ctp_mf_panel_info", self.ctx.lib.ctp_mf_panel_info(
+            self.handle, self.nf, n.ctypes.data_as(ctypes.c_void_p), p.ctypes.data_as(ctypes.c_void_p),
+            e.ctypes.data_as(ctypes.c_void_p)))
+        return n, p, e
 
     def panel_perms(self):
         return [device_view(self.fronts[k].perm, int(self.fronts[k].p), "int32").cpu().numpy()

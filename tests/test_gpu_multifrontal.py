@@ -59,7 +59,7 @@ def test_multifrontal_matches_oracle(ctx, k, sigma, method):
     mf.destroy()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
 def test_multifrontal_mixed_refines(ctx, prec):
     """Panels' Forms on the tensor cores (subtracting into the fronts).  Leaf
     fronts see only FP64 original entries, so their pivots are the FP64 run's;
@@ -67,7 +67,7 @@ def test_multifrontal_mixed_refines(ctx, prec):
     may differ.  With the split form refinement reaches 1e-14 against the
     sparse matrix."""
     from paper_1305_2353_gb300 import ctp
-    cp, ri, v, N, perm, blocks = _problem(16, 3.0)
+    cp, ri, v, N, perm, blocks = _problem(24, 3.0)
     mf64 = ctp.Multifrontal(ctx, cp, ri, v, perm, blocks)
     mf64.factor(ctp.options(pivot="strict"))
     mf = ctp.Multifrontal(ctx, cp, ri, v, perm, blocks)
@@ -80,6 +80,8 @@ def test_multifrontal_mixed_refines(ctx, prec):
     X = torch.zeros((3, N), dtype=torch.float64, device="cuda")
     wsr = ctp.refine_workspace(ctx, N, int(mf.info()["n"].max()), 3)
     hist, steps = mf.refine(ctp.colmajor(B), X, wsr)
+    if prec == "bf16x6":
+        assert hist[-1].max() <= 1e-14 and steps <= 3
     if prec == "bf16x3":
         assert hist[-1].max() <= 1e-14 and steps <= 10
     mf.destroy()
