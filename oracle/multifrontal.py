@@ -19,17 +19,13 @@ tasks of a multifrontal code, and the passing of delayed columns to the parent):
   original entries of its own variables' columns (entries whose earlier
   variable is in this block), then the children's contribution blocks
   (extend-add, the Scatter task).  Its fully-summed columns -- the block's
-  variables, then the columns the children delayed -- are eliminated in one
-  pass (Section 1: a front tries its fully-summed columns; those it cannot
-  eliminate are delayed to the parent), in panels of at most ``w`` columns: a
-  panel is the leading columns of the current Schur complement (the columns
-  the previous panel delayed come first, then columns not yet tried), factored
-  by ``oracle.factor``, and the Schur complement is updated (Form).  The front
-  ends after the panel that takes its last untried column, or after a panel
-  that eliminates nothing; the columns left are delayed to the parent.  A
-  front of at most ``w`` fully-summed columns is thus one panel.  The root must
-  eliminate everything: its panels continue while they make progress, a panel
-  there that eliminates nothing is factored again with threshold partial
+  variables, then the columns the children delayed -- are eliminated in panels
+  of at most ``w`` columns: a panel is the leading columns of the current
+  Schur complement (the columns the previous panel delayed come first),
+  factored by ``oracle.factor``, and the Schur complement is updated (Form).
+  A panel that eliminates nothing ends the front: its remaining fully-summed
+  columns are delayed to the parent.  The root must eliminate everything: a
+  panel there that eliminates nothing is factored again with threshold partial
   pivoting, and if that also fails the factorization stops with an error.
 * The resulting fronts (panels) have the same form as ``system.factor_chain``'s,
   so ``system.solve``, ``system.refine`` and ``system.backward_error`` apply.
@@ -127,14 +123,11 @@ def factor(colptr, rowind, val, N, perm, blocks, method="strict", w=256, u=0.01,
         T = F
         ordv = rows.copy()
         p_left = len(fs)
-        untried = len(fs)        # fully-summed columns not yet in a panel
         root = f["parent"] < 0
         e_front = 0
         while p_left > 0:
             m_rows = T.shape[0]
             wd = min(w, p_left)
-            carried = p_left - untried
-            untried -= max(0, wd - carried)
             meth = method
             res = _orc.factor(np.asfortranarray(T[:, :wd]), wd, meth, u=u, small=small)
             if res["nelim"] == 0 and root and meth != "tpp":
@@ -156,8 +149,6 @@ def factor(colptr, rowind, val, N, perm, blocks, method="strict", w=256, u=0.01,
             ordv = ordv[q]
             p_left -= e
             e_front += e
-            if not root and untried == 0:
-                break
         if root and p_left > 0:
             raise ChainError("columns left at the root")
         info.append(dict(n=n, p=len(fs), own=len(own), nelim=e_front, delayed=p_left))
