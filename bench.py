@@ -562,7 +562,7 @@ def measure_multifrontal(ctx, dev, inputs, k=64, nrhs=16):
         torch.cuda.synchronize()
         tf = time.perf_counter() - t0
         kern = ctx.profile_end()
-        n, p, e = mf.panel_info()
+        n, p, e, _ = mf.panel_info()
         fs = form = 0
         for a, b, c in zip(n, p, e):
             f1, f2 = flops_model(int(a), int(b), int(c))
@@ -571,7 +571,7 @@ def measure_multifrontal(ctx, dev, inputs, k=64, nrhs=16):
         info = mf.info()
         Bd = ctp.colmajor(B, dev)
         X = torch.zeros_like(Bd)
-        ws = ctp.refine_workspace(ctx, N, int(info["n"].max()), nrhs)
+        ws = mf.refine_workspace(nrhs)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hist, steps = mf.refine(Bd, X, ws)

@@ -236,8 +236,11 @@ typedef struct ctp_plan ctp_plan;
  * 1 <= p <= ctp_max_p(), n >= p).  The plan holds the launch geometry and the
  * tables the kernels need; *ws_bytes receives the device workspace the batch
  * needs.  Pivoting: CTP_PIV_STRICT or CTP_PIV_RESTRICTED; prec/smode: FP64
- * with CTP_S_NONE / CTP_S_FP64_PACKED / CTP_S_FP32_PACKED, or CTP_BF16 with
- * CTP_S_FP32_TILED (Form on the tensor cores). */
+ * with CTP_S_NONE / CTP_S_FP64_PACKED / CTP_S_FP32_PACKED / CTP_S_FP64_SUB, or
+ * CTP_BF16 / CTP_BF16X3 / CTP_BF16X6 with CTP_S_FP32_TILED or CTP_S_FP64_SUB
+ * (Form on the tensor cores).  With CTP_S_FP64_SUB each front's S is the full
+ * column-major FP64 matrix at ctp_front.S (leading dimension lds) from which
+ * L21 D11 L21^T is subtracted (lower triangle). */
 ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host,
                                  const int32_t *p_host, const ctp_options *opt, ctp_plan **plan,
                                  size_t *ws_bytes);
@@ -381,10 +384,15 @@ ctp_status ctp_refine_csc(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, in
  *   the fully-summed columns (the block's, then the children's delayed ones)
  *   eliminated in panels of at most ctp_max_p() columns by ctp_factor_supernode
  *   with opt (its smode is ignored: each panel's Form subtracts into the front,
- *   whose trailing block becomes the contribution block).  A panel that
- *   eliminates nothing ends its front; the columns left are delayed to the
- *   parent.  A root front must eliminate all its columns (a panel there that
- *   eliminates nothing is retried with CTP_PIV_TPP); otherwise CTP_ECAPACITY.
+ *   whose trailing block becomes the contribution block).  A front tries its
+ *   fully-summed columns in one pass: it ends after the panel that takes its
+ *   last untried column (so a front of at most ctp_max_p() such columns is one
+ *   panel) or after a panel that eliminates nothing; the columns left are
+ *   delayed to the parent.  A root front must eliminate all its columns: its
+ *   panels continue while they make progress, one that eliminates nothing is
+ *   retried with CTP_PIV_TPP; otherwise CTP_ECAPACITY.  The fronts of a tree
+ *   level are assembled together, and those of at most ctp_max_p() fully-summed
+ *   columns are factored in one batch (strict and restricted pivoting).
  *   Device memory for the fronts is allocated by the call and held by *mf.
  *   Synchronises `stream` once per panel.
  * ctp_mf_fronts: the factored panels, in elimination order, as fronts for
@@ -399,8 +407,25 @@ ctp_status ctp_mf_factor(ctp_ctx *ctx, ctp_mf *mf, const double *val, const ctp_
 ctp_status ctp_mf_fronts(const ctp_mf *mf, int32_t *nf, const ctp_sfront **fronts);
 ctp_status ctp_mf_info(const ctp_mf *mf, int32_t cap, int32_t *nblocks, int32_t *parent, int64_t *n,
                        int64_t *p, int64_t *nelim, int64_t *ndelayed);
-/* Per factored panel (up to cap, elimination order): rows n, columns p, eliminated. */
-ctp_status ctp_mf_panel_info(const ctp_mf *mf, int32_t cap, int64_t *n, int32_t *p, int32_t *nelim);
+/* Solve with the factors, planned by levels of independent panels (one launch
+ * per level and step instead of per panel): X <- M^{-1} X in place (N x nrhs,
+ * device, ldx >= N).  Launches only. */
+ctp_status ctp_mf_solve_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes);
+ctp_status ctp_mf_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *X, int64_t ldx, void *workspace,
+                        size_t ws_bytes, void *stream);
+/* ctp_refine_csc with the planned solve (arguments as there; colptr, rowind,
+ * val: the matrix in device memory). */
+ctp_status ctp_mf_refine_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes);
+ctp_status ctp_mf_refine(ctp_ctx *ctx, const ctp_mf *mf, const int64_t *colptr, const int32_t *rowind,
+                         const double *val, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                         int32_t max_steps, double tol, double *berr_host, int32_t *steps_host, void *workspace,
+                         size_t ws_bytes, void *stream);
+/* Per factored panel (up to cap, in the order of ctp_mf_fronts, an elimination
+ * order): rows n, columns p, eliminated, and the block (front) it belongs to.
+ * The fronts of a tree level are factored together (their narrow fronts in one
+ * batch), so panels come level by level. */
+ctp_status ctp_mf_panel_info(const ctp_mf *mf, int32_t cap, int64_t *n, int32_t *p, int32_t *nelim,
+                             int32_t *block);
 ctp_status ctp_mf_destroy(ctp_mf *mf);
 
 typedef struct ctp_chain ctp_chain;

@@ -7,6 +7,7 @@
 
 #include "chain.cuh"
 #include "ctx.cuh"
+#include "solve_plan.cuh"
 
 namespace ctp {
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
@@ -446,76 +447,10 @@ ctp_status ctp_sym_grad_pattern(ctp_ctx *ctx, int64_t nnz, const int32_t *row, c
     return CTP_OK;
 }
 
-namespace {
-struct RefineLayout {
-    size_t solve, R, rowsum, mx, berr, total;
-};
-RefineLayout refine_layout(int64_t N, int64_t nmax, int nrhs) {
-    RefineLayout L;
-    size_t off = 0;
-    L.solve = off;
-    off += align256(sys_solve_ws_bytes(nmax, nrhs));
-    L.R = off;
-    off += align256(sizeof(double) * (size_t)N * nrhs);
-    L.rowsum = off;
-    off += align256(sizeof(double) * (size_t)N);
-    L.mx = off;
-    off += align256(sizeof(double) * (3 * (size_t)nrhs + 1));
-    L.berr = off;
-    off += align256(sizeof(double) * (size_t)nrhs);
-    L.total = off;
-    return L;
-}
-}  // namespace
-
 ctp_status ctp_refine_workspace_size(int64_t N, int64_t nmax, int32_t nrhs, size_t *bytes) {
     if (bytes == nullptr || N < 1 || nmax < 0 || nrhs < 1) return CTP_EINVAL;
-    *bytes = refine_layout(N, nmax, nrhs).total;
+    *bytes = refine_layout(N, sys_solve_ws_bytes(nmax, nrhs), nrhs).total;
     return CTP_OK;
-}
-
-// The system matrix of a residual: dense (lower triangle, column-major) or
-// sparse (lower triangle in compressed columns), symmetric either way.
-struct MatOp {
-    const double *M = nullptr;
-    int64_t ldm = 0;
-    const int64_t *colptr = nullptr;
-    const int32_t *rowind = nullptr;
-    const double *val = nullptr;
-    bool sparse() const { return colptr != nullptr; }
-};
-
-static cudaError_t mat_residual(ctp_ctx *ctx, const MatOp &A, int64_t N, int nrhs, const double *X,
-                                int64_t ldx, double *R, cudaStream_t st) {
-    if (A.sparse())
-        return timed(ctx, K_SPMV, st, [&] {
-            return launch_spmv_csc_residual(N, A.colptr, A.rowind, A.val, nrhs, X, ldx, R, N, st);
-        });
-    return timed(ctx, K_SYMV, st, [&] { return launch_symv_residual(N, A.M, A.ldm, nrhs, X, ldx, R, N, st); });
-}
-
-static cudaError_t mat_abs_rowsum(ctp_ctx *ctx, const MatOp &A, int64_t N, double *rowsum, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(rowsum, 0, sizeof(double) * N, st);
-    if (e != cudaSuccess) return e;
-    if (A.sparse())
-        return timed(ctx, K_SPMV, st, [&] {
-            return launch_spmv_csc_abs_rowsum(N, A.colptr, A.rowind, A.val, rowsum, st);
-        });
-    return timed(ctx, K_SYMV, st, [&] { return launch_abs_rowsum(N, A.M, A.ldm, rowsum, st); });
-}
-
-// R = B - A X, then the backward errors into berr (device)
-static cudaError_t residual_berr(ctp_ctx *ctx, const MatOp &A, int64_t N, int nrhs, const double *B,
-                                 int64_t ldb, const double *X, int64_t ldx, double *R, const double *rowsum,
-                                 double *mx, double *berr, cudaStream_t st) {
-    cudaError_t e = cudaMemcpy2DAsync(R, sizeof(double) * N, B, sizeof(double) * ldb,
-                                      sizeof(double) * N, nrhs, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
-    e = mat_residual(ctx, A, N, nrhs, X, ldx, R, st);
-    if (e != cudaSuccess) return e;
-    return timed(ctx, K_BERR, st, [&] {
-        return launch_backward_error(N, nrhs, R, N, X, ldx, B, ldb, rowsum, mx, berr, st);
-    });
 }
 
 static ctp_status backward_error_impl(ctp_ctx *ctx, const MatOp &A, int64_t N, int32_t nrhs,
@@ -540,31 +475,12 @@ static ctp_status refine_impl(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts
     for (int32_t k = 0; k < nf && fronts != nullptr; k++) nmax = fronts[k].n > nmax ? fronts[k].n : nmax;
     ctp_status s = check_fronts(nf, fronts, N, nmax);
     if (s != CTP_OK) return s;
-    RefineLayout L = refine_layout(N, nmax, nrhs);
-    if (ws_bytes < L.total) return CTP_ENOMEM;
     cudaStream_t st = (cudaStream_t)stream;
-    char *w = (char *)workspace;
-    void *sws = w + L.solve;
-    double *R = (double *)(w + L.R), *rowsum = (double *)(w + L.rowsum);
-    double *mx = (double *)(w + L.mx), *berr = (double *)(w + L.berr);
-    *steps_host = 0;
-    CTP_CUDA(mat_abs_rowsum(ctx, A, N, rowsum, st));
-    CTP_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * ldx, B, sizeof(double) * ldb, sizeof(double) * N,
-                               nrhs, cudaMemcpyDeviceToDevice, st));
-    CTP_CUDA(solve_fronts(ctx, nf, fronts, nrhs, X, ldx, sws, st));
-    for (int32_t k = 0;; k++) {
-        CTP_CUDA(residual_berr(ctx, A, N, nrhs, B, ldb, X, ldx, R, rowsum, mx, berr, st));
-        double *bh = berr_host + (size_t)k * nrhs;
-        CTP_CUDA(cudaMemcpyAsync(bh, berr, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-        CTP_CUDA(cudaStreamSynchronize(st));
-        double worst = 0.0;
-        for (int r = 0; r < nrhs; r++) worst = bh[r] > worst || bh[r] != bh[r] ? bh[r] : worst;
-        if (!(worst > tol) || k == max_steps) break;
-        CTP_CUDA(solve_fronts(ctx, nf, fronts, nrhs, R, N, sws, st));
-        CTP_CUDA(timed(ctx, K_AXPY, st, [&] { return launch_axpy(N, nrhs, X, ldx, R, N, st); }));
-        *steps_host = k + 1;
-    }
-    return CTP_OK;
+    auto solve = [&](double *Y, int64_t ldy, void *sws) {
+        return solve_fronts(ctx, nf, fronts, nrhs, Y, ldy, sws, st);
+    };
+    return refine_core(ctx, solve, sys_solve_ws_bytes(nmax, nrhs), N, A, nrhs, B, ldb, X, ldx, max_steps, tol,
+                       berr_host, steps_host, workspace, ws_bytes, st);
 }
 
 ctp_status ctp_backward_error(ctp_ctx *ctx, int64_t N, const double *M, int64_t ldm, int32_t nrhs,
@@ -664,6 +580,7 @@ ctp_status ctp_factor_dense(ctp_ctx *ctx, int64_t N, double *M, int64_t ldm, int
     cfg.o_rest = *opt_rest;
     cfg.retry_tpp = true;
     cfg.must_finish = true;
+    cfg.one_pass = false;
     ctp_chain *c = new ctp_chain();
     c->arena.chunk_bytes = (size_t)64 << 20;
     std::vector<int32_t> ord(N);

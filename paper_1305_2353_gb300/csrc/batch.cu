@@ -210,9 +210,9 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     if (opt->prec < CTP_FP64 || opt->prec > CTP_BF16X6) return CTP_EINVAL;
     const bool tc = opt->prec != CTP_FP64 && opt->smode != CTP_S_NONE;
     const int pieces = tc ? prec_pieces(opt->prec) : 0;
-    if (tc && opt->smode != CTP_S_FP32_TILED) return CTP_EUNSUPPORTED;
+    if (tc && opt->smode != CTP_S_FP32_TILED && opt->smode != CTP_S_FP64_SUB) return CTP_EUNSUPPORTED;
     if (!tc && opt->smode != CTP_S_NONE && opt->smode != CTP_S_FP64_PACKED &&
-        opt->smode != CTP_S_FP32_PACKED)
+        opt->smode != CTP_S_FP32_PACKED && opt->smode != CTP_S_FP64_SUB)
         return CTP_EUNSUPPORTED;
     for (int f = 0; f < nb; f++) {
         if (p_host[f] < 1 || n_host[f] < p_host[f]) return CTP_EINVAL;
@@ -406,8 +406,8 @@ cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_
     const int *fitem = reinterpret_cast<const int *>(w + P->off_fitem);
     if (P->tc)
         return launch_form_tc_batch(fr, tab, fitem, P->f_items, P->total_rows, w + P->off_wb, w + P->off_lb,
-                                    P->bo.pieces, reinterpret_cast<int32_t *>(w + P->off_ginfo),
-                                    num_sms, st);
+                                    P->bo.pieces, P->opt.smode == CTP_S_FP64_SUB ? 3 : 2,
+                                    reinterpret_cast<int32_t *>(w + P->off_ginfo), num_sms, st);
     return launch_form_fp64_batch(fr, tab, w, fitem, P->f_items, P->bo, st);
 }
 

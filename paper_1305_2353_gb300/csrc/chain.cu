@@ -78,7 +78,7 @@ ctp_status chain_factor(ctp_ctx *ctx, double *F, int64_t n, int64_t ld, int64_t 
     }
     const int wmax = cfg.w_first > cfg.w_rest ? cfg.w_first : cfg.w_rest;
     if (!wk.reserve(ctx, n, wmax, cand, 3)) return CTP_ENOMEM;
-    int64_t col = 0;
+    int64_t col = 0, untried = p_fs;  // untried: fully-summed columns not yet in a panel
     bool first = true;
     std::vector<int32_t> tmp(kMaxP);
     while (col < p_fs) {
@@ -86,6 +86,8 @@ ctp_status chain_factor(ctp_ctx *ctx, double *F, int64_t n, int64_t ld, int64_t 
         ctp_options ok = first ? cfg.o_first : cfg.o_rest;
         const int64_t wreq = first ? cfg.w_first : cfg.w_rest;
         const int w = (int)(wreq < p_left ? wreq : p_left);
+        const int64_t carried = p_left - untried;
+        untried -= w > carried ? w - carried : 0;
         first = false;
         ok.smode = nk > w ? CTP_S_FP64_SUB : CTP_S_NONE;
         if (ok.pivot == CTP_PIV_TPP) ok.prec = CTP_FP64;
@@ -150,6 +152,7 @@ ctp_status chain_factor(ctp_ctx *ctx, double *F, int64_t n, int64_t ld, int64_t 
         r.pivot = ok.pivot;
         out.push_back(r);
         col += e;
+        if (cfg.one_pass && !cfg.must_finish && untried == 0) break;
     }
     if (cfg.must_finish && col < p_fs) return CTP_ECAPACITY;
     *elim = col;

@@ -36,6 +36,8 @@ struct ChainCfg {
     bool retry_tpp;    // dense system: a panel that eliminates nothing is retried with
                        // TPP and is an error if it still eliminates nothing
     bool must_finish;  // every column must be eliminated (a root front: retry with TPP)
+    bool one_pass;     // a front (not a root): stop after the panel that takes the
+                       // last untried fully-summed column (the rest go to the parent)
 };
 
 struct PanelRec {

@@ -115,7 +115,8 @@ cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, c
                                    cudaStream_t st);
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
-                                 int pieces, int32_t *info, int num_sms, cudaStream_t st);
+                                 int pieces, int layout /* 2 tiled, 3 subtract */, int32_t *info, int num_sms,
+                                 cudaStream_t st);
 constexpr int kBatchKp = 256;  // K stride of the stacked BF16 operand buffers
 
 // the batched launch sequence (batch.cu); the plan type is declared in ctp.h
@@ -157,6 +158,14 @@ cudaError_t launch_sys_forward(const ctp_sfront &f, double *X, int64_t ldx, int 
                                cudaStream_t st);
 cudaError_t launch_sys_backward(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, void *ws,
                                 cudaStream_t st);
+// A level of independent fronts (device descriptors F[0..nfront)); items =
+// (front within the level, row chunk of 256) of the rows below the pivots;
+// part_off[i] = the level's chunks before front i (partial sums are kept per chunk).
+cudaError_t launch_sys_level_forward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
+                                     double *X, int64_t ldx, int nrhs, double *Y, cudaStream_t st);
+cudaError_t launch_sys_level_backward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
+                                      const int64_t *part_off, double *X, int64_t ldx, int nrhs, double *part,
+                                      cudaStream_t st);
 cudaError_t launch_symv_residual(int64_t N, const double *M, int64_t ldm, int nrhs, const double *X,
                                  int64_t ldx, double *R, int64_t ldr, cudaStream_t st);
 cudaError_t launch_abs_rowsum(int64_t N, const double *M, int64_t ldm, double *rowsum,

@@ -76,8 +76,10 @@ __global__ void __launch_bounds__(kTh)
     form_tile<OutT, kPacked, kSub>(L21, ldl, W21, ldw, m, *nelim_p, S, lds, blockIdx.x);
 }
 
-// Batched: CTA b takes work item b = (front, triangular 64 x 64 tile of its S).
-template <typename OutT>
+// Batched: CTA b takes work item b = (front, triangular 64 x 64 tile of its S):
+// S lower-packed per front, or (kSub) subtracted from the front's full
+// column-major S (leading dimension lds).
+template <typename OutT, bool kSub = false>
 __global__ void __launch_bounds__(kTh)
     k_form_fp64_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
                       const int *__restrict__ item_front, BatchOpts o) {
@@ -90,8 +92,8 @@ __global__ void __launch_bounds__(kTh)
     oo.prec = o.prec;
     const BSection sec = bsection(bt.n, bt.p, &oo);
     const double *W21 = reinterpret_cast<const double *>(ws + bt.ws + sec.W21);
-    form_tile<OutT, true>(fr.A + bt.p, fr.lda, W21, bt.m, bt.m, *fr.nelim, (OutT *)fr.S, fr.lds,
-                          (int64_t)blockIdx.x - bt.f0);
+    form_tile<OutT, !kSub, kSub>(fr.A + bt.p, fr.lda, W21, bt.m, bt.m, *fr.nelim, (OutT *)fr.S, fr.lds,
+                                 (int64_t)blockIdx.x - bt.f0);
 }
 
 
@@ -126,7 +128,9 @@ cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, c
                                    const int *item_front, int64_t items, BatchOpts o,
                                    cudaStream_t st) {
     if (items == 0) return cudaSuccess;
-    if (o.smode == CTP_S_FP64_PACKED)
+    if (o.smode == CTP_S_FP64_SUB)
+        k_form_fp64_batch<double, true><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);
+    else if (o.smode == CTP_S_FP64_PACKED)
         k_form_fp64_batch<double><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);
     else
         k_form_fp64_batch<float><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);

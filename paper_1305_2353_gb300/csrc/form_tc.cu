@@ -211,6 +211,7 @@ struct BatchTab {
     const ctp_front *fronts;
     const BFront *tab;
     const int *item_front;
+    int layout;  // 2: S in 128 x 128 blocks; 3: subtracted from the front's full FP64 S (lds)
 };
 
 // Which tiles a CTA takes.  mode 0: round robin over the column-block-major
@@ -250,8 +251,8 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
         x.m = b.m;
         x.nb = b.nM;
         x.S = reinterpret_cast<float *>(bt.fronts[f].S);
-        x.lds = 0;
-        x.layout = 2;
+        x.lds = bt.fronts[f].lds;
+        x.layout = bt.layout;
         return true;
     }
     if (s.mode != 1) {
@@ -671,7 +672,7 @@ cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t piece_off, in
     else
         mode = (pieces > 1 && nN >= 2 * (int64_t)num_sms) ? 1 : 2;
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-    BatchTab none = {nullptr, nullptr, nullptr};
+    BatchTab none = {nullptr, nullptr, nullptr, 0};
     if (pieces == 1) return launch_p<false, 1>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
     if (pieces == 2) return launch_p<false, 2>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
     return launch_p<false, 3>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
@@ -684,14 +685,14 @@ int64_t form_tc_tiles(int64_t m, int pieces) {
 
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
-                                 int pieces, int32_t *info, int num_sms, cudaStream_t st) {
+                                 int pieces, int layout, int32_t *info, int num_sms, cudaStream_t st) {
     if (items == 0) return cudaSuccess;
     if (pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
     CUtensorMap mW[3], mL[3];
     if (!make_maps(mW, mL, Wb, Lb, total_rows * kBatchKp, pieces, total_rows, kBatchKp))
         return cudaErrorInvalidValue;
     const int grid = (int)(items < num_sms ? items : num_sms);
-    BatchTab bt = {fronts, tab, item_front};
+    BatchTab bt = {fronts, tab, item_front, layout};
     if (pieces == 1) return launch_p<true, 1>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
     if (pieces == 2) return launch_p<true, 2>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
     return launch_p<true, 3>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);

@@ -27,6 +27,7 @@
 
 #include "chain.cuh"
 #include "ctx.cuh"
+#include "solve_plan.cuh"
 
 using namespace ctp;
 
@@ -44,6 +45,8 @@ struct ctp_mf {
         int64_t n = 0, p = 0, elim = 0;
         std::vector<int32_t> cb;  // contribution-block variables (new numbering); delayed first
         int64_t ndel = 0;
+        int64_t pa = 0, pb = 0;  // this block's panels in the panel list
+        int last_level = -1;     // solve level of its last panel
     };
     std::vector<Blk> blk;
     // assembly lists: local codes (own variables 0..p_own-1, struct rows p_own + t)
@@ -53,6 +56,8 @@ struct ctp_mf {
     Arena arena;  // frontal matrices and panel blocks
     std::vector<ctp_sfront> fronts;
     std::vector<PanelRec> panels;
+    std::vector<int32_t> panel_block;  // block of each panel
+    SolvePlan plan;  // the panels grouped into levels of independent panels
     bool factored = false;
     ~ctp_mf() {
         if (d_ci) cudaFree(d_ci);
@@ -66,42 +71,55 @@ namespace {
 
 constexpr int kTh = 256;
 
-// Original entries of a front: F(local(ci), local(cj)) += val[q], with struct
-// codes shifted by the number of delayed columns the front received.
-__global__ void __launch_bounds__(kTh) k_mf_assemble(int64_t ne, const int32_t *__restrict__ ci,
-                                                     const int32_t *__restrict__ cj,
-                                                     const int64_t *__restrict__ q,
-                                                     const double *__restrict__ val, int p_own,
-                                                     int64_t d, double *F, int64_t n) {
-    for (int64_t k = (int64_t)blockIdx.x * kTh + threadIdx.x; k < ne; k += (int64_t)gridDim.x * kTh) {
-        int64_t a = ci[k], b = cj[k];
-        if (a >= p_own) a += d;
-        if (b >= p_own) b += d;
+// Level versions: one launch for all fronts of a tree level (blockIdx.y picks
+// the front, resp. blockIdx.z the child).
+struct AsmRowDev {
+    int64_t e0, ne;
+    double *F;
+    int64_t n, d;
+    int p_own, pad;
+};
+struct ExtRowDev {
+    const double *C;
+    int64_t ldc, m, map_off;
+    double *F;
+    int64_t n;
+};
+
+__global__ void __launch_bounds__(kTh) k_mf_assemble_lv(const AsmRowDev *__restrict__ tab,
+                                                        const int32_t *__restrict__ ci,
+                                                        const int32_t *__restrict__ cj,
+                                                        const int64_t *__restrict__ q,
+                                                        const double *__restrict__ val) {
+    const AsmRowDev t = tab[blockIdx.y];
+    for (int64_t k = (int64_t)blockIdx.x * kTh + threadIdx.x; k < t.ne; k += (int64_t)gridDim.x * kTh) {
+        int64_t a = ci[t.e0 + k], b = cj[t.e0 + k];
+        if (a >= t.p_own) a += t.d;
+        if (b >= t.p_own) b += t.d;
         if (a < b) {
-            const int64_t t = a;
+            const int64_t u = a;
             a = b;
-            b = t;
+            b = u;
         }
-        F[b * n + a] += val[q[k]];
+        t.F[b * t.n + a] += val[q[t.e0 + k]];
     }
 }
 
-// Extend-add of a child's contribution block C = Fc[e:, e:] (lower triangle,
-// m x m, leading dimension ldc) into the parent: F(map[i], map[j]) += C(i, j).
-__global__ void __launch_bounds__(kTh) k_mf_extend_add(const double *__restrict__ Fc, int64_t ldc, int64_t m,
-                                                       const int32_t *__restrict__ map, double *F, int64_t n) {
-    const int64_t j = blockIdx.y;
-    for (int64_t jj = j; jj < m; jj += gridDim.y) {
+__global__ void __launch_bounds__(kTh) k_mf_extend_add_lv(const ExtRowDev *__restrict__ tab,
+                                                          const int32_t *__restrict__ maps) {
+    const ExtRowDev t = tab[blockIdx.z];
+    const int32_t *map = maps + t.map_off;
+    for (int64_t jj = blockIdx.y; jj < t.m; jj += gridDim.y) {
         const int64_t bj = map[jj];
-        const double *col = Fc + jj * ldc;
-        for (int64_t i = jj + (int64_t)blockIdx.x * kTh + threadIdx.x; i < m; i += (int64_t)gridDim.x * kTh) {
+        const double *col = t.C + jj * t.ldc;
+        for (int64_t i = jj + (int64_t)blockIdx.x * kTh + threadIdx.x; i < t.m; i += (int64_t)gridDim.x * kTh) {
             int64_t a = map[i], b = bj;
             if (a < b) {
-                const int64_t t = a;
+                const int64_t u = a;
                 a = b;
-                b = t;
+                b = u;
             }
-            F[b * n + a] += col[i];
+            t.F[b * t.n + a] += col[i];
         }
     }
 }
@@ -266,81 +284,410 @@ ctp_status ctp_mf_factor(ctp_ctx *ctx, ctp_mf *mf, const double *val, const ctp_
     mf->arena.release();
     mf->fronts.clear();
     mf->panels.clear();
+    mf->panel_block.clear();
+    mf->plan.clear();
     mf->factored = false;
     ChainCfg cfg;
     cfg.w_first = cfg.w_rest = kMaxP;
     cfg.o_first = cfg.o_rest = *opt;
     cfg.retry_tpp = false;
+    cfg.one_pass = false;
     ChainWork wk;
+    // fronts of one tree level are independent: assemble them together, and
+    // factor the narrow ones (at most kMaxP fully-summed columns, not a root)
+    // in one batch; the batch handles strict and restricted pivoting
+    const bool batchable = opt->pivot == CTP_PIV_STRICT || opt->pivot == CTP_PIV_RESTRICTED;
+    ctp_options bopt = *opt;
+    bopt.smode = CTP_S_FP64_SUB;
+    if (bopt.pivot == CTP_PIV_TPP) bopt.prec = CTP_FP64;
+    const int nblk = (int)mf->blk.size();
+    std::vector<int> lvl(nblk, 0);
+    int nlev = 0;
+    for (int s2 = 0; s2 < nblk; s2++) {
+        for (int c : mf->blk[s2].children) lvl[s2] = std::max(lvl[s2], lvl[c] + 1);
+        nlev = std::max(nlev, lvl[s2] + 1);
+    }
+    std::vector<std::vector<int>> bylev(nlev);
+    for (int s2 = 0; s2 < nblk; s2++) bylev[lvl[s2]].push_back(s2);
     std::vector<int32_t> loc(mf->N, -1);
-    std::vector<int32_t> rows, ord, map;
-    for (size_t s = 0; s < mf->blk.size(); s++) {
-        ctp_mf::Blk &b = mf->blk[s];
-        const int64_t pown = b.hi - b.lo;
-        rows.clear();
-        for (int64_t v = b.lo; v < b.hi; v++) rows.push_back((int32_t)v);
-        for (int c : b.children) {
-            const ctp_mf::Blk &cb = mf->blk[c];
-            rows.insert(rows.end(), cb.cb.begin(), cb.cb.begin() + cb.ndel);
-        }
-        const int64_t d = (int64_t)rows.size() - pown;
-        rows.insert(rows.end(), b.st.begin(), b.st.end());
-        const int64_t n = (int64_t)rows.size(), pfs = pown + d;
-        for (int64_t k = 0; k < n; k++) loc[rows[k]] = (int32_t)k;
-        double *F = (double *)mf->arena.alloc(sizeof(double) * (size_t)n * n);
-        if (F == nullptr) return CTP_ENOMEM;
-        CTP_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * (size_t)n * n, st));
-        if (b.ne > 0) {
-            const unsigned g = (unsigned)std::min<int64_t>((b.ne + kTh - 1) / kTh, 4096);
-            CTP_CUDA(timed(ctx, K_MF_ASSEMBLE, st, [&] {
-                k_mf_assemble<<<g, kTh, 0, st>>>(b.ne, mf->d_ci + b.e0, mf->d_cj + b.e0, mf->d_q + b.e0, val,
-                                                  (int)pown, d, F, n);
-                return cudaGetLastError();
-            }));
-        }
-        for (int c : b.children) {
-            ctp_mf::Blk &cb = mf->blk[c];
-            const int64_t m = (int64_t)cb.cb.size();
-            if (m == 0) continue;
-            map.resize(m);
-            for (int64_t k = 0; k < m; k++) {
-                map[k] = loc[cb.cb[k]];
-                if (map[k] < 0 || map[k] >= n) return CTP_EINVAL;  // a row the parent lacks
+    void *bws = nullptr;
+    size_t bws_cap = 0;
+    struct AsmRow {
+        int64_t e0, ne;
+        double *F;
+        int64_t n, d;
+        int p_own, pad;
+    };
+    struct ExtRow {
+        const double *C;
+        int64_t ldc, m, map_off;
+        double *F;
+        int64_t n;
+    };
+    ctp_status rc = CTP_OK;
+    for (int L = 0; L < nlev && rc == CTP_OK; L++) {
+        const std::vector<int> &lv = bylev[L];
+        const int nl = (int)lv.size();
+        // rows of each front: own variables, delayed columns of its children, struct
+        std::vector<std::vector<int32_t>> rows(nl);
+        std::vector<int64_t> dcount(nl), offF(nl);
+        int64_t total = 0;
+        for (int i = 0; i < nl; i++) {
+            ctp_mf::Blk &b = mf->blk[lv[i]];
+            std::vector<int32_t> &r = rows[i];
+            for (int64_t v = b.lo; v < b.hi; v++) r.push_back((int32_t)v);
+            for (int c : b.children) {
+                const ctp_mf::Blk &cb = mf->blk[c];
+                r.insert(r.end(), cb.cb.begin(), cb.cb.begin() + cb.ndel);
             }
-            int32_t *dmap = (int32_t *)mf->arena.alloc(sizeof(int32_t) * m);
-            if (dmap == nullptr) return CTP_ENOMEM;
-            CTP_CUDA(cudaMemcpyAsync(dmap, map.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-            const double *C = cb.F + cb.elim * cb.n + cb.elim;
-            const unsigned gy = (unsigned)std::min<int64_t>(m, 1024);
-            const unsigned gx = (unsigned)std::min<int64_t>((m + kTh - 1) / kTh, 8);
-            // (a copy from pageable memory has left `map` when cudaMemcpyAsync returns)
-            CTP_CUDA(timed(ctx, K_MF_EXTEND_ADD, st, [&] {
-                k_mf_extend_add<<<dim3(gx, gy), kTh, 0, st>>>(C, cb.n, m, dmap, F, n);
-                return cudaGetLastError();
-            }));
+            dcount[i] = (int64_t)r.size() - (b.hi - b.lo);
+            r.insert(r.end(), b.st.begin(), b.st.end());
+            b.n = (int64_t)r.size();
+            b.p = (b.hi - b.lo) + dcount[i];
+            offF[i] = total;
+            total += (b.n * b.n + 31) / 32 * 32;  // 256-byte aligned fronts
         }
-        // eliminate the fully-summed columns (rows named by original variables)
-        ord.resize(n);
-        for (int64_t k = 0; k < n; k++) ord[k] = mf->perm[rows[k]];
-        cfg.must_finish = b.parent < 0;
-        int64_t elim = 0;
-        const size_t before = mf->panels.size();
-        ctp_status rc = chain_factor(ctx, F, n, n, pfs, cfg, ord.data(), mf->arena, wk, mf->panels, &elim, st);
-        if (rc != CTP_OK) return rc;
-        (void)before;
-        b.F = F;
-        b.n = n;
-        b.p = pfs;
-        b.elim = elim;
-        b.ndel = pfs - elim;
-        b.cb.resize(n - elim);
-        for (int64_t k = elim; k < n; k++) b.cb[k - elim] = mf->inv[ord[k]];
-        for (int64_t k = 0; k < n; k++) loc[rows[k]] = -1;
+        double *Fl = (double *)mf->arena.alloc(sizeof(double) * (size_t)(total > 0 ? total : 1));
+        if (Fl == nullptr) {
+            rc = CTP_ENOMEM;
+            break;
+        }
+        for (int i = 0; i < nl; i++) mf->blk[lv[i]].F = Fl + offF[i];
+        if (cudaMemsetAsync(Fl, 0, sizeof(double) * (size_t)total, st) != cudaSuccess) {
+            rc = CTP_ECUDA;
+            break;
+        }
+        // assembly of the original entries, all fronts of the level
+        std::vector<AsmRow> at;
+        int64_t maxne = 0;
+        for (int i = 0; i < nl; i++) {
+            const ctp_mf::Blk &b = mf->blk[lv[i]];
+            if (b.ne == 0) continue;
+            at.push_back({b.e0, b.ne, b.F, b.n, dcount[i], (int)(b.hi - b.lo), 0});
+            maxne = std::max(maxne, b.ne);
+        }
+        // extend-add maps of all children of the level's fronts, grouped by the
+        // child's rank among its siblings: siblings add into the same parent
+        // entries, so each rank is a launch of its own (no two blocks of a
+        // launch add into one front; the sums stay in a fixed order)
+        std::vector<ExtRow> et;
+        std::vector<int32_t> maps;
+        std::vector<int> rank_of;
+        int64_t maxm = 0;
+        for (int i = 0; i < nl && rc == CTP_OK; i++) {
+            const ctp_mf::Blk &b = mf->blk[lv[i]];
+            for (int64_t k = 0; k < b.n; k++) loc[rows[i][k]] = (int32_t)k;
+            int rank = 0;
+            for (int c : b.children) {
+                const ctp_mf::Blk &cb = mf->blk[c];
+                const int64_t m = (int64_t)cb.cb.size();
+                if (m == 0) continue;
+                const int64_t off = (int64_t)maps.size();
+                for (int64_t k = 0; k < m; k++) {
+                    const int32_t t = loc[cb.cb[k]];
+                    if (t < 0 || t >= b.n) rc = CTP_EINVAL;  // a row the parent lacks
+                    maps.push_back(t);
+                }
+                et.push_back({cb.F + cb.elim * cb.n + cb.elim, cb.n, m, off, b.F, b.n});
+                rank_of.push_back(rank++);
+                maxm = std::max(maxm, m);
+            }
+            for (int64_t k = 0; k < b.n; k++) loc[rows[i][k]] = -1;
+        }
+        if (rc != CTP_OK) break;
+        // order the extend-add rows by sibling rank
+        std::vector<int64_t> rank_ptr(1, 0);
+        {
+            std::vector<int> idx(et.size());
+            for (size_t k = 0; k < idx.size(); k++) idx[k] = (int)k;
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return rank_of[a] < rank_of[c]; });
+            std::vector<ExtRow> sorted;
+            sorted.reserve(et.size());
+            for (size_t k = 0; k < idx.size(); k++) {
+                if (k > 0 && rank_of[idx[k]] != rank_of[idx[k - 1]]) rank_ptr.push_back((int64_t)k);
+                sorted.push_back(et[idx[k]]);
+            }
+            rank_ptr.push_back((int64_t)et.size());
+            et.swap(sorted);
+        }
+        const size_t tbytes = align256(sizeof(AsmRow) * at.size()) + align256(sizeof(ExtRow) * et.size()) +
+                              align256(sizeof(int32_t) * maps.size());
+        char *tb = (char *)mf->arena.alloc(tbytes > 0 ? tbytes : 256);
+        if (tb == nullptr) {
+            rc = CTP_ENOMEM;
+            break;
+        }
+        AsmRow *d_at = (AsmRow *)tb;
+        ExtRow *d_et = (ExtRow *)(tb + align256(sizeof(AsmRow) * at.size()));
+        int32_t *d_maps = (int32_t *)((char *)d_et + align256(sizeof(ExtRow) * et.size()));
+        if ((!at.empty() && cudaMemcpyAsync(d_at, at.data(), sizeof(AsmRow) * at.size(), cudaMemcpyHostToDevice,
+                                            st) != cudaSuccess) ||
+            (!et.empty() && cudaMemcpyAsync(d_et, et.data(), sizeof(ExtRow) * et.size(), cudaMemcpyHostToDevice,
+                                            st) != cudaSuccess) ||
+            (!maps.empty() && cudaMemcpyAsync(d_maps, maps.data(), sizeof(int32_t) * maps.size(),
+                                              cudaMemcpyHostToDevice, st) != cudaSuccess)) {
+            rc = CTP_ECUDA;
+            break;
+        }
+        if (!at.empty()) {
+            const unsigned gx = (unsigned)std::min<int64_t>((maxne + kTh - 1) / kTh, 64);
+            if (timed(ctx, K_MF_ASSEMBLE, st, [&] {
+                    k_mf_assemble_lv<<<dim3(gx, (unsigned)at.size()), kTh, 0, st>>>(
+                        reinterpret_cast<const AsmRowDev *>(d_at), mf->d_ci, mf->d_cj, mf->d_q, val);
+                    return cudaGetLastError();
+                }) != cudaSuccess) {
+                rc = CTP_ECUDA;
+                break;
+            }
+        }
+        for (size_t g = 0; g + 1 < rank_ptr.size() && !et.empty(); g++) {
+            const int64_t r0 = rank_ptr[g], r1 = rank_ptr[g + 1];
+            if (r1 <= r0) continue;
+            const unsigned gx = (unsigned)std::min<int64_t>((maxm + kTh - 1) / kTh, 4);
+            const unsigned gy = (unsigned)std::min<int64_t>(maxm, 256);
+            if (timed(ctx, K_MF_EXTEND_ADD, st, [&] {
+                    k_mf_extend_add_lv<<<dim3(gx, gy, (unsigned)(r1 - r0)), kTh, 0, st>>>(
+                        reinterpret_cast<const ExtRowDev *>(d_et) + r0, d_maps);
+                    return cudaGetLastError();
+                }) != cudaSuccess) {
+                rc = CTP_ECUDA;
+                break;
+            }
+        }
+        if (rc != CTP_OK) break;
+        // the level's fronts other than roots, in batches: each pass factors the
+        // next panel (the leading at most kMaxP remaining fully-summed columns)
+        // of every front still making progress, until none has columns left or
+        // eliminates anything more
+        std::vector<int> bi;  // indices into lv
+        for (int i = 0; i < nl; i++) {
+            const ctp_mf::Blk &b = mf->blk[lv[i]];
+            if (batchable && b.parent >= 0 && b.n > b.p) bi.push_back(i);
+        }
+        std::vector<std::vector<int32_t>> ordb(bi.size());  // current row order (new numbering)
+        for (size_t k = 0; k < bi.size(); k++) {
+            ctp_mf::Blk &b = mf->blk[lv[bi[k]]];
+            ordb[k] = rows[bi[k]];
+            b.elim = 0;
+            b.pa = b.pb = -1;
+        }
+        std::vector<int> active(bi.size());
+        for (size_t k = 0; k < bi.size(); k++) active[k] = (int)k;
+        std::vector<std::vector<PanelRec>> recs(bi.size());
+        while (!active.empty() && rc == CTP_OK) {
+            const int nb = (int)active.size();
+            std::vector<int64_t> nh(nb);
+            std::vector<int32_t> ph(nb);
+            int64_t sp = 0, sn = 0;
+            for (int k = 0; k < nb; k++) {
+                const ctp_mf::Blk &b = mf->blk[lv[bi[active[k]]]];
+                nh[k] = b.n - b.elim;
+                ph[k] = (int32_t)std::min<int64_t>(kMaxP, b.p - b.elim);
+                sp += ph[k];
+                sn += nh[k];
+            }
+            // per-front outputs, contiguous for one read-back: nelim | perm | piv | rows, then D
+            const size_t ib = align256(sizeof(int32_t) * (size_t)(nb + 2 * sp + sn));
+            char *ob = (char *)mf->arena.alloc(ib + align256(sizeof(double) * 2 * (size_t)sp) +
+                                               sizeof(ctp_front) * nb);
+            if (ob == nullptr) {
+                rc = CTP_ENOMEM;
+                break;
+            }
+            int32_t *d_nel = (int32_t *)ob, *d_perm = d_nel + nb, *d_piv = d_perm + sp, *d_rows = d_piv + sp;
+            double *d_D = (double *)(ob + ib);
+            ctp_front *d_fr = (ctp_front *)(ob + ib + align256(sizeof(double) * 2 * (size_t)sp));
+            std::vector<ctp_front> fh(nb);
+            std::vector<int32_t> rows_h;
+            rows_h.reserve(sn);
+            int64_t po = 0;
+            for (int k = 0; k < nb; k++) {
+                ctp_mf::Blk &b = mf->blk[lv[bi[active[k]]]];
+                const int64_t e0 = b.elim;
+                ctp_front &f = fh[k];
+                f.n = nh[k];
+                f.p = ph[k];
+                f.reserved = 0;
+                f.A = b.F + e0 * b.n + e0;
+                f.lda = b.n;
+                f.perm = d_perm + po;
+                f.piv = d_piv + po;
+                f.D = d_D + 2 * po;
+                f.nelim = d_nel + k;
+                f.S = f.A + (int64_t)ph[k] * b.n + ph[k];
+                f.lds = b.n;
+                for (int64_t q = e0; q < b.n; q++) rows_h.push_back(mf->perm[ordb[active[k]][q]]);
+                po += ph[k];
+            }
+            if (cudaMemcpyAsync(d_rows, rows_h.data(), sizeof(int32_t) * rows_h.size(), cudaMemcpyHostToDevice,
+                                st) != cudaSuccess ||
+                cudaMemcpyAsync(d_fr, fh.data(), sizeof(ctp_front) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                rc = CTP_ECUDA;
+                break;
+            }
+            ctp_plan *plan = nullptr;
+            size_t need = 0;
+            rc = ctp_batch_plan_create(ctx, nb, nh.data(), ph.data(), &bopt, &plan, &need);
+            if (rc != CTP_OK) break;
+            if (need > bws_cap) {
+                if (bws) cudaFree(bws);
+                bws = nullptr;
+                bws_cap = 0;
+                if (cudaMalloc(&bws, need) != cudaSuccess) {
+                    ctp_batch_plan_destroy(plan);
+                    rc = CTP_ENOMEM;
+                    break;
+                }
+                bws_cap = need;
+            }
+            rc = ctp_batch_upload(ctx, plan, bws, bws_cap, st);
+            if (rc == CTP_OK) rc = ctp_factor_batch(ctx, plan, d_fr, bws, bws_cap, st);
+            std::vector<int32_t> flags(nb), outh(nb + sp);
+            if (rc == CTP_OK) rc = ctp_batch_read_info(ctx, plan, bws, flags.data(), st);
+            ctp_batch_plan_destroy(plan);
+            if (rc != CTP_OK) break;
+            for (int k = 0; k < nb; k++)
+                if (flags[k] != CTP_OK) rc = (ctp_status)flags[k];
+            if (rc != CTP_OK) break;
+            if (cudaMemcpyAsync(outh.data(), d_nel, sizeof(int32_t) * (nb + sp), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = CTP_ECUDA;
+                break;
+            }
+            std::vector<int> next;
+            std::vector<int32_t> tmp;
+            po = 0;
+            int64_t ro = 0;
+            for (int k = 0; k < nb; k++) {
+                const int a = active[k];
+                ctp_mf::Blk &b = mf->blk[lv[bi[a]]];
+                const int32_t e = outh[k];
+                const int64_t e0 = b.elim, pk = ph[k];
+                // pivot order of this pass's fully-summed rows
+                std::vector<int32_t> &o = ordb[a];
+                tmp.assign(o.begin() + e0, o.begin() + e0 + pk);
+                for (int64_t q = 0; q < pk; q++) o[e0 + q] = tmp[outh[nb + po + q]];
+                if (e > 0) {
+                    PanelRec r;
+                    r.f = {nh[k], (int32_t)pk, 0, fh[k].A, b.n, d_perm + po, d_piv + po, d_D + 2 * po, d_nel + k,
+                           d_rows + ro};
+                    r.e = e;
+                    r.w = (int32_t)pk;
+                    r.pivot = opt->pivot;
+                    recs[a].push_back(r);
+                    b.elim += e;
+                    if (b.elim < b.p) next.push_back(a);
+                }
+                po += pk;
+                ro += nh[k];
+            }
+            active.swap(next);
+        }
+        if (rc != CTP_OK) break;
+        for (size_t k = 0; k < bi.size(); k++) {
+            ctp_mf::Blk &b = mf->blk[lv[bi[k]]];
+            b.pa = (int64_t)mf->panels.size();
+            for (const PanelRec &r : recs[k]) {
+                mf->panels.push_back(r);
+                mf->panel_block.push_back(lv[bi[k]]);
+            }
+            b.pb = (int64_t)mf->panels.size();
+            b.ndel = b.p - b.elim;
+            b.cb.assign(ordb[k].begin() + b.elim, ordb[k].end());
+        }
+        // the other fronts (roots, or all fronts when the pivoting cannot be
+        // batched) by the panel-chain driver
+        for (int i = 0; i < nl && rc == CTP_OK; i++) {
+            ctp_mf::Blk &b = mf->blk[lv[i]];
+            if (std::find(bi.begin(), bi.end(), i) != bi.end()) continue;
+            std::vector<int32_t> ord(b.n);
+            for (int64_t k = 0; k < b.n; k++) ord[k] = mf->perm[rows[i][k]];
+            cfg.must_finish = b.parent < 0;
+            int64_t elim = 0;
+            b.pa = (int64_t)mf->panels.size();
+            rc = chain_factor(ctx, b.F, b.n, b.n, b.p, cfg, ord.data(), mf->arena, wk, mf->panels, &elim, st);
+            if (rc != CTP_OK) break;
+            b.pb = (int64_t)mf->panels.size();
+            mf->panel_block.resize(mf->panels.size(), lv[i]);
+            b.elim = elim;
+            b.ndel = b.p - elim;
+            b.cb.resize(b.n - elim);
+            for (int64_t k = elim; k < b.n; k++) b.cb[k - elim] = mf->inv[ord[k]];
+        }
+    }
+    if (bws) cudaFree(bws);
+    if (rc != CTP_OK) {
+        cudaStreamSynchronize(st);
+        return rc;
     }
     for (const PanelRec &r : mf->panels) mf->fronts.push_back(r.f);
+    // solve levels: a block's first panel follows its children's last panels,
+    // each further panel follows the one before
+    std::vector<int> level(mf->panels.size());
+    for (ctp_mf::Blk &b : mf->blk) {
+        int lv = -1;
+        for (int c : b.children) lv = std::max(lv, mf->blk[c].last_level);
+        for (int64_t k = b.pa; k < b.pb; k++) level[k] = ++lv;
+        b.last_level = lv;
+    }
+    std::vector<int> order(mf->panels.size());
+    for (size_t k = 0; k < order.size(); k++) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return level[a] < level[c]; });
+    std::vector<ctp_sfront> pf;
+    std::vector<int> pl;
+    std::vector<int32_t> pe;
+    for (int k : order) {
+        pf.push_back(mf->panels[k].f);
+        pl.push_back(level[k]);
+        pe.push_back(mf->panels[k].e);
+    }
+    rc = mf->plan.build(pf, pl, pe);
+    if (rc != CTP_OK) return rc;
     mf->factored = true;
     CTP_CUDA(cudaStreamSynchronize(st));
     return CTP_OK;
+}
+
+ctp_status ctp_mf_solve_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes) {
+    if (mf == nullptr || bytes == nullptr || nrhs < 1 || !mf->factored) return CTP_EINVAL;
+    *bytes = mf->plan.ws_bytes(nrhs);
+    return CTP_OK;
+}
+
+ctp_status ctp_mf_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *X, int64_t ldx, void *workspace,
+                        size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || mf == nullptr || X == nullptr || workspace == nullptr || nrhs < 1 || !mf->factored ||
+        ldx < mf->N)
+        return CTP_EINVAL;
+    if (ws_bytes < mf->plan.ws_bytes(nrhs)) return CTP_ENOMEM;
+    CTP_CUDA(mf->plan.solve(ctx, X, ldx, nrhs, workspace, (cudaStream_t)stream));
+    return CTP_OK;
+}
+
+ctp_status ctp_mf_refine_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes) {
+    if (mf == nullptr || bytes == nullptr || nrhs < 1 || !mf->factored) return CTP_EINVAL;
+    *bytes = refine_layout(mf->N, mf->plan.ws_bytes(nrhs), nrhs).total;
+    return CTP_OK;
+}
+
+ctp_status ctp_mf_refine(ctp_ctx *ctx, const ctp_mf *mf, const int64_t *colptr, const int32_t *rowind,
+                         const double *val, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                         int32_t max_steps, double tol, double *berr_host, int32_t *steps_host, void *workspace,
+                         size_t ws_bytes, void *stream) {
+    if (ctx == nullptr || mf == nullptr || !mf->factored || colptr == nullptr || rowind == nullptr ||
+        val == nullptr || B == nullptr || X == nullptr || berr_host == nullptr || steps_host == nullptr ||
+        workspace == nullptr || nrhs < 1 || ldb < mf->N || ldx < mf->N || max_steps < 0 || max_steps > 100 ||
+        !(tol >= 0.0))
+        return CTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    MatOp A;
+    A.colptr = colptr;
+    A.rowind = rowind;
+    A.val = val;
+    auto solve = [&](double *Y, int64_t ldy, void *sws) { return mf->plan.solve(ctx, Y, ldy, nrhs, sws, st); };
+    return refine_core(ctx, solve, mf->plan.ws_bytes(nrhs), mf->N, A, nrhs, B, ldb, X, ldx, max_steps, tol,
+                       berr_host, steps_host, workspace, ws_bytes, st);
 }
 
 ctp_status ctp_mf_fronts(const ctp_mf *mf, int32_t *nf, const ctp_sfront **fronts) {
@@ -365,12 +712,14 @@ ctp_status ctp_mf_info(const ctp_mf *mf, int32_t cap, int32_t *nblocks, int32_t 
     return CTP_OK;
 }
 
-ctp_status ctp_mf_panel_info(const ctp_mf *mf, int32_t cap, int64_t *n, int32_t *p, int32_t *nelim) {
+ctp_status ctp_mf_panel_info(const ctp_mf *mf, int32_t cap, int64_t *n, int32_t *p, int32_t *nelim,
+                             int32_t *block) {
     if (mf == nullptr || cap < 0 || !mf->factored) return CTP_EINVAL;
     for (int32_t k = 0; k < (int32_t)mf->panels.size() && k < cap; k++) {
         if (n) n[k] = mf->panels[k].f.n;
         if (p) p[k] = mf->panels[k].w;
         if (nelim) nelim[k] = mf->panels[k].e;
+        if (block) block[k] = mf->panel_block[k];
     }
     return CTP_OK;
 }

@@ -29,8 +29,7 @@ __device__ __forceinline__ int front_var(const ctp_sfront &f, int64_t r) {
 
 // Forward step of one front: gather, unit-lower solve with L11, keep y for the
 // update of the rows below, scatter z = D^{-1} y.
-__global__ void __launch_bounds__(kTh) k_sys_fwd_tri(ctp_sfront f, double *X, int64_t ldx, int nrhs,
-                                                     double *Y) {
+__device__ __forceinline__ void dev_fwd_tri(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, double *Y) {
     extern __shared__ double sm[];
     double *sl = sm;                      // [kJB][kMaxP]: L(i, j0 + jj) at sl[jj * kMaxP + i]
     double *sy = sm + kJB * kMaxP;        // [kRB][kMaxP]
@@ -93,11 +92,12 @@ __global__ void __launch_bounds__(kTh) k_sys_fwd_tri(ctp_sfront f, double *X, in
 }
 
 // Rows below the pivots: b(var(r)) -= L(r, 0:e) y, one row per thread.
-__global__ void __launch_bounds__(kTh) k_sys_fwd_upd(ctp_sfront f, double *X, int64_t ldx, int nrhs,
-                                                     const double *Y) {
+template <bool kAtomic>
+__device__ __forceinline__ void dev_fwd_upd(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, const double *Y,
+                                            int64_t chunk) {
     __shared__ double sy[kRB][kMaxP];
     const int e = *f.nelim;
-    const int64_t r = (int64_t)e + (int64_t)blockIdx.x * kTh + threadIdx.x;
+    const int64_t r = (int64_t)e + chunk * kTh + threadIdx.x;
     const bool live = r < f.n;
     const int v = live ? front_var(f, r) : 0;
     for (int r0 = 0; r0 < nrhs; r0 += kRB) {
@@ -118,19 +118,23 @@ __global__ void __launch_bounds__(kTh) k_sys_fwd_upd(ctp_sfront f, double *X, in
 #pragma unroll
             for (int rr = 0; rr < kRB; rr++) acc[rr] += l * sy[rr][j];
         }
-        for (int rr = 0; rr < nr; rr++) X[(int64_t)(r0 + rr) * ldx + v] -= acc[rr];
+        for (int rr = 0; rr < nr; rr++) {
+            if (kAtomic)  // fronts of one level may share ancestor rows
+                atomicAdd(X + (int64_t)(r0 + rr) * ldx + v, -acc[rr]);
+            else
+                X[(int64_t)(r0 + rr) * ldx + v] -= acc[rr];
+        }
     }
 }
 
 // Backward step, part 1: per chunk of kTh rows below the pivots,
 // part[c][r][j] = sum over the chunk's rows of L(row, j) x(var(row), r).
-__global__ void __launch_bounds__(kTh) k_sys_bwd_part(ctp_sfront f, const double *X, int64_t ldx,
-                                                      int nrhs, double *part) {
+__device__ __forceinline__ void dev_bwd_part(const ctp_sfront &f, const double *X, int64_t ldx, int nrhs,
+                                             double *part, int64_t c) {
     __shared__ double sx[kRB][kTh];
     const int e = *f.nelim;
     const int64_t below = f.n - e;
     const int64_t nch = (below + kTh - 1) / kTh;
-    const int64_t c = blockIdx.x;
     if (c >= nch) return;
     const int64_t rbase = e + c * kTh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -168,8 +172,8 @@ __global__ void __launch_bounds__(kTh) k_sys_bwd_part(ctp_sfront f, const double
 
 // Backward step, part 2: z = x(piv vars) - sum of the chunk partials, then
 // L11^T x = z, right-looking from the last pivot, 32 rows of L11 staged at a time.
-__global__ void __launch_bounds__(kTh) k_sys_bwd_tri(ctp_sfront f, double *X, int64_t ldx, int nrhs,
-                                                     const double *part) {
+__device__ __forceinline__ void dev_bwd_tri(const ctp_sfront &f, double *X, int64_t ldx, int nrhs,
+                                            const double *part) {
     extern __shared__ double sm[];
     double *sl = sm;                  // [kJB][kMaxP]: L(i0 + ii, j) at sl[ii * kMaxP + j]
     double *sz = sm + kJB * kMaxP;    // [kRB][kMaxP]
@@ -216,6 +220,49 @@ __global__ void __launch_bounds__(kTh) k_sys_bwd_tri(ctp_sfront f, double *X, in
         }
         __syncthreads();
     }
+}
+
+// One front per launch (the generic front-list solve).
+__global__ void __launch_bounds__(kTh) k_sys_fwd_tri(ctp_sfront f, double *X, int64_t ldx, int nrhs,
+                                                     double *Y) {
+    dev_fwd_tri(f, X, ldx, nrhs, Y);
+}
+__global__ void __launch_bounds__(kTh) k_sys_fwd_upd(ctp_sfront f, double *X, int64_t ldx, int nrhs,
+                                                     const double *Y) {
+    dev_fwd_upd<false>(f, X, ldx, nrhs, Y, blockIdx.x);
+}
+__global__ void __launch_bounds__(kTh) k_sys_bwd_part(ctp_sfront f, const double *X, int64_t ldx,
+                                                      int nrhs, double *part) {
+    dev_bwd_part(f, X, ldx, nrhs, part, blockIdx.x);
+}
+__global__ void __launch_bounds__(kTh) k_sys_bwd_tri(ctp_sfront f, double *X, int64_t ldx, int nrhs,
+                                                     const double *part) {
+    dev_bwd_tri(f, X, ldx, nrhs, part);
+}
+
+// A level of independent fronts per launch (the planned solve): front i of the
+// level uses Y slot i and its own range of partial sums (part_off: first chunk
+// of the front within the level); the row updates of the
+// forward sweep are atomic since fronts of a level may share ancestor rows.
+// items[k] = (front index within the level, row chunk).
+__global__ void __launch_bounds__(kTh) k_sys_fwd_tri_lv(const ctp_sfront *F, double *X, int64_t ldx, int nrhs,
+                                                        double *Y) {
+    dev_fwd_tri(F[blockIdx.x], X, ldx, nrhs, Y + (int64_t)blockIdx.x * kMaxP * nrhs);
+}
+__global__ void __launch_bounds__(kTh) k_sys_fwd_upd_lv(const ctp_sfront *F, const int2 *items, double *X,
+                                                        int64_t ldx, int nrhs, const double *Y) {
+    const int2 it = items[blockIdx.x];
+    dev_fwd_upd<true>(F[it.x], X, ldx, nrhs, Y + (int64_t)it.x * kMaxP * nrhs, it.y);
+}
+__global__ void __launch_bounds__(kTh) k_sys_bwd_part_lv(const ctp_sfront *F, const int2 *items,
+                                                         const int64_t *part_off, const double *X, int64_t ldx,
+                                                         int nrhs, double *part) {
+    const int2 it = items[blockIdx.x];
+    dev_bwd_part(F[it.x], X, ldx, nrhs, part + part_off[it.x] * (int64_t)nrhs * kMaxP, it.y);
+}
+__global__ void __launch_bounds__(kTh) k_sys_bwd_tri_lv(const ctp_sfront *F, const int64_t *part_off, double *X,
+                                                        int64_t ldx, int nrhs, const double *part) {
+    dev_bwd_tri(F[blockIdx.x], X, ldx, nrhs, part + part_off[blockIdx.x] * (int64_t)nrhs * kMaxP);
 }
 
 // R -= M X (kAbs = false) or R += |M| 1 (kAbs = true: the row sums of |M|),
@@ -449,6 +496,29 @@ cudaError_t launch_sys_backward(const ctp_sfront &f, double *X, int64_t ldx, int
     const int64_t nch = (f.n + kTh - 1) / kTh;  // upper bound on the chunks below the pivots
     if (nch > 0) k_sys_bwd_part<<<(unsigned)nch, kTh, 0, st>>>(f, X, ldx, nrhs, part);
     k_sys_bwd_tri<<<1, kTh, kTriSmem, st>>>(f, X, ldx, nrhs, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sys_level_forward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
+                                     double *X, int64_t ldx, int nrhs, double *Y, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_sys_fwd_tri_lv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
+        cudaFuncSetAttribute(k_sys_bwd_tri_lv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
+        attr = true;
+    }
+    if (nfront == 0) return cudaSuccess;
+    k_sys_fwd_tri_lv<<<nfront, kTh, kTriSmem, st>>>(F, X, ldx, nrhs, Y);
+    if (nitems > 0) k_sys_fwd_upd_lv<<<(unsigned)nitems, kTh, 0, st>>>(F, items, X, ldx, nrhs, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sys_level_backward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
+                                      const int64_t *part_off, double *X, int64_t ldx, int nrhs, double *part,
+                                      cudaStream_t st) {
+    if (nfront == 0) return cudaSuccess;
+    if (nitems > 0) k_sys_bwd_part_lv<<<(unsigned)nitems, kTh, 0, st>>>(F, items, part_off, X, ldx, nrhs, part);
+    k_sys_bwd_tri_lv<<<nfront, kTh, kTriSmem, st>>>(F, part_off, X, ldx, nrhs, part);
     return cudaGetLastError();
 }
 

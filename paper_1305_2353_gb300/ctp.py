@@ -39,7 +39,8 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_autotune_batch", "ctp_autotune_supernode", "ctp_adjoint_solve",
            "ctp_sym_grad_dense", "ctp_sym_grad_pattern", "ctp_backward_error_csc", "ctp_refine_csc",
            "ctp_mf_analyse", "ctp_mf_factor", "ctp_mf_fronts", "ctp_mf_info", "ctp_mf_destroy",
-           "ctp_mf_panel_info"]
+           "ctp_mf_panel_info", "ctp_mf_solve_workspace_size", "ctp_mf_solve",
+           "ctp_mf_refine_workspace_size", "ctp_mf_refine"]
 TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G = 0, 1, 2
 WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
@@ -126,7 +127,12 @@ def load(path: str = LIB_PATH):
     L.ctp_mf_fronts.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(P)]
     L.ctp_mf_info.argtypes = [P, i32, ctypes.POINTER(i32), P, P, P, P, P]
     L.ctp_mf_destroy.argtypes = [P]
-    L.ctp_mf_panel_info.argtypes = [P, i32, P, P, P]
+    L.ctp_mf_panel_info.argtypes = [P, i32, P, P, P, P]
+    L.ctp_mf_solve_workspace_size.argtypes = [P, i32, ctypes.POINTER(sz)]
+    L.ctp_mf_solve.argtypes = [P, P, i32, P, i64, P, sz, P]
+    L.ctp_mf_refine_workspace_size.argtypes = [P, i32, ctypes.POINTER(sz)]
+    L.ctp_mf_refine.argtypes = [P, P, P, P, P, i32, P, i64, P, i64, i32, ctypes.c_double, P,
+                                ctypes.POINTER(i32), P, sz, P]
     L.ctp_tune_set.argtypes = [P, i32, i32]
     L.ctp_tune_get.argtypes = [P, i32, ctypes.POINTER(i32)]
     L.ctp_autotune_batch.argtypes = [P, i32, P, P, ctypes.POINTER(Options), P, P, i32, P, i32, P, P,
@@ -607,31 +613,58 @@ class Multifrontal:
         return dict(parent=par, n=n, p=p, nelim=e, delayed=d)
 
     def panel_info(self):
+        """Per panel: rows, columns, eliminated, block."""
         n = np.zeros(self.nf, np.int64)
         p = np.zeros(self.nf, np.int32)
         e = np.zeros(self.nf, np.int32)
+        b = np.zeros(self.nf, np.int32)
         _check("ctp_mf_panel_info", self.ctx.lib.ctp_mf_panel_info(
             self.handle, self.nf, n.ctypes.data_as(ctypes.c_void_p), p.ctypes.data_as(ctypes.c_void_p),
-            e.ctypes.data_as(ctypes.c_void_p)))
-        return n, p, e
+            e.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p)))
+        return n, p, e, b
 
     def panel_perms(self):
         return [device_view(self.fronts[k].perm, int(self.fronts[k].p), "int32").cpu().numpy()
                 for k in range(self.nf)]
 
-    def refine(self, B, X, ws, max_steps=10, tol=1e-14, stream=None):
+    def refine(self, B, X, ws, max_steps=10, tol=1e-14, stream=None, planned=True):
         """Solve with FP64 refinement against the sparse matrix (device B, X
-        column-major N x nrhs tensors).  Returns (history, corrections)."""
+        column-major N x nrhs tensors), by the level-planned solve (or, with
+        planned=False, the generic front-list solve).  Returns (history,
+        corrections)."""
         nrhs = B.shape[0]
         hist = np.zeros((max_steps + 1) * nrhs)
         steps = ctypes.c_int32()
-        _check("ctp_refine_csc", self.ctx.lib.ctp_refine_csc(
-            self.ctx.handle, self.nf, ctypes.cast(self.fronts, ctypes.c_void_p), self.N,
-            _ptr(self.d_colptr), _ptr(self.d_rowind), _ptr(self.d_val), nrhs, _ptr(B), self.N,
-            _ptr(X), self.N, max_steps, tol, hist.ctypes.data, ctypes.byref(steps), _ptr(ws),
-            ws.numel(), _stream(stream)))
+        if planned:
+            _check("ctp_mf_refine", self.ctx.lib.ctp_mf_refine(
+                self.ctx.handle, self.handle, _ptr(self.d_colptr), _ptr(self.d_rowind), _ptr(self.d_val),
+                nrhs, _ptr(B), self.N, _ptr(X), self.N, max_steps, tol, hist.ctypes.data,
+                ctypes.byref(steps), _ptr(ws), ws.numel(), _stream(stream)))
+        else:
+            _check("ctp_refine_csc", self.ctx.lib.ctp_refine_csc(
+                self.ctx.handle, self.nf, ctypes.cast(self.fronts, ctypes.c_void_p), self.N,
+                _ptr(self.d_colptr), _ptr(self.d_rowind), _ptr(self.d_val), nrhs, _ptr(B), self.N,
+                _ptr(X), self.N, max_steps, tol, hist.ctypes.data, ctypes.byref(steps), _ptr(ws),
+                ws.numel(), _stream(stream)))
         k = int(steps.value)
         return hist[:(k + 1) * nrhs].reshape(k + 1, nrhs), k
+
+    def refine_workspace(self, nrhs):
+        import torch
+        b1 = ctypes.c_size_t()
+        _check("ctp_mf_refine_workspace_size",
+               self.ctx.lib.ctp_mf_refine_workspace_size(self.handle, nrhs, ctypes.byref(b1)))
+        b2 = ctypes.c_size_t()
+        info = self.info()
+        _check("ctp_refine_workspace_size",
+               self.ctx.lib.ctp_refine_workspace_size(self.N, int(info["n"].max()), nrhs, ctypes.byref(b2)))
+        return torch.empty(max(b1.value, b2.value, 1), dtype=torch.uint8, device=f"cuda:{self.ctx.device}")
+
+    def solve(self, X, ws, stream=None):
+        """X <- M^{-1} X by the level-planned solve (device, column-major)."""
+        _check("ctp_mf_solve", self.ctx.lib.ctp_mf_solve(
+            self.ctx.handle, self.handle, X.shape[0], _ptr(X), self.N, _ptr(ws), ws.numel(),
+            _stream(stream)))
 
     def destroy(self):
         if self.handle:

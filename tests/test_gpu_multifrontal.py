@@ -41,8 +41,14 @@ def test_multifrontal_matches_oracle(ctx, k, sigma, method):
     assert gi["delayed"].tolist() == [i["delayed"] for i in info]
     assert gi["n"].tolist() == [i["n"] for i in info]
     assert mf.nf == len(panels)
-    for k_, (pg, po) in enumerate(zip(mf.panel_perms(), panels)):
-        assert np.array_equal(pg, po["perm"]), k_
+    # panels come level by level on the GPU, block by block in the oracle:
+    # compare them per block, in order within a block
+    _, _, _, blk = mf.panel_info()
+    order = sorted(range(mf.nf), key=lambda k_: (blk[k_], k_))
+    perms = mf.panel_perms()
+    assert [int(blk[k_]) for k_ in order] == [po["front"] for po in panels]
+    for k_, po in zip(order, panels):
+        assert np.array_equal(perms[k_], po["perm"]), k_
     rng = np.random.default_rng(4)
     B = rng.standard_normal((N, 2))
     X = ctp.colmajor(B)
@@ -51,11 +57,16 @@ def test_multifrontal_matches_oracle(ctx, k, sigma, method):
     xo = S.solve(panels, B)
     xg = ctp.to_numpy(X)
     assert np.abs(xg - xo).max() <= 1e-9 * np.abs(xo).max()
+    # the level-planned solve (independent panels of a level in one launch)
+    X2 = ctp.colmajor(B)
+    wsr = mf.refine_workspace(2)
+    mf.solve(X2, wsr)
+    assert np.abs(ctp.to_numpy(X2) - xo).max() <= 1e-9 * np.abs(xo).max()
     if method != "restricted":
-        Xr = torch.zeros_like(X)
-        wsr = ctp.refine_workspace(ctx, N, int(gi["n"].max()), 2)
-        hist, steps = mf.refine(ctp.colmajor(B), Xr, wsr)
-        assert hist[-1].max() <= 1e-14
+        for planned in (True, False):
+            Xr = torch.zeros_like(X)
+            hist, steps = mf.refine(ctp.colmajor(B), Xr, wsr, planned=planned)
+            assert hist[-1].max() <= 1e-14
     mf.destroy()
 
 
@@ -78,7 +89,7 @@ def test_multifrontal_mixed_refines(ctx, prec):
     assert [gi["nelim"][s] for s in leaves] == [g64["nelim"][s] for s in leaves]
     B = np.random.default_rng(5).standard_normal((N, 3))
     X = torch.zeros((3, N), dtype=torch.float64, device="cuda")
-    wsr = ctp.refine_workspace(ctx, N, int(mf.info()["n"].max()), 3)
+    wsr = mf.refine_workspace(3)
     hist, steps = mf.refine(ctp.colmajor(B), X, wsr)
     if prec == "bf16x6":
         assert hist[-1].max() <= 1e-14 and steps <= 3
