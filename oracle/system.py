@@ -176,3 +176,25 @@ def solve_gradient(fronts, x, gx):
     gM = np.tril(full + full.T)
     np.fill_diagonal(gM, np.diag(full))
     return gb, gM
+
+
+def solve_gradient_pattern(fronts, x, gx, row, col):
+    """``solve_gradient`` restricted to a pattern of stored lower-triangle
+    entries (row[k] >= col[k]): returns (gb, g) with g[k] the gradient with
+    respect to the stored entry (row[k], col[k]) -- for an off-diagonal entry
+    -sum_r (gb_ir x_jr + gb_jr x_ir), for a diagonal one -sum_r gb_ir x_ir
+    (the same derivative of x = M^{-1} b as ``solve_gradient``, evaluated only
+    where the sparse matrix stores an entry)."""
+    gb = solve(fronts, gx)
+    G = np.atleast_2d(gb.T).T
+    X = np.atleast_2d(np.asarray(x).T).T
+    row = np.asarray(row, np.int64)
+    col = np.asarray(col, np.int64)
+    g = np.empty(len(row))
+    for k in range(len(row)):
+        i, j = row[k], col[k]
+        if i == j:
+            g[k] = -np.dot(G[i], X[i])
+        else:
+            g[k] = -(np.dot(G[i], X[j]) + np.dot(G[j], X[i]))
+    return gb, g

@@ -82,3 +82,42 @@ def test_panels_split_wide_fronts():
     rp = [p for p in panels if p["front"] == root]
     assert len(rp) >= 4 and all(p["p"] <= 40 for p in rp)
     assert sum(p["e"] for p in rp) == info[root]["nelim"] == info[root]["p"]
+
+
+def _fd_loss(cp, ri, N, vals, B):
+    """loss = ||A^{-1} B||_F^2 by SuperLU (a library solve, not the oracle)."""
+    X = spla.splu(MF.sym_csc(cp, ri, vals, N).tocsc()).solve(B)
+    return float((X * X).sum())
+
+
+@pytest.mark.parametrize("k,leaf,nrhs,sample", [(4, 8, 3, None), (16, 64, 32, 10)])
+def test_pattern_gradient_against_finite_differences(k, leaf, nrhs, sample):
+    """The gradient of loss = ||x||^2, x = A^{-1} B, through the multifrontal
+    panels (adjoint solve with the same factors, then the pattern formula):
+    every stored entry of a 4^3 grid and a sample of the 16^3 grid with 32
+    right-hand sides, and entries of B, against central differences (h = 1e-6)
+    of SuperLU solves.  A stored off-diagonal value stands for both of its
+    symmetric entries, so perturbing it perturbs both."""
+    cp, ri, v, N, perm, blocks = _problem(k, leaf=leaf)
+    panels, _ = MF.factor(cp, ri, v, N, perm, blocks, "strict", w=256)
+    rng = np.random.default_rng(k)
+    B = rng.standard_normal((N, nrhs))
+    x, hist, _ = S.refine(MF.sym_csc(cp, ri, v, N).toarray(), panels, B)
+    assert np.max(hist[-1]) <= 1e-14
+    col = np.repeat(np.arange(N), np.diff(cp))
+    gb, g = S.solve_gradient_pattern(panels, x, 2.0 * x, ri, col)
+    h = 1e-6
+    qs = range(len(v)) if sample is None else rng.choice(len(v), sample, replace=False)
+    for q in qs:
+        vp, vm = v.copy(), v.copy()
+        vp[q] += h
+        vm[q] -= h
+        fd = (_fd_loss(cp, ri, N, vp, B) - _fd_loss(cp, ri, N, vm, B)) / (2 * h)
+        assert abs(fd - g[q]) <= 1e-6 * np.abs(g).max(), (q, fd, g[q])
+    for _ in range(4):
+        i, r = rng.integers(N), rng.integers(nrhs)
+        Bp, Bm = B.copy(), B.copy()
+        Bp[i, r] += h
+        Bm[i, r] -= h
+        fd = (_fd_loss(cp, ri, N, v, Bp) - _fd_loss(cp, ri, N, v, Bm)) / (2 * h)
+        assert abs(fd - gb[i, r]) <= 1e-6 * np.abs(gb).max(), (i, r, fd, gb[i, r])
