@@ -584,9 +584,45 @@ def measure_multifrontal(ctx, dev, inputs, k=64, nrhs=16):
                      "bwd_err_history": [float(x) for x in hist.max(axis=1)],
                      "kernels": {kk: {"launches": vv[0], "ms": vv[1]} for kk, vv in kern.items()}}
         del Bd, X, ws
+        if prec in ("fp64", "bf16x6"):
+            out[prec]["gradient"] = measure_mf_gradient(mf, dev, N, len(v), nrhs=32)
     mf.destroy()
     torch.cuda.empty_cache()
     return out
+
+
+def measure_mf_gradient(mf, dev, N, nnz, nrhs=32):
+    """Config 5 through config 4's factorization: x = M^{-1} B for nrhs N(0,1)
+    right-hand sides (refined), loss = ||x||^2, the refined adjoint solve
+    grad_B = M^{-T} (2x) with the same factors and pivots, and the gradient of
+    the stored lower-triangle entries (the sparsity pattern)."""
+    import torch
+    from paper_1305_2353_gb300 import ctp
+    B = ctp.colmajor(np.random.default_rng(5).standard_normal((N, nrhs)), dev)
+    X = torch.zeros_like(B)
+    Gb = torch.zeros_like(B)
+    gval = torch.empty(nnz, dtype=torch.float64, device=dev)
+    ws = mf.refine_workspace(nrhs)
+    mf.grad_values(Gb, X, gval)   # warm-up: pattern upload, module load
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hx, kx = mf.refine(B, X, ws)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    G = 2.0 * X
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    hg, kg = mf.refine(G, Gb, ws)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    mf.grad_values(Gb, X, gval)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    loss = float((X * X).sum())
+    return {"nrhs": nrhs, "solve_s": t1 - t0, "adjoint_s": t3 - t2, "grad_pattern_s": t4 - t3,
+            "loss": loss, "solve_corrections": kx, "adjoint_corrections": kg,
+            "solve_bwd_err": float(hx[-1].max()), "adjoint_bwd_err": float(hg[-1].max()),
+            "grad_abs_max": float(gval.abs().max())}
 
 
 def batch_accuracy(ctx, fronts, count=12, seed=0):

@@ -384,15 +384,17 @@ ctp_status ctp_refine_csc(ctp_ctx *ctx, int32_t nf, const ctp_sfront *fronts, in
  *   the fully-summed columns (the block's, then the children's delayed ones)
  *   eliminated in panels of at most ctp_max_p() columns by ctp_factor_supernode
  *   with opt (its smode is ignored: each panel's Form subtracts into the front,
- *   whose trailing block becomes the contribution block).  A front tries its
- *   fully-summed columns in one pass: it ends after the panel that takes its
- *   last untried column (so a front of at most ctp_max_p() such columns is one
- *   panel) or after a panel that eliminates nothing; the columns left are
- *   delayed to the parent.  A root front must eliminate all its columns: its
- *   panels continue while they make progress, one that eliminates nothing is
- *   retried with CTP_PIV_TPP; otherwise CTP_ECAPACITY.  The fronts of a tree
- *   level are assembled together, and those of at most ctp_max_p() fully-summed
- *   columns are factored in one batch (strict and restricted pivoting).
+ *   whose trailing block becomes the contribution block).  A front is a chain
+ *   of panels: each panel takes the leading at most ctp_max_p() remaining
+ *   fully-summed columns (those the previous panel delayed first) with a fresh
+ *   compression, and the front keeps starting panels while they eliminate
+ *   something; after a panel that eliminates nothing the columns left are
+ *   delayed to the parent.  A root front must eliminate all its columns: a
+ *   panel there that eliminates nothing is retried with CTP_PIV_TPP; otherwise
+ *   CTP_ECAPACITY.  The fronts of a tree level are assembled together, and
+ *   with strict or restricted pivoting the non-root fronts of a level are
+ *   factored in batched passes (one panel per front still making progress per
+ *   pass).
  *   Device memory for the fronts is allocated by the call and held by *mf.
  *   Synchronises `stream` once per panel.
  * ctp_mf_fronts: the factored panels, in elimination order, as fronts for
@@ -413,6 +415,18 @@ ctp_status ctp_mf_info(const ctp_mf *mf, int32_t cap, int32_t *nblocks, int32_t 
 ctp_status ctp_mf_solve_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes);
 ctp_status ctp_mf_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *X, int64_t ldx, void *workspace,
                         size_t ws_bytes, void *stream);
+/* Adjoint solve with the multifrontal factors: G <- M^{-T} G (N x nrhs,
+ * device, column-major, ldg >= N) by the planned solve, with the same factors
+ * and pivot sequence.  M is symmetric and so is its factored form (the 2x2
+ * blocks of D are symmetric), so M^{-T} = M^{-1}: this is the solve that the
+ * backward pass of a differentiated sparse solve x = M^{-1} b makes for
+ * grad_b = M^{-T} grad_x (Section 1's Solve task run on the adjoint system);
+ * its refined form is ctp_mf_refine with G as the right-hand sides.  The
+ * gradient of the stored entries then comes from ctp_sym_grad_pattern with
+ * the pattern's (row, column) pairs.  Workspace from
+ * ctp_mf_solve_workspace_size.  Launches only. */
+ctp_status ctp_mf_adjoint_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *G, int64_t ldg,
+                                void *workspace, size_t ws_bytes, void *stream);
 /* ctp_refine_csc with the planned solve (arguments as there; colptr, rowind,
  * val: the matrix in device memory). */
 ctp_status ctp_mf_refine_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes);

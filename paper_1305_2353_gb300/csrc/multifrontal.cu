@@ -665,6 +665,12 @@ ctp_status ctp_mf_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *X,
     return CTP_OK;
 }
 
+ctp_status ctp_mf_adjoint_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *G, int64_t ldg,
+                                void *workspace, size_t ws_bytes, void *stream) {
+    // M symmetric, D's 2x2 blocks symmetric: M^{-T} = M^{-1}, the same planned solve
+    return ctp_mf_solve(ctx, mf, nrhs, G, ldg, workspace, ws_bytes, stream);
+}
+
 ctp_status ctp_mf_refine_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes) {
     if (mf == nullptr || bytes == nullptr || nrhs < 1 || !mf->factored) return CTP_EINVAL;
     *bytes = refine_layout(mf->N, mf->plan.ws_bytes(nrhs), nrhs).total;

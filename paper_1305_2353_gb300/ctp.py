@@ -40,7 +40,7 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_sym_grad_dense", "ctp_sym_grad_pattern", "ctp_backward_error_csc", "ctp_refine_csc",
            "ctp_mf_analyse", "ctp_mf_factor", "ctp_mf_fronts", "ctp_mf_info", "ctp_mf_destroy",
            "ctp_mf_panel_info", "ctp_mf_solve_workspace_size", "ctp_mf_solve",
-           "ctp_mf_refine_workspace_size", "ctp_mf_refine"]
+           "ctp_mf_refine_workspace_size", "ctp_mf_refine", "ctp_mf_adjoint_solve"]
 TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G = 0, 1, 2
 WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
@@ -131,6 +131,7 @@ def load(path: str = LIB_PATH):
     L.ctp_mf_solve_workspace_size.argtypes = [P, i32, ctypes.POINTER(sz)]
     L.ctp_mf_solve.argtypes = [P, P, i32, P, i64, P, sz, P]
     L.ctp_mf_refine_workspace_size.argtypes = [P, i32, ctypes.POINTER(sz)]
+    L.ctp_mf_adjoint_solve.argtypes = [P, P, i32, P, i64, P, sz, P]
     L.ctp_mf_refine.argtypes = [P, P, P, P, P, i32, P, i64, P, i64, i32, ctypes.c_double, P,
                                 ctypes.POINTER(i32), P, sz, P]
     L.ctp_tune_set.argtypes = [P, i32, i32]
@@ -666,6 +667,33 @@ class Multifrontal:
             self.ctx.handle, self.handle, X.shape[0], _ptr(X), self.N, _ptr(ws), ws.numel(),
             _stream(stream)))
 
+    def adjoint_solve(self, G, ws, stream=None):
+        """G <- M^{-T} G with the same factors and pivots (device, column-major)."""
+        _check("ctp_mf_adjoint_solve", self.ctx.lib.ctp_mf_adjoint_solve(
+            self.ctx.handle, self.handle, G.shape[0], _ptr(G), self.N, _ptr(ws), ws.numel(),
+            _stream(stream)))
+
+    def set_values(self, val):
+        """Replace the matrix values (same pattern) before the next factor."""
+        self.d_val.copy_(val.reshape(-1))
+
+    def pattern_device(self):
+        """(row, col) int32 device arrays of the stored lower-triangle entries,
+        in the pattern's order."""
+        if getattr(self, "_d_row", None) is None:
+            import torch
+            dev = f"cuda:{self.ctx.device}"
+            col = np.repeat(np.arange(self.N, dtype=np.int32), np.diff(self.colptr))
+            self._d_row = torch.from_numpy(self.rowind).to(dev)
+            self._d_col = torch.from_numpy(col).to(dev)
+        return self._d_row, self._d_col
+
+    def grad_values(self, Gb, X, out, stream=None):
+        """Gradient with respect to the stored entries (pattern order) given
+        Gb = M^{-T} dloss/dX and X (device, column-major N x nrhs)."""
+        row, col = self.pattern_device()
+        sym_grad_pattern(self.ctx, row, col, self.N, X.shape[0], Gb, self.N, X, self.N, out, stream)
+
     def destroy(self):
         if self.handle:
             self.ctx.lib.ctp_mf_destroy(self.handle)
@@ -676,6 +704,80 @@ class Multifrontal:
             self.destroy()
         except Exception:
             pass
+
+
+class SparseSymSolver:
+    """Differentiable solves X = M^{-1} B for a sparse symmetric indefinite M of
+    a fixed pattern (lower triangle in compressed columns, host arrays), its
+    elimination order and supernode blocks; the values are a float64 CUDA
+    tensor in the pattern's order.  Calling the solver factors M
+    multifrontally with `pivot`/`prec` and solves with FP64 refinement; the
+    backward pass solves the adjoint system with the same factors (refined)
+    and gives the gradient of the stored entries only (the sparsity pattern)."""
+
+    def __init__(self, ctx: Context, colptr, rowind, perm, blocks, pivot="strict", prec="fp64",
+                 steps=10, tol=1e-14):
+        self.ctx = ctx
+        self.mf = Multifrontal(ctx, colptr, rowind, np.zeros(len(rowind)), perm, blocks)
+        self.opt = options(pivot=pivot, prec=prec)
+        self.steps, self.tol = steps, tol
+        self.version = 0          # bumped by every factorization
+        self.history = None
+
+    def _factor(self, val):
+        self.mf.set_values(val.detach())
+        self.mf.factor(self.opt)
+        self.version += 1
+        return self.version
+
+    def __call__(self, val, B):
+        return _sparse_sym_solve_fn().apply(val, B, self)
+
+
+_SparseSymSolve = None
+
+
+def _sparse_sym_solve_fn():
+    global _SparseSymSolve
+    if _SparseSymSolve is not None:
+        return _SparseSymSolve
+    import torch
+
+    class SparseSymSolve(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, val, B, solver):
+            mf = solver.mf
+            N = mf.N
+            version = solver._factor(val)
+            Bt = B.detach().reshape(N, -1).t().contiguous()
+            X = torch.zeros_like(Bt)
+            ws = mf.refine_workspace(Bt.shape[0])
+            solver.history, _ = mf.refine(Bt, X, ws, solver.steps, solver.tol)
+            fctx.solver, fctx.version, fctx.bshape = solver, version, B.shape
+            fctx.save_for_backward(val.detach().clone(), X)
+            return X.t().contiguous().reshape(B.shape)
+
+        @staticmethod
+        def backward(fctx, gX):
+            val, X = fctx.saved_tensors
+            solver = fctx.solver
+            mf = solver.mf
+            N = mf.N
+            if solver.version != fctx.version:        # factored again since: restore
+                fctx.version = solver._factor(val)
+            G = gX.reshape(N, -1).t().contiguous()
+            Gb = torch.zeros_like(G)
+            ws = mf.refine_workspace(G.shape[0])
+            mf.refine(G, Gb, ws, solver.steps, solver.tol)     # M^{-T} = M^{-1}
+            gval = None
+            if fctx.needs_input_grad[0]:
+                gval = torch.empty_like(val)
+                mf.grad_values(Gb, X, gval)
+            gB = Gb.t().reshape(fctx.bshape) if fctx.needs_input_grad[1] else None
+            return gval, gB, None
+
+    _SparseSymSolve = SparseSymSolve
+    return SparseSymSolve
 
 
 class Batch:
