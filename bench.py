@@ -476,6 +476,8 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
     del g, b
     ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 200)
     ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
+    import gc
+    gc.collect()
     torch.cuda.empty_cache()
     return {"value": (fs + form) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_batch": ms,
             "prec": prec, "S": smode, "factor_solve_flops": fs, "form_flops": form,
@@ -634,7 +636,13 @@ def batch_accuracy(ctx, fronts, count=12, seed=0):
     pick = order[np.linspace(0, len(order) - 1, count).astype(int)]
     res = {"sample": f"{count} fronts spread over n*p (n from {fronts[pick[0]].shape[0]} to "
                      f"{fronts[pick[-1]].shape[0]}), 2-node systems, 1 RHS, tol 1e-14"}
+    import gc
     import torch
+    # the chain driver allocates its fronts itself: hand back what torch caches
+    gc.collect()
+    torch.cuda.empty_cache()
+    free, total = torch.cuda.mem_get_info()
+    print(f"batch accuracy: {free / 2**30:.1f} GiB free of {total / 2**30:.1f}", file=sys.stderr)
     for prec in ("fp64", "bf16x3", "bf16"):
         worst, steps = 0.0, 0
         for k in pick:

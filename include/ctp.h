@@ -59,7 +59,8 @@ typedef enum {
 } ctp_pivot;
 
 /* Arithmetic of the Form step.  Compression, pivot selection, the 2x2 pivot
- * inversions, D11 and the Solve are always FP64. */
+ * inversions and D11 are always FP64; the Solve is FP64 unless the options ask
+ * for the tensor-core Solve (ctp_solve_kind below). */
 typedef enum {
     CTP_FP64 = 0,  /* FP64 throughout */
     CTP_BF16 = 1,  /* Form on the tensor cores: BF16 operands, FP32 accumulation and
@@ -109,13 +110,26 @@ typedef enum {
 #define CTP_PIVKIND_ZERO (-1)
 #define CTP_PIVKIND_DELAYED 3
 
+/* Arithmetic of the Solve step (L21 = A21 P^T (D11 L11^T)^{-1} and the update
+ * of the delayed columns, Section 1 task list).
+ *  CTP_SOLVE_FP64: FP64 right-looking substitution per row (default).
+ *  CTP_SOLVE_TC: one tensor-core product per supernode, x_e [U D11^{-1} | U |
+ *    -U L_d^T] with U = L11^{-T} formed in FP64 on chip, split-BF16 operands
+ *    (three pieces: products close to FP32) and FP32 accumulation; the outputs (L21 in
+ *    FP64, the Form's BF16 operands, x_d plus its correction in FP64) carry the
+ *    split's rounding, which FP64 iterative refinement on the complete system
+ *    removes.  It applies with a tensor-core Form (prec != CTP_FP64, smode !=
+ *    CTP_S_NONE) and compressed or restricted pivoting; otherwise the Solve is
+ *    FP64.  Pivots do not change. */
+typedef enum { CTP_SOLVE_FP64 = 0, CTP_SOLVE_TC = 1 } ctp_solve_kind;
+
 typedef struct {
     double u;       /* threshold, 0 < u <= 0.5 (Section 2; default 0.01) */
     double small;   /* entries below `small` count as zero (default 1e-20) */
     int32_t pivot;  /* ctp_pivot */
     int32_t prec;   /* ctp_prec */
     int32_t smode;  /* ctp_smode */
-    int32_t reserved;
+    int32_t solve;  /* ctp_solve_kind (0: FP64) */
 } ctp_options;
 
 typedef struct ctp_ctx ctp_ctx;

@@ -18,7 +18,7 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
                                        "batch_form", "w21_from_l", "sys_forward", "sys_backward",
                                        "symv_residual", "backward_error", "axpy", "form_tc_bf16x3",
                                        "sym_grad", "mf_assemble", "mf_extend_add", "spmv_residual",
-                                       "form_tc_bf16x6"};
+                                       "form_tc_bf16x6", "solve_tc"};
 }  // namespace ctp
 
 namespace ctp {
@@ -48,6 +48,9 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     L.aux = off;
     off += align256(opt->pivot == CTP_PIV_RELAXED ? relaxed_aux_bytes(m, p, num_sms)
                                                   : (opt->pivot == CTP_PIV_TPP ? tpp_ws_bytes(p) : 0));
+    // tensor-core Solve: split-BF16 copies of x_e and Z^T
+    L.Xs = off;
+    off += align256(solve_on_tc(opt) ? solve_tc_ws_bytes(m, p, solve_tc_pieces(opt->prec)) : 0);
     L.total = off;
     return L;
 }
@@ -97,6 +100,7 @@ static ctp_status check_opts(const ctp_options *opt) {
     if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
     if (opt->prec < CTP_FP64 || opt->prec > CTP_BF16X6) return CTP_EINVAL;
     if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP64_SUB) return CTP_EINVAL;
+    if (opt->solve != CTP_SOLVE_FP64 && opt->solve != CTP_SOLVE_TC) return CTP_EINVAL;
     return CTP_OK;
 }
 
@@ -273,7 +277,12 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
         fa.C = nullptr;
     }
     CTP_CUDA(timed(ctx, K_FACTOR, st, [&] { return launch_factor_cluster(fa, ctx->factor_g, st); }));
-    if (m > 0)
+    if (m > 0 && solve_on_tc(opt))
+        CTP_CUDA(timed(ctx, K_SOLVE_TC, st, [&] {
+            return launch_solve_tc(A, n, p, lda, perm, piv, Dinv, nelim, ws + L.Xs, solve_tc_pieces(opt->prec), Wb,
+                                   Lbf, lo_off, pieces, info, ctx->num_sms, st);
+        }));
+    else if (m > 0)
         CTP_CUDA(timed(ctx, K_SOLVE, st, [&] {
             return launch_solve_fp64(A, n, p, lda, perm, piv, Dinv, nelim, W21, m, Wb, Lbf, Kp, lo_off, pieces,
                                      st);

@@ -38,11 +38,15 @@ ChainWork::~ChainWork() {
 }
 
 bool ChainWork::reserve(ctp_ctx *ctx, int64_t n, int w, const ctp_options *opts, int nopt) {
+    // any panel width up to w can occur (first panel, last panel, and a
+    // narrower panel has more rows below it for the same K padding)
     size_t need = 0;
-    for (int k = 0; k < nopt; k++) {
-        const size_t b = ws_layout(n, w < n ? w : (int)n, &opts[k], ctx_num_sms(ctx)).total;
-        need = b > need ? b : need;
-    }
+    const int wm = w < n ? w : (int)n;
+    for (int k = 0; k < nopt; k++)
+        for (int wi = 1; wi <= wm; wi++) {
+            const size_t b = ws_layout(n, wi, &opts[k], ctx_num_sms(ctx)).total;
+            need = b > need ? b : need;
+        }
     if (need > ws_bytes) {
         if (ws) cudaFree(ws);
         ws = nullptr;

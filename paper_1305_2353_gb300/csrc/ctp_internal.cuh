@@ -23,7 +23,7 @@ constexpr int kInfoOk = 0;
 //   Wb, Lb              m*Kp BF16 copies of Y and L21 for the tensor-core Form
 //   aux                 method-specific scratch (relaxed candidate lists)
 struct WsLayout {
-    size_t info, C, Dinv, W21, Wb, Lb, aux, total;
+    size_t info, C, Dinv, W21, Wb, Lb, aux, Xs, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -128,6 +128,21 @@ cudaError_t batch_compress(const ctp_plan *P, const ctp_front *fr, char *w, int 
 cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st);
 cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, cudaStream_t st);
 cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
+
+// Tensor-core Solve (solve_tc.cu): BF16 pieces of its operands, its scratch
+// bytes, and the launch sequence (prep of Z^T, gather of x_e, the GEMM with its
+// epilogue).  Its outputs are stored factors, so it always takes three pieces
+// (products close to FP32, whatever the Form's pieces): with two, a chain of
+// fronts whose every Solve and Form was split in two stopped refining at 2e-13.
+inline int solve_tc_pieces(int) { return 3; }
+// the tensor-core Solve runs when asked for and the Form runs on the tensor cores
+inline bool solve_on_tc(const ctp_options *o) {
+    return o->solve == CTP_SOLVE_TC && o->prec != CTP_FP64 && o->smode != CTP_S_NONE && o->pivot != CTP_PIV_TPP;
+}
+size_t solve_tc_ws_bytes(int64_t m, int p, int spieces);
+cudaError_t launch_solve_tc(double *A, int64_t n, int p, int64_t lda, const int32_t *perm, const int32_t *piv,
+                            const double *Dinv, const int32_t *nelim, void *ws, int spieces, void *Wb, void *Lb,
+                            int64_t foff, int fpieces, int32_t *info, int num_sms, cudaStream_t st);
 
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,

@@ -28,121 +28,28 @@
 // Every mbarrier wait is bounded; on timeout the kernel records CTP_ETIMEOUT in
 // the info word, stops issuing work, waits for nothing further, frees its
 // tensor memory and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "ctp_internal.cuh"
+#include "tc_common.cuh"
 
 namespace ctp {
 
+using namespace tc;
+
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 6;
+constexpr int kBM = 128, kBN = 256, kStages = 6;
 constexpr int kMaxKB = 4;  // K blocks of 64 (p <= 256)
-constexpr int kUmmaK = 16;
 constexpr int kEpiWarps = 8;
 constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
 constexpr uint32_t kStageA = kBM * kBK * 2;  // 16 KB
 constexpr uint32_t kStageB = kBN * kBK * 2;  // 32 KB
 constexpr uint32_t kTmemCols = 512;          // two 256-column FP32 accumulators
-constexpr long kSpinLimit = 1L << 22;
-
 struct Bars {
     unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2], bfull, bempty;
     uint32_t tmem_base;
     int abort;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of `bar` with the given parity; false on timeout
-// or when another role has already aborted.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, Bars *b) {
-    for (long it = 0; it < kSpinLimit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255) == 255 && *(volatile int *)&b->abort) return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Shared-memory matrix descriptor for a K-major operand in the canonical
-// 128-byte-swizzle layout written by TMA: rows of 128 bytes, groups of 8 rows
-// 1024 bytes apart (stride byte offset), version bits 46-47 = 1, swizzle mode 2.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
-    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
-    d |= (uint64_t)1 << 46;                   // descriptor version
-    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
 
 // Tile shapes and operand pieces.  Plain BF16 (P = 1): tiles of 128 rows x
 // 256 columns.  Split BF16: every operand x is held as P BF16 pieces -- P = 2:
@@ -336,11 +243,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&bars.tmem_base)),
-                     "r"(C::TmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tmem_alloc(&bars.tmem_base, C::TmemCols);
     }
     tc_fence_before();
     __syncthreads();
@@ -359,7 +262,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 if (x.KB == 0) continue;
                 bool ok = true;
                 if (C::kResident && x.key != cur_key) {
-                    if (!mbar_wait(&bars.bempty, bphase ^ 1u, &bars)) {
+                    if (!mbar_wait(&bars.bempty, bphase ^ 1u, &bars.abort)) {
                         atomicExch(&bars.abort, 1);
                         break;
                     }
@@ -374,7 +277,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     cur_key = x.key;
                 }
                 for (int kb = 0; kb < x.KB; kb++) {
-                    if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars)) {
+                    if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars.abort)) {
                         ok = false;
                         break;
                     }
@@ -407,14 +310,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             uint32_t phase = 0, accphase = 0, bphase = 0;
             TileInfo x;
             for (int64_t k = 0; TILE_K(k, x); k++) {
-                if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars)) {
+                if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars.abort)) {
                     atomicExch(&bars.abort, 1);
                     break;
                 }
                 tc_fence_after();
                 bool ok = true;
                 if (C::kResident && x.KB > 0 && x.key != cur_key) {
-                    if (!mbar_wait(&bars.bfull, bphase, &bars)) {
+                    if (!mbar_wait(&bars.bfull, bphase, &bars.abort)) {
                         atomicExch(&bars.abort, 1);
                         break;
                     }
@@ -424,7 +327,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 const uint32_t dt = tmem + (uint32_t)(acc * BN);
                 for (int kb = 0; kb < x.KB; kb++) {
-                    if (!mbar_wait(&bars.full[stage], phase, &bars)) {
+                    if (!mbar_wait(&bars.full[stage], phase, &bars.abort)) {
                         ok = false;
                         break;
                     }
@@ -490,7 +393,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int ti = x.ti, tj = x.tj, KB = x.KB, layout = x.layout;
             const int64_t m = x.m, nb = x.nb, lds = x.lds;
             float *S = x.S;
-            if (!mbar_wait(&bars.acc_full[acc], accphase, &bars)) {
+            if (!mbar_wait(&bars.acc_full[acc], accphase, &bars.abort)) {
                 if (lane == 0) atomicExch(&bars.abort, 1);
                 break;
             }
@@ -512,7 +415,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + half * (BN / 2) + c * 32);
                 tmem_ld32_nowait(taddr, *reinterpret_cast<uint32_t(*)[32]>(&r[0]));
                 tmem_ld32_nowait(taddr + 32, *reinterpret_cast<uint32_t(*)[32]>(&r[32]));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tmem_wait_ld();
                 if (KB == 0) {
 #pragma unroll
                     for (int xx = 0; xx < 64; xx++) r[xx] = 0u;
@@ -582,12 +485,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (threadIdx.x == 0 && bars.abort) atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TmemCols)
-                     : "memory");
+        tmem_dealloc(tmem, C::TmemCols);
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tc::encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (fn == nullptr) {
         void *p = nullptr;
@@ -600,7 +504,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_rows) {
+bool tc::make_map_bf16(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (enc == nullptr) return false;
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
@@ -612,8 +516,6 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int Kp, int box_
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 int form_tc_kpad(int p) { return (p + kBK - 1) / kBK * kBK; }
 
@@ -633,7 +535,7 @@ bool make_maps(CUtensorMap (&mW)[3], CUtensorMap (&mL)[3], const void *Wb, const
         const int q = pc < P ? pc : 0;  // unused pieces: valid copies of the first
         const char *w = (const char *)Wb + 2 * off * q, *l = (const char *)Lb + 2 * off * q;
         if ((((uintptr_t)w) | ((uintptr_t)l)) & 15) return false;
-        if (!make_map(&mW[pc], w, rows, Kp, kBM) || !make_map(&mL[pc], l, rows, Kp, bn_of(P))) return false;
+        if (!make_map_bf16(&mW[pc], w, rows, Kp, kBM) || !make_map_bf16(&mL[pc], l, rows, Kp, bn_of(P))) return false;
     }
     return true;
 }

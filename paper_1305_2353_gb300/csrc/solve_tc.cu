@@ -1,0 +1,443 @@
+// solve_tc.cu -- K5 on the tensor cores: the Solve task L21 = A21 P^T (D11 L11^T)^{-1}
+// (Section 1 task list; Figure 4.1 (d),(e)) and the update of the delayed
+// columns, as one GEMM per supernode with split-BF16 operands and FP32
+// accumulation (tcgen05), for the mixed-precision factorizations.
+//
+// With x = A21(i, perm) the permuted row of A21, x_e its e eliminated and x_d its
+// d = p - e delayed positions, the FP64 Solve computes
+//   Y = x_e U,  U = L11^{-T}  (unit upper),   L21 = Y D11^{-1},   x_d' = x_d - Y L_d^T,
+// all of which are linear in x_e.  So one product x_e Z gives every output:
+//   Z = [ U D11^{-1} | U | -U L_d^T ]        (e x (e + e + d))
+// -- L21 (written to A21 in FP64 and as the Form's BF16 operand pieces), Y = W21
+// (the Form's other operand) and the correction added to x_d.  The three
+// blocks start at output columns 0, E and 2E with E = e rounded up to 32 (the
+// columns between are zero), so a 32-column slice of the accumulator lies in
+// one block and its BF16 pieces go out as 16-byte stores.  Z is the
+// substitution applied to the identity rows e_k, k < e: the prep kernel runs
+// exactly the FP64 Solve's recurrence on them.
+//
+// Kernels:
+//   k_stc_prep    Z^T in BF16 pieces (K-major: row o of the operand is output
+//                 column o; 640 rows, zero past 2E + d), from the factored
+//                 A11 block in FP64;
+//   k_stc_gather  per 32-row tile: x gathered through the permutation, x_e
+//                 written as BF16 pieces (row-major, K contiguous, zero past
+//                 e), x_d written back in place in FP64 at the delayed
+//                 positions (all reads of a tile precede its writes; tiles own
+//                 disjoint rows), and the Form operands' tails past e zeroed;
+//   k_solve_tc<PS> persistent GEMM x_e Z: 128-row blocks of x_e times
+//                 128-column windows of Z, K = e.  Warp 0: TMA of 128B-swizzled
+//                 K-blocks of both operands through a ring; warp 1: tcgen05.mma
+//                 of the split products (PS pieces: products of total order
+//                 <= PS - 1) into two TMEM accumulators; warps 2-9: epilogue
+//                 (L21 in FP64 into A21 and its BF16 pieces, Y's BF16 pieces,
+//                 x_d += correction in FP64).
+// The products carry the split's error (PS = 2: about 2^-16 relative to
+// |x_e||Z|; PS = 3, what the library uses: close to FP32), which FP64
+// iterative refinement on the complete system removes; pivots are unaffected
+// (they are chosen before).
+// Every mbarrier wait is bounded; on timeout the kernel records CTP_ETIMEOUT,
+// stops, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "ctp_internal.cuh"
+#include "tc_common.cuh"
+
+namespace ctp {
+
+using namespace tc;
+
+namespace {
+
+constexpr int kRowsG = 32;  // rows per gather / prep tile (one per lane)
+constexpr int kWarpsG = 8;
+constexpr int kBM = 128, kBN = 128;  // GEMM tile: 128 rows of x_e by 128 output columns
+constexpr int kZRows = 640;          // rows of the Z^T operand (2 E + d <= p + e + 62 < 640)
+constexpr int kEpiWarps = 8;
+constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
+constexpr uint32_t kPiece = kBM * kBK * 2;  // one 128 x 64 BF16 block (16 KB), both operands
+constexpr size_t kSmemRing = 192 * 1024;
+
+__device__ __forceinline__ void put_pieces(__nv_bfloat16 *dst, int64_t piece_off, int pieces, double v) {
+    // piece k rounds what pieces 0..k-1 left
+    double r = v;
+    for (int pc = 0; pc < pieces; pc++) {
+        const __nv_bfloat16 b = __double2bfloat16(r);
+        dst[pc * piece_off] = b;
+        r -= (double)__bfloat162float(b);
+    }
+}
+
+// 32 consecutive FP32 values of one row as BF16 pieces (16-byte stores; dst
+// 16-byte aligned), each piece rounding what the earlier ones left (exact in
+// FP32: a float minus its BF16 rounding is a float).
+__device__ __forceinline__ void put_pieces32(__nv_bfloat16 *dst, int64_t piece_off, int pieces, const uint32_t (&r)[32]) {
+    float cur[32];
+#pragma unroll
+    for (int x = 0; x < 32; x++) cur[x] = __uint_as_float(r[x]);
+    for (int pc = 0; pc < pieces; pc++) {
+        uint32_t pk[16];
+#pragma unroll
+        for (int x = 0; x < 16; x++) {
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(cur[2 * x]), b1 = __float2bfloat16_rn(cur[2 * x + 1]);
+            cur[2 * x] -= __bfloat162float(b0);
+            cur[2 * x + 1] -= __bfloat162float(b1);
+            pk[x] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+        }
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + pc * piece_off);
+#pragma unroll
+        for (int x = 0; x < 4; x++) d4[x] = make_uint4(pk[4 * x], pk[4 * x + 1], pk[4 * x + 2], pk[4 * x + 3]);
+    }
+}
+
+// The substitution of the FP64 Solve on 32 rows held in xs[k * (kRowsG+1) + lane]
+// (positions k < p): Y = x_e L11^{-T}, x_d -= Y L_d^T.
+__device__ __forceinline__ void substitute(double *xs, const double *__restrict__ A, int p, int64_t lda,
+                                           const int32_t *__restrict__ piv, int e) {
+    constexpr int LDX = kRowsG + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = 0; j < e;) {
+        const int kd = piv[j];
+        if (kd == CTP_PIVKIND_2X2_FIRST) {
+            const double y0 = xs[j * LDX + lane], y1 = xs[(j + 1) * LDX + lane];
+            const double *l0 = A + (int64_t)j * lda, *l1 = A + (int64_t)(j + 1) * lda;
+            for (int k = j + 2 + w; k < p; k += kWarpsG) xs[k * LDX + lane] -= y0 * __ldg(l0 + k) + y1 * __ldg(l1 + k);
+            j += 2;
+        } else {
+            if (kd == CTP_PIVKIND_1X1) {
+                const double y0 = xs[j * LDX + lane];
+                const double *l0 = A + (int64_t)j * lda;
+                for (int k = j + 1 + w; k < p; k += kWarpsG) xs[k * LDX + lane] -= y0 * __ldg(l0 + k);
+            }
+            j += 1;
+        }
+        __syncthreads();
+    }
+}
+
+// L21 entry at position o of a row from its Y entries (D11^{-1} by blocks).
+__device__ __forceinline__ double l21_of(const double *xs, int lane, int o, const int32_t *__restrict__ piv,
+                                         const double *__restrict__ Dinv) {
+    constexpr int LDX = kRowsG + 1;
+    const int kd = piv[o];
+    const double y = xs[o * LDX + lane];
+    if (kd == CTP_PIVKIND_1X1) return y * Dinv[2 * o];
+    if (kd == CTP_PIVKIND_2X2_FIRST) return y * Dinv[2 * o] + xs[(o + 1) * LDX + lane] * Dinv[2 * o + 1];
+    if (kd == CTP_PIVKIND_2X2_SECOND) return xs[(o - 1) * LDX + lane] * Dinv[2 * (o - 1) + 1] + y * Dinv[2 * o];
+    return 0.0;  // zero pivot
+}
+
+// Z^T pieces: Zt[o * Kp + k] for output column o < kZRows, K index k < Kp.
+// CTA t takes the identity rows k = 32 t + lane.
+__global__ void __launch_bounds__(kRowsG * kWarpsG)
+    k_stc_prep(const double *__restrict__ A, int p, int64_t lda, const int32_t *__restrict__ piv,
+               const double *__restrict__ Dinv, const int32_t *__restrict__ nelim_p, __nv_bfloat16 *__restrict__ Zt,
+               int Kp, int64_t zoff, int pieces) {
+    extern __shared__ __align__(16) double xs[];  // [p][kRowsG + 1]
+    constexpr int LDX = kRowsG + 1;
+    const int e = *nelim_p;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = blockIdx.x * kRowsG + lane;
+    for (int j = w; j < p; j += kWarpsG) xs[j * LDX + lane] = (j == k && k < e) ? 1.0 : 0.0;
+    __syncthreads();
+    substitute(xs, A, p, lda, piv, e);
+    const int d = p - e, E = (e + 31) & ~31;
+    for (int o = w; o < kZRows; o += kWarpsG) {
+        double v = 0.0;
+        if (k < e) {
+            if (o < e)
+                v = l21_of(xs, lane, o, piv, Dinv);
+            else if (o >= E && o < E + e)
+                v = xs[(o - E) * LDX + lane];
+            else if (o >= 2 * E && o < 2 * E + d)
+                v = xs[(e + o - 2 * E) * LDX + lane];  // -(U L_d^T)[k, o - 2E]
+        }
+        put_pieces(Zt + (int64_t)o * Kp + k, zoff, pieces, v);
+    }
+}
+
+// Gather of x through perm; x_e to BF16 pieces, x_d back in place (FP64), and
+// the zero tails (K >= e) of the Form's operand pieces.
+__global__ void __launch_bounds__(kRowsG * kWarpsG)
+    k_stc_gather(double *__restrict__ A, int64_t n, int p, int64_t lda, const int32_t *__restrict__ perm,
+                 const int32_t *__restrict__ nelim_p, __nv_bfloat16 *__restrict__ Xb, int64_t xoff, int xpieces,
+                 __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Lb, int64_t foff, int fpieces,
+                 int Kp) {
+    extern __shared__ __align__(16) double xs[];  // [p][kRowsG + 1]
+    constexpr int LDX = kRowsG + 1;
+    const int e = *nelim_p;
+    const int64_t m = n - p;
+    const int64_t row0 = (int64_t)blockIdx.x * kRowsG;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = row0 + lane;
+    const bool valid = row < m;
+    double *A21 = A + p;
+    for (int k = w; k < p; k += kWarpsG) {
+        const int c = perm[k];
+        xs[k * LDX + lane] = valid ? A21[(int64_t)c * lda + row] : 0.0;
+    }
+    __syncthreads();
+    // x_e pieces and the Form operands' zero tails: a warp writes one row at a time
+    for (int rr = w; rr < kRowsG; rr += kWarpsG) {
+        const int64_t rw = row0 + rr;
+        if (rw >= m) break;
+        for (int k = lane; k < Kp; k += 32) {
+            const double v = k < e ? xs[k * LDX + rr] : 0.0;
+            put_pieces(Xb + rw * Kp + k, xoff, xpieces, v);
+            if (k >= e && Lb != nullptr) {
+                put_pieces(Lb + rw * Kp + k, foff, fpieces, 0.0);
+                put_pieces(Wb + rw * Kp + k, foff, fpieces, 0.0);
+            }
+        }
+    }
+    // x_d at the delayed positions, in place (this tile's rows only)
+    if (valid)
+        for (int k = e + w; k < p; k += kWarpsG) A21[(int64_t)k * lda + row] = xs[k * LDX + lane];
+}
+
+struct Bars {
+    unsigned long long full[6], empty[6], acc_full[2], acc_empty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+template <int PS>
+struct SCfg {
+    static constexpr uint32_t Stage = 2 * PS * kPiece;  // PS pieces of x_e, then PS of Z^T
+    static constexpr int Stages = (int)(kSmemRing / Stage) < 6 ? (int)(kSmemRing / Stage) : 6;
+};
+
+template <int PS>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_solve_tc(const __grid_constant__ CUtensorMap mX1, const __grid_constant__ CUtensorMap mX2,
+               const __grid_constant__ CUtensorMap mX3, const __grid_constant__ CUtensorMap mZ1,
+               const __grid_constant__ CUtensorMap mZ2, const __grid_constant__ CUtensorMap mZ3,
+               double *__restrict__ A21, int64_t m, int p, int64_t lda, const int32_t *__restrict__ nelim_p,
+               __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Lb, int64_t foff, int fpieces, int Kp,
+               int32_t *__restrict__ info) {
+    using C = SCfg<PS>;
+    constexpr int NS = C::Stages;
+    const CUtensorMap *mapX[3] = {&mX1, &mX2, &mX3};
+    const CUtensorMap *mapZ[3] = {&mZ1, &mZ2, &mZ3};
+    extern __shared__ unsigned char smraw[];
+    __shared__ Bars bars;
+    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = *nelim_p;
+    const int KB = (e + kBK - 1) / kBK;
+    const int E = (e + 31) & ~31;
+    const int nW = (2 * E + p - e + kBN - 1) / kBN;  // windows of the 2E + d output columns
+    const int64_t nRB = (m + kBM - 1) / kBM;
+    const int64_t ntiles = KB > 0 ? nRB * nW : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; s++) {
+            mbar_init(&bars.full[s], 1);
+            mbar_init(&bars.empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bars.acc_full[b], 1);
+            mbar_init(&bars.acc_empty[b], kEpiWarps);
+        }
+        bars.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&bars.tmem_base, 2 * kBN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_base;
+    const uint32_t idesc = idesc_bf16(kBM, kBN);
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int rb = (int)(t / nW), wdw = (int)(t % nW);
+                for (int kb = 0; kb < KB; kb++) {
+                    if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars.abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&bars.full[stage], C::Stage);
+                    uint8_t *dst = ring + (size_t)stage * C::Stage;
+#pragma unroll
+                    for (int pc = 0; pc < PS; pc++) {
+                        tma_load_2d(dst + pc * kPiece, mapX[pc], kb * kBK, rb * kBM, &bars.full[stage]);
+                        tma_load_2d(dst + (PS + pc) * kPiece, mapZ[pc], kb * kBK, wdw * kBN, &bars.full[stage]);
+                    }
+                    if (++stage == NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) atomicExch(&bars.abort, 1);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, accphase = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars.abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(acc * kBN);
+                for (int kb = 0; kb < KB; kb++) {
+                    if (!mbar_wait(&bars.full[stage], phase, &bars.abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t x0 = smem_u32(ring + (size_t)stage * C::Stage);
+                    const uint32_t z0 = x0 + PS * kPiece;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / kUmmaK; kk++) {
+                        // pieces i of x_e and j of Z^T with i + j <= PS - 1
+                        const uint64_t a1 = sdesc(x0 + kk * 32), b1 = sdesc(z0 + kk * 32);
+                        umma_bf16(dt, a1, b1, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        const uint64_t a2 = sdesc(x0 + kPiece + kk * 32), b2 = sdesc(z0 + kPiece + kk * 32);
+                        umma_bf16(dt, a1, b2, idesc, 1u);
+                        umma_bf16(dt, a2, b1, idesc, 1u);
+                        if (PS >= 3) {
+                            umma_bf16(dt, a1, sdesc(z0 + 2 * kPiece + kk * 32), idesc, 1u);
+                            umma_bf16(dt, sdesc(x0 + 2 * kPiece + kk * 32), b1, idesc, 1u);
+                            umma_bf16(dt, a2, b2, idesc, 1u);
+                        }
+                    }
+                    umma_commit(&bars.empty[stage]);
+                    if (++stage == NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&bars.acc_full[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    accphase ^= 1u;
+                }
+            }
+            if (!ok) atomicExch(&bars.abort, 1);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9
+        const int q = warp & 3;            // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;  // which 64 columns of the window
+        const int d = p - e;
+        int acc = 0;
+        uint32_t accphase = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int rb = (int)(t / nW), wdw = (int)(t % nW);
+            if (!mbar_wait(&bars.acc_full[acc], accphase, &bars.abort)) {
+                if (lane == 0) atomicExch(&bars.abort, 1);
+                break;
+            }
+            tc_fence_after();
+            const int64_t i = (int64_t)rb * kBM + q * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < 64; c += 32) {
+                uint32_t r[32];
+                tmem_ld32_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + half * 64 + c), r);
+                tmem_wait_ld();
+                if (i >= m) continue;
+                const int o0 = wdw * kBN + half * 64 + c;  // a multiple of 32: one block of Z
+                if (o0 < E) {
+                    // L21: FP64 at positions < e; pieces over the whole slice (zero past e)
+                    double *dst = A21 + (int64_t)o0 * lda + i;
+#pragma unroll
+                    for (int x = 0; x < 32; x++)
+                        if (o0 + x < e) dst[(int64_t)x * lda] = (double)__uint_as_float(r[x]);
+                    put_pieces32(Lb + i * Kp + o0, foff, fpieces, r);
+                } else if (o0 < 2 * E) {
+                    put_pieces32(Wb + i * Kp + (o0 - E), foff, fpieces, r);  // Y = W21
+                } else {
+                    // x_d += correction at delayed position e + (o - 2E)
+                    const int j0 = o0 - 2 * E;
+                    double *dst = A21 + (int64_t)(e + j0) * lda + i;
+#pragma unroll
+                    for (int x = 0; x < 32; x++)
+                        if (j0 + x < d) dst[(int64_t)x * lda] += (double)__uint_as_float(r[x]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.acc_empty[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                accphase ^= 1u;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && bars.abort) atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * kBN);
+    }
+}
+
+template <int PS>
+cudaError_t launch_gemm(int grid, const CUtensorMap (&mX)[3], const CUtensorMap (&mZ)[3], double *A21, int64_t m,
+                        int p, int64_t lda, const int32_t *nelim, void *Wb, void *Lb, int64_t foff, int fpieces,
+                        int Kp, int32_t *info, cudaStream_t st) {
+    const size_t smem = kSmemRing + 1024;
+    cudaError_t err = cudaFuncSetAttribute(k_solve_tc<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_solve_tc<PS><<<grid, kThreadsTC, smem, st>>>(mX[0], mX[1], mX[2], mZ[0], mZ[1], mZ[2], A21, m, p, lda, nelim,
+                                                   (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb, foff, fpieces, Kp,
+                                                   info);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t solve_tc_ws_bytes(int64_t m, int p, int spieces) {
+    const int Kp = form_tc_kpad(p);
+    return align256(2 * (size_t)m * Kp * spieces) + align256(2 * (size_t)kZRows * Kp * spieces);
+}
+
+cudaError_t launch_solve_tc(double *A, int64_t n, int p, int64_t lda, const int32_t *perm, const int32_t *piv,
+                            const double *Dinv, const int32_t *nelim, void *ws, int spieces, void *Wb, void *Lb,
+                            int64_t foff, int fpieces, int32_t *info, int num_sms, cudaStream_t st) {
+    const int64_t m = n - p;
+    if (m <= 0) return cudaSuccess;
+    if ((spieces != 2 && spieces != 3) || p < 1 || p > kMaxP) return cudaErrorInvalidValue;
+    const int Kp = form_tc_kpad(p);
+    __nv_bfloat16 *Xb = (__nv_bfloat16 *)ws;
+    __nv_bfloat16 *Zt = (__nv_bfloat16 *)((char *)ws + align256(2 * (size_t)m * Kp * spieces));
+    const int64_t xoff = m * Kp, zoff = (int64_t)kZRows * Kp;
+    const size_t smem = sizeof(double) * (size_t)p * (kRowsG + 1);
+    cudaError_t err = cudaFuncSetAttribute(k_stc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_stc_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_stc_prep<<<Kp / kRowsG, kRowsG * kWarpsG, smem, st>>>(A, p, lda, piv, Dinv, nelim, Zt, Kp, zoff, spieces);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_stc_gather<<<(unsigned)((m + kRowsG - 1) / kRowsG), kRowsG * kWarpsG, smem, st>>>(
+        A, n, p, lda, perm, nelim, Xb, xoff, spieces, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb, foff, fpieces, Kp);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    CUtensorMap mX[3], mZ[3];
+    for (int pc = 0; pc < 3; pc++) {
+        const int q = pc < spieces ? pc : 0;  // unused pieces: valid copies of the first
+        if (!make_map_bf16(&mX[pc], Xb + q * xoff, m, Kp, kBM) ||
+            !make_map_bf16(&mZ[pc], Zt + q * zoff, kZRows, Kp, kBN))
+            return cudaErrorInvalidValue;
+    }
+    const int64_t tiles_max = ((m + kBM - 1) / kBM) * (kZRows / kBN);
+    const int grid = (int)(tiles_max < num_sms ? tiles_max : num_sms);
+    if (spieces == 2)
+        return launch_gemm<2>(grid, mX, mZ, A + p, m, p, lda, nelim, Wb, Lb, foff, fpieces, Kp, info, st);
+    return launch_gemm<3>(grid, mX, mZ, A + p, m, p, lda, nelim, Wb, Lb, foff, fpieces, Kp, info, st);
+}
+
+}  // namespace ctp

@@ -25,6 +25,7 @@ STATUS = {0: "CTP_OK", 1: "CTP_EINVAL", 2: "CTP_ENOMEM", 3: "CTP_ECUDA", 4: "CTP
           5: "CTP_ETIMEOUT", 6: "CTP_ECAPACITY", 7: "CTP_EUNSUPPORTED"}
 PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3}
 PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
+SOLVE = {"fp64": 0, "tc": 1}
 SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4, "fp32_tiled": 5,
          "fp64_sub": 6}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
@@ -47,11 +48,11 @@ WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
 class Options(ctypes.Structure):
     _fields_ = [("u", ctypes.c_double), ("small", ctypes.c_double), ("pivot", ctypes.c_int32),
-                ("prec", ctypes.c_int32), ("smode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("prec", ctypes.c_int32), ("smode", ctypes.c_int32), ("solve", ctypes.c_int32)]
 
 
-def options(u=0.01, small=1e-20, pivot="strict", prec="fp64", smode="none"):
-    return Options(u, small, PIVOT[pivot], PREC[prec], SMODE[smode], 0)
+def options(u=0.01, small=1e-20, pivot="strict", prec="fp64", smode="none", solve="fp64"):
+    return Options(u, small, PIVOT[pivot], PREC[prec], SMODE[smode], SOLVE[solve])
 
 
 class Front(ctypes.Structure):
