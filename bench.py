@@ -243,12 +243,19 @@ def ncu_traffic(name, m):
     return rec["bytes_per_unit"] * units
 
 
-def kernel_roofline(name, launches, ms, a, e, peaks):
+def kernel_roofline(name, launches, ms, a, e, peaks, prec="fp64"):
     """Algorithmic work of one launch of `name` and its roofline."""
     n, p = a.n, a.p
     m = n - p
     t = ms / launches / 1e3
-    if name in ("compress_strict", "compress_relaxed"):
+    if name == "solve_tc":
+        # A21 read and overwritten in FP64, the Form's BF16 operand pieces (W21
+        # and L21) written; the split copy of x_e is the kernel's own scratch
+        fp = {"bf16": 1, "bf16x3": 2, "bf16x6": 3}.get(prec, 1)
+        work = 16.0 * m * p + 2 * fp * 2.0 * m * ((p + 63) // 64 * 64)
+        bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
+        achieved = work / t / 1e9
+    elif name in ("compress_strict", "compress_relaxed"):
         work = 8.0 * m * p
         bound, unit, peak, src = "hbm", "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
         achieved = work / t / 1e9
@@ -292,14 +299,14 @@ def kernel_roofline(name, launches, ms, a, e, peaks):
             "work_per_launch": work, "launch_ms": ms / launches}
 
 
-def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, world, dist):
+def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, world, dist, solve="fp64"):
     """Time `steps` factorizations (after `warmup`), each on a fresh input copy.
     Returns a dict of the measured quantities."""
     import torch
     from paper_1305_2353_gb300 import ctp
     n, p = a.n, a.p
     m = n - p
-    opt = ctp.options(pivot=a.pivot, smode=smode, prec=prec)
+    opt = ctp.options(pivot=a.pivot, smode=smode, prec=prec, solve=solve)
     A0 = ctp.colmajor(A_host, dev)
     bufs = [A0.clone() for _ in range(warmup + steps)]
     perm = torch.empty(p, dtype=torch.int32, device=dev)
@@ -409,12 +416,13 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
     del S, A0, ws
     torch.cuda.empty_cache()
     top = max(kern.items(), key=lambda kv: kv[1][1])
-    roof = kernel_roofline(top[0], top[1][0], top[1][1], a, e, peaks)
+    roof = kernel_roofline(top[0], top[1][0], top[1][1], a, e, peaks, prec)
+    others = {k: kernel_roofline(k, v[0], v[1], a, e, peaks, prec) for k, v in kern.items() if k != top[0]}
     ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
     ctx.tune_set(ctp.TUNE_FACTOR_G, 0)
     return dict(value=value, ms=ms, e=e, fs=fs, form=form, flops_step=flops_step, kern=kern,
                 clocks=clk, e2e=e2e, roofline=roof, launches=sum(v[0] for v in kern.values()),
-                autotune=tuned)
+                autotune=tuned, rooflines_other={k: v for k, v in others.items() if v is not None})
 
 
 def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
@@ -486,7 +494,7 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()}}
 
 
-def refine_embedded(ctx, dev, A, prec, b, mr="tpp", w_rest=256, seed=0):
+def refine_embedded(ctx, dev, A, prec, b, mr="tpp", w_rest=256, seed=0, solve="fp64"):
     """Embed supernode A in its complete system M (inputs.two_node), factor M on
     the GPU as a chain of fronts (the first the supernode, its Form in `prec`),
     refine with FP64 residuals.  Returns timings, steps and backward errors."""
@@ -500,7 +508,7 @@ def refine_embedded(ctx, dev, A, prec, b, mr="tpp", w_rest=256, seed=0):
     X = torch.zeros_like(B)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ch = ctp.factor_dense(ctx, Md, N, N, p, ctp.options(pivot="strict", prec=prec), w_rest,
+    ch = ctp.factor_dense(ctx, Md, N, N, p, ctp.options(pivot="strict", prec=prec, solve=solve), w_rest,
                           ctp.options(pivot=mr))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -511,7 +519,7 @@ def refine_embedded(ctx, dev, A, prec, b, mr="tpp", w_rest=256, seed=0):
     torch.cuda.synchronize()
     t3 = time.perf_counter()
     kern = ctx.profile_end()
-    out = {"prec_first_front": prec, "fronts": ch.nf, "nelim_first": int(ch.nelim[0]),
+    out = {"prec_first_front": prec, "solve_first_front": solve, "fronts": ch.nf, "nelim_first": int(ch.nelim[0]),
            "factor_ms": (t1 - t0) * 1e3, "refine_ms": (t3 - t2) * 1e3, "corrections": k,
            "bwd_err_history": [float(v) for v in hist.max(axis=1)],
            "kernels": {kk: {"launches": v[0], "ms": v[1]} for kk, v in kern.items()}}
@@ -533,6 +541,9 @@ def measure_system(ctx, dev, inputs):
                        "1 RHS N(0,1), tol 1e-14, <= 10 corrections"}
     for prec in ("fp64", "bf16x3", "bf16"):
         out[prec] = refine_embedded(ctx, dev, A, prec, b)
+    # Solve and Form of the supernode on the tensor cores
+    for prec in ("bf16x3", "bf16x6"):
+        out[prec + "_tc_solve"] = refine_embedded(ctx, dev, A, prec, b, solve="tc")
     return out
 
 
@@ -676,24 +687,27 @@ def run_native(a):
 
     main = measure(a, ctx, dev, A_host, a.prec, a.smode, a.steps, a.warmup,
                    0 if a.no_e2e else a.steps, peaks, world, dist)
-    mixed = mixed_bf16 = None
+    mixed = mixed_bf16 = mixed_fp64_solve = None
     if not a.no_mixed and a.prec == "fp64":
-        def mixed_leg(prec, desc):
+        def mixed_leg(prec, desc, solve="tc"):
             k = max(a.steps, 5)
             mx = measure(a, ctx, dev, A_host, prec, "fp32_tiled", k, max(a.warmup, 3),
-                         0 if a.no_e2e else k, peaks, world, dist)
+                         0 if a.no_e2e else k, peaks, world, dist, solve=solve)
             return {"value": mx["value"], "unit": "GFLOP/s", "ms_per_step": mx["ms"] / k,
-                    "prec": desc, "roofline": mx["roofline"], "e2e": mx["e2e"],
+                    "prec": desc, "solve": solve, "roofline": mx["roofline"],
+                    "rooflines_other": mx["rooflines_other"], "e2e": mx["e2e"],
                     "gpu_launches": mx["launches"],
                     "kernels": {kk: {"launches": v[0], "ms": v[1]} for kk, v in mx["kern"].items()},
                     "clocks": mx["clocks"], "autotune": mx["autotune"]}
-        mixed = mixed_leg("bf16x3", "Form on tensor cores with split operands: hi*hi + hi*lo + "
-                                    "lo*hi (bf16 x bf16 -> f32), S fp32 in 128x128 blocks; the "
-                                    "rest f64 (refines to the FP64 backward error, see "
-                                    "complete_system)")
-        mixed_bf16 = mixed_leg("bf16", "Form on tensor cores: bf16 x bf16 -> f32 (single "
-                                       "product), S fp32 in 128x128 blocks; the rest f64 "
-                                       "(refinement does not reach 1e-12, see complete_system)")
+        mixed = mixed_leg("bf16x3", "Solve and Form on tensor cores: Solve as one product with "
+                                    "three-piece split operands, Form with split operands hi*hi + "
+                                    "hi*lo + lo*hi (bf16 x bf16 -> f32), S fp32 in 128x128 blocks; "
+                                    "compression and pivot search f64 (refines to the FP64 backward "
+                                    "error, see complete_system)")
+        mixed_fp64_solve = mixed_leg("bf16x3", "as mixed, with the Solve in FP64", solve="fp64")
+        mixed_bf16 = mixed_leg("bf16", "Solve on tensor cores (three-piece split), Form on tensor "
+                                       "cores bf16 x bf16 -> f32 (single product), S fp32 in 128x128 "
+                                       "blocks (refinement does not reach 1e-12, see complete_system)")
 
     system = None
     if not a.no_system and rank == 0:
@@ -760,6 +774,7 @@ def run_native(a):
             "clocks": main["clocks"],
             "fp64_dgemm_tflops": peaks["fp64_tflops"],
             "mixed": mixed,
+            "mixed_fp64_solve": mixed_fp64_solve,
             "mixed_bf16": mixed_bf16,
             "complete_system": system,
             "multifrontal": multifrontal,
