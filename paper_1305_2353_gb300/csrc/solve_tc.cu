@@ -58,11 +58,15 @@ constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
 constexpr uint32_t kPiece = kBM * kBK * 2;  // one 128 x 64 BF16 block (16 KB), both operands
 constexpr size_t kSmemRing = 192 * 1024;
 
+// BF16 pieces of v: piece k is the BF16 rounding (through FP32) of what pieces
+// 0..k-1 left, and that remainder is kept exactly in FP64 (v minus a BF16 value
+// within 2^-8 of it is exact), so three pieces hold v to about 2^-26.  (Rounding
+// v to FP32 first would cost 2^-24, which the Solve's cancellation amplifies:
+// measured as slower refinement.)
 __device__ __forceinline__ void put_pieces(__nv_bfloat16 *dst, int64_t piece_off, int pieces, double v) {
-    // piece k rounds what pieces 0..k-1 left
     double r = v;
     for (int pc = 0; pc < pieces; pc++) {
-        const __nv_bfloat16 b = __double2bfloat16(r);
+        const __nv_bfloat16 b = __float2bfloat16_rn((float)r);
         dst[pc * piece_off] = b;
         r -= (double)__bfloat162float(b);
     }
@@ -90,69 +94,85 @@ __device__ __forceinline__ void put_pieces32(__nv_bfloat16 *dst, int64_t piece_o
     }
 }
 
-// The substitution of the FP64 Solve on 32 rows held in xs[k * (kRowsG+1) + lane]
-// (positions k < p): Y = x_e L11^{-T}, x_d -= Y L_d^T.
-__device__ __forceinline__ void substitute(double *xs, const double *__restrict__ A, int p, int64_t lda,
-                                           const int32_t *__restrict__ piv, int e) {
-    constexpr int LDX = kRowsG + 1;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j = 0; j < e;) {
-        const int kd = piv[j];
-        if (kd == CTP_PIVKIND_2X2_FIRST) {
-            const double y0 = xs[j * LDX + lane], y1 = xs[(j + 1) * LDX + lane];
-            const double *l0 = A + (int64_t)j * lda, *l1 = A + (int64_t)(j + 1) * lda;
-            for (int k = j + 2 + w; k < p; k += kWarpsG) xs[k * LDX + lane] -= y0 * __ldg(l0 + k) + y1 * __ldg(l1 + k);
-            j += 2;
-        } else {
-            if (kd == CTP_PIVKIND_1X1) {
-                const double y0 = xs[j * LDX + lane];
-                const double *l0 = A + (int64_t)j * lda;
-                for (int k = j + 1 + w; k < p; k += kWarpsG) xs[k * LDX + lane] -= y0 * __ldg(l0 + k);
-            }
-            j += 1;
-        }
-        __syncthreads();
-    }
-}
-
-// L21 entry at position o of a row from its Y entries (D11^{-1} by blocks).
-__device__ __forceinline__ double l21_of(const double *xs, int lane, int o, const int32_t *__restrict__ piv,
+// L21 entry at position o of a row y (positions contiguous) from its Y entries
+// (D11^{-1} by blocks).
+__device__ __forceinline__ double l21_of(const double *y, int o, const int32_t *piv,
                                          const double *__restrict__ Dinv) {
-    constexpr int LDX = kRowsG + 1;
     const int kd = piv[o];
-    const double y = xs[o * LDX + lane];
-    if (kd == CTP_PIVKIND_1X1) return y * Dinv[2 * o];
-    if (kd == CTP_PIVKIND_2X2_FIRST) return y * Dinv[2 * o] + xs[(o + 1) * LDX + lane] * Dinv[2 * o + 1];
-    if (kd == CTP_PIVKIND_2X2_SECOND) return xs[(o - 1) * LDX + lane] * Dinv[2 * (o - 1) + 1] + y * Dinv[2 * o];
+    if (kd == CTP_PIVKIND_1X1) return y[o] * Dinv[2 * o];
+    if (kd == CTP_PIVKIND_2X2_FIRST) return y[o] * Dinv[2 * o] + y[o + 1] * Dinv[2 * o + 1];
+    if (kd == CTP_PIVKIND_2X2_SECOND) return y[o - 1] * Dinv[2 * (o - 1) + 1] + y[o] * Dinv[2 * o];
     return 0.0;  // zero pivot
 }
 
+constexpr int kPrepRows = 8;  // identity rows (warps) per CTA
+
 // Z^T pieces: Zt[o * Kp + k] for output column o < kZRows, K index k < Kp.
-// CTA t takes the identity rows k = 32 t + lane.
-__global__ void __launch_bounds__(kRowsG * kWarpsG)
+// One warp per identity row k (8 per CTA): the row lives in shared memory, each
+// position updated by one lane, and the warp runs the FP64 Solve's recurrence
+// with only warp barriers (row k is zero before position k, so its pivots
+// start at k's block).  The CTA then writes the Z^T columns of its 8 rows with
+// lanes along k.
+__global__ void __launch_bounds__(32 * kPrepRows)
     k_stc_prep(const double *__restrict__ A, int p, int64_t lda, const int32_t *__restrict__ piv,
                const double *__restrict__ Dinv, const int32_t *__restrict__ nelim_p, __nv_bfloat16 *__restrict__ Zt,
                int Kp, int64_t zoff, int pieces) {
-    extern __shared__ __align__(16) double xs[];  // [p][kRowsG + 1]
-    constexpr int LDX = kRowsG + 1;
+    __shared__ double rows[kPrepRows][kMaxP];
     const int e = *nelim_p;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int k = blockIdx.x * kRowsG + lane;
-    for (int j = w; j < p; j += kWarpsG) xs[j * LDX + lane] = (j == k && k < e) ? 1.0 : 0.0;
+    const int k0 = blockIdx.x * kPrepRows, k = k0 + w;
+    __shared__ int spiv[kMaxP];
+    double *x = rows[w];  // this warp's row; position q is updated by lane q % 32 only
+    for (int q = threadIdx.x; q < p; q += blockDim.x) spiv[q] = piv[q];
+    for (int q = lane; q < kMaxP; q += 32) x[q] = (q == k && k < e) ? 1.0 : 0.0;
     __syncthreads();
-    substitute(xs, A, p, lda, piv, e);
-    const int d = p - e, E = (e + 31) & ~31;
-    for (int o = w; o < kZRows; o += kWarpsG) {
-        double v = 0.0;
-        if (k < e) {
-            if (o < e)
-                v = l21_of(xs, lane, o, piv, Dinv);
-            else if (o >= E && o < E + e)
-                v = xs[(o - E) * LDX + lane];
-            else if (o >= 2 * E && o < 2 * E + d)
-                v = xs[(e + o - 2 * E) * LDX + lane];  // -(U L_d^T)[k, o - 2E]
+    if (k < e) {
+        int j = (k > 0 && spiv[k] == CTP_PIVKIND_2X2_SECOND) ? k - 1 : k;
+        while (j < e) {
+            const int kd = spiv[j];
+            const double y0 = x[j];
+            // all of a lane's positions at once (predicated), so that the loads
+            // of the L column(s) are in flight together
+            if (kd == CTP_PIVKIND_2X2_FIRST) {
+                const double y1 = x[j + 1];
+                const double *l0 = A + (int64_t)j * lda, *l1 = A + (int64_t)(j + 1) * lda;
+#pragma unroll
+                for (int s2 = 0; s2 < kMaxP / 32; s2++) {
+                    const int q = lane + 32 * s2;
+                    if (q >= j + 2 && q < p) x[q] -= y0 * __ldg(l0 + q) + y1 * __ldg(l1 + q);
+                }
+                j += 2;
+            } else {
+                if (kd == CTP_PIVKIND_1X1) {
+                    const double *l0 = A + (int64_t)j * lda;
+#pragma unroll
+                    for (int s2 = 0; s2 < kMaxP / 32; s2++) {
+                        const int q = lane + 32 * s2;
+                        if (q > j && q < p) x[q] -= y0 * __ldg(l0 + q);
+                    }
+                }
+                j += 1;  // zero pivots have an all-zero L column
+            }
+            __syncwarp();  // the next pivot's y is written by another lane
         }
-        put_pieces(Zt + (int64_t)o * Kp + k, zoff, pieces, v);
+    }
+    __syncthreads();
+    // Z^T columns of these 8 rows: thread (o, r) writes Zt[o * Kp + k0 + r]
+    const int d = p - e, E = (e + 31) & ~31;
+    for (int idx = threadIdx.x; idx < kZRows * kPrepRows; idx += blockDim.x) {
+        const int o = idx / kPrepRows, r = idx % kPrepRows, kr = k0 + r;
+        if (kr >= Kp) continue;
+        const double *y = rows[r];
+        double v = 0.0;
+        if (kr < e) {
+            if (o < e)
+                v = l21_of(y, o, spiv, Dinv);
+            else if (o >= E && o < E + e)
+                v = y[o - E];
+            else if (o >= 2 * E && o < 2 * E + d)
+                v = y[e + o - 2 * E];  // -(U L_d^T)[k, o - 2E]
+        }
+        put_pieces(Zt + (int64_t)o * Kp + kr, zoff, pieces, v);
     }
 }
 
@@ -415,11 +435,9 @@ cudaError_t launch_solve_tc(double *A, int64_t n, int p, int64_t lda, const int3
     __nv_bfloat16 *Zt = (__nv_bfloat16 *)((char *)ws + align256(2 * (size_t)m * Kp * spieces));
     const int64_t xoff = m * Kp, zoff = (int64_t)kZRows * Kp;
     const size_t smem = sizeof(double) * (size_t)p * (kRowsG + 1);
-    cudaError_t err = cudaFuncSetAttribute(k_stc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_stc_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stc_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_stc_prep<<<Kp / kRowsG, kRowsG * kWarpsG, smem, st>>>(A, p, lda, piv, Dinv, nelim, Zt, Kp, zoff, spieces);
+    k_stc_prep<<<Kp / kPrepRows, 32 * kPrepRows, 0, st>>>(A, p, lda, piv, Dinv, nelim, Zt, Kp, zoff, spieces);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     k_stc_gather<<<(unsigned)((m + kRowsG - 1) / kRowsG), kRowsG * kWarpsG, smem, st>>>(
