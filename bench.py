@@ -438,14 +438,12 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
     # the library's autotuner: cluster budget of the pivot search and the
     # tensor-core Form's tile walk, timed on this batch (untimed here)
     names = {0: "auto", 1: "round_robin", 2: "chunks"}
-    wnames = {0: "win1", 1: "winfull"}
-    kbs = [100, 160, 220]
+    kbs = [64, 100, 160, 220]
     walks = [2, 1] if prec != "fp64" else [0]
-    cand = [(k, w, x) for k in kbs for w in walks for x in (0, 1)]
-    tms, best = b.autotune([ctp.TUNE_BATCH_SMEM_KB, ctp.TUNE_FORM_WALK, ctp.TUNE_FACTOR_WINDOW], cand)
+    cand = [(k, w) for k in kbs for w in walks]
+    tms, best = b.autotune([ctp.TUNE_BATCH_SMEM_KB, ctp.TUNE_FORM_WALK], cand)
     tuned = {"smem_kb": cand[best][0], "form_walk": names[cand[best][1]],
-             "factor_window": wnames[cand[best][2]],
-             "candidates_ms": {f"{k}KB/{names[w]}/{wnames[x]}": float(t) for (k, w, x), t in zip(cand, tms)}}
+             "candidates_ms": {f"{k}KB/{names[w]}": float(t) for (k, w), t in zip(cand, tms)}}
     b.run()
     torch.cuda.synchronize()
     # kernel split from one profiled run outside the graph
@@ -486,7 +484,6 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
     del g, b
     ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 200)
     ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
-    ctx.tune_set(ctp.TUNE_FACTOR_WINDOW, 0)
     import gc
     gc.collect()
     torch.cuda.empty_cache()

@@ -505,20 +505,11 @@ ctp_status ctp_chain_destroy(ctp_chain *chain);
  *   clusters).  Read when a batch plan is created.
  * CTP_TUNE_FACTOR_G: cluster width of the single-supernode pivot search
  *   (0 = by p, the default; else 1, 2, 4, 8 or 16, widened when the columns do
- *   not fit on chip).
- * CTP_TUNE_FACTOR_WINDOW: how many candidates a test round of the pivot search
- *   (single supernode and batch) takes after an accepted pivot: 0 (default)
- *   one, doubling after each round in which every candidate failed; 1 all the
- *   round can hold (8 per CTA of the cluster).  A rejected candidate changes
- *   nothing, so both give the sequential listing's pivots; the full window
- *   saves rounds where most candidates fail (strict compression on N(0,1)
- *   fronts) and spends idle warps where the first candidate passes.  Read when
- *   a batch plan is created. */
+ *   not fit on chip). */
 typedef enum {
     CTP_TUNE_FORM_WALK = 0,
     CTP_TUNE_BATCH_SMEM_KB = 1,
-    CTP_TUNE_FACTOR_G = 2,
-    CTP_TUNE_FACTOR_WINDOW = 3
+    CTP_TUNE_FACTOR_G = 2
 } ctp_tune_key;
 typedef enum {
     CTP_WALK_AUTO = 0,

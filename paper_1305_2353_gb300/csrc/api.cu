@@ -24,7 +24,6 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
 namespace ctp {
 
 int ctx_batch_smem_kb(const ctp_ctx *ctx) { return ctx->batch_smem_kb; }
-int ctx_factor_window(const ctp_ctx *ctx) { return ctx->factor_window; }
 
 WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     WsLayout L;
@@ -80,7 +79,6 @@ ctp_status ctp_create(ctp_ctx **ctx, int32_t device) {
     c->form_walk = CTP_WALK_AUTO;
     c->batch_smem_kb = 200;
     c->factor_g = 0;
-    c->factor_window = 0;
     c->profiling = false;
     c->nrec = 0;
     c->events_made = false;
@@ -124,11 +122,6 @@ ctp_status ctp_tune_set(ctp_ctx *ctx, int32_t key, int32_t value) {
         ctx->factor_g = value;
         return CTP_OK;
     }
-    if (key == CTP_TUNE_FACTOR_WINDOW) {
-        if (value != 0 && value != 1) return CTP_EINVAL;
-        ctx->factor_window = value;
-        return CTP_OK;
-    }
     return CTP_EINVAL;
 }
 
@@ -140,8 +133,6 @@ ctp_status ctp_tune_get(const ctp_ctx *ctx, int32_t key, int32_t *value) {
         *value = ctx->batch_smem_kb;
     else if (key == CTP_TUNE_FACTOR_G)
         *value = ctx->factor_g;
-    else if (key == CTP_TUNE_FACTOR_WINDOW)
-        *value = ctx->factor_window;
     else
         return CTP_EINVAL;
     return CTP_OK;
@@ -262,7 +253,6 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     fa.D = D;
     fa.Dinv = Dinv;
     fa.info = info;
-    fa.win_full = ctx->factor_window;
     if (opt->pivot == CTP_PIV_STRICT) {
         unsigned long long *keys = (unsigned long long *)(ws + L.C);
         CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));

@@ -308,7 +308,6 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     off += align256(tc ? 2 * copies * (size_t)row0 * kBatchKp : 0);
     P->bo.lo_off = pieces > 1 ? row0 * kBatchKp : 0;
     P->bo.pieces = pieces;
-    P->bo.win_full = ctx_factor_window(ctx);
     P->total = off;
     // section offsets are relative to the sections base: shift them to the workspace base
     for (int f = 0; f < nb; f++) tab[f].ws += (int64_t)P->off_sections;

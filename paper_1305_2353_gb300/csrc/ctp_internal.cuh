@@ -30,7 +30,6 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms);
 int ctx_batch_smem_kb(const ctp_ctx *ctx);  // CTP_TUNE_BATCH_SMEM_KB of a context
-int ctx_factor_window(const ctp_ctx *ctx);  // CTP_TUNE_FACTOR_WINDOW of a context
 // BF16 pieces per operand of the tensor-core Form for a precision (0: FP64 Form)
 inline int prec_pieces(int prec) {
     return prec == CTP_BF16 ? 1 : (prec == CTP_BF16X3 ? 2 : (prec == CTP_BF16X6 ? 3 : 0));
@@ -61,7 +60,6 @@ struct FactorArgs {
     int32_t *perm, *piv, *nelim;
     double *D, *Dinv;
     int32_t *info;
-    int win_full;       // 1: full test window after an acceptance (CTP_TUNE_FACTOR_WINDOW)
 };
 cudaError_t launch_factor_cluster(const FactorArgs &a, int G /* 0: by p */, cudaStream_t st);
 
@@ -102,7 +100,6 @@ struct BatchOpts {
     int smode, prec;
     int64_t lo_off;  // elements between the BF16 pieces of the operand copies
     int pieces;      // BF16 pieces per operand (1: plain; 2, 3: split)
-    int win_full;    // pivot search test window (CTP_TUNE_FACTOR_WINDOW)
 };
 cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                 const int *list, int count, int G, int pmax, BatchOpts o,

@@ -21,7 +21,6 @@ struct ctp_ctx {
     int form_walk;      // CTP_TUNE_FORM_WALK
     int batch_smem_kb;  // CTP_TUNE_BATCH_SMEM_KB
     int factor_g;       // CTP_TUNE_FACTOR_G
-    int factor_window;  // CTP_TUNE_FACTOR_WINDOW
     bool profiling;
     int nrec;
     int rec_id[ctp::kMaxRec];

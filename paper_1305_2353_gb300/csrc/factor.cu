@@ -264,9 +264,8 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
 
     const double u = a.u, small = a.small;
     int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, round = 0;
+    int win = 1;                  // candidates tested in the next round
     const int win_max = kNW * G;  // no CTA owns more than kNW of them
-    const int win0 = a.win_full ? win_max : 1;
-    int win = win0;               // candidates tested in the next round
     for (;;) {
         if (nelim >= p) break;
         while (m < p && !sh.live[m]) m++;
@@ -280,9 +279,9 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
         round++;
         // ---------------- test round: the first `win` live candidates >= m
         // (cluster-wide order); each CTA tests the ones it owns, one per warp.
-        // The window is 1 after an acceptance (or full, CTP_TUNE_FACTOR_WINDOW)
-        // and doubles after a round with no pass, so accepted-first candidates
-        // cost a single test and runs of rejections are tested in parallel.
+        // The window is 1 after an acceptance and doubles after a round with no
+        // pass, so accepted-first candidates cost a single test and runs of
+        // rejections are tested in parallel.
         if (tid < nmask) sh.mask[buf][tid] = 0u;
         if (tid == 0) {
             // the window ends at the first live column that would exceed `win`
@@ -352,7 +351,7 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
             win = win * 2 < win_max ? win * 2 : win_max;
             continue;
         }
-        win = win0;
+        win = 1;
         const Decision dv = sh.cur;
         if (dv.kind == DEC_ZERO) {
             if (tid == 0) {
@@ -567,7 +566,6 @@ __global__ void __launch_bounds__(kT)
     a.D = fr.D;
     a.Dinv = reinterpret_cast<double *>(base + sec.Dinv);
     a.info = reinterpret_cast<int32_t *>(base + sec.info);
-    a.win_full = o.win_full;
     factor_cluster_body(a, G);
 }
 

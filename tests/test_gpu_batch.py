@@ -140,24 +140,3 @@ def test_batch_cluster_budget_same_results(ctx, kb):
         p = A.shape[1]
         compare(O.factor(A, p, "strict"), b.result(k), p, A)
 
-
-@pytest.mark.parametrize("pivot", ["strict", "restricted"])
-def test_batch_full_test_window_same_results(ctx, pivot):
-    """CTP_TUNE_FACTOR_WINDOW = 1 (every test round takes all the candidates
-    it can hold) gives the oracle's pivots, front by front: a rejected
-    candidate changes nothing, so the lowest passing candidate of any window is
-    the listing's next pivot."""
-    from paper_1305_2353_gb300 import ctp
-    fr = _fronts(60, seed=9)
-    ctx.tune_set(ctp.TUNE_FACTOR_WINDOW, 1)
-    try:
-        b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr], ctp.options(pivot=pivot))
-    finally:
-        ctx.tune_set(ctp.TUNE_FACTOR_WINDOW, 0)
-    b.run()
-    torch.cuda.synchronize()
-    assert np.all(b.flags() == 0)
-    for k, A in enumerate(fr):
-        p = A.shape[1]
-        ref = O.factor(A, p, pivot, log_cap=200000)
-        compare(ref, b.result(k), p, A)

@@ -437,22 +437,6 @@ def test_supernode_autotune(ctx):
     assert np.array_equal(got["perm"], ref["perm"])
 
 
-@pytest.mark.parametrize("pivot", ["strict", "relaxed", "restricted"])
-@pytest.mark.parametrize("n,p", [(3000, 200), (800, 64), (5000, 256)])
-def test_factor_full_test_window_same_pivots(ctx, pivot, n, p):
-    """CTP_TUNE_FACTOR_WINDOW = 1: every test round takes all the candidates it
-    can hold; the pivots are still the oracle's."""
-    from paper_1305_2353_gb300 import ctp
-    A = _tough(n, p, 21)
-    ctx.tune_set(ctp.TUNE_FACTOR_WINDOW, 1)
-    try:
-        got = run_gpu(ctx, A, p, pivot)
-    finally:
-        ctx.tune_set(ctp.TUNE_FACTOR_WINDOW, 0)
-    ref = O.factor(A, p, pivot, log_cap=200000)
-    compare(ref, got, p, A)
-
-
 @pytest.mark.parametrize("G", [1, 4, 8])
 def test_factor_cluster_width_same_pivots(ctx, G):
     """Any cluster width of the pivot search gives the oracle's pivots."""
