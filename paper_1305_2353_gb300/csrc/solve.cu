@@ -74,13 +74,16 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
     }
 
     // BF16 copy of Y = W21 for the tensor-core Form: row-major, K contiguous,
-    // zero beyond e (a warp writes one row at a time: coalesced)
+    // zero from e to the end of e's last 64-wide K block (the Form reads no
+    // further; a batch's rows are 256 wide whatever the front's p), a warp
+    // writing one row at a time (coalesced)
+    const int Kz = min(Kp, (e + 63) / 64 * 64);
     if (Wb != nullptr) {
         for (int rr = w; rr < kRows; rr += kWarps) {
             const int64_t rw = row0 + rr;
             if (rw >= m) break;
             __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Wb + (brow0 + rw) * Kp);
-            for (int k2 = lane; k2 < Kp / 2; k2 += 32) {
+            for (int k2 = lane; k2 < Kz / 2; k2 += 32) {
                 const int k = 2 * k2;
                 const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
                 const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
@@ -144,7 +147,7 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
             const int64_t rw = row0 + rr;
             if (rw >= m) break;
             __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Lb + (brow0 + rw) * Kp);
-            for (int k2 = lane; k2 < Kp / 2; k2 += 32) {
+            for (int k2 = lane; k2 < Kz / 2; k2 += 32) {
                 const int k = 2 * k2;
                 const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
                 const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
