@@ -63,12 +63,23 @@ constexpr size_t kSmemRing = 192 * 1024;
 // within 2^-8 of it is exact), so three pieces hold v to about 2^-26.  (Rounding
 // v to FP32 first would cost 2^-24, which the Solve's cancellation amplifies:
 // measured as slower refinement.)
+// A BF16 value as a double, built from its bits (no FP64 operation) when it is
+// normal; zero, subnormal, Inf and NaN take the conversion.
+__device__ __forceinline__ double bf16_as_double(__nv_bfloat16 b) {
+    const unsigned int h = __bfloat16_as_ushort(b);
+    const unsigned int ex = (h >> 7) & 0xFFu;
+    if (ex == 0u || ex == 0xFFu) return (double)__bfloat162float(b);
+    const unsigned long long bits = ((unsigned long long)(h >> 15) << 63) |
+                                    ((unsigned long long)(ex - 127u + 1023u) << 52) |
+                                    ((unsigned long long)(h & 0x7Fu) << 45);
+    return __longlong_as_double((long long)bits);
+}
 __device__ __forceinline__ void put_pieces(__nv_bfloat16 *dst, int64_t piece_off, int pieces, double v) {
     double r = v;
     for (int pc = 0; pc < pieces; pc++) {
         const __nv_bfloat16 b = __float2bfloat16_rn((float)r);
         dst[pc * piece_off] = b;
-        r -= (double)__bfloat162float(b);
+        if (pc + 1 < pieces) r -= bf16_as_double(b);
     }
 }
 
@@ -105,14 +116,13 @@ __device__ __forceinline__ double l21_of(const double *y, int o, const int32_t *
     return 0.0;  // zero pivot
 }
 
-constexpr int kPrepRows = 8;  // identity rows (warps) per CTA
+constexpr int kPrepRows = 1;  // identity rows (warps) per CTA: one, so the rows spread over the SMs' FP64 pipes
 
 // Z^T pieces: Zt[o * Kp + k] for output column o < kZRows, K index k < Kp.
-// One warp per identity row k (8 per CTA): the row lives in shared memory, each
+// One warp per identity row k (a CTA per row): the row lives in shared memory, each
 // position updated by one lane, and the warp runs the FP64 Solve's recurrence
 // with only warp barriers (row k is zero before position k, so its pivots
-// start at k's block).  The CTA then writes the Z^T columns of its 8 rows with
-// lanes along k.
+// start at k's block).  The CTA then writes the Z^T column of its row.
 __global__ void __launch_bounds__(32 * kPrepRows)
     k_stc_prep(const double *__restrict__ A, int p, int64_t lda, const int32_t *__restrict__ piv,
                const double *__restrict__ Dinv, const int32_t *__restrict__ nelim_p, __nv_bfloat16 *__restrict__ Zt,
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(32 * kPrepRows)
         }
     }
     __syncthreads();
-    // Z^T columns of these 8 rows: thread (o, r) writes Zt[o * Kp + k0 + r]
+    // Z^T columns of these rows: thread (o, r) writes Zt[o * Kp + k0 + r]
     const int d = p - e, E = (e + 31) & ~31;
     for (int idx = threadIdx.x; idx < kZRows * kPrepRows; idx += blockDim.x) {
         const int o = idx / kPrepRows, r = idx % kPrepRows, kr = k0 + r;
