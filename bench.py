@@ -43,17 +43,22 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic per launch from ncu captures (profiles/), valid only for the
 # kernel source they were taken on (sha1 of the .cu file).
 # Measured at a smaller size than the bench's and scaled by the units one launch
-# processes (the traffic of these kernels is the S they write, proportional to
-# the number of S entries): see profiles/ for the captures.
+# processes (the traffic of the Forms is the S they write, proportional to the
+# number of S entries; the Solve's is proportional to the rows of A21): see
+# profiles/ for the captures.
 NCU_TRAFFIC = {
-    # ncu --set full, n=20000 p=256 relaxed, S FP64 lower-packed: 146.48 MB read +
-    # 1516.63 MB written for m(m+1)/2 = 194,921,640 entries
-    "form_fp64": {"file": "form.cu", "sha1": "7f2c353064294c79b58273da8095be00973639ff",
-                  "unit": "packed_entry", "bytes_per_unit": (146.477568e6 + 1516.633e6) / 194921640},
+    # ncu --set full, n=20000 p=256 relaxed, S FP64 lower-packed: 140.90 MB read +
+    # 1512.81 MB written for m(m+1)/2 = 194,921,640 entries
+    "form_fp64": {"file": "form.cu", "sha1": "042a4c6f69b873290d71454b2f87dbb210410b01",
+                  "unit": "packed_entry", "bytes_per_unit": (140.898048e6 + 1512.805e6) / 194921640},
     # ncu --set full, n=40000 p=256 relaxed, split BF16, S FP32 in 128x128 blocks:
-    # 228.97 MB read + 3118.61 MB written for 48,516 blocks of 16,384 entries
-    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "52739ecaf566efb8e08328d94973028f56c7f359",
-                       "unit": "tiled_entry", "bytes_per_unit": (228.966912e6 + 3118.611e6) / (48516 * 16384)},
+    # 165.73 MB read + 3118.06 MB written for 48,516 blocks of 16,384 entries
+    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "33e0e4154a47663e76edc12346e4a57da6e7108e",
+                       "unit": "tiled_entry", "bytes_per_unit": (165.732608e6 + 3118.057e6) / (48516 * 16384)},
+    # ncu --set full, n=40000 p=256 relaxed, tensor-core Solve before a split-BF16
+    # Form (prep + gather + GEMM): 144.93 MB read + 124.22 MB written for 39,744 rows
+    "solve_tc": {"file": "solve_tc.cu", "sha1": "8b2073a626b858775d57974a529316deb6caa083", "prec": "bf16x3",
+                 "unit": "row", "bytes_per_unit": (144.928256e6 + 124.223e6) / 39744},
 }
 
 
@@ -79,6 +84,8 @@ def parse_args():
                     choices=["none", "fp32", "fp64", "fp32_packed", "fp64_packed", "fp32_tiled"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16", "bf16x3", "bf16x6"],
                     help="Form arithmetic: FP64, or BF16 tensor cores with FP32 accumulation")
+    ap.add_argument("--solve", default="fp64", choices=["fp64", "tc"],
+                    help="Solve of the main leg: FP64, or on the tensor cores (with a tensor-core Form)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -228,11 +235,12 @@ def fp64_peak_tflops(torch, dev):
     return 2 * N ** 3 / best / 1e12
 
 
-def ncu_traffic(name, m):
+def ncu_traffic(name, m, prec=None):
     """DRAM bytes of one launch of `name` on m rows, from the ncu record, or None
-    when there is none or the kernel's source changed since it was taken."""
+    when there is none, it was taken at another precision, or the kernel's
+    source changed since it was taken."""
     rec = NCU_TRAFFIC.get(name)
-    if rec is None:
+    if rec is None or (prec is not None and rec.get("prec", prec) != prec):
         return None
     src_file = os.path.join(ROOT, "paper_1305_2353_gb300", "csrc", rec["file"])
     if hashlib.sha1(open(src_file, "rb").read()).hexdigest() != rec["sha1"]:
@@ -272,7 +280,7 @@ def kernel_roofline(name, launches, ms, a, e, peaks, prec="fp64"):
         achieved = work / t / 1e9
         tensor = form / t / 1e12
         out = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-               "frac": achieved / peak, "traffic": ncu_traffic(name, m), "peak_source": src,
+               "frac": achieved / peak, "traffic": ncu_traffic(name, m, prec), "peak_source": src,
                "work_per_launch": work, "launch_ms": ms / launches,
                "tensor_tflops": tensor,
                "tensor_frac_of_bf16_sustained": tensor / peaks.get("bf16_tflops_sustained", 1715.6)}
@@ -293,7 +301,7 @@ def kernel_roofline(name, launches, ms, a, e, peaks, prec="fp64"):
         achieved = work / t / 1e12
     else:
         return None
-    traffic = ncu_traffic(name, m)
+    traffic = ncu_traffic(name, m, prec)
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic, "peak_source": src,
             "work_per_launch": work, "launch_ms": ms / launches}
@@ -686,7 +694,7 @@ def run_native(a):
     A_host = inputs.single_large(a.seed, n=a.n, p=a.p)
 
     main = measure(a, ctx, dev, A_host, a.prec, a.smode, a.steps, a.warmup,
-                   0 if a.no_e2e else a.steps, peaks, world, dist)
+                   0 if a.no_e2e else a.steps, peaks, world, dist, solve=a.solve)
     mixed = mixed_bf16 = mixed_fp64_solve = None
     if not a.no_mixed and a.prec == "fp64":
         def mixed_leg(prec, desc, solve="tc"):
@@ -761,7 +769,7 @@ def run_native(a):
             "dtype": "f64" if a.prec == "fp64" else "f64 (Form: bf16 x bf16 -> f32)",
             "data": "synthetic",
             "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "u": 0.01,
-                       "pivot": a.pivot, "prec": a.prec, "S": a.smode, "nelim": e,
+                       "pivot": a.pivot, "prec": a.prec, "solve": a.solve, "S": a.smode, "nelim": e,
                        "flops_per_step": main["flops_step"], "factor_solve_flops": main["fs"],
                        "form_flops": main["form"] if a.smode != "none" else 0,
                        "l2": "inputs larger than L2: a distinct 409 MB input copy per step",
