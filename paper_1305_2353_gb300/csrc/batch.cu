@@ -182,16 +182,14 @@ struct ctp_plan {
 };
 
 static int batch_cluster_width(int p, int R, int budget_kb) {
-    // narrowest cluster whose shared memory per CTA (its columns of [A11; C]
-    // plus two pivot columns) fits the budget (100 KB by default, so that two
+    // narrowest cluster whose shared memory per CTA (its columns of [A11; C],
+    // two pivot columns and the update's per-column scalars) fits the budget (100 KB by default, so that two
     // clusters' CTAs share an SM), and never more than the kernel can take
     size_t budget = (size_t)budget_kb * 1024;
     const size_t cap = factor_batch_max_dynamic_smem();
     if (budget > cap) budget = cap;
     for (int G = 1; G <= 16; G <<= 1) {
-        const int ncl = (p + G - 1) / G;
-        const size_t smem = sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R));
-        if (smem <= budget) return G;
+        if (factor_smem_bytes(p, R, G) <= budget) return G;
     }
     return 16;
 }

@@ -35,6 +35,7 @@ inline int prec_pieces(int prec) {
     return prec == CTP_BF16 ? 1 : (prec == CTP_BF16X3 ? 2 : (prec == CTP_BF16X6 ? 3 : 0));
 }
 size_t factor_batch_max_dynamic_smem();     // dynamic shared memory the batched pivot search can take
+size_t factor_smem_bytes(int p, int R, int G);  // dynamic shared memory of a pivot-search CTA
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns cudaError_t of the launch)

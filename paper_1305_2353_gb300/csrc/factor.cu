@@ -68,6 +68,7 @@ struct Shared {
     int cstar, hiall;
     int rowmap[kMaxP];  // nonzero outer rows
     int nz_count;
+    unsigned char nzflag[kMaxP];
 };
 
 // Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
@@ -121,7 +122,8 @@ __device__ __forceinline__ double key_val(unsigned long long k) {
 }
 
 // The tests of Listing 1 for candidate c (one warp): zero test, 2x2 with the
-// partner t, 1x1.  cm is the candidate's column (rows 0..p-1 A11, then outer).
+// partner t, 1x1, from two scans of the column (the partner, then the maxima).
+// cm is the candidate's column (rows 0..p-1 A11, then outer).
 // Column maxima of |a| are taken on the IEEE bit patterns with the sign cleared
 // (integer order = magnitude order), which keeps the scans off the FP64 pipe.
 template <typename ColPtr>
@@ -135,16 +137,6 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     d.m = c;
     d.pad = 0;
     d.d0 = d.d1 = d.d2 = d.i0 = d.i1 = d.i2 = 0.0;
-    unsigned long long v = 0;
-    for (int i = lane; i < LD; i += 32)
-        if (i >= p || live[i]) {
-            const unsigned long long k = akey(cm[i]);
-            v = k > v ? k : v;
-        }
-    if (key_val(warp_max_key(v)) < small) {
-        d.kind = DEC_ZERO;
-        return d;
-    }
     // partner t: largest |a(c, j)| over live j < c, lowest j on ties
     unsigned long long bv = 0;
     int bi = -1;
@@ -166,35 +158,39 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
         }
     }
     const int t = bi;
-    double maxm2 = 0.0;
-    if (t >= 0) {
-        const double *ct = colptr(t);
-        unsigned long long vm = 0, vt = 0;
-        for (int i = lane; i < LD; i += 32)
-            if (i >= p || (live[i] && i != t && i != c)) {
-                const unsigned long long km = akey(cm[i]), kt = akey(ct[i]);
-                vm = km > vm ? km : vm;
+    // one pass over the live rows but t and c: the column maximum of c (and of
+    // the partner's column); the zero test's maximum over every live row of c
+    // adds rows t and c back
+    const double *ct = t >= 0 ? colptr(t) : cm;
+    unsigned long long vm = 0, vt = 0;
+    for (int i = lane; i < LD; i += 32)
+        if (i >= p || (live[i] && i != t && i != c)) {
+            const unsigned long long km = akey(cm[i]);
+            vm = km > vm ? km : vm;
+            if (t >= 0) {
+                const unsigned long long kt = akey(ct[i]);
                 vt = kt > vt ? kt : vt;
             }
-        maxm2 = key_val(warp_max_key(vm));
+        }
+    vm = warp_max_key(vm);
+    unsigned long long vall = vm > akey(cm[c]) ? vm : akey(cm[c]);
+    if (t >= 0 && akey(cm[t]) > vall) vall = akey(cm[t]);
+    if (key_val(vall) < small) {
+        d.kind = DEC_ZERO;
+        return d;
+    }
+    double maxm1;
+    if (t >= 0) {
+        const double maxm2 = key_val(vm);
         const double maxt = key_val(warp_max_key(vt));
         if (test_2x2(ct[t], cm[t], cm[c], maxt, maxm2, u, small, d)) {
             d.kind = DEC_2X2;
             d.t = t;
             return d;
         }
-    }
-    double maxm1;
-    if (t >= 0) {
         maxm1 = fmax(maxm2, fabs(cm[t]));
     } else {
-        unsigned long long w = 0;
-        for (int i = lane; i < LD; i += 32)
-            if (i >= p || (live[i] && i != c)) {
-                const unsigned long long k = akey(cm[i]);
-                w = k > w ? k : w;
-            }
-        maxm1 = key_val(warp_max_key(w));
+        maxm1 = key_val(vm);  // the live rows but c
     }
     const double amm = cm[c];
     if (fabs(amm) >= __dmul_rn(u, maxm1)) {
@@ -217,19 +213,46 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
     // J_j is empty, or a relaxed row past the last A21 row) stay zero under the
     // updates and never change a column maximum, so only the nonzero rows are
     // kept: R <= min(p, m).  Every CTA builds the same list.
-    if (tid == 0) sh.nz_count = 0;
-    __syncthreads();
-    for (int j = tid; j < a.R; j += kT) {
-        bool nz = false;
-        for (int k = 0; k < p && !nz; k++) nz = a.C[(int64_t)j * p + k] != 0.0;
-        sh.rowmap[j] = nz ? 1 : 0;
+    // (All per-entry loops below run over flattened (column, row) indices so
+    // that every thread has work whatever the front's size: a loop over
+    // columns with the rows spread over the threads leaves most of them idle
+    // when the columns are short, and its steps add up.)
+    // a row whose first entry is nonzero is nonzero (almost every row of a
+    // front with many A21 rows); only the others are scanned in full, all of
+    // them together over (row, column) pairs
+    if (warp == 0) {
+        int r = 0;
+        for (int j0 = 0; j0 < a.R; j0 += 32) {
+            const int j = j0 + lane;
+            const bool first = j < a.R && a.C[(int64_t)j * p] != 0.0;
+            if (j < a.R) sh.nzflag[j] = first ? 1 : 0;
+            const bool scan = j < a.R && !first;
+            const unsigned int bal = __ballot_sync(0xffffffffu, scan);
+            if (scan) sh.rowmap[r + __popc(bal & ((1u << lane) - 1u))] = j;  // rows still to scan
+            r += __popc(bal);
+        }
+        if (lane == 0) sh.nz_count = r;
     }
     __syncthreads();
-    if (tid == 0) {
+    {
+        const int ns = sh.nz_count;
+        for (int idx = tid; idx < ns * p; idx += kT) {
+            const int q = idx / p, k = idx - q * p;
+            const int j = sh.rowmap[q];
+            if (a.C[(int64_t)j * p + k] != 0.0) sh.nzflag[j] = 1;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {  // compaction of the nonzero rows, 32 at a time
         int r = 0;
-        for (int j = 0; j < a.R; j++)
-            if (sh.rowmap[j]) sh.rowmap[r++] = j;
-        sh.nz_count = r;
+        for (int j0 = 0; j0 < a.R; j0 += 32) {
+            const int j = j0 + lane;
+            const bool nz = j < a.R && sh.nzflag[j];
+            const unsigned int bal = __ballot_sync(0xffffffffu, nz);
+            if (nz) sh.rowmap[r + __popc(bal & ((1u << lane) - 1u))] = j;
+            r += __popc(bal);
+        }
+        if (lane == 0) sh.nz_count = r;
     }
     __syncthreads();
     const int R = sh.nz_count, LD = p + R;
@@ -237,6 +260,7 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
     double *cols = dsm;                    // [ncl][LD]
     double *pc0 = dsm + (size_t)ncl * LD;  // pivot column copies
     double *pc1 = pc0 + LD;
+    double *cs0 = pc1 + LD, *cs1 = cs0 + ncl, *cas0 = cs1 + ncl, *cas1 = cas0 + ncl;  // update scalars
     const int nmask = (p + 31) / 32;
     auto colptr = [&](int c) -> const double * {
         return cluster.map_shared_rank(cols, c % G) + (size_t)(c / G) * LD;
@@ -244,19 +268,26 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
 
     // ---- load: own columns of A11 (full symmetric) and of the nonzero outer rows
     bool nonfinite = false;
-    for (int lc = 0; lc < ncl; lc++) {
+    // flattened (column, row) loops step their indices by kT without divisions
+    const int dl = kT / LD, di = kT - dl * LD;
+    for (int idx = tid, lc = tid / LD, i = tid - (tid / LD) * LD; idx < ncl * LD; idx += kT) {
         const int c = lc * G + rank;
-        if (c >= p) break;
-        double *col = cols + (size_t)lc * LD;
-        for (int i = tid; i < LD; i += kT) {
-            double v;
-            if (i < p)
-                v = (i >= c) ? a.A[(int64_t)c * a.lda + i] : a.A[(int64_t)i * a.lda + c];
-            else
-                v = a.C[(int64_t)sh.rowmap[i - p] * p + c];
-            nonfinite |= !isfinite(v);
-            col[i] = v;
+        const int ii = i;
+        i += di;
+        lc += dl;
+        if (i >= LD) {
+            i -= LD;
+            lc++;
         }
+        if (c >= p) continue;
+        const int i0 = ii;
+        double v;
+        if (i0 < p)
+            v = (i0 >= c) ? a.A[(int64_t)c * a.lda + i0] : a.A[(int64_t)i0 * a.lda + c];
+        else
+            v = a.C[(int64_t)sh.rowmap[i0 - p] * p + c];
+        nonfinite |= !isfinite(v);
+        cols[idx] = v;
     }
     for (int i = tid; i < p; i += kT) sh.live[i] = 1;
     if (nonfinite) atomicCAS(a.info, kInfoOk, (int32_t)CTP_ENONFINITE);
@@ -277,31 +308,24 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
         }
         const int buf = round & 1;
         round++;
-        // ---------------- test round: the first `win` live candidates >= m
+        // ---------------- test round: the live candidates in [m, m + win)
         // (cluster-wide order); each CTA tests the ones it owns, one per warp.
         // The window is 1 after an acceptance and doubles after a round with no
         // pass, so accepted-first candidates cost a single test and runs of
         // rejections are tested in parallel.
         if (tid < nmask) sh.mask[buf][tid] = 0u;
-        if (tid == 0) {
-            // the window ends at the first live column that would exceed `win`
-            // candidates or a CTA's kNW warps; every CTA computes the same end
-            int owned[16];
-            for (int r = 0; r < G; r++) owned[r] = 0;
-            int k = 0, seen = 0, hi = p;
-            for (int c = m; c < p; c++) {
-                if (!sh.live[c]) continue;
-                const int o = c % G;
-                if (seen == win || owned[o] == kNW) {
-                    hi = c;
-                    break;
-                }
-                seen++;
-                owned[o]++;
-                if (o == rank) sh.cand[k++] = c;
-            }
-            for (int w = k; w < kNW; w++) sh.cand[w] = -1;
-            sh.hi[buf] = hi;
+        if (warp == 0) {
+            // the window is the index range [m, m + win) (win <= kNW * G, so no
+            // CTA owns more than kNW of its columns); this CTA's live columns in
+            // it, in order, go to its warps (one ballot over its column slots)
+            const int hi = min(p, m + win);
+            const int j0 = m > rank ? (m - rank + G - 1) / G : 0;
+            const int c = rank + G * (j0 + lane);
+            const bool ok = c < hi && sh.live[c];
+            const unsigned int bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) sh.cand[__popc(bal & ((1u << lane) - 1u))] = c;
+            if (lane >= __popc(bal) && lane < kNW) sh.cand[lane] = -1;
+            if (lane == 0) sh.hi[buf] = hi;
         }
         __syncthreads();
         {
@@ -382,44 +406,53 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
         }
         __syncthreads();
         const bool abs_rows = a.abs_update != 0;
-        for (int lc = 0; lc < ncl; lc++) {
+        // per own live column: the update's scalars (a column that is not live,
+        // or is a pivot column, gets none and is skipped)
+        for (int lc = tid; lc < ncl; lc += kT) {
             const int c = lc * G + rank;
-            if (c >= p) break;
-            if (!sh.live[c] || c == q0 || c == q1) continue;
-            double *col = cols + (size_t)lc * LD;
-            if (q1 < 0) {
-                // 1x1: a(i,c) -= a(i,q) (a(c,q) / d); C rows (strict): c += chat |a(c,q)|
-                const double s0 = pc0[c] * dv.i0;
-                const double as0 = fabs(pc0[c]) * fabs(dv.i0);
-                for (int i = tid; i < LD; i += kT) {
-                    if (i < p) {
-                        if (!sh.live[i] || i == q0) continue;
-                        col[i] -= pc0[i] * s0;
-                    } else if (abs_rows) {
-                        col[i] += pc0[i] * as0;  // eq. (4.3)
-                    } else {
-                        col[i] -= pc0[i] * s0;
-                    }
-                }
-            } else {
-                // 2x2: a(i,c) -= [a(i,t) a(i,m)] (D^-1 [a(c,t) a(c,m)]^T)
+            const bool upd = c < p && sh.live[c] && c != q0 && c != q1;
+            double s0 = 0.0, s1 = 0.0, as0 = 0.0, as1 = 0.0;
+            if (upd && q1 < 0) {
+                s0 = pc0[c] * dv.i0;
+                as0 = fabs(pc0[c]) * fabs(dv.i0);
+            } else if (upd) {
                 const double i11 = dv.i0, i21 = dv.i1, i22 = dv.i2;
                 const double b0 = pc0[c], b1 = pc1[c];
-                const double s0 = i11 * b0 + i21 * b1, s1 = i21 * b0 + i22 * b1;
+                s0 = i11 * b0 + i21 * b1;
+                s1 = i21 * b0 + i22 * b1;
                 const double ab0 = fabs(b0), ab1 = fabs(b1);
-                const double as0 = fabs(i11) * ab0 + fabs(i21) * ab1;
-                const double as1 = fabs(i21) * ab0 + fabs(i22) * ab1;
-                for (int i = tid; i < LD; i += kT) {
-                    const double x0 = pc0[i], x1 = pc1[i];
-                    if (i < p) {
-                        if (!sh.live[i] || i == q0 || i == q1) continue;
-                        col[i] -= x0 * s0 + x1 * s1;
-                    } else if (abs_rows) {
-                        col[i] += x0 * as0 + x1 * as1;
-                    } else {
-                        col[i] -= x0 * s0 + x1 * s1;
-                    }
-                }
+                as0 = fabs(i11) * ab0 + fabs(i21) * ab1;
+                as1 = fabs(i21) * ab0 + fabs(i22) * ab1;
+            }
+            cs0[lc] = s0, cs1[lc] = s1, cas0[lc] = as0, cas1[lc] = as1;
+            sh.nzflag[lc] = upd ? 1 : 0;
+        }
+        __syncthreads();
+        // the update over (column, row) pairs
+        for (int idx = tid, lc2 = tid / LD, i2 = tid - (tid / LD) * LD; idx < ncl * LD; idx += kT) {
+            const int lc = lc2, i = i2;
+            i2 += di;
+            lc2 += dl;
+            if (i2 >= LD) {
+                i2 -= LD;
+                lc2++;
+            }
+            if (!sh.nzflag[lc]) continue;
+            if (i < p && (!sh.live[i] || i == q0 || i == q1)) continue;
+            double *e = cols + idx;
+            if (q1 < 0) {
+                // 1x1: a(i,c) -= a(i,q) (a(c,q) / d); C rows (strict): c += chat |a(c,q)|
+                if (i < p || !abs_rows)
+                    *e -= pc0[i] * cs0[lc];
+                else
+                    *e += pc0[i] * cas0[lc];  // eq. (4.3)
+            } else {
+                // 2x2: a(i,c) -= [a(i,t) a(i,m)] (D^-1 [a(c,t) a(c,m)]^T)
+                const double x0 = pc0[i], x1 = pc1[i];
+                if (i < p || !abs_rows)
+                    *e -= x0 * cs0[lc] + x1 * cs1[lc];
+                else
+                    *e += x0 * cas0[lc] + x1 * cas1[lc];
             }
         }
         __syncthreads();
@@ -473,52 +506,48 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
     for (int k = tid; k < p; k += kT) sh.pos_of[sh.order[k]] = k;
     __syncthreads();
 
-    // ---- write back the A11 block in pivot order (lower triangle)
-    for (int lc = 0; lc < ncl; lc++) {
+    // ---- write back the A11 block in pivot order (lower triangle), over
+    // (column, row) pairs of the own columns
+    const int dlp = kT / p, dip = kT - dlp * p;
+    for (int idx = tid, lc2 = tid / p, i2 = tid - (tid / p) * p; idx < ncl * p; idx += kT) {
+        const int lc = lc2, i = i2;
+        i2 += dip;
+        lc2 += dlp;
+        if (i2 >= p) {
+            i2 -= p;
+            lc2++;
+        }
         const int c = lc * G + rank;
-        if (c >= p) break;
+        if (c >= p) continue;
         const double *col = cols + (size_t)lc * LD;
         const int pos = sh.pos_of[c];
         const int kd = sh.kind[pos];
         double *out = a.A + (int64_t)pos * a.lda;
+        const int pi = sh.pos_of[i];
         if (kd == CTP_PIVKIND_DELAYED) {
-            for (int i = tid; i < p; i += kT) {
-                const int pi = sh.pos_of[i];
-                if (pi >= pos) out[pi] = col[i];
-            }
+            if (pi >= pos) out[pi] = col[i];
         } else if (kd == CTP_PIVKIND_ZERO) {
-            for (int i = tid; i < p; i += kT) {
-                const int pi = sh.pos_of[i];
-                if (pi >= pos) out[pi] = 0.0;
-            }
+            if (pi >= pos) out[pi] = 0.0;
         } else if (kd == CTP_PIVKIND_1X1) {
-            const double inv = sh.sInv[2 * pos];
-            for (int i = tid; i < p; i += kT) {
-                const int pi = sh.pos_of[i];
-                if (pi > pos) out[pi] = col[i] * inv;
-            }
-            if (tid == 0) out[pos] = sh.sD[2 * pos];
+            if (pi > pos) out[pi] = col[i] * sh.sInv[2 * pos];
+            if (i == 0) out[pos] = sh.sD[2 * pos];
         } else if (kd == CTP_PIVKIND_2X2_FIRST) {
             const int mo = sh.order[pos + 1];
-            const double *cmo = cluster.map_shared_rank(cols, mo % G) + (size_t)(mo / G) * LD;
-            const double i11 = sh.sInv[2 * pos], i21 = sh.sInv[2 * pos + 1];
-            for (int i = tid; i < p; i += kT) {
-                const int pi = sh.pos_of[i];
-                if (pi > pos + 1) out[pi] = col[i] * i11 + cmo[i] * i21;
+            if (pi > pos + 1) {
+                const double *cmo = cluster.map_shared_rank(cols, mo % G) + (size_t)(mo / G) * LD;
+                out[pi] = col[i] * sh.sInv[2 * pos] + cmo[i] * sh.sInv[2 * pos + 1];
             }
-            if (tid == 0) {
+            if (i == 0) {
                 out[pos] = sh.sD[2 * pos];
                 out[pos + 1] = sh.sD[2 * pos + 1];
             }
         } else {  // second column of a 2x2
             const int to = sh.order[pos - 1];
-            const double *cto = cluster.map_shared_rank(cols, to % G) + (size_t)(to / G) * LD;
-            const double i21 = sh.sInv[2 * (pos - 1) + 1], i22 = sh.sInv[2 * (pos - 1) + 2];
-            for (int i = tid; i < p; i += kT) {
-                const int pi = sh.pos_of[i];
-                if (pi > pos) out[pi] = cto[i] * i21 + col[i] * i22;
+            if (pi > pos) {
+                const double *cto = cluster.map_shared_rank(cols, to % G) + (size_t)(to / G) * LD;
+                out[pi] = cto[i] * sh.sInv[2 * (pos - 1) + 1] + col[i] * sh.sInv[2 * (pos - 1) + 2];
             }
-            if (tid == 0) out[pos] = sh.sD[2 * pos];
+            if (i == 0) out[pos] = sh.sD[2 * pos];
         }
     }
     if (rank == 0) {
@@ -535,11 +564,11 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
     cluster.sync();  // no CTA leaves while its shared memory may still be read
 }
 
-__global__ void __launch_bounds__(kT) k_factor_cluster(FactorArgs a, int G) { factor_cluster_body(a, G); }
+__global__ void __launch_bounds__(kT, 3) k_factor_cluster(FactorArgs a, int G) { factor_cluster_body(a, G); }
 
 // Batched: cluster c factors front list[c]; its arguments come from the
 // front's descriptor and its workspace section.
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 3)
     k_factor_cluster_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
                            char *ws, const int *__restrict__ list, BatchOpts o, int G) {
     const int f = list[blockIdx.x / G];
@@ -573,8 +602,9 @@ __global__ void __launch_bounds__(kT)
 
 static size_t factor_smem(int p, int R, int G) {
     int ncl = (p + G - 1) / G;
-    return sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R));
+    return sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R) + 4 * (size_t)ncl);
 }
+size_t factor_smem_bytes(int p, int R, int G) { return factor_smem(p, R, G); }
 
 cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t st) {
     // preferred cluster width by p (unless the caller asks for one): more CTAs
