@@ -297,6 +297,7 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
     int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, round = 0;
     int win = 1;                  // candidates tested in the next round
     const int win_max = kNW * G;  // no CTA owns more than kNW of them
+    int m0 = m;                   // where the search for the next pivot began
     for (;;) {
         if (nelim >= p) break;
         while (m < p && !sh.live[m]) m++;
@@ -304,6 +305,7 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
             if (!accepted) break;  // a whole sweep without a pivot: stop
             accepted = 0;
             m = 0;  // new sweep from the first live column
+            m0 = 0;
             continue;
         }
         const int buf = round & 1;
@@ -375,7 +377,16 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
             win = win * 2 < win_max ? win * 2 : win_max;
             continue;
         }
-        win = 1;
+        // the next search starts with a window of twice the distance this one
+        // covered (1 when the first candidate passed): all-accepting runs test
+        // one candidate per round, runs of rejections start wide
+        {
+            const int gap = cstar - m0;
+            win = 1;
+            while (win < 2 * gap && win < win_max) win *= 2;
+            if (win > win_max) win = win_max;
+            m0 = cstar + 1;
+        }
         const Decision dv = sh.cur;
         if (dv.kind == DEC_ZERO) {
             if (tid == 0) {
