@@ -368,7 +368,7 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
         const int id = K_B_FACTOR_G1 + (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4);
         CTP_CUDA(timed(ctx, id, st, [&] { return batch_factor_class(plan, c, fronts, w, st); }));
     }
-    CTP_CUDA(timed(ctx, K_B_SOLVE, st, [&] { return batch_solve(plan, fronts, w, st); }));
+    CTP_CUDA(timed(ctx, K_B_SOLVE, st, [&] { return batch_solve(plan, fronts, w, ctx->num_sms, st); }));
     CTP_CUDA(timed(ctx, K_B_FORM, st, [&] { return batch_form(plan, fronts, w, ctx->num_sms, st); }));
     return CTP_OK;
 }

@@ -170,9 +170,9 @@ struct ctp_plan {
     bool tc;
     // workspace layout
     size_t off_ginfo, off_tab, off_citem, off_sitem, off_fitem, off_lists, off_flags, off_sections, off_wb,
-        off_lb;
+        off_lb, off_qitem, off_ritem, off_xt, off_zt;
     size_t total;
-    int64_t c_items, s_items, f_items, total_rows;
+    int64_t c_items, s_items, f_items, total_rows, q_items, r_items, nxt, nzt;
     struct Class {
         int G, pmax, count;
         size_t list_off;  // element offset in the class-list array
@@ -208,6 +208,7 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     if (opt->prec < CTP_FP64 || opt->prec > CTP_BF16X6) return CTP_EINVAL;
     const bool tc = opt->prec != CTP_FP64 && opt->smode != CTP_S_NONE;
     const int pieces = tc ? prec_pieces(opt->prec) : 0;
+    const bool stc = solve_on_tc(opt);
     if (tc && opt->smode != CTP_S_FP32_TILED && opt->smode != CTP_S_FP64_SUB) return CTP_EUNSUPPORTED;
     if (!tc && opt->smode != CTP_S_NONE && opt->smode != CTP_S_FP64_PACKED &&
         opt->smode != CTP_S_FP32_PACKED && opt->smode != CTP_S_FP64_SUB)
@@ -228,9 +229,9 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     P->tc = tc;
     P->pmax = 1;
     std::vector<BFront> tab(nb);
-    std::vector<int> citem, sitem, fitem;
+    std::vector<int> citem, sitem, fitem, qitem, ritem;
     size_t sec_off = 0;
-    int64_t row0 = 0;
+    int64_t row0 = 0, xt = 0, zt = 0;
     for (int f = 0; f < nb; f++) {
         BFront &b = tab[f];
         b.n = n_host[f];
@@ -251,6 +252,19 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         if (opt->smode != CTP_S_NONE) {
             const int64_t ft = tc ? form_tc_tiles(b.m, pieces) : form_fp64_tiles(b.m);
             for (int64_t t = 0; t < ft; t++) fitem.push_back(f);
+        }
+        b.kbx = (b.p + 63) / 64;
+        b.nwz = stc ? solve_tc_windows(b.p) : 0;
+        b.xt0 = xt;
+        b.zt0 = zt;
+        b.q0 = (int64_t)qitem.size();
+        b.r0 = (int64_t)ritem.size();
+        if (stc && b.m > 0) {
+            const int64_t nrb = (b.m + 127) / 128;
+            xt += nrb * b.kbx;
+            zt += (int64_t)b.nwz * b.kbx;
+            for (int64_t t = 0; t < nrb * b.nwz; t++) qitem.push_back(f);
+            for (int64_t t = 0; t < (int64_t)b.kbx * 8; t++) ritem.push_back(f);  // 8 rows per item
         }
         P->pmax = std::max(P->pmax, b.p);
     }
@@ -278,6 +292,10 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     P->c_items = (int64_t)citem.size();
     P->s_items = (int64_t)sitem.size();
     P->f_items = (int64_t)fitem.size();
+    P->q_items = (int64_t)qitem.size();
+    P->r_items = (int64_t)ritem.size();
+    P->nxt = xt;
+    P->nzt = zt;
     P->total_rows = row0;
     // workspace layout
     size_t off = 0;
@@ -293,6 +311,10 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     off += align256(sizeof(int) * fitem.size());
     P->off_lists = off;
     off += align256(sizeof(int) * lists.size());
+    P->off_qitem = off;
+    off += align256(sizeof(int) * qitem.size());
+    P->off_ritem = off;
+    off += align256(sizeof(int) * ritem.size());
     P->off_flags = off;
     off += align256(sizeof(int32_t) * (size_t)nb);
     const size_t tables_end = off;
@@ -306,6 +328,14 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     off += align256(tc ? 2 * copies * (size_t)row0 * kBatchKp : 0);
     P->bo.lo_off = pieces > 1 ? row0 * kBatchKp : 0;
     P->bo.pieces = pieces;
+    // tensor-core Solve: x_e and Z^T tiles, three pieces each
+    P->bo.stc = stc ? 1 : 0;
+    P->bo.xoff = (int64_t)xt * (int64_t)solve_tc_tile_elems();
+    P->bo.zoff = (int64_t)zt * (int64_t)solve_tc_tile_elems();
+    P->off_xt = off;
+    off += align256(stc ? 2 * 3 * (size_t)P->bo.xoff : 0);
+    P->off_zt = off;
+    off += align256(stc ? 2 * 3 * (size_t)P->bo.zoff : 0);
     P->total = off;
     // section offsets are relative to the sections base: shift them to the workspace base
     for (int f = 0; f < nb; f++) tab[f].ws += (int64_t)P->off_sections;
@@ -315,6 +345,8 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     if (!sitem.empty()) memcpy(P->blob.data() + P->off_sitem, sitem.data(), sizeof(int) * sitem.size());
     if (!fitem.empty()) memcpy(P->blob.data() + P->off_fitem, fitem.data(), sizeof(int) * fitem.size());
     if (!lists.empty()) memcpy(P->blob.data() + P->off_lists, lists.data(), sizeof(int) * lists.size());
+    if (!qitem.empty()) memcpy(P->blob.data() + P->off_qitem, qitem.data(), sizeof(int) * qitem.size());
+    if (!ritem.empty()) memcpy(P->blob.data() + P->off_ritem, ritem.data(), sizeof(int) * ritem.size());
     *plan = P;
     if (ws_bytes) *ws_bytes = P->total;
     return CTP_OK;
@@ -336,7 +368,7 @@ ctp_status ctp_batch_upload(ctp_ctx *ctx, const ctp_plan *plan, void *workspace,
     if (plan->tc) {
         // padding rows of the stacked operands must read as zero
         if (cudaMemsetAsync(w + plan->off_wb, 0, plan->off_lb - plan->off_wb, st) != cudaSuccess ||
-            cudaMemsetAsync(w + plan->off_lb, 0, plan->total - plan->off_lb, st) != cudaSuccess)
+            cudaMemsetAsync(w + plan->off_lb, 0, plan->off_xt - plan->off_lb, st) != cudaSuccess)
             return CTP_ECUDA;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) return CTP_ECUDA;  // the blob is pageable
@@ -392,7 +424,14 @@ cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, c
                                reinterpret_cast<const int *>(w + P->off_lists) + c.list_off, c.count, c.G,
                                c.pmax, P->bo, st);
 }
-cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, cudaStream_t st) {
+cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st) {
+    if (P->bo.stc)
+        return launch_solve_tc_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
+                                     reinterpret_cast<const int *>(w + P->off_sitem), P->s_items,
+                                     reinterpret_cast<const int *>(w + P->off_qitem), P->q_items,
+                                     reinterpret_cast<const int *>(w + P->off_ritem), P->r_items, P->bo,
+                                     w + P->off_xt, w + P->off_zt, P->nxt, P->nzt, w + P->off_wb, w + P->off_lb,
+                                     reinterpret_cast<int32_t *>(w + P->off_ginfo), num_sms, st);
     return launch_solve_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
                               reinterpret_cast<const int *>(w + P->off_sitem), P->s_items, P->bo,
                               P->tc ? w + P->off_wb : nullptr, P->tc ? w + P->off_lb : nullptr, P->pmax,

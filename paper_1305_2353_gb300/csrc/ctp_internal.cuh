@@ -73,6 +73,10 @@ struct BFront {
     int64_t ws;          // byte offset of this front's workspace section
     int64_t row0;        // first row of this front in the stacked BF16 operand buffers
     int64_t c0, s0, f0;  // first compression / solve / form work item of this front
+    // tensor-core Solve: first 128 x 64 tile of x_e and of Z^T, first GEMM item,
+    // K blocks and output windows at most (from p)
+    int64_t xt0, zt0, q0, r0;  // r0: first prep item (8 identity rows each)
+    int32_t kbx, nwz;
 };
 // offsets inside a front's section: info word, compressed matrix (strict),
 // Dinv, and W21 = L21 D11 when an FP64 Form follows
@@ -101,6 +105,8 @@ struct BatchOpts {
     int smode, prec;
     int64_t lo_off;  // elements between the BF16 pieces of the operand copies
     int pieces;      // BF16 pieces per operand (1: plain; 2, 3: split)
+    int stc;         // the Solve runs on the tensor cores
+    int64_t xoff, zoff;  // elements between the pieces of the x_e / Z^T tile arrays
 };
 cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                 const int *list, int count, int G, int pmax, BatchOpts o,
@@ -127,7 +133,7 @@ size_t batch_total(const ctp_plan *P);
 cudaError_t batch_prepare(const ctp_plan *P, char *w, cudaStream_t st);
 cudaError_t batch_compress(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st);
-cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, cudaStream_t st);
+cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 
 // Tensor-core Solve (solve_tc.cu): BF16 pieces of its operands, its scratch
@@ -144,6 +150,16 @@ size_t solve_tc_ws_bytes(int64_t m, int p, int spieces);
 cudaError_t launch_solve_tc(double *A, int64_t n, int p, int64_t lda, const int32_t *perm, const int32_t *piv,
                             const double *Dinv, const int32_t *nelim, void *ws, int spieces, void *Wb, void *Lb,
                             int64_t foff, int fpieces, int32_t *info, int num_sms, cudaStream_t st);
+
+// Batched tensor-core Solve: x_e and Z^T of every front in 128 x 64 BF16 tiles
+// (three pieces each), GEMM items (front, 128-row block, output window).
+size_t solve_tc_tile_elems();  // elements of one tile
+int solve_tc_windows(int p);   // output windows of a front of width p, at most
+cudaError_t launch_solve_tc_batch(const ctp_front *fronts, const BFront *tab, char *ws, const int *sitem,
+                                  int64_t s_items, const int *qitem, int64_t q_items, const int *ritem,
+                                  int64_t r_items, BatchOpts o,
+                                  void *Xt, void *Zt, int64_t nxt, int64_t nzt, void *Wb, void *Lb,
+                                  int32_t *ginfo, int num_sms, cudaStream_t st);
 
 cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const int32_t *perm,
                               const int32_t *piv, const double *Dinv, const int32_t *nelim,

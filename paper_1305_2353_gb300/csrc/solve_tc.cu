@@ -225,6 +225,151 @@ __global__ void __launch_bounds__(kRowsG * kWarpsG)
         for (int k = e + w; k < p; k += kWarpsG) A21[(int64_t)k * lda + row] = xs[k * LDX + lane];
 }
 
+// ---- batched forms: x_e and Z^T of every front in 128 x 64 BF16 tiles (the
+// K blocks of a 128-row block, or of a 128-column window, are consecutive
+// tiles), three pieces per tile array.
+constexpr int64_t kTileElems = (int64_t)kBM * kBK;
+
+// One CTA per group of 8 identity rows of a front (a warp each; the groups of
+// a front run in parallel), written to the front's Z^T tiles as 16-byte pieces
+// of 8 consecutive K.
+__global__ void __launch_bounds__(256)
+    k_stc_prep_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
+                     const int *__restrict__ item_front, BatchOpts o, __nv_bfloat16 *__restrict__ Zt) {
+    __shared__ double rows[8][kMaxP];
+    __shared__ int spiv[kMaxP];
+    const int f = item_front[blockIdx.x];
+    const BFront b = tab[f];
+    const ctp_front fr = fronts[f];
+    if (b.m <= 0) return;
+    ctp_options oo;
+    oo.pivot = o.pivot;
+    oo.smode = o.smode;
+    oo.prec = o.prec;
+    const double *Dinv = reinterpret_cast<const double *>(ws + b.ws + bsection(b.n, b.p, &oo).Dinv);
+    const int p = b.p, e = *fr.nelim;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int d = p - e, E = (e + 31) & ~31;
+    const int KZ = (e + kBK - 1) / kBK * kBK;  // K columns the GEMM reads
+    const int nW = (2 * E + d + kBN - 1) / kBN;
+    for (int q = threadIdx.x; q < p; q += blockDim.x) spiv[q] = fr.piv[q];
+    __syncthreads();
+    {
+        const int k0 = (int)((int64_t)blockIdx.x - b.r0) * 8;
+        if (k0 >= KZ) return;
+        const int k = k0 + w;
+        double *x = rows[w];
+        for (int q = lane; q < kMaxP; q += 32) x[q] = (q == k && k < e) ? 1.0 : 0.0;
+        __syncwarp();
+        if (k < e) {
+            int j = (k > 0 && spiv[k] == CTP_PIVKIND_2X2_SECOND) ? k - 1 : k;
+            while (j < e) {
+                const int kd = spiv[j];
+                const double y0 = x[j];
+                if (kd == CTP_PIVKIND_2X2_FIRST) {
+                    const double y1 = x[j + 1];
+                    const double *l0 = fr.A + (int64_t)j * fr.lda, *l1 = fr.A + (int64_t)(j + 1) * fr.lda;
+#pragma unroll
+                    for (int s2 = 0; s2 < kMaxP / 32; s2++) {
+                        const int q = lane + 32 * s2;
+                        if (q >= j + 2 && q < p) x[q] -= y0 * __ldg(l0 + q) + y1 * __ldg(l1 + q);
+                    }
+                    j += 2;
+                } else {
+                    if (kd == CTP_PIVKIND_1X1) {
+                        const double *l0 = fr.A + (int64_t)j * fr.lda;
+#pragma unroll
+                        for (int s2 = 0; s2 < kMaxP / 32; s2++) {
+                            const int q = lane + 32 * s2;
+                            if (q > j && q < p) x[q] -= y0 * __ldg(l0 + q);
+                        }
+                    }
+                    j += 1;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // Z^T rows oc of the windows this front uses, K columns k0..k0+7
+        for (int oc = threadIdx.x; oc < nW * kBN; oc += blockDim.x) {
+            uint32_t pk[3][4];
+            for (int h = 0; h < 4; h++) {
+                double v2[2];
+                for (int r = 0; r < 2; r++) {
+                    const int kr = k0 + 2 * h + r;
+                    const double *y = rows[2 * h + r];
+                    double v = 0.0;
+                    if (kr < e) {
+                        if (oc < e)
+                            v = l21_of(y, oc, spiv, Dinv);
+                        else if (oc >= E && oc < E + e)
+                            v = y[oc - E];
+                        else if (oc >= 2 * E && oc < 2 * E + d)
+                            v = y[e + oc - 2 * E];
+                    }
+                    v2[r] = v;
+                }
+                // three pieces of the pair, each rounding what the earlier left
+                double r0 = v2[0], r1 = v2[1];
+                for (int pc = 0; pc < 3; pc++) {
+                    const __nv_bfloat16 b0 = __float2bfloat16_rn((float)r0), b1 = __float2bfloat16_rn((float)r1);
+                    pk[pc][h] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+                    r0 -= bf16_as_double(b0);
+                    r1 -= bf16_as_double(b1);
+                }
+            }
+            const int64_t tile = b.zt0 + (int64_t)(oc / kBN) * b.kbx + k0 / kBK;
+            const int64_t el = tile * kTileElems + (int64_t)(oc % kBN) * kBK + (k0 % kBK);
+#pragma unroll
+            for (int pc = 0; pc < 3; pc++)
+                *reinterpret_cast<uint4 *>(Zt + el + pc * o.zoff) = make_uint4(pk[pc][0], pk[pc][1], pk[pc][2], pk[pc][3]);
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per (front, 32-row tile): x gathered through the permutation, x_e
+// into the front's x_e tiles (K < e's last 64-wide block), x_d back in place,
+// and the Form operands' zero tails from e to that block's end.
+__global__ void __launch_bounds__(kRowsG * kWarpsG)
+    k_stc_gather_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
+                       const int *__restrict__ item_front, BatchOpts o, __nv_bfloat16 *__restrict__ Xt,
+                       __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Lb) {
+    extern __shared__ __align__(16) double xs[];  // [p][kRowsG + 1]
+    constexpr int LDX = kRowsG + 1;
+    const int f = item_front[blockIdx.x];
+    const BFront b = tab[f];
+    const ctp_front fr = fronts[f];
+    const int p = b.p, e = *fr.nelim;
+    const int64_t m = b.m;
+    const int64_t row0 = ((int64_t)blockIdx.x - b.s0) * kRowsG;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = row0 + lane;
+    const bool valid = row < m;
+    double *A21 = fr.A + p;
+    for (int k = w; k < p; k += kWarpsG) {
+        const int c = fr.perm[k];
+        xs[k * LDX + lane] = valid ? A21[(int64_t)c * fr.lda + row] : 0.0;
+    }
+    __syncthreads();
+    const int KZ = (e + kBK - 1) / kBK * kBK;
+    for (int rr = w; rr < kRowsG; rr += kWarpsG) {
+        const int64_t rw = row0 + rr;
+        if (rw >= m) break;
+        const int64_t tbase = (b.xt0 + (rw / kBM) * b.kbx) * kTileElems + (rw % kBM) * kBK;
+        for (int k = lane; k < KZ; k += 32) {
+            const double v = k < e ? xs[k * LDX + rr] : 0.0;
+            put_pieces(Xt + tbase + (int64_t)(k / kBK) * kTileElems + (k % kBK), o.xoff, 3, v);
+            if (k >= e) {
+                put_pieces(Lb + (b.row0 + rw) * kBatchKp + k, o.lo_off, o.pieces, 0.0);
+                put_pieces(Wb + (b.row0 + rw) * kBatchKp + k, o.lo_off, o.pieces, 0.0);
+            }
+        }
+    }
+    if (valid)
+        for (int k = e + w; k < p; k += kWarpsG) A21[(int64_t)k * fr.lda + row] = xs[k * LDX + lane];
+}
+
 struct Bars {
     unsigned long long full[6], empty[6], acc_full[2], acc_empty[2];
     uint32_t tmem_base;
@@ -237,14 +382,103 @@ struct SCfg {
     static constexpr int Stages = (int)(kSmemRing / Stage) < 6 ? (int)(kSmemRing / Stage) : 6;
 };
 
-template <int PS>
+// What the roles of the GEMM need to know about one tile (128 rows of x_e by
+// one 128-column window of Z^T): its front, the TMA rows/columns of its K
+// blocks, and where the epilogue writes.
+struct STile {
+    double *A21;
+    int64_t lda, m, i0;  // i0: first row of the tile within the front
+    int p, e, E, KB, o0;  // o0: first output column of the window
+    __nv_bfloat16 *Lb, *Wb;
+    int64_t lrow0;  // the front's first row in the Form's operand buffers
+    int Kst;        // their K stride
+    int xk, xy, zk, zy, kstep_x, kstep_y;  // TMA coordinates of K block 0, and per K block
+};
+
+// Kernel arguments of the single-supernode and the batched GEMM.
+struct SArgs {
+    // single supernode
+    double *A21;
+    int64_t m, lda;
+    int p;
+    const int32_t *nelim;
+    int Kp;
+    // batch
+    const ctp_front *fronts;
+    const BFront *tab;
+    const int *qitem;
+    int64_t q_items;
+    // both
+    __nv_bfloat16 *Wb, *Lb;
+    int64_t foff;
+    int fpieces;
+    int32_t *info;
+};
+
+// Output windows of a front of width p, at most over its possible e.
+int windows_for(int p) {
+    int w = 1;
+    for (int e = 1; e <= p; e++) {
+        const int we = (2 * ((e + 31) & ~31) + p - e + kBN - 1) / kBN;
+        w = we > w ? we : w;
+    }
+    return w;
+}
+
+// Tiles of this launch: the single supernode's from its e (read on the
+// device), the batch's from the plan's item table.
+template <bool kBatch>
+__device__ __forceinline__ int64_t tile_count(const SArgs &g) {
+    if (kBatch) return g.q_items;
+    const int e = *g.nelim;
+    const int KB = (e + kBK - 1) / kBK;
+    const int E = (e + 31) & ~31;
+    const int nW = (2 * E + g.p - e + kBN - 1) / kBN;
+    return KB > 0 ? ((g.m + kBM - 1) / kBM) * nW : 0;
+}
+
+// Tile t, or false when it has no work (a batch window past its front's
+// outputs, or a front that eliminated nothing); every role decodes alike.
+template <bool kBatch>
+__device__ __forceinline__ bool tile_at(int64_t t, const SArgs &g, STile &s) {
+    if (!kBatch) {
+        const int e = *g.nelim;
+        const int E = (e + 31) & ~31;
+        const int nW = (2 * E + g.p - e + kBN - 1) / kBN;
+        const int rb = (int)(t / nW), w = (int)(t % nW);
+        s.A21 = g.A21, s.lda = g.lda, s.m = g.m, s.p = g.p, s.e = e, s.E = E;
+        s.KB = (e + kBK - 1) / kBK;
+        s.i0 = (int64_t)rb * kBM, s.o0 = w * kBN;
+        s.Lb = g.Lb, s.Wb = g.Wb, s.lrow0 = 0, s.Kst = g.Kp;
+        s.xk = 0, s.xy = rb * kBM, s.zk = 0, s.zy = w * kBN, s.kstep_x = kBK, s.kstep_y = 0;
+        return true;
+    }
+    const int f = g.qitem[t];
+    const BFront b = g.tab[f];
+    const ctp_front fr = g.fronts[f];
+    const int e = *fr.nelim;
+    const int64_t local = t - b.q0;
+    const int rb = (int)(local / b.nwz), w = (int)(local % b.nwz);
+    const int E = (e + 31) & ~31;
+    const int nW = (2 * E + b.p - e + kBN - 1) / kBN;
+    if (e <= 0 || w >= nW) return false;
+    s.A21 = fr.A + b.p, s.lda = fr.lda, s.m = b.m, s.p = b.p, s.e = e, s.E = E;
+    s.KB = (e + kBK - 1) / kBK;
+    s.i0 = (int64_t)rb * kBM, s.o0 = w * kBN;
+    s.Lb = g.Lb, s.Wb = g.Wb, s.lrow0 = b.row0, s.Kst = kBatchKp;
+    // tiles of 128 x 64: K blocks of a row block (or window) are consecutive tiles
+    s.xk = 0, s.xy = (int)((b.xt0 + (int64_t)rb * b.kbx) * kBM);
+    s.zk = 0, s.zy = (int)((b.zt0 + (int64_t)w * b.kbx) * kBN);
+    s.kstep_x = 0, s.kstep_y = kBM;
+    return true;
+}
+
+template <int PS, bool kBatch>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_solve_tc(const __grid_constant__ CUtensorMap mX1, const __grid_constant__ CUtensorMap mX2,
                const __grid_constant__ CUtensorMap mX3, const __grid_constant__ CUtensorMap mZ1,
                const __grid_constant__ CUtensorMap mZ2, const __grid_constant__ CUtensorMap mZ3,
-               double *__restrict__ A21, int64_t m, int p, int64_t lda, const int32_t *__restrict__ nelim_p,
-               __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Lb, int64_t foff, int fpieces, int Kp,
-               int32_t *__restrict__ info) {
+               const SArgs g) {
     using C = SCfg<PS>;
     constexpr int NS = C::Stages;
     const CUtensorMap *mapX[3] = {&mX1, &mX2, &mX3};
@@ -253,12 +487,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __shared__ Bars bars;
     uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int e = *nelim_p;
-    const int KB = (e + kBK - 1) / kBK;
-    const int E = (e + 31) & ~31;
-    const int nW = (2 * E + p - e + kBN - 1) / kBN;  // windows of the 2E + d output columns
-    const int64_t nRB = (m + kBM - 1) / kBM;
-    const int64_t ntiles = KB > 0 ? nRB * nW : 0;
+    const int64_t ntiles = tile_count<kBatch>(g);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; s++) {
@@ -286,18 +515,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             uint32_t phase = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int rb = (int)(t / nW), wdw = (int)(t % nW);
-                for (int kb = 0; kb < KB; kb++) {
+                STile s;
+                if (!tile_at<kBatch>(t, g, s)) continue;
+                for (int kb = 0; kb < s.KB; kb++) {
                     if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars.abort)) {
                         ok = false;
                         break;
                     }
                     mbar_expect_tx(&bars.full[stage], C::Stage);
                     uint8_t *dst = ring + (size_t)stage * C::Stage;
+                    const int dx = kb * s.kstep_x, dy = kb * s.kstep_y;
 #pragma unroll
                     for (int pc = 0; pc < PS; pc++) {
-                        tma_load_2d(dst + pc * kPiece, mapX[pc], kb * kBK, rb * kBM, &bars.full[stage]);
-                        tma_load_2d(dst + (PS + pc) * kPiece, mapZ[pc], kb * kBK, wdw * kBN, &bars.full[stage]);
+                        tma_load_2d(dst + pc * kPiece, mapX[pc], s.xk + dx, s.xy + dy, &bars.full[stage]);
+                        tma_load_2d(dst + (PS + pc) * kPiece, mapZ[pc], s.zk + dx, s.zy + dy, &bars.full[stage]);
                     }
                     if (++stage == NS) {
                         stage = 0;
@@ -314,13 +545,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             uint32_t phase = 0, accphase = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                STile s;
+                if (!tile_at<kBatch>(t, g, s)) continue;
                 if (!mbar_wait(&bars.acc_empty[acc], accphase ^ 1u, &bars.abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)(acc * kBN);
-                for (int kb = 0; kb < KB; kb++) {
+                for (int kb = 0; kb < s.KB; kb++) {
                     if (!mbar_wait(&bars.full[stage], phase, &bars.abort)) {
                         ok = false;
                         break;
@@ -361,40 +594,41 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         // ---------------- epilogue: warps 2..9
         const int q = warp & 3;            // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2;  // which 64 columns of the window
-        const int d = p - e;
         int acc = 0;
         uint32_t accphase = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const int rb = (int)(t / nW), wdw = (int)(t % nW);
+            STile s;
+            if (!tile_at<kBatch>(t, g, s)) continue;
             if (!mbar_wait(&bars.acc_full[acc], accphase, &bars.abort)) {
                 if (lane == 0) atomicExch(&bars.abort, 1);
                 break;
             }
             tc_fence_after();
-            const int64_t i = (int64_t)rb * kBM + q * 32 + lane;
+            const int64_t i = s.i0 + q * 32 + lane;
+            const int e = s.e, E = s.E, d = s.p - e;
 #pragma unroll 1
             for (int c = 0; c < 64; c += 32) {
                 uint32_t r[32];
                 tmem_ld32_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + half * 64 + c), r);
                 tmem_wait_ld();
-                if (i >= m) continue;
-                const int o0 = wdw * kBN + half * 64 + c;  // a multiple of 32: one block of Z
+                if (i >= s.m) continue;
+                const int o0 = s.o0 + half * 64 + c;  // a multiple of 32: one block of Z
                 if (o0 < E) {
                     // L21: FP64 at positions < e; pieces over the whole slice (zero past e)
-                    double *dst = A21 + (int64_t)o0 * lda + i;
+                    double *dst = s.A21 + (int64_t)o0 * s.lda + i;
 #pragma unroll
                     for (int x = 0; x < 32; x++)
-                        if (o0 + x < e) dst[(int64_t)x * lda] = (double)__uint_as_float(r[x]);
-                    put_pieces32(Lb + i * Kp + o0, foff, fpieces, r);
+                        if (o0 + x < e) dst[(int64_t)x * s.lda] = (double)__uint_as_float(r[x]);
+                    put_pieces32(s.Lb + (s.lrow0 + i) * s.Kst + o0, g.foff, g.fpieces, r);
                 } else if (o0 < 2 * E) {
-                    put_pieces32(Wb + i * Kp + (o0 - E), foff, fpieces, r);  // Y = W21
+                    put_pieces32(s.Wb + (s.lrow0 + i) * s.Kst + (o0 - E), g.foff, g.fpieces, r);  // Y = W21
                 } else {
                     // x_d += correction at delayed position e + (o - 2E)
                     const int j0 = o0 - 2 * E;
-                    double *dst = A21 + (int64_t)(e + j0) * lda + i;
+                    double *dst = s.A21 + (int64_t)(e + j0) * s.lda + i;
 #pragma unroll
                     for (int x = 0; x < 32; x++)
-                        if (j0 + x < d) dst[(int64_t)x * lda] += (double)__uint_as_float(r[x]);
+                        if (j0 + x < d) dst[(int64_t)x * s.lda] += (double)__uint_as_float(r[x]);
                 }
             }
             tc_fence_before();
@@ -407,27 +641,56 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && bars.abort) atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
+    if (threadIdx.x == 0 && bars.abort) atomicCAS(g.info, kInfoOk, (int32_t)CTP_ETIMEOUT);
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * kBN);
     }
 }
 
-template <int PS>
-cudaError_t launch_gemm(int grid, const CUtensorMap (&mX)[3], const CUtensorMap (&mZ)[3], double *A21, int64_t m,
-                        int p, int64_t lda, const int32_t *nelim, void *Wb, void *Lb, int64_t foff, int fpieces,
-                        int Kp, int32_t *info, cudaStream_t st) {
+template <int PS, bool kBatch>
+cudaError_t launch_gemm(int grid, const CUtensorMap (&mX)[3], const CUtensorMap (&mZ)[3], const SArgs &g,
+                        cudaStream_t st) {
     const size_t smem = kSmemRing + 1024;
-    cudaError_t err = cudaFuncSetAttribute(k_solve_tc<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_solve_tc<PS, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_solve_tc<PS><<<grid, kThreadsTC, smem, st>>>(mX[0], mX[1], mX[2], mZ[0], mZ[1], mZ[2], A21, m, p, lda, nelim,
-                                                   (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb, foff, fpieces, Kp,
-                                                   info);
+    k_solve_tc<PS, kBatch><<<grid, kThreadsTC, smem, st>>>(mX[0], mX[1], mX[2], mZ[0], mZ[1], mZ[2], g);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t solve_tc_tile_elems() { return (size_t)kTileElems; }
+int solve_tc_windows(int p) { return windows_for(p); }
+
+cudaError_t launch_solve_tc_batch(const ctp_front *fronts, const BFront *tab, char *ws, const int *sitem,
+                                  int64_t s_items, const int *qitem, int64_t q_items, const int *ritem,
+                                  int64_t r_items, BatchOpts o,
+                                  void *Xt, void *Zt, int64_t nxt, int64_t nzt, void *Wb, void *Lb,
+                                  int32_t *ginfo, int num_sms, cudaStream_t st) {
+    if (q_items == 0 || s_items == 0 || r_items == 0) return cudaSuccess;
+    k_stc_prep_batch<<<(unsigned)r_items, 256, 0, st>>>(fronts, tab, ws, ritem, o, (__nv_bfloat16 *)Zt);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const size_t smem = sizeof(double) * (size_t)kMaxP * (kRowsG + 1);
+    err = cudaFuncSetAttribute(k_stc_gather_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_stc_gather_batch<<<(unsigned)s_items, kRowsG * kWarpsG, smem, st>>>(
+        fronts, tab, sitem, o, (__nv_bfloat16 *)Xt, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    CUtensorMap mX[3], mZ[3];
+    for (int pc = 0; pc < 3; pc++)
+        if (!make_map_bf16(&mX[pc], (__nv_bfloat16 *)Xt + pc * o.xoff, nxt * kBM, kBK, kBM) ||
+            !make_map_bf16(&mZ[pc], (__nv_bfloat16 *)Zt + pc * o.zoff, nzt * kBN, kBK, kBN))
+            return cudaErrorInvalidValue;
+    SArgs g = {};
+    g.fronts = fronts, g.tab = tab, g.qitem = qitem, g.q_items = q_items;
+    g.Wb = (__nv_bfloat16 *)Wb, g.Lb = (__nv_bfloat16 *)Lb, g.foff = o.lo_off, g.fpieces = o.pieces, g.info = ginfo;
+    const int grid = (int)(q_items < num_sms ? q_items : num_sms);
+    return launch_gemm<3, true>(grid, mX, mZ, g, st);
+}
 
 size_t solve_tc_ws_bytes(int64_t m, int p, int spieces) {
     const int Kp = form_tc_kpad(p);
@@ -463,9 +726,11 @@ cudaError_t launch_solve_tc(double *A, int64_t n, int p, int64_t lda, const int3
     }
     const int64_t tiles_max = ((m + kBM - 1) / kBM) * (kZRows / kBN);
     const int grid = (int)(tiles_max < num_sms ? tiles_max : num_sms);
-    if (spieces == 2)
-        return launch_gemm<2>(grid, mX, mZ, A + p, m, p, lda, nelim, Wb, Lb, foff, fpieces, Kp, info, st);
-    return launch_gemm<3>(grid, mX, mZ, A + p, m, p, lda, nelim, Wb, Lb, foff, fpieces, Kp, info, st);
+    SArgs g = {};
+    g.A21 = A + p, g.m = m, g.lda = lda, g.p = p, g.nelim = nelim, g.Kp = Kp;
+    g.Wb = (__nv_bfloat16 *)Wb, g.Lb = (__nv_bfloat16 *)Lb, g.foff = foff, g.fpieces = fpieces, g.info = info;
+    if (spieces == 2) return launch_gemm<2, false>(grid, mX, mZ, g, st);
+    return launch_gemm<3, false>(grid, mX, mZ, g, st);
 }
 
 }  // namespace ctp

@@ -190,3 +190,74 @@ def test_solve_tc_system_refines(ctx, prec):
         assert hist[-1] <= 1e-14 and k2 <= 10, (hist.tolist(), k2)
     else:
         assert hist[-1] <= 1e-12 and np.all(hist[1:] <= 0.25 * hist[:-1]), (hist.tolist(), k2)
+
+
+def _batch_fronts(count, seed):
+    """Uneven fronts with the tough structure (rejections, 2x2 and zero pivots,
+    delayed columns), plus edge cases: a 1x1 front, a front without A21 rows,
+    the widest front, and a front whose p is just above 2 K blocks."""
+    shapes = inputs.batch_shapes(count, seed=seed, pmax=256)
+    fr = [_tough(int(n), int(p), seed * 7919 + k) for k, (n, p) in enumerate(shapes)]
+    fr += [inputs.supernode(1, 1, seed=5), inputs.supernode(40, 40, seed=6), _tough(700, 256, 7),
+           _tough(500, 129, 8)]
+    return fr
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "bf16x6"])
+def test_batch_solve_tc_matches_oracle(ctx, prec):
+    """The batched tensor-core Solve (one prep per front, tiles of x_e and Z^T,
+    one GEMM launch over every front's (row block, window) items), front by
+    front: pivots and A11 as the oracle's, L21 and the delayed columns within the
+    split's bound, S within the Form's bound plus the Solve's error."""
+    from paper_1305_2353_gb300 import ctp
+    fr = _batch_fronts(50, 11)
+    b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr],
+                  ctp.options(pivot="strict", prec=prec, smode="fp32_tiled", solve="tc"))
+    b.run()
+    torch.cuda.synchronize()
+    assert np.all(b.flags() == 0)
+    for k, A in enumerate(fr):
+        p = A.shape[1]
+        ref = O.factor(A, p, "strict", log_cap=200000)
+        got = b.result(k)
+        e = ref["nelim"]
+        assert got["nelim"] == e
+        assert np.array_equal(got["perm"], ref["perm"]) and np.array_equal(got["piv"], ref["piv"])
+        if A.shape[0] == p or e == 0:
+            continue
+        ops = _operands(A, ref, p)
+        err_L = np.abs(got["A"][p:, :e] - ops["L21"])
+        assert np.all(err_L <= TOL_SOLVE * ops["bL"] + 1e-300), k
+        want_d = ref["A"][p:, e:p]
+        assert np.all(np.abs(got["A"][p:, e:p] - want_d) <= TOL_SOLVE * ops["bd"] + 2.0 ** -52 * np.abs(want_d)
+                      + 1e-300), k
+        S = O.form(ops["L21"], ref["piv"][:e], ref["D"])
+        lo = np.tril(np.ones_like(S, dtype=bool))
+        aL, aW = np.abs(ops["L21"]), np.abs(ops["W21"])
+        bound = (TOL_FORM[prec] * (aW @ aL.T) + 2 * TOL_SOLVE * (ops["bY"] @ aL.T + aW @ ops["bL"].T)
+                 + 2.0 ** -23 * np.abs(S))
+        assert np.all(np.abs(got["S"] - S)[lo] <= bound[lo] + 1e-300), k
+
+
+def test_multifrontal_solve_tc_refines(ctx):
+    """The shifted 24^3 Laplacian factored multifrontally with every panel's
+    Solve and Form on the tensor cores (batched fronts and root chains):
+    refinement against the sparse matrix reaches 1e-14 with the three-piece
+    Form, and leaf fronts keep the FP64 run's pivots."""
+    from paper_1305_2353_gb300 import ctp
+    cp, ri, v = inputs.laplacian_3d(24, 3.0)
+    perm, blocks = inputs.nested_dissection_3d(24, 64)
+    N = 24 ** 3
+    mf64 = ctp.Multifrontal(ctx, cp, ri, v, perm, blocks)
+    mf64.factor(ctp.options(pivot="strict"))
+    mf = ctp.Multifrontal(ctx, cp, ri, v, perm, blocks)
+    mf.factor(ctp.options(pivot="strict", prec="bf16x6", solve="tc"))
+    gi, g64 = mf.info(), mf64.info()
+    leaves = [s for s in range(len(gi["parent"])) if s not in set(gi["parent"].tolist())]
+    assert [gi["nelim"][s] for s in leaves] == [g64["nelim"][s] for s in leaves]
+    B = np.random.default_rng(5).standard_normal((N, 3))
+    X = torch.zeros((3, N), dtype=torch.float64, device="cuda")
+    hist, steps = mf.refine(ctp.colmajor(B), X, mf.refine_workspace(3))
+    assert hist[-1].max() <= 1e-14 and steps <= 6, hist.max(axis=1)
+    mf.destroy()
+    mf64.destroy()
