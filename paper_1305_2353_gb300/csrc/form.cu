@@ -4,7 +4,9 @@
 // W21 = L21 D11 is the Y produced by the Solve kernel.  The kernel walks only the
 // tiles on or below the diagonal (a triangular tile index), stages 64 x 16
 // slabs of W21 and L21 in shared memory, and gives each of 256 threads a 4 x 4
-// block of S.  The inner dimension e is read from device memory (it is only
+// block of S, rows strided by 16 along the lanes so that a warp's stores (or
+// read-modify-writes) of S cover 16 consecutive rows of a column: coalesced,
+// which matters when the inner dimension e is small and S traffic dominates.  The inner dimension e is read from device memory (it is only
 // known after pivoting).  S is written as FP64 or FP32, full column-major or
 // lower-packed by columns; strictly upper entries are never written.
 #include "ctp_internal.cuh"
@@ -43,8 +45,8 @@ __device__ __forceinline__ void form_tile(const double *__restrict__ L21, int64_
             double a[4], bb[4];
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                a[q] = sw[kk][ty + 16 * q];
-                bb[q] = sl[kk][tx + 16 * q];
+                a[q] = sw[kk][tx + 16 * q];
+                bb[q] = sl[kk][ty + 16 * q];
             }
 #pragma unroll
             for (int q = 0; q < 4; q++)
@@ -53,15 +55,26 @@ __device__ __forceinline__ void form_tile(const double *__restrict__ L21, int64_
         }
         __syncthreads();
     }
+    // subtracting: every old value is loaded before any is stored, so that the
+    // 16 loads are in flight together
+    OutT old[4][4];
 #pragma unroll
     for (int q = 0; q < 4; q++)
 #pragma unroll
         for (int s = 0; s < 4; s++) {
-            const int64_t gi = i0 + ty + 16 * q, gj = j0 + tx + 16 * s;
+            const int64_t gi = i0 + tx + 16 * q, gj = j0 + ty + 16 * s;
+            old[q][s] = (OutT)0;
+            if (kSub && gi < m && gj < m && gi >= gj) old[q][s] = S[gj * lds + gi];
+        }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            const int64_t gi = i0 + tx + 16 * q, gj = j0 + ty + 16 * s;
             if (gi < m && gj < m && gi >= gj) {
                 const int64_t idx = kPacked ? gj * m - gj * (gj - 1) / 2 + (gi - gj) : gj * lds + gi;
                 if (kSub)
-                    S[idx] -= (OutT)acc[q][s];
+                    S[idx] = old[q][s] - (OutT)acc[q][s];
                 else
                     S[idx] = (OutT)acc[q][s];
             }

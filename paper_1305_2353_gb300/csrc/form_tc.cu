@@ -422,12 +422,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 const int64_t j0 = jbase + c * 32;
                 if (layout == 3) {
-                    // subtract into a full column-major FP64 matrix (lower triangle)
+                    // subtract into a full column-major FP64 matrix (lower
+                    // triangle): 16 old values loaded before any is stored, so
+                    // that the loads are in flight together
                     double *dp = reinterpret_cast<double *>(S) + j0 * lds + i;
 #pragma unroll
-                    for (int xx = 0; xx < 64; xx++) {
-                        if (interior || (i < m && j0 + xx <= i)) *dp -= (double)__uint_as_float(r[xx]);
-                        dp += lds;
+                    for (int h = 0; h < 64; h += 16) {
+                        double old[16];
+#pragma unroll
+                        for (int xx = 0; xx < 16; xx++) {
+                            old[xx] = 0.0;
+                            if (interior || (i < m && j0 + h + xx <= i)) old[xx] = dp[(int64_t)(h + xx) * lds];
+                        }
+#pragma unroll
+                        for (int xx = 0; xx < 16; xx++)
+                            if (interior || (i < m && j0 + h + xx <= i))
+                                dp[(int64_t)(h + xx) * lds] = old[xx] - (double)__uint_as_float(r[h + xx]);
                     }
                     continue;
                 }
