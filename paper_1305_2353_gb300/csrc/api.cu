@@ -51,6 +51,8 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     // tensor-core Solve: split-BF16 copies of x_e and Z^T
     L.Xs = off;
     off += align256(solve_on_tc(opt) ? solve_tc_ws_bytes(m, p, solve_tc_pieces(opt->prec)) : 0);
+    L.flags = off;  // strict: which rows of C receive an A21 row
+    off += align256(opt->pivot == CTP_PIV_STRICT ? sizeof(int32_t) * (size_t)p : 0);
     L.total = off;
     return L;
 }
@@ -163,7 +165,7 @@ ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double 
     CTP_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
     CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));
     CTP_CUDA(timed(ctx, K_COMPRESS_STRICT, st, [&] {
-        return launch_compress_strict(A21, m, p, lda, keys, J, info, ctx->num_sms, st);
+        return launch_compress_strict(A21, m, p, lda, keys, J, nullptr, info, ctx->num_sms, st);
     }));
     CTP_CUDA(timed(ctx, K_KEYS, st, [&] { return launch_keys_to_rowmajor(keys, C, p, st); }));
     return CTP_OK;
@@ -253,12 +255,16 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     fa.D = D;
     fa.Dinv = Dinv;
     fa.info = info;
+    fa.rowflags = nullptr;
     if (opt->pivot == CTP_PIV_STRICT) {
         unsigned long long *keys = (unsigned long long *)(ws + L.C);
+        int32_t *flags = (int32_t *)(ws + L.flags);
         CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));
+        CTP_CUDA(cudaMemsetAsync(flags, 0, sizeof(int32_t) * (size_t)p, st));
         CTP_CUDA(timed(ctx, K_COMPRESS_STRICT, st, [&] {
-            return launch_compress_strict(A + p, m, p, lda, keys, nullptr, info, ctx->num_sms, st);
+            return launch_compress_strict(A + p, m, p, lda, keys, nullptr, flags, info, ctx->num_sms, st);
         }));
+        fa.rowflags = flags;
         fa.R = p;
         fa.abs_update = 1;
         fa.C = (const double *)keys;  // non-negative keys are the doubles themselves

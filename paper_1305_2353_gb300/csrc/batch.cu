@@ -49,6 +49,8 @@ __global__ void k_batch_prepare(const BFront *__restrict__ tab, char *ws, BatchO
     if (o.pivot == CTP_PIV_STRICT) {
         unsigned long long *keys = reinterpret_cast<unsigned long long *>(base + sec.C);
         for (int i = threadIdx.x; i < bt.p * bt.p; i += blockDim.x) keys[i] = 0;
+        int32_t *nz = reinterpret_cast<int32_t *>(base + sec.nz);
+        for (int i = threadIdx.x; i < bt.p; i += blockDim.x) nz[i] = 0;
     }
 }
 
@@ -112,6 +114,8 @@ __global__ void __launch_bounds__(kThreads)
             }
         }
         rowJ[threadIdx.x] = bi;
+        // row bi of C has a member: the pivot search keeps only such rows
+        if (threadIdx.x < nrows && bi >= 0) reinterpret_cast<int32_t *>(base + sec.nz)[bi] = 1;
     }
     __syncthreads();
     for (int rr = warp; rr < nrows; rr += kThreads / 32) {

@@ -54,6 +54,7 @@ __device__ __forceinline__ void load_tile(const double *__restrict__ A21, int64_
 __global__ void __launch_bounds__(kThreads)
     k_compress_strict(const double *__restrict__ A21, int64_t m, int p, int64_t lda,
                       unsigned long long *__restrict__ Ckeys, int32_t *__restrict__ J,
+                      int32_t *__restrict__ rowflags,
                       int32_t *__restrict__ info) {
     extern __shared__ __align__(16) double smem[];
     const int tile_elems = p * (kTR + 1);
@@ -120,6 +121,9 @@ __global__ void __launch_bounds__(kThreads)
             }
             rowJ[threadIdx.x] = bi;
             if (J != nullptr && threadIdx.x < nrows) J[row0 + threadIdx.x] = bi;
+            // row bi of C has a member (J_bi is not empty): the pivot search
+            // keeps only such rows
+            if (rowflags != nullptr && threadIdx.x < nrows && bi >= 0) rowflags[bi] = 1;
         }
         __syncthreads();
 
@@ -178,7 +182,7 @@ static size_t strict_smem(int p) {
 }
 
 cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
-                                   unsigned long long *Ckeys, int32_t *J, int32_t *info,
+                                   unsigned long long *Ckeys, int32_t *J, int32_t *rowflags, int32_t *info,
                                    int num_sms, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     size_t smem = strict_smem(p);
@@ -192,7 +196,7 @@ cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t 
     int64_t ntiles = (m + kTR - 1) / kTR;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > ntiles) grid = ntiles;
-    k_compress_strict<<<(unsigned)grid, kThreads, smem, st>>>(A21, m, p, lda, Ckeys, J, info);
+    k_compress_strict<<<(unsigned)grid, kThreads, smem, st>>>(A21, m, p, lda, Ckeys, J, rowflags, info);
     return cudaGetLastError();
 }
 
@@ -268,7 +272,7 @@ extern "C" ctp_status ctp_compress_strict_noalloc(int64_t m, int32_t p, const do
     if (cudaMemsetAsync(info, 0, sizeof(int32_t), st) != cudaSuccess) return CTP_ECUDA;
     if (cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)p * p, st) != cudaSuccess)
         return CTP_ECUDA;
-    if (ctp::launch_compress_strict(A21, m, p, lda, keys, J, info, num_sms, st) != cudaSuccess)
+    if (ctp::launch_compress_strict(A21, m, p, lda, keys, J, nullptr, info, num_sms, st) != cudaSuccess)
         return CTP_ECUDA;
     if (ctp::launch_keys_to_rowmajor(keys, C, p, st) != cudaSuccess) return CTP_ECUDA;
     if (info_host != nullptr) {

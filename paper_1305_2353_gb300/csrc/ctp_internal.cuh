@@ -23,7 +23,7 @@ constexpr int kInfoOk = 0;
 //   Wb, Lb              m*Kp BF16 copies of Y and L21 for the tensor-core Form
 //   aux                 method-specific scratch (relaxed candidate lists)
 struct WsLayout {
-    size_t info, C, Dinv, W21, Wb, Lb, aux, Xs, total;
+    size_t info, C, Dinv, W21, Wb, Lb, aux, Xs, flags, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -39,8 +39,10 @@ size_t factor_smem_bytes(int p, int R, int G);  // dynamic shared memory of a pi
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns cudaError_t of the launch)
+// rowflags (optional, p int32 cleared by the caller): set to 1 for every row of
+// C that receives an A21 row (the rows the pivot search must keep)
 cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
-                                   unsigned long long *Ckeys, int32_t *J, int32_t *info,
+                                   unsigned long long *Ckeys, int32_t *J, int32_t *rowflags, int32_t *info,
                                    int num_sms, cudaStream_t st);
 int relaxed_segments(int64_t m, int p, int num_sms);
 size_t relaxed_aux_bytes(int64_t m, int p, int num_sms);
@@ -57,6 +59,7 @@ struct FactorArgs {
     int R;              // outer rows held on chip: p (compressed) or 0 (restricted)
     int abs_update;     // 1: strict worst-case update of the outer rows
     const double *C;    // R x p row-major outer rows (doubles), or nullptr
+    const int32_t *rowflags;  // R flags: nonzero for rows of C that may be nonzero (nullptr: scan C)
     double u, small;
     int32_t *perm, *piv, *nelim;
     double *D, *Dinv;
@@ -81,7 +84,7 @@ struct BFront {
 // offsets inside a front's section: info word, compressed matrix (strict),
 // Dinv, and W21 = L21 D11 when an FP64 Form follows
 struct BSection {
-    size_t info, C, Dinv, W21, total;
+    size_t info, C, Dinv, W21, nz, total;
 };
 __host__ __device__ inline size_t align256hd(size_t x) { return (x + 255) & ~size_t(255); }
 __host__ __device__ inline BSection bsection(int64_t n, int p, const ctp_options *opt) {
@@ -95,6 +98,8 @@ __host__ __device__ inline BSection bsection(int64_t n, int p, const ctp_options
     off += align256hd(sizeof(double) * (2 * (size_t)p + 2));
     s.W21 = off;
     off += align256hd((opt->smode != CTP_S_NONE && opt->prec == CTP_FP64) ? sizeof(double) * (size_t)(n - p) * p : 0);
+    s.nz = off;  // strict: which rows of C receive an A21 row
+    off += align256hd(opt->pivot == CTP_PIV_STRICT ? sizeof(int32_t) * (size_t)p : 0);
     s.total = off;
     return s;
 }

@@ -217,10 +217,14 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
     // that every thread has work whatever the front's size: a loop over
     // columns with the rows spread over the threads leaves most of them idle
     // when the columns are short, and its steps add up.)
-    // a row whose first entry is nonzero is nonzero (almost every row of a
-    // front with many A21 rows); only the others are scanned in full, all of
-    // them together over (row, column) pairs
-    if (warp == 0) {
+    // With the compression's flags (which rows of C received an A21 row) no
+    // scan is needed.  Otherwise a row whose first entry is nonzero is nonzero
+    // (almost every row of a front with many A21 rows); only the others are
+    // scanned in full, all of them together over (row, column) pairs.
+    if (a.rowflags != nullptr) {
+        for (int j = tid; j < a.R; j += kT) sh.nzflag[j] = a.rowflags[j] != 0 ? 1 : 0;
+        if (tid == 0) sh.nz_count = 0;
+    } else if (warp == 0) {
         int r = 0;
         for (int j0 = 0; j0 < a.R; j0 += 32) {
             const int j = j0 + lane;
@@ -606,6 +610,7 @@ __global__ void __launch_bounds__(kT, 3)
     a.D = fr.D;
     a.Dinv = reinterpret_cast<double *>(base + sec.Dinv);
     a.info = reinterpret_cast<int32_t *>(base + sec.info);
+    a.rowflags = o.pivot == CTP_PIV_STRICT ? reinterpret_cast<const int32_t *>(base + sec.nz) : nullptr;
     factor_cluster_body(a, G);
 }
 
