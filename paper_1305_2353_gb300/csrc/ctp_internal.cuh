@@ -195,14 +195,6 @@ cudaError_t launch_sys_forward(const ctp_sfront &f, double *X, int64_t ldx, int 
                                cudaStream_t st);
 cudaError_t launch_sys_backward(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, void *ws,
                                 cudaStream_t st);
-// A level of independent fronts (device descriptors F[0..nfront)); items =
-// (front within the level, row chunk of 256) of the rows below the pivots;
-// part_off[i] = the level's chunks before front i (partial sums are kept per chunk).
-cudaError_t launch_sys_level_forward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
-                                     double *X, int64_t ldx, int nrhs, double *Y, cudaStream_t st);
-cudaError_t launch_sys_level_backward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
-                                      const int64_t *part_off, double *X, int64_t ldx, int nrhs, double *part,
-                                      cudaStream_t st);
 cudaError_t launch_symv_residual(int64_t N, const double *M, int64_t ldm, int nrhs, const double *X,
                                  int64_t ldx, double *R, int64_t ldr, cudaStream_t st);
 cudaError_t launch_abs_rowsum(int64_t N, const double *M, int64_t ldm, double *rowsum,

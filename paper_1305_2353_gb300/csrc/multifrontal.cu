@@ -642,7 +642,7 @@ ctp_status ctp_mf_factor(ctp_ctx *ctx, ctp_mf *mf, const double *val, const ctp_
         pl.push_back(level[k]);
         pe.push_back(mf->panels[k].e);
     }
-    rc = mf->plan.build(pf, pl, pe);
+    rc = mf->plan.build(pf, pl, pe, st);
     if (rc != CTP_OK) return rc;
     mf->factored = true;
     CTP_CUDA(cudaStreamSynchronize(st));

@@ -1,89 +1,447 @@
 // solve_plan.cu -- the level-planned front-list solve and the residual helpers
 // of iterative refinement (declared in solve_plan.cuh).
+//
+// The solve is the front-by-front substitution of system.cu (eq. (1.2) applied
+// front by front: y = L11^{-1} b_f, b_rest -= L_rest y, z = D^{-1} y forward;
+// x_f = L11^{-T} (z - L_rest^T x_rest) backward), run one level of independent
+// panels per launch.  A level's work is cut into items (panel, chunk of 64
+// rows below the pivots) so that the FP64 products of a tall panel spread over
+// the SMs:
+//   forward   every item solves the panel's small triangular system itself
+//             (nothing is exchanged between CTAs), subtracts its rows' share
+//             from the variables below with atomics, and the panel's first
+//             item stores z in a per-panel buffer (not in X: other items of
+//             the panel still read b there);
+//   backward  every item writes the partial sums L_rest^T x_rest of its rows;
+//             the panel's last item to finish (a fenced counter, no waiting)
+//             adds them in chunk order and solves with L11^T.
 #include "solve_plan.cuh"
 
 namespace ctp {
 
+namespace {
+
+constexpr int kLT = 256;           // threads per item
+constexpr int kRC = 64;            // rows below the pivots per item
+constexpr int kLJ = 32;            // columns (forward) / rows (backward) of L11 staged at a time
+constexpr int kLD = kMaxP + 1;     // padded length of a staged column / row of L11
+constexpr int kWork = kLJ * kLD;   // doubles of the staging / reduction area
+
+// A panel of the plan.  pvar[q] = rows[perm[q]] (q < p): the variable at
+// position q after pivoting; rows[r] for r >= p.  zoff, poff count doubles
+// per right-hand side.
+struct LvFront {
+    const double *L;
+    int64_t ldl;
+    int64_t n;
+    const int32_t *rows;
+    const int32_t *pvar;
+    const int32_t *piv;
+    const double *D;
+    int64_t zoff;  // z of the panel: Z[zoff * nrhs + r * e + q]
+    int64_t poff;  // partial sums: part[poff * nrhs + (c * nrhs + r) * e + j] (level-local)
+    int32_t e, p, nch, pad;
+};
+
+template <int RG>
+struct LvShape {
+    static constexpr int kRGP = RG == 1 ? 1 : RG + 1;  // padded stride of reduction rows
+    static constexpr size_t kSmem = sizeof(double) * ((size_t)RG * kMaxP + kWork);
+    static_assert(4 * kRC * kRGP <= kWork, "forward reduction area");
+    static_assert(kRC * RG + kLJ * (kRC + 1) + kLT * kRGP <= kWork, "backward partial-sum area");
+};
+
+__device__ __forceinline__ int row_var(const LvFront &f, int64_t r) {
+    return r < f.p ? f.pvar[r] : f.rows[r];
+}
+
+// z = D^{-1} y for pivot q (1x1, either column of a 2x2 block, or a zero pivot -> 0).
+__device__ __forceinline__ double d_solve(const LvFront &f, const int *pk, const double *y, int q) {
+    const int k = pk[q];
+    if (k == CTP_PIVKIND_1X1) return y[q] / f.D[2 * q];
+    if (k == CTP_PIVKIND_2X2_FIRST || k == CTP_PIVKIND_2X2_SECOND) {
+        const int a = (k == CTP_PIVKIND_2X2_FIRST) ? q : q - 1;
+        const double d11 = f.D[2 * a], d21 = f.D[2 * a + 1], d22 = f.D[2 * a + 2];
+        const double det = d11 * d22 - d21 * d21;
+        return (k == CTP_PIVKIND_2X2_FIRST) ? (d22 * y[a] - d21 * y[a + 1]) / det
+                                            : (d11 * y[a + 1] - d21 * y[a]) / det;
+    }
+    return 0.0;
+}
+
+// L11(i, j) as the substitutions use it: strictly below the diagonal, except
+// the (j+1, j) slot of a 2x2 block, which holds D.
+__device__ __forceinline__ double l11(const LvFront &f, const int *pk, int i, int j) {
+    if (i <= j || (i == j + 1 && pk[j] == CTP_PIVKIND_2X2_FIRST)) return 0.0;
+    return f.L[(int64_t)j * f.ldl + i];
+}
+
+template <int RG>
+__global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ F, const int2 *__restrict__ items,
+                                                    double *X, int64_t ldx, int nrhs, double *__restrict__ Z) {
+    constexpr int RGP = LvShape<RG>::kRGP;
+    extern __shared__ double sm[];
+    double *sy = sm;                // [RG][kMaxP]: b, then y, of the pivot variables
+    double *wk = sm + RG * kMaxP;   // L11 columns [kLJ][kLD], then the slice sums [4][kRC][RGP]
+    __shared__ int pvar[kMaxP], pk[kMaxP], rvar[kRC];
+    const int2 it = items[blockIdx.x];
+    const LvFront f = F[it.x];
+    const int e = f.e;
+    if (e == 0) return;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int64_t rbase = e + (int64_t)it.y * kRC;
+    const int nr = (int)max((int64_t)0, min((int64_t)kRC, f.n - rbase));
+    for (int q = t; q < e; q += kLT) {
+        pvar[q] = f.pvar[q];
+        pk[q] = f.piv[q];
+    }
+    if (t < nr) rvar[t] = row_var(f, rbase + t);
+    const int rl = t & (kRC - 1), sl = t / kRC;  // this thread's row of the chunk; its slice of the columns
+    for (int g0 = 0; g0 < nrhs; g0 += RG) {
+        const int ng = min(RG, nrhs - g0);
+        __syncthreads();
+        for (int idx = t; idx < ng * e; idx += kLT) {
+            const int r = idx / e, q = idx - r * e;
+            sy[r * kMaxP + q] = X[(int64_t)(g0 + r) * ldx + pvar[q]];
+        }
+        // y = L11^{-1} b: warp w takes right-hand sides w, w + 8, ...; lanes take rows
+        for (int j0 = 0; j0 < e; j0 += kLJ) {
+            const int nj = min(kLJ, e - j0);
+            __syncthreads();
+            for (int idx = t; idx < nj * e; idx += kLT) {
+                const int jj = idx / e, i = idx - jj * e;
+                wk[jj * kLD + i] = l11(f, pk, i, j0 + jj);
+            }
+            __syncthreads();
+            for (int r = warp; r < ng; r += kLT / 32) {
+                double *y = sy + r * kMaxP;
+                for (int jj = 0; jj < nj; jj++) {
+                    const int j = j0 + jj;
+                    const double yj = y[j];
+                    for (int i = j + 1 + lane; i < e; i += 32) y[i] -= wk[jj * kLD + i] * yj;
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+        if (it.y == 0)
+            for (int idx = t; idx < ng * e; idx += kLT) {
+                const int r = idx / e, q = idx - r * e;
+                Z[f.zoff * nrhs + (int64_t)(g0 + r) * e + q] = d_solve(f, pk, sy + r * kMaxP, q);
+            }
+        if (nr == 0) continue;
+        // rows below: b(var(row)) -= L(row, 0:e) y; slice sl takes the columns j = sl mod 4
+        double acc[RG];
+#pragma unroll
+        for (int r = 0; r < RG; r++) acc[r] = 0.0;
+        if (rl < nr) {
+            const double *lp = f.L + rbase + rl;
+            int j = sl;
+            for (; j + 12 < e; j += 16) {
+                const double l0 = lp[(int64_t)j * f.ldl], l1 = lp[(int64_t)(j + 4) * f.ldl];
+                const double l2 = lp[(int64_t)(j + 8) * f.ldl], l3 = lp[(int64_t)(j + 12) * f.ldl];
+#pragma unroll
+                for (int r = 0; r < RG; r++) {
+                    const double *y = sy + r * kMaxP;
+                    acc[r] += l0 * y[j];
+                    acc[r] += l1 * y[j + 4];
+                    acc[r] += l2 * y[j + 8];
+                    acc[r] += l3 * y[j + 12];
+                }
+            }
+            for (; j < e; j += 4) {
+                const double l0 = lp[(int64_t)j * f.ldl];
+#pragma unroll
+                for (int r = 0; r < RG; r++) acc[r] += l0 * sy[r * kMaxP + j];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RG; r++) wk[(sl * kRC + rl) * RGP + r] = acc[r];
+        __syncthreads();
+        for (int idx = t; idx < ng * nr; idx += kLT) {
+            const int r = idx / nr, q = idx - r * nr;
+            double v = wk[q * RGP + r];
+            v += wk[(kRC + q) * RGP + r];
+            v += wk[(2 * kRC + q) * RGP + r];
+            v += wk[(3 * kRC + q) * RGP + r];
+            atomicAdd(X + (int64_t)(g0 + r) * ldx + rvar[q], -v);  // panels of a level may share rows below
+        }
+    }
+}
+
+// Sums over this item's rows of L(row, j) x(var(row), g0 + r) for every pivot
+// column j: into part (out_part != nullptr) or subtracted from sz[r][j].
+template <int RG>
+__device__ __forceinline__ void chunk_sums(const LvFront &f, const int *rvar, int64_t rbase, int nr, const double *X,
+                                           int64_t ldx, int g0, int ng, double *wk, double *out_part, int nrhs,
+                                           int chunk, double *sz) {
+    constexpr int RGP = LvShape<RG>::kRGP;
+    constexpr int kS = kLT / kLJ, kRS = kRC / kS;  // row slices, rows per slice
+    double *xs = wk;                      // [kRC][RG]
+    double *ls = xs + kRC * RG;           // [kLJ][kRC + 1]: L(rbase + row, j0 + jj)
+    double *red = ls + kLJ * (kRC + 1);   // [kS][kLJ][RGP]
+    const int e = f.e, t = threadIdx.x, jj = t % kLJ, s = t / kLJ;
+    __syncthreads();
+    for (int idx = t; idx < kRC * RG; idx += kLT) {
+        const int row = idx / RG, r = idx - row * RG;
+        xs[idx] = (row < nr && r < ng) ? X[(int64_t)(g0 + r) * ldx + rvar[row]] : 0.0;
+    }
+    for (int j0 = 0; j0 < e; j0 += kLJ) {
+        const int nj = min(kLJ, e - j0);
+        __syncthreads();
+        for (int idx = t; idx < nj * kRC; idx += kLT) {
+            const int c = idx / kRC, row = idx - c * kRC;
+            ls[c * (kRC + 1) + row] = row < nr ? f.L[(int64_t)(j0 + c) * f.ldl + rbase + row] : 0.0;
+        }
+        __syncthreads();
+        double acc[RG];
+#pragma unroll
+        for (int r = 0; r < RG; r++) acc[r] = 0.0;
+        if (jj < nj) {
+#pragma unroll
+            for (int k = 0; k < kRS; k++) {
+                const int row = s * kRS + k;
+                const double l = ls[jj * (kRC + 1) + row];
+#pragma unroll
+                for (int r = 0; r < RG; r++) acc[r] += l * xs[row * RG + r];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RG; r++) red[(s * kLJ + jj) * RGP + r] = acc[r];
+        __syncthreads();
+        for (int idx = t; idx < ng * nj; idx += kLT) {
+            const int r = idx / nj, c = idx - r * nj;
+            double v = 0.0;
+#pragma unroll
+            for (int s2 = 0; s2 < kS; s2++) v += red[(s2 * kLJ + c) * RGP + r];
+            if (out_part != nullptr)
+                out_part[((int64_t)chunk * nrhs + g0 + r) * e + j0 + c] = v;
+            else
+                sz[r * kMaxP + j0 + c] -= v;
+        }
+    }
+}
+
+template <int RG>
+__global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__ F, const int2 *__restrict__ items,
+                                                     double *X, int64_t ldx, int nrhs, const double *__restrict__ Z,
+                                                     double *part, int *cnt) {
+    extern __shared__ double sm[];
+    double *sz = sm;               // [RG][kMaxP]: z - L_rest^T x_rest, then x, of the pivot variables
+    double *wk = sm + RG * kMaxP;  // partial sums; then rows of L11 [kLJ][kLD]
+    __shared__ int pvar[kMaxP], pk[kMaxP], rvar[kRC];
+    __shared__ int last;
+    const int2 it = items[blockIdx.x];
+    const LvFront f = F[it.x];
+    const int e = f.e;
+    if (e == 0) return;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int64_t rbase = e + (int64_t)it.y * kRC;
+    const int nr = (int)max((int64_t)0, min((int64_t)kRC, f.n - rbase));
+    for (int q = t; q < e; q += kLT) {
+        pvar[q] = f.pvar[q];
+        pk[q] = f.piv[q];
+    }
+    if (t < nr) rvar[t] = row_var(f, rbase + t);
+    double *fpart = part + f.poff * nrhs;
+    if (f.nch > 1) {
+        for (int g0 = 0; g0 < nrhs; g0 += RG)
+            chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, min(RG, nrhs - g0), wk, fpart, nrhs, it.y, nullptr);
+        // the last item of the panel to get here finishes it
+        __threadfence();
+        __syncthreads();
+        if (t == 0) last = atomicAdd(cnt + it.x, 1) == f.nch - 1;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        if (t == 0) cnt[it.x] = 0;  // ready for the next solve
+    }
+    for (int g0 = 0; g0 < nrhs; g0 += RG) {
+        const int ng = min(RG, nrhs - g0);
+        __syncthreads();
+        for (int idx = t; idx < ng * e; idx += kLT) {
+            const int r = idx / e, q = idx - r * e;
+            double v = Z[f.zoff * nrhs + (int64_t)(g0 + r) * e + q];
+            if (f.nch > 1)
+                for (int c = 0; c < f.nch; c++) v -= __ldcg(fpart + ((int64_t)c * nrhs + g0 + r) * e + q);
+            sz[r * kMaxP + q] = v;
+        }
+        if (f.nch == 1 && nr > 0) chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, ng, wk, nullptr, nrhs, 0, sz);
+        // L11^T x = z from the last pivot up, kLJ rows of L11 staged at a time;
+        // warp w takes right-hand sides w, w + 8, ...; lanes take columns
+        for (int i1 = e; i1 > 0; i1 -= kLJ) {
+            const int i0 = max(0, i1 - kLJ), ni = i1 - i0;
+            __syncthreads();
+            for (int idx = t; idx < ni * i1; idx += kLT) {
+                const int j = idx / ni, ii = idx - j * ni;
+                wk[ii * kLD + j] = l11(f, pk, i0 + ii, j);
+            }
+            __syncthreads();
+            for (int r = warp; r < ng; r += kLT / 32) {
+                double *z = sz + r * kMaxP;
+                for (int ii = ni - 1; ii >= 0; ii--) {
+                    const int i = i0 + ii;
+                    const double xi = z[i];
+                    for (int j = lane; j < i; j += 32) z[j] -= wk[ii * kLD + j] * xi;
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+        for (int idx = t; idx < ng * e; idx += kLT) {
+            const int r = idx / e, q = idx - r * e;
+            X[(int64_t)(g0 + r) * ldx + pvar[q]] = sz[r * kMaxP + q];
+        }
+    }
+}
+
+// pvar[off[k] + q] = rows[perm[q]] for the panels' fully-summed positions.
+__global__ void k_lv_pvar(const ctp_sfront *__restrict__ sf, const int64_t *__restrict__ off, int32_t *pvar) {
+    const ctp_sfront f = sf[blockIdx.x];
+    for (int q = threadIdx.x; q < f.p; q += blockDim.x) pvar[off[blockIdx.x] + q] = f.rows[f.perm[q]];
+}
+
+template <int RG>
+cudaError_t launch_level(bool forward, const LvFront *F, const int2 *items, int64_t nitems, double *X,
+                         int64_t ldx, int nrhs, double *Z, double *part, int *cnt, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_lv_forward<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)LvShape<RG>::kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_lv_backward<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LvShape<RG>::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (nitems == 0) return cudaSuccess;
+    if (forward)
+        k_lv_forward<RG><<<(unsigned)nitems, kLT, LvShape<RG>::kSmem, st>>>(F, items, X, ldx, nrhs, Z);
+    else
+        k_lv_backward<RG><<<(unsigned)nitems, kLT, LvShape<RG>::kSmem, st>>>(F, items, X, ldx, nrhs, Z, part, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_rg(bool forward, const LvFront *F, const int2 *items, int64_t nitems, double *X,
+                            int64_t ldx, int nrhs, double *Z, double *part, int *cnt, cudaStream_t st) {
+    if (nrhs <= 1) return launch_level<1>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    if (nrhs <= 2) return launch_level<2>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    if (nrhs <= 4) return launch_level<4>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    if (nrhs <= 8) return launch_level<8>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    return launch_level<16>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+}
+
+}  // namespace
+
 void SolvePlan::clear() {
     if (d_F) cudaFree(d_F);
     if (d_items) cudaFree(d_items);
-    if (d_poff) cudaFree(d_poff);
+    if (d_pvar) cudaFree(d_pvar);
+    if (d_cnt) cudaFree(d_cnt);
     d_F = nullptr;
     d_items = nullptr;
-    d_poff = nullptr;
+    d_pvar = nullptr;
+    d_cnt = nullptr;
     nf = nlev = 0;
-    lev_ptr.clear();
     item_ptr.clear();
-    max_fronts = 0;
-    max_chunks = 0;
+    z_per_rhs = 0;
+    part_per_rhs = 0;
 }
 
 ctp_status SolvePlan::build(const std::vector<ctp_sfront> &fronts, const std::vector<int> &level,
-                            const std::vector<int32_t> &nelim) {
+                            const std::vector<int32_t> &nelim, cudaStream_t st) {
     clear();
     nf = (int)fronts.size();
     if (nf == 0) return CTP_OK;
+    std::vector<LvFront> lf(nf);
     std::vector<int2> items;
     std::vector<int64_t> poff(nf);
-    lev_ptr.push_back(0);
+    int64_t pv = 0, zo = 0, level_part = 0;
     item_ptr.push_back(0);
-    int64_t chunks_in_level = 0;
     for (int k = 0; k < nf; k++) {
+        const ctp_sfront &s = fronts[k];
         if (k > 0 && level[k] < level[k - 1]) return CTP_EINVAL;
+        if (nelim[k] < 0 || nelim[k] > s.p || s.p > kMaxP || s.n < s.p) return CTP_EINVAL;
         if (k > 0 && level[k] != level[k - 1]) {
-            lev_ptr.push_back(k);
             item_ptr.push_back((int64_t)items.size());
-            chunks_in_level = 0;
+            level_part = 0;
         }
-        const int local = k - lev_ptr.back();
-        const int64_t below = fronts[k].n - nelim[k];
-        const int64_t nch = (below + 255) / 256;
-        poff[k] = chunks_in_level;
-        for (int64_t c = 0; c < nch; c++) items.push_back(make_int2(local, (int)c));
-        chunks_in_level += nch;
-        max_chunks = chunks_in_level > max_chunks ? chunks_in_level : max_chunks;
+        LvFront &f = lf[k];
+        f.L = s.L;
+        f.ldl = s.ldl;
+        f.n = s.n;
+        f.rows = s.rows;
+        f.piv = s.piv;
+        f.D = s.D;
+        f.e = nelim[k];
+        f.p = s.p;
+        f.pad = 0;
+        poff[k] = pv;
+        pv += s.p;
+        f.zoff = zo;
+        zo += f.e;
+        const int64_t below = s.n - f.e;
+        const int64_t nch = below > 0 ? (below + kRC - 1) / kRC : 1;
+        if (nch > 0x7fffffffLL) return CTP_EINVAL;
+        f.nch = (int32_t)nch;
+        f.poff = level_part;
+        if (nch > 1) level_part += nch * f.e;
+        part_per_rhs = level_part > part_per_rhs ? level_part : part_per_rhs;
+        if (f.e > 0)
+            for (int64_t c = 0; c < nch; c++) items.push_back(make_int2(k, (int)c));
     }
-    lev_ptr.push_back(nf);
     item_ptr.push_back((int64_t)items.size());
-    nlev = (int)lev_ptr.size() - 1;
-    for (int l = 0; l < nlev; l++) {
-        const int nfl = lev_ptr[l + 1] - lev_ptr[l];
-        max_fronts = nfl > max_fronts ? nfl : max_fronts;
-    }
-    if (cudaMalloc(&d_F, sizeof(ctp_sfront) * nf) != cudaSuccess ||
-        cudaMalloc(&d_items, sizeof(int2) * (items.size() > 0 ? items.size() : 1)) != cudaSuccess ||
-        cudaMalloc(&d_poff, sizeof(int64_t) * nf) != cudaSuccess)
+    nlev = (int)item_ptr.size() - 1;
+    z_per_rhs = zo;
+    ctp_sfront *d_sf = nullptr;
+    int64_t *d_off = nullptr;
+    bool ok = cudaMalloc(&d_F, sizeof(LvFront) * nf) == cudaSuccess &&
+              cudaMalloc(&d_items, sizeof(int2) * (items.empty() ? 1 : items.size())) == cudaSuccess &&
+              cudaMalloc(&d_pvar, sizeof(int32_t) * (pv > 0 ? pv : 1)) == cudaSuccess &&
+              cudaMalloc(&d_cnt, sizeof(int) * nf) == cudaSuccess &&
+              cudaMalloc(&d_sf, sizeof(ctp_sfront) * nf) == cudaSuccess &&
+              cudaMalloc(&d_off, sizeof(int64_t) * nf) == cudaSuccess;
+    if (!ok) {
+        if (d_sf) cudaFree(d_sf);
+        if (d_off) cudaFree(d_off);
         return CTP_ENOMEM;
-    if (cudaMemcpy(d_F, fronts.data(), sizeof(ctp_sfront) * nf, cudaMemcpyHostToDevice) != cudaSuccess ||
-        (!items.empty() &&
-         cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
-        cudaMemcpy(d_poff, poff.data(), sizeof(int64_t) * nf, cudaMemcpyHostToDevice) != cudaSuccess)
-        return CTP_ECUDA;
-    return CTP_OK;
+    }
+    for (int k = 0; k < nf; k++) lf[k].pvar = d_pvar + poff[k];
+    ok = cudaMemcpy(d_F, lf.data(), sizeof(LvFront) * nf, cudaMemcpyHostToDevice) == cudaSuccess &&
+         (items.empty() ||
+          cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
+         cudaMemcpy(d_sf, fronts.data(), sizeof(ctp_sfront) * nf, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(d_off, poff.data(), sizeof(int64_t) * nf, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemsetAsync(d_cnt, 0, sizeof(int) * nf, st) == cudaSuccess;
+    if (ok) {
+        k_lv_pvar<<<nf, 128, 0, st>>>(d_sf, d_off, d_pvar);
+        ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    cudaFree(d_sf);
+    cudaFree(d_off);
+    return ok ? CTP_OK : CTP_ECUDA;
 }
 
 size_t SolvePlan::ws_bytes(int nrhs) const {
-    return align256(sizeof(double) * (size_t)(max_fronts > 0 ? max_fronts : 1) * kMaxP * nrhs) +
-           align256(sizeof(double) * (size_t)(max_chunks > 0 ? max_chunks : 1) * nrhs * kMaxP);
+    return align256(sizeof(double) * (size_t)(z_per_rhs > 0 ? z_per_rhs : 1) * nrhs) +
+           align256(sizeof(double) * (size_t)(part_per_rhs > 0 ? part_per_rhs : 1) * nrhs);
 }
 
 cudaError_t SolvePlan::solve(ctp_ctx *ctx, double *X, int64_t ldx, int nrhs, void *ws, cudaStream_t st) const {
-    double *Y = (double *)ws;
-    double *part = (double *)((char *)ws + align256(sizeof(double) * (size_t)(max_fronts > 0 ? max_fronts : 1) *
-                                                    kMaxP * nrhs));
+    double *Z = (double *)ws;
+    double *part = (double *)((char *)ws + align256(sizeof(double) * (size_t)(z_per_rhs > 0 ? z_per_rhs : 1) * nrhs));
+    const LvFront *F = (const LvFront *)d_F;
     for (int l = 0; l < nlev; l++) {
-        const int f0 = lev_ptr[l], nfl = lev_ptr[l + 1] - f0;
         cudaError_t e = timed(ctx, K_SYS_FWD, st, [&] {
-            return launch_sys_level_forward(d_F + f0, nfl, d_items + item_ptr[l], item_ptr[l + 1] - item_ptr[l], X,
-                                            ldx, nrhs, Y, st);
+            return launch_level_rg(true, F, d_items + item_ptr[l], item_ptr[l + 1] - item_ptr[l], X, ldx, nrhs, Z,
+                                   part, d_cnt, st);
         });
         if (e != cudaSuccess) return e;
     }
     for (int l = nlev - 1; l >= 0; l--) {
-        const int f0 = lev_ptr[l], nfl = lev_ptr[l + 1] - f0;
         cudaError_t e = timed(ctx, K_SYS_BWD, st, [&] {
-            return launch_sys_level_backward(d_F + f0, nfl, d_items + item_ptr[l], item_ptr[l + 1] - item_ptr[l],
-                                             d_poff + f0, X, ldx, nrhs, part, st);
+            return launch_level_rg(false, F, d_items + item_ptr[l], item_ptr[l + 1] - item_ptr[l], X, ldx, nrhs, Z,
+                                   part, d_cnt, st);
         });
         if (e != cudaSuccess) return e;
     }

@@ -10,25 +10,27 @@
 
 namespace ctp {
 
-// Fronts in an elimination order grouped by level: level l holds fronts
-// [lev_ptr[l], lev_ptr[l+1]), none of which updates another's pivot rows.
+// Fronts in an elimination order grouped by level: the fronts of a level are
+// independent (none updates another's pivot rows), so a level is one launch
+// per sweep over items (front, chunk of rows below its pivots).
 struct SolvePlan {
     int nf = 0, nlev = 0;
-    std::vector<int> lev_ptr;
     std::vector<int64_t> item_ptr;  // items of level l: [item_ptr[l], item_ptr[l+1])
-    ctp_sfront *d_F = nullptr;
-    int2 *d_items = nullptr;
-    int64_t *d_poff = nullptr;
-    int max_fronts = 0;
-    int64_t max_chunks = 0;
+    void *d_F = nullptr;            // the fronts' descriptors (solve_plan.cu)
+    int2 *d_items = nullptr;        // (front, chunk)
+    int32_t *d_pvar = nullptr;      // per front: the variables of its pivot positions
+    int *d_cnt = nullptr;           // per front: items done in the backward sweep (0 between solves)
+    int64_t z_per_rhs = 0;          // doubles per right-hand side: z of every front
+    int64_t part_per_rhs = 0;       // doubles per right-hand side: the largest level's partial sums
     SolvePlan() = default;
     SolvePlan(const SolvePlan &) = delete;
     SolvePlan &operator=(const SolvePlan &) = delete;
     ~SolvePlan() { clear(); }
     void clear();
-    // fronts and their levels (nondecreasing) and eliminated counts
+    // fronts with their levels (nondecreasing) and eliminated counts; perm and
+    // rows are read on `st` (synchronised before returning)
     ctp_status build(const std::vector<ctp_sfront> &fronts, const std::vector<int> &level,
-                     const std::vector<int32_t> &nelim);
+                     const std::vector<int32_t> &nelim, cudaStream_t st);
     size_t ws_bytes(int nrhs) const;
     cudaError_t solve(ctp_ctx *ctx, double *X, int64_t ldx, int nrhs, void *ws, cudaStream_t st) const;
 };

@@ -92,7 +92,6 @@ __device__ __forceinline__ void dev_fwd_tri(const ctp_sfront &f, double *X, int6
 }
 
 // Rows below the pivots: b(var(r)) -= L(r, 0:e) y, one row per thread.
-template <bool kAtomic>
 __device__ __forceinline__ void dev_fwd_upd(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, const double *Y,
                                             int64_t chunk) {
     __shared__ double sy[kRB][kMaxP];
@@ -118,12 +117,7 @@ __device__ __forceinline__ void dev_fwd_upd(const ctp_sfront &f, double *X, int6
 #pragma unroll
             for (int rr = 0; rr < kRB; rr++) acc[rr] += l * sy[rr][j];
         }
-        for (int rr = 0; rr < nr; rr++) {
-            if (kAtomic)  // fronts of one level may share ancestor rows
-                atomicAdd(X + (int64_t)(r0 + rr) * ldx + v, -acc[rr]);
-            else
-                X[(int64_t)(r0 + rr) * ldx + v] -= acc[rr];
-        }
+        for (int rr = 0; rr < nr; rr++) X[(int64_t)(r0 + rr) * ldx + v] -= acc[rr];
     }
 }
 
@@ -229,7 +223,7 @@ __global__ void __launch_bounds__(kTh) k_sys_fwd_tri(ctp_sfront f, double *X, in
 }
 __global__ void __launch_bounds__(kTh) k_sys_fwd_upd(ctp_sfront f, double *X, int64_t ldx, int nrhs,
                                                      const double *Y) {
-    dev_fwd_upd<false>(f, X, ldx, nrhs, Y, blockIdx.x);
+    dev_fwd_upd(f, X, ldx, nrhs, Y, blockIdx.x);
 }
 __global__ void __launch_bounds__(kTh) k_sys_bwd_part(ctp_sfront f, const double *X, int64_t ldx,
                                                       int nrhs, double *part) {
@@ -238,31 +232,6 @@ __global__ void __launch_bounds__(kTh) k_sys_bwd_part(ctp_sfront f, const double
 __global__ void __launch_bounds__(kTh) k_sys_bwd_tri(ctp_sfront f, double *X, int64_t ldx, int nrhs,
                                                      const double *part) {
     dev_bwd_tri(f, X, ldx, nrhs, part);
-}
-
-// A level of independent fronts per launch (the planned solve): front i of the
-// level uses Y slot i and its own range of partial sums (part_off: first chunk
-// of the front within the level); the row updates of the
-// forward sweep are atomic since fronts of a level may share ancestor rows.
-// items[k] = (front index within the level, row chunk).
-__global__ void __launch_bounds__(kTh) k_sys_fwd_tri_lv(const ctp_sfront *F, double *X, int64_t ldx, int nrhs,
-                                                        double *Y) {
-    dev_fwd_tri(F[blockIdx.x], X, ldx, nrhs, Y + (int64_t)blockIdx.x * kMaxP * nrhs);
-}
-__global__ void __launch_bounds__(kTh) k_sys_fwd_upd_lv(const ctp_sfront *F, const int2 *items, double *X,
-                                                        int64_t ldx, int nrhs, const double *Y) {
-    const int2 it = items[blockIdx.x];
-    dev_fwd_upd<true>(F[it.x], X, ldx, nrhs, Y + (int64_t)it.x * kMaxP * nrhs, it.y);
-}
-__global__ void __launch_bounds__(kTh) k_sys_bwd_part_lv(const ctp_sfront *F, const int2 *items,
-                                                         const int64_t *part_off, const double *X, int64_t ldx,
-                                                         int nrhs, double *part) {
-    const int2 it = items[blockIdx.x];
-    dev_bwd_part(F[it.x], X, ldx, nrhs, part + part_off[it.x] * (int64_t)nrhs * kMaxP, it.y);
-}
-__global__ void __launch_bounds__(kTh) k_sys_bwd_tri_lv(const ctp_sfront *F, const int64_t *part_off, double *X,
-                                                        int64_t ldx, int nrhs, const double *part) {
-    dev_bwd_tri(F[blockIdx.x], X, ldx, nrhs, part + part_off[blockIdx.x] * (int64_t)nrhs * kMaxP);
 }
 
 // R -= M X (kAbs = false) or R += |M| 1 (kAbs = true: the row sums of |M|),
@@ -496,29 +465,6 @@ cudaError_t launch_sys_backward(const ctp_sfront &f, double *X, int64_t ldx, int
     const int64_t nch = (f.n + kTh - 1) / kTh;  // upper bound on the chunks below the pivots
     if (nch > 0) k_sys_bwd_part<<<(unsigned)nch, kTh, 0, st>>>(f, X, ldx, nrhs, part);
     k_sys_bwd_tri<<<1, kTh, kTriSmem, st>>>(f, X, ldx, nrhs, part);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sys_level_forward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
-                                     double *X, int64_t ldx, int nrhs, double *Y, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_sys_fwd_tri_lv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
-        cudaFuncSetAttribute(k_sys_bwd_tri_lv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
-        attr = true;
-    }
-    if (nfront == 0) return cudaSuccess;
-    k_sys_fwd_tri_lv<<<nfront, kTh, kTriSmem, st>>>(F, X, ldx, nrhs, Y);
-    if (nitems > 0) k_sys_fwd_upd_lv<<<(unsigned)nitems, kTh, 0, st>>>(F, items, X, ldx, nrhs, Y);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sys_level_backward(const ctp_sfront *F, int nfront, const int2 *items, int64_t nitems,
-                                      const int64_t *part_off, double *X, int64_t ldx, int nrhs, double *part,
-                                      cudaStream_t st) {
-    if (nfront == 0) return cudaSuccess;
-    if (nitems > 0) k_sys_bwd_part_lv<<<(unsigned)nitems, kTh, 0, st>>>(F, items, part_off, X, ldx, nrhs, part);
-    k_sys_bwd_tri_lv<<<nfront, kTh, kTriSmem, st>>>(F, part_off, X, ldx, nrhs, part);
     return cudaGetLastError();
 }
 
