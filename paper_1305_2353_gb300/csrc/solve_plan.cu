@@ -46,10 +46,19 @@ struct LvFront {
 template <int RG>
 struct LvShape {
     static constexpr int kRGP = RG == 1 ? 1 : RG + 1;  // padded stride of reduction rows
-    static constexpr size_t kSmem = sizeof(double) * ((size_t)RG * kMaxP + kWork);
-    static_assert(4 * kRC * kRGP <= kWork, "forward reduction area");
-    static_assert(kRC * RG + kLJ * (kRC + 1) + kLT * kRGP <= kWork, "backward partial-sum area");
+    // backward: x of the chunk's rows, L columns of the chunk, slice sums
+    static constexpr int kChunk = kRC * RG + kLJ * (kRC + 1) + kLT * kRGP;
+    static constexpr int kSmall = kLJ * (kLJ + 1);  // L11 of a panel with e <= kLJ, staged once
+    static constexpr int kArea = kWork > kChunk + kSmall ? kWork : kChunk + kSmall;
+    static constexpr size_t kSmem = sizeof(double) * ((size_t)RG * kMaxP + kArea);
+    static_assert(kSmall + 4 * kRC * kRGP <= kArea, "forward reduction area");
 };
+
+// Programmatic dependent launch: a level's kernel loads what no earlier kernel
+// writes (descriptors, L, pivot kinds) while the previous level runs, then
+// waits for it before touching X, Z or the partial sums.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ int row_var(const LvFront &f, int64_t r) {
     return r < f.p ? f.pvar[r] : f.rows[r];
@@ -80,9 +89,11 @@ template <int RG>
 __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ F, const int2 *__restrict__ items,
                                                     double *X, int64_t ldx, int nrhs, double *__restrict__ Z) {
     constexpr int RGP = LvShape<RG>::kRGP;
+    constexpr int kPre = kLJ / 4;   // update columns per thread loaded before the wait
     extern __shared__ double sm[];
     double *sy = sm;                // [RG][kMaxP]: b, then y, of the pivot variables
-    double *wk = sm + RG * kMaxP;   // L11 columns [kLJ][kLD], then the slice sums [4][kRC][RGP]
+    double *wk = sm + RG * kMaxP;   // L11 columns [kLJ][lds]; slice sums [4][kRC][RGP] after kSmall
+    double *red = wk + LvShape<RG>::kSmall;
     __shared__ int pvar[kMaxP], pk[kMaxP], rvar[kRC];
     const int2 it = items[blockIdx.x];
     const LvFront f = F[it.x];
@@ -91,12 +102,25 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int64_t rbase = e + (int64_t)it.y * kRC;
     const int nr = (int)max((int64_t)0, min((int64_t)kRC, f.n - rbase));
+    const int lds = e <= kLJ ? kLJ + 1 : kLD;
     for (int q = t; q < e; q += kLT) {
         pvar[q] = f.pvar[q];
         pk[q] = f.piv[q];
     }
     if (t < nr) rvar[t] = row_var(f, rbase + t);
     const int rl = t & (kRC - 1), sl = t / kRC;  // this thread's row of the chunk; its slice of the columns
+    const double *lp = f.L + rbase + rl;
+    double lpre[kPre];  // L(row, sl + 4k)
+#pragma unroll
+    for (int k = 0; k < kPre; k++) lpre[k] = (rl < nr && sl + 4 * k < e) ? lp[(int64_t)(sl + 4 * k) * f.ldl] : 0.0;
+    __syncthreads();
+    if (e <= kLJ)  // the whole L11 of a small panel, staged once
+        for (int idx = t; idx < e * e; idx += kLT) {
+            const int jj = idx / e, i = idx - jj * e;
+            wk[jj * lds + i] = l11(f, pk, i, jj);
+        }
+    pdl_trigger();
+    pdl_wait();
     for (int g0 = 0; g0 < nrhs; g0 += RG) {
         const int ng = min(RG, nrhs - g0);
         __syncthreads();
@@ -108,17 +132,19 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
         for (int j0 = 0; j0 < e; j0 += kLJ) {
             const int nj = min(kLJ, e - j0);
             __syncthreads();
-            for (int idx = t; idx < nj * e; idx += kLT) {
-                const int jj = idx / e, i = idx - jj * e;
-                wk[jj * kLD + i] = l11(f, pk, i, j0 + jj);
+            if (e > kLJ) {
+                for (int idx = t; idx < nj * e; idx += kLT) {
+                    const int jj = idx / e, i = idx - jj * e;
+                    wk[jj * lds + i] = l11(f, pk, i, j0 + jj);
+                }
+                __syncthreads();
             }
-            __syncthreads();
             for (int r = warp; r < ng; r += kLT / 32) {
                 double *y = sy + r * kMaxP;
                 for (int jj = 0; jj < nj; jj++) {
                     const int j = j0 + jj;
                     const double yj = y[j];
-                    for (int i = j + 1 + lane; i < e; i += 32) y[i] -= wk[jj * kLD + i] * yj;
+                    for (int i = j + 1 + lane; i < e; i += 32) y[i] -= wk[jj * lds + i] * yj;
                     __syncwarp();
                 }
             }
@@ -135,8 +161,14 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
 #pragma unroll
         for (int r = 0; r < RG; r++) acc[r] = 0.0;
         if (rl < nr) {
-            const double *lp = f.L + rbase + rl;
-            int j = sl;
+#pragma unroll
+            for (int k = 0; k < kPre; k++) {
+                const int j = sl + 4 * k;
+                if (j < e)
+#pragma unroll
+                    for (int r = 0; r < RG; r++) acc[r] += lpre[k] * sy[r * kMaxP + j];
+            }
+            int j = sl + 4 * kPre;
             for (; j + 12 < e; j += 16) {
                 const double l0 = lp[(int64_t)j * f.ldl], l1 = lp[(int64_t)(j + 4) * f.ldl];
                 const double l2 = lp[(int64_t)(j + 8) * f.ldl], l3 = lp[(int64_t)(j + 12) * f.ldl];
@@ -156,25 +188,34 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
             }
         }
 #pragma unroll
-        for (int r = 0; r < RG; r++) wk[(sl * kRC + rl) * RGP + r] = acc[r];
+        for (int r = 0; r < RG; r++) red[(sl * kRC + rl) * RGP + r] = acc[r];
         __syncthreads();
         for (int idx = t; idx < ng * nr; idx += kLT) {
             const int r = idx / nr, q = idx - r * nr;
-            double v = wk[q * RGP + r];
-            v += wk[(kRC + q) * RGP + r];
-            v += wk[(2 * kRC + q) * RGP + r];
-            v += wk[(3 * kRC + q) * RGP + r];
+            double v = red[q * RGP + r];
+            v += red[(kRC + q) * RGP + r];
+            v += red[(2 * kRC + q) * RGP + r];
+            v += red[(3 * kRC + q) * RGP + r];
             atomicAdd(X + (int64_t)(g0 + r) * ldx + rvar[q], -v);  // panels of a level may share rows below
         }
     }
 }
 
+// Stage columns j0 .. j0+nj-1 of L over this item's rows: ls[c][row].
+__device__ __forceinline__ void stage_chunk_cols(const LvFront &f, int64_t rbase, int nr, int j0, int nj, double *ls) {
+    for (int idx = threadIdx.x; idx < nj * kRC; idx += kLT) {
+        const int c = idx / kRC, row = idx - c * kRC;
+        ls[c * (kRC + 1) + row] = row < nr ? f.L[(int64_t)(j0 + c) * f.ldl + rbase + row] : 0.0;
+    }
+}
+
 // Sums over this item's rows of L(row, j) x(var(row), g0 + r) for every pivot
 // column j: into part (out_part != nullptr) or subtracted from sz[r][j].
+// pre0: columns 0 .. kLJ-1 are already staged in ls.
 template <int RG>
 __device__ __forceinline__ void chunk_sums(const LvFront &f, const int *rvar, int64_t rbase, int nr, const double *X,
-                                           int64_t ldx, int g0, int ng, double *wk, double *out_part, int nrhs,
-                                           int chunk, double *sz) {
+                                           int64_t ldx, int g0, int ng, double *wk, bool pre0, double *out_part,
+                                           int nrhs, int chunk, double *sz) {
     constexpr int RGP = LvShape<RG>::kRGP;
     constexpr int kS = kLT / kLJ, kRS = kRC / kS;  // row slices, rows per slice
     double *xs = wk;                      // [kRC][RG]
@@ -189,11 +230,10 @@ __device__ __forceinline__ void chunk_sums(const LvFront &f, const int *rvar, in
     for (int j0 = 0; j0 < e; j0 += kLJ) {
         const int nj = min(kLJ, e - j0);
         __syncthreads();
-        for (int idx = t; idx < nj * kRC; idx += kLT) {
-            const int c = idx / kRC, row = idx - c * kRC;
-            ls[c * (kRC + 1) + row] = row < nr ? f.L[(int64_t)(j0 + c) * f.ldl + rbase + row] : 0.0;
+        if (!(j0 == 0 && pre0)) {
+            stage_chunk_cols(f, rbase, nr, j0, nj, ls);
+            __syncthreads();
         }
-        __syncthreads();
         double acc[RG];
 #pragma unroll
         for (int r = 0; r < RG; r++) acc[r] = 0.0;
@@ -229,6 +269,7 @@ __global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__
     extern __shared__ double sm[];
     double *sz = sm;               // [RG][kMaxP]: z - L_rest^T x_rest, then x, of the pivot variables
     double *wk = sm + RG * kMaxP;  // partial sums; then rows of L11 [kLJ][kLD]
+    double *l11s = wk + LvShape<RG>::kChunk;  // L11 of a panel with e <= kLJ: [e][kLJ + 1] by rows
     __shared__ int pvar[kMaxP], pk[kMaxP], rvar[kRC];
     __shared__ int last;
     const int2 it = items[blockIdx.x];
@@ -243,10 +284,22 @@ __global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__
         pk[q] = f.piv[q];
     }
     if (t < nr) rvar[t] = row_var(f, rbase + t);
+    const bool small = e <= kLJ;
+    const bool pre0 = nr > 0;
+    if (pre0) stage_chunk_cols(f, rbase, nr, 0, min(kLJ, e), wk + kRC * RG);
+    __syncthreads();
+    if (small)
+        for (int idx = t; idx < e * e; idx += kLT) {
+            const int j = idx / e, ii = idx - j * e;
+            l11s[ii * (kLJ + 1) + j] = l11(f, pk, ii, j);
+        }
+    pdl_trigger();
+    pdl_wait();
     double *fpart = part + f.poff * nrhs;
     if (f.nch > 1) {
         for (int g0 = 0; g0 < nrhs; g0 += RG)
-            chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, min(RG, nrhs - g0), wk, fpart, nrhs, it.y, nullptr);
+            chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, min(RG, nrhs - g0), wk, pre0 && (small || g0 == 0),
+                           fpart, nrhs, it.y, nullptr);
         // the last item of the panel to get here finishes it
         __threadfence();
         __syncthreads();
@@ -266,23 +319,30 @@ __global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__
                 for (int c = 0; c < f.nch; c++) v -= __ldcg(fpart + ((int64_t)c * nrhs + g0 + r) * e + q);
             sz[r * kMaxP + q] = v;
         }
-        if (f.nch == 1 && nr > 0) chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, ng, wk, nullptr, nrhs, 0, sz);
+        if (f.nch == 1 && nr > 0)
+            chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, ng, wk, pre0 && (small || g0 == 0), nullptr, nrhs, 0, sz);
         // L11^T x = z from the last pivot up, kLJ rows of L11 staged at a time;
         // warp w takes right-hand sides w, w + 8, ...; lanes take columns
         for (int i1 = e; i1 > 0; i1 -= kLJ) {
             const int i0 = max(0, i1 - kLJ), ni = i1 - i0;
+            const double *rowsL = l11s;
+            int ldr = kLJ + 1;
             __syncthreads();
-            for (int idx = t; idx < ni * i1; idx += kLT) {
-                const int j = idx / ni, ii = idx - j * ni;
-                wk[ii * kLD + j] = l11(f, pk, i0 + ii, j);
+            if (!small) {
+                for (int idx = t; idx < ni * i1; idx += kLT) {
+                    const int j = idx / ni, ii = idx - j * ni;
+                    wk[ii * kLD + j] = l11(f, pk, i0 + ii, j);
+                }
+                __syncthreads();
+                rowsL = wk;
+                ldr = kLD;
             }
-            __syncthreads();
             for (int r = warp; r < ng; r += kLT / 32) {
                 double *z = sz + r * kMaxP;
                 for (int ii = ni - 1; ii >= 0; ii--) {
                     const int i = i0 + ii;
                     const double xi = z[i];
-                    for (int j = lane; j < i; j += 32) z[j] -= wk[ii * kLD + j] * xi;
+                    for (int j = lane; j < i; j += 32) z[j] -= rowsL[ii * ldr + j] * xi;
                     __syncwarp();
                 }
             }
@@ -315,11 +375,18 @@ cudaError_t launch_level(bool forward, const LvFront *F, const int2 *items, int6
         attr = true;
     }
     if (nitems == 0) return cudaSuccess;
-    if (forward)
-        k_lv_forward<RG><<<(unsigned)nitems, kLT, LvShape<RG>::kSmem, st>>>(F, items, X, ldx, nrhs, Z);
-    else
-        k_lv_backward<RG><<<(unsigned)nitems, kLT, LvShape<RG>::kSmem, st>>>(F, items, X, ldx, nrhs, Z, part, cnt);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nitems);
+    cfg.blockDim = dim3(kLT);
+    cfg.dynamicSmemBytes = LvShape<RG>::kSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr_pdl[1];
+    attr_pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr_pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr_pdl;
+    cfg.numAttrs = 1;
+    if (forward) return cudaLaunchKernelEx(&cfg, k_lv_forward<RG>, F, items, X, ldx, nrhs, Z);
+    return cudaLaunchKernelEx(&cfg, k_lv_backward<RG>, F, items, X, ldx, nrhs, (const double *)Z, part, cnt);
 }
 
 cudaError_t launch_level_rg(bool forward, const LvFront *F, const int2 *items, int64_t nitems, double *X,

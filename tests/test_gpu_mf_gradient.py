@@ -118,9 +118,12 @@ def test_mf_gradient_finite_differences(ctx, prec):
 
 def test_mf_backward_after_refactor(ctx):
     """A second solve with other values before the first backward: the first
-    backward still uses its own factors (it factors its values again)."""
+    backward still uses its own factors (it factors its values again).  The
+    grid is 7^3: with k + 1 divisible by 3 (8^3, 32^3) the shift 3 is an exact
+    eigenvalue of the 7-point Laplacian (3 (2 - 2 cos(pi/3))), the system is
+    singular and its gradients are rounding noise."""
     from paper_1305_2353_gb300 import ctp
-    cp, ri, v, N, perm, blocks = _problem(8, leaf=16)
+    cp, ri, v, N, perm, blocks = _problem(7, leaf=16)
     B = np.random.default_rng(6).standard_normal((N, 2))
     solver = ctp.SparseSymSolver(ctx, cp, ri, perm, blocks)
     v1 = torch.tensor(v, device="cuda", requires_grad=True)
