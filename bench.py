@@ -47,18 +47,18 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # number of S entries; the Solve's is proportional to the rows of A21): see
 # profiles/ for the captures.
 NCU_TRAFFIC = {
-    # ncu --set full, n=20000 p=256 relaxed, S FP64 lower-packed: 140.90 MB read +
-    # 1512.81 MB written for m(m+1)/2 = 194,921,640 entries
-    "form_fp64": {"file": "form.cu", "sha1": "042a4c6f69b873290d71454b2f87dbb210410b01",
-                  "unit": "packed_entry", "bytes_per_unit": (140.898048e6 + 1512.805e6) / 194921640},
+    # ncu --set full, n=20000 p=256 relaxed, S FP64 lower-packed: 163.76 MB read +
+    # 1513.69 MB written for m(m+1)/2 = 194,921,640 entries
+    "form_fp64": {"file": "form.cu", "sha1": "798d569f67e7e8f417e75b162e2622426e55e05e",
+                  "unit": "packed_entry", "bytes_per_unit": (163.760384e6 + 1513.690e6) / 194921640},
     # ncu --set full, n=40000 p=256 relaxed, split BF16, S FP32 in 128x128 blocks:
-    # 165.73 MB read + 3118.06 MB written for 48,516 blocks of 16,384 entries
-    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "33e0e4154a47663e76edc12346e4a57da6e7108e",
-                       "unit": "tiled_entry", "bytes_per_unit": (165.732608e6 + 3118.057e6) / (48516 * 16384)},
+    # 229.67 MB read + 3118.82 MB written for 48,516 blocks of 16,384 entries
+    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "bfa43a4a21fb66e6600646343c32937c25a38cbf",
+                       "unit": "tiled_entry", "bytes_per_unit": (229.674240e6 + 3118.824e6) / (48516 * 16384)},
     # ncu --set full, n=40000 p=256 relaxed, tensor-core Solve before a split-BF16
-    # Form (prep + gather + GEMM): 144.93 MB read + 124.22 MB written for 39,744 rows
-    "solve_tc": {"file": "solve_tc.cu", "sha1": "8b2073a626b858775d57974a529316deb6caa083", "prec": "bf16x3",
-                 "unit": "row", "bytes_per_unit": (144.928256e6 + 124.223e6) / 39744},
+    # Form (prep + gather + GEMM): 145.23 MB read + 124.64 MB written for 39,744 rows
+    "solve_tc": {"file": "solve_tc.cu", "sha1": "b625943159839444dd75e137c8f4021fbb3e3789", "prec": "bf16x3",
+                 "unit": "row", "bytes_per_unit": (145.232896e6 + 124.638e6) / 39744},
 }
 
 
