@@ -74,7 +74,11 @@ struct Cfg {
     static constexpr uint32_t StageA = PieceA * P + (kResident ? 0 : PieceB * P);
     static constexpr uint32_t StageB = PieceB * P;           // resident block, per K block
     static constexpr size_t ResidentBytes = kResident ? (size_t)kMaxKB * StageB : 0;
-    static constexpr uint32_t TmemCols = 2 * BN;             // two FP32 accumulators
+    // Split forms: one MMA of N = 256 takes the hi and next pieces of L21 together
+    // (they are contiguous), so a tile's accumulator is 256 columns wide and the
+    // epilogue adds its two 128-column halves.
+    static constexpr int AccN = 256;
+    static constexpr uint32_t TmemCols = 2 * AccN;           // two FP32 accumulators
 };
 constexpr size_t kSmemBody = (size_t)kMaxKB * kStageB + (size_t)kStages * kStageA;
 static_assert(Cfg<1>::ResidentBytes + Cfg<1>::Stages * Cfg<1>::StageA <= kSmemBody, "smem P=1");
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     tc_fence_after();
     const uint32_t tmem = bars.tmem_base;
     const uint32_t idesc = idesc_bf16(kBM, BN);
+    const uint32_t idesc_w = idesc_bf16(kBM, 256);
 
     if (warp == 0) {
         // ---------------- TMA producer: the L21 block of the current column block
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     bphase ^= 1u;
                     cur_key = x.key;
                 }
-                const uint32_t dt = tmem + (uint32_t)(acc * BN);
+                const uint32_t dt = tmem + (uint32_t)(acc * C::AccN);
                 for (int kb = 0; kb < x.KB; kb++) {
                     if (!mbar_wait(&bars.full[stage], phase, &bars.abort)) {
                         ok = false;
@@ -338,18 +343,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
                     for (int kk = 0; kk < kBK / kUmmaK; kk++) {
                         // advance 16 BF16 = 32 bytes along K inside the swizzled rows;
-                        // products of pieces i, j with i + j <= P - 1
+                        // products of pieces i, j with i + j <= P - 1.  Split forms:
+                        // B pieces 0 and 1 side by side as one N = 256 operand, so
+                        //   P = 2: [hi*hi | hi*lo] + lo*hi into the first half;
+                        //   P = 3: [hi*hi | hi*mid] + [mid*hi | mid*mid], then
+                        //          hi*lo and lo*hi into the first half.
                         const uint64_t a1 = sdesc(a0 + kk * 32), b1 = sdesc(b0 + kk * 32);
-                        umma_bf16(dt, a1, b1, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                        if (P >= 2) {
+                        const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+                        if (P == 1) {
+                            umma_bf16(dt, a1, b1, idesc, first);
+                        } else {
                             const uint64_t a2 = sdesc(a0 + C::PieceA + kk * 32);
-                            const uint64_t b2 = sdesc(b0 + C::PieceB + kk * 32);
-                            umma_bf16(dt, a1, b2, idesc, 1u);
-                            umma_bf16(dt, a2, b1, idesc, 1u);
-                            if (P >= 3) {
+                            umma_bf16(dt, a1, b1, idesc_w, first);
+                            if (P == 2) {
+                                umma_bf16(dt, a2, b1, idesc, 1u);
+                            } else {
+                                umma_bf16(dt, a2, b1, idesc_w, 1u);
                                 umma_bf16(dt, a1, sdesc(b0 + 2 * C::PieceB + kk * 32), idesc, 1u);
                                 umma_bf16(dt, sdesc(a0 + 2 * C::PieceA + kk * 32), b1, idesc, 1u);
-                                umma_bf16(dt, a2, b2, idesc, 1u);
                             }
                         }
                     }
@@ -412,10 +423,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (int c = 0; c < BN / 64; c += 2) {
                 uint32_t r[64];
                 const uint32_t taddr =
-                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + half * (BN / 2) + c * 32);
+                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C::AccN + half * (BN / 2) + c * 32);
                 tmem_ld32_nowait(taddr, *reinterpret_cast<uint32_t(*)[32]>(&r[0]));
                 tmem_ld32_nowait(taddr + 32, *reinterpret_cast<uint32_t(*)[32]>(&r[32]));
                 tmem_wait_ld();
+                if (P > 1) {  // the accumulator's second half holds the other products
+#pragma unroll
+                    for (int hh = 0; hh < 64; hh += 32) {
+                        uint32_t t2[32];
+                        tmem_ld32_nowait(taddr + 128 + hh, t2);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int xx = 0; xx < 32; xx++)
+                            r[hh + xx] = __float_as_uint(__uint_as_float(r[hh + xx]) + __uint_as_float(t2[xx]));
+                    }
+                }
                 if (KB == 0) {
 #pragma unroll
                     for (int xx = 0; xx < 64; xx++) r[xx] = 0u;
