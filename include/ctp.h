@@ -442,7 +442,12 @@ ctp_status ctp_mf_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *X,
 ctp_status ctp_mf_adjoint_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *G, int64_t ldg,
                                 void *workspace, size_t ws_bytes, void *stream);
 /* ctp_refine_csc with the planned solve (arguments as there; colptr, rowind,
- * val: the matrix in device memory). */
+ * val: the matrix in device memory).  When the last ctp_mf_factor ran with a
+ * tensor-core Form (opt->prec other than CTP_FP64), the solves inside the
+ * refinement compute in FP32 arithmetic on the FP64 factors: X, the residuals
+ * and the backward errors stay FP64 (Section 7), and the refinement contracts
+ * the solves' rounding together with the factorization's.  After an FP64
+ * factorization the solves are FP64. */
 ctp_status ctp_mf_refine_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes);
 ctp_status ctp_mf_refine(ctp_ctx *ctx, const ctp_mf *mf, const int64_t *colptr, const int32_t *rowind,
                          const double *val, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,

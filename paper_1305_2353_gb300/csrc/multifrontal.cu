@@ -59,6 +59,7 @@ struct ctp_mf {
     std::vector<int32_t> panel_block;  // block of each panel
     SolvePlan plan;  // the panels grouped into levels of independent panels
     bool factored = false;
+    bool mixed = false;  // the last factorization's Form ran on the tensor cores
     ~ctp_mf() {
         if (d_ci) cudaFree(d_ci);
         if (d_cj) cudaFree(d_cj);
@@ -645,6 +646,7 @@ ctp_status ctp_mf_factor(ctp_ctx *ctx, ctp_mf *mf, const double *val, const ctp_
     rc = mf->plan.build(pf, pl, pe, st);
     if (rc != CTP_OK) return rc;
     mf->factored = true;
+    mf->mixed = opt->prec != CTP_FP64;
     CTP_CUDA(cudaStreamSynchronize(st));
     return CTP_OK;
 }
@@ -691,7 +693,10 @@ ctp_status ctp_mf_refine(ctp_ctx *ctx, const ctp_mf *mf, const int64_t *colptr, 
     A.colptr = colptr;
     A.rowind = rowind;
     A.val = val;
-    auto solve = [&](double *Y, int64_t ldy, void *sws) { return mf->plan.solve(ctx, Y, ldy, nrhs, sws, st); };
+    // factors of a tensor-core Form: FP32 sweeps (the refinement corrects both errors)
+    auto solve = [&](double *Y, int64_t ldy, void *sws) {
+        return mf->plan.solve(ctx, Y, ldy, nrhs, sws, st, mf->mixed);
+    };
     return refine_core(ctx, solve, mf->plan.ws_bytes(nrhs), mf->N, A, nrhs, B, ldb, X, ldx, max_steps, tol,
                        berr_host, steps_host, workspace, ws_bytes, st);
 }

@@ -15,6 +15,10 @@
 //   backward  every item writes the partial sums L_rest^T x_rest of its rows;
 //             the panel's last item to finish (a fenced counter, no waiting)
 //             adds them in chunk order and solves with L11^T.
+// The sweeps compute in FP64, or in FP32 (the factors, D and X stay FP64 in
+// memory and are rounded as they are loaded; X is updated in FP64): the
+// correction solves of a refinement whose residuals are FP64 (Section 7) need
+// only to contract the error, and GB300's FP32 pipe is many times its FP64 one.
 #include "solve_plan.cuh"
 
 namespace ctp {
@@ -25,7 +29,7 @@ constexpr int kLT = 256;           // threads per item
 constexpr int kRC = 64;            // rows below the pivots per item
 constexpr int kLJ = 32;            // columns (forward) / rows (backward) of L11 staged at a time
 constexpr int kLD = kMaxP + 1;     // padded length of a staged column / row of L11
-constexpr int kWork = kLJ * kLD;   // doubles of the staging / reduction area
+constexpr int kWork = kLJ * kLD;   // elements of the staging / reduction area
 
 // A panel of the plan.  pvar[q] = rows[perm[q]] (q < p): the variable at
 // position q after pivoting; rows[r] for r >= p.  zoff, poff count doubles
@@ -43,14 +47,14 @@ struct LvFront {
     int32_t e, p, nch, pad;
 };
 
-template <int RG>
+template <typename T, int RG>
 struct LvShape {
     static constexpr int kRGP = RG == 1 ? 1 : RG + 1;  // padded stride of reduction rows
     // backward: x of the chunk's rows, L columns of the chunk, slice sums
     static constexpr int kChunk = kRC * RG + kLJ * (kRC + 1) + kLT * kRGP;
     static constexpr int kSmall = kLJ * (kLJ + 1);  // L11 of a panel with e <= kLJ, staged once
     static constexpr int kArea = kWork > kChunk + kSmall ? kWork : kChunk + kSmall;
-    static constexpr size_t kSmem = sizeof(double) * ((size_t)RG * kMaxP + kArea);
+    static constexpr size_t kSmem = sizeof(T) * ((size_t)RG * kMaxP + kArea);
     static_assert(kSmall + 4 * kRC * kRGP <= kArea, "forward reduction area");
 };
 
@@ -65,35 +69,38 @@ __device__ __forceinline__ int row_var(const LvFront &f, int64_t r) {
 }
 
 // z = D^{-1} y for pivot q (1x1, either column of a 2x2 block, or a zero pivot -> 0).
-__device__ __forceinline__ double d_solve(const LvFront &f, const int *pk, const double *y, int q) {
+template <typename T>
+__device__ __forceinline__ T d_solve(const LvFront &f, const int *pk, const T *y, int q) {
     const int k = pk[q];
-    if (k == CTP_PIVKIND_1X1) return y[q] / f.D[2 * q];
+    if (k == CTP_PIVKIND_1X1) return y[q] / (T)f.D[2 * q];
     if (k == CTP_PIVKIND_2X2_FIRST || k == CTP_PIVKIND_2X2_SECOND) {
         const int a = (k == CTP_PIVKIND_2X2_FIRST) ? q : q - 1;
-        const double d11 = f.D[2 * a], d21 = f.D[2 * a + 1], d22 = f.D[2 * a + 2];
-        const double det = d11 * d22 - d21 * d21;
+        const T d11 = (T)f.D[2 * a], d21 = (T)f.D[2 * a + 1], d22 = (T)f.D[2 * a + 2];
+        const T det = d11 * d22 - d21 * d21;
         return (k == CTP_PIVKIND_2X2_FIRST) ? (d22 * y[a] - d21 * y[a + 1]) / det
                                             : (d11 * y[a + 1] - d21 * y[a]) / det;
     }
-    return 0.0;
+    return T(0);
 }
 
 // L11(i, j) as the substitutions use it: strictly below the diagonal, except
 // the (j+1, j) slot of a 2x2 block, which holds D.
-__device__ __forceinline__ double l11(const LvFront &f, const int *pk, int i, int j) {
-    if (i <= j || (i == j + 1 && pk[j] == CTP_PIVKIND_2X2_FIRST)) return 0.0;
-    return f.L[(int64_t)j * f.ldl + i];
+template <typename T>
+__device__ __forceinline__ T l11(const LvFront &f, const int *pk, int i, int j) {
+    if (i <= j || (i == j + 1 && pk[j] == CTP_PIVKIND_2X2_FIRST)) return T(0);
+    return (T)f.L[(int64_t)j * f.ldl + i];
 }
 
-template <int RG>
+template <typename T, int RG>
 __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ F, const int2 *__restrict__ items,
-                                                    double *X, int64_t ldx, int nrhs, double *__restrict__ Z) {
-    constexpr int RGP = LvShape<RG>::kRGP;
+                                                    double *X, int64_t ldx, int nrhs, T *__restrict__ Z) {
+    constexpr int RGP = LvShape<T, RG>::kRGP;
     constexpr int kPre = kLJ / 4;   // update columns per thread loaded before the wait
-    extern __shared__ double sm[];
-    double *sy = sm;                // [RG][kMaxP]: b, then y, of the pivot variables
-    double *wk = sm + RG * kMaxP;   // L11 columns [kLJ][lds]; slice sums [4][kRC][RGP] after kSmall
-    double *red = wk + LvShape<RG>::kSmall;
+    extern __shared__ __align__(16) unsigned char lv_smem[];
+    T *sm = reinterpret_cast<T *>(lv_smem);
+    T *sy = sm;                // [RG][kMaxP]: b, then y, of the pivot variables
+    T *wk = sm + RG * kMaxP;   // L11 columns [kLJ][lds]; slice sums [4][kRC][RGP] after kSmall
+    T *red = wk + LvShape<T, RG>::kSmall;
     __shared__ int pvar[kMaxP], pk[kMaxP], rvar[kRC];
     const int2 it = items[blockIdx.x];
     const LvFront f = F[it.x];
@@ -110,14 +117,14 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
     if (t < nr) rvar[t] = row_var(f, rbase + t);
     const int rl = t & (kRC - 1), sl = t / kRC;  // this thread's row of the chunk; its slice of the columns
     const double *lp = f.L + rbase + rl;
-    double lpre[kPre];  // L(row, sl + 4k)
+    T lpre[kPre];  // L(row, sl + 4k)
 #pragma unroll
-    for (int k = 0; k < kPre; k++) lpre[k] = (rl < nr && sl + 4 * k < e) ? lp[(int64_t)(sl + 4 * k) * f.ldl] : 0.0;
+    for (int k = 0; k < kPre; k++) lpre[k] = (rl < nr && sl + 4 * k < e) ? (T)lp[(int64_t)(sl + 4 * k) * f.ldl] : T(0);
     __syncthreads();
     if (e <= kLJ)  // the whole L11 of a small panel, staged once
         for (int idx = t; idx < e * e; idx += kLT) {
             const int jj = idx / e, i = idx - jj * e;
-            wk[jj * lds + i] = l11(f, pk, i, jj);
+            wk[jj * lds + i] = l11<T>(f, pk, i, jj);
         }
     pdl_trigger();
     pdl_wait();
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
         __syncthreads();
         for (int idx = t; idx < ng * e; idx += kLT) {
             const int r = idx / e, q = idx - r * e;
-            sy[r * kMaxP + q] = X[(int64_t)(g0 + r) * ldx + pvar[q]];
+            sy[r * kMaxP + q] = (T)X[(int64_t)(g0 + r) * ldx + pvar[q]];
         }
         // y = L11^{-1} b: warp w takes right-hand sides w, w + 8, ...; lanes take rows
         for (int j0 = 0; j0 < e; j0 += kLJ) {
@@ -135,15 +142,15 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
             if (e > kLJ) {
                 for (int idx = t; idx < nj * e; idx += kLT) {
                     const int jj = idx / e, i = idx - jj * e;
-                    wk[jj * lds + i] = l11(f, pk, i, j0 + jj);
+                    wk[jj * lds + i] = l11<T>(f, pk, i, j0 + jj);
                 }
                 __syncthreads();
             }
             for (int r = warp; r < ng; r += kLT / 32) {
-                double *y = sy + r * kMaxP;
+                T *y = sy + r * kMaxP;
                 for (int jj = 0; jj < nj; jj++) {
                     const int j = j0 + jj;
-                    const double yj = y[j];
+                    const T yj = y[j];
                     for (int i = j + 1 + lane; i < e; i += 32) y[i] -= wk[jj * lds + i] * yj;
                     __syncwarp();
                 }
@@ -153,13 +160,13 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
         if (it.y == 0)
             for (int idx = t; idx < ng * e; idx += kLT) {
                 const int r = idx / e, q = idx - r * e;
-                Z[f.zoff * nrhs + (int64_t)(g0 + r) * e + q] = d_solve(f, pk, sy + r * kMaxP, q);
+                Z[f.zoff * nrhs + (int64_t)(g0 + r) * e + q] = d_solve<T>(f, pk, sy + r * kMaxP, q);
             }
         if (nr == 0) continue;
         // rows below: b(var(row)) -= L(row, 0:e) y; slice sl takes the columns j = sl mod 4
-        double acc[RG];
+        T acc[RG];
 #pragma unroll
-        for (int r = 0; r < RG; r++) acc[r] = 0.0;
+        for (int r = 0; r < RG; r++) acc[r] = T(0);
         if (rl < nr) {
 #pragma unroll
             for (int k = 0; k < kPre; k++) {
@@ -170,11 +177,11 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
             }
             int j = sl + 4 * kPre;
             for (; j + 12 < e; j += 16) {
-                const double l0 = lp[(int64_t)j * f.ldl], l1 = lp[(int64_t)(j + 4) * f.ldl];
-                const double l2 = lp[(int64_t)(j + 8) * f.ldl], l3 = lp[(int64_t)(j + 12) * f.ldl];
+                const T l0 = (T)lp[(int64_t)j * f.ldl], l1 = (T)lp[(int64_t)(j + 4) * f.ldl];
+                const T l2 = (T)lp[(int64_t)(j + 8) * f.ldl], l3 = (T)lp[(int64_t)(j + 12) * f.ldl];
 #pragma unroll
                 for (int r = 0; r < RG; r++) {
-                    const double *y = sy + r * kMaxP;
+                    const T *y = sy + r * kMaxP;
                     acc[r] += l0 * y[j];
                     acc[r] += l1 * y[j + 4];
                     acc[r] += l2 * y[j + 8];
@@ -182,7 +189,7 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
                 }
             }
             for (; j < e; j += 4) {
-                const double l0 = lp[(int64_t)j * f.ldl];
+                const T l0 = (T)lp[(int64_t)j * f.ldl];
 #pragma unroll
                 for (int r = 0; r < RG; r++) acc[r] += l0 * sy[r * kMaxP + j];
             }
@@ -192,40 +199,41 @@ __global__ void __launch_bounds__(kLT) k_lv_forward(const LvFront *__restrict__ 
         __syncthreads();
         for (int idx = t; idx < ng * nr; idx += kLT) {
             const int r = idx / nr, q = idx - r * nr;
-            double v = red[q * RGP + r];
+            T v = red[q * RGP + r];
             v += red[(kRC + q) * RGP + r];
             v += red[(2 * kRC + q) * RGP + r];
             v += red[(3 * kRC + q) * RGP + r];
-            atomicAdd(X + (int64_t)(g0 + r) * ldx + rvar[q], -v);  // panels of a level may share rows below
+            atomicAdd(X + (int64_t)(g0 + r) * ldx + rvar[q], -(double)v);  // panels of a level may share rows below
         }
     }
 }
 
 // Stage columns j0 .. j0+nj-1 of L over this item's rows: ls[c][row].
-__device__ __forceinline__ void stage_chunk_cols(const LvFront &f, int64_t rbase, int nr, int j0, int nj, double *ls) {
+template <typename T>
+__device__ __forceinline__ void stage_chunk_cols(const LvFront &f, int64_t rbase, int nr, int j0, int nj, T *ls) {
     for (int idx = threadIdx.x; idx < nj * kRC; idx += kLT) {
         const int c = idx / kRC, row = idx - c * kRC;
-        ls[c * (kRC + 1) + row] = row < nr ? f.L[(int64_t)(j0 + c) * f.ldl + rbase + row] : 0.0;
+        ls[c * (kRC + 1) + row] = row < nr ? (T)f.L[(int64_t)(j0 + c) * f.ldl + rbase + row] : T(0);
     }
 }
 
 // Sums over this item's rows of L(row, j) x(var(row), g0 + r) for every pivot
 // column j: into part (out_part != nullptr) or subtracted from sz[r][j].
 // pre0: columns 0 .. kLJ-1 are already staged in ls.
-template <int RG>
+template <typename T, int RG>
 __device__ __forceinline__ void chunk_sums(const LvFront &f, const int *rvar, int64_t rbase, int nr, const double *X,
-                                           int64_t ldx, int g0, int ng, double *wk, bool pre0, double *out_part,
-                                           int nrhs, int chunk, double *sz) {
-    constexpr int RGP = LvShape<RG>::kRGP;
+                                           int64_t ldx, int g0, int ng, T *wk, bool pre0, T *out_part,
+                                           int nrhs, int chunk, T *sz) {
+    constexpr int RGP = LvShape<T, RG>::kRGP;
     constexpr int kS = kLT / kLJ, kRS = kRC / kS;  // row slices, rows per slice
-    double *xs = wk;                      // [kRC][RG]
-    double *ls = xs + kRC * RG;           // [kLJ][kRC + 1]: L(rbase + row, j0 + jj)
-    double *red = ls + kLJ * (kRC + 1);   // [kS][kLJ][RGP]
+    T *xs = wk;                      // [kRC][RG]
+    T *ls = xs + kRC * RG;           // [kLJ][kRC + 1]: L(rbase + row, j0 + jj)
+    T *red = ls + kLJ * (kRC + 1);   // [kS][kLJ][RGP]
     const int e = f.e, t = threadIdx.x, jj = t % kLJ, s = t / kLJ;
     __syncthreads();
     for (int idx = t; idx < kRC * RG; idx += kLT) {
         const int row = idx / RG, r = idx - row * RG;
-        xs[idx] = (row < nr && r < ng) ? X[(int64_t)(g0 + r) * ldx + rvar[row]] : 0.0;
+        xs[idx] = (row < nr && r < ng) ? (T)X[(int64_t)(g0 + r) * ldx + rvar[row]] : T(0);
     }
     for (int j0 = 0; j0 < e; j0 += kLJ) {
         const int nj = min(kLJ, e - j0);
@@ -234,14 +242,14 @@ __device__ __forceinline__ void chunk_sums(const LvFront &f, const int *rvar, in
             stage_chunk_cols(f, rbase, nr, j0, nj, ls);
             __syncthreads();
         }
-        double acc[RG];
+        T acc[RG];
 #pragma unroll
-        for (int r = 0; r < RG; r++) acc[r] = 0.0;
+        for (int r = 0; r < RG; r++) acc[r] = T(0);
         if (jj < nj) {
 #pragma unroll
             for (int k = 0; k < kRS; k++) {
                 const int row = s * kRS + k;
-                const double l = ls[jj * (kRC + 1) + row];
+                const T l = ls[jj * (kRC + 1) + row];
 #pragma unroll
                 for (int r = 0; r < RG; r++) acc[r] += l * xs[row * RG + r];
             }
@@ -251,7 +259,7 @@ __device__ __forceinline__ void chunk_sums(const LvFront &f, const int *rvar, in
         __syncthreads();
         for (int idx = t; idx < ng * nj; idx += kLT) {
             const int r = idx / nj, c = idx - r * nj;
-            double v = 0.0;
+            T v = T(0);
 #pragma unroll
             for (int s2 = 0; s2 < kS; s2++) v += red[(s2 * kLJ + c) * RGP + r];
             if (out_part != nullptr)
@@ -262,14 +270,15 @@ __device__ __forceinline__ void chunk_sums(const LvFront &f, const int *rvar, in
     }
 }
 
-template <int RG>
+template <typename T, int RG>
 __global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__ F, const int2 *__restrict__ items,
-                                                     double *X, int64_t ldx, int nrhs, const double *__restrict__ Z,
-                                                     double *part, int *cnt) {
-    extern __shared__ double sm[];
-    double *sz = sm;               // [RG][kMaxP]: z - L_rest^T x_rest, then x, of the pivot variables
-    double *wk = sm + RG * kMaxP;  // partial sums; then rows of L11 [kLJ][kLD]
-    double *l11s = wk + LvShape<RG>::kChunk;  // L11 of a panel with e <= kLJ: [e][kLJ + 1] by rows
+                                                     double *X, int64_t ldx, int nrhs, const T *__restrict__ Z,
+                                                     T *part, int *cnt) {
+    extern __shared__ __align__(16) unsigned char lv_smem[];
+    T *sm = reinterpret_cast<T *>(lv_smem);
+    T *sz = sm;               // [RG][kMaxP]: z - L_rest^T x_rest, then x, of the pivot variables
+    T *wk = sm + RG * kMaxP;  // partial sums; then rows of L11 [kLJ][kLD]
+    T *l11s = wk + LvShape<T, RG>::kChunk;  // L11 of a panel with e <= kLJ: [e][kLJ + 1] by rows
     __shared__ int pvar[kMaxP], pk[kMaxP], rvar[kRC];
     __shared__ int last;
     const int2 it = items[blockIdx.x];
@@ -286,19 +295,19 @@ __global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__
     if (t < nr) rvar[t] = row_var(f, rbase + t);
     const bool small = e <= kLJ;
     const bool pre0 = nr > 0;
-    if (pre0) stage_chunk_cols(f, rbase, nr, 0, min(kLJ, e), wk + kRC * RG);
+    if (pre0) stage_chunk_cols<T>(f, rbase, nr, 0, min(kLJ, e), wk + kRC * RG);
     __syncthreads();
     if (small)
         for (int idx = t; idx < e * e; idx += kLT) {
             const int j = idx / e, ii = idx - j * e;
-            l11s[ii * (kLJ + 1) + j] = l11(f, pk, ii, j);
+            l11s[ii * (kLJ + 1) + j] = l11<T>(f, pk, ii, j);
         }
     pdl_trigger();
     pdl_wait();
-    double *fpart = part + f.poff * nrhs;
+    T *fpart = part + f.poff * nrhs;
     if (f.nch > 1) {
         for (int g0 = 0; g0 < nrhs; g0 += RG)
-            chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, min(RG, nrhs - g0), wk, pre0 && (small || g0 == 0),
+            chunk_sums<T, RG>(f, rvar, rbase, nr, X, ldx, g0, min(RG, nrhs - g0), wk, pre0 && (small || g0 == 0),
                            fpart, nrhs, it.y, nullptr);
         // the last item of the panel to get here finishes it
         __threadfence();
@@ -314,34 +323,34 @@ __global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__
         __syncthreads();
         for (int idx = t; idx < ng * e; idx += kLT) {
             const int r = idx / e, q = idx - r * e;
-            double v = Z[f.zoff * nrhs + (int64_t)(g0 + r) * e + q];
+            T v = Z[f.zoff * nrhs + (int64_t)(g0 + r) * e + q];
             if (f.nch > 1)
                 for (int c = 0; c < f.nch; c++) v -= __ldcg(fpart + ((int64_t)c * nrhs + g0 + r) * e + q);
             sz[r * kMaxP + q] = v;
         }
         if (f.nch == 1 && nr > 0)
-            chunk_sums<RG>(f, rvar, rbase, nr, X, ldx, g0, ng, wk, pre0 && (small || g0 == 0), nullptr, nrhs, 0, sz);
+            chunk_sums<T, RG>(f, rvar, rbase, nr, X, ldx, g0, ng, wk, pre0 && (small || g0 == 0), nullptr, nrhs, 0, sz);
         // L11^T x = z from the last pivot up, kLJ rows of L11 staged at a time;
         // warp w takes right-hand sides w, w + 8, ...; lanes take columns
         for (int i1 = e; i1 > 0; i1 -= kLJ) {
             const int i0 = max(0, i1 - kLJ), ni = i1 - i0;
-            const double *rowsL = l11s;
+            const T *rowsL = l11s;
             int ldr = kLJ + 1;
             __syncthreads();
             if (!small) {
                 for (int idx = t; idx < ni * i1; idx += kLT) {
                     const int j = idx / ni, ii = idx - j * ni;
-                    wk[ii * kLD + j] = l11(f, pk, i0 + ii, j);
+                    wk[ii * kLD + j] = l11<T>(f, pk, i0 + ii, j);
                 }
                 __syncthreads();
                 rowsL = wk;
                 ldr = kLD;
             }
             for (int r = warp; r < ng; r += kLT / 32) {
-                double *z = sz + r * kMaxP;
+                T *z = sz + r * kMaxP;
                 for (int ii = ni - 1; ii >= 0; ii--) {
                     const int i = i0 + ii;
-                    const double xi = z[i];
+                    const T xi = z[i];
                     for (int j = lane; j < i; j += 32) z[j] -= rowsL[ii * ldr + j] * xi;
                     __syncwarp();
                 }
@@ -350,7 +359,7 @@ __global__ void __launch_bounds__(kLT) k_lv_backward(const LvFront *__restrict__
         __syncthreads();
         for (int idx = t; idx < ng * e; idx += kLT) {
             const int r = idx / e, q = idx - r * e;
-            X[(int64_t)(g0 + r) * ldx + pvar[q]] = sz[r * kMaxP + q];
+            X[(int64_t)(g0 + r) * ldx + pvar[q]] = (double)sz[r * kMaxP + q];
         }
     }
 }
@@ -361,16 +370,16 @@ __global__ void k_lv_pvar(const ctp_sfront *__restrict__ sf, const int64_t *__re
     for (int q = threadIdx.x; q < f.p; q += blockDim.x) pvar[off[blockIdx.x] + q] = f.rows[f.perm[q]];
 }
 
-template <int RG>
+template <typename T, int RG>
 cudaError_t launch_level(bool forward, const LvFront *F, const int2 *items, int64_t nitems, double *X,
-                         int64_t ldx, int nrhs, double *Z, double *part, int *cnt, cudaStream_t st) {
+                         int64_t ldx, int nrhs, T *Z, T *part, int *cnt, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_lv_forward<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)LvShape<RG>::kSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_lv_forward<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)LvShape<T, RG>::kSmem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_lv_backward<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)LvShape<RG>::kSmem);
+            e = cudaFuncSetAttribute(k_lv_backward<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LvShape<T, RG>::kSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -378,24 +387,28 @@ cudaError_t launch_level(bool forward, const LvFront *F, const int2 *items, int6
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nitems);
     cfg.blockDim = dim3(kLT);
-    cfg.dynamicSmemBytes = LvShape<RG>::kSmem;
+    cfg.dynamicSmemBytes = LvShape<T, RG>::kSmem;
     cfg.stream = st;
     cudaLaunchAttribute attr_pdl[1];
     attr_pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr_pdl[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr_pdl;
     cfg.numAttrs = 1;
-    if (forward) return cudaLaunchKernelEx(&cfg, k_lv_forward<RG>, F, items, X, ldx, nrhs, Z);
-    return cudaLaunchKernelEx(&cfg, k_lv_backward<RG>, F, items, X, ldx, nrhs, (const double *)Z, part, cnt);
+    if (forward) return cudaLaunchKernelEx(&cfg, k_lv_forward<T, RG>, F, items, X, ldx, nrhs, Z);
+    return cudaLaunchKernelEx(&cfg, k_lv_backward<T, RG>, F, items, X, ldx, nrhs, (const T *)Z, part, cnt);
 }
 
+template <typename T>
 cudaError_t launch_level_rg(bool forward, const LvFront *F, const int2 *items, int64_t nitems, double *X,
-                            int64_t ldx, int nrhs, double *Z, double *part, int *cnt, cudaStream_t st) {
-    if (nrhs <= 1) return launch_level<1>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
-    if (nrhs <= 2) return launch_level<2>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
-    if (nrhs <= 4) return launch_level<4>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
-    if (nrhs <= 8) return launch_level<8>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
-    return launch_level<16>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+                            int64_t ldx, int nrhs, T *Z, T *part, int *cnt, cudaStream_t st) {
+    if (nrhs <= 1) return launch_level<T, 1>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    if (nrhs <= 2) return launch_level<T, 2>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    if (nrhs <= 4) return launch_level<T, 4>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    if (nrhs <= 8) return launch_level<T, 8>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    if constexpr (sizeof(T) == 4) {  // FP32: 32 right-hand sides per pass fit in shared memory
+        if (nrhs > 16) return launch_level<T, 32>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
+    }
+    return launch_level<T, 16>(forward, F, items, nitems, X, ldx, nrhs, Z, part, cnt, st);
 }
 
 }  // namespace
@@ -494,25 +507,33 @@ size_t SolvePlan::ws_bytes(int nrhs) const {
            align256(sizeof(double) * (size_t)(part_per_rhs > 0 ? part_per_rhs : 1) * nrhs);
 }
 
-cudaError_t SolvePlan::solve(ctp_ctx *ctx, double *X, int64_t ldx, int nrhs, void *ws, cudaStream_t st) const {
-    double *Z = (double *)ws;
-    double *part = (double *)((char *)ws + align256(sizeof(double) * (size_t)(z_per_rhs > 0 ? z_per_rhs : 1) * nrhs));
-    const LvFront *F = (const LvFront *)d_F;
-    for (int l = 0; l < nlev; l++) {
+template <typename T>
+static cudaError_t plan_sweeps(ctp_ctx *ctx, const SolvePlan &pl, double *X, int64_t ldx, int nrhs, void *ws,
+                               cudaStream_t st) {
+    T *Z = (T *)ws;
+    T *part = (T *)((char *)ws + align256(sizeof(double) * (size_t)(pl.z_per_rhs > 0 ? pl.z_per_rhs : 1) * nrhs));
+    const LvFront *F = (const LvFront *)pl.d_F;
+    for (int l = 0; l < pl.nlev; l++) {
         cudaError_t e = timed(ctx, K_SYS_FWD, st, [&] {
-            return launch_level_rg(true, F, d_items + item_ptr[l], item_ptr[l + 1] - item_ptr[l], X, ldx, nrhs, Z,
-                                   part, d_cnt, st);
+            return launch_level_rg<T>(true, F, pl.d_items + pl.item_ptr[l], pl.item_ptr[l + 1] - pl.item_ptr[l], X,
+                                      ldx, nrhs, Z, part, pl.d_cnt, st);
         });
         if (e != cudaSuccess) return e;
     }
-    for (int l = nlev - 1; l >= 0; l--) {
+    for (int l = pl.nlev - 1; l >= 0; l--) {
         cudaError_t e = timed(ctx, K_SYS_BWD, st, [&] {
-            return launch_level_rg(false, F, d_items + item_ptr[l], item_ptr[l + 1] - item_ptr[l], X, ldx, nrhs, Z,
-                                   part, d_cnt, st);
+            return launch_level_rg<T>(false, F, pl.d_items + pl.item_ptr[l], pl.item_ptr[l + 1] - pl.item_ptr[l], X,
+                                      ldx, nrhs, Z, part, pl.d_cnt, st);
         });
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t SolvePlan::solve(ctp_ctx *ctx, double *X, int64_t ldx, int nrhs, void *ws, cudaStream_t st,
+                             bool fp32) const {
+    return fp32 ? plan_sweeps<float>(ctx, *this, X, ldx, nrhs, ws, st)
+                : plan_sweeps<double>(ctx, *this, X, ldx, nrhs, ws, st);
 }
 
 RefineLayout refine_layout(int64_t N, size_t solve_ws, int nrhs) {

@@ -32,7 +32,9 @@ struct SolvePlan {
     ctp_status build(const std::vector<ctp_sfront> &fronts, const std::vector<int> &level,
                      const std::vector<int32_t> &nelim, cudaStream_t st);
     size_t ws_bytes(int nrhs) const;
-    cudaError_t solve(ctp_ctx *ctx, double *X, int64_t ldx, int nrhs, void *ws, cudaStream_t st) const;
+    // X <- M^{-1} X; fp32: the sweeps' arithmetic in FP32 (X read and written in FP64)
+    cudaError_t solve(ctp_ctx *ctx, double *X, int64_t ldx, int nrhs, void *ws, cudaStream_t st,
+                      bool fp32 = false) const;
 };
 
 // The system matrix of a residual: dense (lower triangle, column-major) or
