@@ -52,9 +52,9 @@ NCU_TRAFFIC = {
     "form_fp64": {"file": "form.cu", "sha1": "798d569f67e7e8f417e75b162e2622426e55e05e",
                   "unit": "packed_entry", "bytes_per_unit": (163.760384e6 + 1513.690e6) / 194921640},
     # ncu --set full, n=40000 p=256 relaxed, split BF16, S FP32 in 128x128 blocks:
-    # 229.67 MB read + 3118.82 MB written for 48,516 blocks of 16,384 entries
-    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "bfa43a4a21fb66e6600646343c32937c25a38cbf",
-                       "unit": "tiled_entry", "bytes_per_unit": (229.674240e6 + 3118.824e6) / (48516 * 16384)},
+    # 188.44 MB read + 3118.11 MB written for 48,516 blocks of 16,384 entries
+    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "f42cb5618b32f27438bd8a88393945b4d1c3750f",
+                       "unit": "tiled_entry", "bytes_per_unit": (188.438784e6 + 3118.110e6) / (48516 * 16384)},
     # ncu --set full, n=40000 p=256 relaxed, tensor-core Solve before a split-BF16
     # Form (prep + gather + GEMM): 145.23 MB read + 124.64 MB written for 39,744 rows
     "solve_tc": {"file": "solve_tc.cu", "sha1": "b625943159839444dd75e137c8f4021fbb3e3789", "prec": "bf16x3",
