@@ -62,6 +62,23 @@ NCU_TRAFFIC = {
 }
 
 
+def max_over_ranks(x, dist):
+    """The slowest rank's value of x (a time): the job ends when its last rank
+    does.  Every rank gets the same result; dist is torch.distributed or None."""
+    if not dist:
+        return float(x)
+    import torch
+    tt = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt[0])
+
+
+def job_rate(world, work_per_rank, seconds):
+    """Whole-job throughput of `world` replicas that each did work_per_rank
+    units in (at most) `seconds`."""
+    return world * work_per_rank / seconds
+
+
 def flops_model(n, p, e):
     m = n - p
     fs = 0
@@ -380,14 +397,10 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
     torch.cuda.synchronize()
     kern = ctx.profile_end()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt[0])
+    ms = max_over_ranks(t0.elapsed_time(t1), dist)
     fs, form = flops_model(n, p, e)
     flops_step = fs + (form if smode != "none" else 0)
-    value = world * flops_step * steps / (ms / 1e3) / 1e9
+    value = job_rate(world, flops_step * steps, ms / 1e3) / 1e9
     del bufs
 
     # e2e through the public API with host buffers: H2D of the supernode from
@@ -419,12 +432,8 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
         for _ in range(e2e_steps):
             e2e_step()
         torch.cuda.synchronize()
-        te = time.perf_counter() - s0
-        if dist:
-            tt = torch.tensor([te], dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt[0])
-        e2e = {"value": world * flops_step * e2e_steps / te / 1e9, "unit": "GFLOP/s",
+        te = max_over_ranks(time.perf_counter() - s0, dist)
+        e2e = {"value": job_rate(world, flops_step * e2e_steps, te) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": hA.numel() * 8,
                "d2h_bytes_per_step": hOut.numel() * 8 + hp.numel() * 4 + hv.numel() * 4 +
                hD.numel() * 8 + 4}
