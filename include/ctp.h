@@ -424,8 +424,11 @@ ctp_status ctp_mf_fronts(const ctp_mf *mf, int32_t *nf, const ctp_sfront **front
 ctp_status ctp_mf_info(const ctp_mf *mf, int32_t cap, int32_t *nblocks, int32_t *parent, int64_t *n,
                        int64_t *p, int64_t *nelim, int64_t *ndelayed);
 /* Solve with the factors, planned by levels of independent panels (one launch
- * per level and step instead of per panel): X <- M^{-1} X in place (N x nrhs,
- * device, ldx >= N).  Launches only. */
+ * per level and sweep, over items of 64 rows below a panel's pivots, instead
+ * of one per panel), in FP64: X <- M^{-1} X in place (N x nrhs, device,
+ * ldx >= N).  The forward sweep adds into rows shared by the panels of a level
+ * with atomics, so two solves agree to rounding, not bit for bit.  Launches
+ * only. */
 ctp_status ctp_mf_solve_workspace_size(const ctp_mf *mf, int32_t nrhs, size_t *bytes);
 ctp_status ctp_mf_solve(ctp_ctx *ctx, const ctp_mf *mf, int32_t nrhs, double *X, int64_t ldx, void *workspace,
                         size_t ws_bytes, void *stream);

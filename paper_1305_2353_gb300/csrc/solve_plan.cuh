@@ -1,5 +1,5 @@
 // solve_plan.cuh -- a front-list solve planned by levels (fronts of a level are
-// independent: one launch per level and step), and FP64 iterative refinement
+// independent: one launch per level and sweep), and FP64 iterative refinement
 // (Section 7) around any solve: the helpers shared by the ABI's complete-system
 // entry points.
 #pragma once
