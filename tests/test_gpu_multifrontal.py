@@ -97,3 +97,29 @@ def test_multifrontal_mixed_refines(ctx, prec):
         assert hist[-1].max() <= 1e-14 and steps <= 10
     mf.destroy()
     mf64.destroy()
+
+
+@pytest.mark.parametrize("nrhs", [1, 17, 40])
+def test_planned_solve_many_rhs(ctx, nrhs):
+    """The level-planned solve takes the right-hand sides in groups (16 per pass
+    in FP64, 32 in the FP32 sweeps of a mixed refinement); partial and several
+    groups give the generic front-list solve's result, and the FP32 sweeps
+    still refine split-BF16 factors to 1e-14."""
+    from paper_1305_2353_gb300 import ctp
+    cp, ri, v, N, perm, blocks = _problem(12, 3.0, leaf=32)
+    mf = ctp.Multifrontal(ctx, cp, ri, v, perm, blocks)
+    mf.factor(ctp.options(pivot="strict"))
+    B = np.random.default_rng(nrhs).standard_normal((N, nrhs))
+    X1 = ctp.colmajor(B)
+    mf.solve(X1, mf.refine_workspace(nrhs))
+    X2 = ctp.colmajor(B)
+    ws = ctp.solve_workspace(ctx, int(mf.info()["n"].max()), nrhs)
+    ctp.solve(ctx, mf.fronts, mf.nf, N, nrhs, X2, N, ws)
+    torch.cuda.synchronize()
+    x1, x2 = ctp.to_numpy(X1), ctp.to_numpy(X2)
+    assert np.abs(x1 - x2).max() <= 1e-10 * np.abs(x2).max()
+    mf.factor(ctp.options(pivot="strict", prec="bf16x6"))
+    X = torch.zeros((nrhs, N), dtype=torch.float64, device="cuda")
+    hist, steps = mf.refine(ctp.colmajor(B), X, mf.refine_workspace(nrhs))
+    assert hist[-1].max() <= 1e-14 and steps <= 6
+    mf.destroy()
