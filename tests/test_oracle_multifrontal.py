@@ -121,3 +121,34 @@ def test_pattern_gradient_against_finite_differences(k, leaf, nrhs, sample):
         Bm[i, r] -= h
         fd = (_fd_loss(cp, ri, N, v, Bp) - _fd_loss(cp, ri, N, v, Bm)) / (2 * h)
         assert abs(fd - gb[i, r]) <= 1e-6 * np.abs(gb).max(), (i, r, fd, gb[i, r])
+
+
+def _closed_form_eigs(k, sigma):
+    """Eigenvalues of the 7-point Dirichlet Laplacian on k^3 minus sigma I:
+    sum over the three axes of 2 - 2 cos(pi i / (k + 1)), i = 1..k, minus sigma."""
+    lam = 2.0 - 2.0 * np.cos(np.pi * np.arange(1, k + 1) / (k + 1))
+    return (lam[:, None, None] + lam[None, :, None] + lam[None, None, :]).ravel() - sigma
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_shifted_laplacian_spectrum(k):
+    """The input generator's matrix has the closed-form spectrum (checked with a
+    dense symmetric eigensolver), including the exact zero eigenvalue that
+    sigma = 3 gives when 3 divides k + 1 (here k = 5)."""
+    cp, ri, v = inputs.laplacian_3d(k, 3.0)
+    M = MF.sym_csc(cp, ri, v, k ** 3).toarray()
+    got = np.sort(np.linalg.eigvalsh(M))
+    want = np.sort(_closed_form_eigs(k, 3.0))
+    assert np.abs(got - want).max() <= 1e-12
+    assert (np.abs(want).min() <= 1e-14) == ((k + 1) % 3 == 0)
+
+
+def test_grids_in_use_are_nonsingular():
+    """Every grid of the GPU tests and the benchmark keeps the shift away from
+    the spectrum; 8^3 and 32^3, which do not, are singular."""
+    for k in (4, 6, 7, 9, 10, 12, 16, 24, 64):
+        assert np.abs(_closed_form_eigs(k, 3.0)).min() > 1e-4, k
+    assert np.abs(_closed_form_eigs(10, 6.0)).min() > 1e-4
+    assert np.abs(_closed_form_eigs(12, 6.0)).min() > 1e-4
+    for k in (8, 32):
+        assert np.abs(_closed_form_eigs(k, 3.0)).min() < 1e-14, k
