@@ -84,6 +84,7 @@ ctp_status ctp_create(ctp_ctx **ctx, int32_t device) {
     c->profiling = false;
     c->nrec = 0;
     c->events_made = false;
+    c->side_made = false;
     *ctx = c;
     return CTP_OK;
 }
@@ -91,6 +92,13 @@ ctp_status ctp_create(ctp_ctx **ctx, int32_t device) {
 ctp_status ctp_destroy(ctp_ctx *ctx) {
     if (ctx != nullptr && ctx->events_made)
         for (int i = 0; i < 2 * kMaxRec; i++) cudaEventDestroy(ctx->ev[i]);
+    if (ctx != nullptr && ctx->side_made) {
+        for (int i = 0; i < kSideStreams; i++) {
+            cudaStreamDestroy(ctx->side[i]);
+            cudaEventDestroy(ctx->join_ev[i]);
+        }
+        cudaEventDestroy(ctx->fork_ev);
+    }
     free(ctx);
     return CTP_OK;
 }
@@ -361,6 +369,22 @@ ctp_status ctp_profile_end(ctp_ctx *ctx, int32_t max_kernels, char *names, doubl
     return CTP_OK;
 }
 
+// The context's side streams, made on first use outside a stream capture
+// (false: run on st alone).
+static bool side_streams(ctp_ctx *ctx, cudaStream_t st) {
+    if (ctx->side_made) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    for (int i = 0; i < kSideStreams; i++) {
+        if (cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
+            return false;
+    }
+    if (cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    ctx->side_made = true;
+    return true;
+}
+
 ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front *fronts,
                             void *workspace, size_t ws_bytes, void *stream) {
     if (ctx == nullptr || plan == nullptr || fronts == nullptr || workspace == nullptr) return CTP_EINVAL;
@@ -369,10 +393,26 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
     char *w = (char *)workspace;
     CTP_CUDA(timed(ctx, K_B_PREPARE, st, [&] { return batch_prepare(plan, w, st); }));
     CTP_CUDA(timed(ctx, K_B_COMPRESS, st, [&] { return batch_compress(plan, fronts, w, ctx->num_sms, st); }));
-    for (int c = 0; c < batch_num_classes(plan); c++) {
-        const int G = batch_class_G(plan, c);
-        const int id = K_B_FACTOR_G1 + (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4);
-        CTP_CUDA(timed(ctx, id, st, [&] { return batch_factor_class(plan, c, fronts, w, st); }));
+    const int ncls = batch_num_classes(plan);
+    if (!ctx->profiling && ncls > 1 && side_streams(ctx, st)) {
+        // the classes touch disjoint fronts: run them side by side (the widest
+        // first, so that its clusters take SMs before the narrow CTAs fill the
+        // rest), joined back into st before the Solve; capturable as a fork/join
+        CTP_CUDA(cudaEventRecord(ctx->fork_ev, st));
+        for (int i = 0; i < ncls; i++) {
+            const int c = ncls - 1 - i;
+            cudaStream_t s = ctx->side[i % kSideStreams];
+            CTP_CUDA(cudaStreamWaitEvent(s, ctx->fork_ev, 0));
+            CTP_CUDA(batch_factor_class(plan, c, fronts, w, s));
+            CTP_CUDA(cudaEventRecord(ctx->join_ev[i % kSideStreams], s));
+        }
+        for (int i = 0; i < ncls && i < kSideStreams; i++) CTP_CUDA(cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
+    } else {
+        for (int c = 0; c < ncls; c++) {
+            const int G = batch_class_G(plan, c);
+            const int id = K_B_FACTOR_G1 + (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4);
+            CTP_CUDA(timed(ctx, id, st, [&] { return batch_factor_class(plan, c, fronts, w, st); }));
+        }
     }
     CTP_CUDA(timed(ctx, K_B_SOLVE, st, [&] { return batch_solve(plan, fronts, w, ctx->num_sms, st); }));
     CTP_CUDA(timed(ctx, K_B_FORM, st, [&] { return batch_form(plan, fronts, w, ctx->num_sms, st); }));

@@ -6,6 +6,7 @@
 
 namespace ctp {
 constexpr int kMaxRec = 32768;
+constexpr int kSideStreams = 5;  // one per cluster-width class (G = 1, 2, 4, 8, 16)
 enum KernelId {
     K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP,
     K_B_PREPARE, K_B_COMPRESS, K_B_FACTOR_G1, K_B_FACTOR_G2, K_B_FACTOR_G4, K_B_FACTOR_G8,
@@ -26,6 +27,10 @@ struct ctp_ctx {
     int rec_id[ctp::kMaxRec];
     cudaEvent_t ev[2 * ctp::kMaxRec];
     bool events_made;
+    // side streams on which a batch's pivot-search classes run side by side
+    cudaStream_t side[ctp::kSideStreams];
+    cudaEvent_t fork_ev, join_ev[ctp::kSideStreams];
+    bool side_made;
 };
 
 namespace ctp {
