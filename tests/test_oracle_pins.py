@@ -326,6 +326,38 @@ def test_relaxed_more_columns_than_rows():
     assert np.array_equal(C[0], A21[0]) and np.array_equal(C[1], A21[1])
 
 
+def _relaxed_restated(A21):
+    """Section 4.2 restated directly: column by column, the largest |a(i, j)|
+    among rows not yet taken (the lowest row on ties) is taken; its signed row
+    is row j of C; with every row taken, the remaining rows of C are zero."""
+    m, p = A21.shape
+    taken = np.zeros(m, dtype=bool)
+    C = np.zeros((p, p))
+    rows = -np.ones(p, dtype=np.int64)
+    for j in range(p):
+        if taken.all():
+            break
+        mag = np.where(taken, -1.0, np.abs(A21[:, j]))
+        r = int(np.argmax(mag))          # first maximum: the lowest row on ties
+        taken[r] = True
+        rows[j] = r
+        C[j] = A21[r]
+    return C, rows
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_relaxed_compression_brute_force(seed):
+    """Tie-heavy inputs (small integers) of several shapes, including fewer rows
+    than columns: the oracle's relaxed compression equals the restatement."""
+    rng = np.random.default_rng(100 + seed)
+    for m, p in ((1, 1), (3, 5), (7, 4), (40, 6), (200, 16), (5, 5)):
+        A21 = rng.integers(-3, 4, size=(m, p)).astype(float)
+        C, rows = O.compress_relaxed(A21)
+        Cw, rw = _relaxed_restated(A21)
+        assert np.array_equal(np.asarray(rows, dtype=np.int64), rw), (m, p)
+        assert np.array_equal(C, Cw), (m, p)
+
+
 def test_strict_compression_entries_are_exact_maxima():
     rng = np.random.default_rng(5)
     A21 = rng.standard_normal((300, 9))
