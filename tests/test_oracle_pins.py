@@ -369,6 +369,25 @@ def test_strict_compression_entries_are_exact_maxima():
     assert np.array_equal(J, np.argmax(np.abs(A21), axis=1))
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_strict_compression_ties_brute_force(seed):
+    """Tie-heavy inputs (small integers, whole zero rows): J(i) is the lowest
+    column of a row's largest |a| (an all-zero row goes to column 0), and C's
+    row j holds the column maxima of |a| over the rows with J(i) = j, zero when
+    none (eq. (4.1))."""
+    rng = np.random.default_rng(200 + seed)
+    for m, p in ((1, 1), (6, 3), (50, 7), (300, 12)):
+        A21 = rng.integers(-2, 3, size=(m, p)).astype(float)
+        A21[::4] = 0.0
+        C, J = O.compress_strict(A21)
+        Jw = np.array([int(np.argmax(np.abs(r))) for r in A21])
+        assert np.array_equal(np.asarray(J), Jw), (m, p)
+        for j in range(p):
+            sel = np.abs(A21[Jw == j])
+            want = sel.max(axis=0) if len(sel) else np.zeros(p)
+            assert np.array_equal(C[j], want), (m, p, j)
+
+
 def test_app_a_operation_count():
     """Appendix A: with every pivot a 2x2 accepted on its first test, the counted
     operations equal TPP_ops(n,p) = 29/6 p - 3/4 p^2 - 1/3 p^3 + 2np + 1/2 np^2."""
