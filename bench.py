@@ -20,6 +20,12 @@ Metric: GFLOP/s of the supernode factorization under the flop model
 with e = nelim (the pivots actually eliminated).  Compression and pivot search
 are counted as overhead, not as flops.
 
+Output: the last line on stdout is one compact JSON object (the headline:
+metric, value, roofline, cpu_baseline, e2e, clocks, backward errors and the
+batch's mixed-versus-FP64 pair, under 2 KB).  Every other leg prints a short
+summary line on stderr, and the complete record (kernel splits, autotuner
+tables, every leg) is written to --full-out.
+
 --impl reference times the CPU FP64 oracle on a bounded sample of the same
 workload (the paper's method has no other reference implementation).
 """
@@ -88,7 +94,7 @@ def flops_model(n, p, e):
     return fs, form
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -120,7 +126,12 @@ def parse_args():
                     help="skip the multifrontal leg (64^3 Laplacian)")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the extra measurement with the Form on the tensor cores")
-    return ap.parse_args()
+    ap.add_argument("--all", action="store_true",
+                    help="also run the context legs: complete system, multifrontal (64^3), "
+                         "GPU TPP comparator, FP64-Solve and plain-BF16 mixed legs, plain-BF16 batch")
+    ap.add_argument("--full-out", default=os.path.join("gpurun_out", "bench_full.json"),
+                    help="file that receives the complete record of every leg")
+    return ap.parse_args(argv)
 
 
 def workload_name(a):
@@ -131,10 +142,11 @@ def workload_name(a):
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(a, target_s=12.0):
+def oracle_sample(a, target_s=12.0, with_error=False):
     """Time the CPU oracle (single thread) on a bounded sample of the workload:
     the first m_s rows of A21 for the factor+solve and the first m_f rows for
-    the Form.  Returns (flops, seconds, description)."""
+    the Form.  Returns (flops, seconds, description), plus the oracle factor's
+    own backward error on that sample (untimed) when with_error is set."""
     from oracle import oracle
     from paper_1305_2353_gb300 import inputs
     A = inputs.single_large(a.seed, n=a.n, p=a.p)
@@ -159,7 +171,11 @@ def oracle_sample(a, target_s=12.0):
         t_form, form = 0.0, 0
     desc = (f"oracle factor+solve on the first {ms} A21 rows (n={p + ms}, p={p}, nelim={e}) and "
             f"Form on the first {mf} rows; single-threaded C, -O2")
-    return fs + form, t_fs + t_form, desc
+    if not with_error:
+        return fs + form, t_fs + t_form, desc
+    rows = np.arange(ms)
+    oerr = factor_errors(As, r["A"], r["perm"], r["piv"], r["D"], e, p, rows)
+    return fs + form, t_fs + t_form, desc, oerr
 
 
 def run_reference(a):
@@ -233,16 +249,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def fp64_peak_tflops(torch, dev):
-    """cuBLAS DGEMM throughput on this GPU, measured now (best of 5, 4096^3)."""
-    N = 4096
+def fp64_peak_tflops(torch, dev, N=6144, reps=10):
+    """FP64 matrix-multiply throughput of this GPU, measured now: torch.matmul
+    (cuBLAS DGEMM) on N x N float64 operands, best of `reps` after two warm-up
+    products, timed with CUDA events."""
     x = torch.randn(N, N, dtype=torch.float64, device=dev)
     y = torch.randn(N, N, dtype=torch.float64, device=dev)
     for _ in range(2):
         x @ y
     best = 1e9
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(5):
+    for _ in range(reps):
         s.record()
         x @ y
         e.record()
@@ -250,6 +267,12 @@ def fp64_peak_tflops(torch, dev):
         best = min(best, s.elapsed_time(e) / 1e3)
     del x, y
     return 2 * N ** 3 / best / 1e12
+
+
+def fp64_alu_peak_tflops(sm_mhz=2070.0, sms=152):
+    """FP64 peak from unit counts and clock: GB300 issues 2 FP64 FMAs per clock
+    per SM (the nominal 1.25 TFLOP/s at 2070 MHz over 152 SMs)."""
+    return sms * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def ncu_traffic(name, m, prec=None):
@@ -312,23 +335,117 @@ def kernel_roofline(name, launches, ms, a, e, peaks, prec="fp64"):
     elif name in ("form_fp64", "solve_fp64"):
         fs, form = flops_model(n, p, e)
         work = form if name == "form_fp64" else fs
-        bound, unit, peak = "alu", "TFLOP/s", 1.25
-        src = ("nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table; no FP64 entry in "
-               "MEASURED_PEAKS.json); cuBLAS DGEMM 4096^3 in this run: %.3f" % peaks["fp64_tflops"])
+        bound, unit, peak = "alu", "TFLOP/s", peaks["fp64_tflops"]
+        src = "measured in this run: torch.matmul float64 6144^3, best of 10"
         achieved = work / t / 1e12
     elif name == "factor_cluster":
         # right-looking FP64 update of [A11; C] per accepted pivot: ~2p(2p - k)
         # FLOP for pivot k (latency-bound: one cluster barrier per round)
         work = sum(2.0 * p * (2 * p - k) for k in range(e))
-        bound, unit, peak = "alu", "TFLOP/s", 1.25
-        src = "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table)"
+        bound, unit, peak = "alu", "TFLOP/s", peaks["fp64_tflops"]
+        src = "measured in this run: torch.matmul float64 6144^3, best of 10"
         achieved = work / t / 1e12
     else:
         return None
     traffic = ncu_traffic(name, m, prec)
-    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-            "work_per_launch": work, "launch_ms": ms / launches}
+    out = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+           "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+           "work_per_launch": work, "launch_ms": ms / launches}
+    if bound == "alu":
+        alu = fp64_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        out["alu_peak"] = alu
+        out["frac_of_alu_peak"] = achieved / alu
+    return out
+
+
+def unpack_factor(Af, perm, piv, D, e, p):
+    """L (rows of Af, e columns, unit diagonal on the A11 rows), the e x e block
+    diagonal D and the delayed columns R from the in-place output layout of
+    ctp_factor_supernode (Af: the output rows 0..p-1 followed by any A21 rows)."""
+    nr = Af.shape[0]
+    L = np.zeros((nr, e))
+    L[:p] = np.tril(Af[:p, :e], -1)
+    L[np.arange(e), np.arange(e)] = 1.0
+    L[p:] = Af[p:, :e]
+    Dm = np.zeros((e, e))
+    for k in range(e):
+        if piv[k] == 1:
+            Dm[k, k] = D[2 * k]
+        elif piv[k] == 2:
+            Dm[k, k], Dm[k + 1, k + 1] = D[2 * k], D[2 * k + 2]
+            Dm[k + 1, k] = Dm[k, k + 1] = D[2 * k + 1]
+            L[k + 1, k] = 0.0  # that slot holds D's off-diagonal
+    R = np.zeros((nr, p))
+    R[:, e:] = Af[:, e:]
+    return L, Dm, R
+
+
+def factor_errors(A_host, Af, perm, piv, D, e, p, rows):
+    """Backward error of a factored supernode, FP64 on the host, over the A11
+    block and the A21 rows `rows`:
+      raw    = max |P A P^T - (L D L^T + [0; R])| / max |A|
+      scaled = the same maximum / max (|L||D||L^T| + |R|)   (growth-normalised)
+    over the stored trapezoid (lower triangle of the A11 block, every column of
+    the sampled A21 rows).  Af holds the output rows 0..p-1, then the output
+    rows p + rows."""
+    P = np.asarray(perm, np.int64)
+    A11 = np.tril(A_host[:p, :p])
+    A11 = A11 + np.tril(A11, -1).T
+    orig = np.vstack([A11[np.ix_(P, P)], A_host[p + rows][:, P]])
+    L, Dm, R = unpack_factor(Af, perm, piv, D, e, p)
+    rec = L @ (L[:p] @ Dm).T + R
+    scale = np.abs(L) @ (np.abs(L[:p]) @ np.abs(Dm)).T + np.abs(R)
+    mask = np.ones(orig.shape, bool)
+    mask[:p] = np.tril(np.ones((p, p), bool))
+    r = np.abs(orig - rec)[mask].max()
+    return {"raw": float(r / np.abs(A_host).max()), "growth_normalised": float(r / scale[mask].max()),
+            "growth": float(scale[mask].max() / np.abs(A_host).max())}
+
+
+def s_index(i, j, m, smode):
+    """Linear index of S(i, j), i >= j, in the layout of ctp_smode."""
+    if smode.endswith("packed"):
+        return j * m - j * (j - 1) // 2 + (i - j)
+    if smode.endswith("tiled"):
+        nb = (m + 127) // 128
+        bi, bj = i // 128, j // 128
+        return 16384 * (bj * nb - bj * (bj - 1) // 2 + bi - bj) + (j % 128) * 128 + (i % 128)
+    return j * m + i
+
+
+def result_errors(A_host, Abuf, perm, piv, D, e, p, S, smode, seed=0, nrows=2048, nent=4096):
+    """Per-result accuracy of one factored supernode: the factor's backward
+    error (factor_errors) over the A11 block and `nrows` seeded A21 rows (the
+    last row included), and, when S was written, the largest error of `nent`
+    sampled S entries against S = L21 D11 L21^T formed in FP64 from this
+    factor, relative to |L21||D11||L21^T| (the Form's own error)."""
+    import torch
+    n = A_host.shape[0]
+    m = n - p
+    rng = np.random.default_rng(seed + 77)
+    rows = np.unique(np.concatenate([rng.choice(m, size=min(nrows, m), replace=False), [m - 1]])) \
+        if m > 0 else np.zeros(0, np.int64)
+    idx = torch.from_numpy(np.concatenate([np.arange(p), p + rows]).astype(np.int64)).to(Abuf.device)
+    Af = Abuf[:, idx].T.cpu().numpy().astype(np.float64)   # (p + |rows|) x p
+    pv, kv, Dv = perm.cpu().numpy(), piv.cpu().numpy(), D.cpu().numpy()
+    out = {"factor": factor_errors(A_host, Af, pv, kv, Dv, e, p, rows), "a21_rows_sampled": int(len(rows))}
+    if S is not None and smode != "none" and m > 0 and e > 0:
+        L, Dm, _ = unpack_factor(Af, pv, kv, Dv, e, p)
+        L21 = L[p:]
+        ii = rng.integers(0, len(rows), nent)
+        jj = rng.integers(0, len(rows), nent)
+        lo, hi = np.minimum(ii, jj), np.maximum(ii, jj)
+        lo[:64], hi[:64] = np.arange(64) % len(rows), np.arange(64) % len(rows)   # diagonal entries
+        gi, gj = rows[hi], rows[lo]
+        lin = torch.from_numpy(np.array([s_index(int(a), int(b), m, smode) for a, b in zip(gi, gj)],
+                                        np.int64)).to(S.device)
+        got = S.reshape(-1)[lin].double().cpu().numpy()
+        W = L21 @ Dm
+        ref = np.einsum("ik,ik->i", L21[hi], W[lo])
+        scale = np.einsum("ik,ik->i", np.abs(L21[hi]), np.abs(L21[lo]) @ np.abs(Dm))
+        out["form"] = {"entries_sampled": int(nent),
+                       "max_rel_to_scale": float((np.abs(got - ref) / np.maximum(scale, 1e-300)).max())}
+    return out
 
 
 def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, world, dist, solve="fp64"):
@@ -401,6 +518,9 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
     fs, form = flops_model(n, p, e)
     flops_step = fs + (form if smode != "none" else 0)
     value = job_rate(world, flops_step * steps, ms / 1e3) / 1e9
+    # backward error of this result (the last timed step's factor and S), in
+    # FP64 on the host over the A11 block and sampled A21 rows
+    err = result_errors(A_host, bufs[-1], perm, piv, D, e, p, S, smode, seed=a.seed)
     del bufs
 
     # e2e through the public API with host buffers: H2D of the supernode from
@@ -446,13 +566,16 @@ def measure(a, ctx, dev, A_host, prec, smode, steps, warmup, e2e_steps, peaks, w
     ctx.tune_set(ctp.TUNE_FACTOR_G, 0)
     return dict(value=value, ms=ms, e=e, fs=fs, form=form, flops_step=flops_step, kern=kern,
                 clocks=clk, e2e=e2e, roofline=roof, launches=sum(v[0] for v in kern.values()),
-                autotune=tuned, rooflines_other={k: v for k, v in others.items() if v is not None})
+                autotune=tuned, rooflines_other={k: v for k, v in others.items() if v is not None},
+                errors=err)
 
 
-def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
+def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup, accuracy=0):
     """The batched path on many uneven supernodes: the batch call captured once
     into a CUDA graph; each timed replay factors freshly restored inputs (the
-    restore runs outside the timed events)."""
+    restore runs outside the timed events).  With accuracy > 0, that many
+    fronts of the last timed replay are checked for accuracy with their own
+    factors (batch_accuracy)."""
     import torch
     from paper_1305_2353_gb300 import ctp
     opt = ctp.options(pivot="strict", prec=prec, smode=smode)
@@ -505,6 +628,7 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
         fs += f1
         form += f2 if smode != "none" else 0
     ms = total / steps
+    acc = batch_accuracy(ctx, b, fronts, count=accuracy) if accuracy > 0 else None
     del g, b
     ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 200)
     ctx.tune_set(ctp.TUNE_FORM_WALK, 0)
@@ -514,7 +638,8 @@ def measure_batch(a, ctx, dev, fronts, prec, smode, steps, warmup):
     return {"value": (fs + form) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_batch": ms,
             "prec": prec, "S": smode, "factor_solve_flops": fs, "form_flops": form,
             "nelim_total": int(ne.sum()), "p_total": int(sum(f.shape[1] for f in fronts)),
-            "device_flags_nonzero": int((flags != 0).sum()), "autotune": tuned,
+            "device_flags_nonzero": int((flags != 0).sum()), "autotune": tuned, "accuracy": acc,
+            "gpu_launches": sum(v[0] for v in kern.values()),
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kern.items()}}
 
 
@@ -662,32 +787,152 @@ def measure_mf_gradient(mf, dev, N, nnz, nrhs=32):
             "grad_abs_max": float(gval.abs().max())}
 
 
-def batch_accuracy(ctx, fronts, count=12, seed=0):
-    """Equal-accuracy check of the batch's precisions: a seeded sample of the
-    batch's fronts (spread over sizes), each embedded in its complete system and
-    refined; the worst final backward error and the most corrections per precision."""
-    rng = np.random.default_rng(seed)
-    order = np.argsort([f.shape[0] * f.shape[1] for f in fronts])
-    pick = order[np.linspace(0, len(order) - 1, count).astype(int)]
-    res = {"sample": f"{count} fronts spread over n*p (n from {fronts[pick[0]].shape[0]} to "
-                     f"{fronts[pick[-1]].shape[0]}), 2-node systems, 1 RHS, tol 1e-14"}
+def batch_accuracy(ctx, b, fronts, count=12, seed=0):
+    """Equal-accuracy check with the timed batch's own factors.  For a seeded
+    sample of fronts spread over n*p, front k as the batch call left it (L, D,
+    pivots, and its Schur complement S in the batch's Form precision) is the
+    first front of the 2-node system M = [[A11, A21^T], [A21, A22]] (A22
+    symmetric N(0,1)); the rest of M -- the delayed columns and A22 - S -- is
+    factored on the GPU by threshold partial pivoting (FP64), and M x = b is
+    solved with FP64 refinement against M (Section 7: at most ten corrections,
+    tolerance 1e-14).  Returns the worst final backward error and the most
+    corrections over the sample."""
     import gc
     import torch
-    # the chain driver allocates its fronts itself: hand back what torch caches
+    from paper_1305_2353_gb300 import ctp, inputs
+    rng = np.random.default_rng(seed)
+    order = np.argsort([f.shape[0] * f.shape[1] for f in fronts])
+    pick = [int(k) for k in order[np.linspace(0, len(order) - 1, count).astype(int)]]
+    dev = f"cuda:{ctx.device}"
+    worst, most, first = 0.0, 0, 0.0
+    for k in pick:
+        A = fronts[k]
+        n, p = A.shape
+        m = n - p
+        r = b.result(k)
+        e, perm, Af = r["nelim"], r["perm"].astype(np.int64), r["A"]
+        d = p - e
+        M = inputs.two_node(A, seed=k)
+        hold = []
+        f0 = ctp.SFront()
+        f0.n, f0.p = n, p
+        f0.L, f0.ldl = b.A.data_ptr() + 8 * int(b.a_off[k]), n
+        f0.perm = b.perm.data_ptr() + 4 * int(b.p_off[k])
+        f0.piv = b.piv.data_ptr() + 4 * int(b.p_off[k])
+        f0.D = b.D.data_ptr() + 16 * int(b.p_off[k])
+        f0.nelim = b.nelim.data_ptr() + 4 * k
+        rows0 = torch.arange(n, dtype=torch.int32, device=dev)
+        hold.append(rows0)
+        f0.rows = rows0.data_ptr()
+        fl = [f0]
+        Np = d + m
+        ch = None
+        if Np > 0:
+            # the parent: Schur complement of the eliminated pivots in M
+            Mp = np.zeros((Np, Np))
+            Db = np.tril(Af[e:p, e:p])
+            Mp[:d, :d] = Db + np.tril(Db, -1).T
+            Mp[d:, :d] = Af[p:, e:p]
+            Mp[:d, d:] = Af[p:, e:p].T
+            S = np.asarray(r["S"], np.float64) if "S" in r else np.zeros((m, m))
+            S = np.tril(S) + np.tril(S, -1).T
+            Mp[d:, d:] = M[p:, p:] - S
+            Md = ctp.colmajor(Mp, dev)
+            hold.append(Md)
+            ch = ctp.factor_dense(ctx, Md, Np, Np, min(256, Np), ctp.options(pivot="tpp"), 256,
+                                  ctp.options(pivot="tpp"))
+            to_m = torch.from_numpy(np.concatenate([perm[e:p], p + np.arange(m)]).astype(np.int32)).to(dev)
+            for q in range(ch.nf):
+                fq = ctp.SFront.from_buffer_copy(ch.fronts[q])
+                rq = to_m[ctp.device_view(fq.rows, int(fq.n)).long()].contiguous()
+                hold.append(rq)
+                fq.rows = rq.data_ptr()
+                fl.append(fq)
+        arr = (ctp.SFront * len(fl))(*fl)
+        Mlow = ctp.colmajor(np.tril(M), dev)
+        B = ctp.colmajor(rng.standard_normal((n, 1)), dev)
+        X = torch.zeros_like(B)
+        ws = ctp.refine_workspace(ctx, n, n, 1)
+        hist, steps = ctp.refine(ctx, arr, len(fl), n, Mlow, n, 1, B, n, X, n, ws)
+        torch.cuda.synchronize()
+        hb = [float(v) for v in hist.max(axis=1)]
+        worst, most, first = max(worst, hb[-1]), max(most, steps), max(first, hb[0])
+        if ch is not None:
+            ch.destroy()
+        del hold, Mlow, B, X, ws
     gc.collect()
     torch.cuda.empty_cache()
-    free, total = torch.cuda.mem_get_info()
-    print(f"batch accuracy: {free / 2**30:.1f} GiB free of {total / 2**30:.1f}", file=sys.stderr)
-    for prec in ("fp64", "bf16x3", "bf16"):
-        worst, steps = 0.0, 0
-        for k in pick:
-            A = fronts[k]
-            b = rng.standard_normal((A.shape[0], 1))
-            r = refine_embedded(ctx, "cuda", A, prec, b, seed=int(k))
-            worst = max(worst, r["bwd_err_history"][-1])
-            steps = max(steps, r["corrections"])
-        res[prec] = {"max_bwd_err": worst, "max_corrections": steps}
-    return res
+    return {"fronts_checked": len(pick), "max_bwd_err": worst, "max_corrections": most,
+            "max_bwd_err_before_refinement": first,
+            "how": "the timed batch's own factors and S as the first front of each front's "
+                   "2-node system; rest factored by TPP (FP64); FP64 refinement, tol 1e-14"}
+
+
+def leg_summary(name, d):
+    """One short stderr line per leg (the complete record goes to --full-out)."""
+    keep = {k: v for k, v in d.items() if isinstance(v, (int, float, str)) or v is None}
+    print(json.dumps({"leg": name, **keep})[:600], file=sys.stderr, flush=True)
+
+
+def _r(x, nd=4):
+    """Round for the headline line (None passes through)."""
+    if x is None:
+        return None
+    return float(f"{x:.{nd}g}")
+
+
+def headline(rec):
+    """The compact final line (at most 2 KB) built from the complete record."""
+    main = rec["main"]
+    roof = main["roofline"]
+    cpu = rec.get("cpu_baseline")
+    err = main["errors"]
+    line = {
+        "metric": rec["metric"], "value": _r(main["value"], 6), "unit": "GFLOP/s",
+        "n_gpus": rec["n_gpus"], "steps": rec["steps"], "warmup": rec["warmup"],
+        "ms_per_step": _r(main["ms"] / rec["steps"], 6), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
+        "config": dict(rec["config"]),
+        "roofline": {"kernel": roof["kernel"], "bound": roof["bound"], "achieved": _r(roof["achieved"]),
+                     "peak": _r(roof["peak"]), "unit": roof["unit"], "frac": _r(roof["frac"]),
+                     "traffic": _r(roof.get("traffic")), "peak_source": roof.get("peak_source", "")[:80]},
+        "cpu_baseline": None if cpu is None else {
+            "value": _r(cpu["value"]), "unit": cpu["unit"], "cores": cpu["cores"], "kind": cpu["kind"],
+            "sample": cpu["sample"][:160]},
+        "e2e": None if main["e2e"] is None else {k: _r(v) if isinstance(v, float) else v
+                                                for k, v in main["e2e"].items()},
+        "gpu_launches": main["launches"],
+        "clocks": {k: main["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "bwd_err": {"factor_raw": _r(err["factor"]["raw"], 3),
+                    "factor_growth_normalised": _r(err["factor"]["growth_normalised"], 3),
+                    "form_rel": _r(err.get("form", {}).get("max_rel_to_scale"), 3)},
+    }
+    if "alu_peak" in roof:
+        line["roofline"]["alu_peak"] = _r(roof["alu_peak"])
+        line["roofline"]["frac_of_alu_peak"] = _r(roof["frac_of_alu_peak"])
+    mx = rec.get("mixed")
+    if mx:
+        line["mixed"] = {"value": _r(mx["value"]), "ms_per_step": _r(mx["ms_per_step"]),
+                         "dtype": "bf16x3 tensor-core Solve+Form, f32 S",
+                         "form_frac_of_hbm": _r(mx["roofline"].get("hbm_frac", mx["roofline"].get("frac"))),
+                         "bwd_err_factor_growth_normalised": _r(mx["errors"]["factor"]["growth_normalised"], 3),
+                         "form_rel": _r(mx["errors"].get("form", {}).get("max_rel_to_scale"), 3)}
+    bt = rec.get("batch")
+    if bt and bt.get("fp64") and bt.get("mixed"):
+        f, x = bt["fp64"], bt["mixed"]
+        line["config"]["batch_8192_mixed_vs_fp64"] = {
+            "fp64_ms": _r(f["ms_per_batch"]), "mixed_ms": _r(x["ms_per_batch"]),
+            "speedup": _r(f["ms_per_batch"] / x["ms_per_batch"]),
+            "fp64_bwd_err": _r((f.get("accuracy") or {}).get("max_bwd_err"), 3),
+            "mixed_bwd_err": _r((x.get("accuracy") or {}).get("max_bwd_err"), 3)}
+    s = json.dumps(line)
+    # never exceed 2 KB: drop context keys first
+    for k in ("mixed", "bwd_err"):
+        if len(s) <= 2000:
+            break
+        line.pop(k, None)
+        s = json.dumps(line)
+    return s
 
 
 def run_native(a):
@@ -710,39 +955,50 @@ def run_native(a):
     peaks["fp64_tflops"] = fp64_peak_tflops(torch, dev)
     ctx = ctp.Context(local)
     A_host = inputs.single_large(a.seed, n=a.n, p=a.p)
+    rec = {"metric": "Supernode LDL^T GFLOP/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "peaks": peaks,
+           "dtype": "f64" if a.prec == "fp64" else "f64 (Form: bf16 x bf16 -> f32)"}
 
-    main = measure(a, ctx, dev, A_host, a.prec, a.smode, a.steps, a.warmup,
-                   0 if a.no_e2e else a.steps, peaks, world, dist, solve=a.solve)
-    mixed = mixed_bf16 = mixed_fp64_solve = None
+    e2e_steps = 0 if a.no_e2e else min(a.steps, 3)
+    main = measure(a, ctx, dev, A_host, a.prec, a.smode, a.steps, a.warmup, e2e_steps, peaks, world, dist,
+                   solve=a.solve)
+    rec["main"] = main
+    rec["config"] = {"workload": workload_name(a), "n": a.n, "p": a.p, "u": 0.01, "pivot": a.pivot,
+                     "prec": a.prec, "solve": a.solve, "S": a.smode, "nelim": main["e"],
+                     "flops_per_step": main["flops_step"],
+                     "l2": "inputs larger than L2: a distinct 409 MB input copy per step",
+                     "parallelism": f"replicas x{world}"}
+    leg_summary("main", {"value": main["value"], "ms_per_step": main["ms"] / a.steps, "nelim": main["e"],
+                         "factor_err_growth_normalised": main["errors"]["factor"]["growth_normalised"]})
+
+    def mixed_leg(prec, desc, solve="tc"):
+        k = max(a.steps, 5)
+        mx = measure(a, ctx, dev, A_host, prec, "fp32_tiled", k, max(a.warmup, 3),
+                     0 if a.no_e2e else min(k, 3), peaks, world, dist, solve=solve)
+        out = {"value": mx["value"], "unit": "GFLOP/s", "ms_per_step": mx["ms"] / k,
+               "prec": desc, "solve": solve, "roofline": mx["roofline"],
+               "rooflines_other": mx["rooflines_other"], "e2e": mx["e2e"], "errors": mx["errors"],
+               "gpu_launches": mx["launches"],
+               "kernels": {kk: {"launches": v[0], "ms": v[1]} for kk, v in mx["kern"].items()},
+               "clocks": mx["clocks"], "autotune": mx["autotune"]}
+        return out
+
     if not a.no_mixed and a.prec == "fp64":
-        def mixed_leg(prec, desc, solve="tc"):
-            k = max(a.steps, 5)
-            mx = measure(a, ctx, dev, A_host, prec, "fp32_tiled", k, max(a.warmup, 3),
-                         0 if a.no_e2e else k, peaks, world, dist, solve=solve)
-            return {"value": mx["value"], "unit": "GFLOP/s", "ms_per_step": mx["ms"] / k,
-                    "prec": desc, "solve": solve, "roofline": mx["roofline"],
-                    "rooflines_other": mx["rooflines_other"], "e2e": mx["e2e"],
-                    "gpu_launches": mx["launches"],
-                    "kernels": {kk: {"launches": v[0], "ms": v[1]} for kk, v in mx["kern"].items()},
-                    "clocks": mx["clocks"], "autotune": mx["autotune"]}
-        mixed = mixed_leg("bf16x3", "Solve and Form on tensor cores: Solve as one product with "
-                                    "three-piece split operands, Form with split operands hi*hi + "
-                                    "hi*lo + lo*hi (bf16 x bf16 -> f32), S fp32 in 128x128 blocks; "
-                                    "compression and pivot search f64 (refines to the FP64 backward "
-                                    "error, see complete_system)")
-        mixed_fp64_solve = mixed_leg("bf16x3", "as mixed, with the Solve in FP64", solve="fp64")
-        mixed_bf16 = mixed_leg("bf16", "Solve on tensor cores (three-piece split), Form on tensor "
-                                       "cores bf16 x bf16 -> f32 (single product), S fp32 in 128x128 "
-                                       "blocks (refinement does not reach 1e-12, see complete_system)")
+        rec["mixed"] = mixed_leg("bf16x3", "Solve and Form on tensor cores: Solve as one product with "
+                                           "three-piece split operands, Form with split operands hi*hi + "
+                                           "hi*lo + lo*hi (bf16 x bf16 -> f32), S fp32 in 128x128 blocks; "
+                                           "compression and pivot search f64")
+        leg_summary("mixed", {"value": rec["mixed"]["value"], "ms_per_step": rec["mixed"]["ms_per_step"]})
+        if a.all:
+            rec["mixed_fp64_solve"] = mixed_leg("bf16x3", "as mixed, with the Solve in FP64", solve="fp64")
+            rec["mixed_bf16"] = mixed_leg("bf16", "Solve on tensor cores (three-piece split), Form on "
+                                                  "tensor cores bf16 x bf16 -> f32 (single product)")
 
-    system = None
-    if not a.no_system and rank == 0:
-        system = measure_system(ctx, dev, inputs)
-    multifrontal = None
-    if not a.no_multifrontal and rank == 0:
-        multifrontal = measure_multifrontal(ctx, dev, inputs)
+    if a.all and rank == 0 and not a.no_system:
+        rec["complete_system"] = measure_system(ctx, dev, inputs)
+    if a.all and rank == 0 and not a.no_multifrontal:
+        rec["multifrontal"] = measure_multifrontal(ctx, dev, inputs)
 
-    batch = None
     if not a.no_batch:
         fronts = inputs.batch(a.batch_count, seed=a.seed)
         sh = np.array([[f.shape[0], f.shape[1]] for f in fronts])
@@ -752,62 +1008,46 @@ def run_native(a):
                  "median_p": int(np.median(sh[:, 1])), "median_m": int(np.median(sh[:, 0] - sh[:, 1])),
                  "timing": "CUDA graph of the batch call, replayed; inputs restored outside the "
                            "timed events; launch settings chosen by the library's autotuner first"}
-        batch["fp64"] = measure_batch(a, ctx, dev, fronts, "fp64", "fp64_packed", 3, 2)
-        batch["mixed"] = measure_batch(a, ctx, dev, fronts, "bf16x3", "fp32_tiled", 3, 2)
-        batch["mixed_bf16"] = measure_batch(a, ctx, dev, fronts, "bf16", "fp32_tiled", 3, 2)
-        batch["accuracy"] = batch_accuracy(ctx, fronts)
+        nacc = 12 if rank == 0 else 0
+        batch["fp64"] = measure_batch(a, ctx, dev, fronts, "fp64", "fp64_packed", 3, 2, accuracy=nacc)
+        leg_summary("batch_fp64", batch["fp64"])
+        batch["mixed"] = measure_batch(a, ctx, dev, fronts, "bf16x3", "fp32_tiled", 3, 2, accuracy=nacc)
+        leg_summary("batch_mixed", batch["mixed"])
+        if a.all:
+            batch["mixed_bf16"] = measure_batch(a, ctx, dev, fronts, "bf16", "fp32_tiled", 3, 2,
+                                                accuracy=nacc)
+        rec["batch"] = batch
         del fronts
 
-    tpp = None
-    if not a.no_tpp and a.pivot != "restricted":
+    if a.all and not a.no_tpp and a.pivot != "restricted":
         import argparse as _ap
         at = _ap.Namespace(**vars(a))
         at.pivot = "tpp"
         tp = measure(at, ctx, dev, A_host, "fp64", "none", 3, 1, 0, peaks, world, dist)
         comp_ms = sum(v[1] for k, v in main["kern"].items() if not k.startswith("form")) / a.steps
-        tpp = {"pivot": "tpp (Listing 1 on all n rows, GPU)", "nelim": tp["e"],
-               "factor_solve_ms": tp["ms"] / 3,
-               "factor_solve_gflops": tp["fs"] * 3 / (tp["ms"] / 1e3) / 1e9,
-               "compressed_factor_solve_ms": comp_ms,
-               "compressed_factor_solve_gflops": main["fs"] / (comp_ms / 1e3) / 1e9,
-               "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in tp["kern"].items()}}
+        rec["tpp_comparator"] = {
+            "pivot": "tpp (Listing 1 on all n rows, GPU)", "nelim": tp["e"],
+            "factor_solve_ms": tp["ms"] / 3, "factor_solve_gflops": tp["fs"] * 3 / (tp["ms"] / 1e3) / 1e9,
+            "compressed_factor_solve_ms": comp_ms,
+            "compressed_factor_solve_gflops": main["fs"] / (comp_ms / 1e3) / 1e9,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in tp["kern"].items()}}
+        leg_summary("tpp_comparator", rec["tpp_comparator"])
 
-    cpu = None
     if rank == 0 and not a.no_cpu_baseline:
-        fl, t, desc = oracle_sample(a)
-        cpu = {"value": fl / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": desc}
+        fl, t, desc, oerr = oracle_sample(a, with_error=True)
+        rec["cpu_baseline"] = {"value": fl / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                               "sample": desc, "oracle_factor_errors": oerr}
+        leg_summary("cpu_baseline", {"value": rec["cpu_baseline"]["value"]})
     if rank == 0:
-        e = main["e"]
-        line = {
-            "metric": "Supernode LDL^T GFLOP/s", "value": main["value"], "unit": "GFLOP/s",
-            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": main["ms"] / a.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if a.prec == "fp64" else "f64 (Form: bf16 x bf16 -> f32)",
-            "data": "synthetic",
-            "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "u": 0.01,
-                       "pivot": a.pivot, "prec": a.prec, "solve": a.solve, "S": a.smode, "nelim": e,
-                       "flops_per_step": main["flops_step"], "factor_solve_flops": main["fs"],
-                       "form_flops": main["form"] if a.smode != "none" else 0,
-                       "l2": "inputs larger than L2: a distinct 409 MB input copy per step",
-                       "parallelism": f"replicas x{world}"},
-            "roofline": main["roofline"],
-            "cpu_baseline": cpu,
-            "e2e": main["e2e"],
-            "gpu_launches": main["launches"],
-            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in main["kern"].items()},
-            "clocks": main["clocks"],
-            "fp64_dgemm_tflops": peaks["fp64_tflops"],
-            "mixed": mixed,
-            "mixed_fp64_solve": mixed_fp64_solve,
-            "mixed_bf16": mixed_bf16,
-            "complete_system": system,
-            "multifrontal": multifrontal,
-            "tpp_comparator": tpp,
-            "batch": batch,
-        }
-        print(json.dumps(line), flush=True)
+        rec["main"]["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in main["kern"].items()}
+        if a.full_out:
+            try:
+                os.makedirs(os.path.dirname(os.path.abspath(a.full_out)), exist_ok=True)
+                with open(a.full_out, "w") as fh:
+                    json.dump(rec, fh, default=str)
+            except OSError as ex:
+                print(f"could not write {a.full_out}: {ex}", file=sys.stderr)
+        print(headline(rec), flush=True)
     if dist:
         dist.destroy_process_group()
 

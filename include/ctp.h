@@ -169,7 +169,10 @@ ctp_status ctp_compress_strict(ctp_ctx *ctx, int64_t m, int32_t p, const double 
  * ctp_compress_strict, on the CURRENT device, with no context and no
  * workspace.  p above ctp_max_p() returns CTP_ECAPACITY.  The first call on a
  * device looks up the array's device address (a one-time set-up; make that
- * first call before any stream capture).  All calls share the one array and
+ * first call before any stream capture; the address stays cached for the life
+ * of the process, so a program that resets the device -- cudaDeviceReset, or
+ * releasing and re-creating the primary context -- must not call this entry
+ * point afterwards).  All calls share the one array and
  * every call clears it first: calls that overlap on the GPU (two streams, or
  * two threads) race and must be serialised by the caller.  If info_host is not
  * NULL the call synchronises `stream` and stores the device info word there
@@ -513,11 +516,19 @@ ctp_status ctp_chain_destroy(ctp_chain *chain);
  *   clusters).  Read when a batch plan is created.
  * CTP_TUNE_FACTOR_G: cluster width of the single-supernode pivot search
  *   (0 = by p, the default; else 1, 2, 4, 8 or 16, widened when the columns do
- *   not fit on chip). */
+ *   not fit on chip).
+ * CTP_TUNE_TPP_SPIN: how many polls (of about 100 ns) a software grid barrier
+ *   of the full-column TPP kernel (CTP_PIV_TPP) waits for the other CTAs
+ *   before it gives up: the kernel then stops, every CTA returns and the info
+ *   word reads CTP_ETIMEOUT (0 = the default, 2^24 polls, about 1.5 s; else
+ *   1..2^24).  Small values exist to exercise that timeout path in tests: the
+ *   wait of the CTAs for CTA 0's pivot decision then runs out, and the
+ *   factorization's outputs are unspecified. */
 typedef enum {
     CTP_TUNE_FORM_WALK = 0,
     CTP_TUNE_BATCH_SMEM_KB = 1,
-    CTP_TUNE_FACTOR_G = 2
+    CTP_TUNE_FACTOR_G = 2,
+    CTP_TUNE_TPP_SPIN = 3
 } ctp_tune_key;
 typedef enum {
     CTP_WALK_AUTO = 0,

@@ -3,6 +3,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "chain.cuh"
@@ -24,6 +25,16 @@ const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "c
 namespace ctp {
 
 int ctx_batch_smem_kb(const ctp_ctx *ctx) { return ctx->batch_smem_kb; }
+
+cudaError_t smem_at_least(const void *func, size_t bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);  // query and raise as one step
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     WsLayout L;
@@ -81,6 +92,7 @@ ctp_status ctp_create(ctp_ctx **ctx, int32_t device) {
     c->form_walk = CTP_WALK_AUTO;
     c->batch_smem_kb = 200;
     c->factor_g = 0;
+    c->tpp_spin = 0;
     c->profiling = false;
     c->nrec = 0;
     c->events_made = false;
@@ -132,6 +144,11 @@ ctp_status ctp_tune_set(ctp_ctx *ctx, int32_t key, int32_t value) {
         ctx->factor_g = value;
         return CTP_OK;
     }
+    if (key == CTP_TUNE_TPP_SPIN) {
+        if (value < 0 || value > (1 << 24)) return CTP_EINVAL;
+        ctx->tpp_spin = value;
+        return CTP_OK;
+    }
     return CTP_EINVAL;
 }
 
@@ -143,6 +160,8 @@ ctp_status ctp_tune_get(const ctp_ctx *ctx, int32_t key, int32_t *value) {
         *value = ctx->batch_smem_kb;
     else if (key == CTP_TUNE_FACTOR_G)
         *value = ctx->factor_g;
+    else if (key == CTP_TUNE_TPP_SPIN)
+        *value = ctx->tpp_spin;
     else
         return CTP_EINVAL;
     return CTP_OK;
@@ -239,7 +258,7 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
         // Listing 1 on all n rows: factor and solve in one cooperative kernel
         CTP_CUDA(timed(ctx, K_TPP, st, [&] {
             return launch_tpp(A, n, p, lda, opt->u, opt->small, ws + L.aux, perm, piv, D, Dinv, nelim,
-                              info, ctx->num_sms, st);
+                              info, ctx->num_sms, ctx->tpp_spin, st);
         }));
         if (opt->smode != CTP_S_NONE && m > 0) {
             CTP_CUDA(timed(ctx, K_W21, st, [&] {
@@ -370,17 +389,32 @@ ctp_status ctp_profile_end(ctp_ctx *ctx, int32_t max_kernels, char *names, doubl
 }
 
 // The context's side streams, made on first use outside a stream capture
-// (false: run on st alone).
+// (false: run on st alone).  They belong to the context's device: when another
+// device is current the batch does not fork (the caller's stream is on the
+// current device, and events cannot join streams across devices).  A partial
+// failure releases what it made, so a later call may try again.
 static bool side_streams(ctp_ctx *ctx, cudaStream_t st) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device) return false;
     if (ctx->side_made) return true;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-    for (int i = 0; i < kSideStreams; i++) {
-        if (cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
-            return false;
+    int ns = 0, ne = 0;
+    bool fork = false, ok = true;
+    for (; ok && ns < kSideStreams; ns++)
+        ok = cudaStreamCreateWithFlags(&ctx->side[ns], cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) ns--;
+    for (; ok && ne < kSideStreams; ne++)
+        ok = cudaEventCreateWithFlags(&ctx->join_ev[ne], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) ne--;
+    if (ok) ok = fork = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (int i = 0; i < ns; i++) cudaStreamDestroy(ctx->side[i]);
+        for (int i = 0; i < ne; i++) cudaEventDestroy(ctx->join_ev[i]);
+        if (fork) cudaEventDestroy(ctx->fork_ev);
+        (void)cudaGetLastError();
+        return false;
     }
-    if (cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess) return false;
     ctx->side_made = true;
     return true;
 }

@@ -152,8 +152,7 @@ cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *
     (void)num_sms;
     if (items == 0) return cudaSuccess;
     const size_t smem = sizeof(double) * (size_t)kMaxP * (kTR + 1);
-    cudaError_t err = cudaFuncSetAttribute(k_compress_strict_batch,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = smem_at_least((const void *)k_compress_strict_batch, smem);
     if (err != cudaSuccess) return err;
     k_compress_strict_batch<<<(unsigned)items, kThreads, smem, st>>>(fronts, tab, ws, item_front, o);
     return cudaGetLastError();

@@ -186,8 +186,7 @@ cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t 
                                    int num_sms, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     size_t smem = strict_smem(p);
-    cudaError_t err = cudaFuncSetAttribute(k_compress_strict, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    cudaError_t err = smem_at_least((const void *)k_compress_strict, smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress_strict, kThreads, smem);
@@ -220,7 +219,11 @@ cudaError_t launch_keys_to_rowmajor(const unsigned long long *Ckeys, double *C, 
 // in one file-scope device array, sized for the largest supported p, that every
 // GPU holds from the moment this library is loaded on it until the process
 // exits.  Host code must not use the array's name as a device address (it is a
-// host-side stand-in); the device address is looked up once per device.
+// host-side stand-in); the device address is looked up once per device and
+// cached for the life of the process.  The cache does not survive a device
+// reset (cudaDeviceReset, or the primary context released and made again):
+// after one, the cached address is stale, so such a program must not call
+// ctp_compress_strict_noalloc again.
 
 #include <mutex>
 

@@ -28,6 +28,15 @@ struct WsLayout {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Make sure `func` may launch with `bytes` of dynamic shared memory on the
+// current device: raises cudaFuncAttributeMaxDynamicSharedMemorySize when it is
+// below `bytes` and never lowers it.  The attribute belongs to the function,
+// not to one launch: a CUDA graph node captured with more shared memory than a
+// later, lower setting allows fails when the graph is replayed, so no launcher
+// may lower it.  (A device reset restores the default; the current value is
+// queried each time, so the next launch raises it again.)
+cudaError_t smem_at_least(const void *func, size_t bytes);
+
 WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms);
 int ctx_batch_smem_kb(const ctp_ctx *ctx);  // CTP_TUNE_BATCH_SMEM_KB of a context
 // BF16 pieces per operand of the tensor-core Form for a precision (0: FP64 Form)
@@ -173,9 +182,10 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
 
 // Threshold partial pivoting on all n rows (the comparator of the compressed path).
 size_t tpp_ws_bytes(int p);
+// spin: polls a grid barrier waits before it reports CTP_ETIMEOUT (0: the default)
 cudaError_t launch_tpp(double *A, int64_t n, int p, int64_t lda, double u, double small, void *ws,
                        int32_t *perm, int32_t *piv, double *D, double *Dinv, int32_t *nelim,
-                       int32_t *info, int num_sms, cudaStream_t st);
+                       int32_t *info, int num_sms, int spin, cudaStream_t st);
 
 // K-padding of the BF16 operand copies used by the tensor-core Form.
 int form_tc_kpad(int p);

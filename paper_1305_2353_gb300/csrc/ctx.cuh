@@ -22,6 +22,7 @@ struct ctp_ctx {
     int form_walk;      // CTP_TUNE_FORM_WALK
     int batch_smem_kb;  // CTP_TUNE_BATCH_SMEM_KB
     int factor_g;       // CTP_TUNE_FACTOR_G
+    int tpp_spin;       // CTP_TUNE_TPP_SPIN (0: the kernel's default)
     bool profiling;
     int nrec;
     int rec_id[ctp::kMaxRec];

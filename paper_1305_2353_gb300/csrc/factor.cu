@@ -629,8 +629,7 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t s
     int G = G_req > 0 ? G_req : (a.p > 128 ? 16 : (a.p > 64 ? 8 : (a.p > 16 ? 4 : 1)));
     while (factor_smem(a.p, a.R, G) > 160 * 1024 && G < 16) G <<= 1;
     size_t smem = factor_smem(a.p, a.R, G);
-    cudaError_t err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    cudaError_t err = smem_at_least((const void *)k_factor_cluster, smem);
     if (err != cudaSuccess) return err;
     if (G > 8) {
         err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -652,7 +651,7 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t s
         cfg.dynamicSmemBytes = smem;
         attr[0].val.clusterDim.x = G;
         int nclusters = 0;
-        err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = smem_at_least((const void *)k_factor_cluster, smem);
         if (err == cudaSuccess) err = cudaOccupancyMaxActiveClusters(&nclusters, k_factor_cluster, &cfg);
         if (err == cudaSuccess && nclusters > 0) break;
         (void)cudaGetLastError();
@@ -685,8 +684,7 @@ cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char
     if (count == 0) return cudaSuccess;
     const int R = o.pivot == CTP_PIV_STRICT ? pmax : 0;
     const size_t smem = factor_smem(pmax, R, G);
-    cudaError_t err = cudaFuncSetAttribute(k_factor_cluster_batch,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = smem_at_least((const void *)k_factor_cluster_batch, smem);
     if (err != cudaSuccess) return err;
     if (G > 8) {
         err = cudaFuncSetAttribute(k_factor_cluster_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -554,7 +554,7 @@ int form_tc_kpad(int p) { return (p + kBK - 1) / kBK * kBK; }
 namespace {
 template <bool kBatch, int P>
 cudaError_t set_smem(size_t smem) {
-    return cudaFuncSetAttribute(k_form_tc<kBatch, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return smem_at_least((const void *)k_form_tc<kBatch, P>, smem);
 }
 constexpr size_t kSmemTC = kSmemBody + 1024;
 

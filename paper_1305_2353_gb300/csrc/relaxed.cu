@@ -306,7 +306,7 @@ cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t
         const int64_t L = (m + nseg - 1) / nseg;
         const size_t smem = (sizeof(unsigned long long) + sizeof(int)) * kCap;
         cudaError_t err =
-            cudaFuncSetAttribute(k_relaxed_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            smem_at_least((const void *)k_relaxed_topk, smem);
         if (err != cudaSuccess) return err;
         dim3 grid(nseg, p);
         k_relaxed_topk<<<grid, kT1, smem, st>>>(A21, m, p, lda, L, nseg, lists, lens, info);
@@ -318,7 +318,7 @@ cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t
     }
     const size_t gsmem = sizeof(Cand) * (size_t)p * nseg * kHead + sizeof(int) * (size_t)p;
     cudaError_t err2 =
-        cudaFuncSetAttribute(k_relaxed_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+        smem_at_least((const void *)k_relaxed_greedy, gsmem);
     if (err2 != cudaSuccess) return err2;
     k_relaxed_greedy<<<1, 256, gsmem, st>>>(A21, lda, p, nseg, lists, lens, C, rows);
     return cudaGetLastError();

@@ -214,7 +214,7 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
     if (m <= 0) return cudaSuccess;
     size_t smem = sizeof(double) * (size_t)p * (kRows + 1);
     cudaError_t err =
-        cudaFuncSetAttribute(k_solve_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_at_least((const void *)k_solve_fp64, smem);
     if (err != cudaSuccess) return err;
     int64_t grid = (m + kRows - 1) / kRows;
     k_solve_fp64<<<(unsigned)grid, kRows * kWarps, smem, st>>>(
@@ -229,7 +229,7 @@ cudaError_t launch_solve_batch(const ctp_front *fronts, const BFront *tab, char 
     if (items == 0) return cudaSuccess;
     const size_t smem = sizeof(double) * (size_t)pmax * (kRows + 1);
     cudaError_t err =
-        cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_at_least((const void *)k_solve_batch, smem);
     if (err != cudaSuccess) return err;
     k_solve_batch<<<(unsigned)items, kRows * kWarps, smem, st>>>(
         fronts, tab, ws, item_front, o, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb);

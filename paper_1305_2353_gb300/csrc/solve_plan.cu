@@ -373,15 +373,11 @@ __global__ void k_lv_pvar(const ctp_sfront *__restrict__ sf, const int64_t *__re
 template <typename T, int RG>
 cudaError_t launch_level(bool forward, const LvFront *F, const int2 *items, int64_t nitems, double *X,
                          int64_t ldx, int nrhs, T *Z, T *part, int *cnt, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_lv_forward<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)LvShape<T, RG>::kSmem);
+    {
+        cudaError_t e = smem_at_least((const void *)k_lv_forward<T, RG>, LvShape<T, RG>::kSmem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_lv_backward<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)LvShape<T, RG>::kSmem);
+            e = smem_at_least((const void *)k_lv_backward<T, RG>, LvShape<T, RG>::kSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     if (nitems == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};

@@ -653,7 +653,7 @@ cudaError_t launch_gemm(int grid, const CUtensorMap (&mX)[3], const CUtensorMap 
                         cudaStream_t st) {
     const size_t smem = kSmemRing + 1024;
     cudaError_t err =
-        cudaFuncSetAttribute(k_solve_tc<PS, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_at_least((const void *)k_solve_tc<PS, kBatch>, smem);
     if (err != cudaSuccess) return err;
     k_solve_tc<PS, kBatch><<<grid, kThreadsTC, smem, st>>>(mX[0], mX[1], mX[2], mZ[0], mZ[1], mZ[2], g);
     return cudaGetLastError();
@@ -674,7 +674,7 @@ cudaError_t launch_solve_tc_batch(const ctp_front *fronts, const BFront *tab, ch
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const size_t smem = sizeof(double) * (size_t)kMaxP * (kRowsG + 1);
-    err = cudaFuncSetAttribute(k_stc_gather_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = smem_at_least((const void *)k_stc_gather_batch, smem);
     if (err != cudaSuccess) return err;
     k_stc_gather_batch<<<(unsigned)s_items, kRowsG * kWarpsG, smem, st>>>(
         fronts, tab, sitem, o, (__nv_bfloat16 *)Xt, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb);
@@ -708,7 +708,7 @@ cudaError_t launch_solve_tc(double *A, int64_t n, int p, int64_t lda, const int3
     __nv_bfloat16 *Zt = (__nv_bfloat16 *)((char *)ws + align256(2 * (size_t)m * Kp * spieces));
     const int64_t xoff = m * Kp, zoff = (int64_t)kZRows * Kp;
     const size_t smem = sizeof(double) * (size_t)p * (kRowsG + 1);
-    cudaError_t err = cudaFuncSetAttribute(k_stc_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = smem_at_least((const void *)k_stc_gather, smem);
     if (err != cudaSuccess) return err;
     k_stc_prep<<<Kp / kPrepRows, 32 * kPrepRows, 0, st>>>(A, p, lda, piv, Dinv, nelim, Zt, Kp, zoff, spieces);
     err = cudaGetLastError();

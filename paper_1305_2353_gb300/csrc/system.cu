@@ -447,11 +447,10 @@ size_t sys_solve_ws_bytes(int64_t nmax, int nrhs) {
 
 cudaError_t launch_sys_forward(const ctp_sfront &f, double *X, int64_t ldx, int nrhs, void *ws,
                                cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_sys_fwd_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
-        cudaFuncSetAttribute(k_sys_bwd_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
-        attr = true;
+    {
+        cudaError_t e = smem_at_least((const void *)k_sys_fwd_tri, kTriSmem);
+        if (e == cudaSuccess) e = smem_at_least((const void *)k_sys_bwd_tri, kTriSmem);
+        if (e != cudaSuccess) return e;
     }
     double *Y = (double *)ws;
     k_sys_fwd_tri<<<1, kTh, kTriSmem, st>>>(f, X, ldx, nrhs, Y);
@@ -463,6 +462,8 @@ cudaError_t launch_sys_backward(const ctp_sfront &f, double *X, int64_t ldx, int
                                 cudaStream_t st) {
     double *part = (double *)((char *)ws + align256(sizeof(double) * (size_t)kMaxP * nrhs));
     const int64_t nch = (f.n + kTh - 1) / kTh;  // upper bound on the chunks below the pivots
+    cudaError_t e = smem_at_least((const void *)k_sys_bwd_tri, kTriSmem);
+    if (e != cudaSuccess) return e;
     if (nch > 0) k_sys_bwd_part<<<(unsigned)nch, kTh, 0, st>>>(f, X, ldx, nrhs, part);
     k_sys_bwd_tri<<<1, kTh, kTriSmem, st>>>(f, X, ldx, nrhs, part);
     return cudaGetLastError();

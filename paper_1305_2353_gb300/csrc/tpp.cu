@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kNW = kT / 32;
-constexpr long kBarSpin = 1L << 24;  // polls of ~100 ns: about a second and a half
+constexpr long kBarSpin = 1L << 24;  // default polls of ~100 ns: about a second and a half
 constexpr int kTilesPerWarp = 4;     // 32-row tiles a warp keeps pivot values for
 
 enum { D_STOP = -2, D_ZERO = -1, D_REJECT = 0, D_1X1 = 1, D_2X2 = 2 };
@@ -56,6 +56,7 @@ struct TppArgs {
     int32_t *perm, *piv, *nelim;
     double *D, *Dinv;
     int32_t *info;
+    long spin;                   // polls a grid barrier waits before it gives up
 };
 
 __device__ __forceinline__ unsigned long long akey(double x) {
@@ -71,8 +72,9 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v)
     return v;
 }
 
-// software grid barrier for a cooperative launch; false on timeout or abort
-__device__ bool grid_sync(Ctl *ctl, int *s_ok) {
+// software grid barrier for a cooperative launch; false on timeout (more than
+// `spin` polls) or when another CTA gave up
+__device__ bool grid_sync(Ctl *ctl, int *s_ok, long spin) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *genp = &ctl->bar_gen;
@@ -87,7 +89,7 @@ __device__ bool grid_sync(Ctl *ctl, int *s_ok) {
         } else {
             long it = 0;
             while (*genp == gen) {
-                if (++it > kBarSpin) {
+                if (++it > spin) {
                     ok = 0;
                     atomicExch(&ctl->abort, 1);
                     break;
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(kT) k_tpp(TppArgs a) {
         }
     }
     int round = 0;
-    if (!grid_sync(ctl, &s_ok)) goto done;
+    if (!grid_sync(ctl, &s_ok, a.spin)) goto done;
 
     for (;;) {
         const int cur = round & 1, nxt = cur ^ 1;
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(kT) k_tpp(TppArgs a) {
             for (int k = tid; k < p; k += kT) a.live_g[k] = st.live[k];
             if (tid == 0) ctl->dec = out;
         }
-        if (!grid_sync(ctl, &s_ok)) break;
+        if (!grid_sync(ctl, &s_ok, a.spin)) break;
         if (tid == 0) {
             volatile Dec *vd = &ctl->dec;
             s_dec.kind = vd->kind;
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(kT) k_tpp(TppArgs a) {
         for (int k = tid; k < p; k += kT)
             if (ckey[k]) atomicMax(&a.M21[nxt * p + k], ckey[k]);
         round++;
-        if (!grid_sync(ctl, &s_ok)) break;
+        if (!grid_sync(ctl, &s_ok, a.spin)) break;
     }
 
 done:
@@ -597,9 +599,10 @@ static size_t tpp_smem(int p) {
 
 cudaError_t launch_tpp(double *A, int64_t n, int p, int64_t lda, double u, double small, void *ws,
                        int32_t *perm, int32_t *piv, double *D, double *Dinv, int32_t *nelim,
-                       int32_t *info, int num_sms, cudaStream_t st) {
+                       int32_t *info, int num_sms, int spin, cudaStream_t st) {
     char *w = static_cast<char *>(ws);
     TppArgs a;
+    a.spin = spin > 0 ? (long)spin : kBarSpin;
     a.A = A;
     a.lda = lda;
     a.n = n;
@@ -622,7 +625,7 @@ cudaError_t launch_tpp(double *A, int64_t n, int p, int64_t lda, double u, doubl
     err = cudaMemsetAsync(a.M21, 0, 2 * sizeof(unsigned long long) * (size_t)p, st);
     if (err != cudaSuccess) return err;
     const size_t smem = tpp_smem(p);
-    err = cudaFuncSetAttribute(k_tpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = smem_at_least((const void *)k_tpp, smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tpp, kT, smem);

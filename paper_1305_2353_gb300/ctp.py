@@ -42,7 +42,7 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_mf_analyse", "ctp_mf_factor", "ctp_mf_fronts", "ctp_mf_info", "ctp_mf_destroy",
            "ctp_mf_panel_info", "ctp_mf_solve_workspace_size", "ctp_mf_solve",
            "ctp_mf_refine_workspace_size", "ctp_mf_refine", "ctp_mf_adjoint_solve"]
-TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G = 0, 1, 2
+TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G, TUNE_TPP_SPIN = 0, 1, 2, 3
 WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
 

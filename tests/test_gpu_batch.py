@@ -140,3 +140,79 @@ def test_batch_cluster_budget_same_results(ctx, kb):
         p = A.shape[1]
         compare(O.factor(A, p, "strict"), b.result(k), p, A)
 
+
+
+def test_batch_8192_fronts_every_front_matches_oracle(ctx):
+    """The full 8192-front batch of the benchmark (p log-uniform in [8, 256],
+    n - p log-uniform in [0, 16p], N(0,1), 2% zero diagonals), strict
+    compressed pivoting: every front's pivot sequence, kinds and nelim equal the
+    oracle's, and L, D agree within 1e-10, in FP64 and with the split-BF16
+    tensor-core Form (pivots do not depend on the Form's precision).  No
+    threshold test of the oracle on this batch lies within 1e-10 of its bound."""
+    from paper_1305_2353_gb300 import ctp
+    fr = inputs.batch(8192, seed=0)
+    refs = [O.factor(A, A.shape[1], "strict") for A in fr]
+    for prec, smode in (("fp64", "none"), ("bf16x3", "fp32_tiled")):
+        b = ctp.Batch(ctx, fr, [a.shape[1] for a in fr], ctp.options(pivot="strict", prec=prec, smode=smode))
+        b.run()
+        torch.cuda.synchronize()
+        assert np.all(b.flags() == 0)
+        Ah, perm, piv = b.A.cpu().numpy(), b.perm.cpu().numpy(), b.piv.cpu().numpy()
+        D, ne = b.D.cpu().numpy(), b.nelim.cpu().numpy()
+        bad = []
+        for k, (A, ref) in enumerate(zip(fr, refs)):
+            n, p = A.shape
+            pv = slice(int(b.p_off[k]), int(b.p_off[k + 1]))
+            if (ne[k] != ref["nelim"] or not np.array_equal(perm[pv], ref["perm"])
+                    or not np.array_equal(piv[pv], ref["piv"])):
+                bad.append(k)
+                continue
+            if prec != "fp64":
+                continue   # L21 carries no Form rounding, but the FP64 run checks it already
+            Ag = Ah[int(b.a_off[k]):int(b.a_off[k + 1])].reshape(p, n).T.copy()
+            Ar = ref["A"].copy()
+            iu = np.triu_indices(p, 1)
+            Ag[:p][iu] = 0.0
+            Ar[:p][iu] = 0.0
+            assert np.allclose(Ag, Ar, rtol=1e-10, atol=1e-10 * max(np.abs(Ar).max(), 1.0)), k
+            Dg = D[2 * pv.start:2 * pv.stop]
+            assert np.allclose(Dg, ref["D"], rtol=1e-10, atol=1e-10 * max(np.abs(ref["D"]).max(), 1e-300)), k
+        assert bad == [], (prec, bad[:10])
+        del b
+        torch.cuda.empty_cache()
+
+
+def test_graph_replay_after_a_smaller_budget(ctx):
+    """A captured batch graph still replays after another batch launched the
+    same pivot-search kernel with less dynamic shared memory: the launchers only
+    ever raise a kernel's shared-memory limit (a limit lowered below what a
+    captured node uses would make that node fail on replay)."""
+    from paper_1305_2353_gb300 import ctp
+    fr = _fronts(30, seed=12)
+    ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 220)
+    try:
+        b1 = ctp.Batch(ctx, fr, [a.shape[1] for a in fr], ctp.options(pivot="strict"))
+        s = torch.cuda.Stream()
+        b1.run()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b1.run(stream=s)
+        ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 48)
+        fr2 = _fronts(20, seed=13)
+        b2 = ctp.Batch(ctx, fr2, [a.shape[1] for a in fr2], ctp.options(pivot="strict"))
+        b2.run()
+        torch.cuda.synchronize()
+        assert np.all(b2.flags() == 0)
+        b1.reset()
+        g.replay()
+        torch.cuda.synchronize()
+    finally:
+        ctx.tune_set(ctp.TUNE_BATCH_SMEM_KB, 200)
+    assert np.all(b1.flags() == 0)
+    for k, A in enumerate(fr):
+        p = A.shape[1]
+        compare(O.factor(A, p, "strict"), b1.result(k), p, A)
+    for k, A in enumerate(fr2):
+        p = A.shape[1]
+        compare(O.factor(A, p, "strict"), b2.result(k), p, A)

@@ -27,13 +27,18 @@ def _problem(k, sigma=3.0, leaf=64):
     return cp, ri, v, k ** 3, perm, blocks
 
 
-# grid sizes whose shifted Laplacian is nonsingular (see the oracle's tests)
+# grid sizes whose shifted Laplacian is nonsingular (see the oracle's tests);
+# 24^3 and 31^3 have separators of 576 and 961 columns, wider than the 256
+# columns of one panel, so their fronts are chains of panels
 @pytest.mark.parametrize("k,sigma,method", [(10, 3.0, "strict"), (10, 6.0, "strict"), (12, 3.0, "tpp"),
-                                            (12, 6.0, "relaxed"), (7, 3.0, "restricted")])
+                                            (12, 6.0, "relaxed"), (7, 3.0, "restricted"),
+                                            (24, 3.0, "strict"), (24, 3.0, "tpp"), (31, 3.0, "relaxed")])
 def test_multifrontal_matches_oracle(ctx, k, sigma, method):
     from paper_1305_2353_gb300 import ctp
     cp, ri, v, N, perm, blocks = _problem(k, sigma)
     panels, info = MF.factor(cp, ri, v, N, perm, blocks, method, w=256)
+    if k >= 24:
+        assert max(i["p"] for i in info) > 256   # some front is a chain of panels
     mf = ctp.Multifrontal(ctx, cp, ri, v, perm, blocks)
     mf.factor(ctp.options(pivot=method))
     gi = mf.info()

@@ -64,23 +64,46 @@ def recon_error(A, p, res):
     return np.abs(Ap - rec)[mask].max() / max(scale[mask].max(), np.abs(A).max())
 
 
+def raw_error(A, p, res):
+    """max |PAP^T - (LDL^T + [0; R])| over the stored trapezoid, divided by
+    max |A| (the plain, not growth-normalised, backward error)."""
+    n = A.shape[0]
+    e = res["nelim"]
+    L, Dm, R = O.unpack(res, p)
+    Ap = O.permuted_supernode(A, p, res["perm"])
+    rec = L @ Dm @ L[:p, :].T
+    rec[:, e:] += R
+    mask = np.ones((n, p), bool)
+    mask[:p, :] = np.tril(np.ones((p, p), bool))
+    return np.abs(Ap - rec)[mask].max() / max(np.abs(A).max(), 1e-300)
+
+
 def compare(ref, got, p, A, check_recon=True):
+    """Parity of one GPU factorization with the oracle's.  Pivot sequence, kinds
+    and nelim must be identical, and L, D within 1e-10.  The cases in the suite
+    are chosen so that no logged threshold test of the oracle lies within 1e-10
+    (relative) of its bound; a case that does would make pivot parity depend on
+    FP64 rounding order, so it fails here instead of being skipped.  With
+    check_recon the GPU's growth-normalised backward error must be <= 1e-14 and
+    its raw backward error at most twice the oracle's own plus 1e-15."""
     assert got["info"] == 0
+    assert ref["log_len"] <= len(ref["log"]) or len(ref["log"]) == 0, "oracle decision log truncated"
     margin = min_margin(ref["log"])
-    if margin > 1e-10:
-        assert got["nelim"] == ref["nelim"]
-        assert np.array_equal(got["perm"], ref["perm"])
-        assert np.array_equal(got["piv"], ref["piv"])
-        Ag, Ar = got["A"].copy(), ref["A"].copy()
-        # the strict upper triangle of the A11 block is unspecified
-        iu = np.triu_indices(p, 1)
-        Ag[:p][iu] = 0.0
-        Ar[:p][iu] = 0.0
-        scale = max(np.abs(Ar).max(), 1.0)
-        assert np.allclose(Ag, Ar, rtol=1e-10, atol=1e-10 * scale)
-        assert np.allclose(got["D"], ref["D"], rtol=1e-10, atol=1e-10 * np.abs(ref["D"]).max())
+    assert margin > 1e-10, f"a threshold test lies within {margin:.1e} of its bound: pick another case"
+    assert got["nelim"] == ref["nelim"]
+    assert np.array_equal(got["perm"], ref["perm"])
+    assert np.array_equal(got["piv"], ref["piv"])
+    Ag, Ar = got["A"].copy(), ref["A"].copy()
+    # the strict upper triangle of the A11 block is unspecified
+    iu = np.triu_indices(p, 1)
+    Ag[:p][iu] = 0.0
+    Ar[:p][iu] = 0.0
+    scale = max(np.abs(Ar).max(), 1.0)
+    assert np.allclose(Ag, Ar, rtol=1e-10, atol=1e-10 * scale)
+    assert np.allclose(got["D"], ref["D"], rtol=1e-10, atol=1e-10 * np.abs(ref["D"]).max())
     if check_recon:
         assert recon_error(A, p, got) <= 1e-14
+        assert raw_error(A, p, got) <= 2.0 * raw_error(A, p, ref) + 1e-15
 
 
 # --------------------------------------------------------------------------- K1
@@ -212,6 +235,49 @@ def test_large_supernode_relaxed_full_size(ctx):
     sub = dict(got)
     sub["A"] = got["A"][rows_s]
     assert recon_error(A[rows_s], p, sub) <= 1e-14
+    _form_fp64_packed_full_size(ctx, A, ref)
+
+
+def _form_fp64_packed_full_size(ctx, A, ref):
+    """The benchmarked FP64 Form at full size: S = L21 D11 L21^T of the
+    n = 200000, p = 256 relaxed supernode, lower-packed FP64 (m(m+1)/2 =
+    1.99e10 entries, 160 GB), sampled entries against the oracle's
+    form_entries on the oracle's own factor: the diagonal, the first and last
+    rows, the last 64 x 64 tile and 10^4 random entries, each within 1e-11 of
+    sum_k |L21(i,k)| |(L21 D11)(j,k)|."""
+    from paper_1305_2353_gb300 import ctp
+    n, p = A.shape
+    m, e = n - p, ref["nelim"]
+    opt = ctp.options(pivot="relaxed", smode="fp64_packed")
+    dA = ctp.colmajor(A)
+    perm = torch.empty(p, dtype=torch.int32, device="cuda")
+    piv = torch.empty(p, dtype=torch.int32, device="cuda")
+    D = torch.empty(2 * p, dtype=torch.float64, device="cuda")
+    nel = torch.empty(1, dtype=torch.int32, device="cuda")
+    S = torch.empty(m * (m + 1) // 2, dtype=torch.float64, device="cuda")
+    ws = ctx.factor_supernode(dA, n, p, n, opt, perm, piv, D, nel, S, m)
+    torch.cuda.synchronize()
+    assert ctx.read_info(ws) == 0 and int(nel.cpu()[0]) == e
+    del dA, ws
+    rng = np.random.default_rng(11)
+    ii, jj = rng.integers(0, m, 10000), rng.integers(0, m, 10000)
+    ii, jj = np.maximum(ii, jj), np.minimum(ii, jj)
+    t = np.arange(m - 64, m)
+    ti, tj = np.meshgrid(t, t, indexing="ij")
+    keep = ti >= tj
+    diag = np.r_[0:64, rng.integers(0, m, 200), m - 64:m]
+    ii = np.r_[ii, ti[keep], diag, np.arange(0, m, 997), np.full(64, m - 1)]
+    jj = np.r_[jj, tj[keep], diag, np.zeros(len(range(0, m, 997)), np.int64), np.arange(64)]
+    lin = jj * m - jj * (jj - 1) // 2 + (ii - jj)
+    got = S[torch.as_tensor(lin, device="cuda")].cpu().numpy()
+    del S
+    torch.cuda.empty_cache()
+    L21 = ref["A"][p:, :e]
+    want = O.form_entries(L21, ref["piv"][:e], ref["D"], ii, jj)
+    _, Dm, _ = O.unpack(ref, p)
+    Wd = L21 @ Dm
+    bound = np.einsum("tk,tk->t", np.abs(L21[ii]), np.abs(Wd[jj]))
+    assert np.all(np.abs(got - want) <= 1e-11 * bound)
 
 
 def test_large_supernode_tpp_full_size(ctx):
