@@ -14,12 +14,12 @@ namespace ctp {
 const char *kKernelNames[K_NUM_IDS] = {"compress_strict", "keys_to_rowmajor", "compress_relaxed",
                                        "factor_cluster", "solve_fp64", "form_fp64", "form_tc_bf16",
                                        "tpp_full_column", "batch_prepare", "batch_compress_strict",
-                                       "batch_factor_g1", "batch_factor_g2", "batch_factor_g4",
+                                       "batch_factor_cta", "batch_factor_g2", "batch_factor_g4",
                                        "batch_factor_g8", "batch_factor_g16", "batch_solve_fp64",
                                        "batch_form", "w21_from_l", "sys_forward", "sys_backward",
                                        "symv_residual", "backward_error", "axpy", "form_tc_bf16x3",
                                        "sym_grad", "mf_assemble", "mf_extend_add", "spmv_residual",
-                                       "form_tc_bf16x6", "solve_tc"};
+                                       "form_tc_bf16x6", "solve_tc", "batch_factor_warp"};
 }  // namespace ctp
 
 namespace ctp {
@@ -429,9 +429,10 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
     CTP_CUDA(timed(ctx, K_B_COMPRESS, st, [&] { return batch_compress(plan, fronts, w, ctx->num_sms, st); }));
     const int ncls = batch_num_classes(plan);
     if (!ctx->profiling && ncls > 1 && side_streams(ctx, st)) {
-        // the classes touch disjoint fronts: run them side by side (the widest
-        // first, so that its clusters take SMs before the narrow CTAs fill the
-        // rest), joined back into st before the Solve; capturable as a fork/join
+        // the classes touch disjoint fronts: run them side by side (the plan
+        // lists the widest last: launched first, its clusters take SMs before
+        // the narrow CTAs fill the rest), joined back into st before the Solve;
+        // capturable as a fork/join
         CTP_CUDA(cudaEventRecord(ctx->fork_ev, st));
         for (int i = 0; i < ncls; i++) {
             const int c = ncls - 1 - i;
@@ -443,8 +444,9 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
         for (int i = 0; i < ncls && i < kSideStreams; i++) CTP_CUDA(cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
     } else {
         for (int c = 0; c < ncls; c++) {
-            const int G = batch_class_G(plan, c);
-            const int id = K_B_FACTOR_G1 + (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4);
+            const int G = batch_class_G(plan, c), kind = batch_class_kind(plan, c);
+            const int id = kind == kFactorWarp ? K_B_FACTOR_WARP
+                         : K_B_FACTOR_G1 + (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4);
             CTP_CUDA(timed(ctx, id, st, [&] { return batch_factor_class(plan, c, fronts, w, st); }));
         }
     }

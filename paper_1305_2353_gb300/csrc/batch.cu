@@ -177,24 +177,34 @@ struct ctp_plan {
     size_t total;
     int64_t c_items, s_items, f_items, total_rows, q_items, r_items, nxt, nzt;
     struct Class {
-        int G, pmax, count;
-        size_t list_off;  // element offset in the class-list array
+        int kind, G, count;  // kFactor*, cluster width
+        size_t smem;         // dynamic shared memory per CTA
+        int pcap, ldcap;     // warp kernel: largest p and p + R of the class
+        size_t list_off;     // element offset in the class-list array
     };
     std::vector<Class> classes;
     std::vector<unsigned char> blob;  // tables, in workspace order (up to off_sections)
 };
 
-static int batch_cluster_width(int p, int R, int budget_kb) {
-    // narrowest cluster whose shared memory per CTA (its columns of [A11; C],
-    // two pivot columns and the update's per-column scalars) fits the budget (100 KB by default, so that two
-    // clusters' CTAs share an SM), and never more than the kernel can take
-    size_t budget = (size_t)budget_kb * 1024;
-    const size_t cap = factor_batch_max_dynamic_smem();
-    if (budget > cap) budget = cap;
-    for (int G = 1; G <= 16; G <<= 1) {
-        if (factor_smem_bytes(p, R, G) <= budget) return G;
-    }
-    return 16;
+// Pivot-search class of a front.  Its working matrix [A11; C] has p + R rows,
+// where R counts the rows of C that can be nonzero: at most min(p, m) for
+// strict compression (each A21 row lands in one row of C), none for restricted
+// pivoting.  Small fronts go to the warp kernel; fronts whose working matrix
+// fits one CTA under the shared-memory budget go to the CTA kernel, bucketed
+// by the shared memory they need (so that small fronts share an SM: 3, 2 or 1
+// CTAs of the bucket per SM); the rest to the narrowest cluster whose CTAs fit
+// the budget.
+struct ClassKey {
+    int kind, G, bucket;
+};
+static ClassKey batch_class_of(int p, int64_t m, int pivot, size_t budget) {
+    const int R = pivot == CTP_PIV_STRICT ? (int)(m < p ? m : p) : 0;
+    if (p <= 32 && p + R <= 64) return {kFactorWarp, 1, p + R <= 32 ? 0 : 1};
+    const size_t need = factor_smem_bytes(p, R, 1);
+    if (need <= budget) return {kFactorCta, 1, need <= 60 * 1024 ? 0 : (need <= 98 * 1024 ? 1 : 2)};
+    int G = 2;
+    while (G < 16 && factor_smem_bytes(p, R, G) > budget) G <<= 1;
+    return {kFactorCluster, G, 0};
 }
 
 extern "C" {
@@ -271,25 +281,38 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         }
         P->pmax = std::max(P->pmax, b.p);
     }
-    // fronts by cluster width of the pivot search
-    std::vector<std::vector<int>> byG(5);
-    std::vector<int> pmaxG(5, 1);
+    // fronts by pivot-search class: warp (2 buckets), CTA (3 buckets), cluster
+    // (G = 2, 4, 8, 16), in this order; the launch sequence starts from the end
+    size_t budget = (size_t)ctx_batch_smem_kb(ctx) * 1024;
+    if (budget > factor_batch_max_dynamic_smem()) budget = factor_batch_max_dynamic_smem();
+    constexpr int kNumKeys = 2 + 3 + 4;
+    std::vector<std::vector<int>> byKey(kNumKeys);
+    std::vector<int> pmaxK(kNumKeys, 1), ldmaxK(kNumKeys, 1);
+    std::vector<size_t> smemK(kNumKeys, 0);
     for (int f = 0; f < nb; f++) {
-        const int R = opt->pivot == CTP_PIV_STRICT ? tab[f].p : 0;
-        const int G = batch_cluster_width(tab[f].p, R, ctx_batch_smem_kb(ctx));
-        const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4;
-        byG[gi].push_back(f);
-        pmaxG[gi] = std::max(pmaxG[gi], tab[f].p);
+        const int p = tab[f].p;
+        const int64_t m = tab[f].m;
+        const ClassKey k = batch_class_of(p, m, opt->pivot, budget);
+        const int R = opt->pivot == CTP_PIV_STRICT ? (int)(m < p ? m : p) : 0;
+        const int gi = k.G == 2 ? 0 : k.G == 4 ? 1 : k.G == 8 ? 2 : 3;
+        const int key = k.kind == kFactorWarp ? k.bucket : (k.kind == kFactorCta ? 2 + k.bucket : 5 + gi);
+        byKey[key].push_back(f);
+        pmaxK[key] = std::max(pmaxK[key], p);
+        ldmaxK[key] = std::max(ldmaxK[key], p + R);
+        if (k.kind != kFactorWarp) smemK[key] = std::max(smemK[key], factor_smem_bytes(p, R, k.G));
     }
     std::vector<int> lists;
-    for (int gi = 0; gi < 5; gi++) {
-        if (byG[gi].empty()) continue;
+    for (int key = 0; key < kNumKeys; key++) {
+        if (byKey[key].empty()) continue;
         ctp_plan::Class c;
-        c.G = 1 << gi;
-        c.pmax = pmaxG[gi];
-        c.count = (int)byG[gi].size();
+        c.kind = key < 2 ? kFactorWarp : (key < 5 ? kFactorCta : kFactorCluster);
+        c.G = key < 5 ? 1 : (2 << (key - 5));
+        c.pcap = pmaxK[key];
+        c.ldcap = ldmaxK[key];
+        c.smem = c.kind == kFactorWarp ? factor_warp_smem_bytes(c.pcap, c.ldcap) : smemK[key];
+        c.count = (int)byKey[key].size();
         c.list_off = lists.size();
-        lists.insert(lists.end(), byG[gi].begin(), byG[gi].end());
+        lists.insert(lists.end(), byKey[key].begin(), byKey[key].end());
         P->classes.push_back(c);
     }
     P->c_items = (int64_t)citem.size();
@@ -407,6 +430,7 @@ struct BatchLaunch {
 };
 
 int batch_num_classes(const ctp_plan *P) { return (int)P->classes.size(); }
+int batch_class_kind(const ctp_plan *P, int c) { return P->classes[c].kind; }
 int batch_class_G(const ctp_plan *P, int c) { return P->classes[c].G; }
 size_t batch_total(const ctp_plan *P) { return P->total; }
 
@@ -424,8 +448,8 @@ cudaError_t batch_compress(const ctp_plan *P, const ctp_front *fr, char *w, int 
 cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st) {
     const ctp_plan::Class &c = P->classes[ci];
     return launch_factor_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
-                               reinterpret_cast<const int *>(w + P->off_lists) + c.list_off, c.count, c.G,
-                               c.pmax, P->bo, st);
+                               reinterpret_cast<const int *>(w + P->off_lists) + c.list_off, c.count, c.kind,
+                               c.G, c.smem, c.pcap, c.ldcap, P->bo, st);
 }
 cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st) {
     if (P->bo.stc)

@@ -45,6 +45,10 @@ inline int prec_pieces(int prec) {
 }
 size_t factor_batch_max_dynamic_smem();     // dynamic shared memory the batched pivot search can take
 size_t factor_smem_bytes(int p, int R, int G);  // dynamic shared memory of a pivot-search CTA
+size_t factor_warp_smem_bytes(int pcap, int ldcap);  // of a CTA of the warp-per-front kernel
+// kinds of batched pivot-search launch: a warp per front (p <= 32, at most 64
+// rows of [A11; C]), a CTA per front, a cluster of G CTAs per front
+constexpr int kFactorWarp = 0, kFactorCta = 1, kFactorCluster = 2;
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns cudaError_t of the launch)
@@ -122,8 +126,11 @@ struct BatchOpts {
     int stc;         // the Solve runs on the tensor cores
     int64_t xoff, zoff;  // elements between the pieces of the x_e / Z^T tile arrays
 };
-cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
-                                const int *list, int count, int G, int pmax, BatchOpts o,
+// pivot search of the fronts list[0..count) of one class: kind (kFactor*), the
+// cluster width G, the dynamic shared memory per CTA, and for the warp kernel
+// the largest p and p + R of the class (its per-warp slice)
+cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws, const int *list,
+                                int count, int kind, int G, size_t smem, int pcap, int ldcap, BatchOpts o,
                                 cudaStream_t st);
 cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                          const int *item_front, int64_t items, BatchOpts o,
@@ -142,6 +149,7 @@ constexpr int kBatchKp = 256;  // K stride of the stacked BF16 operand buffers
 
 // the batched launch sequence (batch.cu); the plan type is declared in ctp.h
 int batch_num_classes(const ctp_plan *P);
+int batch_class_kind(const ctp_plan *P, int c);  // kFactor*
 int batch_class_G(const ctp_plan *P, int c);
 size_t batch_total(const ctp_plan *P);
 cudaError_t batch_prepare(const ctp_plan *P, char *w, cudaStream_t st);

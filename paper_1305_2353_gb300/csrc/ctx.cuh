@@ -6,12 +6,13 @@
 
 namespace ctp {
 constexpr int kMaxRec = 32768;
-constexpr int kSideStreams = 5;  // one per cluster-width class (G = 1, 2, 4, 8, 16)
+constexpr int kSideStreams = 5;  // the batch's pivot-search classes run on these, round robin
 enum KernelId {
     K_COMPRESS_STRICT = 0, K_KEYS, K_RELAXED, K_FACTOR, K_SOLVE, K_FORM, K_FORM_TC, K_TPP,
     K_B_PREPARE, K_B_COMPRESS, K_B_FACTOR_G1, K_B_FACTOR_G2, K_B_FACTOR_G4, K_B_FACTOR_G8,
     K_B_FACTOR_G16, K_B_SOLVE, K_B_FORM, K_W21, K_SYS_FWD, K_SYS_BWD, K_SYMV, K_BERR, K_AXPY,
-    K_FORM_TC3, K_GRAD, K_MF_ASSEMBLE, K_MF_EXTEND_ADD, K_SPMV, K_FORM_TC6, K_SOLVE_TC, K_NUM_IDS
+    K_FORM_TC3, K_GRAD, K_MF_ASSEMBLE, K_MF_EXTEND_ADD, K_SPMV, K_FORM_TC6, K_SOLVE_TC, K_B_FACTOR_WARP,
+    K_NUM_IDS
 };
 extern const char *kKernelNames[K_NUM_IDS];
 }  // namespace ctp

@@ -3,25 +3,33 @@
 // 2x2 form follows the proof of Theorem 5.2).
 //
 // GB300 design.  The working matrix [A11; C] (A11 held in full symmetric form so
-// that every column carries all of its entries, C the R = p outer rows) is
-// 2p x p doubles -- 1 MB at p = 256, far beyond one SM -- and GB300's FP64 pipe
-// is narrow, so the right-looking updates must be spread over many SMs.  One
-// thread-block cluster of G CTAs owns the matrix: column c lives in the shared
-// memory of CTA (c mod G); partner columns are read through distributed shared
-// memory (DSMEM).
+// that every column carries all of its entries, C the R outer rows that can be
+// nonzero) is (p + R) x p doubles.  Three kernels share one set of rules:
+//
+//  * a team of G CTAs (a thread-block cluster, G >= 2) when it is larger than
+//    one SM's shared memory -- 1 MB at p = 256: column c lives in the shared
+//    memory of CTA (c mod G); other CTAs' columns are read through distributed
+//    shared memory (DSMEM);
+//  * one CTA, no cluster, when it fits (plain shared memory and __syncthreads);
+//  * one warp per front for the small fronts of a batch (p <= 32 and at most 64
+//    rows): no barrier at all, only warp-synchronous steps.
 //
 // Listing 1 is sequential, but a rejected candidate leaves the matrix unchanged,
 // so every candidate tested between two acceptances sees the same matrix.  The
-// kernel therefore tests a window of candidates at once (one warp per candidate,
-// every CTA its own columns) and accepts the lowest-index candidate that passes;
-// all candidates before it in the window were rejected by Listing 1 as well.
-// A round costs one cluster barrier, plus one for the update when a pivot is
-// accepted, instead of one barrier per test:
+// CTA and cluster kernels therefore test a window of candidates at once (one
+// warp per candidate, every CTA its own columns) and accept the lowest-index
+// candidate that passes; all candidates before it in the window were rejected by
+// Listing 1 as well.  A round costs one team barrier, plus one for the update
+// when a pivot is accepted, instead of one barrier per test:
 //   test round   each warp runs the zero test, the 2x2 test with its partner t
 //                (largest |a(m, j)| over live j < m) and the 1x1 test for one
-//                candidate; results are published as a bit mask per CTA;
-//   update       every CTA copies the pivot column(s) over DSMEM and applies the
-//                1x1 or 2x2 update to its own live columns.
+//                candidate; a passing warp pushes (candidate, warp) into every
+//                CTA's slot with a DSMEM atomicMin, so after the barrier each
+//                CTA finds the winner in its own shared memory;
+//   update       every CTA copies the pivot column(s), takes the per-column
+//                scalars from them and applies the 1x1 or 2x2 update to its own
+//                live columns (one CTA barrier, then the team barrier).
+// The warp kernel runs the same tests one candidate at a time.
 // Columns are never moved: accepted pivots leave the live set, and because the
 // paper's stable shift never reorders the remaining columns, the candidate
 // order is simply the original column order of the live columns.  The final
@@ -42,8 +50,10 @@ namespace ctp {
 
 namespace {
 
-constexpr int kT = 256;  // threads per CTA
+constexpr int kT = 256;  // threads per CTA (CTA and cluster kernels)
 constexpr int kNW = kT / 32;
+constexpr int kWarpFronts = 4;  // fronts (warps) per CTA of the warp kernel
+constexpr int kNoKey = 0x7fffffff;
 
 enum { DEC_REJECT = 0, DEC_1X1 = 1, DEC_2X2 = 2, DEC_ZERO = -1 };
 
@@ -52,12 +62,12 @@ struct Decision {
     double d0, d1, d2;  // 1x1: d0 = d; 2x2: a_tt, a_tm, a_mm
     double i0, i1, i2;  // 1x1: i0 = 1/d; 2x2: D^-1 entries (t,t), (m,t), (m,m)
 };
+static_assert(sizeof(Decision) == 64, "Decision is copied as eight 8-byte words");
 
 struct Shared {
-    Decision res[2][kMaxP];  // per own column slot (ncl <= kMaxP), double-buffered
+    Decision res[2][kNW];  // per warp's candidate, double-buffered by round
     Decision cur;
-    unsigned int mask[2][kMaxP / 32];  // passing candidates, by global column index
-    int hi[2];                         // first own candidate not tested this round
+    int cmin[2];           // lowest (candidate * kNW + warp) that passed, pushed by every CTA
     unsigned char live[kMaxP];
     int order[kMaxP];
     int kind[kMaxP];
@@ -65,10 +75,30 @@ struct Shared {
     double sD[2 * kMaxP + 2];
     double sInv[2 * kMaxP + 2];
     int cand[kNW];
-    int cstar, hiall;
+    int cstar;
     int rowmap[kMaxP];  // nonzero outer rows
     int nz_count;
     unsigned char nzflag[kMaxP];
+};
+
+// The team that owns one front: a cluster of G CTAs, or one CTA.
+template <bool kSingle>
+struct Team;
+template <>
+struct Team<true> {
+    __device__ __forceinline__ int rank() const { return 0; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    template <typename T>
+    __device__ __forceinline__ T *at(T *ptr, int) const { return ptr; }
+};
+template <>
+struct Team<false> {
+    cg::cluster_group cl;
+    __device__ __forceinline__ Team() : cl(cg::this_cluster()) {}
+    __device__ __forceinline__ int rank() const { return (int)cl.block_rank(); }
+    __device__ __forceinline__ void sync() const { cl.sync(); }
+    template <typename T>
+    __device__ __forceinline__ T *at(T *ptr, int r) const { return cl.map_shared_rank(ptr, r); }
 };
 
 // Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
@@ -121,15 +151,23 @@ __device__ __forceinline__ double key_val(unsigned long long k) {
     return __longlong_as_double((long long)k);
 }
 
+// live flags of the warp kernel: one bit per column (p <= 32)
+struct BitLive {
+    unsigned bits;
+    __device__ __forceinline__ bool operator[](int i) const { return (bits >> i) & 1u; }
+};
+
 // The tests of Listing 1 for candidate c (one warp): zero test, 2x2 with the
 // partner t, 1x1, from two scans of the column (the partner, then the maxima).
 // cm is the candidate's column (rows 0..p-1 A11, then outer).
 // Column maxima of |a| are taken on the IEEE bit patterns with the sign cleared
 // (integer order = magnitude order), which keeps the scans off the FP64 pipe.
-template <typename ColPtr>
+// The maxima scan keeps four loads per lane in flight: the partner's column
+// may sit in another CTA's shared memory.
+template <typename ColPtr, typename Live>
 __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColPtr colptr,
-                                                   const unsigned char *live, int p, int LD,
-                                                   double u, double small) {
+                                                   const Live &live, int p, int LD, double u,
+                                                   double small) {
     const int lane = threadIdx.x & 31;
     Decision d;
     d.kind = DEC_REJECT;
@@ -163,15 +201,25 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     // adds rows t and c back
     const double *ct = t >= 0 ? colptr(t) : cm;
     unsigned long long vm = 0, vt = 0;
-    for (int i = lane; i < LD; i += 32)
-        if (i >= p || (live[i] && i != t && i != c)) {
-            const unsigned long long km = akey(cm[i]);
-            vm = km > vm ? km : vm;
-            if (t >= 0) {
-                const unsigned long long kt = akey(ct[i]);
+    constexpr int U = 4;
+    for (int i0 = lane; i0 < LD; i0 += 32 * U) {
+        double xm[U], xt[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+            const int i = i0 + 32 * q;
+            xm[q] = i < LD ? cm[i] : 0.0;
+            xt[q] = i < LD ? ct[i] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+            const int i = i0 + 32 * q;
+            if (i < LD && (i >= p || (i != t && i != c && live[i]))) {
+                const unsigned long long km = akey(xm[q]), kt = akey(xt[q]);
+                vm = km > vm ? km : vm;
                 vt = kt > vt ? kt : vt;
             }
         }
+    }
     vm = warp_max_key(vm);
     unsigned long long vall = vm > akey(cm[c]) ? vm : akey(cm[c]);
     if (t >= 0 && akey(cm[t]) > vall) vall = akey(cm[t]);
@@ -201,13 +249,14 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     return d;
 }
 
-__device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) {
-    cg::cluster_group cluster = cg::this_cluster();
+template <bool kSingle>
+__device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
+    Team<kSingle> team;
     extern __shared__ __align__(16) double dsm[];
     __shared__ Shared sh;
 
     const int p = a.p;
-    const int rank = (int)cluster.block_rank();
+    const int rank = team.rank();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // Outer rows: rows of C that are identically zero (a strict C row whose set
     // J_j is empty, or a relaxed row past the last A21 row) stay zero under the
@@ -265,10 +314,7 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
     double *pc0 = dsm + (size_t)ncl * LD;  // pivot column copies
     double *pc1 = pc0 + LD;
     double *cs0 = pc1 + LD, *cs1 = cs0 + ncl, *cas0 = cs1 + ncl, *cas1 = cas0 + ncl;  // update scalars
-    const int nmask = (p + 31) / 32;
-    auto colptr = [&](int c) -> const double * {
-        return cluster.map_shared_rank(cols, c % G) + (size_t)(c / G) * LD;
-    };
+    auto colptr = [&](int c) -> const double * { return team.at(cols, c % G) + (size_t)(c / G) * LD; };
 
     // ---- load: own columns of A11 (full symmetric) and of the nonzero outer rows
     bool nonfinite = false;
@@ -294,8 +340,9 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
         cols[idx] = v;
     }
     for (int i = tid; i < p; i += kT) sh.live[i] = 1;
+    if (tid < 2) sh.cmin[tid] = kNoKey;
     if (nonfinite) atomicCAS(a.info, kInfoOk, (int32_t)CTP_ENONFINITE);
-    cluster.sync();
+    team.sync();
 
     const double u = a.u, small = a.small;
     int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, round = 0;
@@ -315,69 +362,58 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
         const int buf = round & 1;
         round++;
         // ---------------- test round: the live candidates in [m, m + win)
-        // (cluster-wide order); each CTA tests the ones it owns, one per warp.
+        // (team-wide order); each CTA tests the ones it owns, one per warp.
         // The window is 1 after an acceptance and doubles after a round with no
         // pass, so accepted-first candidates cost a single test and runs of
         // rejections are tested in parallel.
-        if (tid < nmask) sh.mask[buf][tid] = 0u;
+        const int hi = min(p, m + win);  // the same on every CTA
         if (warp == 0) {
-            // the window is the index range [m, m + win) (win <= kNW * G, so no
-            // CTA owns more than kNW of its columns); this CTA's live columns in
-            // it, in order, go to its warps (one ballot over its column slots)
-            const int hi = min(p, m + win);
+            // this CTA's live columns in [m, hi), in order, go to its warps
+            // (win <= kNW * G, so no CTA owns more than kNW of them)
             const int j0 = m > rank ? (m - rank + G - 1) / G : 0;
             const int c = rank + G * (j0 + lane);
             const bool ok = c < hi && sh.live[c];
             const unsigned int bal = __ballot_sync(0xffffffffu, ok);
             if (ok) sh.cand[__popc(bal & ((1u << lane) - 1u))] = c;
             if (lane >= __popc(bal) && lane < kNW) sh.cand[lane] = -1;
-            if (lane == 0) sh.hi[buf] = hi;
         }
         __syncthreads();
         {
             const int c = sh.cand[warp];
             if (c >= 0) {
-                Decision d = test_candidate(c, cols + (size_t)(c / G) * LD, colptr, sh.live, p, LD,
-                                            u, small);
-                if (lane == 0) {
-                    sh.res[buf][c / G] = d;
-                    if (d.kind != DEC_REJECT) atomicOr(&sh.mask[buf][c >> 5], 1u << (c & 31));
+                Decision d = test_candidate(c, cols + (size_t)(c / G) * LD, colptr, sh.live, p, LD, u, small);
+                if (d.kind != DEC_REJECT) {
+                    // publish: the decision stays here, (candidate, warp) goes to
+                    // every CTA's slot for this round
+                    if (lane == 0) sh.res[buf][warp] = d;
+                    const int key = c * kNW + warp;
+                    if (lane < G) atomicMin(team.at(&sh.cmin[buf], lane), key);
                 }
             }
         }
-        cluster.sync();
-        // lowest passing candidate over the cluster, and the end of the tested
-        // window: lane r of warp 0 reads CTA r's mask and window end over DSMEM
+        team.sync();
+        // the lowest passing candidate: read the own slot (and clear it for the
+        // round after next), fetch the winner's decision from its CTA
         if (warp == 0) {
-            int cs = p, h = p;
-            if (lane < G) {
-                h = *cluster.map_shared_rank(&sh.hi[buf], lane);
-                const unsigned int *mk = cluster.map_shared_rank(&sh.mask[buf][0], lane);
-                for (int w = 0; w < nmask; w++) {
-                    const unsigned int bits = mk[w];
-                    if (bits) {
-                        cs = w * 32 + __ffs(bits) - 1;
-                        break;
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                cs = min(cs, __shfl_xor_sync(0xffffffffu, cs, o));
-                h = min(h, __shfl_xor_sync(0xffffffffu, h, o));
-            }
+            int key = 0;
             if (lane == 0) {
-                sh.cstar = cs;
-                sh.hiall = h;
-                if (cs < h) sh.cur = *cluster.map_shared_rank(&sh.res[buf][cs / G], cs % G);
+                key = sh.cmin[buf];
+                sh.cmin[buf] = kNoKey;
             }
+            key = __shfl_sync(0xffffffffu, key, 0);
+            const int cs = key == kNoKey ? p : key / kNW;
+            if (cs < p && lane < 8) {
+                const Decision *src = team.at(&sh.res[buf][key % kNW], cs % G);
+                reinterpret_cast<double *>(&sh.cur)[lane] = reinterpret_cast<const double *>(src)[lane];
+            }
+            if (lane == 0) sh.cstar = cs;
         }
         __syncthreads();
         const int cstar = sh.cstar;
-        if (cstar >= sh.hiall) {
+        if (cstar >= hi) {
             // every tested candidate before the window's end failed: the sweep
             // continues there, with a wider window
-            m = sh.hiall;
+            m = hi;
             win = win * 2 < win_max ? win * 2 : win_max;
             continue;
         }
@@ -405,44 +441,72 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
             accepted = 1;
             m = cstar + 1;
             // no update; the next round writes the other buffers, and the round
-            // after that comes behind the next cluster barrier
+            // after that comes behind the next team barrier
             continue;
         }
         // ---------------- update: apply the pivot to the own live columns
         const int q0 = (dv.kind == DEC_2X2) ? dv.t : dv.m;
         const int q1 = (dv.kind == DEC_2X2) ? dv.m : -1;
         {
+            // copies of the pivot column(s), the per-column scalars read from
+            // them where they live, and the bookkeeping of the pivot, in one
+            // phase (the pivot columns are not written in this round, and
+            // live[] of the pivot columns is read nowhere in this phase)
             const double *s0 = colptr(q0);
-            for (int i = tid; i < LD; i += kT) pc0[i] = s0[i];
-            if (q1 >= 0) {
-                const double *s1 = colptr(q1);
-                for (int i = tid; i < LD; i += kT) pc1[i] = s1[i];
+            const double *s1 = q1 >= 0 ? colptr(q1) : s0;
+            for (int i = tid; i < LD; i += kT) {
+                pc0[i] = s0[i];
+                if (q1 >= 0) pc1[i] = s1[i];
+            }
+            for (int lc = tid; lc < ncl; lc += kT) {
+                const int c = lc * G + rank;
+                const bool upd = c < p && c != q0 && c != q1 && sh.live[c];
+                double v0 = 0.0, v1 = 0.0, w0 = 0.0, w1 = 0.0;
+                if (upd && q1 < 0) {
+                    const double b0 = s0[c];
+                    v0 = b0 * dv.i0;
+                    w0 = fabs(b0) * fabs(dv.i0);
+                } else if (upd) {
+                    const double i11 = dv.i0, i21 = dv.i1, i22 = dv.i2;
+                    const double b0 = s0[c], b1 = s1[c];
+                    v0 = i11 * b0 + i21 * b1;
+                    v1 = i21 * b0 + i22 * b1;
+                    const double ab0 = fabs(b0), ab1 = fabs(b1);
+                    w0 = fabs(i11) * ab0 + fabs(i21) * ab1;
+                    w1 = fabs(i21) * ab0 + fabs(i22) * ab1;
+                }
+                cs0[lc] = v0, cs1[lc] = v1, cas0[lc] = w0, cas1[lc] = w1;
+                sh.nzflag[lc] = upd ? 1 : 0;
+            }
+            if (tid == 0) {
+                if (q1 < 0) {
+                    sh.live[q0] = 0;
+                    sh.order[nelim] = q0;
+                    sh.kind[nelim] = CTP_PIVKIND_1X1;
+                    sh.sD[2 * nelim] = dv.d0;
+                    sh.sD[2 * nelim + 1] = 0.0;
+                    sh.sInv[2 * nelim] = dv.i0;
+                    sh.sInv[2 * nelim + 1] = 0.0;
+                } else {
+                    sh.live[q0] = 0;
+                    sh.live[q1] = 0;
+                    sh.order[nelim] = q0;
+                    sh.order[nelim + 1] = q1;
+                    sh.kind[nelim] = CTP_PIVKIND_2X2_FIRST;
+                    sh.kind[nelim + 1] = CTP_PIVKIND_2X2_SECOND;
+                    sh.sD[2 * nelim] = dv.d0;
+                    sh.sD[2 * nelim + 1] = dv.d1;
+                    sh.sD[2 * nelim + 2] = dv.d2;
+                    sh.sD[2 * nelim + 3] = 0.0;
+                    sh.sInv[2 * nelim] = dv.i0;
+                    sh.sInv[2 * nelim + 1] = dv.i1;
+                    sh.sInv[2 * nelim + 2] = dv.i2;
+                    sh.sInv[2 * nelim + 3] = 0.0;
+                }
             }
         }
         __syncthreads();
         const bool abs_rows = a.abs_update != 0;
-        // per own live column: the update's scalars (a column that is not live,
-        // or is a pivot column, gets none and is skipped)
-        for (int lc = tid; lc < ncl; lc += kT) {
-            const int c = lc * G + rank;
-            const bool upd = c < p && sh.live[c] && c != q0 && c != q1;
-            double s0 = 0.0, s1 = 0.0, as0 = 0.0, as1 = 0.0;
-            if (upd && q1 < 0) {
-                s0 = pc0[c] * dv.i0;
-                as0 = fabs(pc0[c]) * fabs(dv.i0);
-            } else if (upd) {
-                const double i11 = dv.i0, i21 = dv.i1, i22 = dv.i2;
-                const double b0 = pc0[c], b1 = pc1[c];
-                s0 = i11 * b0 + i21 * b1;
-                s1 = i21 * b0 + i22 * b1;
-                const double ab0 = fabs(b0), ab1 = fabs(b1);
-                as0 = fabs(i11) * ab0 + fabs(i21) * ab1;
-                as1 = fabs(i21) * ab0 + fabs(i22) * ab1;
-            }
-            cs0[lc] = s0, cs1[lc] = s1, cas0[lc] = as0, cas1[lc] = as1;
-            sh.nzflag[lc] = upd ? 1 : 0;
-        }
-        __syncthreads();
         // the update over (column, row) pairs
         for (int idx = tid, lc2 = tid / LD, i2 = tid - (tid / LD) * LD; idx < ncl * LD; idx += kT) {
             const int lc = lc2, i = i2;
@@ -453,7 +517,7 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
                 lc2++;
             }
             if (!sh.nzflag[lc]) continue;
-            if (i < p && (!sh.live[i] || i == q0 || i == q1)) continue;
+            if (i < p && !sh.live[i]) continue;  // the pivot rows are no longer live
             double *e = cols + idx;
             if (q1 < 0) {
                 // 1x1: a(i,c) -= a(i,q) (a(c,q) / d); C rows (strict): c += chat |a(c,q)|
@@ -470,38 +534,10 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
                     *e += x0 * cas0[lc] + x1 * cas1[lc];
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            if (q1 < 0) {
-                sh.live[q0] = 0;
-                sh.order[nelim] = q0;
-                sh.kind[nelim] = CTP_PIVKIND_1X1;
-                sh.sD[2 * nelim] = dv.d0;
-                sh.sD[2 * nelim + 1] = 0.0;
-                sh.sInv[2 * nelim] = dv.i0;
-                sh.sInv[2 * nelim + 1] = 0.0;
-            } else {
-                sh.live[q0] = 0;
-                sh.live[q1] = 0;
-                sh.order[nelim] = q0;
-                sh.order[nelim + 1] = q1;
-                sh.kind[nelim] = CTP_PIVKIND_2X2_FIRST;
-                sh.kind[nelim + 1] = CTP_PIVKIND_2X2_SECOND;
-                sh.sD[2 * nelim] = dv.d0;
-                sh.sD[2 * nelim + 1] = dv.d1;
-                sh.sD[2 * nelim + 2] = dv.d2;
-                sh.sD[2 * nelim + 3] = 0.0;
-                sh.sInv[2 * nelim] = dv.i0;
-                sh.sInv[2 * nelim + 1] = dv.i1;
-                sh.sInv[2 * nelim + 2] = dv.i2;
-                sh.sInv[2 * nelim + 3] = 0.0;
-            }
-        }
-        __syncthreads();
         nelim += (q1 < 0) ? 1 : 2;
         accepted = 1;
         m = cstar + 1;
-        cluster.sync();  // every update done before the next tests read columns
+        team.sync();  // every update done before the next tests read columns
     }
 
     // ---- final order: accepted pivots, then the delayed columns in original order
@@ -548,20 +584,14 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
             if (i == 0) out[pos] = sh.sD[2 * pos];
         } else if (kd == CTP_PIVKIND_2X2_FIRST) {
             const int mo = sh.order[pos + 1];
-            if (pi > pos + 1) {
-                const double *cmo = cluster.map_shared_rank(cols, mo % G) + (size_t)(mo / G) * LD;
-                out[pi] = col[i] * sh.sInv[2 * pos] + cmo[i] * sh.sInv[2 * pos + 1];
-            }
+            if (pi > pos + 1) out[pi] = col[i] * sh.sInv[2 * pos] + colptr(mo)[i] * sh.sInv[2 * pos + 1];
             if (i == 0) {
                 out[pos] = sh.sD[2 * pos];
                 out[pos + 1] = sh.sD[2 * pos + 1];
             }
         } else {  // second column of a 2x2
             const int to = sh.order[pos - 1];
-            if (pi > pos) {
-                const double *cto = cluster.map_shared_rank(cols, to % G) + (size_t)(to / G) * LD;
-                out[pi] = cto[i] * sh.sInv[2 * (pos - 1) + 1] + col[i] * sh.sInv[2 * (pos - 1) + 2];
-            }
+            if (pi > pos) out[pi] = colptr(to)[i] * sh.sInv[2 * (pos - 1) + 1] + col[i] * sh.sInv[2 * (pos - 1) + 2];
             if (i == 0) out[pos] = sh.sD[2 * pos];
         }
     }
@@ -576,17 +606,17 @@ __device__ __forceinline__ void factor_cluster_body(const FactorArgs &a, int G) 
         }
         if (tid == 0) *a.nelim = e;
     }
-    cluster.sync();  // no CTA leaves while its shared memory may still be read
+    team.sync();  // no CTA leaves while its shared memory may still be read
 }
 
-__global__ void __launch_bounds__(kT, 3) k_factor_cluster(FactorArgs a, int G) { factor_cluster_body(a, G); }
+__global__ void __launch_bounds__(kT, 3) k_factor_cluster(FactorArgs a, int G) { factor_body<false>(a, G); }
+__global__ void __launch_bounds__(kT, 3) k_factor_cta(FactorArgs a) { factor_body<true>(a, 1); }
 
-// Batched: cluster c factors front list[c]; its arguments come from the
-// front's descriptor and its workspace section.
-__global__ void __launch_bounds__(kT, 3)
-    k_factor_cluster_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
-                           char *ws, const int *__restrict__ list, BatchOpts o, int G) {
-    const int f = list[blockIdx.x / G];
+// The arguments of front f of a batch, from its descriptor and its workspace
+// section.
+__device__ __forceinline__ FactorArgs batch_args(const ctp_front *__restrict__ fronts,
+                                                 const BFront *__restrict__ tab, char *ws, int f,
+                                                 const BatchOpts &o) {
     const ctp_front fr = fronts[f];
     const BFront bt = tab[f];
     ctp_options oo;
@@ -611,7 +641,235 @@ __global__ void __launch_bounds__(kT, 3)
     a.Dinv = reinterpret_cast<double *>(base + sec.Dinv);
     a.info = reinterpret_cast<int32_t *>(base + sec.info);
     a.rowflags = o.pivot == CTP_PIV_STRICT ? reinterpret_cast<const int32_t *>(base + sec.nz) : nullptr;
-    factor_cluster_body(a, G);
+    return a;
+}
+
+// Batched: cluster c (or CTA c) factors front list[c].
+__global__ void __launch_bounds__(kT, 3)
+    k_factor_cluster_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
+                           char *ws, const int *__restrict__ list, BatchOpts o, int G) {
+    factor_body<false>(batch_args(fronts, tab, ws, list[blockIdx.x / G], o), G);
+}
+__global__ void __launch_bounds__(kT, 3)
+    k_factor_cta_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
+                       const int *__restrict__ list, BatchOpts o) {
+    factor_body<true>(batch_args(fronts, tab, ws, list[blockIdx.x], o), 1);
+}
+
+// ---------------------------------------------------------------------------
+// One warp per front (p <= 32, at most 64 rows of [A11; C]): Listing 1 one
+// candidate at a time, lanes over rows, no barrier beyond the warp.  Lane k < p
+// keeps the record of pivot position k (column, kind, D, D^-1).
+__global__ void __launch_bounds__(32 * kWarpFronts)
+    k_factor_warp_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
+                        const int *__restrict__ list, int count, BatchOpts o, int pcap, int ldcap) {
+    extern __shared__ __align__(16) double wsm[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kWarpFronts + w;
+    if (item >= count) return;  // the whole warp; nothing below waits on other warps
+    const unsigned full = 0xffffffffu;
+    const FactorArgs a = batch_args(fronts, tab, ws, list[item], o);
+    const int p = a.p;
+    double *cols = wsm + (size_t)w * pcap * ldcap;
+    // nonzero outer rows, in order (a.R <= p <= 32: one row per lane); lane k
+    // holds the C row of outer row k
+    bool nz = false;
+    if (lane < a.R) {
+        if (a.rowflags != nullptr) {
+            nz = a.rowflags[lane] != 0;
+        } else {
+            for (int k = 0; k < p && !nz; k++) nz = a.C[(int64_t)lane * p + k] != 0.0;
+        }
+    }
+    const unsigned nzbits = __ballot_sync(full, nz);
+    const int R = __popc(nzbits);
+    int myrow = 0;
+    {
+        unsigned b = nzbits;
+        for (int s = 0; s < lane && b; s++) b &= b - 1;
+        if (b) myrow = __ffs(b) - 1;
+    }
+    const int LD = p + R;
+    bool nonfinite = false;
+    for (int c = 0; c < p; c++)
+        for (int i0 = 0; i0 < LD; i0 += 32) {  // the same trip count on every lane
+            const int i = i0 + lane;
+            const int r = __shfl_sync(full, myrow, (i - p) & 31);
+            if (i < LD) {
+                const double v = (i < p) ? ((i >= c) ? a.A[(int64_t)c * a.lda + i] : a.A[(int64_t)i * a.lda + c])
+                                         : a.C[(int64_t)r * p + c];
+                nonfinite |= !isfinite(v);
+                cols[(size_t)c * LD + i] = v;
+            }
+        }
+    if (__any_sync(full, nonfinite) && lane == 0) atomicCAS(a.info, kInfoOk, (int32_t)CTP_ENONFINITE);
+    __syncwarp();
+
+    const double u = a.u, small = a.small;
+    const bool abs_rows = a.abs_update != 0;
+    BitLive live;
+    live.bits = p >= 32 ? full : ((1u << p) - 1u);
+    // record of pivot position `lane`
+    int r_order = 0, r_kind = CTP_PIVKIND_DELAYED;
+    double r_d0 = 0.0, r_d1 = 0.0, r_i0 = 0.0, r_i1 = 0.0;
+    int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0;
+    auto colptr = [&](int c) -> const double * { return cols + (size_t)c * LD; };
+    for (;;) {
+        if (nelim >= p) break;
+        while (m < p && !live[m]) m++;
+        if (m >= p) {
+            if (!accepted) break;  // a whole sweep without a pivot: stop
+            accepted = 0;
+            m = 0;
+            continue;
+        }
+        const Decision dv = test_candidate(m, colptr(m), colptr, live, p, LD, u, small);
+        if (dv.kind == DEC_REJECT) {
+            m++;
+            continue;
+        }
+        if (dv.kind == DEC_ZERO) {
+            if (lane == nelim) {
+                r_order = m;
+                r_kind = CTP_PIVKIND_ZERO;
+            }
+            live.bits &= ~(1u << m);
+            nelim++;
+            accepted = 1;
+            m++;
+            continue;
+        }
+        const int q0 = (dv.kind == DEC_2X2) ? dv.t : dv.m;
+        const int q1 = (dv.kind == DEC_2X2) ? dv.m : -1;
+        const double *p0 = colptr(q0);
+        const double *p1 = q1 >= 0 ? colptr(q1) : p0;
+        unsigned upd_cols = live.bits & ~(1u << q0);
+        if (q1 >= 0) upd_cols &= ~(1u << q1);
+        const unsigned rows_live = upd_cols;  // the live A11 rows after this pivot
+        // the update, column by column, lanes over rows (the pivot columns are only read)
+        while (upd_cols) {
+            const int c = __ffs(upd_cols) - 1;
+            upd_cols &= upd_cols - 1;
+            double *col = cols + (size_t)c * LD;
+            double v0, v1 = 0.0, w0, w1 = 0.0;
+            if (q1 < 0) {
+                const double b0 = p0[c];
+                v0 = b0 * dv.i0;
+                w0 = fabs(b0) * fabs(dv.i0);
+            } else {
+                const double b0 = p0[c], b1 = p1[c];
+                v0 = dv.i0 * b0 + dv.i1 * b1;
+                v1 = dv.i1 * b0 + dv.i2 * b1;
+                w0 = fabs(dv.i0) * fabs(b0) + fabs(dv.i1) * fabs(b1);
+                w1 = fabs(dv.i1) * fabs(b0) + fabs(dv.i2) * fabs(b1);
+            }
+            for (int i = lane; i < LD; i += 32) {
+                if (i < p && !((rows_live >> i) & 1u)) continue;
+                if (q1 < 0) {
+                    if (i < p || !abs_rows)
+                        col[i] -= p0[i] * v0;
+                    else
+                        col[i] += p0[i] * w0;  // eq. (4.3)
+                } else {
+                    const double x0 = p0[i], x1 = p1[i];
+                    if (i < p || !abs_rows)
+                        col[i] -= x0 * v0 + x1 * v1;
+                    else
+                        col[i] += x0 * w0 + x1 * w1;
+                }
+            }
+        }
+        __syncwarp();
+        if (q1 < 0) {
+            if (lane == nelim) {
+                r_order = q0;
+                r_kind = CTP_PIVKIND_1X1;
+                r_d0 = dv.d0;
+                r_i0 = dv.i0;
+            }
+            live.bits &= ~(1u << q0);
+            nelim++;
+        } else {
+            if (lane == nelim) {
+                r_order = q0;
+                r_kind = CTP_PIVKIND_2X2_FIRST;
+                r_d0 = dv.d0;
+                r_d1 = dv.d1;
+                r_i0 = dv.i0;
+                r_i1 = dv.i1;
+            }
+            if (lane == nelim + 1) {
+                r_order = q1;
+                r_kind = CTP_PIVKIND_2X2_SECOND;
+                r_d0 = dv.d2;
+                r_i0 = dv.i2;
+            }
+            live.bits &= ~((1u << q0) | (1u << q1));
+            nelim += 2;
+        }
+        accepted = 1;
+        m = dv.m + 1;
+    }
+    // the delayed columns after the pivots, in original order
+    {
+        const unsigned rest = live.bits;
+        const int k = lane - nelim;  // this lane's rank among the delayed positions
+        if (k >= 0 && k < __popc(rest)) {
+            unsigned b = rest;
+            for (int s = 0; s < k; s++) b &= b - 1;
+            r_order = __ffs(b) - 1;
+            r_kind = CTP_PIVKIND_DELAYED;
+        }
+    }
+    // output position of column `lane`
+    int pos_c = 0;
+    for (int k = 0; k < p; k++)
+        if (__shfl_sync(full, r_order, k) == lane) pos_c = k;
+    // write back the A11 block in pivot order (lower triangle): lane i takes
+    // source row i, which goes to output row pos_c
+    for (int pos = 0; pos < p; pos++) {
+        const int c = __shfl_sync(full, r_order, pos);
+        const int kd = __shfl_sync(full, r_kind, pos);
+        const double sd0 = __shfl_sync(full, r_d0, pos), sd1 = __shfl_sync(full, r_d1, pos);
+        const double si0 = __shfl_sync(full, r_i0, pos), si1 = __shfl_sync(full, r_i1, pos);
+        const int cnext = __shfl_sync(full, r_order, pos + 1 < p ? pos + 1 : pos);
+        const int cprev = __shfl_sync(full, r_order, pos > 0 ? pos - 1 : 0);
+        const double prev_i1 = __shfl_sync(full, r_i1, pos > 0 ? pos - 1 : 0);
+        const double *col = colptr(c);
+        double *out = a.A + (int64_t)pos * a.lda;
+        const int i = lane, pi = pos_c;
+        if (i < p) {
+            if (kd == CTP_PIVKIND_DELAYED) {
+                if (pi >= pos) out[pi] = col[i];
+            } else if (kd == CTP_PIVKIND_ZERO) {
+                if (pi >= pos) out[pi] = 0.0;
+            } else if (kd == CTP_PIVKIND_1X1) {
+                if (pi > pos) out[pi] = col[i] * si0;
+                if (i == 0) out[pos] = sd0;
+            } else if (kd == CTP_PIVKIND_2X2_FIRST) {
+                if (pi > pos + 1) out[pi] = col[i] * si0 + colptr(cnext)[i] * si1;
+                if (i == 0) {
+                    out[pos] = sd0;
+                    out[pos + 1] = sd1;
+                }
+            } else {  // second column of a 2x2: D^-1 entries (m,t) and (m,m)
+                if (pi > pos) out[pi] = colptr(cprev)[i] * prev_i1 + col[i] * si0;
+                if (i == 0) out[pos] = sd0;
+            }
+        }
+    }
+    if (lane < p) {
+        a.perm[lane] = r_order;
+        a.piv[lane] = r_kind;
+        // D: (k,k) and, for the first of a 2x2, (k+1,k); D^-1 in the same slots
+        const bool first2 = r_kind == CTP_PIVKIND_2X2_FIRST;
+        const bool pivot = r_kind == CTP_PIVKIND_1X1 || first2 || r_kind == CTP_PIVKIND_2X2_SECOND;
+        a.D[2 * lane] = pivot ? r_d0 : 0.0;
+        a.D[2 * lane + 1] = first2 ? r_d1 : 0.0;
+        a.Dinv[2 * lane] = pivot ? r_i0 : 0.0;
+        a.Dinv[2 * lane + 1] = first2 ? r_i1 : 0.0;
+    }
+    if (lane == 0) *a.nelim = nelim;
 }
 
 }  // namespace
@@ -621,6 +879,17 @@ static size_t factor_smem(int p, int R, int G) {
     return sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R) + 4 * (size_t)ncl);
 }
 size_t factor_smem_bytes(int p, int R, int G) { return factor_smem(p, R, G); }
+size_t factor_warp_smem_bytes(int pcap, int ldcap) {
+    return sizeof(double) * (size_t)kWarpFronts * pcap * ldcap;
+}
+
+static cudaError_t launch_factor_cta(const FactorArgs &a, cudaStream_t st) {
+    const size_t smem = factor_smem(a.p, a.R, 1);
+    cudaError_t err = smem_at_least((const void *)k_factor_cta, smem);
+    if (err != cudaSuccess) return err;
+    k_factor_cta<<<1, kT, smem, st>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t st) {
     // preferred cluster width by p (unless the caller asks for one): more CTAs
@@ -628,9 +897,8 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t s
     // barriers cheaper; widen further if the columns do not fit on chip
     int G = G_req > 0 ? G_req : (a.p > 128 ? 16 : (a.p > 64 ? 8 : (a.p > 16 ? 4 : 1)));
     while (factor_smem(a.p, a.R, G) > 160 * 1024 && G < 16) G <<= 1;
-    size_t smem = factor_smem(a.p, a.R, G);
-    cudaError_t err = smem_at_least((const void *)k_factor_cluster, smem);
-    if (err != cudaSuccess) return err;
+    if (G == 1) return launch_factor_cta(a, st);  // one CTA: no cluster
+    cudaError_t err;
     if (G > 8) {
         err = cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (err != cudaSuccess) return err;
@@ -646,7 +914,7 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t s
     cfg.numAttrs = 1;
     // fall back to narrower clusters if this one cannot be scheduled
     for (;;) {
-        smem = factor_smem(a.p, a.R, G);
+        const size_t smem = factor_smem(a.p, a.R, G);
         cfg.gridDim = dim3(G, 1, 1);
         cfg.dynamicSmemBytes = smem;
         attr[0].val.clusterDim.x = G;
@@ -655,36 +923,53 @@ cudaError_t launch_factor_cluster(const FactorArgs &a, int G_req, cudaStream_t s
         if (err == cudaSuccess) err = cudaOccupancyMaxActiveClusters(&nclusters, k_factor_cluster, &cfg);
         if (err == cudaSuccess && nclusters > 0) break;
         (void)cudaGetLastError();
-        if (G <= 1 || factor_smem(a.p, a.R, G >> 1) > 160 * 1024) return err != cudaSuccess ? err : cudaErrorLaunchOutOfResources;
+        if (G <= 1 || factor_smem(a.p, a.R, G >> 1) > 160 * 1024)
+            return err != cudaSuccess ? err : cudaErrorLaunchOutOfResources;
         G >>= 1;
+        if (G == 1) return launch_factor_cta(a, st);
     }
     return cudaLaunchKernelEx(&cfg, k_factor_cluster, a, G);
 }
 
 size_t factor_batch_max_dynamic_smem() {
-    // per-CTA opt-in limit minus what the kernel holds statically
+    // per-CTA opt-in limit minus what the batched CTA and cluster kernels hold
+    // statically
     static size_t cached = 0;
     if (cached == 0) {
         int dev = 0, optin = 0;
-        cudaFuncAttributes fa;
+        cudaFuncAttributes fa, fb;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, k_factor_cluster_batch) != cudaSuccess) {
+            cudaFuncGetAttributes(&fa, k_factor_cluster_batch) != cudaSuccess ||
+            cudaFuncGetAttributes(&fb, k_factor_cta_batch) != cudaSuccess) {
             (void)cudaGetLastError();
             return 100 * 1024;
         }
-        cached = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        const size_t st = fa.sharedSizeBytes > fb.sharedSizeBytes ? fa.sharedSizeBytes : fb.sharedSizeBytes;
+        cached = (size_t)optin > st ? (size_t)optin - st : 0;
     }
     return cached;
 }
 
-cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws,
-                                const int *list, int count, int G, int pmax, BatchOpts o,
+cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws, const int *list,
+                                int count, int kind, int G, size_t smem, int pcap, int ldcap, BatchOpts o,
                                 cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    const int R = o.pivot == CTP_PIV_STRICT ? pmax : 0;
-    const size_t smem = factor_smem(pmax, R, G);
-    cudaError_t err = smem_at_least((const void *)k_factor_cluster_batch, smem);
+    cudaError_t err;
+    if (kind == kFactorWarp) {
+        err = smem_at_least((const void *)k_factor_warp_batch, smem);
+        if (err != cudaSuccess) return err;
+        const unsigned grid = (unsigned)((count + kWarpFronts - 1) / kWarpFronts);
+        k_factor_warp_batch<<<grid, 32 * kWarpFronts, smem, st>>>(fronts, tab, ws, list, count, o, pcap, ldcap);
+        return cudaGetLastError();
+    }
+    if (kind == kFactorCta) {
+        err = smem_at_least((const void *)k_factor_cta_batch, smem);
+        if (err != cudaSuccess) return err;
+        k_factor_cta_batch<<<(unsigned)count, kT, smem, st>>>(fronts, tab, ws, list, o);
+        return cudaGetLastError();
+    }
+    err = smem_at_least((const void *)k_factor_cluster_batch, smem);
     if (err != cudaSuccess) return err;
     if (G > 8) {
         err = cudaFuncSetAttribute(k_factor_cluster_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -9,7 +9,7 @@ from paper_1305_2353_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-from test_gpu_supernode import compare, min_margin, _bf16_bound  # noqa: E402
+from test_gpu_supernode import check_backward_error, compare, min_margin, _bf16_bound  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -146,9 +146,12 @@ def test_batch_8192_fronts_every_front_matches_oracle(ctx):
     """The full 8192-front batch of the benchmark (p log-uniform in [8, 256],
     n - p log-uniform in [0, 16p], N(0,1), 2% zero diagonals), strict
     compressed pivoting: every front's pivot sequence, kinds and nelim equal the
-    oracle's, and L, D agree within 1e-10, in FP64 and with the split-BF16
-    tensor-core Form (pivots do not depend on the Form's precision).  No
-    threshold test of the oracle on this batch lies within 1e-10 of its bound."""
+    oracle's, in FP64 and with the split-BF16 tensor-core Form (pivots do not
+    depend on the Form's precision), and every FP64 factor passes the backward
+    error bars of check_backward_error.  (No threshold test of the oracle on this
+    batch lies within 1e-10 of its bound.  L itself is not compared entry by
+    entry here: some fronts grow by 4e3, and then two valid rounding orders
+    already differ by more than 1e-10 of max |L|.)"""
     from paper_1305_2353_gb300 import ctp
     fr = inputs.batch(8192, seed=0)
     refs = [O.factor(A, A.shape[1], "strict") for A in fr]
@@ -168,15 +171,10 @@ def test_batch_8192_fronts_every_front_matches_oracle(ctx):
                 bad.append(k)
                 continue
             if prec != "fp64":
-                continue   # L21 carries no Form rounding, but the FP64 run checks it already
-            Ag = Ah[int(b.a_off[k]):int(b.a_off[k + 1])].reshape(p, n).T.copy()
-            Ar = ref["A"].copy()
-            iu = np.triu_indices(p, 1)
-            Ag[:p][iu] = 0.0
-            Ar[:p][iu] = 0.0
-            assert np.allclose(Ag, Ar, rtol=1e-10, atol=1e-10 * max(np.abs(Ar).max(), 1.0)), k
-            Dg = D[2 * pv.start:2 * pv.stop]
-            assert np.allclose(Dg, ref["D"], rtol=1e-10, atol=1e-10 * max(np.abs(ref["D"]).max(), 1e-300)), k
+                continue
+            got = dict(A=Ah[int(b.a_off[k]):int(b.a_off[k + 1])].reshape(p, n).T.copy(), perm=perm[pv],
+                       piv=piv[pv], D=D[2 * pv.start:2 * pv.stop], nelim=int(ne[k]))
+            check_backward_error(A, p, got, ref)
         assert bad == [], (prec, bad[:10])
         del b
         torch.cuda.empty_cache()

@@ -1,13 +1,16 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Bars: the strict compressed matrix and the row sets J are bit-exact; pivot
-sequences, pivot kinds and nelim are identical whenever no threshold test of
-the oracle lies within 1e-10 (relative) of its bound; L, D, the delayed block
-and S agree within FP64 rounding (1e-10 relative to the largest entry); the
-GPU factor satisfies ||PAP^T - LDL^T|| <= 1e-14 (max-abs norm over
-the stored trapezoid, delayed block counted as residual) relative to
-max |L||D||L^T|: the growth-normalised backward error (it equals the plain
-||A||-normalised one when the factor does not grow).
+sequences, pivot kinds and nelim are identical (every case is chosen so that no
+threshold test of the oracle lies within 1e-10, relative, of its bound, and a
+case that does fails); L, D, the delayed block and S agree within FP64 rounding
+(1e-10 relative to the largest entry); the GPU factor satisfies
+||PAP^T - LDL^T|| <= 1e-14 (max-abs norm over the stored trapezoid, delayed
+block counted as residual) relative to max |L||D||L^T| -- the growth-normalised
+backward error, which equals the plain ||A||-normalised one when the factor
+does not grow -- and its plain (||A||-normalised) backward error is at most
+twice the oracle's own on the same input plus 8 units of FP64 rounding at the
+factor's growth.
 """
 import numpy as np
 import pytest
@@ -46,36 +49,36 @@ def run_gpu(ctx, A, p, pivot="strict", smode="none", u=0.01):
     return sn.result()
 
 
-def recon_error(A, p, res):
-    """Backward error of the factor, max |PAP^T - (LDL^T + [0; R])| over the
-    stored trapezoid, divided by max |L||D||L^T| + |R| (the scale that FP64
-    rounding of the recurrence is proportional to; u = 0.01 lets |L||D||L^T|
-    exceed |A| by four orders of magnitude on random inputs)."""
+def factor_errors(A, p, res):
+    """(growth-normalised error, raw error, growth) of a factored supernode over
+    the stored trapezoid: the error is max |PAP^T - (LDL^T + [0; R])|, divided by
+    max(|L||D||L^T| + |R|) (at least max |A|) or by max |A|; the growth is
+    max(|L||D||L^T| + |R|) / max |A|."""
     n = A.shape[0]
     e = res["nelim"]
     L, Dm, R = O.unpack(res, p)
     Ap = O.permuted_supernode(A, p, res["perm"])
-    rec = L @ Dm @ L[:p, :].T
-    scale = np.abs(L) @ np.abs(Dm) @ np.abs(L[:p, :].T)
+    rec = (L @ Dm) @ L[:p, :].T
+    scale = np.abs(L) @ (np.abs(Dm) @ np.abs(L[:p, :].T))
     rec[:, e:] += R
     scale[:, e:] += np.abs(R)
     mask = np.ones((n, p), bool)
     mask[:p, :] = np.tril(np.ones((p, p), bool))
-    return np.abs(Ap - rec)[mask].max() / max(scale[mask].max(), np.abs(A).max())
+    err = np.abs(Ap - rec)[mask].max()
+    amax = max(np.abs(A).max(), 1e-300)
+    smax = scale[mask].max()
+    return err / max(smax, amax), err / amax, smax / amax
 
 
-def raw_error(A, p, res):
-    """max |PAP^T - (LDL^T + [0; R])| over the stored trapezoid, divided by
-    max |A| (the plain, not growth-normalised, backward error)."""
-    n = A.shape[0]
-    e = res["nelim"]
-    L, Dm, R = O.unpack(res, p)
-    Ap = O.permuted_supernode(A, p, res["perm"])
-    rec = L @ Dm @ L[:p, :].T
-    rec[:, e:] += R
-    mask = np.ones((n, p), bool)
-    mask[:p, :] = np.tril(np.ones((p, p), bool))
-    return np.abs(Ap - rec)[mask].max() / max(np.abs(A).max(), 1e-300)
+def check_backward_error(A, p, got, ref):
+    """The GPU factor's growth-normalised backward error is <= 1e-14, and its raw
+    error is at most twice the oracle's own raw error on the same input plus 8
+    units of FP64 rounding at the factor's growth (the two round in different
+    orders, the GPU with fused multiply-adds)."""
+    g, raw_g, growth = factor_errors(A, p, got)
+    _, raw_o, _ = factor_errors(A, p, ref)
+    assert g <= 1e-14
+    assert raw_g <= 2.0 * raw_o + 8.0 * 2.0 ** -52 * growth, (raw_g, raw_o, growth)
 
 
 def compare(ref, got, p, A, check_recon=True):
@@ -84,8 +87,7 @@ def compare(ref, got, p, A, check_recon=True):
     are chosen so that no logged threshold test of the oracle lies within 1e-10
     (relative) of its bound; a case that does would make pivot parity depend on
     FP64 rounding order, so it fails here instead of being skipped.  With
-    check_recon the GPU's growth-normalised backward error must be <= 1e-14 and
-    its raw backward error at most twice the oracle's own plus 1e-15."""
+    check_recon the backward error is checked as check_backward_error states."""
     assert got["info"] == 0
     assert ref["log_len"] <= len(ref["log"]) or len(ref["log"]) == 0, "oracle decision log truncated"
     margin = min_margin(ref["log"])
@@ -102,8 +104,7 @@ def compare(ref, got, p, A, check_recon=True):
     assert np.allclose(Ag, Ar, rtol=1e-10, atol=1e-10 * scale)
     assert np.allclose(got["D"], ref["D"], rtol=1e-10, atol=1e-10 * np.abs(ref["D"]).max())
     if check_recon:
-        assert recon_error(A, p, got) <= 1e-14
-        assert raw_error(A, p, got) <= 2.0 * raw_error(A, p, ref) + 1e-15
+        check_backward_error(A, p, got, ref)
 
 
 # --------------------------------------------------------------------------- K1
@@ -232,9 +233,9 @@ def test_large_supernode_relaxed_full_size(ctx):
     assert ref["nelim"] == p
     compare(ref, got, p, A, check_recon=False)
     rows_s = np.r_[0:p + 64, np.random.default_rng(1).choice(np.arange(p, n), 4000, replace=False)]
-    sub = dict(got)
-    sub["A"] = got["A"][rows_s]
-    assert recon_error(A[rows_s], p, sub) <= 1e-14
+    sub, sref = dict(got), dict(ref)
+    sub["A"], sref["A"] = got["A"][rows_s], ref["A"][rows_s]
+    check_backward_error(A[rows_s], p, sub, sref)
     _form_fp64_packed_full_size(ctx, A, ref)
 
 
@@ -290,9 +291,9 @@ def test_large_supernode_tpp_full_size(ctx):
     assert ref["nelim"] == p
     compare(ref, got, p, A, check_recon=False)
     rows_s = np.r_[0:p + 64, np.random.default_rng(2).choice(np.arange(p, n), 4000, replace=False)]
-    sub = dict(got)
-    sub["A"] = got["A"][rows_s]
-    assert recon_error(A[rows_s], p, sub) <= 1e-14
+    sub, sref = dict(got), dict(ref)
+    sub["A"], sref["A"] = got["A"][rows_s], ref["A"][rows_s]
+    check_backward_error(A[rows_s], p, sub, sref)
 
 
 def test_large_supernode_full_size(ctx):
@@ -316,9 +317,9 @@ def test_large_supernode_full_size(ctx):
     got = run_gpu(ctx, A, p, "strict")
     compare(ref, got, p, A, check_recon=False)
     rows = np.r_[0:p + 64, np.random.default_rng(0).choice(np.arange(p, n), 4000, replace=False)]
-    sub = {k: v for k, v in got.items()}
-    sub["A"] = got["A"][rows]
-    assert recon_error(A[rows], p, sub) <= 1e-14
+    sub, sref = dict(got), dict(ref)
+    sub["A"], sref["A"] = got["A"][rows], ref["A"][rows]
+    check_backward_error(A[rows], p, sub, sref)
 
 
 # --------------------------------------------------------------------------- errors
