@@ -9,7 +9,10 @@
  * the CUDA library, and it never calls into it.
  *
  * Style: single thread, natural loop orders, no blocking, compiled with
- * -ffp-contract=off so that every multiply and add is rounded separately.
+ * -ffp-contract=off so that every multiply and add is rounded separately --
+ * except the trailing update of Listing 1's working matrix, where each
+ * a(i,k) - l(i) a(k,q) (or + for the worst-case rows) is one explicit fma()
+ * (reading Q18 below).
  * Columns and A11 rows are moved physically, exactly as the paper's listing
  * describes ("permute m to position nelim+1"), with a stable shift.
  *
@@ -39,6 +42,11 @@
  *   Q11 relaxed: ties go to the lowest row; columns left after every A21 row
  *       is flagged get a zero row of C.
  *   Q13 Solve is L21 = (A21 P^T)(D11 L11^T)^-1; rows of A21 never move.
+ *   Q18 IEEE FP64, round to nearest even.  The paper fixes no rounding order.
+ *       The multipliers l(i) = a(i,q)/d (and [a(i,t) a(i,m)] D^-1) are rounded
+ *       per operation; each update a(i,k) -= l(i) a(k,q) of the working matrix
+ *       (A11 lower triangle, mirrored, and the outer rows) rounds once, as a
+ *       fused multiply-add, the 2x2 terms in the order t, then m.
  */
 #include <math.h>
 #include <stdint.h>
@@ -204,14 +212,14 @@ static void pivot_1x1(work_t *wk, int q, double *lcol) {
     /* trailing update (right-looking) */
     for (int k = q + 1; k < p; k++) {
         double akq = W(k, q);
-        for (int i = k; i < p; i++) W(i, k) -= lcol[i] * akq; /* A11 lower incl. diagonal */
-        for (int i = k + 1; i < p; i++) W(k, i) = W(i, k);    /* keep symmetric copy */
+        for (int i = k; i < p; i++) W(i, k) = fma(-lcol[i], akq, W(i, k)); /* A11 lower incl. diagonal */
+        for (int i = k + 1; i < p; i++) W(k, i) = W(i, k);                 /* keep symmetric copy */
         for (int i = p; i < nrow; i++) {
             int is_abs = (wk->tmode == UPD_ABS) && i < p + wk->rt;
             if (is_abs)
-                W(i, k) += lcol[i] * fabs(akq);
+                W(i, k) = fma(lcol[i], fabs(akq), W(i, k));
             else
-                W(i, k) -= lcol[i] * akq;
+                W(i, k) = fma(-lcol[i], akq, W(i, k));
         }
         if (wk->st) wk->st->ops_update += (p - k) + (nrow - p);
     }
@@ -249,14 +257,14 @@ static void pivot_2x2(work_t *wk, int q, double *l0, double *l1) {
     }
     for (int k = q + 2; k < p; k++) {
         double akq = W(k, q), akq1 = W(k, q + 1);
-        for (int i = k; i < p; i++) W(i, k) -= l0[i] * akq + l1[i] * akq1;
+        for (int i = k; i < p; i++) W(i, k) = fma(-l1[i], akq1, fma(-l0[i], akq, W(i, k)));
         for (int i = k + 1; i < p; i++) W(k, i) = W(i, k);
         for (int i = p; i < nrow; i++) {
             int is_abs = (wk->tmode == UPD_ABS) && i < p + wk->rt;
             if (is_abs)
-                W(i, k) += l0[i] * fabs(akq) + l1[i] * fabs(akq1);
+                W(i, k) = fma(l1[i], fabs(akq1), fma(l0[i], fabs(akq), W(i, k)));
             else
-                W(i, k) -= l0[i] * akq + l1[i] * akq1;
+                W(i, k) = fma(-l1[i], akq1, fma(-l0[i], akq, W(i, k)));
         }
         if (wk->st) wk->st->ops_update += 2 * ((p - k) + (nrow - p));
     }

@@ -37,9 +37,9 @@
 // original order) is applied only when the factor is written back.
 //
 // Determinism: every CTA holds the same replicated control state (live flags,
-// nelim, m) and executes the same sequence of barriers.  The test arithmetic
-// uses explicitly rounded operations (no FMA contraction) so that it matches
-// the plain-CPU formulas up to the rounding of the inputs.
+// nelim, m) and executes the same sequence of barriers.  Tests use explicitly
+// rounded operations (no FMA contraction) and updates one fused multiply-add
+// per term, in the order of a plain sequential implementation of the listing.
 #include <cooperative_groups.h>
 
 #include "ctp_internal.cuh"
@@ -101,41 +101,6 @@ struct Team<false> {
     __device__ __forceinline__ T *at(T *ptr, int r) const { return cl.map_shared_rank(ptr, r); }
 };
 
-// Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
-// test of eq. (2.2), |D^-1| (maxt, maxm)^T <= 1/u.  Fills d on acceptance.
-__device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, double maxt,
-                                         double maxm, double u, double small, Decision &d) {
-    double amax = fmax(fabs(a_tt), fmax(fabs(a_tm), fabs(a_mm)));
-    if (amax < small) return false;
-    double detscale = __ddiv_rn(1.0, amax);
-    double detpiv1 = __dmul_rn(__dmul_rn(a_tm, detscale), a_tm);
-    double detpiv0 = __dmul_rn(__dmul_rn(a_mm, detscale), a_tt);
-    double detpiv = __dsub_rn(detpiv0, detpiv1);
-    double guard = fmax(small, fmax(0.5 * fabs(detpiv0), 0.5 * fabs(detpiv1)));
-    if (fabs(detpiv) <= guard) return false;
-    bool ok;
-    if (fmax(maxm, maxt) < small) {
-        ok = true;
-    } else {
-        // |D^-1| (maxt, maxm)^T <= 1/u, each row compared as num*detscale <= |detpiv|/u
-        // (the quotient form of the test, without FP64 divisions)
-        const double lim = __dmul_rn(fabs(detpiv), __drcp_rn(u));
-        const double gt = __dmul_rn(__dadd_rn(__dmul_rn(fabs(a_mm), maxt), __dmul_rn(fabs(a_tm), maxm)), detscale);
-        const double gm = __dmul_rn(__dadd_rn(__dmul_rn(fabs(a_tm), maxt), __dmul_rn(fabs(a_tt), maxm)), detscale);
-        ok = (gt <= lim) && (gm <= lim);
-    }
-    if (ok) {
-        const double rdet = __ddiv_rn(detscale, detpiv);
-        d.d0 = a_tt;
-        d.d1 = a_tm;
-        d.d2 = a_mm;
-        d.i0 = __dmul_rn(a_mm, rdet);
-        d.i1 = __dmul_rn(-a_tm, rdet);
-        d.i2 = __dmul_rn(a_tt, rdet);
-    }
-    return ok;
-}
-
 __device__ __forceinline__ unsigned long long akey(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
@@ -149,6 +114,80 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v)
 }
 __device__ __forceinline__ double key_val(unsigned long long k) {
     return __longlong_as_double((long long)k);
+}
+// x is Inf or NaN: all exponent bits set (an integer test)
+__device__ __forceinline__ bool nonfinite_bits(double x) { return akey(x) >= 0x7FF0000000000000ull; }
+// x != 0 (either sign)
+__device__ __forceinline__ bool nonzero_bits(double x) { return akey(x) != 0ull; }
+// |x| and -x on the sign bit (integer instructions, never the FP64 pipe)
+__device__ __forceinline__ double abs_bits(double x) { return key_val(akey(x)); }
+__device__ __forceinline__ double neg_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+// GB300's FP64 pipe takes about 70 cycles per warp instruction whatever the
+// number of active lanes, while integer instructions cost one.  So the tests
+// below do every comparison, maximum and absolute value of non-negative
+// doubles on their IEEE bit patterns (for x, y >= 0, x < y as doubles iff
+// bits(x) < bits(y) as unsigned integers), and keep FP64 arithmetic for the
+// products, sums and reciprocals whose rounding the test defines.
+
+// |x| / 2 as a key: an exponent decrement, exact for normal x above the
+// smallest binade; the rare others take the FP64 product.
+__device__ __forceinline__ unsigned long long half_key(unsigned long long k) {
+    return (k >> 52) > 1 ? k - (1ull << 52) : akey(0.5 * key_val(k));
+}
+
+// Listing 1's test_2x2 with the nonsingularity/cancellation guard and the growth
+// test of eq. (2.2), |D^-1| (maxt, maxm)^T <= 1/u, on keys maxt, maxm of the
+// column maxima.  rcp_u = 1/u rounded, small_k = key of `small`.  Fills d on
+// acceptance.
+__device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, unsigned long long maxt,
+                                         unsigned long long maxm, double rcp_u, unsigned long long small_k,
+                                         Decision &d) {
+    const unsigned long long ktt = akey(a_tt), ktm = akey(a_tm), kmm = akey(a_mm);
+    unsigned long long kmax = ktt > ktm ? ktt : ktm;
+    kmax = kmm > kmax ? kmm : kmax;
+    if (kmax < small_k) return false;
+    // 1/amax correctly rounded: the same value as the division 1.0/amax
+    const double detscale = __drcp_rn(key_val(kmax));
+    const double detpiv1 = __dmul_rn(__dmul_rn(a_tm, detscale), a_tm);
+    const double detpiv0 = __dmul_rn(__dmul_rn(a_mm, detscale), a_tt);
+    const double detpiv = __dsub_rn(detpiv0, detpiv1);
+    unsigned long long guard = half_key(akey(detpiv0));
+    const unsigned long long g1 = half_key(akey(detpiv1));
+    guard = g1 > guard ? g1 : guard;
+    guard = small_k > guard ? small_k : guard;
+    const unsigned long long kdet = akey(detpiv);
+    if (kdet <= guard) return false;
+    bool ok;
+    if ((maxm > maxt ? maxm : maxt) < small_k) {
+        ok = true;
+    } else {
+        // |D^-1| (maxt, maxm)^T <= 1/u, each row compared as num*detscale <= |detpiv|/u
+        // (the quotient form of the test, without FP64 divisions)
+        const double vt = key_val(maxt), vm = key_val(maxm);
+        const unsigned long long lim = akey(__dmul_rn(key_val(kdet), rcp_u));
+        const unsigned long long gt = akey(
+            __dmul_rn(__dadd_rn(__dmul_rn(key_val(kmm), vt), __dmul_rn(key_val(ktm), vm)), detscale));
+        ok = gt <= lim;
+        if (ok) {
+            const unsigned long long gm = akey(
+                __dmul_rn(__dadd_rn(__dmul_rn(key_val(ktm), vt), __dmul_rn(key_val(ktt), vm)), detscale));
+            ok = gm <= lim;
+        }
+    }
+    if (ok) {
+        // D^-1 = (detscale / detpiv) [[a_mm, -a_tm], [-a_tm, a_tt]], each entry
+        // scaled first and then divided, as the update's multipliers expect
+        d.d0 = a_tt;
+        d.d1 = a_tm;
+        d.d2 = a_mm;
+        d.i0 = __ddiv_rn(__dmul_rn(a_mm, detscale), detpiv);
+        d.i1 = __ddiv_rn(__dmul_rn(-a_tm, detscale), detpiv);
+        d.i2 = __ddiv_rn(__dmul_rn(a_tt, detscale), detpiv);
+    }
+    return ok;
 }
 
 // live flags of the warp kernel: one bit per column (p <= 32)
@@ -167,7 +206,7 @@ struct BitLive {
 template <typename ColPtr, typename Live>
 __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColPtr colptr,
                                                    const Live &live, int p, int LD, double u,
-                                                   double small) {
+                                                   double rcp_u, unsigned long long small_k) {
     const int lane = threadIdx.x & 31;
     Decision d;
     d.kind = DEC_REJECT;
@@ -221,30 +260,27 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
         }
     }
     vm = warp_max_key(vm);
-    unsigned long long vall = vm > akey(cm[c]) ? vm : akey(cm[c]);
-    if (t >= 0 && akey(cm[t]) > vall) vall = akey(cm[t]);
-    if (key_val(vall) < small) {
+    const double amm = cm[c];
+    const unsigned long long kmm = akey(amm), ktm = t >= 0 ? akey(cm[t]) : 0ull;
+    unsigned long long vall = vm > kmm ? vm : kmm;
+    vall = ktm > vall ? ktm : vall;
+    if (vall < small_k) {
         d.kind = DEC_ZERO;
         return d;
     }
-    double maxm1;
+    unsigned long long maxm1 = vm;  // the live rows but c (and t, added back for the 1x1 test)
     if (t >= 0) {
-        const double maxm2 = key_val(vm);
-        const double maxt = key_val(warp_max_key(vt));
-        if (test_2x2(ct[t], cm[t], cm[c], maxt, maxm2, u, small, d)) {
+        if (test_2x2(ct[t], cm[t], amm, warp_max_key(vt), vm, rcp_u, small_k, d)) {
             d.kind = DEC_2X2;
             d.t = t;
             return d;
         }
-        maxm1 = fmax(maxm2, fabs(cm[t]));
-    } else {
-        maxm1 = key_val(vm);  // the live rows but c
+        maxm1 = ktm > vm ? ktm : vm;
     }
-    const double amm = cm[c];
-    if (fabs(amm) >= __dmul_rn(u, maxm1)) {
+    if (kmm >= akey(__dmul_rn(u, key_val(maxm1)))) {
         d.kind = DEC_1X1;
         d.d0 = amm;
-        d.i0 = __ddiv_rn(1.0, amm);
+        d.i0 = __drcp_rn(amm);
     }
     return d;
 }
@@ -277,7 +313,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
         int r = 0;
         for (int j0 = 0; j0 < a.R; j0 += 32) {
             const int j = j0 + lane;
-            const bool first = j < a.R && a.C[(int64_t)j * p] != 0.0;
+            const bool first = j < a.R && nonzero_bits(a.C[(int64_t)j * p]);
             if (j < a.R) sh.nzflag[j] = first ? 1 : 0;
             const bool scan = j < a.R && !first;
             const unsigned int bal = __ballot_sync(0xffffffffu, scan);
@@ -292,7 +328,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
         for (int idx = tid; idx < ns * p; idx += kT) {
             const int q = idx / p, k = idx - q * p;
             const int j = sh.rowmap[q];
-            if (a.C[(int64_t)j * p + k] != 0.0) sh.nzflag[j] = 1;
+            if (nonzero_bits(a.C[(int64_t)j * p + k])) sh.nzflag[j] = 1;
         }
     }
     __syncthreads();
@@ -309,19 +345,21 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
     }
     __syncthreads();
     const int R = sh.nz_count, LD = p + R;
-    const int ncl = (p + G - 1) / G;
+    const int gs = __ffs(G) - 1, gm = G - 1;  // G is a power of two: column c is slot c >> gs of CTA c & gm
+    const int ncl = (p + gm) >> gs;
     double *cols = dsm;                    // [ncl][LD]
     double *pc0 = dsm + (size_t)ncl * LD;  // pivot column copies
     double *pc1 = pc0 + LD;
-    double *cs0 = pc1 + LD, *cs1 = cs0 + ncl, *cas0 = cs1 + ncl, *cas1 = cas0 + ncl;  // update scalars
-    auto colptr = [&](int c) -> const double * { return team.at(cols, c % G) + (size_t)(c / G) * LD; };
+    double *rl0 = pc1 + LD, *rl1 = rl0 + LD;  // row multipliers of the pivot, signed
+    double *apc0 = rl1 + LD, *apc1 = apc0 + p;  // |pivot column| on the A11 rows
+    auto colptr = [&](int c) -> const double * { return team.at(cols, c & gm) + (size_t)(c >> gs) * LD; };
 
     // ---- load: own columns of A11 (full symmetric) and of the nonzero outer rows
     bool nonfinite = false;
     // flattened (column, row) loops step their indices by kT without divisions
     const int dl = kT / LD, di = kT - dl * LD;
     for (int idx = tid, lc = tid / LD, i = tid - (tid / LD) * LD; idx < ncl * LD; idx += kT) {
-        const int c = lc * G + rank;
+        const int c = (lc << gs) + rank;
         const int ii = i;
         i += di;
         lc += dl;
@@ -336,7 +374,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             v = (i0 >= c) ? a.A[(int64_t)c * a.lda + i0] : a.A[(int64_t)i0 * a.lda + c];
         else
             v = a.C[(int64_t)sh.rowmap[i0 - p] * p + c];
-        nonfinite |= !isfinite(v);
+        nonfinite |= nonfinite_bits(v);
         cols[idx] = v;
     }
     for (int i = tid; i < p; i += kT) sh.live[i] = 1;
@@ -344,7 +382,8 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
     if (nonfinite) atomicCAS(a.info, kInfoOk, (int32_t)CTP_ENONFINITE);
     team.sync();
 
-    const double u = a.u, small = a.small;
+    const double u = a.u, rcp_u = __drcp_rn(a.u);
+    const unsigned long long small_k = akey(a.small);
     int nelim = 0, m = (p >= 2) ? 1 : 0, accepted = 0, round = 0;
     int win = 1;                  // candidates tested in the next round
     const int win_max = kNW * G;  // no CTA owns more than kNW of them
@@ -370,7 +409,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
         if (warp == 0) {
             // this CTA's live columns in [m, hi), in order, go to its warps
             // (win <= kNW * G, so no CTA owns more than kNW of them)
-            const int j0 = m > rank ? (m - rank + G - 1) / G : 0;
+            const int j0 = m > rank ? (m - rank + gm) >> gs : 0;
             const int c = rank + G * (j0 + lane);
             const bool ok = c < hi && sh.live[c];
             const unsigned int bal = __ballot_sync(0xffffffffu, ok);
@@ -381,7 +420,8 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
         {
             const int c = sh.cand[warp];
             if (c >= 0) {
-                Decision d = test_candidate(c, cols + (size_t)(c / G) * LD, colptr, sh.live, p, LD, u, small);
+                Decision d = test_candidate(c, cols + (size_t)(c >> gs) * LD, colptr, sh.live, p, LD, u, rcp_u,
+                                            small_k);
                 if (d.kind != DEC_REJECT) {
                     // publish: the decision stays here, (candidate, warp) goes to
                     // every CTA's slot for this round
@@ -403,7 +443,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             key = __shfl_sync(0xffffffffu, key, 0);
             const int cs = key == kNoKey ? p : key / kNW;
             if (cs < p && lane < 8) {
-                const Decision *src = team.at(&sh.res[buf][key % kNW], cs % G);
+                const Decision *src = team.at(&sh.res[buf][key % kNW], cs & gm);
                 reinterpret_cast<double *>(&sh.cur)[lane] = reinterpret_cast<const double *>(src)[lane];
             }
             if (lane == 0) sh.cstar = cs;
@@ -444,39 +484,47 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             // after that comes behind the next team barrier
             continue;
         }
-        // ---------------- update: apply the pivot to the own live columns
+        // ---------------- update: apply the pivot to the own live columns with
+        // the rounding of a plain right-looking update: row multipliers
+        // l(i) = a(i,q)/d (1x1) or [a(i,t) a(i,m)] D^-1 (2x2; abs rows of strict
+        // C with |d|, |D^-1|), rounded per operation, then
+        // a(i,c) = fma(-l(i), a(c,q), a(i,c)) (and the m term after the t term):
+        // one rounding per term; entries above the diagonal take their mirror's
+        // operands, so the full symmetric copy stays exactly symmetric.  Equal
+        // inputs then give bit-identical working matrices on any team shape,
+        // and exact ties between entries (Listing 1's partner choice) are broken
+        // identically.
         const int q0 = (dv.kind == DEC_2X2) ? dv.t : dv.m;
         const int q1 = (dv.kind == DEC_2X2) ? dv.m : -1;
+        const bool abs_rows = a.abs_update != 0;
         {
-            // copies of the pivot column(s), the per-column scalars read from
-            // them where they live, and the bookkeeping of the pivot, in one
-            // phase (the pivot columns are not written in this round, and
-            // live[] of the pivot columns is read nowhere in this phase)
+            // copies of the pivot column(s), every row's multipliers, and the
+            // bookkeeping of the pivot, in one phase (the pivot columns are not
+            // written in this round; live[] is read nowhere in this phase)
+            // multipliers are stored with the sign of their term (-l on normal
+            // rows, +l on abs rows) and the A11 pivot entries also as |.|, so
+            // that the update loop needs no FP64 sign or abs operation
             const double *s0 = colptr(q0);
             const double *s1 = q1 >= 0 ? colptr(q1) : s0;
+            const double ad0 = abs_bits(dv.d0), ai0 = abs_bits(dv.i0), ai1 = abs_bits(dv.i1), ai2 = abs_bits(dv.i2);
             for (int i = tid; i < LD; i += kT) {
-                pc0[i] = s0[i];
-                if (q1 >= 0) pc1[i] = s1[i];
-            }
-            for (int lc = tid; lc < ncl; lc += kT) {
-                const int c = lc * G + rank;
-                const bool upd = c < p && c != q0 && c != q1 && sh.live[c];
-                double v0 = 0.0, v1 = 0.0, w0 = 0.0, w1 = 0.0;
-                if (upd && q1 < 0) {
-                    const double b0 = s0[c];
-                    v0 = b0 * dv.i0;
-                    w0 = fabs(b0) * fabs(dv.i0);
-                } else if (upd) {
-                    const double i11 = dv.i0, i21 = dv.i1, i22 = dv.i2;
-                    const double b0 = s0[c], b1 = s1[c];
-                    v0 = i11 * b0 + i21 * b1;
-                    v1 = i21 * b0 + i22 * b1;
-                    const double ab0 = fabs(b0), ab1 = fabs(b1);
-                    w0 = fabs(i11) * ab0 + fabs(i21) * ab1;
-                    w1 = fabs(i21) * ab0 + fabs(i22) * ab1;
+                const double x = s0[i];
+                pc0[i] = x;
+                const bool ab = abs_rows && i >= p;
+                if (i < p) apc0[i] = abs_bits(x);
+                if (q1 < 0) {
+                    const double l = __ddiv_rn(x, ab ? ad0 : dv.d0);
+                    rl0[i] = ab ? l : neg_bits(l);
+                } else {
+                    const double y = s1[i];
+                    pc1[i] = y;
+                    if (i < p) apc1[i] = abs_bits(y);
+                    const double i11 = ab ? ai0 : dv.i0, i21 = ab ? ai1 : dv.i1, i22 = ab ? ai2 : dv.i2;
+                    const double l0 = __dadd_rn(__dmul_rn(x, i11), __dmul_rn(y, i21));
+                    const double l1 = __dadd_rn(__dmul_rn(x, i21), __dmul_rn(y, i22));
+                    rl0[i] = ab ? l0 : neg_bits(l0);
+                    rl1[i] = ab ? l1 : neg_bits(l1);
                 }
-                cs0[lc] = v0, cs1[lc] = v1, cas0[lc] = w0, cas1[lc] = w1;
-                sh.nzflag[lc] = upd ? 1 : 0;
             }
             if (tid == 0) {
                 if (q1 < 0) {
@@ -506,8 +554,10 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             }
         }
         __syncthreads();
-        const bool abs_rows = a.abs_update != 0;
-        // the update over (column, row) pairs
+        // the update over (column, row) pairs of the live columns and rows.  An
+        // A11 entry above the diagonal (i < c) gets the value of its mirror
+        // (c, i) below it, from row c's multipliers and row i's pivot entries,
+        // so both halves hold bit-identical values without any exchange.
         for (int idx = tid, lc2 = tid / LD, i2 = tid - (tid / LD) * LD; idx < ncl * LD; idx += kT) {
             const int lc = lc2, i = i2;
             i2 += di;
@@ -516,23 +566,17 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
                 i2 -= LD;
                 lc2++;
             }
-            if (!sh.nzflag[lc]) continue;
+            const int c = (lc << gs) + rank;
+            if (c >= p || !sh.live[c]) continue;
             if (i < p && !sh.live[i]) continue;  // the pivot rows are no longer live
-            double *e = cols + idx;
-            if (q1 < 0) {
-                // 1x1: a(i,c) -= a(i,q) (a(c,q) / d); C rows (strict): c += chat |a(c,q)|
-                if (i < p || !abs_rows)
-                    *e -= pc0[i] * cs0[lc];
-                else
-                    *e += pc0[i] * cas0[lc];  // eq. (4.3)
-            } else {
-                // 2x2: a(i,c) -= [a(i,t) a(i,m)] (D^-1 [a(c,t) a(c,m)]^T)
-                const double x0 = pc0[i], x1 = pc1[i];
-                if (i < p || !abs_rows)
-                    *e -= x0 * cs0[lc] + x1 * cs1[lc];
-                else
-                    *e += x0 * cas0[lc] + x1 * cas1[lc];
-            }
+            // one fused multiply-add per pivot column: -l(r) a(k,q), or
+            // +l(r) |a(k,q)| on the abs rows (eq. (4.3)); (r, k) = (i, c), or
+            // (c, i) above the diagonal
+            const bool up = i < c, ab = abs_rows && i >= p;
+            const int r = up ? c : i, k = up ? i : c;
+            double v = fma(rl0[r], ab ? apc0[k] : pc0[k], cols[idx]);
+            if (q1 >= 0) v = fma(rl1[r], ab ? apc1[k] : pc1[k], v);
+            cols[idx] = v;
         }
         nelim += (q1 < 0) ? 1 : 2;
         accepted = 1;
@@ -568,7 +612,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             i2 -= p;
             lc2++;
         }
-        const int c = lc * G + rank;
+        const int c = (lc << gs) + rank;
         if (c >= p) continue;
         const double *col = cols + (size_t)lc * LD;
         const int pos = sh.pos_of[c];
@@ -678,7 +722,7 @@ __global__ void __launch_bounds__(32 * kWarpFronts)
         if (a.rowflags != nullptr) {
             nz = a.rowflags[lane] != 0;
         } else {
-            for (int k = 0; k < p && !nz; k++) nz = a.C[(int64_t)lane * p + k] != 0.0;
+            for (int k = 0; k < p && !nz; k++) nz = nonzero_bits(a.C[(int64_t)lane * p + k]);
         }
     }
     const unsigned nzbits = __ballot_sync(full, nz);
@@ -698,14 +742,15 @@ __global__ void __launch_bounds__(32 * kWarpFronts)
             if (i < LD) {
                 const double v = (i < p) ? ((i >= c) ? a.A[(int64_t)c * a.lda + i] : a.A[(int64_t)i * a.lda + c])
                                          : a.C[(int64_t)r * p + c];
-                nonfinite |= !isfinite(v);
+                nonfinite |= nonfinite_bits(v);
                 cols[(size_t)c * LD + i] = v;
             }
         }
     if (__any_sync(full, nonfinite) && lane == 0) atomicCAS(a.info, kInfoOk, (int32_t)CTP_ENONFINITE);
     __syncwarp();
 
-    const double u = a.u, small = a.small;
+    const double u = a.u, rcp_u = __drcp_rn(a.u);
+    const unsigned long long small_k = akey(a.small);
     const bool abs_rows = a.abs_update != 0;
     BitLive live;
     live.bits = p >= 32 ? full : ((1u << p) - 1u);
@@ -723,7 +768,7 @@ __global__ void __launch_bounds__(32 * kWarpFronts)
             m = 0;
             continue;
         }
-        const Decision dv = test_candidate(m, colptr(m), colptr, live, p, LD, u, small);
+        const Decision dv = test_candidate(m, colptr(m), colptr, live, p, LD, u, rcp_u, small_k);
         if (dv.kind == DEC_REJECT) {
             m++;
             continue;
@@ -746,37 +791,49 @@ __global__ void __launch_bounds__(32 * kWarpFronts)
         unsigned upd_cols = live.bits & ~(1u << q0);
         if (q1 >= 0) upd_cols &= ~(1u << q1);
         const unsigned rows_live = upd_cols;  // the live A11 rows after this pivot
-        // the update, column by column, lanes over rows (the pivot columns are only read)
+        // row multipliers of this lane's rows (the same arithmetic as factor_body)
+        double l0[2] = {0.0, 0.0}, l1[2] = {0.0, 0.0};  // signed: -l normal rows, +l abs rows
+        const double ad0 = abs_bits(dv.d0), ai0 = abs_bits(dv.i0), ai1 = abs_bits(dv.i1), ai2 = abs_bits(dv.i2);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int i = lane + 32 * h;
+            if (i < LD) {
+                const bool ab = abs_rows && i >= p;
+                const double x = p0[i];
+                if (q1 < 0) {
+                    const double l = __ddiv_rn(x, ab ? ad0 : dv.d0);
+                    l0[h] = ab ? l : neg_bits(l);
+                } else {
+                    const double y = p1[i];
+                    const double i11 = ab ? ai0 : dv.i0, i21 = ab ? ai1 : dv.i1, i22 = ab ? ai2 : dv.i2;
+                    const double a0 = __dadd_rn(__dmul_rn(x, i11), __dmul_rn(y, i21));
+                    const double a1 = __dadd_rn(__dmul_rn(x, i21), __dmul_rn(y, i22));
+                    l0[h] = ab ? a0 : neg_bits(a0);
+                    l1[h] = ab ? a1 : neg_bits(a1);
+                }
+            }
+        }
+        // |pivot entry| of A11 row `lane` (p <= 32)
+        const double ap0 = lane < p ? abs_bits(p0[lane]) : 0.0, ap1 = lane < p ? abs_bits(p1[lane]) : 0.0;
+        // the update, column by column, lanes over rows (the pivot columns are
+        // only read); above the diagonal from the mirror's operands (row c's
+        // multipliers, row i's pivot entries), as in factor_body
         while (upd_cols) {
             const int c = __ffs(upd_cols) - 1;
             upd_cols &= upd_cols - 1;
             double *col = cols + (size_t)c * LD;
-            double v0, v1 = 0.0, w0, w1 = 0.0;
-            if (q1 < 0) {
-                const double b0 = p0[c];
-                v0 = b0 * dv.i0;
-                w0 = fabs(b0) * fabs(dv.i0);
-            } else {
-                const double b0 = p0[c], b1 = p1[c];
-                v0 = dv.i0 * b0 + dv.i1 * b1;
-                v1 = dv.i1 * b0 + dv.i2 * b1;
-                w0 = fabs(dv.i0) * fabs(b0) + fabs(dv.i1) * fabs(b1);
-                w1 = fabs(dv.i1) * fabs(b0) + fabs(dv.i2) * fabs(b1);
-            }
-            for (int i = lane; i < LD; i += 32) {
-                if (i < p && !((rows_live >> i) & 1u)) continue;
-                if (q1 < 0) {
-                    if (i < p || !abs_rows)
-                        col[i] -= p0[i] * v0;
-                    else
-                        col[i] += p0[i] * w0;  // eq. (4.3)
-                } else {
-                    const double x0 = p0[i], x1 = p1[i];
-                    if (i < p || !abs_rows)
-                        col[i] -= x0 * v0 + x1 * v1;
-                    else
-                        col[i] += x0 * w0 + x1 * w1;
-                }
+            const double lc0 = __shfl_sync(full, l0[0], c), lc1 = __shfl_sync(full, l1[0], c);  // row c's
+            const double ac0 = __shfl_sync(full, ap0, c), ac1 = __shfl_sync(full, ap1, c);   // |a(c, q)|
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int i = lane + 32 * h;
+                if (i >= LD || (i < p && !((rows_live >> i) & 1u))) continue;
+                const bool up = i < c, ab = abs_rows && i >= p;  // eq. (4.3) for abs rows
+                const double m0 = up ? lc0 : l0[h], m1 = up ? lc1 : l1[h];
+                const double b0 = up ? p0[i] : (ab ? ac0 : p0[c]), b1 = up ? p1[i] : (ab ? ac1 : p1[c]);
+                double v = fma(m0, b0, col[i]);
+                if (q1 >= 0) v = fma(m1, b1, v);
+                col[i] = v;
             }
         }
         __syncwarp();
@@ -876,7 +933,7 @@ __global__ void __launch_bounds__(32 * kWarpFronts)
 
 static size_t factor_smem(int p, int R, int G) {
     int ncl = (p + G - 1) / G;
-    return sizeof(double) * ((size_t)ncl * (p + R) + 2 * (size_t)(p + R) + 4 * (size_t)ncl);
+    return sizeof(double) * ((size_t)ncl * (p + R) + 4 * (size_t)(p + R) + 2 * (size_t)p);
 }
 size_t factor_smem_bytes(int p, int R, int G) { return factor_smem(p, R, G); }
 size_t factor_warp_smem_bytes(int pcap, int ldcap) {
