@@ -868,6 +868,70 @@ def batch_accuracy(ctx, b, fronts, count=12, seed=0):
                    "2-node system; rest factored by TPP (FP64); FP64 refinement, tol 1e-14"}
 
 
+def measure_delays(ctx, dev, inputs, batch_count=8192, seed=0):
+    """Delayed pivots by method (NEXT-3; the analogue of the paper's delay
+    comparisons, Section 7.2, on synthetic inputs): TPP on all rows, strict,
+    relaxed, restricted and single-row compression, each supernode factored on
+    its own through the C ABI.  Workloads: the 8192-front batch (N(0,1), 2%
+    zero diagonals), a set of tough fronts (a sixth of the A11 columns scaled by
+    1e-3, 20% zero diagonals, A21 x5), the n = 2000, p = 64 supernode with eight
+    tiny columns, and the n = 200000, p = 256 U[-1,1] supernode."""
+    import torch
+    from paper_1305_2353_gb300 import ctp
+
+    def tough(n, p, s):
+        A = inputs.supernode(n, p, seed=s, dist="normal", scale_cols=max(1, p // 6), scale=1e-3,
+                             zero_diag_frac=0.2)
+        A[p:, :] *= 5.0
+        return A
+
+    sets = {
+        "batch_8192": inputs.batch(batch_count, seed=seed),
+        "tough_60": [tough(int(n), int(p), 1000 + k)
+                     for k, (n, p) in enumerate(inputs.batch_shapes(60, seed=7, pmin=8, pmax=256))],
+        "single_small": [inputs.single_small(0)],
+        "single_large": [inputs.single_large(seed)],
+    }
+    methods = ("tpp", "strict", "relaxed", "restricted", "single_row")
+    out = {}
+    for name, fronts in sets.items():
+        n = np.array([a.shape[0] for a in fronts], np.int64)
+        p = np.array([a.shape[1] for a in fronts], np.int64)
+        off = np.concatenate([[0], np.cumsum(n * p)])
+        host = np.empty(int(off[-1]))
+        for k, a in enumerate(fronts):
+            host[off[k]:off[k + 1]] = np.asarray(a, np.float64).ravel(order="F")
+        A0 = torch.from_numpy(host).to(dev)
+        A = torch.empty_like(A0)
+        pmax = int(p.max())
+        perm = torch.empty(pmax, dtype=torch.int32, device=dev)
+        piv = torch.empty(pmax, dtype=torch.int32, device=dev)
+        D = torch.empty(2 * pmax, dtype=torch.float64, device=dev)
+        nel = torch.empty(len(fronts), dtype=torch.int32, device=dev)
+        row = {}
+        t0 = time.perf_counter()
+        for meth in methods:
+            opt = ctp.options(pivot=meth)
+            need = max(ctx.workspace_size(int(a), int(b), opt) for a, b in set(zip(n.tolist(), p.tolist())))
+            ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+            A.copy_(A0)
+            for k in range(len(fronts)):
+                ctx.factor_supernode(A[int(off[k]):int(off[k + 1])], int(n[k]), int(p[k]), int(n[k]), opt,
+                                     perm, piv, D, nel[k:k + 1], None, 0, ws)
+            torch.cuda.synchronize()
+            if ctx.read_info(ws) != 0:
+                raise RuntimeError(f"device info after {name}/{meth}")
+            e = nel.cpu().numpy().astype(np.int64)
+            row[meth] = {"nelim": int(e.sum()), "delayed": int((p - e).sum()),
+                         "fronts_with_delays": int((e < p).sum())}
+            del ws
+        out[name] = {"fronts": len(fronts), "columns": int(p.sum()), "by_method": row,
+                     "seconds": time.perf_counter() - t0}
+        del A0, A
+        torch.cuda.empty_cache()
+    return out
+
+
 def leg_summary(name, d):
     """One short stderr line per leg (the complete record goes to --full-out)."""
     keep = {k: v for k, v in d.items() if isinstance(v, (int, float, str)) or v is None}
@@ -1018,6 +1082,11 @@ def run_native(a):
                                                 accuracy=nacc)
         rec["batch"] = batch
         del fronts
+
+    if a.all and rank == 0:
+        rec["delays"] = measure_delays(ctx, dev, inputs, a.batch_count, a.seed)
+        for nm, v in rec["delays"].items():
+            leg_summary("delays_" + nm, {m: d["delayed"] for m, d in v["by_method"].items()})
 
     if a.all and not a.no_tpp and a.pivot != "restricted":
         import argparse as _ap

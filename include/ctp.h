@@ -55,7 +55,11 @@ typedef enum {
     CTP_PIV_TPP = 2,        /* threshold partial pivoting on all n rows, Listing 1 (Section 2);
                                the comparator of the compressed strategies (FP64 only;
                                any smode but CTP_S_FP32_TILED) */
-    CTP_PIV_RESTRICTED = 3  /* restricted pivoting: tests look at A11 only, Section 3.2 */
+    CTP_PIV_RESTRICTED = 3, /* restricted pivoting: tests look at A11 only, Section 3.2 */
+    CTP_PIV_SINGLE_ROW = 4  /* single-row compression, the variant Section 4.1 closes with:
+                               eq. (4.1) with one set J = all A21 rows, so C is the one
+                               row of column maxima of |A21|, with the worst-case update
+                               eq. (4.3); single supernodes only (not in batches) */
 } ctp_pivot;
 
 /* Arithmetic of the Form step.  Compression, pivot selection, the 2x2 pivot
@@ -189,6 +193,47 @@ ctp_status ctp_compress_strict_noalloc(int64_t m, int32_t p, const double *A21, 
 ctp_status ctp_compress_relaxed(ctp_ctx *ctx, int64_t m, int32_t p, const double *A21,
                                 int64_t lda, double *C, int32_t *rows, void *workspace,
                                 size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Row split of one supernode (Section 6, Table 6.1; Appendix A): the rows of
+ * A21 are cut into P blocks (one per processor), each block is compressed on
+ * its own, and one exchange builds the compressed matrix C of the whole
+ * supernode.  These are the per-block steps and the exchange steps of that
+ * scheme; with every block on one GPU they reproduce ctp_compress_strict and
+ * ctp_compress_relaxed bit for bit.  A block is rows [row0, row0 + m) of A21,
+ * passed as the pointer to its first row (A21 + row0) with A21's lda.
+ *
+ * Strict (Section 4.1, eq. (4.1)): every block runs ctp_compress_strict on its
+ * rows; C is the elementwise maximum of the blocks' matrices, exact and
+ * independent of order (an allreduce with max across processors).
+ * C_blocks: P row-major p x p matrices, block b at C_blocks + b * block_stride
+ * (block_stride >= p*p elements); C: p x p output.  Device pointers. */
+ctp_status ctp_compress_strict_merge(ctp_ctx *ctx, int32_t P, int32_t p, const double *C_blocks,
+                                     int64_t block_stride, double *C, void *stream);
+
+/* Relaxed (Section 4.2): column j's row lies among the j+1 largest |a21(i,j)|
+ * of the column (ties to the lower row), and so among the union of every
+ * block's j+1 largest.  Each block writes its per-column candidate lists into
+ * slot `block` of a shared candidate buffer (a gather across processors);
+ * ctp_compress_relaxed_select runs the paper's greedy over the union and gives
+ * the chosen A21 row of every row of C (-1 when every row was already taken);
+ * ctp_gather_rows copies those rows, with their signs, into C (the owners of
+ * the rows send them).  P <= 8.  cand: device buffer of
+ * ctp_relaxed_candidates_size(P, p) bytes, opaque except that its first int32
+ * is an info word: it must be zero before the first block's call (clear the
+ * buffer once), a block that meets Inf or NaN sets it to CTP_ENONFINITE, and
+ * ctp_read_info(ctx, cand, ...) reads it.  Rows are reported as row0 + local
+ * row, so row0 + m must stay below 2^31. */
+ctp_status ctp_relaxed_candidates_size(int32_t P, int32_t p, size_t *bytes);
+ctp_status ctp_compress_relaxed_candidates(ctp_ctx *ctx, int64_t m, int32_t p, const double *A21, int64_t lda,
+                                           int64_t row0, int32_t P, int32_t block, void *cand,
+                                           size_t cand_bytes, void *stream);
+ctp_status ctp_compress_relaxed_select(ctp_ctx *ctx, int32_t P, int32_t p, const void *cand, size_t cand_bytes,
+                                       int32_t *rows, void *stream);
+/* C(j, :) = A21(rows[j], :) for j < p (a zero row where rows[j] < 0), C
+ * row-major p x p; A21 with leading dimension lda.  Device pointers. */
+ctp_status ctp_gather_rows(ctp_ctx *ctx, int32_t p, const double *A21, int64_t lda, const int32_t *rows, double *C,
+                           void *stream);
 
 /* The whole per-supernode hot path (Section 1 task list; Figure 4.1):
  * compression of A21 (strict or relaxed), pivot selection by Listing 1 on

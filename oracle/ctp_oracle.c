@@ -42,6 +42,9 @@
  *   Q11 relaxed: ties go to the lowest row; columns left after every A21 row
  *       is flagged get a zero row of C.
  *   Q13 Solve is L21 = (A21 P^T)(D11 L11^T)^-1; rows of A21 never move.
+ *   Q21 single-row compression (Section 4.1, closing remark): eq. (4.1) with
+ *       the one set J = all rows of A21, so C is one row of column maxima,
+ *       updated by the worst-case rule eq. (4.3).
  *   Q18 IEEE FP64, round to nearest even.  The paper fixes no rounding order.
  *       The multipliers l(i) = a(i,q)/d (and [a(i,t) a(i,m)] D^-1) are rounded
  *       per operation; each update a(i,k) -= l(i) a(k,q) of the working matrix
@@ -62,6 +65,7 @@
 #define ORC_RELAXED 1
 #define ORC_TPP 2
 #define ORC_RESTRICTED 3
+#define ORC_SINGLE_ROW 4
 
 /* per-position pivot kinds */
 #define PIV_1X1 1
@@ -525,9 +529,9 @@ static void apply_solve(int m, int p, int e, const double *Wf, int64_t ldw, cons
     free(y);
 }
 
-/* Full supernode: compression (strict / relaxed), Listing 1 on [A11; C] (or on
- * [A11; A21] for TPP, on A11 alone for restricted pivoting), then Solve and the
- * delayed-column update.  A is overwritten in place:
+/* Full supernode: compression (strict / relaxed / single-row), Listing 1 on
+ * [A11; C] (or on [A11; A21] for TPP, on A11 alone for restricted pivoting),
+ * then Solve and the delayed-column update.  A is overwritten in place:
  *   rows 0..p-1, lower triangle, in pivot order: L11 (unit diagonal implied),
  *     D on the diagonal and in the (q+1,q) slot of each 2x2 block, L_d in the
  *     delayed rows, and the updated delayed block;
@@ -537,9 +541,9 @@ int orc_factor(int n, int p, double *A, int64_t lda, int method, double u, doubl
                int32_t *perm, int32_t *piv, double *D, int32_t *nelim, double *C_out,
                orc_stats *st, orc_log_entry *log, int log_cap, int32_t *log_len) {
     if (p < 1 || n < p || lda < n || !(u > 0.0) || u > 0.5) return ORC_EINVAL;
-    if (method < 0 || method > 3) return ORC_EINVAL;
+    if (method < 0 || method > 4) return ORC_EINVAL;
     int m = n - p;
-    int rt = (method == ORC_TPP) ? m : (method == ORC_RESTRICTED ? 0 : p);
+    int rt = (method == ORC_TPP) ? m : (method == ORC_RESTRICTED ? 0 : (method == ORC_SINGLE_ROW ? 1 : p));
     int64_t ldw = p + rt;
     double *Wm = (double *)calloc((size_t)ldw * (size_t)p, sizeof(double));
     if (!Wm) return ORC_ENOMEM;
@@ -556,15 +560,25 @@ int orc_factor(int n, int p, double *A, int64_t lda, int method, double u, doubl
         orc_compress_strict(m, p, A + p, lda, Wm + p, ldw, NULL);
     } else if (method == ORC_RELAXED) {
         orc_compress_relaxed(m, p, A + p, lda, Wm + p, ldw, NULL);
+    } else if (method == ORC_SINGLE_ROW) {
+        /* eq. (4.1) with one set J = {1, ..., n-p}: C is the single row of
+           column maxima c(k) = max_i |a21(i,k)| (0 when A21 has no rows) */
+        for (int k = 0; k < p; k++) {
+            double c = 0.0;
+            for (int i = 0; i < m; i++) c = fmax(c, fabs(A[(int64_t)k * lda + p + i]));
+            Wm[(int64_t)k * ldw + p] = c;
+        }
     }
     if (C_out) {
         for (int j = 0; j < p; j++)
             for (int i = 0; i < p; i++)
-                C_out[(int64_t)j * p + i] = (method == ORC_STRICT || method == ORC_RELAXED)
+                C_out[(int64_t)j * p + i] = (method == ORC_STRICT || method == ORC_RELAXED ||
+                                             (method == ORC_SINGLE_ROW && i == 0))
                                                 ? Wm[(int64_t)j * ldw + p + i]
                                                 : 0.0;
     }
-    int rc = orc_listing1(p, rt, 0, method == ORC_STRICT ? UPD_ABS : UPD_NORMAL, Wm, ldw, u, small, -1,
+    int rc = orc_listing1(p, rt, 0, (method == ORC_STRICT || method == ORC_SINGLE_ROW) ? UPD_ABS : UPD_NORMAL,
+                          Wm, ldw, u, small, -1,
                           perm, piv, D, nelim, st, log, log_cap, log_len);
     if (rc != ORC_OK) {
         free(Wm);

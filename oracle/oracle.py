@@ -27,8 +27,9 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-STRICT, RELAXED, TPP, RESTRICTED = 0, 1, 2, 3
-METHODS = {"strict": STRICT, "relaxed": RELAXED, "tpp": TPP, "restricted": RESTRICTED}
+STRICT, RELAXED, TPP, RESTRICTED, SINGLE_ROW = 0, 1, 2, 3, 4
+METHODS = {"strict": STRICT, "relaxed": RELAXED, "tpp": TPP, "restricted": RESTRICTED,
+           "single_row": SINGLE_ROW}
 PIV_1X1, PIV_2X2_FIRST, PIV_2X2_SECOND, PIV_ZERO, PIV_DELAYED = 1, 2, 0, -1, 3
 UPD_NORMAL, UPD_ABS = 0, 1
 LOG_KINDS = {0: "zero", 1: "2x2_max", 2: "2x2_det", 3: "2x2_tiny", 4: "2x2_growth", 5: "1x1"}

@@ -43,7 +43,8 @@ WsLayout ws_layout(int64_t n, int p, const ctp_options *opt, int num_sms) {
     L.info = off;
     off += 256;
     L.C = off;
-    const bool compressed = opt->pivot == CTP_PIV_STRICT || opt->pivot == CTP_PIV_RELAXED;
+    const bool compressed = opt->pivot == CTP_PIV_STRICT || opt->pivot == CTP_PIV_RELAXED ||
+                            opt->pivot == CTP_PIV_SINGLE_ROW;
     off += align256(compressed ? sizeof(double) * (size_t)p * p : 0);
     L.Dinv = off;
     off += align256(sizeof(double) * (2 * (size_t)p + 2));
@@ -119,7 +120,7 @@ static ctp_status check_opts(const ctp_options *opt) {
     if (opt == nullptr) return CTP_EINVAL;
     if (!(opt->u > 0.0) || opt->u > 0.5) return CTP_EINVAL;
     if (!(opt->small >= 0.0)) return CTP_EINVAL;
-    if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_RESTRICTED) return CTP_EINVAL;
+    if (opt->pivot < CTP_PIV_STRICT || opt->pivot > CTP_PIV_SINGLE_ROW) return CTP_EINVAL;
     if (opt->prec < CTP_FP64 || opt->prec > CTP_BF16X6) return CTP_EINVAL;
     if (opt->smode < CTP_S_NONE || opt->smode > CTP_S_FP64_SUB) return CTP_EINVAL;
     if (opt->solve != CTP_SOLVE_FP64 && opt->solve != CTP_SOLVE_TC) return CTP_EINVAL;
@@ -304,6 +305,16 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
         fa.R = p;
         fa.abs_update = 0;
         fa.C = C;
+    } else if (opt->pivot == CTP_PIV_SINGLE_ROW) {
+        // one row of column maxima (eq. (4.1) with J = all rows), worst-case update
+        unsigned long long *keys = (unsigned long long *)(ws + L.C);
+        CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p, st));
+        CTP_CUDA(timed(ctx, K_COMPRESS_STRICT, st, [&] {
+            return launch_compress_single_row(A + p, m, p, lda, keys, info, ctx->num_sms, st);
+        }));
+        fa.R = 1;
+        fa.abs_update = 1;
+        fa.C = (const double *)keys;
     } else {  // restricted: the tests look at A11 only
         fa.R = 0;
         fa.abs_update = 0;

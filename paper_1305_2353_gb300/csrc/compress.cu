@@ -167,6 +167,31 @@ __global__ void __launch_bounds__(kThreads)
     if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
 }
 
+// Single-row compression (eq. (4.1) with one set J = all rows): the column
+// maxima of |A21| as integer keys.  CTA (seg, k) reduces rows [seg*L, ...) of
+// column k with 16-byte loads and merges into ckey[k] with atomicMax.
+__global__ void __launch_bounds__(256)
+    k_colmax(const double *__restrict__ A21, int64_t m, int64_t lda, int64_t L,
+             unsigned long long *__restrict__ ckey, int32_t *__restrict__ info) {
+    const int k = blockIdx.y;
+    const int64_t r0 = (int64_t)blockIdx.x * L, r1 = r0 + L < m ? r0 + L : m;
+    const double *col = A21 + (int64_t)k * lda;
+    unsigned long long best = 0;
+    bool nonfinite = false;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const unsigned long long key = abs_key(__ldcs(col + r));
+        nonfinite |= key >= kInfKey;
+        best = key > best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+        best = w > best ? w : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(ckey + k, best);
+    if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
+}
+
 __global__ void k_keys_to_rowmajor(const unsigned long long *__restrict__ Ckeys,
                                    double *__restrict__ C, int pp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,6 +221,19 @@ cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t 
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > ntiles) grid = ntiles;
     k_compress_strict<<<(unsigned)grid, kThreads, smem, st>>>(A21, m, p, lda, Ckeys, J, rowflags, info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compress_single_row(const double *A21, int64_t m, int p, int64_t lda,
+                                       unsigned long long *ckey, int32_t *info, int num_sms, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    // about four CTAs per SM in all, segments of at least 4096 rows
+    int64_t nseg = (4LL * num_sms + p - 1) / p;
+    const int64_t maxseg = (m + 4095) / 4096;
+    if (nseg > maxseg) nseg = maxseg;
+    if (nseg < 1) nseg = 1;
+    const int64_t L = (m + nseg - 1) / nseg;
+    k_colmax<<<dim3((unsigned)nseg, p), 256, 0, st>>>(A21, m, lda, L, ckey, info);
     return cudaGetLastError();
 }
 

@@ -57,6 +57,9 @@ constexpr int kFactorWarp = 0, kFactorCta = 1, kFactorCluster = 2;
 cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
                                    unsigned long long *Ckeys, int32_t *J, int32_t *rowflags, int32_t *info,
                                    int num_sms, cudaStream_t st);
+// single-row compression: ckey[k] (p keys, zeroed by the caller) = max_i |a21(i,k)|
+cudaError_t launch_compress_single_row(const double *A21, int64_t m, int p, int64_t lda,
+                                       unsigned long long *ckey, int32_t *info, int num_sms, cudaStream_t st);
 int relaxed_segments(int64_t m, int p, int num_sms);
 size_t relaxed_aux_bytes(int64_t m, int p, int num_sms);
 cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t lda, double *C,

@@ -70,10 +70,13 @@ __device__ __forceinline__ int next_pow2(int x) {
     return n;
 }
 
-// Phase 1: CTA (seg, j) keeps the top K_j entries of rows [seg*L, (seg+1)*L) of column j.
+// Phase 1: CTA (seg, j) keeps the top K_j entries of rows [seg*L, (seg+1)*L) of
+// column j.  Its list goes to slot s = seg_base + seg of nslot lists per column;
+// rows are reported as row0 + (row in A21) (row0 > 0 when A21 is one row block
+// of a larger matrix).
 __global__ void __launch_bounds__(kT1)
     k_relaxed_topk(const double *__restrict__ A21, int64_t m, int p, int64_t lda, int64_t L,
-                   int nseg, Cand *__restrict__ lists, int *__restrict__ lens,
+                   int seg_base, int nslot, int row0, Cand *__restrict__ lists, int *__restrict__ lens,
                    int32_t *__restrict__ info) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *key = reinterpret_cast<unsigned long long *>(smraw);  // [kCap]
@@ -139,15 +142,16 @@ __global__ void __launch_bounds__(kT1)
     }
     compact(true);
     const int k = cnt < K ? cnt : K;
-    Cand *out = lists + ((int64_t)j * nseg + seg) * (int64_t)p;
+    const int slot = j * nslot + seg_base + seg;
+    Cand *out = lists + (int64_t)slot * p;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         Cand c;
         c.key = key[i];
-        c.row = row[i];
+        c.row = row0 + row[i];
         c.pad = 0;
         out[i] = c;
     }
-    if (threadIdx.x == 0) lens[j * nseg + seg] = k;
+    if (threadIdx.x == 0) lens[slot] = k;
     if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
 }
 
@@ -270,13 +274,24 @@ __global__ void __launch_bounds__(256)
         }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < p * p; idx += blockDim.x) {
-        const int j = idx / p, k = idx % p;
-        const int r = chosen[j];
-        C[idx] = (r >= 0) ? A21[(int64_t)k * lda + r] : 0.0;
-    }
+    if (C != nullptr)
+        for (int idx = threadIdx.x; idx < p * p; idx += blockDim.x) {
+            const int j = idx / p, k = idx % p;
+            const int r = chosen[j];
+            C[idx] = (r >= 0) ? A21[(int64_t)k * lda + r] : 0.0;
+        }
     if (rows_out != nullptr)
         for (int j = threadIdx.x; j < p; j += blockDim.x) rows_out[j] = chosen[j];
+}
+
+// C(j, :) = A21(rows[j], :) (zero where rows[j] < 0), row-major
+__global__ void k_gather_rows(const double *__restrict__ A21, int64_t lda, int p,
+                              const int32_t *__restrict__ rows, double *__restrict__ C) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < p * p; idx += gridDim.x * blockDim.x) {
+        const int j = idx / p, k = idx % p;
+        const int r = rows[j];
+        C[idx] = (r >= 0) ? A21[(int64_t)k * lda + r] : 0.0;
+    }
 }
 
 }  // namespace
@@ -309,7 +324,7 @@ cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t
             smem_at_least((const void *)k_relaxed_topk, smem);
         if (err != cudaSuccess) return err;
         dim3 grid(nseg, p);
-        k_relaxed_topk<<<grid, kT1, smem, st>>>(A21, m, p, lda, L, nseg, lists, lens, info);
+        k_relaxed_topk<<<grid, kT1, smem, st>>>(A21, m, p, lda, L, 0, nseg, 0, lists, lens, info);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     } else {
@@ -321,6 +336,49 @@ cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t
         smem_at_least((const void *)k_relaxed_greedy, gsmem);
     if (err2 != cudaSuccess) return err2;
     k_relaxed_greedy<<<1, 256, gsmem, st>>>(A21, lda, p, nseg, lists, lens, C, rows);
+    return cudaGetLastError();
+}
+
+size_t relaxed_candidate_bytes(int nslot, int p) {
+    return sizeof(Cand) * (size_t)p * nslot * p + sizeof(int) * (size_t)p * nslot;
+}
+
+// Row split (Section 6): the candidate lists of one row block of A21 (one
+// segment), into slot `slot` of `nslot`.
+cudaError_t launch_relaxed_candidates(const double *A21, int64_t m, int p, int64_t lda, int row0, int slot,
+                                      int nslot, void *cand, int32_t *info, cudaStream_t st) {
+    Cand *lists = reinterpret_cast<Cand *>(cand);
+    int *lens = reinterpret_cast<int *>(lists + (size_t)p * nslot * p);
+    if (m == 0) {
+        // an empty block contributes empty lists
+        for (int j = 0; j < p; j++) {
+            cudaError_t e = cudaMemsetAsync(lens + (size_t)j * nslot + slot, 0, sizeof(int), st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const size_t smem = (sizeof(unsigned long long) + sizeof(int)) * kCap;
+    cudaError_t err = smem_at_least((const void *)k_relaxed_topk, smem);
+    if (err != cudaSuccess) return err;
+    k_relaxed_topk<<<dim3(1, p), kT1, smem, st>>>(A21, m, p, lda, m, slot, nslot, row0, lists, lens, info);
+    return cudaGetLastError();
+}
+
+// The greedy over the nslot lists of every column; rows[j] = the chosen A21
+// row of C row j (-1: none).  C is not written.
+cudaError_t launch_relaxed_select(int p, int nslot, const void *cand, int32_t *rows, cudaStream_t st) {
+    const Cand *lists = reinterpret_cast<const Cand *>(cand);
+    const int *lens = reinterpret_cast<const int *>(lists + (size_t)p * nslot * p);
+    const size_t gsmem = sizeof(Cand) * (size_t)p * nslot * kHead + sizeof(int) * (size_t)p;
+    cudaError_t err = smem_at_least((const void *)k_relaxed_greedy, gsmem);
+    if (err != cudaSuccess) return err;
+    k_relaxed_greedy<<<1, 256, gsmem, st>>>(nullptr, 0, p, nslot, lists, lens, nullptr, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const double *A21, int64_t lda, int p, const int32_t *rows, double *C,
+                               cudaStream_t st) {
+    k_gather_rows<<<(p * p + 255) / 256, 256, 0, st>>>(A21, lda, p, rows, C);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ CTP_OK, CTP_EINVAL, CTP_ENOMEM, CTP_ECUDA, CTP_ENONFINITE, CTP_ETIMEOUT, CTP_ECA
     CTP_EUNSUPPORTED = range(8)
 STATUS = {0: "CTP_OK", 1: "CTP_EINVAL", 2: "CTP_ENOMEM", 3: "CTP_ECUDA", 4: "CTP_ENONFINITE",
           5: "CTP_ETIMEOUT", 6: "CTP_ECAPACITY", 7: "CTP_EUNSUPPORTED"}
-PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3}
+PIVOT = {"strict": 0, "relaxed": 1, "tpp": 2, "restricted": 3, "single_row": 4}
 PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
 SOLVE = {"fp64": 0, "tc": 1}
 SMODE = {"none": 0, "fp64": 1, "fp32": 2, "fp64_packed": 3, "fp32_packed": 4, "fp32_tiled": 5,
@@ -41,7 +41,9 @@ EXPORTS = ["ctp_max_p", "ctp_create", "ctp_destroy", "ctp_workspace_size", "ctp_
            "ctp_sym_grad_dense", "ctp_sym_grad_pattern", "ctp_backward_error_csc", "ctp_refine_csc",
            "ctp_mf_analyse", "ctp_mf_factor", "ctp_mf_fronts", "ctp_mf_info", "ctp_mf_destroy",
            "ctp_mf_panel_info", "ctp_mf_solve_workspace_size", "ctp_mf_solve",
-           "ctp_mf_refine_workspace_size", "ctp_mf_refine", "ctp_mf_adjoint_solve"]
+           "ctp_mf_refine_workspace_size", "ctp_mf_refine", "ctp_mf_adjoint_solve",
+           "ctp_compress_strict_merge", "ctp_relaxed_candidates_size", "ctp_compress_relaxed_candidates",
+           "ctp_compress_relaxed_select", "ctp_gather_rows"]
 TUNE_FORM_WALK, TUNE_BATCH_SMEM_KB, TUNE_FACTOR_G, TUNE_TPP_SPIN = 0, 1, 2, 3
 WALK = {"auto": 0, "round_robin": 1, "chunks": 2, "panels": 3}
 
@@ -141,6 +143,11 @@ def load(path: str = LIB_PATH):
                                      ctypes.POINTER(i32), P]
     L.ctp_autotune_supernode.argtypes = [P, i64, i32, P, i64, ctypes.POINTER(Options), P, P, P, P,
                                          P, i64, P, sz, i32, P, i32, P, P, ctypes.POINTER(i32), P]
+    L.ctp_compress_strict_merge.argtypes = [P, i32, i32, P, i64, P, P]
+    L.ctp_relaxed_candidates_size.argtypes = [i32, i32, ctypes.POINTER(sz)]
+    L.ctp_compress_relaxed_candidates.argtypes = [P, i64, i32, P, i64, i64, i32, i32, P, sz, P]
+    L.ctp_compress_relaxed_select.argtypes = [P, i32, i32, P, sz, P, P]
+    L.ctp_gather_rows.argtypes = [P, i32, P, i64, P, P, P]
     L.ctp_profile_begin.argtypes = [P]
     L.ctp_profile_end.argtypes = [P, i32, P, P, P, ctypes.POINTER(i32)]
     for f in EXPORTS[1:]:
@@ -226,6 +233,31 @@ class Context:
                                              _ptr(perm), _ptr(piv), _ptr(D), _ptr(nelim), _ptr(S),
                                              lds, _ptr(ws), ws.numel(), _stream(stream)))
         return ws
+
+    def compress_strict_merge(self, P, p, C_blocks, block_stride, C, stream=None):
+        """C = elementwise max of P stacked strict compressed matrices (the
+        exchange of the row split, Section 6)."""
+        _check("ctp_compress_strict_merge", self.lib.ctp_compress_strict_merge(
+            self.handle, P, p, _ptr(C_blocks), block_stride, _ptr(C), _stream(stream)))
+
+    def relaxed_candidates_buffer(self, P, p):
+        import torch
+        b = ctypes.c_size_t()
+        _check("ctp_relaxed_candidates_size", self.lib.ctp_relaxed_candidates_size(P, p, ctypes.byref(b)))
+        return torch.zeros(int(b.value), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def compress_relaxed_candidates(self, A21_block, m, p, lda, row0, P, block, cand, stream=None):
+        """Candidate lists of one row block (rows row0.. of A21) into slot `block`."""
+        _check("ctp_compress_relaxed_candidates", self.lib.ctp_compress_relaxed_candidates(
+            self.handle, m, p, _ptr(A21_block), lda, row0, P, block, _ptr(cand), cand.numel(), _stream(stream)))
+
+    def compress_relaxed_select(self, P, p, cand, rows, stream=None):
+        _check("ctp_compress_relaxed_select", self.lib.ctp_compress_relaxed_select(
+            self.handle, P, p, _ptr(cand), cand.numel(), _ptr(rows), _stream(stream)))
+
+    def gather_rows(self, p, A21, lda, rows, C, stream=None):
+        _check("ctp_gather_rows", self.lib.ctp_gather_rows(
+            self.handle, p, _ptr(A21), lda, _ptr(rows), _ptr(C), _stream(stream)))
 
     def tune_set(self, key, value):
         _check("ctp_tune_set", self.lib.ctp_tune_set(self.handle, key, value))

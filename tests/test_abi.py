@@ -94,3 +94,18 @@ def test_tuning_knobs_check_arguments(lib):
                                   None, None) == ctp.CTP_EINVAL
     assert lib.ctp_autotune_supernode(None, 10, 2, None, 10, None, None, None, None, None, None, 0,
                                       None, 0, 1, None, 1, None, None, None, None) == ctp.CTP_EINVAL
+
+
+def test_row_split_entry_points_check_arguments(lib):
+    sz = ctypes.c_size_t()
+    assert lib.ctp_relaxed_candidates_size(0, 4, ctypes.byref(sz)) == ctp.CTP_EINVAL
+    assert lib.ctp_relaxed_candidates_size(9, 4, ctypes.byref(sz)) == ctp.CTP_EUNSUPPORTED
+    assert lib.ctp_relaxed_candidates_size(2, 257, ctypes.byref(sz)) == ctp.CTP_EUNSUPPORTED
+    assert lib.ctp_relaxed_candidates_size(8, 256, ctypes.byref(sz)) == ctp.CTP_OK
+    # 256-byte info word, then (16-byte candidate) x p x P x p lists and P x p lengths
+    assert sz.value == 256 + 16 * 256 * 8 * 256 + 4 * 256 * 8
+    assert lib.ctp_compress_strict_merge(None, 2, 4, None, 16, None, None) == ctp.CTP_EINVAL
+    assert lib.ctp_compress_relaxed_candidates(None, 10, 4, None, 10, 0, 2, 0, None, 0,
+                                               None) == ctp.CTP_EINVAL
+    assert lib.ctp_compress_relaxed_select(None, 2, 4, None, 0, None, None) == ctp.CTP_EINVAL
+    assert lib.ctp_gather_rows(None, 4, None, 10, None, None, None) == ctp.CTP_EINVAL

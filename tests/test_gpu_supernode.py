@@ -176,7 +176,7 @@ CASES = [(1, 1), (2, 2), (3, 1), (30, 30), (300, 17), (513, 33), (1200, 100), (8
          (3000, 256), (700, 129)]
 
 
-@pytest.mark.parametrize("pivot", ["strict", "relaxed", "restricted", "tpp"])
+@pytest.mark.parametrize("pivot", ["strict", "relaxed", "restricted", "tpp", "single_row"])
 @pytest.mark.parametrize("n,p", CASES)
 @pytest.mark.parametrize("seed", [0, 1])
 def test_factor_matches_oracle(ctx, pivot, n, p, seed):

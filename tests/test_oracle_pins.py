@@ -14,7 +14,7 @@ from listing_restated import restated_listing
 from oracle import oracle as O
 from paper_1305_2353_gb300 import inputs
 
-METHODS = ["strict", "relaxed", "tpp", "restricted"]
+METHODS = ["strict", "relaxed", "tpp", "restricted", "single_row"]
 
 
 # --------------------------------------------------------------------------
@@ -104,11 +104,12 @@ def test_reconstruction(method, seed):
     assert _recon_error(A, p, res) <= tol
 
 
-@pytest.mark.parametrize("method", ["strict", "tpp"])
+@pytest.mark.parametrize("method", ["strict", "tpp", "single_row"])
 @pytest.mark.parametrize("seed", range(8))
 def test_threshold_bound_all_rows(method, seed):
     """Theorem 5.2 (strict) and the classical TPP bound: |l_ij| <= 1/u for every
-    row, A21 included."""
+    row, A21 included.  Theorem 5.2's proof holds for any partition of the A21
+    rows into the sets J_j, so it covers single-row compression too (one set)."""
     n, p, u = 80, 16, 0.1
     A = _tough(n, p, seed)
     res = O.factor(A, p, method, u=u)
@@ -208,7 +209,7 @@ def test_n_equals_p_all_methods_identical(seed):
     p = 24
     A = _tough(p, p, seed)
     ref = O.factor(A, p, "tpp")
-    for method in ("strict", "relaxed", "restricted"):
+    for method in ("strict", "relaxed", "restricted", "single_row"):
         r = O.factor(A, p, method)
         assert np.array_equal(r["perm"], ref["perm"])
         assert np.array_equal(r["piv"], ref["piv"])
@@ -474,3 +475,55 @@ def test_2x2_column_maxima_exclude_partner():
     assert list(r["piv"]) == [O.PIV_2X2_FIRST, O.PIV_2X2_SECOND]
     g = r["log"][r["log"]["kind"] == 4][0]
     assert abs(g["lhs"] - 3.6) < 1e-15 and g["rhs"] == 4.0
+
+
+# --------------------------------------------------------------------------
+# single-row compression (Section 4.1, closing remark): eq. (4.1) with the one
+# set J = all A21 rows, i.e. C is the row of column maxima of |A21|
+
+def test_single_row_on_fig42(golden):
+    """The worked example of Figure 4.2 compressed with one set: the column
+    maxima of its A21, which are also the column maxima of the strict C the
+    figure prints."""
+    g = golden("fig4_2_strict.txt")
+    A21 = g["A21"]
+    p = A21.shape[1]
+    A = np.vstack([np.eye(p) * 50.0, A21])
+    r = O.factor(A, p, "single_row")
+    assert np.array_equal(r["C"][0], [4.0, 10.0, 10.0])
+    assert np.array_equal(r["C"][0], g["C"].max(axis=0))
+    assert not r["C"][1:].any()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_single_row_is_column_max_of_strict(seed):
+    A = _tough(400, 24, seed)
+    s1 = O.factor(A, 24, "single_row")
+    st = O.factor(A, 24, "strict")
+    assert np.array_equal(s1["C"][0], st["C"].max(axis=0))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_single_row_with_one_a21_row_is_strict(seed):
+    """With one A21 row, strict compression has a single nonzero row, |a21|,
+    which is also the single row: the factorizations coincide bit for bit."""
+    p = 18
+    A = _tough(p + 1, p, seed)
+    s1 = O.factor(A, p, "single_row")
+    st = O.factor(A, p, "strict")
+    assert np.array_equal(s1["perm"], st["perm"]) and np.array_equal(s1["piv"], st["piv"])
+    assert np.array_equal(s1["A"], st["A"]) and np.array_equal(s1["D"], st["D"])
+
+
+def test_single_row_rejects_more_than_strict():
+    """The paper's observation: one row over-estimates the growth, and most
+    pivots beyond the first few are rejected (here: over a seeded sample of the
+    uneven N(0,1) fronts with many A21 rows, fewer eliminated than strict)."""
+    fr = inputs.batch(200, seed=3)
+    tot_s1 = tot_st = 0
+    for A in fr:
+        if A.shape[0] < 4 * A.shape[1]:
+            continue
+        tot_s1 += O.factor(A, A.shape[1], "single_row")["nelim"]
+        tot_st += O.factor(A, A.shape[1], "strict")["nelim"]
+    assert tot_s1 < tot_st
