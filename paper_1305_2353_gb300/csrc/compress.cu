@@ -14,6 +14,7 @@
 // tile [p][TR+1] without passing through registers; STAGES tiles are in flight
 // per CTA.  The CTA grid is persistent (a multiple of the SM count).
 #include "ctp_internal.cuh"
+#include "tc_common.cuh"
 
 namespace ctp {
 
@@ -192,6 +193,138 @@ __global__ void __launch_bounds__(256)
     if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
 }
 
+// The same compression with the tiles brought in by TMA: one
+// cp.async.bulk.tensor per tile of 16 rows x p columns (16 rows of a column are
+// the 128 bytes of one swizzle span), three tiles in flight per CTA, two CTAs
+// per SM.  With the 128-byte swizzle, the 16-byte chunk c of column k sits at
+// chunk c ^ (k mod 8) of its 128-byte row, so both the row-per-lane reads of
+// the argmax and the column-per-lane reads of the merge into C meet few bank
+// conflicts.  Each tile costs one instruction to load instead of one per
+// element, which is what kept the per-element kernel above at a quarter of HBM.
+constexpr int kTT = 16;         // rows per TMA tile
+constexpr int kStagesT = 3;     // tiles in flight per CTA
+constexpr int kGroupsT = kThreads / kTT;  // column groups of the argmax
+
+__device__ __forceinline__ double tile_at(const uint8_t *t, int k, int r) {
+    return *reinterpret_cast<const double *>(t + k * 128 + ((((r >> 1) ^ (k & 7)) & 7) << 4) + ((r & 1) << 3));
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_compress_strict_tma(const __grid_constant__ CUtensorMap map, int64_t m, int p, uint32_t stage_bytes,
+                          unsigned long long *__restrict__ Ckeys, int32_t *__restrict__ J,
+                          int32_t *__restrict__ rowflags, int32_t *__restrict__ info) {
+    extern __shared__ unsigned char smraw[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    __shared__ unsigned long long full[kStagesT];
+    __shared__ unsigned long long pkey[kGroupsT][kTT];
+    __shared__ int pidx[kGroupsT][kTT];
+    __shared__ int rowJ[kTT];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntiles = (m + kTT - 1) / kTT;
+    if (tid == 0) {
+        for (int s = 0; s < kStagesT; s++) tc::mbar_init(&full[s], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int64_t k) {  // the k-th tile of this CTA into its stage
+        const int64_t t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) return;
+        const int s = (int)(k % kStagesT);
+        tc::mbar_expect_tx(&full[s], (uint32_t)(kTT * 8 * p));  // the box: 16 rows x p columns
+        tc::tma_load_2d(tiles + (size_t)s * stage_bytes, &map, (int)(t * kTT), 0, &full[s]);
+    };
+    if (tid == 0)
+        for (int k = 0; k < kStagesT - 1; k++) issue(k);
+    bool nonfinite = false;
+    const int r = tid % kTT, g = tid / kTT;
+    for (int64_t k = 0;; k++) {
+        const int64_t t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        if (tid == 0) issue(k + kStagesT - 1);  // that stage was released at the end of round k-1
+        const int s = (int)(k % kStagesT);
+        const bool ok = tc::mbar_wait(&full[s], (uint32_t)((k / kStagesT) & 1), &abort_flag);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
+                // wait (bounded) for the copies still in flight into this CTA's stages
+                for (int64_t k2 = k + 1; k2 < k + kStagesT; k2++)
+                    if (blockIdx.x + k2 * gridDim.x < ntiles)
+                        tc::mbar_wait(&full[k2 % kStagesT], (uint32_t)((k2 / kStagesT) & 1), &abort_flag);
+            }
+            break;
+        }
+        const uint8_t *tile = tiles + (size_t)s * stage_bytes;
+        const int64_t row0 = t * kTT;
+        const int nrows = (int)((m - row0) < kTT ? (m - row0) : kTT);
+        // (1) row argmax: thread (r, g) scans columns g, g + kGroupsT, ... ascending
+        unsigned long long best = 0;
+        int bidx = -1;
+        if (r < nrows)
+            for (int kc = g; kc < p; kc += kGroupsT) {
+                const unsigned long long key = abs_key(tile_at(tile, kc, r));
+                nonfinite |= key >= kInfKey;
+                if (bidx < 0 || key > best) {
+                    best = key;
+                    bidx = kc;
+                }
+            }
+        pkey[g][r] = best;
+        pidx[g][r] = bidx;
+        __syncthreads();
+        if (tid < kTT) {
+            unsigned long long b = 0;
+            int bi = -1;
+            for (int gg = 0; gg < kGroupsT; gg++) {
+                const int ii = pidx[gg][tid];
+                const unsigned long long kk = pkey[gg][tid];
+                if (ii < 0) continue;
+                if (bi < 0 || kk > b || (kk == b && ii < bi)) {
+                    b = kk;
+                    bi = ii;
+                }
+            }
+            rowJ[tid] = bi;
+            if (J != nullptr && tid < nrows) J[row0 + tid] = bi;
+            if (rowflags != nullptr && tid < nrows && bi >= 0) rowflags[bi] = 1;
+        }
+        __syncthreads();
+        // (2) merge the tile's rows into C: warp w takes rows w and w + 8, lanes
+        // walk k; every C key is loaded before any compare (the L2 round trips
+        // overlap), the atomic fires only on a new maximum
+        constexpr int KPL = kMaxP / 32;
+        constexpr int RPW = kTT / (kThreads / 32);
+        unsigned long long cur[RPW][KPL];
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+            const int rr = warp + q * (kThreads / 32);
+            const unsigned long long *crow = Ckeys + (int64_t)(rr < nrows ? rowJ[rr] : 0) * p;
+#pragma unroll
+            for (int u = 0; u < KPL; u++) {
+                const int kc = lane + 32 * u;
+                cur[q][u] = (rr < nrows && kc < p) ? __ldcg(crow + kc) : ~0ull;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+            const int rr = warp + q * (kThreads / 32);
+            if (rr >= nrows) continue;
+            unsigned long long *crow = Ckeys + (int64_t)rowJ[rr] * p;
+#pragma unroll
+            for (int u = 0; u < KPL; u++) {
+                const int kc = lane + 32 * u;
+                if (kc < p) {
+                    const unsigned long long key = abs_key(tile_at(tile, kc, rr));
+                    if (key > cur[q][u]) atomicMax(crow + kc, key);
+                }
+            }
+        }
+        __syncthreads();  // this stage is refilled next round
+    }
+    if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
+}
+
 __global__ void k_keys_to_rowmajor(const unsigned long long *__restrict__ Ckeys,
                                    double *__restrict__ C, int pp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,10 +339,44 @@ static size_t strict_smem(int p) {
            kTR * sizeof(int);
 }
 
+// TMA map of A21 (m x p column-major, lda) in boxes of 16 rows x p columns with
+// the 128-byte swizzle; false when the addresses do not allow one (A21 or lda*8
+// not a multiple of 16 bytes) or the encoder is unavailable
+static bool make_map_a21(CUtensorMap *map, const double *A21, int64_t m, int p, int64_t lda) {
+    if ((reinterpret_cast<uintptr_t>(A21) & 15) != 0 || ((lda * 8) & 15) != 0) return false;
+    if (m >= ((int64_t)1 << 31)) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tc::encode_fn();
+    if (enc == nullptr) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)p};
+    cuuint64_t strides[1] = {(cuuint64_t)lda * 8};
+    cuuint32_t box[2] = {(cuuint32_t)kTT, (cuuint32_t)p};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(A21), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
                                    unsigned long long *Ckeys, int32_t *J, int32_t *rowflags, int32_t *info,
                                    int num_sms, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
+    CUtensorMap map;
+    if (make_map_a21(&map, A21, m, p, lda)) {
+        const uint32_t stage_bytes = (uint32_t)((p * 128 + 1023) / 1024 * 1024);
+        const size_t smem = (size_t)kStagesT * stage_bytes + 1024;
+        cudaError_t err = smem_at_least((const void *)k_compress_strict_tma, smem);
+        if (err != cudaSuccess) return err;
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress_strict_tma, kThreads, smem);
+        if (err != cudaSuccess) return err;
+        if (per_sm < 1) per_sm = 1;
+        const int64_t ntiles = (m + kTT - 1) / kTT;
+        int64_t grid = (int64_t)num_sms * per_sm;
+        if (grid > ntiles) grid = ntiles;
+        k_compress_strict_tma<<<(unsigned)grid, kThreads, smem, st>>>(map, m, p, stage_bytes, Ckeys, J, rowflags,
+                                                                      info);
+        return cudaGetLastError();
+    }
     size_t smem = strict_smem(p);
     cudaError_t err = smem_at_least((const void *)k_compress_strict, smem);
     if (err != cudaSuccess) return err;

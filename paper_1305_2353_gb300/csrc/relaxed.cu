@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kT1 = 512;      // threads per CTA in phase 1
 constexpr int kCap = 4096;    // candidate buffer (power of two)
-constexpr int kChunk = 2048;  // rows read per iteration (4 per thread)
+constexpr int kChunk = 2048;  // rows read per pass (4 per thread)
 constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long kInfKey = 0x7FF0000000000000ull;
 
@@ -70,10 +70,147 @@ __device__ __forceinline__ int next_pow2(int x) {
     return n;
 }
 
+// The K-th largest of the keys a CTA holds (keys with the top bit clear),
+// found digit by digit (8 bits at a time) with a 256-bin histogram in shared
+// memory: exact, and no sort.  Every thread passes its own keys through
+// `each(f)` (f(key) is called once per key it holds).
+struct RadixScratch {
+    unsigned hist[256];
+    unsigned long long prefix;
+    int k;
+};
+template <typename Each>
+__device__ unsigned long long kth_largest(int K, RadixScratch &rs, Each each) {
+    unsigned long long prefix = 0, mask = 0;
+    int k = K;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) rs.hist[b] = 0;
+        __syncthreads();
+        each([&](unsigned long long v) {
+            if ((v & mask) == prefix) atomicAdd(&rs.hist[(v >> shift) & 255u], 1u);
+        });
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // lane l sums bins 255-8l .. 248-8l (descending order of digits)
+            const int lane = threadIdx.x;
+            unsigned cnt[8], tot = 0;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                cnt[q] = rs.hist[255 - 8 * lane - q];
+                tot += cnt[q];
+            }
+            unsigned incl = tot;  // inclusive prefix over lanes (larger digits first)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned excl = incl - tot;
+            // the lane whose range holds the k-th largest
+            if (excl < (unsigned)k && (unsigned)k <= incl) {
+                unsigned c = excl;
+                int d = 255 - 8 * lane;
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    if (c + cnt[q] >= (unsigned)k) {
+                        d = 255 - 8 * lane - q;
+                        break;
+                    }
+                    c += cnt[q];
+                }
+                rs.prefix = prefix | ((unsigned long long)d << shift);
+                rs.k = k - (int)c;
+            }
+        }
+        __syncthreads();
+        prefix = rs.prefix;
+        k = rs.k;
+        mask |= 0xFFull << shift;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+// Append the (key, row) pairs with keep = true to the buffer, one shared atomic
+// per warp (the order inside the buffer does not matter).
+__device__ __forceinline__ void warp_append(bool keep, unsigned long long kv, int rw, unsigned long long *key,
+                                            int *row, int *cnt) {
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (bal == 0) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(bal) - 1) base = atomicAdd(cnt, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+    if (keep) {
+        const int at = base + __popc(bal & ((1u << lane) - 1u));
+        key[at] = kv;
+        row[at] = rw;
+    }
+}
+
+// Keep the buffer entries with key >= thr, in place (every thread reads its
+// entries before the barrier and writes after it).
+__device__ void compact_ge(unsigned long long thr, unsigned long long *key, int *row, int *cnt, int *wsum) {
+    const int n = *cnt;
+    constexpr int kPerT = kCap / kT1;
+    unsigned long long kk[kPerT];
+    int rr[kPerT];
+    bool kp[kPerT];
+    int mine = 0;
+#pragma unroll
+    for (int q = 0; q < kPerT; q++) {
+        const int i = threadIdx.x * kPerT + q;  // contiguous runs keep the order stable
+        kp[q] = i < n && key[i] >= thr;
+        kk[q] = i < n ? key[i] : 0;
+        rr[q] = i < n ? row[i] : 0;
+        mine += kp[q] ? 1 : 0;
+    }
+    // exclusive scan of `mine` over the CTA
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < kT1 / 32 ? wsum[threadIdx.x] : 0, in2 = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, in2, o);
+            if (threadIdx.x >= o) in2 += y;
+        }
+        if (threadIdx.x < kT1 / 32) wsum[threadIdx.x] = in2 - v;  // exclusive, per warp
+        if (threadIdx.x == kT1 / 32 - 1) wsum[kT1 / 32] = in2;    // total
+    }
+    __syncthreads();
+    int at = wsum[w] + incl - mine;
+#pragma unroll
+    for (int q = 0; q < kPerT; q++)
+        if (kp[q]) {
+            key[at] = kk[q];
+            row[at] = rr[q];
+            ++at;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) *cnt = wsum[kT1 / 32];
+    __syncthreads();
+}
+
 // Phase 1: CTA (seg, j) keeps the top K_j entries of rows [seg*L, (seg+1)*L) of
 // column j.  Its list goes to slot s = seg_base + seg of nslot lists per column;
 // rows are reported as row0 + (row in A21) (row0 > 0 when A21 is one row block
 // of a larger matrix).
+// The stream is HBM-bound: each pass reads kChunk rows, four per thread in
+// flight.  A threshold thr (a lower bound of the K-th largest key of the
+// segment, taken as the K-th largest of what was seen so far by radix
+// selection) filters the stream, so only entries >= thr reach the shared
+// buffer (ties kept: a superset of the top K); when the buffer fills, the
+// threshold is raised and the buffer filtered again.  At the end the survivors
+// (K plus ties) are sorted once into the paper's order (|a| descending, lower
+// row first).
 __global__ void __launch_bounds__(kT1)
     k_relaxed_topk(const double *__restrict__ A21, int64_t m, int p, int64_t lda, int64_t L,
                    int seg_base, int nslot, int row0, Cand *__restrict__ lists, int *__restrict__ lens,
@@ -82,69 +219,96 @@ __global__ void __launch_bounds__(kT1)
     unsigned long long *key = reinterpret_cast<unsigned long long *>(smraw);  // [kCap]
     int *row = reinterpret_cast<int *>(key + kCap);                           // [kCap]
     __shared__ int cnt;
-    __shared__ unsigned long long thr_key;  // current K-th best (valid when have_thr)
-    __shared__ int thr_row, have_thr;
+    __shared__ int wsum[kT1 / 32 + 1];
+    __shared__ RadixScratch rs;
     const int j = blockIdx.y, seg = blockIdx.x;
-    const int K = (int)((int64_t)j + 1 < m ? (int64_t)j + 1 : m);
     const int64_t r0 = (int64_t)seg * L, r1 = (r0 + L < m) ? r0 + L : m;
+    const int64_t len = r1 > r0 ? r1 - r0 : 0;
+    const int K = (int)((int64_t)j + 1 < len ? (int64_t)j + 1 : len);
     const double *col = A21 + (int64_t)j * lda;
-    if (threadIdx.x == 0) {
-        cnt = 0;
-        have_thr = 0;
-        thr_key = 0;
-        thr_row = 0x7fffffff;
-    }
+    if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     bool nonfinite = false;
-    auto compact = [&](bool final) {
-        const int n = cnt, N = next_pow2(n > 1 ? n : 1);
-        for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
-            key[i] = 0;
-            row[i] = 0x7fffffff;  // padding sorts last
-        }
-        __syncthreads();
-        bitonic_desc(key, row, N);
-        if (!final && threadIdx.x == 0) {
-            cnt = n < K ? n : K;
-            if (n >= K) {
-                have_thr = 1;
-                thr_key = key[K - 1];
-                thr_row = row[K - 1];
-            }
-        }
-        __syncthreads();
+    bool have_thr = false;
+    // thr: the K-th largest key among the rows seen so far.  A later row whose
+    // key equals it ranks after every earlier tie (rows only grow along the
+    // stream), so it cannot enter the top K: later rows need key > thr.
+    unsigned long long thr = 0;
+    auto buffer_each = [&](auto f) {
+        for (int i = threadIdx.x; i < cnt; i += kT1) f(key[i]);
     };
+    constexpr int kPer = kChunk / kT1;
     for (int64_t base = r0; base < r1; base += kChunk) {
-        const int ht = have_thr;
-        const unsigned long long tk = thr_key;
-        const int tr = thr_row;
-        double v[kChunk / kT1];
+        double v[kPer];
 #pragma unroll
-        for (int q = 0; q < kChunk / kT1; q++) {
+        for (int q = 0; q < kPer; q++) {
             const int64_t r = base + q * kT1 + threadIdx.x;
             v[q] = (r < r1) ? __ldcs(col + r) : 0.0;
         }
+        unsigned long long kv[kPer];
 #pragma unroll
-        for (int q = 0; q < kChunk / kT1; q++) {
+        for (int q = 0; q < kPer; q++) {
             const int64_t r = base + q * kT1 + threadIdx.x;
-            if (r >= r1) continue;
-            const unsigned long long k = (unsigned long long)__double_as_longlong(v[q]) & kAbsMask;
-            nonfinite |= k >= kInfKey;
-            if (!ht || k > tk || (k == tk && (int)r < tr)) {
-                const int at = atomicAdd(&cnt, 1);
-                key[at] = k;  // at < kCap: a compaction keeps at least kChunk slots free
-                row[at] = (int)r;
-            }
+            kv[q] = (unsigned long long)__double_as_longlong(v[q]) & kAbsMask;
+            nonfinite |= (r < r1) && kv[q] >= kInfKey;
+        }
+        const int64_t nin = (r1 - base) < kChunk ? (r1 - base) : kChunk;
+        bool fresh = false;  // thr taken from this chunk: its own ties stay
+        if (!have_thr && cnt == 0 && nin >= K && K > 0) {
+            // the first chunk alone holds K entries: its K-th largest is a valid threshold
+            thr = kth_largest(K, rs, [&](auto f) {
+#pragma unroll
+                for (int q = 0; q < kPer; q++)
+                    if (base + q * kT1 + threadIdx.x < r1) f(kv[q]);
+            });
+            have_thr = true;
+            fresh = true;
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const int64_t r = base + q * kT1 + threadIdx.x;
+            const bool keep = r < r1 && (!have_thr || kv[q] > thr || (fresh && kv[q] == thr));
+            warp_append(keep, kv[q], (int)r, key, row, &cnt);
         }
         __syncthreads();
-        // set the threshold as soon as K candidates exist, and compact when full
-        if ((!have_thr && cnt >= K) || cnt > kCap - kChunk) compact(false);
+        // room for another chunk: raise the threshold and filter when needed
+        if (cnt > kCap - kChunk || (!have_thr && cnt >= K && K > 0)) {
+            thr = kth_largest(K, rs, buffer_each);
+            have_thr = true;
+            compact_ge(thr, key, row, &cnt, wsum);
+            if (cnt > kCap - kChunk) {
+                // many entries tie with the threshold: sort and keep exactly the
+                // first K
+                const int N = next_pow2(cnt);
+                for (int i = cnt + threadIdx.x; i < N; i += kT1) {
+                    key[i] = 0;
+                    row[i] = 0x7fffffff;
+                }
+                __syncthreads();
+                bitonic_desc(key, row, N);
+                thr = key[K - 1];
+                __syncthreads();
+                if (threadIdx.x == 0) cnt = K;
+                __syncthreads();
+            }
+        }
     }
-    compact(true);
-    const int k = cnt < K ? cnt : K;
+    // survivors: the top K plus ties, sorted once
+    if (have_thr && cnt > K) {
+        const unsigned long long t2 = kth_largest(K, rs, buffer_each);
+        compact_ge(t2, key, row, &cnt, wsum);
+    }
+    const int n = cnt, N = next_pow2(n > 1 ? n : 1);
+    for (int i = n + threadIdx.x; i < N; i += kT1) {
+        key[i] = 0;
+        row[i] = 0x7fffffff;  // padding sorts last
+    }
+    __syncthreads();
+    bitonic_desc(key, row, N);
+    const int k = n < K ? n : K;
     const int slot = j * nslot + seg_base + seg;
     Cand *out = lists + (int64_t)slot * p;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    for (int i = threadIdx.x; i < k; i += kT1) {
         Cand c;
         c.key = key[i];
         c.row = row0 + row[i];
@@ -298,7 +462,8 @@ __global__ void k_gather_rows(const double *__restrict__ A21, int64_t lda, int p
 
 size_t relaxed_aux_bytes(int64_t m, int p, int num_sms) {
     const int nseg = relaxed_segments(m, p, num_sms);
-    return sizeof(Cand) * (size_t)p * nseg * p + sizeof(int) * (size_t)p * nseg;
+    // candidate lists, their lengths, the chosen rows
+    return sizeof(Cand) * (size_t)p * nseg * p + sizeof(int) * (size_t)p * nseg + sizeof(int32_t) * (size_t)p;
 }
 
 int relaxed_segments(int64_t m, int p, int num_sms) {
@@ -331,12 +496,20 @@ cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t
         cudaError_t err = cudaMemsetAsync(lens, 0, sizeof(int) * (size_t)p * nseg, st);
         if (err != cudaSuccess) return err;
     }
+    // the greedy (one CTA) picks the rows; the gather of those rows into C (p^2
+    // scattered reads) runs over many CTAs so that the reads overlap
     const size_t gsmem = sizeof(Cand) * (size_t)p * nseg * kHead + sizeof(int) * (size_t)p;
     cudaError_t err2 =
         smem_at_least((const void *)k_relaxed_greedy, gsmem);
     if (err2 != cudaSuccess) return err2;
-    k_relaxed_greedy<<<1, 256, gsmem, st>>>(A21, lda, p, nseg, lists, lens, C, rows);
-    return cudaGetLastError();
+    int32_t *chosen = reinterpret_cast<int32_t *>(lens + (size_t)p * nseg);
+    k_relaxed_greedy<<<1, 256, gsmem, st>>>(nullptr, 0, p, nseg, lists, lens, nullptr, chosen);
+    err2 = cudaGetLastError();
+    if (err2 != cudaSuccess) return err2;
+    k_gather_rows<<<(p * p + 255) / 256, 256, 0, st>>>(A21, lda, p, chosen, C);
+    err2 = cudaGetLastError();
+    if (err2 != cudaSuccess || rows == nullptr) return err2;
+    return cudaMemcpyAsync(rows, chosen, sizeof(int32_t) * (size_t)p, cudaMemcpyDeviceToDevice, st);
 }
 
 size_t relaxed_candidate_bytes(int nslot, int p) {
