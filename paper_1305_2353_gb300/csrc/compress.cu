@@ -195,20 +195,13 @@ __global__ void __launch_bounds__(256)
 
 // The same compression with the tiles brought in by TMA: one
 // cp.async.bulk.tensor per tile of 16 rows x p columns (16 rows of a column are
-// the 128 bytes of one swizzle span), three tiles in flight per CTA, two CTAs
-// per SM.  With the 128-byte swizzle, the 16-byte chunk c of column k sits at
+// the 128 bytes of one swizzle span), three stages per CTA, two CTAs per SM.  With the 128-byte swizzle, the 16-byte chunk c of column k sits at
 // chunk c ^ (k mod 8) of its 128-byte row, so both the row-per-lane reads of
 // the argmax and the column-per-lane reads of the merge into C meet few bank
 // conflicts.  Each tile costs one instruction to load instead of one per
 // element, which is what kept the per-element kernel above at a quarter of HBM.
 constexpr int kTT = 16;         // rows per TMA tile
-constexpr int kStagesT = 3;     // tiles in flight per CTA
-constexpr int kGroupsT = kThreads / kTT;  // column groups of the argmax
-
-__device__ __forceinline__ double tile_at(const uint8_t *t, int k, int r) {
-    return *reinterpret_cast<const double *>(t + k * 128 + ((((r >> 1) ^ (k & 7)) & 7) << 4) + ((r & 1) << 3));
-}
-
+constexpr int kStagesT = 3;     // tiles per CTA: one in use, two in flight
 __global__ void __launch_bounds__(kThreads, 2)
     k_compress_strict_tma(const __grid_constant__ CUtensorMap map, int64_t m, int p, uint32_t stage_bytes,
                           unsigned long long *__restrict__ Ckeys, int32_t *__restrict__ J,
@@ -216,8 +209,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     extern __shared__ unsigned char smraw[];
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ unsigned long long full[kStagesT];
-    __shared__ unsigned long long pkey[kGroupsT][kTT];
-    __shared__ int pidx[kGroupsT][kTT];
+    __shared__ unsigned long long pkey[kThreads / 32][kTT];  // per warp: best key of each row
+    __shared__ int pidx[kThreads / 32][kTT];
     __shared__ int rowJ[kTT];
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -238,13 +231,18 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (tid == 0)
         for (int k = 0; k < kStagesT - 1; k++) issue(k);
     bool nonfinite = false;
-    const int r = tid % kTT, g = tid / kTT;
+    // phase 1 mapping: thread (rp, g) takes rows 2rp, 2rp+1 (one 16-byte chunk)
+    // of columns g, g + 32, ...; a warp covers four column groups
+    const int rp = tid & 7, g = tid >> 3;
     for (int64_t k = 0;; k++) {
         const int64_t t = blockIdx.x + k * gridDim.x;
         if (t >= ntiles) break;
         if (tid == 0) issue(k + kStagesT - 1);  // that stage was released at the end of round k-1
         const int s = (int)(k % kStagesT);
-        const bool ok = tc::mbar_wait(&full[s], (uint32_t)((k / kStagesT) & 1), &abort_flag);
+        // one warp waits for the tile; the others wait at the barrier (issuing
+        // nothing), which then orders the tile's shared memory for all of them
+        bool ok = true;
+        if (warp == 0) ok = tc::mbar_wait(&full[s], (uint32_t)((k / kStagesT) & 1), &abort_flag);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
@@ -258,27 +256,50 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint8_t *tile = tiles + (size_t)s * stage_bytes;
         const int64_t row0 = t * kTT;
         const int nrows = (int)((m - row0) < kTT ? (m - row0) : kTT);
-        // (1) row argmax: thread (r, g) scans columns g, g + kGroupsT, ... ascending
-        unsigned long long best = 0;
-        int bidx = -1;
-        if (r < nrows)
-            for (int kc = g; kc < p; kc += kGroupsT) {
-                const unsigned long long key = abs_key(tile_at(tile, kc, r));
-                nonfinite |= key >= kInfKey;
-                if (bidx < 0 || key > best) {
-                    best = key;
-                    bidx = kc;
-                }
+        // (1) row argmax, two rows per 16-byte load; columns ascend per thread,
+        // so a strict > keeps the lowest column on ties
+        unsigned long long b0 = 0, b1 = 0;
+        int i0 = -1, i1 = -1;
+        for (int kc = g; kc < p; kc += 32) {
+            const ulonglong2 v =
+                *reinterpret_cast<const ulonglong2 *>(tile + kc * 128 + (((rp ^ (kc & 7)) & 7) << 4));
+            const unsigned long long x = v.x & kAbsMask, y = v.y & kAbsMask;
+            if (i0 < 0 || x > b0) {
+                b0 = x;
+                i0 = kc;
             }
-        pkey[g][r] = best;
-        pidx[g][r] = bidx;
+            if (i1 < 0 || y > b1) {
+                b1 = y;
+                i1 = kc;
+            }
+        }
+        // the four column groups of this warp (lanes 8 apart), lowest column on ties
+#pragma unroll
+        for (int o = 8; o < 32; o <<= 1) {
+            const unsigned long long ob0 = __shfl_xor_sync(0xffffffffu, b0, o), ob1 = __shfl_xor_sync(0xffffffffu, b1, o);
+            const int oi0 = __shfl_xor_sync(0xffffffffu, i0, o), oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
+            if (oi0 >= 0 && (i0 < 0 || ob0 > b0 || (ob0 == b0 && oi0 < i0))) {
+                b0 = ob0;
+                i0 = oi0;
+            }
+            if (oi1 >= 0 && (i1 < 0 || ob1 > b1 || (ob1 == b1 && oi1 < i1))) {
+                b1 = ob1;
+                i1 = oi1;
+            }
+        }
+        if (lane < 8) {
+            pkey[warp][2 * rp] = b0;
+            pidx[warp][2 * rp] = i0;
+            pkey[warp][2 * rp + 1] = b1;
+            pidx[warp][2 * rp + 1] = i1;
+        }
         __syncthreads();
         if (tid < kTT) {
             unsigned long long b = 0;
             int bi = -1;
-            for (int gg = 0; gg < kGroupsT; gg++) {
-                const int ii = pidx[gg][tid];
-                const unsigned long long kk = pkey[gg][tid];
+            for (int ww = 0; ww < kThreads / 32; ww++) {
+                const int ii = pidx[ww][tid];
+                const unsigned long long kk = pkey[ww][tid];
                 if (ii < 0) continue;
                 if (bi < 0 || kk > b || (kk == b && ii < bi)) {
                     b = kk;
@@ -286,38 +307,36 @@ __global__ void __launch_bounds__(kThreads, 2)
                 }
             }
             rowJ[tid] = bi;
+            // an Inf or NaN anywhere in a row is its maximum key
+            if (tid < nrows && b >= kInfKey) nonfinite = true;
             if (J != nullptr && tid < nrows) J[row0 + tid] = bi;
             if (rowflags != nullptr && tid < nrows && bi >= 0) rowflags[bi] = 1;
         }
         __syncthreads();
-        // (2) merge the tile's rows into C: warp w takes rows w and w + 8, lanes
-        // walk k; every C key is loaded before any compare (the L2 round trips
-        // overlap), the atomic fires only on a new maximum
+        // (2) merge rows 2w, 2w+1 into C (warp w), lanes walk k with one 16-byte
+        // load per two entries; every C key is loaded before any compare (the
+        // L2 round trips overlap), the atomic fires only on a new maximum
         constexpr int KPL = kMaxP / 32;
-        constexpr int RPW = kTT / (kThreads / 32);
-        unsigned long long cur[RPW][KPL];
+        const int ra = 2 * warp, rb = ra + 1;
+        const bool va = ra < nrows, vb = rb < nrows;
+        const unsigned long long *ca = Ckeys + (int64_t)(va ? rowJ[ra] : 0) * p;
+        const unsigned long long *cb = Ckeys + (int64_t)(vb ? rowJ[rb] : 0) * p;
+        unsigned long long cura[KPL], curb[KPL];
 #pragma unroll
-        for (int q = 0; q < RPW; q++) {
-            const int rr = warp + q * (kThreads / 32);
-            const unsigned long long *crow = Ckeys + (int64_t)(rr < nrows ? rowJ[rr] : 0) * p;
-#pragma unroll
-            for (int u = 0; u < KPL; u++) {
-                const int kc = lane + 32 * u;
-                cur[q][u] = (rr < nrows && kc < p) ? __ldcg(crow + kc) : ~0ull;
-            }
+        for (int u = 0; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            cura[u] = (va && kc < p) ? __ldcg(ca + kc) : ~0ull;
+            curb[u] = (vb && kc < p) ? __ldcg(cb + kc) : ~0ull;
         }
 #pragma unroll
-        for (int q = 0; q < RPW; q++) {
-            const int rr = warp + q * (kThreads / 32);
-            if (rr >= nrows) continue;
-            unsigned long long *crow = Ckeys + (int64_t)rowJ[rr] * p;
-#pragma unroll
-            for (int u = 0; u < KPL; u++) {
-                const int kc = lane + 32 * u;
-                if (kc < p) {
-                    const unsigned long long key = abs_key(tile_at(tile, kc, rr));
-                    if (key > cur[q][u]) atomicMax(crow + kc, key);
-                }
+        for (int u = 0; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            if (kc < p) {
+                const ulonglong2 v =
+                    *reinterpret_cast<const ulonglong2 *>(tile + kc * 128 + (((warp ^ (kc & 7)) & 7) << 4));
+                const unsigned long long x = v.x & kAbsMask, y = v.y & kAbsMask;
+                if (x > cura[u]) atomicMax(const_cast<unsigned long long *>(ca) + kc, x);
+                if (y > curb[u]) atomicMax(const_cast<unsigned long long *>(cb) + kc, y);
             }
         }
         __syncthreads();  // this stage is refilled next round

@@ -238,12 +238,21 @@ __global__ void __launch_bounds__(kT1)
         for (int i = threadIdx.x; i < cnt; i += kT1) f(key[i]);
     };
     constexpr int kPer = kChunk / kT1;
+    // the next chunk's loads are issued before this chunk is processed, so one
+    // chunk is always in flight per thread
+    double vn[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        const int64_t r = r0 + q * kT1 + threadIdx.x;
+        vn[q] = (r < r1) ? __ldcs(col + r) : 0.0;
+    }
     for (int64_t base = r0; base < r1; base += kChunk) {
         double v[kPer];
 #pragma unroll
         for (int q = 0; q < kPer; q++) {
-            const int64_t r = base + q * kT1 + threadIdx.x;
-            v[q] = (r < r1) ? __ldcs(col + r) : 0.0;
+            v[q] = vn[q];
+            const int64_t r = base + kChunk + q * kT1 + threadIdx.x;
+            vn[q] = (r < r1) ? __ldcs(col + r) : 0.0;
         }
         unsigned long long kv[kPer];
 #pragma unroll
