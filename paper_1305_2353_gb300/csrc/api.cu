@@ -204,7 +204,7 @@ ctp_status ctp_compress_relaxed(ctp_ctx *ctx, int64_t m, int32_t p, const double
                                 size_t ws_bytes, void *stream) {
     if (ctx == nullptr || A21 == nullptr || C == nullptr || workspace == nullptr) return CTP_EINVAL;
     if (m < 0 || p < 1 || lda < (m > 0 ? m : 1)) return CTP_EINVAL;
-    if (p > kMaxP) return CTP_EUNSUPPORTED;
+    if (p > kMaxP || m > 0x7fffffffLL) return CTP_EUNSUPPORTED;  // rows are reported as int32
     ctp_options o = {0.01, 1e-20, CTP_PIV_RELAXED, CTP_FP64, CTP_S_NONE, 0};
     WsLayout L = ws_layout(m + p, p, &o, ctx->num_sms);
     if (ws_bytes < L.total) return CTP_ENOMEM;
@@ -233,7 +233,7 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
                         opt->smode == CTP_S_FP32_TILED;
     if (opt->smode != CTP_S_NONE && (S == nullptr || (!packed && lds < (m > 0 ? m : 1))))
         return CTP_EINVAL;
-    if (p > kMaxP) return CTP_EUNSUPPORTED;
+    if (p > kMaxP || n > 0x7fffffffLL) return CTP_EUNSUPPORTED;  // row indices are int32
     const bool tc = opt->prec != CTP_FP64 && opt->smode != CTP_S_NONE;
     if (opt->pivot == CTP_PIV_TPP && tc) return CTP_EUNSUPPORTED;
     if (tc && opt->smode != CTP_S_FP32 && opt->smode != CTP_S_FP32_PACKED &&
@@ -283,16 +283,16 @@ ctp_status ctp_factor_supernode(ctp_ctx *ctx, int64_t n, int32_t p, double *A, i
     fa.D = D;
     fa.Dinv = Dinv;
     fa.info = info;
-    fa.rowflags = nullptr;
+    fa.rowbits = nullptr;
     if (opt->pivot == CTP_PIV_STRICT) {
         unsigned long long *keys = (unsigned long long *)(ws + L.C);
-        int32_t *flags = (int32_t *)(ws + L.flags);
+        uint32_t *flags = (uint32_t *)(ws + L.flags);
         CTP_CUDA(cudaMemsetAsync(keys, 0, sizeof(double) * (size_t)p * p, st));
-        CTP_CUDA(cudaMemsetAsync(flags, 0, sizeof(int32_t) * (size_t)p, st));
+        CTP_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (size_t)((p + 31) / 32), st));
         CTP_CUDA(timed(ctx, K_COMPRESS_STRICT, st, [&] {
             return launch_compress_strict(A + p, m, p, lda, keys, nullptr, flags, info, ctx->num_sms, st);
         }));
-        fa.rowflags = flags;
+        fa.rowbits = flags;
         fa.R = p;
         fa.abs_update = 1;
         fa.C = (const double *)keys;  // non-negative keys are the doubles themselves

@@ -49,7 +49,7 @@ __global__ void k_batch_prepare(const BFront *__restrict__ tab, char *ws, BatchO
     if (o.pivot == CTP_PIV_STRICT) {
         unsigned long long *keys = reinterpret_cast<unsigned long long *>(base + sec.C);
         for (int i = threadIdx.x; i < bt.p * bt.p; i += blockDim.x) keys[i] = 0;
-        int32_t *nz = reinterpret_cast<int32_t *>(base + sec.nz);
+        int32_t *nz = reinterpret_cast<int32_t *>(base + sec.nz);  // covers the ceil(p/32) words of bits
         for (int i = threadIdx.x; i < bt.p; i += blockDim.x) nz[i] = 0;
     }
 }
@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ unsigned long long pkey[kThreads];
     __shared__ int pidx[kThreads];
     __shared__ int rowJ[kTR];
+    __shared__ unsigned rbits[kMaxP / 32];  // rows of C that receive a row of this tile
+    if (threadIdx.x < kMaxP / 32) rbits[threadIdx.x] = 0u;
     const int f = item_front[blockIdx.x];
     const BFront bt = tab[f];
     const ctp_front fr = fronts[f];
@@ -115,9 +117,11 @@ __global__ void __launch_bounds__(kThreads)
         }
         rowJ[threadIdx.x] = bi;
         // row bi of C has a member: the pivot search keeps only such rows
-        if (threadIdx.x < nrows && bi >= 0) reinterpret_cast<int32_t *>(base + sec.nz)[bi] = 1;
+        if (threadIdx.x < nrows && bi >= 0) atomicOr(&rbits[bi >> 5], 1u << (bi & 31));
     }
     __syncthreads();
+    if (threadIdx.x < (p + 31) / 32 && rbits[threadIdx.x] != 0u)
+        atomicOr(reinterpret_cast<uint32_t *>(base + sec.nz) + threadIdx.x, rbits[threadIdx.x]);
     for (int rr = warp; rr < nrows; rr += kThreads / 32) {
         unsigned long long *crow = Ckeys + (int64_t)rowJ[rr] * p;
         for (int k = lane; k < p; k += 32) {

@@ -55,7 +55,7 @@ __device__ __forceinline__ void load_tile(const double *__restrict__ A21, int64_
 __global__ void __launch_bounds__(kThreads)
     k_compress_strict(const double *__restrict__ A21, int64_t m, int p, int64_t lda,
                       unsigned long long *__restrict__ Ckeys, int32_t *__restrict__ J,
-                      int32_t *__restrict__ rowflags,
+                      uint32_t *__restrict__ rowbits,
                       int32_t *__restrict__ info) {
     extern __shared__ __align__(16) double smem[];
     const int tile_elems = p * (kTR + 1);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads)
             if (J != nullptr && threadIdx.x < nrows) J[row0 + threadIdx.x] = bi;
             // row bi of C has a member (J_bi is not empty): the pivot search
             // keeps only such rows
-            if (rowflags != nullptr && threadIdx.x < nrows && bi >= 0) rowflags[bi] = 1;
+            if (rowbits != nullptr && threadIdx.x < nrows && bi >= 0) atomicOr(rowbits + (bi >> 5), 1u << (bi & 31));
         }
         __syncthreads();
 
@@ -193,134 +193,155 @@ __global__ void __launch_bounds__(256)
     if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
 }
 
-// The same compression with the tiles brought in by TMA: one
-// cp.async.bulk.tensor per tile of 16 rows x p columns (16 rows of a column are
-// the 128 bytes of one swizzle span), three stages per CTA, two CTAs per SM.  With the 128-byte swizzle, the 16-byte chunk c of column k sits at
-// chunk c ^ (k mod 8) of its 128-byte row, so both the row-per-lane reads of
-// the argmax and the column-per-lane reads of the merge into C meet few bank
-// conflicts.  Each tile costs one instruction to load instead of one per
-// element, which is what kept the per-element kernel above at a quarter of HBM.
-constexpr int kTT = 16;         // rows per TMA tile
-constexpr int kStagesT = 3;     // tiles per CTA: one in use, two in flight
-__global__ void __launch_bounds__(kThreads, 2)
+// The same compression with the tiles brought in by TMA, one cp.async.bulk.tensor
+// per tile of 16 rows x p columns (16 rows of a column are the 128 bytes of one
+// swizzle span), and no CTA-wide barrier in the loop: warp w (of 8) owns rows
+// 2w and 2w+1 of every tile.  It reads them in one 16-byte load per column
+// (with the 128-byte swizzle, the chunk of rows 2c, 2c+1 of column k sits at
+// chunk c ^ (k mod 8) of its span, so a warp's 32 columns spread over all
+// banks), releases the stage as soon as the values are in registers, finds the
+// two row maxima with warp reductions on the 32-bit halves of the keys, and
+// merges the rows into C.  A ninth warp only issues the copies: a stage is
+// refilled once all eight warps have released it (an mbarrier per stage each
+// way), so the warps drift apart by up to three tiles instead of meeting at
+// every barrier.
+constexpr int kTT = 16;                           // rows per TMA tile
+constexpr int kStagesT = 3;                       // tiles in flight per CTA
+constexpr int kConsWarps = kTT / 2;               // two rows per consumer warp
+constexpr int kThreadsT = 32 * (kConsWarps + 1);  // + the producer warp
+
+// Lowest index among the lanes' (key, index) pairs with the largest key
+// (keys compared as unsigned 64-bit integers by their 32-bit halves).
+__device__ __forceinline__ int warp_argmax(unsigned long long key, int idx, unsigned &hi_out) {
+    const unsigned h = (unsigned)(key >> 32), l = (unsigned)key;
+    const unsigned H = __reduce_max_sync(0xffffffffu, h);
+    const unsigned L = __reduce_max_sync(0xffffffffu, h == H ? l : 0u);
+    hi_out = H;
+    return __reduce_min_sync(0xffffffffu, (h == H && l == L) ? idx : 0x7fffffff);
+}
+
+__global__ void __launch_bounds__(kThreadsT, 2)
     k_compress_strict_tma(const __grid_constant__ CUtensorMap map, int64_t m, int p, uint32_t stage_bytes,
                           unsigned long long *__restrict__ Ckeys, int32_t *__restrict__ J,
-                          int32_t *__restrict__ rowflags, int32_t *__restrict__ info) {
+                          uint32_t *__restrict__ rowbits, int32_t *__restrict__ info) {
     extern __shared__ unsigned char smraw[];
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    __shared__ unsigned long long full[kStagesT];
-    __shared__ unsigned long long pkey[kThreads / 32][kTT];  // per warp: best key of each row
-    __shared__ int pidx[kThreads / 32][kTT];
-    __shared__ int rowJ[kTT];
+    __shared__ unsigned long long full[kStagesT], empty[kStagesT];
+    __shared__ unsigned seen[kMaxP / 32];  // rows of C that received a row of this CTA
     __shared__ int abort_flag;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = (m + kTT - 1) / kTT;
-    if (tid == 0) {
-        for (int s = 0; s < kStagesT; s++) tc::mbar_init(&full[s], 1);
+    if (threadIdx.x < kMaxP / 32) seen[threadIdx.x] = 0;
+    // this CTA's tiles are blockIdx.x + k * gridDim.x, k < nk
+    const int64_t nk = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStagesT; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], kConsWarps);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](int64_t k) {  // the k-th tile of this CTA into its stage
-        const int64_t t = blockIdx.x + k * gridDim.x;
-        if (t >= ntiles) return;
-        const int s = (int)(k % kStagesT);
-        tc::mbar_expect_tx(&full[s], (uint32_t)(kTT * 8 * p));  // the box: 16 rows x p columns
-        tc::tma_load_2d(tiles + (size_t)s * stage_bytes, &map, (int)(t * kTT), 0, &full[s]);
-    };
-    if (tid == 0)
-        for (int k = 0; k < kStagesT - 1; k++) issue(k);
-    bool nonfinite = false;
-    // phase 1 mapping: thread (rp, g) takes rows 2rp, 2rp+1 (one 16-byte chunk)
-    // of columns g, g + 32, ...; a warp covers four column groups
-    const int rp = tid & 7, g = tid >> 3;
-    for (int64_t k = 0;; k++) {
-        const int64_t t = blockIdx.x + k * gridDim.x;
-        if (t >= ntiles) break;
-        if (tid == 0) issue(k + kStagesT - 1);  // that stage was released at the end of round k-1
-        const int s = (int)(k % kStagesT);
-        // one warp waits for the tile; the others wait at the barrier (issuing
-        // nothing), which then orders the tile's shared memory for all of them
-        bool ok = true;
-        if (warp == 0) ok = tc::mbar_wait(&full[s], (uint32_t)((k / kStagesT) & 1), &abort_flag);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
+    if (warp == kConsWarps) {
+        // ---- producer: tile k goes to stage k mod S once tile k - S has been released
+        if (lane == 0) {
+            int64_t issued = 0;
+            bool ok = true;
+            for (int64_t k = 0; k < nk; k++) {
+                const int s = (int)(k % kStagesT);
+                if (k >= kStagesT && !tc::mbar_wait(&empty[s], (uint32_t)((k / kStagesT - 1) & 1), &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const int64_t t = blockIdx.x + k * gridDim.x;
+                tc::mbar_expect_tx(&full[s], (uint32_t)(kTT * 8 * p));  // the box: 16 rows x p columns
+                tc::tma_load_2d(tiles + (size_t)s * stage_bytes, &map, (int)(t * kTT), 0, &full[s]);
+                issued = k + 1;
+            }
+            if (!ok) {
+                atomicExch(&abort_flag, 1);
                 atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
-                // wait (bounded) for the copies still in flight into this CTA's stages
-                for (int64_t k2 = k + 1; k2 < k + kStagesT; k2++)
-                    if (blockIdx.x + k2 * gridDim.x < ntiles)
-                        tc::mbar_wait(&full[k2 % kStagesT], (uint32_t)((k2 / kStagesT) & 1), &abort_flag);
+                // the CTA's shared memory must outlive every copy into it: wait
+                // (bounded, whatever the abort flag says) for the last ones issued
+                int never = 0;
+                for (int64_t k = issued > kStagesT ? issued - kStagesT : 0; k < issued; k++)
+                    tc::mbar_wait(&full[k % kStagesT], (uint32_t)((k / kStagesT) & 1), &never);
+            }
+        }
+        return;
+    }
+    // ---- consumers
+    constexpr int KPL = kMaxP / 32;  // columns per lane
+    bool nonfinite = false;
+    const int ra = 2 * warp, rb = ra + 1;
+    const int chunk = warp << 4;  // byte offset of rows ra, rb in an unswizzled span
+    for (int64_t k = 0; k < nk; k++) {
+        const int s = (int)(k % kStagesT);
+        if (!tc::mbar_wait(&full[s], (uint32_t)((k / kStagesT) & 1), &abort_flag)) {
+            if (lane == 0) {
+                atomicExch(&abort_flag, 1);
+                atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
             }
             break;
         }
         const uint8_t *tile = tiles + (size_t)s * stage_bytes;
-        const int64_t row0 = t * kTT;
-        const int nrows = (int)((m - row0) < kTT ? (m - row0) : kTT);
-        // (1) row argmax, two rows per 16-byte load; columns ascend per thread,
-        // so a strict > keeps the lowest column on ties
-        unsigned long long b0 = 0, b1 = 0;
-        int i0 = -1, i1 = -1;
-        for (int kc = g; kc < p; kc += 32) {
-            const ulonglong2 v =
-                *reinterpret_cast<const ulonglong2 *>(tile + kc * 128 + (((rp ^ (kc & 7)) & 7) << 4));
-            const unsigned long long x = v.x & kAbsMask, y = v.y & kAbsMask;
-            if (i0 < 0 || x > b0) {
-                b0 = x;
-                i0 = kc;
-            }
-            if (i1 < 0 || y > b1) {
-                b1 = y;
-                i1 = kc;
-            }
-        }
-        // the four column groups of this warp (lanes 8 apart), lowest column on ties
+        unsigned long long xa[KPL], xb[KPL];
 #pragma unroll
-        for (int o = 8; o < 32; o <<= 1) {
-            const unsigned long long ob0 = __shfl_xor_sync(0xffffffffu, b0, o), ob1 = __shfl_xor_sync(0xffffffffu, b1, o);
-            const int oi0 = __shfl_xor_sync(0xffffffffu, i0, o), oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
-            if (oi0 >= 0 && (i0 < 0 || ob0 > b0 || (ob0 == b0 && oi0 < i0))) {
-                b0 = ob0;
-                i0 = oi0;
-            }
-            if (oi1 >= 0 && (i1 < 0 || ob1 > b1 || (ob1 == b1 && oi1 < i1))) {
-                b1 = ob1;
-                i1 = oi1;
+        for (int u = 0; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            xa[u] = xb[u] = 0;
+            if (kc < p) {
+                const ulonglong2 v =
+                    *reinterpret_cast<const ulonglong2 *>(tile + kc * 128 + (chunk ^ ((kc & 7) << 4)));
+                xa[u] = v.x & kAbsMask;
+                xb[u] = v.y & kAbsMask;
             }
         }
-        if (lane < 8) {
-            pkey[warp][2 * rp] = b0;
-            pidx[warp][2 * rp] = i0;
-            pkey[warp][2 * rp + 1] = b1;
-            pidx[warp][2 * rp + 1] = i1;
-        }
-        __syncthreads();
-        if (tid < kTT) {
-            unsigned long long b = 0;
-            int bi = -1;
-            for (int ww = 0; ww < kThreads / 32; ww++) {
-                const int ii = pidx[ww][tid];
-                const unsigned long long kk = pkey[ww][tid];
-                if (ii < 0) continue;
-                if (bi < 0 || kk > b || (kk == b && ii < bi)) {
-                    b = kk;
-                    bi = ii;
+        // per lane: the largest key of its columns (ascending, so the lowest
+        // column wins ties); lanes without a column offer none
+        unsigned long long ba = xa[0], bb = xb[0];
+        int ia = lane < p ? lane : 0x7fffffff, ib = ia;
+#pragma unroll
+        for (int u = 1; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            if (kc < p) {
+                if (xa[u] > ba) {
+                    ba = xa[u];
+                    ia = kc;
+                }
+                if (xb[u] > bb) {
+                    bb = xb[u];
+                    ib = kc;
                 }
             }
-            rowJ[tid] = bi;
-            // an Inf or NaN anywhere in a row is its maximum key
-            if (tid < nrows && b >= kInfKey) nonfinite = true;
-            if (J != nullptr && tid < nrows) J[row0 + tid] = bi;
-            if (rowflags != nullptr && tid < nrows && bi >= 0) rowflags[bi] = 1;
         }
-        __syncthreads();
-        // (2) merge rows 2w, 2w+1 into C (warp w), lanes walk k with one 16-byte
-        // load per two entries; every C key is loaded before any compare (the
-        // L2 round trips overlap), the atomic fires only on a new maximum
-        constexpr int KPL = kMaxP / 32;
-        const int ra = 2 * warp, rb = ra + 1;
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[s]);  // the rows are in registers
+        unsigned ha, hb;
+        const int Ia = warp_argmax(ba, ia, ha), Ib = warp_argmax(bb, ib, hb);
+        const int64_t t = blockIdx.x + k * gridDim.x, row0 = t * kTT;
+        const int nrows = (int)((m - row0) < kTT ? (m - row0) : kTT);
         const bool va = ra < nrows, vb = rb < nrows;
-        const unsigned long long *ca = Ckeys + (int64_t)(va ? rowJ[ra] : 0) * p;
-        const unsigned long long *cb = Ckeys + (int64_t)(vb ? rowJ[rb] : 0) * p;
+        // an Inf or NaN anywhere in a row is its maximum key
+        nonfinite |= (va && ha >= 0x7FF00000u) || (vb && hb >= 0x7FF00000u);
+        if (lane == 0) {
+            // row Ia of C has a member: the CTA gathers these bits in shared
+            // memory and publishes them once at the end (a global store per row
+            // would queue ~m stores on the one or two L2 lines of the bits)
+            if (va) {
+                if (J != nullptr) J[row0 + ra] = Ia;
+                atomicOr(&seen[Ia >> 5], 1u << (Ia & 31));
+            }
+            if (vb) {
+                if (J != nullptr) J[row0 + rb] = Ib;
+                atomicOr(&seen[Ib >> 5], 1u << (Ib & 31));
+            }
+        }
+        // merge into rows Ia, Ib of C: every C key is loaded before any compare
+        // (the L2 round trips overlap); the atomic fires only on a new maximum
+        unsigned long long *ca = Ckeys + (int64_t)(va ? Ia : 0) * p;
+        unsigned long long *cb = Ckeys + (int64_t)(vb ? Ib : 0) * p;
         unsigned long long cura[KPL], curb[KPL];
 #pragma unroll
         for (int u = 0; u < KPL; u++) {
@@ -331,17 +352,16 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int u = 0; u < KPL; u++) {
             const int kc = lane + 32 * u;
-            if (kc < p) {
-                const ulonglong2 v =
-                    *reinterpret_cast<const ulonglong2 *>(tile + kc * 128 + (((warp ^ (kc & 7)) & 7) << 4));
-                const unsigned long long x = v.x & kAbsMask, y = v.y & kAbsMask;
-                if (x > cura[u]) atomicMax(const_cast<unsigned long long *>(ca) + kc, x);
-                if (y > curb[u]) atomicMax(const_cast<unsigned long long *>(cb) + kc, y);
-            }
+            if (xa[u] > cura[u]) atomicMax(ca + kc, xa[u]);
+            if (xb[u] > curb[u]) atomicMax(cb + kc, xb[u]);
         }
-        __syncthreads();  // this stage is refilled next round
     }
     if (nonfinite) atomicCAS(info, kInfoOk, (int32_t)CTP_ENONFINITE);
+    // every consumer warp is past its last tile (named barrier 1: the producer
+    // warp has left)
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsWarps) : "memory");
+    if (rowbits != nullptr && threadIdx.x < (p + 31) / 32 && seen[threadIdx.x] != 0u)
+        atomicOr(rowbits + threadIdx.x, seen[threadIdx.x]);
 }
 
 __global__ void k_keys_to_rowmajor(const unsigned long long *__restrict__ Ckeys,
@@ -376,7 +396,7 @@ static bool make_map_a21(CUtensorMap *map, const double *A21, int64_t m, int p, 
 }
 
 cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
-                                   unsigned long long *Ckeys, int32_t *J, int32_t *rowflags, int32_t *info,
+                                   unsigned long long *Ckeys, int32_t *J, uint32_t *rowbits, int32_t *info,
                                    int num_sms, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     CUtensorMap map;
@@ -386,14 +406,14 @@ cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t 
         cudaError_t err = smem_at_least((const void *)k_compress_strict_tma, smem);
         if (err != cudaSuccess) return err;
         int per_sm = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress_strict_tma, kThreads, smem);
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress_strict_tma, kThreadsT, smem);
         if (err != cudaSuccess) return err;
         if (per_sm < 1) per_sm = 1;
         const int64_t ntiles = (m + kTT - 1) / kTT;
         int64_t grid = (int64_t)num_sms * per_sm;
         if (grid > ntiles) grid = ntiles;
-        k_compress_strict_tma<<<(unsigned)grid, kThreads, smem, st>>>(map, m, p, stage_bytes, Ckeys, J, rowflags,
-                                                                      info);
+        k_compress_strict_tma<<<(unsigned)grid, kThreadsT, smem, st>>>(map, m, p, stage_bytes, Ckeys, J, rowbits,
+                                                                       info);
         return cudaGetLastError();
     }
     size_t smem = strict_smem(p);
@@ -406,7 +426,7 @@ cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t 
     int64_t ntiles = (m + kTR - 1) / kTR;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > ntiles) grid = ntiles;
-    k_compress_strict<<<(unsigned)grid, kThreads, smem, st>>>(A21, m, p, lda, Ckeys, J, rowflags, info);
+    k_compress_strict<<<(unsigned)grid, kThreads, smem, st>>>(A21, m, p, lda, Ckeys, J, rowbits, info);
     return cudaGetLastError();
 }
 

@@ -52,15 +52,15 @@ constexpr int kFactorWarp = 0, kFactorCta = 1, kFactorCluster = 2;
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns cudaError_t of the launch)
-// rowflags (optional, p int32 cleared by the caller): set to 1 for every row of
-// C that receives an A21 row (the rows the pivot search must keep)
+// rowbits (optional, ceil(p/32) words cleared by the caller): bit j set for
+// every row j of C that receives an A21 row (the rows the pivot search must keep)
 cudaError_t launch_compress_strict(const double *A21, int64_t m, int p, int64_t lda,
-                                   unsigned long long *Ckeys, int32_t *J, int32_t *rowflags, int32_t *info,
+                                   unsigned long long *Ckeys, int32_t *J, uint32_t *rowbits, int32_t *info,
                                    int num_sms, cudaStream_t st);
 // single-row compression: ckey[k] (p keys, zeroed by the caller) = max_i |a21(i,k)|
 cudaError_t launch_compress_single_row(const double *A21, int64_t m, int p, int64_t lda,
                                        unsigned long long *ckey, int32_t *info, int num_sms, cudaStream_t st);
-int relaxed_segments(int64_t m, int p, int num_sms);
+int relaxed_block_lg(int64_t m, int p);
 size_t relaxed_aux_bytes(int64_t m, int p, int num_sms);
 cudaError_t launch_compress_relaxed(const double *A21, int64_t m, int p, int64_t lda, double *C,
                                     int32_t *rows, void *aux, int32_t *info, int num_sms,
@@ -75,7 +75,7 @@ struct FactorArgs {
     int R;              // outer rows held on chip: p (compressed) or 0 (restricted)
     int abs_update;     // 1: strict worst-case update of the outer rows
     const double *C;    // R x p row-major outer rows (doubles), or nullptr
-    const int32_t *rowflags;  // R flags: nonzero for rows of C that may be nonzero (nullptr: scan C)
+    const uint32_t *rowbits;  // R bits: set for rows of C that may be nonzero (nullptr: scan C)
     double u, small;
     int32_t *perm, *piv, *nelim;
     double *D, *Dinv;
@@ -114,7 +114,7 @@ __host__ __device__ inline BSection bsection(int64_t n, int p, const ctp_options
     off += align256hd(sizeof(double) * (2 * (size_t)p + 2));
     s.W21 = off;
     off += align256hd((opt->smode != CTP_S_NONE && opt->prec == CTP_FP64) ? sizeof(double) * (size_t)(n - p) * p : 0);
-    s.nz = off;  // strict: which rows of C receive an A21 row
+    s.nz = off;  // strict: which rows of C receive an A21 row (one bit per row)
     off += align256hd(opt->pivot == CTP_PIV_STRICT ? sizeof(int32_t) * (size_t)p : 0);
     s.total = off;
     return s;

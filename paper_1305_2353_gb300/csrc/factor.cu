@@ -306,8 +306,8 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
     // scan is needed.  Otherwise a row whose first entry is nonzero is nonzero
     // (almost every row of a front with many A21 rows); only the others are
     // scanned in full, all of them together over (row, column) pairs.
-    if (a.rowflags != nullptr) {
-        for (int j = tid; j < a.R; j += kT) sh.nzflag[j] = a.rowflags[j] != 0 ? 1 : 0;
+    if (a.rowbits != nullptr) {
+        for (int j = tid; j < a.R; j += kT) sh.nzflag[j] = (a.rowbits[j >> 5] >> (j & 31)) & 1u;
         if (tid == 0) sh.nz_count = 0;
     } else if (warp == 0) {
         int r = 0;
@@ -684,7 +684,7 @@ __device__ __forceinline__ FactorArgs batch_args(const ctp_front *__restrict__ f
     a.D = fr.D;
     a.Dinv = reinterpret_cast<double *>(base + sec.Dinv);
     a.info = reinterpret_cast<int32_t *>(base + sec.info);
-    a.rowflags = o.pivot == CTP_PIV_STRICT ? reinterpret_cast<const int32_t *>(base + sec.nz) : nullptr;
+    a.rowbits = o.pivot == CTP_PIV_STRICT ? reinterpret_cast<const uint32_t *>(base + sec.nz) : nullptr;
     return a;
 }
 
@@ -719,8 +719,8 @@ __global__ void __launch_bounds__(32 * kWarpFronts)
     // holds the C row of outer row k
     bool nz = false;
     if (lane < a.R) {
-        if (a.rowflags != nullptr) {
-            nz = a.rowflags[lane] != 0;
+        if (a.rowbits != nullptr) {
+            nz = (a.rowbits[0] >> lane) & 1u;
         } else {
             for (int k = 0; k < p && !nz; k++) nz = nonzero_bits(a.C[(int64_t)lane * p + k]);
         }

@@ -163,6 +163,51 @@ def test_compress_relaxed_bit_exact(ctx, m, p):
     assert np.array_equal(C.cpu().numpy().reshape(p, p), Cref)
 
 
+def _relaxed_input(kind, m, p, rng):
+    A21 = rng.standard_normal((m, p))
+    if kind == "levels":          # a handful of values: ties everywhere
+        A21 = rng.integers(-3, 4, size=(m, p)).astype(float)
+    elif kind == "constant":      # every entry of a column ties
+        A21 = np.ones((m, p))
+        A21[::3] *= -1.0
+    elif kind.startswith("front_heavy"):
+        # the leading rows are 100x larger: the blocks that hold column maxima
+        # are full of candidates (more than one CTA's buffer in the second case)
+        lead = 2000 if kind == "front_heavy" else 6000
+        A21[:lead] *= 100.0
+    return A21
+
+
+@pytest.mark.parametrize("kind,m,p", [("random", 10000, 256), ("random", 300, 64), ("random", 50, 64),
+                                      ("random", 4097, 256), ("levels", 5000, 64), ("constant", 9000, 40),
+                                      ("front_heavy", 60000, 256), ("front_heavy_overflow", 60000, 256)])
+def test_compress_relaxed_candidate_paths(ctx, kind, m, p):
+    """Relaxed compression through block maxima of 1 to 64 rows (the block
+    size follows m / p), candidate blocks read again, and the streaming
+    fallback when ties or crowded blocks overflow the candidate buffer: C and
+    the chosen rows bit-exact with the oracle."""
+    from paper_1305_2353_gb300 import ctp
+    A21 = _relaxed_input(kind, m, p, np.random.default_rng(m + p))
+    Cref, rref = O.compress_relaxed(A21)
+    C = torch.empty(p * p, dtype=torch.float64, device="cuda")
+    rows = torch.empty(p, dtype=torch.int32, device="cuda")
+    ws = ctx.compress_relaxed(ctp.colmajor(A21), m, p, m, C, rows)
+    torch.cuda.synchronize()
+    assert ctx.read_info(ws) == 0
+    assert np.array_equal(rows.cpu().numpy(), rref)
+    assert np.array_equal(C.cpu().numpy().reshape(p, p), Cref)
+
+
+def test_compress_relaxed_flags_nonfinite(ctx):
+    from paper_1305_2353_gb300 import ctp
+    A21 = np.random.default_rng(3).standard_normal((700, 8))
+    A21[613, 5] = -np.inf
+    C = torch.empty(64, dtype=torch.float64, device="cuda")
+    rows = torch.empty(8, dtype=torch.int32, device="cuda")
+    ws = ctx.compress_relaxed(ctp.colmajor(A21), 700, 8, 700, C, rows)
+    assert ctx.read_info(ws) == ctp.CTP_ENONFINITE
+
+
 # --------------------------------------------------------------------------- full path
 
 def _tough(n, p, seed):
