@@ -201,6 +201,75 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
     return true;
 }
 
+// Store 64 consecutive columns j0..j0+63 of row i of S (FP32 values in r) in
+// the layout of S: 0 full column-major (lds), 1 lower-packed by columns, 2 in
+// 128 x 128 blocks (this row's block row bi, block column bj, from column boffc
+// of the block on; quarter q and lane name the row inside the block), 3
+// subtracted from a full column-major FP64 matrix (lds).  Entries above the
+// diagonal or below row m are skipped unless `interior` says there are none.
+__device__ __forceinline__ void store64(const uint32_t (&r)[64], int layout, float *S, int64_t m, int64_t lds,
+                                        int64_t nb, int64_t i, int64_t j0, bool interior, int64_t bi, int64_t bj,
+                                        int boffc, int q, int lane) {
+    if (layout == 3) {
+        // subtract into a full column-major FP64 matrix (lower
+        // triangle): 16 old values loaded before any is stored, so
+        // that the loads are in flight together
+        double *dp = reinterpret_cast<double *>(S) + j0 * lds + i;
+#pragma unroll
+        for (int h = 0; h < 64; h += 16) {
+            double old[16];
+#pragma unroll
+            for (int xx = 0; xx < 16; xx++) {
+                old[xx] = 0.0;
+                if (interior || (i < m && j0 + h + xx <= i)) old[xx] = dp[(int64_t)(h + xx) * lds];
+            }
+#pragma unroll
+            for (int xx = 0; xx < 16; xx++)
+                if (interior || (i < m && j0 + h + xx <= i))
+                    dp[(int64_t)(h + xx) * lds] = old[xx] - (double)__uint_as_float(r[h + xx]);
+        }
+        return;
+    }
+    if (layout == 2) {
+        // whole blocks, front to back: column c of the block is the
+        // 512 bytes written by the four lane quarters
+        float *blk = S + (int64_t)16384 * (bj * nb - bj * (bj - 1) / 2 + (bi - bj));
+        float *ptr = blk + (int64_t)boffc * 128 + q * 32 + lane;
+#pragma unroll
+        for (int xx = 0; xx < 64; xx++) __stcs(ptr + xx * 128, __uint_as_float(r[xx]));
+        return;
+    }
+    // S(i, j) lives at S + col(j) + i, with col(j) = j*lds (full) or
+    // j*m - j(j+1)/2 (packed; consecutive columns are m-1-j apart)
+    const bool packed = layout == 1;
+    float *ptr = S + (packed ? j0 * m - j0 * (j0 + 1) / 2 : j0 * lds) + i;
+    if (interior) {
+        if (packed) {
+            int d = (int)(m - 1 - j0);
+#pragma unroll
+            for (int xx = 0; xx < 64; xx++) {
+                __stcs(ptr, __uint_as_float(r[xx]));
+                ptr += d;
+                --d;
+            }
+        } else {
+#pragma unroll
+            for (int xx = 0; xx < 64; xx++) {
+                __stcs(ptr, __uint_as_float(r[xx]));
+                ptr += lds;
+            }
+        }
+    } else {
+        int64_t j = j0;
+#pragma unroll
+        for (int xx = 0; xx < 64; xx++) {
+            if (i < m && j <= i) __stcs(ptr, __uint_as_float(r[xx]));
+            ptr += packed ? (m - 1 - j) : lds;
+            ++j;
+        }
+    }
+}
+
 // Maps: pieces 1..3 of W21 (mW1..3) and of L21 (mL1..3); pieces beyond P unused.
 template <bool kBatch, int P>
 __global__ void __launch_bounds__(kThreadsTC, 1)
@@ -443,64 +512,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     for (int xx = 0; xx < 64; xx++) r[xx] = 0u;
                 }
                 const int64_t j0 = jbase + c * 32;
-                if (layout == 3) {
-                    // subtract into a full column-major FP64 matrix (lower
-                    // triangle): 16 old values loaded before any is stored, so
-                    // that the loads are in flight together
-                    double *dp = reinterpret_cast<double *>(S) + j0 * lds + i;
-#pragma unroll
-                    for (int h = 0; h < 64; h += 16) {
-                        double old[16];
-#pragma unroll
-                        for (int xx = 0; xx < 16; xx++) {
-                            old[xx] = 0.0;
-                            if (interior || (i < m && j0 + h + xx <= i)) old[xx] = dp[(int64_t)(h + xx) * lds];
-                        }
-#pragma unroll
-                        for (int xx = 0; xx < 16; xx++)
-                            if (interior || (i < m && j0 + h + xx <= i))
-                                dp[(int64_t)(h + xx) * lds] = old[xx] - (double)__uint_as_float(r[h + xx]);
-                    }
-                    continue;
-                }
-                if (tiled) {
-                    // whole blocks, front to back: column c of the block is the
-                    // 512 bytes written by the four lane quarters
-                    float *blk = S + (int64_t)16384 * (bj * nb - bj * (bj - 1) / 2 + (ti - bj));
-                    float *ptr = blk + (int64_t)(boff + c * 32) * 128 + q * 32 + lane;
-#pragma unroll
-                    for (int xx = 0; xx < 64; xx++) ptr[xx * 128] = __uint_as_float(r[xx]);
-                    continue;
-                }
-                // S(i, j) lives at S + col(j) + i, with col(j) = j*lds (full) or
-                // j*m - j(j+1)/2 (packed; consecutive columns are m-1-j apart)
-                const bool packed = layout == 1;
-                float *ptr = S + (packed ? j0 * m - j0 * (j0 + 1) / 2 : j0 * lds) + i;
-                if (interior) {
-                    if (packed) {
-                        int d = (int)(m - 1 - j0);
-#pragma unroll
-                        for (int xx = 0; xx < 64; xx++) {
-                            *ptr = __uint_as_float(r[xx]);
-                            ptr += d;
-                            --d;
-                        }
-                    } else {
-#pragma unroll
-                        for (int xx = 0; xx < 64; xx++) {
-                            *ptr = __uint_as_float(r[xx]);
-                            ptr += lds;
-                        }
-                    }
-                } else {
-                    int64_t j = j0;
-#pragma unroll
-                    for (int xx = 0; xx < 64; xx++) {
-                        if (i < m && j <= i) *ptr = __uint_as_float(r[xx]);
-                        ptr += packed ? (m - 1 - j) : lds;
-                        ++j;
-                    }
-                }
+                store64(r, layout, S, m, lds, nb, i, j0, interior, ti, bj, boff + c * 32, q, lane);
             }
         next_tile_half:
             tc_fence_before();
@@ -518,6 +530,302 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, C::TmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Split BF16 with two pieces (hi, lo) on pairs of SMs (cta_group::2): each
+// pair computes 256 x 256 tiles of S.  CTA r of the pair holds the W21 rows
+// and the L21 rows (the A and the B half of the MMA) of its 128 rows and its
+// 128 of the tile's 256 columns; one thread of CTA 0 issues M=256, N=256,
+// K=16 MMAs, hi*hi, hi*lo and lo*hi into one accumulator, and each CTA's
+// tensor memory receives its 128 rows of the tile.  Against the one-SM kernel
+// every SM reads half of B per product and the W21 tile it streams serves 256
+// columns instead of 128, so the operands' shared-memory and L2 traffic per
+// product halves.
+// Protocol: CTA 1's copies complete on its own barriers and a relay thread
+// (warp 1 of CTA 1) passes each completion on to CTA 0's barrier (2 arrivals);
+// MMA completions are multicast to both CTAs' barriers; CTA 1's epilogue warps
+// arrive on CTA 0's accumulator barriers remotely.  Every wait is bounded; a
+// timeout raises the abort flag of both CTAs.
+struct PairBars {
+    unsigned long long full[Cfg<2>::Stages], empty[Cfg<2>::Stages], acc_full[2], acc_empty[2], bfull, bempty, drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
+    k_form_tc_pair(const __grid_constant__ CUtensorMap mW1, const __grid_constant__ CUtensorMap mL1,
+                   const __grid_constant__ CUtensorMap mW2, const __grid_constant__ CUtensorMap mL2, int64_t m,
+                   const int32_t *__restrict__ nelim_p, float *__restrict__ S, int64_t lds, int layout,
+                   int32_t *__restrict__ info, int sched_mode) {
+    using C = Cfg<2>;
+    constexpr int NS = C::Stages;
+    constexpr uint32_t kAccCols = 256;
+    const CUtensorMap *mapW[2] = {&mW1, &mW2};
+    const CUtensorMap *mapL[2] = {&mL1, &mL2};
+    extern __shared__ unsigned char smraw[];
+    __shared__ PairBars bars;
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sB = smem;                     // [kMaxKB][StageB]: this CTA's 128 L21 rows, hi and lo
+    uint8_t *sA = smem + C::ResidentBytes;  // [NS][StageA]: this CTA's 128 W21 rows, hi and lo
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int KB1 = (*nelim_p + kBK - 1) / kBK;
+    const int nM2 = (int)((m + 255) / 256);  // 256-row blocks
+    const int64_t nb128 = (m + kBM - 1) / kBM;
+    Sched sc;
+    sc.mode = sched_mode;
+    sc.nM = nM2;
+    sc.nN = nM2;
+    sc.ntiles = tile_count(nM2, 1);
+    sc.G = gridDim.x >> 1;
+    sc.c = blockIdx.x >> 1;
+    sc.t0 = sc.ntiles * sc.c / sc.G;
+    sc.t1 = sc.ntiles * (sc.c + 1) / sc.G;
+    const BatchTab none = {nullptr, nullptr, nullptr, 0};
+#define TILE_P(k, x) tile_k<false, 1>((k), sc, KB1, m, S, lds, layout, none, (x))
+    auto raise_abort = [&]() {
+        atomicExch(&bars.abort, 1);
+        st_remote_u32(peer_addr(&bars.abort, rank ^ 1u), 1u);
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; s++) {
+            mbar_init(&bars.full[s], rank == 0 ? 2 : 1);  // CTA 0: its copies + CTA 1's relay
+            mbar_init(&bars.empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bars.acc_full[b], 1);
+            mbar_init(&bars.acc_empty[b], 2 * kEpiWarps);  // both CTAs' epilogue warps (used in CTA 0)
+        }
+        mbar_init(&bars.bfull, rank == 0 ? 2 : 1);
+        mbar_init(&bars.bempty, 1);
+        mbar_init(&bars.drain, 1);
+        bars.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    cluster_sync_all();  // both CTAs' barriers exist before any remote arrival
+    if (warp == 0) tmem_alloc_pair(&bars.tmem_base, 2 * kAccCols);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_base;
+
+    if (warp == 0) {
+        // ---------------- TMA producer (both CTAs): this CTA's L21 half of the
+        // column block stays resident; its W21 rows stream through the ring
+        if (lane == 0) {
+            int stage = 0, cur_key = -1;
+            uint32_t phase = 0, bphase = 0;
+            TileInfo x;
+            for (int64_t k = 0; TILE_P(k, x); k++) {
+                if (x.KB == 0) continue;
+                const int arow = x.ti * 256 + 128 * (int)rank, brow = x.tj * 256 + 128 * (int)rank;
+                if (x.key != cur_key) {
+                    if (!mbar_wait(&bars.bempty, bphase ^ 1u, &bars.abort)) {
+                        raise_abort();
+                        break;
+                    }
+                    mbar_expect_tx(&bars.bfull, (uint32_t)x.KB * C::StageB);
+                    for (int kb = 0; kb < x.KB; kb++)
+#pragma unroll
+                        for (int pc = 0; pc < 2; pc++)
+                            tma_load_2d(sB + (size_t)kb * C::StageB + pc * C::PieceB, mapL[pc], kb * kBK, brow,
+                                        &bars.bfull);
+                    bphase ^= 1u;
+                    cur_key = x.key;
+                }
+                bool ok = true;
+                for (int kb = 0; kb < x.KB; kb++) {
+                    if (!mbar_wait(&bars.empty[stage], phase ^ 1u, &bars.abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&bars.full[stage], C::StageA);
+#pragma unroll
+                    for (int pc = 0; pc < 2; pc++)
+                        tma_load_2d(sA + (size_t)stage * C::StageA + pc * C::PieceA, mapW[pc], kb * kBK, arow,
+                                    &bars.full[stage]);
+                    if (++stage == NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) {
+                    raise_abort();
+                    break;
+                }
+            }
+        }
+    } else if (warp == 1 && rank == 1) {
+        // ---------------- relay (CTA 1): pass each of this CTA's completed
+        // copies on to CTA 0's barrier, in the MMA's order
+        if (lane == 0) {
+            int stage = 0, cur_key = -1;
+            uint32_t phase = 0, bphase = 0;
+            const uint32_t rb = peer_addr(&bars.bfull, 0);
+            TileInfo x;
+            for (int64_t k = 0; TILE_P(k, x); k++) {
+                if (x.KB == 0) continue;
+                bool ok = true;
+                if (x.key != cur_key) {
+                    if (!mbar_wait(&bars.bfull, bphase, &bars.abort)) {
+                        raise_abort();
+                        break;
+                    }
+                    mbar_arrive_remote(rb);
+                    bphase ^= 1u;
+                    cur_key = x.key;
+                }
+                for (int kb = 0; kb < x.KB; kb++) {
+                    if (!mbar_wait(&bars.full[stage], phase, &bars.abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_remote(peer_addr(&bars.full[stage], 0));
+                    if (++stage == NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) {
+                    raise_abort();
+                    break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (CTA 0)
+        if (lane == 0) {
+            int stage = 0, acc = 0, cur_key = -1;
+            uint32_t phase = 0, accphase = 0, bphase = 0;
+            const uint32_t idesc = idesc_bf16(256, 256);
+            TileInfo x;
+            for (int64_t k = 0; TILE_P(k, x); k++) {
+                if (!mbar_wait_cl(&bars.acc_empty[acc], accphase ^ 1u, &bars.abort)) {
+                    raise_abort();
+                    break;
+                }
+                tc_fence_after();
+                if (x.KB > 0 && x.key != cur_key) {
+                    if (!mbar_wait_cl(&bars.bfull, bphase, &bars.abort)) {
+                        raise_abort();
+                        break;
+                    }
+                    tc_fence_after();
+                    bphase ^= 1u;
+                    cur_key = x.key;
+                }
+                const uint32_t dt = tmem + (uint32_t)(acc * kAccCols);
+                bool ok = true;
+                for (int kb = 0; kb < x.KB; kb++) {
+                    if (!mbar_wait_cl(&bars.full[stage], phase, &bars.abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + (size_t)stage * C::StageA);
+                    const uint32_t b0 = smem_u32(sB + (size_t)kb * C::StageB);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / kUmmaK; kk++) {
+                        const uint64_t ah = sdesc(a0 + kk * 32), al = sdesc(a0 + C::PieceA + kk * 32);
+                        const uint64_t bh = sdesc(b0 + kk * 32), bl = sdesc(b0 + C::PieceB + kk * 32);
+                        umma_bf16_pair(dt, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);  // hi*hi
+                        umma_bf16_pair(dt, ah, bl, idesc, 1u);                            // hi*lo
+                        umma_bf16_pair(dt, al, bh, idesc, 1u);                            // lo*hi
+                    }
+                    umma_commit_pair(&bars.empty[stage], (uint16_t)0x3);  // both CTAs' stage free
+                    if (++stage == NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) {
+                    raise_abort();
+                    break;
+                }
+                umma_commit_pair(&bars.acc_full[acc], (uint16_t)0x3);  // both halves of the tile ready
+                if (x.KB > 0) {
+                    int next_key = -2;
+                    TileInfo y;
+                    for (int64_t kn = k + 1; TILE_P(kn, y); kn++) {
+                        if (y.KB > 0) {
+                            next_key = y.key;
+                            break;
+                        }
+                    }
+                    if (next_key != x.key) umma_commit_pair(&bars.bempty, (uint16_t)0x3);
+                }
+                if (++acc == 2) {
+                    acc = 0;
+                    accphase ^= 1u;
+                }
+            }
+            // every MMA issued has completed before the pair tears down
+            umma_commit_pair(&bars.drain, (uint16_t)0x1);
+            int never = 0;
+            mbar_wait(&bars.drain, 0, &never);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9 of both CTAs, this CTA's 128 rows
+        const int q = warp & 3;            // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;  // which 128 of the tile's 256 columns
+        const uint32_t ae0 = peer_addr(&bars.acc_empty[0], 0), ae1 = peer_addr(&bars.acc_empty[1], 0);
+        int acc = 0;
+        uint32_t accphase = 0;
+        TileInfo x;
+        for (int64_t k = 0; TILE_P(k, x); k++) {
+            if (!mbar_wait_cl(&bars.acc_full[acc], accphase, &bars.abort)) {
+                if (lane == 0) raise_abort();
+                break;
+            }
+            tc_fence_after();
+            const int64_t rbase = (int64_t)x.ti * 256 + 128 * rank;  // this CTA's first row
+            const int64_t i = rbase + q * 32 + lane;
+            const int64_t jbase = (int64_t)x.tj * 256 + half * 128;
+            const bool interior = (jbase + 127 < rbase) && (rbase + kBM <= m);
+            const int64_t bi = rbase / 128, bj = jbase / 128;
+            if (!(layout == 2 && bj > bi) && rbase < m) {
+#pragma unroll 1
+                for (int c = 0; c < 4; c += 2) {
+                    uint32_t r[64];
+                    const uint32_t taddr =
+                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols + half * 128 + c * 32);
+                    tmem_ld32_nowait(taddr, *reinterpret_cast<uint32_t(*)[32]>(&r[0]));
+                    tmem_ld32_nowait(taddr + 32, *reinterpret_cast<uint32_t(*)[32]>(&r[32]));
+                    tmem_wait_ld();
+                    if (x.KB == 0) {
+#pragma unroll
+                        for (int xx = 0; xx < 64; xx++) r[xx] = 0u;
+                    }
+                    store64(r, layout, S, m, lds, nb128, i, jbase + c * 32, interior, bi, bj, c * 32, q, lane);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0)
+                    mbar_arrive(&bars.acc_empty[acc]);
+                else
+                    mbar_arrive_remote(acc == 0 ? ae0 : ae1);
+            }
+            if (++acc == 2) {
+                acc = 0;
+                accphase ^= 1u;
+            }
+        }
+    }
+#undef TILE_P
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // no remote access into either CTA from here on
+    if (threadIdx.x == 0 && bars.abort) atomicCAS(info, kInfoOk, (int32_t)CTP_ETIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 2 * kAccCols);
     }
 }
 
@@ -605,6 +913,20 @@ cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t piece_off, in
         mode = nN >= (int64_t)num_sms ? 1 : 2;
     else
         mode = (pieces > 1 && nN >= 2 * (int64_t)num_sms) ? 1 : 2;
+    if (pieces == 2 && m > kBM && num_sms >= 2) {
+        // two pieces: 256 x 256 tiles on pairs of SMs
+        const int nM2 = (int)((m + 255) / 256);
+        const int64_t nt2 = tile_count(nM2, 1);
+        int64_t pairs = num_sms / 2;
+        if (pairs > nt2) pairs = nt2;
+        int mode2 = mode;
+        if (mode2 == 1 && nM2 < pairs) mode2 = 2;  // panels need a column block per pair
+        cudaError_t err = smem_at_least((const void *)k_form_tc_pair, kSmemTC);
+        if (err != cudaSuccess) return err;
+        k_form_tc_pair<<<(unsigned)(2 * pairs), kThreadsTC, kSmemTC, st>>>(mW[0], mL[0], mW[1], mL[1], m, nelim, S,
+                                                                          lds, layout, info, mode2);
+        return cudaGetLastError();
+    }
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
     BatchTab none = {nullptr, nullptr, nullptr, 0};
     if (pieces == 1) return launch_p<false, 1>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
