@@ -177,7 +177,7 @@ struct ctp_plan {
     bool tc;
     // workspace layout
     size_t off_ginfo, off_tab, off_citem, off_sitem, off_fitem, off_lists, off_flags, off_sections, off_wb,
-        off_lb, off_qitem, off_ritem, off_xt, off_zt;
+        off_lb, off_qitem, off_ritem, off_xt, off_zt, off_csitem, off_cstile;
     size_t total;
     int64_t c_items, s_items, f_items, total_rows, q_items, r_items, nxt, nzt;
     struct Class {
@@ -185,6 +185,8 @@ struct ctp_plan {
         size_t smem;         // dynamic shared memory per CTA
         int pcap, ldcap;     // warp kernel: largest p and p + R of the class
         size_t list_off;     // element offset in the class-list array
+        int pmax;            // largest p of the class
+        int64_t s_off, s_count;  // the class's Solve items (front, tile) in the class Solve lists
     };
     std::vector<Class> classes;
     std::vector<unsigned char> blob;  // tables, in workspace order (up to off_sections)
@@ -305,10 +307,18 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         ldmaxK[key] = std::max(ldmaxK[key], p + R);
         if (k.kind != kFactorWarp) smemK[key] = std::max(smemK[key], factor_smem_bytes(p, R, k.G));
     }
-    std::vector<int> lists;
+    std::vector<int> lists, csitem, cstile;
     for (int key = 0; key < kNumKeys; key++) {
         if (byKey[key].empty()) continue;
         ctp_plan::Class c;
+        c.pmax = pmaxK[key];
+        c.s_off = (int64_t)csitem.size();
+        for (int f : byKey[key])
+            for (int64_t t = 0; t < (tab[f].m + kTR - 1) / kTR; t++) {
+                csitem.push_back(f);
+                cstile.push_back((int)t);
+            }
+        c.s_count = (int64_t)csitem.size() - c.s_off;
         c.kind = key < 2 ? kFactorWarp : (key < 5 ? kFactorCta : kFactorCluster);
         c.G = key < 5 ? 1 : (2 << (key - 5));
         c.pcap = pmaxK[key];
@@ -345,6 +355,10 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     off += align256(sizeof(int) * qitem.size());
     P->off_ritem = off;
     off += align256(sizeof(int) * ritem.size());
+    P->off_csitem = off;
+    off += align256(sizeof(int) * csitem.size());
+    P->off_cstile = off;
+    off += align256(sizeof(int) * cstile.size());
     P->off_flags = off;
     off += align256(sizeof(int32_t) * (size_t)nb);
     const size_t tables_end = off;
@@ -377,6 +391,10 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     if (!lists.empty()) memcpy(P->blob.data() + P->off_lists, lists.data(), sizeof(int) * lists.size());
     if (!qitem.empty()) memcpy(P->blob.data() + P->off_qitem, qitem.data(), sizeof(int) * qitem.size());
     if (!ritem.empty()) memcpy(P->blob.data() + P->off_ritem, ritem.data(), sizeof(int) * ritem.size());
+    if (!csitem.empty()) {
+        memcpy(P->blob.data() + P->off_csitem, csitem.data(), sizeof(int) * csitem.size());
+        memcpy(P->blob.data() + P->off_cstile, cstile.data(), sizeof(int) * cstile.size());
+    }
     *plan = P;
     if (ws_bytes) *ws_bytes = P->total;
     return CTP_OK;
@@ -467,6 +485,16 @@ cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, int num
                               reinterpret_cast<const int *>(w + P->off_sitem), P->s_items, P->bo,
                               P->tc ? w + P->off_wb : nullptr, P->tc ? w + P->off_lb : nullptr, P->pmax,
                               st);
+}
+// The FP64 Solve of one pivot-search class's fronts (false when the batch
+// solves on the tensor cores: that Solve runs once over all fronts)
+bool batch_solve_per_class(const ctp_plan *P) { return !P->bo.stc; }
+cudaError_t batch_solve_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st) {
+    const ctp_plan::Class &c = P->classes[ci];
+    return launch_solve_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
+                              reinterpret_cast<const int *>(w + P->off_csitem) + c.s_off, c.s_count, P->bo,
+                              P->tc ? w + P->off_wb : nullptr, P->tc ? w + P->off_lb : nullptr, c.pmax, st,
+                              reinterpret_cast<const int *>(w + P->off_cstile) + c.s_off);
 }
 cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st) {
     if (P->opt.smode == CTP_S_NONE) return cudaSuccess;

@@ -138,9 +138,11 @@ cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char
 cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                          const int *item_front, int64_t items, BatchOpts o,
                                          int num_sms, cudaStream_t st);
+// item_tile (optional): each item's 32-row tile of its front; without it the
+// items of a front are consecutive, from tab[front].s0 on
 cudaError_t launch_solve_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                const int *item_front, int64_t items, BatchOpts o, void *Wb, void *Lb,
-                               int pmax, cudaStream_t st);
+                               int pmax, cudaStream_t st, const int *item_tile = nullptr);
 cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                    const int *item_front, int64_t items, BatchOpts o,
                                    cudaStream_t st);
@@ -159,6 +161,8 @@ cudaError_t batch_prepare(const ctp_plan *P, char *w, cudaStream_t st);
 cudaError_t batch_compress(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st);
 cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
+bool batch_solve_per_class(const ctp_plan *P);
+cudaError_t batch_solve_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st);
 cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 
 // Tensor-core Solve (solve_tc.cu): BF16 pieces of its operands, its scratch

@@ -182,11 +182,13 @@ __global__ void __launch_bounds__(kRows * kWarps)
     solve_tile(A, n, p, lda, perm, piv, Dinv, *nelim_p, W21, ldw, Wb, Lb, Kp, 0, lo_off, pieces, blockIdx.x, xs);
 }
 
-// Batched: CTA b takes work item b = (front, 32-row tile of its A21).
+// Batched: CTA b takes work item b = (front, 32-row tile of its A21): the
+// front is item_front[b], the tile item_tile[b] (or, without that list, the
+// item's place among the front's consecutive items).
 __global__ void __launch_bounds__(kRows * kWarps)
     k_solve_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
-                  const int *__restrict__ item_front, BatchOpts o, __nv_bfloat16 *__restrict__ Wb,
-                  __nv_bfloat16 *__restrict__ Lb) {
+                  const int *__restrict__ item_front, const int *__restrict__ item_tile, BatchOpts o,
+                  __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Lb) {
     extern __shared__ __align__(16) double xs[];
     const int f = item_front[blockIdx.x];
     const ctp_front fr = fronts[f];
@@ -200,7 +202,8 @@ __global__ void __launch_bounds__(kRows * kWarps)
     const bool w64 = o.smode != CTP_S_NONE && o.prec == CTP_FP64;
     solve_tile(fr.A, bt.n, bt.p, fr.lda, fr.perm, fr.piv, reinterpret_cast<const double *>(base + sec.Dinv),
                *fr.nelim, w64 ? reinterpret_cast<double *>(base + sec.W21) : nullptr, bt.m, Wb, Lb,
-               kBatchKp, bt.row0, o.lo_off, o.pieces, (int64_t)blockIdx.x - bt.s0, xs);
+               kBatchKp, bt.row0, o.lo_off, o.pieces,
+               item_tile != nullptr ? (int64_t)item_tile[blockIdx.x] : (int64_t)blockIdx.x - bt.s0, xs);
 }
 
 
@@ -225,14 +228,14 @@ cudaError_t launch_solve_fp64(double *A, int64_t n, int p, int64_t lda, const in
 
 cudaError_t launch_solve_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                const int *item_front, int64_t items, BatchOpts o, void *Wb, void *Lb,
-                               int pmax, cudaStream_t st) {
+                               int pmax, cudaStream_t st, const int *item_tile) {
     if (items == 0) return cudaSuccess;
     const size_t smem = sizeof(double) * (size_t)pmax * (kRows + 1);
     cudaError_t err =
         smem_at_least((const void *)k_solve_batch, smem);
     if (err != cudaSuccess) return err;
     k_solve_batch<<<(unsigned)items, kRows * kWarps, smem, st>>>(
-        fronts, tab, ws, item_front, o, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb);
+        fronts, tab, ws, item_front, item_tile, o, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Lb);
     return cudaGetLastError();
 }
 
