@@ -27,7 +27,6 @@ namespace {
 constexpr int kTR = 32;     // rows per compression item
 constexpr int kThreads = 256;
 constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
-constexpr unsigned long long kInfKey = 0x7FF0000000000000ull;
 
 __device__ __forceinline__ unsigned long long abs_key(double x) {
     return static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
@@ -54,16 +53,29 @@ __global__ void k_batch_prepare(const BFront *__restrict__ tab, char *ws, BatchO
     }
 }
 
+// Lowest index among the lanes' (key, index) pairs with the largest key
+// (keys compared as unsigned 64-bit integers by their 32-bit halves).
+__device__ __forceinline__ int warp_argmax_key(unsigned long long key, int idx, unsigned &hi_out) {
+    const unsigned h = (unsigned)(key >> 32), l = (unsigned)key;
+    const unsigned H = __reduce_max_sync(0xffffffffu, h);
+    const unsigned L = __reduce_max_sync(0xffffffffu, h == H ? l : 0u);
+    hi_out = H;
+    return __reduce_min_sync(0xffffffffu, (h == H && l == L) ? idx : 0x7fffffff);
+}
+
 // Strict compression (Section 4.1, eq. (4.1)), one 32-row tile of one front per
-// CTA: integer argmax per row, then test-then-atomicMax into the front's C.
-__global__ void __launch_bounds__(kThreads)
+// CTA and no shared-memory tile: warp w takes rows 4w..4w+3 of the tile, two at
+// a time.  Lane l loads columns l, l+32, ... of both rows with 8-byte loads
+// through L1 (a 32-byte sector holds four consecutive rows of a column, so the
+// tile's sectors come from memory once), the rows' maxima come from warp
+// reductions on the 32-bit halves of the integer keys (lowest column on ties),
+// then test-then-atomicMax into the front's C.  The rows of C that receive a
+// row are gathered as bits in shared memory and published once per CTA.
+__global__ void __launch_bounds__(kThreads, 3)
     k_compress_strict_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
                             char *ws, const int *__restrict__ item_front, BatchOpts o) {
-    extern __shared__ __align__(16) double tile[];  // [p][kTR+1]
-    __shared__ unsigned long long pkey[kThreads];
-    __shared__ int pidx[kThreads];
-    __shared__ int rowJ[kTR];
-    __shared__ unsigned rbits[kMaxP / 32];  // rows of C that receive a row of this tile
+    __shared__ unsigned rbits[kMaxP / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < kMaxP / 32) rbits[threadIdx.x] = 0u;
     const int f = item_front[blockIdx.x];
     const BFront bt = tab[f];
@@ -79,56 +91,71 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t m = bt.m;
     const int64_t row0 = (blockIdx.x - bt.c0) * (int64_t)kTR;
     const double *A21 = fr.A + p;
+    const int64_t lda = fr.lda;
     const int nrows = (int)((m - row0) < kTR ? (m - row0) : kTR);
-    for (int idx = threadIdx.x; idx < kTR * p; idx += kThreads) {
-        const int k = idx / kTR, r = idx % kTR;
-        tile[k * (kTR + 1) + r] = r < nrows ? A21[(int64_t)k * fr.lda + row0 + r] : 0.0;
-    }
     __syncthreads();
-    constexpr int NG = kThreads / kTR;
-    const int r = threadIdx.x % kTR, g = threadIdx.x / kTR;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr int KPL = kMaxP / 32;
     bool nonfinite = false;
-    unsigned long long best = 0;
-    int bidx = -1;
-    if (r < nrows)
-        for (int k = g; k < p; k += NG) {
-            const unsigned long long key = abs_key(tile[k * (kTR + 1) + r]);
-            nonfinite |= key >= kInfKey;
-            if (bidx < 0 || key > best) {
-                best = key;
-                bidx = k;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; pass++) {
+        const int ra = 4 * warp + 2 * pass;
+        if (ra >= nrows) break;  // warp-uniform
+        const bool vb = ra + 1 < nrows;
+        const double *pa = A21 + row0 + ra;
+        unsigned long long xa[KPL], xb[KPL];
+#pragma unroll
+        for (int u = 0; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            xa[u] = kc < p ? abs_key(pa[(int64_t)kc * lda]) : 0ull;
+            xb[u] = (vb && kc < p) ? abs_key(pa[(int64_t)kc * lda + 1]) : 0ull;
+        }
+        // per lane: the largest key of its columns (ascending, so the lowest
+        // column wins ties); lanes without a column offer none
+        unsigned long long ba = xa[0], bb = xb[0];
+        int ia = lane < p ? lane : 0x7fffffff, ib = ia;
+#pragma unroll
+        for (int u = 1; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            if (kc < p) {
+                if (xa[u] > ba) {
+                    ba = xa[u];
+                    ia = kc;
+                }
+                if (xb[u] > bb) {
+                    bb = xb[u];
+                    ib = kc;
+                }
             }
         }
-    pkey[g * kTR + r] = best;
-    pidx[g * kTR + r] = bidx;
-    __syncthreads();
-    if (threadIdx.x < kTR) {
-        unsigned long long b = 0;
-        int bi = -1;
-        for (int gg = 0; gg < NG; gg++) {
-            const int ii = pidx[gg * kTR + threadIdx.x];
-            const unsigned long long kk = pkey[gg * kTR + threadIdx.x];
-            if (ii < 0) continue;
-            if (bi < 0 || kk > b || (kk == b && ii < bi)) {
-                b = kk;
-                bi = ii;
-            }
+        unsigned ha, hb;
+        const int Ia = warp_argmax_key(ba, ia, ha), Ib = warp_argmax_key(bb, ib, hb);
+        // an Inf or NaN anywhere in a row is its maximum key
+        nonfinite |= ha >= 0x7FF00000u || (vb && hb >= 0x7FF00000u);
+        if (lane == 0) {
+            atomicOr(&rbits[Ia >> 5], 1u << (Ia & 31));
+            if (vb) atomicOr(&rbits[Ib >> 5], 1u << (Ib & 31));
         }
-        rowJ[threadIdx.x] = bi;
-        // row bi of C has a member: the pivot search keeps only such rows
-        if (threadIdx.x < nrows && bi >= 0) atomicOr(&rbits[bi >> 5], 1u << (bi & 31));
+        // every C key is loaded before any compare (the L2 round trips overlap);
+        // the atomic fires only on a new maximum
+        unsigned long long *ca = Ckeys + (int64_t)Ia * p, *cb = Ckeys + (int64_t)(vb ? Ib : Ia) * p;
+        unsigned long long cura[KPL], curb[KPL];
+#pragma unroll
+        for (int u = 0; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            cura[u] = kc < p ? __ldcg(ca + kc) : ~0ull;
+            curb[u] = (vb && kc < p) ? __ldcg(cb + kc) : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < KPL; u++) {
+            const int kc = lane + 32 * u;
+            if (xa[u] > cura[u]) atomicMax(ca + kc, xa[u]);
+            if (xb[u] > curb[u]) atomicMax(cb + kc, xb[u]);
+        }
     }
     __syncthreads();
+    // row bi of C has a member: the pivot search keeps only such rows
     if (threadIdx.x < (p + 31) / 32 && rbits[threadIdx.x] != 0u)
         atomicOr(reinterpret_cast<uint32_t *>(base + sec.nz) + threadIdx.x, rbits[threadIdx.x]);
-    for (int rr = warp; rr < nrows; rr += kThreads / 32) {
-        unsigned long long *crow = Ckeys + (int64_t)rowJ[rr] * p;
-        for (int k = lane; k < p; k += 32) {
-            const unsigned long long key = abs_key(tile[k * (kTR + 1) + rr]);
-            if (key > __ldcg(crow + k)) atomicMax(crow + k, key);
-        }
-    }
     if (nonfinite) atomicCAS(reinterpret_cast<int32_t *>(base + sec.info), kInfoOk, (int32_t)CTP_ENONFINITE);
 }
 
@@ -155,10 +182,7 @@ cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *
                                          int num_sms, cudaStream_t st) {
     (void)num_sms;
     if (items == 0) return cudaSuccess;
-    const size_t smem = sizeof(double) * (size_t)kMaxP * (kTR + 1);
-    cudaError_t err = smem_at_least((const void *)k_compress_strict_batch, smem);
-    if (err != cudaSuccess) return err;
-    k_compress_strict_batch<<<(unsigned)items, kThreads, smem, st>>>(fronts, tab, ws, item_front, o);
+    k_compress_strict_batch<<<(unsigned)items, kThreads, 0, st>>>(fronts, tab, ws, item_front, o);
     return cudaGetLastError();
 }
 
