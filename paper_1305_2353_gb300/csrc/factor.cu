@@ -79,6 +79,9 @@ struct Shared {
     int rowmap[kMaxP];  // nonzero outer rows
     int nz_count;
     unsigned char nzflag[kMaxP];
+    unsigned short lrow[kMaxP];  // the live A11 rows, ascending (rebuilt before each update)
+    unsigned short lpos[kMaxP];  // lpos[i]: how many live rows lie above row i
+    int nlive;
 };
 
 // The team that owns one front: a cluster of G CTAs, or one CTA.
@@ -554,29 +557,51 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             }
         }
         __syncthreads();
-        // the update over (column, row) pairs of the live columns and rows.  An
-        // A11 entry above the diagonal (i < c) gets the value of its mirror
-        // (c, i) below it, from row c's multipliers and row i's pivot entries,
-        // so both halves hold bit-identical values without any exchange.
-        for (int idx = tid, lc2 = tid / LD, i2 = tid - (tid / LD) * LD; idx < ncl * LD; idx += kT) {
-            const int lc = lc2, i = i2;
-            i2 += di;
-            lc2 += dl;
-            if (i2 >= LD) {
-                i2 -= LD;
-                lc2++;
+        // the live A11 rows in order (the pivot rows were just retired) and,
+        // for every row, the number of live rows above it
+        if (warp == 0) {
+            int r = 0;
+            for (int j0 = 0; j0 < p; j0 += 32) {
+                const int j = j0 + lane;
+                const bool lv = j < p && sh.live[j];
+                const unsigned bal = __ballot_sync(0xffffffffu, lv);
+                const int at = r + __popc(bal & ((1u << lane) - 1u));
+                if (j < p) sh.lpos[j] = (unsigned short)at;
+                if (lv) sh.lrow[at] = (unsigned short)j;
+                r += __popc(bal);
             }
-            const int c = (lc << gs) + rank;
-            if (c >= p || !sh.live[c]) continue;
-            if (i < p && !sh.live[i]) continue;  // the pivot rows are no longer live
-            // one fused multiply-add per pivot column: -l(r) a(k,q), or
-            // +l(r) |a(k,q)| on the abs rows (eq. (4.3)); (r, k) = (i, c), or
-            // (c, i) above the diagonal
-            const bool up = i < c, ab = abs_rows && i >= p;
-            const int r = up ? c : i, k = up ? i : c;
-            double v = fma(rl0[r], ab ? apc0[k] : pc0[k], cols[idx]);
-            if (q1 >= 0) v = fma(rl1[r], ab ? apc1[k] : pc1[k], v);
-            cols[idx] = v;
+            if (lane == 0) sh.nlive = r;
+        }
+        __syncthreads();
+        // the update: warp w takes the own live columns w, w + kNW, ...; column
+        // c gets its live A11 rows from the diagonal down and the R outer rows,
+        // one fused multiply-add per pivot column: -l(i) a(c,q), or +l(i)
+        // |a(c,q)| on the abs rows (eq. (4.3)).  The entry (c, i) above the
+        // diagonal, in row i's column, is the same product (row i's multiplier,
+        // row c's pivot entry) on the same old value (the working matrix is
+        // symmetric), so column c's owner stores the result there too (in
+        // another CTA's shared memory when column i lives there): the upper half
+        // costs a store instead of a second FP64 update, and both halves stay
+        // bit-identical.  Only live rows are visited, so no lane of an FP64
+        // instruction idles on a retired row.
+        {
+            const int nl = sh.nlive;
+            for (int lc = warp; lc < ncl; lc += kNW) {
+                const int c = (lc << gs) + rank;
+                if (c >= p || !sh.live[c]) continue;  // warp-uniform
+                const int a0 = sh.lpos[c], lenA = nl - a0, len = lenA + R;
+                double *col = cols + (size_t)lc * LD;
+                const double q0c = pc0[c], aq0c = apc0[c];
+                const double q1c = q1 >= 0 ? pc1[c] : 0.0, aq1c = q1 >= 0 ? apc1[c] : 0.0;
+                for (int j = lane; j < len; j += 32) {
+                    const int i = j < lenA ? (int)sh.lrow[a0 + j] : p + (j - lenA);
+                    const bool ab = abs_rows && i >= p;
+                    double v = fma(rl0[i], ab ? aq0c : q0c, col[i]);
+                    if (q1 >= 0) v = fma(rl1[i], ab ? aq1c : q1c, v);
+                    col[i] = v;
+                    if (i < p && i != c) team.at(cols, i & gm)[(size_t)(i >> gs) * LD + c] = v;
+                }
+            }
         }
         nelim += (q1 < 0) ? 1 : 2;
         accepted = 1;
