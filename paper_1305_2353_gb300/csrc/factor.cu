@@ -380,7 +380,12 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
         nonfinite |= nonfinite_bits(v);
         cols[idx] = v;
     }
-    for (int i = tid; i < p; i += kT) sh.live[i] = 1;
+    for (int i = tid; i < p; i += kT) {
+        sh.live[i] = 1;
+        sh.lrow[i] = (unsigned short)i;
+        sh.lpos[i] = (unsigned short)i;
+    }
+    if (tid == 0) sh.nlive = p;
     if (tid < 2) sh.cmin[tid] = kNoKey;
     if (nonfinite) atomicCAS(a.info, kInfoOk, (int32_t)CTP_ENONFINITE);
     team.sync();
@@ -472,7 +477,15 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
         }
         const Decision dv = sh.cur;
         if (dv.kind == DEC_ZERO) {
+            // the live-row list without cstar (every thread reads its own rows'
+            // old positions only)
+            for (int i = tid; i < p; i += kT) {
+                const int np = sh.lpos[i] - (cstar < i ? 1 : 0);
+                sh.lpos[i] = (unsigned short)np;
+                if (sh.live[i] && i != cstar) sh.lrow[np] = (unsigned short)i;
+            }
             if (tid == 0) {
+                sh.nlive--;
                 sh.live[cstar] = 0;
                 sh.order[nelim] = cstar;
                 sh.kind[nelim] = CTP_PIVKIND_ZERO;
@@ -511,6 +524,14 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             const double *s1 = q1 >= 0 ? colptr(q1) : s0;
             const double ad0 = abs_bits(dv.d0), ai0 = abs_bits(dv.i0), ai1 = abs_bits(dv.i1), ai2 = abs_bits(dv.i2);
             for (int i = tid; i < LD; i += kT) {
+                if (i < p) {
+                    // the live-row list without the pivot rows: the rank of a
+                    // row drops by the pivots above it (the pivots' own flags
+                    // are cleared in this phase, so they are named explicitly)
+                    const int np = sh.lpos[i] - (q0 < i ? 1 : 0) - (q1 >= 0 && q1 < i ? 1 : 0);
+                    sh.lpos[i] = (unsigned short)np;
+                    if (sh.live[i] && i != q0 && i != q1) sh.lrow[np] = (unsigned short)i;
+                }
                 const double x = s0[i];
                 pc0[i] = x;
                 const bool ab = abs_rows && i >= p;
@@ -530,6 +551,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
                 }
             }
             if (tid == 0) {
+                sh.nlive -= q1 < 0 ? 1 : 2;
                 if (q1 < 0) {
                     sh.live[q0] = 0;
                     sh.order[nelim] = q0;
@@ -555,22 +577,6 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
                     sh.sInv[2 * nelim + 3] = 0.0;
                 }
             }
-        }
-        __syncthreads();
-        // the live A11 rows in order (the pivot rows were just retired) and,
-        // for every row, the number of live rows above it
-        if (warp == 0) {
-            int r = 0;
-            for (int j0 = 0; j0 < p; j0 += 32) {
-                const int j = j0 + lane;
-                const bool lv = j < p && sh.live[j];
-                const unsigned bal = __ballot_sync(0xffffffffu, lv);
-                const int at = r + __popc(bal & ((1u << lane) - 1u));
-                if (j < p) sh.lpos[j] = (unsigned short)at;
-                if (lv) sh.lrow[at] = (unsigned short)j;
-                r += __popc(bal);
-            }
-            if (lane == 0) sh.nlive = r;
         }
         __syncthreads();
         // the update: warp w takes the own live columns w, w + kNW, ...; column
