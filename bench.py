@@ -57,14 +57,24 @@ NCU_TRAFFIC = {
     # 1513.69 MB written for m(m+1)/2 = 194,921,640 entries
     "form_fp64": {"file": "form.cu", "sha1": "798d569f67e7e8f417e75b162e2622426e55e05e",
                   "unit": "packed_entry", "bytes_per_unit": (163.760384e6 + 1513.690e6) / 194921640},
-    # ncu --set full, n=40000 p=256 relaxed, split BF16, S FP32 in 128x128 blocks:
-    # 188.44 MB read + 3118.11 MB written for 48,516 blocks of 16,384 entries
-    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "f42cb5618b32f27438bd8a88393945b4d1c3750f",
-                       "unit": "tiled_entry", "bytes_per_unit": (188.438784e6 + 3118.110e6) / (48516 * 16384)},
+    # ncu --set full, n=40000 p=256 relaxed, split BF16 on SM pairs, S FP32 in 128x128
+    # blocks: 88.03 MB read + 3118.41 MB written for 48,516 blocks of 16,384 entries
+    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "c4a552e28a454e98fc4698e1b898fff9da558d1b",
+                       "unit": "tiled_entry", "bytes_per_unit": (88.028160e6 + 3118.409e6) / (48516 * 16384)},
     # ncu --set full, n=40000 p=256 relaxed, tensor-core Solve before a split-BF16
-    # Form (prep + gather + GEMM): 145.23 MB read + 124.64 MB written for 39,744 rows
-    "solve_tc": {"file": "solve_tc.cu", "sha1": "b625943159839444dd75e137c8f4021fbb3e3789", "prec": "bf16x3",
-                 "unit": "row", "bytes_per_unit": (145.232896e6 + 124.638e6) / 39744},
+    # Form (prep + gather + GEMM): 144.97 MB read + 124.87 MB written for 39,744 rows
+    "solve_tc": {"file": "solve_tc.cu", "sha1": "986f68bd883bd413248fac53507ed870abbd31cb", "prec": "bf16x3",
+                 "unit": "row", "bytes_per_unit": (144.965376e6 + 124.866e6) / 39744},
+    # ncu --set full, n=200000 p=256 strict: 409.64 MB read + 3.59 MB written for
+    # 199,744 A21 rows
+    "compress_strict": {"file": "compress.cu", "sha1": "64d01d59c6c3d5f92ce7b20d803e44db5ce0659b",
+                        "unit": "row", "bytes_per_unit": (409.639936e6 + 3.588608e6) / 199744},
+    # ncu --set full, n=200000 p=256 relaxed, the four launches of one compression
+    # (block maxima, per-column top-K, greedy, gather): 441.90 MB read + 8.10 MB
+    # written for 199,744 A21 rows
+    "compress_relaxed": {"file": "relaxed.cu", "sha1": "914805816d1f1d77f7a1c544998af6cea6749c3a",
+                         "unit": "row", "bytes_per_unit": (409.117184e6 + 23.292928e6 + 0.161536e6 + 8.32768e6
+                                                           + 8.1024e6) / 199744},
 }
 
 
@@ -977,6 +987,7 @@ def headline(rec):
         line["mixed"] = {"value": _r(mx["value"]), "ms_per_step": _r(mx["ms_per_step"]),
                          "dtype": "bf16x3 tensor-core Solve+Form, f32 S",
                          "form_frac_of_hbm": _r(mx["roofline"].get("hbm_frac", mx["roofline"].get("frac"))),
+                         "form_tensor_frac_executed": _r(mx["roofline"].get("tensor_frac_executed_of_bf16_burst")),
                          "bwd_err_factor_growth_normalised": _r(mx["errors"]["factor"]["growth_normalised"], 3),
                          "form_rel": _r(mx["errors"].get("form", {}).get("max_rel_to_scale"), 3)}
     bt = rec.get("batch")
