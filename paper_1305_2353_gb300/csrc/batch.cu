@@ -71,13 +71,17 @@ __device__ __forceinline__ int warp_argmax_key(unsigned long long key, int idx, 
 // reductions on the 32-bit halves of the integer keys (lowest column on ties),
 // then test-then-atomicMax into the front's C.  The rows of C that receive a
 // row are gathered as bits in shared memory and published once per CTA.
-__global__ void __launch_bounds__(kThreads, 3)
+// The items come bucketed by p (KPL = ceil(p / 32) columns per lane at most):
+// this launch takes items ibase + blockIdx.x.
+template <int KPL>
+__global__ void __launch_bounds__(kThreads, KPL <= 2 ? 6 : (KPL == 4 ? 4 : 3))
     k_compress_strict_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
-                            char *ws, const int *__restrict__ item_front, BatchOpts o) {
+                            char *ws, const int *__restrict__ item_front, int64_t ibase, BatchOpts o) {
     __shared__ unsigned rbits[kMaxP / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < kMaxP / 32) rbits[threadIdx.x] = 0u;
-    const int f = item_front[blockIdx.x];
+    const int64_t item = ibase + blockIdx.x;
+    const int f = item_front[item];
     const BFront bt = tab[f];
     const ctp_front fr = fronts[f];
     ctp_options oo;
@@ -89,12 +93,11 @@ __global__ void __launch_bounds__(kThreads, 3)
     unsigned long long *Ckeys = reinterpret_cast<unsigned long long *>(base + sec.C);
     const int p = bt.p;
     const int64_t m = bt.m;
-    const int64_t row0 = (blockIdx.x - bt.c0) * (int64_t)kTR;
+    const int64_t row0 = (item - bt.c0) * (int64_t)kTR;
     const double *A21 = fr.A + p;
     const int64_t lda = fr.lda;
     const int nrows = (int)((m - row0) < kTR ? (m - row0) : kTR);
     __syncthreads();
-    constexpr int KPL = kMaxP / 32;
     bool nonfinite = false;
 #pragma unroll 1
     for (int pass = 0; pass < 2; pass++) {
@@ -178,12 +181,25 @@ __global__ void k_batch_flags(const BFront *__restrict__ tab, const char *ws, Ba
 }  // namespace
 
 cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *tab, char *ws,
-                                         const int *item_front, int64_t items, BatchOpts o,
-                                         int num_sms, cudaStream_t st) {
-    (void)num_sms;
-    if (items == 0) return cudaSuccess;
-    k_compress_strict_batch<<<(unsigned)items, kThreads, 0, st>>>(fronts, tab, ws, item_front, o);
-    return cudaGetLastError();
+                                         const int *item_front, const int64_t (&bucket)[5], BatchOpts o,
+                                         cudaStream_t st) {
+    // bucket[b] .. bucket[b+1]: the items of fronts with p <= 32 << b
+    for (int b = 0; b < 4; b++) {
+        const int64_t n = bucket[b + 1] - bucket[b];
+        if (n == 0) continue;
+        const unsigned g = (unsigned)n;
+        if (b == 0)
+            k_compress_strict_batch<1><<<g, kThreads, 0, st>>>(fronts, tab, ws, item_front, bucket[b], o);
+        else if (b == 1)
+            k_compress_strict_batch<2><<<g, kThreads, 0, st>>>(fronts, tab, ws, item_front, bucket[b], o);
+        else if (b == 2)
+            k_compress_strict_batch<4><<<g, kThreads, 0, st>>>(fronts, tab, ws, item_front, bucket[b], o);
+        else
+            k_compress_strict_batch<8><<<g, kThreads, 0, st>>>(fronts, tab, ws, item_front, bucket[b], o);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ctp
@@ -204,6 +220,7 @@ struct ctp_plan {
         off_lb, off_qitem, off_ritem, off_xt, off_zt, off_csitem, off_cstile;
     size_t total;
     int64_t c_items, s_items, f_items, total_rows, q_items, r_items, nxt, nzt;
+    int64_t cbucket[5] = {0, 0, 0, 0, 0};  // compression items of fronts with p <= 32, 64, 128, 256
     struct Class {
         int kind, G, count;  // kFactor*, cluster width
         size_t smem;         // dynamic shared memory per CTA
@@ -285,10 +302,7 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         sec_off += bsection(b.n, b.p, opt).total;
         b.row0 = row0;
         if (tc) row0 += (b.m + 255) / 256 * 256;
-        b.c0 = (int64_t)citem.size();
         const int64_t nt = (b.m + kTR - 1) / kTR;
-        if (opt->pivot == CTP_PIV_STRICT)
-            for (int64_t t = 0; t < nt; t++) citem.push_back(f);
         b.s0 = (int64_t)sitem.size();
         for (int64_t t = 0; t < nt; t++) sitem.push_back(f);
         b.f0 = (int64_t)fitem.size();
@@ -311,6 +325,21 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         }
         P->pmax = std::max(P->pmax, b.p);
     }
+    // compression items (32-row tiles), bucketed by p so that each launch's
+    // kernel holds no more columns per lane than its fronts need
+    if (opt->pivot == CTP_PIV_STRICT) {
+        for (int bk = 0; bk < 4; bk++) {
+            P->cbucket[bk] = (int64_t)citem.size();
+            for (int f = 0; f < nb; f++) {
+                const int p = tab[f].p;
+                const int fb = p <= 32 ? 0 : (p <= 64 ? 1 : (p <= 128 ? 2 : 3));
+                if (fb != bk) continue;
+                tab[f].c0 = (int64_t)citem.size();
+                for (int64_t t = 0; t < (tab[f].m + kTR - 1) / kTR; t++) citem.push_back(f);
+            }
+        }
+    }
+    P->cbucket[4] = (int64_t)citem.size();
     // fronts by pivot-search class: warp (2 buckets), CTA (3 buckets), cluster
     // (G = 2, 4, 8, 16), in this order; the launch sequence starts from the end
     size_t budget = (size_t)ctx_batch_smem_kb(ctx) * 1024;
@@ -487,9 +516,9 @@ cudaError_t batch_prepare(const ctp_plan *P, char *w, cudaStream_t st) {
 }
 cudaError_t batch_compress(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st) {
     if (P->opt.pivot != CTP_PIV_STRICT) return cudaSuccess;
+    (void)num_sms;
     return launch_compress_strict_batch(fr, reinterpret_cast<const BFront *>(w + P->off_tab), w,
-                                        reinterpret_cast<const int *>(w + P->off_citem), P->c_items, P->bo,
-                                        num_sms, st);
+                                        reinterpret_cast<const int *>(w + P->off_citem), P->cbucket, P->bo, st);
 }
 cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st) {
     const ctp_plan::Class &c = P->classes[ci];

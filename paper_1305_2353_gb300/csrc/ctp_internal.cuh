@@ -135,9 +135,10 @@ struct BatchOpts {
 cudaError_t launch_factor_batch(const ctp_front *fronts, const BFront *tab, char *ws, const int *list,
                                 int count, int kind, int G, size_t smem, int pcap, int ldcap, BatchOpts o,
                                 cudaStream_t st);
+// bucket[b] .. bucket[b+1]: the items (32-row tiles) of the fronts with p <= 32 << b
 cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *tab, char *ws,
-                                         const int *item_front, int64_t items, BatchOpts o,
-                                         int num_sms, cudaStream_t st);
+                                         const int *item_front, const int64_t (&bucket)[5], BatchOpts o,
+                                         cudaStream_t st);
 // item_tile (optional): each item's 32-row tile of its front; without it the
 // items of a front are consecutive, from tab[front].s0 on
 cudaError_t launch_solve_batch(const ctp_front *fronts, const BFront *tab, char *ws,
