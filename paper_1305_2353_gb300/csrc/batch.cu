@@ -238,8 +238,8 @@ struct ctp_plan {
 // strict compression (each A21 row lands in one row of C), none for restricted
 // pivoting.  Small fronts go to the warp kernel; fronts whose working matrix
 // fits one CTA under the shared-memory budget go to the CTA kernel, bucketed
-// by the shared memory they need (so that small fronts share an SM: 3, 2 or 1
-// CTAs of the bucket per SM); the rest to the narrowest cluster whose CTAs fit
+// by the shared memory they need (one launch per bucket, so that a launch's
+// CTAs are of similar size); the rest to the narrowest cluster whose CTAs fit
 // the budget.
 struct ClassKey {
     int kind, G, bucket;

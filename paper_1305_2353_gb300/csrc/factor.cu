@@ -50,7 +50,11 @@ namespace ctp {
 
 namespace {
 
-constexpr int kT = 256;  // threads per CTA (CTA and cluster kernels)
+// threads per CTA (CTA and cluster kernels): 16 warps, one CTA per SM.  Eight
+// warps with up to three CTAs per SM were slower: a front's FP64 update then
+// has half the warps of its SM to issue from (the pipe is about 70 cycles per
+// warp instruction), while small fronts sharing an SM gained nothing measurable
+constexpr int kT = 512;
 constexpr int kNW = kT / 32;
 constexpr int kWarpFronts = 4;  // fronts (warps) per CTA of the warp kernel
 constexpr int kNoKey = 0x7fffffff;
@@ -684,8 +688,8 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
     team.sync();  // no CTA leaves while its shared memory may still be read
 }
 
-__global__ void __launch_bounds__(kT, 3) k_factor_cluster(FactorArgs a, int G) { factor_body<false>(a, G); }
-__global__ void __launch_bounds__(kT, 3) k_factor_cta(FactorArgs a) { factor_body<true>(a, 1); }
+__global__ void __launch_bounds__(kT, 1) k_factor_cluster(FactorArgs a, int G) { factor_body<false>(a, G); }
+__global__ void __launch_bounds__(kT, 1) k_factor_cta(FactorArgs a) { factor_body<true>(a, 1); }
 
 // The arguments of front f of a batch, from its descriptor and its workspace
 // section.
@@ -720,12 +724,12 @@ __device__ __forceinline__ FactorArgs batch_args(const ctp_front *__restrict__ f
 }
 
 // Batched: cluster c (or CTA c) factors front list[c].
-__global__ void __launch_bounds__(kT, 3)
+__global__ void __launch_bounds__(kT, 1)
     k_factor_cluster_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab,
                            char *ws, const int *__restrict__ list, BatchOpts o, int G) {
     factor_body<false>(batch_args(fronts, tab, ws, list[blockIdx.x / G], o), G);
 }
-__global__ void __launch_bounds__(kT, 3)
+__global__ void __launch_bounds__(kT, 1)
     k_factor_cta_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
                        const int *__restrict__ list, BatchOpts o) {
     factor_body<true>(batch_args(fronts, tab, ws, list[blockIdx.x], o), 1);
