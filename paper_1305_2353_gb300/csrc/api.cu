@@ -443,8 +443,9 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
         // the classes touch disjoint fronts: run them side by side (the plan
         // lists the widest last: launched first, its clusters take SMs before
         // the narrow CTAs fill the rest), each followed on its stream by the
-        // FP64 Solve of its own fronts (which then overlaps the classes still
-        // searching), joined back into st; capturable as a fork/join
+        // FP64 Solve and the Form of its own fronts (which then overlap the
+        // classes still searching), joined back into st; capturable as a
+        // fork/join
         const bool per_class = batch_solve_per_class(plan);
         CTP_CUDA(cudaEventRecord(ctx->fork_ev, st));
         for (int i = 0; i < ncls; i++) {
@@ -452,12 +453,18 @@ ctp_status ctp_factor_batch(ctp_ctx *ctx, const ctp_plan *plan, const ctp_front 
             cudaStream_t s = ctx->side[i % kSideStreams];
             CTP_CUDA(cudaStreamWaitEvent(s, ctx->fork_ev, 0));
             CTP_CUDA(batch_factor_class(plan, c, fronts, w, s));
-            if (per_class) CTP_CUDA(batch_solve_class(plan, c, fronts, w, s));
+            if (per_class) {
+                CTP_CUDA(batch_solve_class(plan, c, fronts, w, s));
+                CTP_CUDA(batch_form_class(plan, c, fronts, w, ctx->num_sms, s));
+            }
             CTP_CUDA(cudaEventRecord(ctx->join_ev[i % kSideStreams], s));
         }
         for (int i = 0; i < ncls && i < kSideStreams; i++) CTP_CUDA(cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
-        if (!per_class)
+        if (!per_class) {
             CTP_CUDA(timed(ctx, K_B_SOLVE, st, [&] { return batch_solve(plan, fronts, w, ctx->num_sms, st); }));
+            CTP_CUDA(timed(ctx, K_B_FORM, st, [&] { return batch_form(plan, fronts, w, ctx->num_sms, st); }));
+        }
+        return CTP_OK;
     } else {
         for (int c = 0; c < ncls; c++) {
             const int G = batch_class_G(plan, c), kind = batch_class_kind(plan, c);

@@ -217,7 +217,7 @@ struct ctp_plan {
     bool tc;
     // workspace layout
     size_t off_ginfo, off_tab, off_citem, off_sitem, off_fitem, off_lists, off_flags, off_sections, off_wb,
-        off_lb, off_qitem, off_ritem, off_xt, off_zt, off_csitem, off_cstile;
+        off_lb, off_qitem, off_ritem, off_xt, off_zt, off_csitem, off_cstile, off_cfitem, off_cftile;
     size_t total;
     int64_t c_items, s_items, f_items, total_rows, q_items, r_items, nxt, nzt;
     int64_t cbucket[5] = {0, 0, 0, 0, 0};  // compression items of fronts with p <= 32, 64, 128, 256
@@ -228,6 +228,7 @@ struct ctp_plan {
         size_t list_off;     // element offset in the class-list array
         int pmax;            // largest p of the class
         int64_t s_off, s_count;  // the class's Solve items (front, tile) in the class Solve lists
+        int64_t f_off, f_count;  // the class's Form items (front, tile) in the class Form lists
     };
     std::vector<Class> classes;
     std::vector<unsigned char> blob;  // tables, in workspace order (up to off_sections)
@@ -360,7 +361,7 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         ldmaxK[key] = std::max(ldmaxK[key], p + R);
         if (k.kind != kFactorWarp) smemK[key] = std::max(smemK[key], factor_smem_bytes(p, R, k.G));
     }
-    std::vector<int> lists, csitem, cstile;
+    std::vector<int> lists, csitem, cstile, cfitem, cftile;
     for (int key = 0; key < kNumKeys; key++) {
         if (byKey[key].empty()) continue;
         ctp_plan::Class c;
@@ -372,6 +373,16 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
                 cstile.push_back((int)t);
             }
         c.s_count = (int64_t)csitem.size() - c.s_off;
+        c.f_off = (int64_t)cfitem.size();
+        if (opt->smode != CTP_S_NONE)
+            for (int f : byKey[key]) {
+                const int64_t ft = tc ? form_tc_tiles(tab[f].m, pieces) : form_fp64_tiles(tab[f].m);
+                for (int64_t t = 0; t < ft; t++) {
+                    cfitem.push_back(f);
+                    cftile.push_back((int)t);
+                }
+            }
+        c.f_count = (int64_t)cfitem.size() - c.f_off;
         c.kind = key < 2 ? kFactorWarp : (key < 5 ? kFactorCta : kFactorCluster);
         c.G = key < 5 ? 1 : (2 << (key - 5));
         c.pcap = pmaxK[key];
@@ -412,6 +423,10 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     off += align256(sizeof(int) * csitem.size());
     P->off_cstile = off;
     off += align256(sizeof(int) * cstile.size());
+    P->off_cfitem = off;
+    off += align256(sizeof(int) * cfitem.size());
+    P->off_cftile = off;
+    off += align256(sizeof(int) * cftile.size());
     P->off_flags = off;
     off += align256(sizeof(int32_t) * (size_t)nb);
     const size_t tables_end = off;
@@ -447,6 +462,10 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
     if (!csitem.empty()) {
         memcpy(P->blob.data() + P->off_csitem, csitem.data(), sizeof(int) * csitem.size());
         memcpy(P->blob.data() + P->off_cstile, cstile.data(), sizeof(int) * cstile.size());
+    }
+    if (!cfitem.empty()) {
+        memcpy(P->blob.data() + P->off_cfitem, cfitem.data(), sizeof(int) * cfitem.size());
+        memcpy(P->blob.data() + P->off_cftile, cftile.data(), sizeof(int) * cftile.size());
     }
     *plan = P;
     if (ws_bytes) *ws_bytes = P->total;
@@ -548,6 +567,20 @@ cudaError_t batch_solve_class(const ctp_plan *P, int ci, const ctp_front *fr, ch
                               reinterpret_cast<const int *>(w + P->off_csitem) + c.s_off, c.s_count, P->bo,
                               P->tc ? w + P->off_wb : nullptr, P->tc ? w + P->off_lb : nullptr, c.pmax, st,
                               reinterpret_cast<const int *>(w + P->off_cstile) + c.s_off);
+}
+// The Form of one pivot-search class's fronts (after that class's Solve)
+cudaError_t batch_form_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, int num_sms,
+                             cudaStream_t st) {
+    if (P->opt.smode == CTP_S_NONE) return cudaSuccess;
+    const ctp_plan::Class &c = P->classes[ci];
+    const BFront *tab = reinterpret_cast<const BFront *>(w + P->off_tab);
+    const int *fitem = reinterpret_cast<const int *>(w + P->off_cfitem) + c.f_off;
+    const int *ftile = reinterpret_cast<const int *>(w + P->off_cftile) + c.f_off;
+    if (P->tc)
+        return launch_form_tc_batch(fr, tab, fitem, c.f_count, P->total_rows, w + P->off_wb, w + P->off_lb,
+                                    P->bo.pieces, P->opt.smode == CTP_S_FP64_SUB ? 3 : 2,
+                                    reinterpret_cast<int32_t *>(w + P->off_ginfo), num_sms, st, ftile);
+    return launch_form_fp64_batch(fr, tab, w, fitem, c.f_count, P->bo, st, ftile);
 }
 cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st) {
     if (P->opt.smode == CTP_S_NONE) return cudaSuccess;

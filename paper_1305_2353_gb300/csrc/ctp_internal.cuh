@@ -144,13 +144,15 @@ cudaError_t launch_compress_strict_batch(const ctp_front *fronts, const BFront *
 cudaError_t launch_solve_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                const int *item_front, int64_t items, BatchOpts o, void *Wb, void *Lb,
                                int pmax, cudaStream_t st, const int *item_tile = nullptr);
+// item_tile (optional, both batched Forms): each item's tile of its front;
+// without it the items of a front are consecutive, from tab[front].f0 on
 cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                    const int *item_front, int64_t items, BatchOpts o,
-                                   cudaStream_t st);
+                                   cudaStream_t st, const int *item_tile = nullptr);
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
                                  int pieces, int layout /* 2 tiled, 3 subtract */, int32_t *info, int num_sms,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const int *item_tile = nullptr);
 constexpr int kBatchKp = 256;  // K stride of the stacked BF16 operand buffers
 
 // the batched launch sequence (batch.cu); the plan type is declared in ctp.h
@@ -164,6 +166,7 @@ cudaError_t batch_factor_class(const ctp_plan *P, int ci, const ctp_front *fr, c
 cudaError_t batch_solve(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 bool batch_solve_per_class(const ctp_plan *P);
 cudaError_t batch_solve_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, cudaStream_t st);
+cudaError_t batch_form_class(const ctp_plan *P, int ci, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 cudaError_t batch_form(const ctp_plan *P, const ctp_front *fr, char *w, int num_sms, cudaStream_t st);
 
 // Tensor-core Solve (solve_tc.cu): BF16 pieces of its operands, its scratch

@@ -91,11 +91,13 @@ __global__ void __launch_bounds__(kTh)
 
 // Batched: CTA b takes work item b = (front, triangular 64 x 64 tile of its S):
 // S lower-packed per front, or (kSub) subtracted from the front's full
-// column-major S (leading dimension lds).
+// column-major S (leading dimension lds).  The front is item_front[b], the tile
+// item_tile[b] (or, without that list, the item's place among the front's
+// consecutive items).
 template <typename OutT, bool kSub = false>
 __global__ void __launch_bounds__(kTh)
     k_form_fp64_batch(const ctp_front *__restrict__ fronts, const BFront *__restrict__ tab, char *ws,
-                      const int *__restrict__ item_front, BatchOpts o) {
+                      const int *__restrict__ item_front, const int *__restrict__ item_tile, BatchOpts o) {
     const int f = item_front[blockIdx.x];
     const ctp_front fr = fronts[f];
     const BFront bt = tab[f];
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kTh)
     const BSection sec = bsection(bt.n, bt.p, &oo);
     const double *W21 = reinterpret_cast<const double *>(ws + bt.ws + sec.W21);
     form_tile<OutT, !kSub, kSub>(fr.A + bt.p, fr.lda, W21, bt.m, bt.m, *fr.nelim, (OutT *)fr.S, fr.lds,
-                                 (int64_t)blockIdx.x - bt.f0);
+                                 item_tile != nullptr ? (int64_t)item_tile[blockIdx.x] : (int64_t)blockIdx.x - bt.f0);
 }
 
 
@@ -139,14 +141,15 @@ cudaError_t launch_form_fp64(const double *L21, int64_t ldl, const double *W21, 
 
 cudaError_t launch_form_fp64_batch(const ctp_front *fronts, const BFront *tab, char *ws,
                                    const int *item_front, int64_t items, BatchOpts o,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, const int *item_tile) {
     if (items == 0) return cudaSuccess;
     if (o.smode == CTP_S_FP64_SUB)
-        k_form_fp64_batch<double, true><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);
+        k_form_fp64_batch<double, true>
+            <<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, item_tile, o);
     else if (o.smode == CTP_S_FP64_PACKED)
-        k_form_fp64_batch<double><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);
+        k_form_fp64_batch<double><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, item_tile, o);
     else
-        k_form_fp64_batch<float><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, o);
+        k_form_fp64_batch<float><<<(unsigned)items, kTh, 0, st>>>(fronts, tab, ws, item_front, item_tile, o);
     return cudaGetLastError();
 }
 

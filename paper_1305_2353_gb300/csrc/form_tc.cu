@@ -123,6 +123,7 @@ struct BatchTab {
     const BFront *tab;
     const int *item_front;
     int layout;  // 2: S in 128 x 128 blocks; 3: subtracted from the front's full FP64 S (lds)
+    const int *item_tile;  // each item's tile of its front (nullptr: items of a front are consecutive from f0)
 };
 
 // Which tiles a CTA takes.  mode 0: round robin over the column-block-major
@@ -151,7 +152,7 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
         if (t >= (s.mode == 2 ? s.t1 : s.ntiles)) return false;
         const int f = bt.item_front[t];
         const BFront b = bt.tab[f];
-        decode_tile(t - b.f0, b.nM, R, ti, tj);
+        decode_tile(bt.item_tile != nullptr ? (int64_t)bt.item_tile[t] : t - b.f0, b.nM, R, ti, tj);
         const int e = *bt.fronts[f].nelim;
         x.ti = ti;
         x.tj = tj;
@@ -583,7 +584,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     sc.c = blockIdx.x >> 1;
     sc.t0 = sc.ntiles * sc.c / sc.G;
     sc.t1 = sc.ntiles * (sc.c + 1) / sc.G;
-    const BatchTab none = {nullptr, nullptr, nullptr, 0};
+    const BatchTab none = {nullptr, nullptr, nullptr, 0, nullptr};
 #define TILE_P(k, x) tile_k<false, 1>((k), sc, KB1, m, S, lds, layout, none, (x))
     auto raise_abort = [&]() {
         atomicExch(&bars.abort, 1);
@@ -928,7 +929,7 @@ cudaError_t launch_form_tc(const void *Wb, const void *Lb, int64_t piece_off, in
         return cudaGetLastError();
     }
     const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-    BatchTab none = {nullptr, nullptr, nullptr, 0};
+    BatchTab none = {nullptr, nullptr, nullptr, 0, nullptr};
     if (pieces == 1) return launch_p<false, 1>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
     if (pieces == 2) return launch_p<false, 2>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
     return launch_p<false, 3>(grid, mW, mL, m, nelim, S, lds, layout, info, 0, none, mode, st);
@@ -941,14 +942,15 @@ int64_t form_tc_tiles(int64_t m, int pieces) {
 
 cudaError_t launch_form_tc_batch(const ctp_front *fronts, const BFront *tab, const int *item_front,
                                  int64_t items, int64_t total_rows, const void *Wb, const void *Lb,
-                                 int pieces, int layout, int32_t *info, int num_sms, cudaStream_t st) {
+                                 int pieces, int layout, int32_t *info, int num_sms, cudaStream_t st,
+                                 const int *item_tile) {
     if (items == 0) return cudaSuccess;
     if (pieces < 1 || pieces > 3) return cudaErrorInvalidValue;
     CUtensorMap mW[3], mL[3];
     if (!make_maps(mW, mL, Wb, Lb, total_rows * kBatchKp, pieces, total_rows, kBatchKp))
         return cudaErrorInvalidValue;
     const int grid = (int)(items < num_sms ? items : num_sms);
-    BatchTab bt = {fronts, tab, item_front, layout};
+    BatchTab bt = {fronts, tab, item_front, layout, item_tile};
     if (pieces == 1) return launch_p<true, 1>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
     if (pieces == 2) return launch_p<true, 2>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
     return launch_p<true, 3>(grid, mW, mL, 0, nullptr, nullptr, 0, 2, info, items, bt, 2, st);
