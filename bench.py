@@ -53,10 +53,10 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # number of S entries; the Solve's is proportional to the rows of A21): see
 # profiles/ for the captures.
 NCU_TRAFFIC = {
-    # ncu --set full, n=20000 p=256 relaxed, S FP64 lower-packed: 163.76 MB read +
-    # 1513.69 MB written for m(m+1)/2 = 194,921,640 entries
-    "form_fp64": {"file": "form.cu", "sha1": "798d569f67e7e8f417e75b162e2622426e55e05e",
-                  "unit": "packed_entry", "bytes_per_unit": (163.760384e6 + 1513.690e6) / 194921640},
+    # ncu --set full, n=20000 p=256 relaxed, S FP64 lower-packed: 163.66 MB read +
+    # 1512.10 MB written for m(m+1)/2 = 194,921,640 entries
+    "form_fp64": {"file": "form.cu", "sha1": "bed329d47e2e3d13657366883dcf61b1968adf7a",
+                  "unit": "packed_entry", "bytes_per_unit": (163.662592e6 + 1512.099e6) / 194921640},
     # ncu --set full, n=40000 p=256 relaxed, split BF16 on SM pairs, S FP32 in 128x128
     # blocks: 88.03 MB read + 3118.41 MB written for 48,516 blocks of 16,384 entries
     "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "c4a552e28a454e98fc4698e1b898fff9da558d1b",

@@ -40,8 +40,7 @@ __device__ __forceinline__ void form_tile(const double *__restrict__ L21, int64_
             sl[kk][rr] = (k < e && gj < m) ? L21[(int64_t)k * ldl + gj] : 0.0;
         }
         __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kK; kk++) {
+        auto step = [&](int kk) {
             double a[4], bb[4];
 #pragma unroll
             for (int q = 0; q < 4; q++) {
@@ -52,6 +51,14 @@ __device__ __forceinline__ void form_tile(const double *__restrict__ L21, int64_
             for (int q = 0; q < 4; q++)
 #pragma unroll
                 for (int s = 0; s < 4; s++) acc[q][s] += a[q] * bb[s];
+        };
+        if (k0 + kK <= e) {
+#pragma unroll
+            for (int kk = 0; kk < kK; kk++) step(kk);
+        } else {
+            // the last slab: only its e - k0 real terms (the FP64 pipe is the
+            // bound, and small e -- a few dozen -- is common in batches)
+            for (int kk = 0; kk < e - k0; kk++) step(kk);
         }
         __syncthreads();
     }
