@@ -58,9 +58,9 @@ NCU_TRAFFIC = {
     "form_fp64": {"file": "form.cu", "sha1": "bed329d47e2e3d13657366883dcf61b1968adf7a",
                   "unit": "packed_entry", "bytes_per_unit": (163.662592e6 + 1512.099e6) / 194921640},
     # ncu --set full, n=40000 p=256 relaxed, split BF16 on SM pairs, S FP32 in 128x128
-    # blocks: 88.03 MB read + 3118.41 MB written for 48,516 blocks of 16,384 entries
-    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "c4a552e28a454e98fc4698e1b898fff9da558d1b",
-                       "unit": "tiled_entry", "bytes_per_unit": (88.028160e6 + 3118.409e6) / (48516 * 16384)},
+    # blocks: 89.63 MB read + 3118.79 MB written for 48,516 blocks of 16,384 entries
+    "form_tc_bf16x3": {"file": "form_tc.cu", "sha1": "488eb8cb39a135fe2b96ff90b589d43a008cdf37",
+                       "unit": "tiled_entry", "bytes_per_unit": (89.629184e6 + 3118.794e6) / (48516 * 16384)},
     # ncu --set full, n=40000 p=256 relaxed, tensor-core Solve before a split-BF16
     # Form (prep + gather + GEMM): 144.97 MB read + 124.87 MB written for 39,744 rows
     "solve_tc": {"file": "solve_tc.cu", "sha1": "986f68bd883bd413248fac53507ed870abbd31cb", "prec": "bf16x3",

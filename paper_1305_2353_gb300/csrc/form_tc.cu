@@ -112,6 +112,7 @@ __device__ __forceinline__ void decode_tile(int64_t t, int nM, int R, int &ti, i
 // Everything the roles need to know about one tile of work.
 struct TileInfo {
     int ti, tj, KB, key;  // key: identifies the resident L21 block (front and column block)
+    int klast;            // 16-wide K-steps of the last K block that hold columns below e
     int64_t arow, brow;   // first rows of the W21 / L21 boxes in the operand buffers
     int64_t m, nb, lds;
     float *S;
@@ -144,7 +145,7 @@ struct Sched {
 };
 
 template <bool kBatch, int R>
-__device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64_t m1, float *S1,
+__device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int e1, int64_t m1, float *S1,
                                        int64_t lds1, int layout1, const BatchTab &bt, TileInfo &x) {
     int ti, tj;
     if (kBatch) {
@@ -157,6 +158,7 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
         x.ti = ti;
         x.tj = tj;
         x.KB = (e + kBK - 1) / kBK;
+        x.klast = (e - (x.KB - 1) * kBK + kUmmaK - 1) / kUmmaK;
         x.key = f * 65536 + tj;
         x.arow = b.row0 + (int64_t)ti * kBM;
         x.brow = b.row0 + (int64_t)tj * R * kBM;
@@ -190,7 +192,8 @@ __device__ __forceinline__ bool tile_k(int64_t k, const Sched &s, int KB1, int64
     }
     x.ti = ti;
     x.tj = tj;
-    x.KB = KB1;
+    x.KB = (e1 + kBK - 1) / kBK;
+    x.klast = (e1 - (x.KB - 1) * kBK + kUmmaK - 1) / kUmmaK;
     x.key = tj;
     x.arow = (int64_t)ti * kBM;
     x.brow = (int64_t)tj * R * kBM;
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     uint8_t *sB = smem;                       // [kMaxKB][StageB]: resident L21 block (P <= 2)
     uint8_t *sA = smem + C::ResidentBytes;    // [NS][StageA]: W21 ring (and L21 for P = 3)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int KB1 = kBatch ? 0 : (*nelim_p + kBK - 1) / kBK;
+    const int e1 = kBatch ? 0 : *nelim_p;
     Sched sc;
     sc.mode = sched_mode;
     sc.nM = kBatch ? 0 : (int)((m_single + kBM - 1) / kBM);
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     sc.c = blockIdx.x;
     sc.t0 = sc.ntiles * sc.c / sc.G;
     sc.t1 = sc.ntiles * (sc.c + 1) / sc.G;
-#define TILE_K(k, x) tile_k<kBatch, R>((k), sc, KB1, m_single, S_single, lds_single, layout_single, btab, (x))
+#define TILE_K(k, x) tile_k<kBatch, R>((k), sc, e1, m_single, S_single, lds_single, layout_single, btab, (x))
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; s++) {
@@ -410,8 +413,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     const uint32_t a0 = smem_u32(sA + (size_t)stage * C::StageA);
                     const uint32_t b0 = C::kResident ? smem_u32(sB + (size_t)kb * C::StageB)
                                                      : a0 + P * C::PieceA;
+                    // the operands are zero past column e: the last block runs only
+                    // the K-steps that reach below e
+                    const int nkk = kb == x.KB - 1 ? x.klast : kBK / kUmmaK;
 #pragma unroll
                     for (int kk = 0; kk < kBK / kUmmaK; kk++) {
+                        if (kk >= nkk) break;
                         // advance 16 BF16 = 32 bytes along K inside the swizzled rows;
                         // products of pieces i, j with i + j <= P - 1.  Split forms:
                         // B pieces 0 and 1 side by side as one N = 256 operand, so
@@ -572,7 +579,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     uint8_t *sA = smem + C::ResidentBytes;  // [NS][StageA]: this CTA's 128 W21 rows, hi and lo
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
-    const int KB1 = (*nelim_p + kBK - 1) / kBK;
+    const int e1 = *nelim_p;
     const int nM2 = (int)((m + 255) / 256);  // 256-row blocks
     const int64_t nb128 = (m + kBM - 1) / kBM;
     Sched sc;
@@ -585,7 +592,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     sc.t0 = sc.ntiles * sc.c / sc.G;
     sc.t1 = sc.ntiles * (sc.c + 1) / sc.G;
     const BatchTab none = {nullptr, nullptr, nullptr, 0, nullptr};
-#define TILE_P(k, x) tile_k<false, 1>((k), sc, KB1, m, S, lds, layout, none, (x))
+#define TILE_P(k, x) tile_k<false, 1>((k), sc, e1, m, S, lds, layout, none, (x))
     auto raise_abort = [&]() {
         atomicExch(&bars.abort, 1);
         st_remote_u32(peer_addr(&bars.abort, rank ^ 1u), 1u);
@@ -730,8 +737,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + (size_t)stage * C::StageA);
                     const uint32_t b0 = smem_u32(sB + (size_t)kb * C::StageB);
+                    const int nkk = kb == x.KB - 1 ? x.klast : kBK / kUmmaK;  // zero past column e
 #pragma unroll
                     for (int kk = 0; kk < kBK / kUmmaK; kk++) {
+                        if (kk >= nkk) break;
                         const uint64_t ah = sdesc(a0 + kk * 32), al = sdesc(a0 + C::PieceA + kk * 32);
                         const uint64_t bh = sdesc(b0 + kk * 32), bl = sdesc(b0 + C::PieceB + kk * 32);
                         umma_bf16_pair(dt, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);  // hi*hi
