@@ -23,6 +23,45 @@ namespace {
 constexpr int kRows = 32;   // rows per tile (one per lane)
 constexpr int kWarps = 8;   // warps per CTA: warp w updates the columns k = w (mod 8)
 
+// The BF16 pieces of the first e columns of a tile's rows (rows of xs, [k][kRows+1])
+// into the K-major operand copy B (row brow of B is the tile's first row), each
+// piece rounding what the previous ones left (lo_off elements apart), and
+// zeros from e to Kz.  Every thread of the CTA takes (row, column pair) items
+// of the real columns, so that lanes do not idle on the zero tail (the
+// conversions cost about a nanosecond per value per SM).
+__device__ __forceinline__ void write_pieces(__nv_bfloat16 *__restrict__ B, int64_t brow, int rows, int Kp, int e,
+                                             int Kz, int pieces, int64_t lo_off, const double *xs) {
+    constexpr int LDX = kRows + 1;
+    const int eh = (e + 1) >> 1, zn = (Kz >> 1) - eh;
+    for (int t = threadIdx.x; t < rows * eh; t += blockDim.x) {
+        const int rr = t / eh, k = 2 * (t - rr * eh);
+        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(B + (brow + rr) * Kp) + (k >> 1);
+        const double v0 = xs[k * LDX + rr];
+        const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
+        __nv_bfloat162 b;
+        b.x = __double2bfloat16(v0);
+        b.y = __double2bfloat16(v1);
+        dst[0] = b;
+        double r0 = v0 - (double)__bfloat162float(b.x);
+        double r1 = v1 - (double)__bfloat162float(b.y);
+        for (int pc = 1; pc < pieces; pc++) {
+            __nv_bfloat162 l;
+            l.x = __double2bfloat16(r0);
+            l.y = __double2bfloat16(r1);
+            dst[pc * (lo_off / 2)] = l;
+            r0 -= (double)__bfloat162float(l.x);
+            r1 -= (double)__bfloat162float(l.y);
+        }
+    }
+    if (zn <= 0) return;
+    const __nv_bfloat162 z = __floats2bfloat162_rn(0.0f, 0.0f);
+    for (int t = threadIdx.x; t < rows * zn; t += blockDim.x) {
+        const int rr = t / zn, k2 = eh + (t - rr * zn);
+        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(B + (brow + rr) * Kp) + k2;
+        for (int pc = 0; pc < pieces; pc++) dst[pc * (lo_off / 2)] = z;
+    }
+}
+
 // Right-looking substitution over a tile of 32 rows: for each eliminated
 // position j, every warp reads y_j of its lane's row and updates its share of
 // the later columns; a CTA barrier separates consecutive pivots.  Eight warps
@@ -75,37 +114,10 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
 
     // BF16 copy of Y = W21 for the tensor-core Form: row-major, K contiguous,
     // zero from e to the end of e's last 64-wide K block (the Form reads no
-    // further; a batch's rows are 256 wide whatever the front's p), a warp
-    // writing one row at a time (coalesced)
+    // further; a batch's rows are 256 wide whatever the front's p)
     const int Kz = min(Kp, (e + 63) / 64 * 64);
-    if (Wb != nullptr) {
-        for (int rr = w; rr < kRows; rr += kWarps) {
-            const int64_t rw = row0 + rr;
-            if (rw >= m) break;
-            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Wb + (brow0 + rw) * Kp);
-            for (int k2 = lane; k2 < Kz / 2; k2 += 32) {
-                const int k = 2 * k2;
-                const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
-                const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
-                __nv_bfloat162 b;
-                b.x = __double2bfloat16(v0);
-                b.y = __double2bfloat16(v1);
-                dst[k2] = b;
-                if (pieces > 1) {  // split operands: each piece rounds what the previous left
-                    double r0 = v0 - (double)__bfloat162float(b.x);
-                    double r1 = v1 - (double)__bfloat162float(b.y);
-                    for (int pc = 1; pc < pieces; pc++) {
-                        __nv_bfloat162 l;
-                        l.x = __double2bfloat16(r0);
-                        l.y = __double2bfloat16(r1);
-                        dst[k2 + pc * (lo_off / 2)] = l;
-                        r0 -= (double)__bfloat162float(l.x);
-                        r1 -= (double)__bfloat162float(l.y);
-                    }
-                }
-            }
-        }
-    }
+    const int tile_rows = m - row0 < kRows ? (int)(m - row0) : kRows;
+    if (Wb != nullptr) write_pieces(Wb, brow0 + row0, tile_rows, Kp, e, Kz, pieces, lo_off, xs);
     // W21 = Y (= L21 D11) for the FP64 Form step, L21 = Y D11^{-1}, delayed columns
     constexpr int kPer = kMaxP / kWarps;
     double lv[kPer];
@@ -143,32 +155,7 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
             if (k < e) xs[k * LDX + lane] = lv[q];
         }
         __syncthreads();
-        for (int rr = w; rr < kRows; rr += kWarps) {
-            const int64_t rw = row0 + rr;
-            if (rw >= m) break;
-            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Lb + (brow0 + rw) * Kp);
-            for (int k2 = lane; k2 < Kz / 2; k2 += 32) {
-                const int k = 2 * k2;
-                const double v0 = k < e ? xs[k * LDX + rr] : 0.0;
-                const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
-                __nv_bfloat162 b;
-                b.x = __double2bfloat16(v0);
-                b.y = __double2bfloat16(v1);
-                dst[k2] = b;
-                if (pieces > 1) {  // split operands: each piece rounds what the previous left
-                    double r0 = v0 - (double)__bfloat162float(b.x);
-                    double r1 = v1 - (double)__bfloat162float(b.y);
-                    for (int pc = 1; pc < pieces; pc++) {
-                        __nv_bfloat162 l;
-                        l.x = __double2bfloat16(r0);
-                        l.y = __double2bfloat16(r1);
-                        dst[k2 + pc * (lo_off / 2)] = l;
-                        r0 -= (double)__bfloat162float(l.x);
-                        r1 -= (double)__bfloat162float(l.y);
-                    }
-                }
-            }
-        }
+        write_pieces(Lb, brow0 + row0, tile_rows, Kp, e, Kz, pieces, lo_off, xs);
     }
 }
 
