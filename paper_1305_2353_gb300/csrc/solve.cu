@@ -23,21 +23,36 @@ namespace {
 constexpr int kRows = 32;   // rows per tile (one per lane)
 constexpr int kWarps = 8;   // warps per CTA: warp w updates the columns k = w (mod 8)
 
-// The BF16 pieces of the first e columns of a tile's rows (rows of xs, [k][kRows+1])
-// into the K-major operand copy B (row brow of B is the tile's first row), each
+// Entry k of row rr of L21 = Y D11^{-1}, from the rows of Y in xs ([k][kRows+1]):
+// 1x1 and 2x2 blocks of D11^{-1}; zero pivots give 0.
+__device__ __forceinline__ double l21_of(const double *xs, int k, int rr, const int32_t *__restrict__ piv,
+                                         const double *__restrict__ Dinv) {
+    constexpr int LDX = kRows + 1;
+    const int kd = piv[k];
+    const double y = xs[k * LDX + rr];
+    if (kd == CTP_PIVKIND_1X1) return y * Dinv[2 * k];
+    if (kd == CTP_PIVKIND_2X2_FIRST) return __fma_rn(xs[(k + 1) * LDX + rr], Dinv[2 * k + 1], y * Dinv[2 * k]);
+    if (kd == CTP_PIVKIND_2X2_SECOND) return __fma_rn(y, Dinv[2 * k], xs[(k - 1) * LDX + rr] * Dinv[2 * k - 1]);
+    return 0.0;
+}
+
+// The BF16 pieces of the first e columns of a tile's rows (rows of Y in xs, or
+// with kL the rows of L21 computed from them) into the K-major operand copy B (row brow of B is the tile's first row), each
 // piece rounding what the previous ones left (lo_off elements apart), and
 // zeros from e to Kz.  Every thread of the CTA takes (row, column pair) items
 // of the real columns, so that lanes do not idle on the zero tail (the
 // conversions cost about a nanosecond per value per SM).
+template <bool kL>
 __device__ __forceinline__ void write_pieces(__nv_bfloat16 *__restrict__ B, int64_t brow, int rows, int Kp, int e,
-                                             int Kz, int pieces, int64_t lo_off, const double *xs) {
+                                             int Kz, int pieces, int64_t lo_off, const double *xs,
+                                             const int32_t *__restrict__ piv, const double *__restrict__ Dinv) {
     constexpr int LDX = kRows + 1;
     const int eh = (e + 1) >> 1, zn = (Kz >> 1) - eh;
     for (int t = threadIdx.x; t < rows * eh; t += blockDim.x) {
         const int rr = t / eh, k = 2 * (t - rr * eh);
         __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(B + (brow + rr) * Kp) + (k >> 1);
-        const double v0 = xs[k * LDX + rr];
-        const double v1 = k + 1 < e ? xs[(k + 1) * LDX + rr] : 0.0;
+        const double v0 = kL ? l21_of(xs, k, rr, piv, Dinv) : xs[k * LDX + rr];
+        const double v1 = k + 1 < e ? (kL ? l21_of(xs, k + 1, rr, piv, Dinv) : xs[(k + 1) * LDX + rr]) : 0.0;
         __nv_bfloat162 b;
         b.x = __double2bfloat16(v0);
         b.y = __double2bfloat16(v1);
@@ -64,8 +79,11 @@ __device__ __forceinline__ void write_pieces(__nv_bfloat16 *__restrict__ B, int6
 
 // Right-looking substitution over a tile of 32 rows: for each eliminated
 // position j, every warp reads y_j of its lane's row and updates its share of
-// the later columns; a CTA barrier separates consecutive pivots.  Eight warps
-// per CTA (and three CTAs per SM) keep all four FP64 pipes of an SM busy.
+// the later columns (four independent updates in flight per warp); a CTA
+// barrier separates consecutive pivots.  The outputs are computed from the
+// rows of Y in shared memory without a register copy, so that a CTA needs few
+// registers and as many CTAs fit on an SM as its shared memory allows (three at
+// p = 256, more for narrower fronts): enough warps for all four FP64 pipes.
 // One 32-row tile.  brow0: row of this front's first A21 row in the BF16
 // operand copies (0 for a single supernode; the stacked offset in a batch).
 // pieces > 1: also write the further BF16 pieces of the split operands (piece
@@ -98,6 +116,7 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
         if (kd == CTP_PIVKIND_2X2_FIRST) {
             const double y0 = xs[j * LDX + lane], y1 = xs[(j + 1) * LDX + lane];
             const double *l0 = A + (int64_t)j * lda, *l1 = A + (int64_t)(j + 1) * lda;
+#pragma unroll 4
             for (int k = j + 2 + w; k < p; k += kWarps)
                 xs[k * LDX + lane] -= y0 * __ldg(l0 + k) + y1 * __ldg(l1 + k);
             j += 2;
@@ -105,6 +124,7 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
             if (kd == CTP_PIVKIND_1X1) {
                 const double y0 = xs[j * LDX + lane];
                 const double *l0 = A + (int64_t)j * lda;
+#pragma unroll 4
                 for (int k = j + 1 + w; k < p; k += kWarps) xs[k * LDX + lane] -= y0 * __ldg(l0 + k);
             }
             j += 1;  // zero pivots have an all-zero L column
@@ -117,46 +137,22 @@ __device__ __forceinline__ void solve_tile(double *__restrict__ A, int64_t n, in
     // further; a batch's rows are 256 wide whatever the front's p)
     const int Kz = min(Kp, (e + 63) / 64 * 64);
     const int tile_rows = m - row0 < kRows ? (int)(m - row0) : kRows;
-    if (Wb != nullptr) write_pieces(Wb, brow0 + row0, tile_rows, Kp, e, Kz, pieces, lo_off, xs);
-    // W21 = Y (= L21 D11) for the FP64 Form step, L21 = Y D11^{-1}, delayed columns
-    constexpr int kPer = kMaxP / kWarps;
-    double lv[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; q++) {
-        const int k = w + q * kWarps;
-        lv[q] = 0.0;
-        if (k >= p) continue;
-        const double y = xs[k * LDX + lane];
+    if (Wb != nullptr) write_pieces<false>(Wb, brow0 + row0, tile_rows, Kp, e, Kz, pieces, lo_off, xs, piv, Dinv);
+    // W21 = Y (= L21 D11) for the FP64 Form step, L21 = Y D11^{-1} in place, the
+    // delayed columns as they are.  xs is only read from here on.
+    for (int k = w; k < p; k += kWarps) {
+        if (!valid) break;
         double out;
         if (k >= e) {
-            out = y;
+            out = xs[k * LDX + lane];
         } else {
-            if (W21 != nullptr && valid) W21[(int64_t)k * ldw + row] = y;
-            const int kd = piv[k];
-            if (kd == CTP_PIVKIND_1X1) {
-                out = y * Dinv[2 * k];
-            } else if (kd == CTP_PIVKIND_2X2_FIRST) {
-                out = y * Dinv[2 * k] + xs[(k + 1) * LDX + lane] * Dinv[2 * k + 1];
-            } else if (kd == CTP_PIVKIND_2X2_SECOND) {
-                out = xs[(k - 1) * LDX + lane] * Dinv[2 * (k - 1) + 1] + y * Dinv[2 * k];
-            } else {
-                out = 0.0;
-            }
+            if (W21 != nullptr) W21[(int64_t)k * ldw + row] = xs[k * LDX + lane];
+            out = l21_of(xs, k, lane, piv, Dinv);
         }
-        lv[q] = out;
-        if (valid) A21[(int64_t)k * lda + row] = out;
+        A21[(int64_t)k * lda + row] = out;
     }
     // BF16 copy of L21 for the tensor-core Form
-    if (Lb != nullptr) {
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kPer; q++) {
-            const int k = w + q * kWarps;
-            if (k < e) xs[k * LDX + lane] = lv[q];
-        }
-        __syncthreads();
-        write_pieces(Lb, brow0 + row0, tile_rows, Kp, e, Kz, pieces, lo_off, xs);
-    }
+    if (Lb != nullptr) write_pieces<true>(Lb, brow0 + row0, tile_rows, Kp, e, Kz, pieces, lo_off, xs, piv, Dinv);
 }
 
 __global__ void __launch_bounds__(kRows * kWarps)
