@@ -361,6 +361,17 @@ ctp_status ctp_batch_plan_create(ctp_ctx *ctx, int32_t nb, const int64_t *n_host
         ldmaxK[key] = std::max(ldmaxK[key], p + R);
         if (k.kind != kFactorWarp) smemK[key] = std::max(smemK[key], factor_smem_bytes(p, R, k.G));
     }
+    // within a class, the fronts with the most pivot-search work first (about
+    // p^2 (p + R) terms), so that no large front starts in the launch's last
+    // wave; the results do not depend on the order
+    for (int key = 0; key < kNumKeys; key++) {
+        auto work = [&](int f) {
+            const int64_t p = tab[f].p, m = tab[f].m;
+            const int64_t R = opt->pivot == CTP_PIV_STRICT ? (m < p ? m : p) : 0;
+            return p * p * (p + R);
+        };
+        std::stable_sort(byKey[key].begin(), byKey[key].end(), [&](int x, int y) { return work(x) > work(y); });
+    }
     std::vector<int> lists, csitem, cstile, cfitem, cftile;
     for (int key = 0; key < kNumKeys; key++) {
         if (byKey[key].empty()) continue;
