@@ -139,6 +139,72 @@ __device__ __forceinline__ double neg_bits(double x) {
 // bits(x) < bits(y) as unsigned integers), and keep FP64 arithmetic for the
 // products, sums and reciprocals whose rounding the test defines.
 
+// FP32 filters in front of the FP64 tests.  Most candidates of a strict front
+// fail their tests, and a failing test's FP64 instructions (a reciprocal and a
+// dozen products) are most of its latency.  Where FP32 arithmetic with wide
+// error margins already proves the outcome the FP64 test would reach, the
+// FP64 test is skipped; every other case runs it unchanged, so the decisions
+// are exactly those of the FP64 test.
+//
+// key_f32: binary32 value of a magnitude key whose binary exponent lies in
+// [-32, 32] (or 0): same exponent, the top 23 mantissa bits (truncated, so
+// 0 <= |x| - f < 2^-23 |x|).  Integer instructions only; false out of range.
+__device__ __forceinline__ bool key_f32(unsigned long long k, float &f) {
+    if (k == 0ull) {
+        f = 0.0f;
+        return true;
+    }
+    const unsigned e = (unsigned)(k >> 52);
+    if (e < 1023u - 32u || e > 1023u + 32u) return false;
+    f = __uint_as_float((unsigned)((k >> 29) - (896ull << 23)));
+    return true;
+}
+
+// true when the 2x2 test below surely rejects (t, m).  With inputs truncated
+// by < 2^-23 and a handful of FP32 roundings (2^-24 each), every FP32 product
+// here is within 2^-20 of the FP64 value the test computes (whose own
+// roundings are 2^-53), so:
+//   |detpiv - det| <= 2^-20 (|d0| + |d1|) + 2^-24 |det| < err = 2^-16 (p0 + p1 + |det|),
+//   glow = (1 - 2^-16) max(p0, p1) / 2 <= max(|d0|, |d1|) / 2 <= guard,
+// and |det| + err < glow proves |detpiv| <= guard.  Likewise the growth test
+// fails for sure when (1 - 2^-16) gt_f exceeds an upper bound of
+// lim = |detpiv| / u, which the FP64 test only evaluates when the column
+// maxima reach `small` (the same integer condition here).
+__device__ __forceinline__ bool reject_2x2_f32(double a_tt, double a_tm, double a_mm, unsigned long long ktt,
+                                               unsigned long long ktm, unsigned long long kmm,
+                                               unsigned long long kmax, unsigned long long maxt,
+                                               unsigned long long maxm, double rcp_u, unsigned long long small_k) {
+    float ftt, ftm, fmm, fmax;
+    if (kmax == 0ull || !key_f32(ktt, ftt) || !key_f32(ktm, ftm) || !key_f32(kmm, fmm) || !key_f32(kmax, fmax))
+        return false;
+    const float ds = 1.0f / fmax;
+    const float p0 = (fmm * ds) * ftt;  // |detpiv0| = |a_mm| |a_tt| / amax
+    const float p1 = (ftm * ds) * ftm;  // detpiv1 = a_tm^2 / amax >= 0
+    const bool neg0 = (__double_as_longlong(a_mm) ^ __double_as_longlong(a_tt)) < 0;
+    const float adet = fabsf((neg0 ? -p0 : p0) - p1);
+    const float err = 0x1p-16f * (p0 + p1 + adet);
+    const float glow = 0.5f * fmaxf(p0, p1) * (1.0f - 0x1p-16f);
+    if (adet + err < glow) return true;
+    if ((maxm > maxt ? maxm : maxt) < small_k) return false;  // the FP64 test accepts without growth test
+    float fvt, fvm, fru;
+    if (!key_f32(maxt, fvt) || !key_f32(maxm, fvm) || !key_f32(akey(rcp_u), fru) || fru > 0x1p20f) return false;
+    const float lim_up = (adet + err) * (fru * (1.0f + 0x1p-21f)) * (1.0f + 0x1p-16f);
+    const float gt = (fmm * fvt + ftm * fvm) * ds;
+    const float gm = (ftm * fvt + ftt * fvm) * ds;
+    return gt * (1.0f - 0x1p-16f) > lim_up || gm * (1.0f - 0x1p-16f) > lim_up;
+}
+
+// The 1x1 test |a_mm| >= u * maxm1 (rounded in FP64) decided in FP32 when the
+// margin is wide: 1 accept, 0 reject, -1 undecided (run the FP64 test).
+__device__ __forceinline__ int test_1x1_f32(unsigned long long kmm, unsigned long long maxm1, double u) {
+    float fmm, fmx, fu;
+    if (!key_f32(kmm, fmm) || !key_f32(maxm1, fmx) || !key_f32(akey(u), fu)) return -1;
+    const float lim = fu * fmx;  // u maxm1 (1 - 2^-22) <= lim <= u maxm1 (1 + 2^-24)
+    if (fmm * (1.0f + 0x1p-16f) < lim * (1.0f - 0x1p-16f)) return 0;
+    if (fmm * (1.0f - 0x1p-16f) > lim * (1.0f + 0x1p-16f)) return 1;
+    return -1;
+}
+
 // |x| / 2 as a key: an exponent decrement, exact for normal x above the
 // smallest binade; the rare others take the FP64 product.
 __device__ __forceinline__ unsigned long long half_key(unsigned long long k) {
@@ -156,6 +222,7 @@ __device__ __forceinline__ bool test_2x2(double a_tt, double a_tm, double a_mm, 
     unsigned long long kmax = ktt > ktm ? ktt : ktm;
     kmax = kmm > kmax ? kmm : kmax;
     if (kmax < small_k) return false;
+    if (reject_2x2_f32(a_tt, a_tm, a_mm, ktt, ktm, kmm, kmax, maxt, maxm, rcp_u, small_k)) return false;
     // 1/amax correctly rounded: the same value as the division 1.0/amax
     const double detscale = __drcp_rn(key_val(kmax));
     const double detpiv1 = __dmul_rn(__dmul_rn(a_tm, detscale), a_tm);
@@ -284,7 +351,8 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
         }
         maxm1 = ktm > vm ? ktm : vm;
     }
-    if (kmm >= akey(__dmul_rn(u, key_val(maxm1)))) {
+    const int f1 = test_1x1_f32(kmm, maxm1, u);
+    if (f1 == 1 || (f1 < 0 && kmm >= akey(__dmul_rn(u, key_val(maxm1))))) {
         d.kind = DEC_1X1;
         d.d0 = amm;
         d.i0 = __drcp_rn(amm);
