@@ -231,6 +231,42 @@ def test_factor_matches_oracle(ctx, pivot, n, p, seed):
     compare(ref, got, p, A)
 
 
+def _boundary_case(kind, s, delta):
+    """A tiny supernode whose first threshold test of the given kind sits a
+    relative distance of about delta from its bound, on the side s (+1 or -1):
+    1x1: |a_mm| = u (1 + s delta) against u max|a21| = u (Listing 1's 1x1 test);
+    det: the 2x2 [[1, x], [x, 1]] with x^2 = (1 + s delta) / 2 against the
+         cancellation guard |det| <= max(|d0|, |d1|) / 2;
+    grow: the 2x2 [[1, .3], [.3, -1]] with both column maxima v = 109/1.3 (1 + s delta)
+         against the growth bound |D^-1| (maxt, maxm)^T <= 1/u (eq. (2.2))."""
+    if kind == "1x1":
+        return np.array([[0.01 * (1.0 + s * delta)], [1.0]]), 1
+    if kind == "det":
+        x = np.sqrt(0.5 * (1.0 + s * delta))
+        return np.array([[1.0, x], [x, 1.0], [0.01, 0.01]]), 2
+    v = 109.0 / 1.3 * (1.0 + s * delta)
+    return np.array([[1.0, 0.3], [0.3, -1.0], [v, v]]), 2
+
+
+@pytest.mark.parametrize("kind,logkind", [("1x1", 5), ("det", 2), ("grow", 4)])
+@pytest.mark.parametrize("pivot", ["strict", "relaxed", "tpp"])
+def test_threshold_tests_near_their_bounds(ctx, kind, logkind, pivot):
+    """Decisions on both sides of each threshold test's bound, from far (1e-2)
+    to within 1e-8 of it: the kernels decide the clear cases in FP32 with 2^-16
+    margins and leave the close ones to the FP64 test; either way the outcome,
+    pivots and factors equal the oracle's (and the two sides differ)."""
+    for delta in (1e-2, 1e-4, 3e-6, 1e-8):
+        outcomes = []
+        for s in (1.0, -1.0):
+            A, p = _boundary_case(kind, s, delta)
+            ref = O.factor(A, p, pivot, log_cap=1000)
+            first = [e for e in ref["log"] if e["kind"] == logkind]
+            assert first, (kind, pivot, delta, s)
+            outcomes.append(int(first[0]["outcome"]))
+            compare(ref, run_gpu(ctx, A, p, pivot), p, A)
+        assert outcomes[0] != outcomes[1], (kind, pivot, delta, outcomes)
+
+
 def test_single_small_workload(ctx):
     """n = 2000, p = 64, N(0,1), eight A11 rows/columns scaled by 1e-8."""
     for seed in range(3):
