@@ -111,13 +111,14 @@ struct Team<false> {
 __device__ __forceinline__ unsigned long long akey(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
+// Largest key of the warp: two single-instruction reductions on the 32-bit
+// halves (the high halves, then the low halves of the lanes that hold the
+// highest) instead of five shuffle steps on the 64-bit value.
 __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
+    const unsigned h = (unsigned)(v >> 32);
+    const unsigned H = __reduce_max_sync(0xffffffffu, h);
+    const unsigned L = __reduce_max_sync(0xffffffffu, h == H ? (unsigned)v : 0u);
+    return ((unsigned long long)H << 32) | L;
 }
 __device__ __forceinline__ double key_val(unsigned long long k) {
     return __longlong_as_double((long long)k);
@@ -299,16 +300,14 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
                 bi = j;
             }
         }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
-            bv = ov;
-            bi = oi;
-        }
-    }
-    const int t = bi;
+    // the warp's largest key among the lanes that have a candidate (lanes
+    // without one offer key 0, which never beats a candidate's key, and are
+    // left out of the index), then the lowest column holding it
+    const unsigned bh = bi >= 0 ? (unsigned)(bv >> 32) : 0u, bl = bi >= 0 ? (unsigned)bv : 0u;
+    const unsigned BH = __reduce_max_sync(0xffffffffu, bh);
+    const unsigned BL = __reduce_max_sync(0xffffffffu, bh == BH ? bl : 0u);
+    const int t0 = __reduce_min_sync(0xffffffffu, (bi >= 0 && bh == BH && bl == BL) ? bi : 0x7fffffff);
+    const int t = t0 == 0x7fffffff ? -1 : t0;
     // one pass over the live rows but t and c: the column maximum of c (and of
     // the partner's column); the zero test's maximum over every live row of c
     // adds rows t and c back
