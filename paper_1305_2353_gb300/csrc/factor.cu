@@ -290,16 +290,27 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     d.pad = 0;
     d.d0 = d.d1 = d.d2 = d.i0 = d.i1 = d.i2 = 0.0;
     // partner t: largest |a(c, j)| over live j < c, lowest j on ties
+    // (four rows per lane per step, their loads issued together; each lane
+    // visits its rows in ascending order, so it keeps the lowest on ties)
     unsigned long long bv = 0;
     int bi = -1;
-    for (int j = lane; j < c; j += 32)
-        if (live[j]) {
-            const unsigned long long k = akey(cm[j]);
-            if (bi < 0 || k > bv) {
-                bv = k;
-                bi = j;
-            }
+    constexpr int UP = 4;
+    for (int j0 = lane; j0 < c; j0 += 32 * UP) {
+        unsigned long long kq[UP];
+        bool lq[UP];
+#pragma unroll
+        for (int q = 0; q < UP; q++) {
+            const int j = j0 + 32 * q;
+            lq[q] = j < c && live[j];
+            kq[q] = j < c ? akey(cm[j]) : 0ull;
         }
+#pragma unroll
+        for (int q = 0; q < UP; q++)
+            if (lq[q] && (bi < 0 || kq[q] > bv)) {
+                bv = kq[q];
+                bi = j0 + 32 * q;
+            }
+    }
     // the warp's largest key among the lanes that have a candidate (lanes
     // without one offer key 0, which never beats a candidate's key, and are
     // left out of the index), then the lowest column holding it
@@ -316,16 +327,17 @@ __device__ __forceinline__ Decision test_candidate(int c, const double *cm, ColP
     constexpr int U = 4;
     for (int i0 = lane; i0 < LD; i0 += 32 * U) {
         double xm[U], xt[U];
+        bool lq[U];
 #pragma unroll
         for (int q = 0; q < U; q++) {
             const int i = i0 + 32 * q;
             xm[q] = i < LD ? cm[i] : 0.0;
             xt[q] = i < LD ? ct[i] : 0.0;
+            lq[q] = i < LD && (i >= p || (i != t && i != c && live[i]));
         }
 #pragma unroll
         for (int q = 0; q < U; q++) {
-            const int i = i0 + 32 * q;
-            if (i < LD && (i >= p || (i != t && i != c && live[i]))) {
+            if (lq[q]) {
                 const unsigned long long km = akey(xm[q]), kt = akey(xt[q]);
                 vm = km > vm ? km : vm;
                 vt = kt > vt ? kt : vt;
