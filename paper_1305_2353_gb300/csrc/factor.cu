@@ -493,9 +493,10 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
         round++;
         // ---------------- test round: the live candidates in [m, m + win)
         // (team-wide order); each CTA tests the ones it owns, one per warp.
-        // The window is 1 after an acceptance and doubles after a round with no
-        // pass, so accepted-first candidates cost a single test and runs of
-        // rejections are tested in parallel.
+        // The window is 1 after an acceptance and grows fourfold after a round
+        // with no pass, so accepted-first candidates cost a single test and runs
+        // of rejections are tested in parallel (a rejection is cheap: most are
+        // settled by the FP32 filters).
         const int hi = min(p, m + win);  // the same on every CTA
         if (warp == 0) {
             // this CTA's live columns in [m, hi), in order, go to its warps
@@ -545,7 +546,7 @@ __device__ __forceinline__ void factor_body(const FactorArgs &a, int G) {
             // every tested candidate before the window's end failed: the sweep
             // continues there, with a wider window
             m = hi;
-            win = win * 2 < win_max ? win * 2 : win_max;
+            win = win * 4 < win_max ? win * 4 : win_max;
             continue;
         }
         // the next search starts with a window of twice the distance this one
