@@ -134,6 +134,8 @@ def parse_args(argv=None):
                     help="skip the complete-system leg (2-node embedding, refinement)")
     ap.add_argument("--no-multifrontal", action="store_true",
                     help="skip the multifrontal leg (64^3 Laplacian)")
+    ap.add_argument("--no-delays", action="store_true",
+                    help="skip the delayed-pivot count leg of --all")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the extra measurement with the Form on the tensor cores")
     ap.add_argument("--all", action="store_true",
@@ -1092,7 +1094,7 @@ def run_native(a):
         rec["batch"] = batch
         del fronts
 
-    if a.all and rank == 0:
+    if a.all and rank == 0 and not a.no_delays:
         rec["delays"] = measure_delays(ctx, dev, inputs, a.batch_count, a.seed)
         for nm, v in rec["delays"].items():
             leg_summary("delays_" + nm, {m: d["delayed"] for m, d in v["by_method"].items()})
